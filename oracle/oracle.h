@@ -1,0 +1,103 @@
+/*
+ * oracle.h -- plain FP64 CPU reference ("oracle") of the RZ electrostatic
+ * PIC-MCC step of the dc magnetron model (arXiv:2507.10727).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library exists to check the CUDA library
+ * against an independent, slow, obviously correct implementation.  Only the
+ * test suite, the smoke check and the benchmark's CPU-baseline leg may load
+ * it.  It shares no code, header, table or constant with the CUDA library.
+ *
+ * Everything is double precision, single threaded, in the order the method
+ * states: gather -> Boris push -> walls / secondary emission -> MCC -> births
+ * -> deposit -> circuit -> Poisson.  Citations name the paper's sections,
+ * equations and Table 1; where the paper is silent the comment says which
+ * reading is taken (the readings are listed with the design notes).
+ *
+ * Parity status per function (what pins it, in tests/test_oracle_*.py):
+ *   orc_philox4x64         known-answer test against numpy's Philox
+ *   orc_boris_move         Larmor polygon radius, rotation angle, E x B drift,
+ *                          |v| conservation (closed forms)
+ *   orc_bfield             div B = 0, curl B = 0 (finite differences), B_r zero
+ *                          near the J1 root at the cathode edge
+ *   orc_deposit            total charge, single-particle split, r^2 moment
+ *   orc_poisson            exact quadratic solution, 2nd-order convergence,
+ *                          Gauss law
+ *   orc_efield_at          MC zero axial self-force, EC force = -dW/dx
+ *   MCC inside orc_step    collision counts vs nu_k dt, exact energy losses
+ *   circuit inside orc_step  prescribed-charge drive; Table 1 cases 1-2
+ */
+#ifndef PIC_ORACLE_H
+#define PIC_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct orc_config {
+  int32_t nr, nz;          /* cells in r and z */
+  double R, L, Rc;         /* domain radius, length, cathode radius (m) */
+  double dt;               /* time step (s) */
+  double weight;           /* real particles per macroparticle */
+  double m_ion;            /* ion mass (kg) */
+  double n_gas, T_gas;     /* background argon density (m^-3), temperature (K) */
+  int32_t b_mode;          /* 0: magnetron node table, 1: uniform (B0r, B0z) */
+  double B_kA0, B_k;       /* k*A0 (T), k (1/m) */
+  double B0r, B0z;         /* uniform field (T), b_mode 1 */
+  double gamma_i, gamma_e; /* ion- and electron-induced secondary yields */
+  int32_t circuit_mode;    /* 0: cathode fixed at Vc_fixed, 1: external circuit */
+  double Vc_fixed, Vs, Rext;
+  int32_t n_avg;           /* steps in the cathode-current average */
+  int32_t gather;          /* 0: EC-PIC, 1: MC-PIC */
+  int32_t rweight;         /* 0: linear tent in r, 1: volume (r^2) weighting */
+  int32_t mcc_on, push_on, field_on, walls_reflect;
+  uint64_t seed;
+  double sigma_el, ion_a, ion_I, exc_C, exc_E, E_cap;
+} orc_config;
+
+typedef struct orc_diag {
+  double t, I_cath, V_cath, n_e_peak, n_i_peak, W_field, K_e, K_i;
+  int64_t N_e, N_i;
+  int64_t n_ion_cath, n_e_cath, n_sey, n_ionize, n_excite, n_elastic;
+} orc_diag;
+
+typedef struct orc_sim orc_sim;
+
+/* ---- pure pieces (used by the pins) ---- */
+void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+void orc_boris_move(double q_over_m, double dt, double Er, double Ez, double Br, double Bz,
+                    double* r, double* z, double* vr, double* vt, double* vz);
+void orc_bfield(const orc_config* c, double r, double z, double* Br, double* Bz);
+double orc_node_volume(const orc_config* c, int m, int n);
+void orc_deposit(const orc_config* c, int64_t np, const double* r, const double* z,
+                 double qw, double* Q /* (nr+1)*(nz+1), accumulated into */);
+int orc_poisson(const orc_config* c, const double* rho, const double* phi_bc, double* phi);
+void orc_efield_at(const orc_config* c, const double* phi, double r, double z,
+                   double* Er, double* Ez);
+void orc_sigma(const orc_config* c, double E_eV, double out[3]);
+double orc_nu_max(const orc_config* c);
+double orc_field_energy(const orc_config* c, const double* phi);
+
+/* ---- the time stepper ---- */
+orc_sim* orc_create(const orc_config* c);
+int orc_set_particles(orc_sim* s, int species, int64_t n, const double* r, const double* z,
+                      const double* vr, const double* vt, const double* vz, const int64_t* id);
+int64_t orc_count(const orc_sim* s, int species);
+int orc_get_particles(const orc_sim* s, int species, double* r, double* z, double* vr,
+                      double* vt, double* vz, int64_t* id);
+int orc_solve_fields(orc_sim* s);              /* phi from current particles and V_c */
+void orc_set_phi(orc_sim* s, const double* phi);
+void orc_get_fields(const orc_sim* s, double* phi, double* rho, double* Q);
+void orc_set_circuit(orc_sim* s, double Vc, int64_t step, const double* qhist, int n);
+int orc_step(orc_sim* s, int64_t nsteps);
+void orc_get_diag(const orc_sim* s, orc_diag* d);
+void orc_set_next_id(orc_sim* s, int64_t next_id);
+int64_t orc_get_next_id(const orc_sim* s);
+int64_t orc_get_step(const orc_sim* s);
+void orc_destroy(orc_sim* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
