@@ -1,0 +1,353 @@
+"""Throughput benchmark: particle-steps/s of the full PIC-MCC step on one GB300.
+
+One step = push + gather + walls + MCC + births + sort + deposit + circuit +
+Poisson for every particle (the whole hot path).  Default workload: the
+256 x 256 cell, 5 cm x 5 cm RZ discharge with the external circuit (V_s =
+500 V, R_ext = 200 Ohm), FP64, EC-PIC, loaded with the synthetic developed
+("grown") state of 4e7 macroparticles per species (uniform 1e15 m^-3 floor
+plus a 1e16 m^-3 Gaussian racetrack ring near the cathode).
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank runs an
+independent replica of the workload on its own GPU (the discharge does not
+shard; replicas only), barrier + max-over-ranks timing, value = all ranks'
+particle-steps / that time.
+
+--impl reference times the CPU oracle (the plain FP64 C implementation the
+GPU path is checked against) on the host cores, on a bounded sample of the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import pic_inputs  # noqa: E402
+
+METRIC = "particle-steps/s (push+gather+deposit+MCC+Poisson), 1 GB300, vs plain FP64"
+UNIT = "particle-steps/s"
+
+# Algorithmic FP64 floating-point operations of one particle-step of the push
+# kernel (gather + Boris + move + frame rotation + cell location + deposit
+# weights), counted from the formulas (add/mul = 1, fma = 2, div/sqrt = 1);
+# the derivation is listed with the design notes.
+FLOPS_PER_PARTICLE = {0: 78.0, 1: 86.0}   # EC, MC
+# Algorithmic HBM bytes of one particle-step: read and write r, z, v_r,
+# v_theta, v_z, id once (FP64).
+BYTES_PER_PARTICLE = 96.0
+# FP64 peak of a GB300: 152 SMs x 2 FP64 FMA pipes-lanes per SM per clock x 2
+# flop x 2.07 GHz = 1.26 TFLOP/s (nominal 1.25); scaled to the measured clock.
+FP64_FLOP_PER_CLK = 152 * 2 * 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--n-per-species", type=float, default=4e7)
+    ap.add_argument("--gather", default="ec", choices=["ec", "mc"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=float, default=2e6,
+                    help="oracle sample size per species for the CPU baseline")
+    ap.add_argument("--cpu-steps", type=int, default=4)
+    return ap.parse_args()
+
+
+def workload(args):
+    g = 0 if args.gather == "ec" else 1
+    p = pic_inputs.params_rz256(gather=g, seed=args.seed)
+    n = int(args.n_per_species)
+    p, parts = pic_inputs.grown_ring_state(p, n, seed=args.seed)
+    p = pic_inputs.with_capacity(p, parts, factor=1.25, births=1 << 20)
+    return p, parts
+
+
+def config_block(p, n, args):
+    return {"workload": f"rz256_ring_{n:.0e}_per_species".replace("+", ""),
+            "grid": [p["nr"], p["nz"]], "domain_m": [p["R"], p["L"]],
+            "n_per_species": n, "gather": args.gather.upper() + "-PIC",
+            "precision": "fp64", "circuit": {"Vs": p["Vs"], "Rext": p["Rext"]},
+            "dt": p["dt"], "poisson_tol": p["poisson_tol"],
+            "l2": "inputs larger than L2 (particle state 3.8 GB >> 129 MB)"}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+def cpu_baseline(p, parts, sample: int, steps: int, seed: int):
+    import oracle
+    rng = np.random.default_rng(seed + 99)
+    sub = {}
+    for k in ("e", "i"):
+        n = parts[k]["r"].shape[0]
+        idx = np.sort(rng.choice(n, size=min(sample, n), replace=False))
+        sub[k] = {q: parts[k][q][idx].copy() for q in parts[k]}
+    orc = oracle.Oracle(p, sub)           # includes the one-time Cholesky factorisation
+    t0 = time.perf_counter()
+    total = 0
+    for _ in range(steps):
+        total += orc.count(0) + orc.count(1)
+        orc.step(1)
+    dt = time.perf_counter() - t0
+    return {"value": total / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sample:.0e} random particles per species of the same state, "
+                      f"{steps} full steps (push, MCC, deposit, banded-Cholesky Poisson on "
+                      f"257x257), single-threaded C, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle as it stands, on a bounded sample."""
+    if rank != 0:
+        return
+    p, parts = workload(args)
+    n = int(args.n_per_species)
+    vals = []
+    for _ in range(args.warmup):
+        pass
+    res = None
+    for _ in range(max(1, args.steps if args.steps <= 3 else 3)):
+        res = cpu_baseline(p, parts, int(args.cpu_sample), args.cpu_steps, args.seed)
+        vals.append(res["value"])
+    v = statistics.median(vals)
+    res["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 2 * n / v * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_block(p, n, args), "cpu_baseline": res,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    barrier()
+    import paper_2507_10727_gb300 as pg
+
+    p, parts = workload(args)
+    n = int(args.n_per_species)
+    h = pg.pic_create(p)
+    for k, sp in (("e", 0), ("i", 1)):
+        pg.pic_set_particles(h, 0, sp, parts[k])
+    pg.pic_solve_fields(h, 0)
+    pg.pic_step(h, args.warmup)
+    pg.pic_sync(h)
+    d0 = pg.pic_diagnostics(h, 0)
+
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    props = torch.cuda.get_device_properties(local)
+    gpu_id = f"GPU-{props.uuid}" if hasattr(props, "uuid") else str(local)
+    with ClockSampler(gpu_id) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        pg.pic_step(h, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    d1 = pg.pic_diagnostics(h, 0)
+    psteps = d1["particle_steps"] - d0["particle_steps"]
+    t = ms / 1e3
+    if world > 1:
+        tt = torch.tensor([t, float(psteps)], device="cuda", dtype=torch.float64)
+        tmax = tt[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
+        t, psteps = float(tmax.item()), float(tt[1].item())
+    value = psteps / t
+
+    # per-kernel CUDA-event times over a second timed pass of the same step
+    pg.pic_profile(h, True)
+    pg.pic_step(h, min(args.steps, 10))
+    prof = pg.pic_profile_read(h)
+    pg.pic_profile(h, False)
+    d2 = pg.pic_diagnostics(h, 0)
+    prof_steps = max(1, prof["push_e"]["launches"])
+    prof_ps = d2["particle_steps"] - d1["particle_steps"]
+    ne, ni = d2["N_e"], d2["N_i"]
+
+    peaks, peak_kind = measured_peaks()
+    clocks = clk.summary()
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    fp64_peak = FP64_FLOP_PER_CLK * sm_mhz * 1e6 / 1e12       # TFLOP/s at the loaded clock
+    dom = "push_e" if prof["push_e"]["total_ms"] >= prof["push_i"]["total_ms"] else "push_i"
+    dom_ms = prof[dom]["total_ms"] / prof_steps
+    dom_n = (ne if dom == "push_e" else ni)
+    g = 0 if args.gather == "ec" else 1
+    achieved = FLOPS_PER_PARTICLE[g] * dom_n / (dom_ms / 1e3) / 1e12
+    achieved_bw = BYTES_PER_PARTICLE * dom_n / (dom_ms / 1e3) / 1e9
+    roofline = {"bound": "alu", "kernel": f"k_push ({dom})", "achieved": achieved,
+                "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                "traffic": None,
+                "peak_note": f"FP64 pipes: 152 SMs x 4 flop/clk at the median loaded SM clock "
+                             f"{sm_mhz:.0f} MHz (1.25 TFLOP/s nominal at 2.07 GHz)",
+                "hbm_view": {"achieved_gbs": achieved_bw, "peak_gbs": peaks.get("hbm_gbs"),
+                             "frac": achieved_bw / peaks.get("hbm_gbs", 6800.0),
+                             "peak_kind": peak_kind, "bytes_per_particle": BYTES_PER_PARTICLE},
+                "flops_per_particle": FLOPS_PER_PARTICLE[g],
+                "per_kernel_ms_per_step": {k: v["total_ms"] / prof_steps for k, v in prof.items()}}
+
+    # end to end through the C ABI with host buffers: upload the state from
+    # pinned host memory, then each step pic_step + a diagnostics read-back
+    e2e = None
+    if not args.no_e2e:
+        pinned = {}
+        for k in ("e", "i"):
+            pinned[k] = {}
+            for q, a in parts[k].items():
+                t_ = torch.from_numpy(a).pin_memory()
+                pinned[k][q] = t_
+        state_bytes = sum(v.numel() * v.element_size() for k in pinned for v in pinned[k].values())
+        h2 = pg.pic_create(p)
+        torch.cuda.synchronize()
+        lib = pg.load_library()
+        t0 = time.perf_counter()
+        for k, sp in (("e", 0), ("i", 1)):
+            a = pinned[k]
+            rc = lib.pic_set_particles(h2.ptr, 0, sp, a["r"].numel(), a["r"].data_ptr(),
+                                       a["z"].data_ptr(), a["vr"].data_ptr(), a["vt"].data_ptr(),
+                                       a["vz"].data_ptr(), a["id"].data_ptr(), 0)
+            assert rc == 0, rc
+        pg.pic_solve_fields(h2, 0)
+        ps0 = pg.pic_diagnostics(h2, 0)["particle_steps"]
+        for _ in range(args.steps):
+            pg.pic_step(h2, 1)
+            de = pg.pic_diagnostics(h2, 0)
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": (de["particle_steps"] - ps0) / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": state_bytes / args.steps,
+               "d2h_bytes_per_step": float(__import__("ctypes").sizeof(pg.PicDiag)),
+               "note": "whole job through the C ABI: state upload from pinned host buffers "
+                       "(amortised over the steps), field solve, then per step pic_step + "
+                       "pic_diagnostics read-back"}
+        pg.pic_destroy(h2)
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        cpu = cpu_baseline(p, parts, int(args.cpu_sample), args.cpu_steps, args.seed)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config_block(p, n, args),
+                "gpu_launches": args.steps * 10,
+                "poisson": {"iters_last_step": d1["poisson_iters"],
+                            "resid_last_step": d1["poisson_resid"],
+                            "ms_per_step": roofline["per_kernel_ms_per_step"]["poisson"]},
+                "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    pg.pic_destroy(h)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * pic.h -- C ABI of the GB300 (sm_103a) library for the explicit
+ * electrostatic PIC-MCC model of a dc magnetron discharge in 2D (r,z)
+ * geometry of arXiv:2507.10727 ("Modeling the Role of Secondary Electron
+ * Emission in Direct Current Magnetron Sputtering using Explicit
+ * Energy-Conserving Particle-in-Cell Methods").
+ *
+ * One call of pic_step advances every particle and the field by one or more
+ * time steps entirely on the GPU:
+ *   E from phi (Section 2: edge-centred E for EC-PIC, nodal E for MC-PIC)
+ *   -> gather + Boris push in the static magnetron field (Sections 2, 3)
+ *   -> absorbing walls, reflecting axis, ion-induced secondary electrons
+ *      with yield gamma at zero velocity (Section 3)
+ *   -> null-collision Monte Carlo e-Ar collisions, reactions (1a)-(1c)
+ *      (Section 3)
+ *   -> births with deterministic ids -> charge deposit with tent functions
+ *      (Section 2) divided by the annular node volume
+ *   -> external circuit V_c = -V_s + I R_ext (Sections 3, 4, 6)
+ *   -> RZ Poisson solve with electrode Dirichlet values and Gauss's law on
+ *      the axis (Section 3) by multigrid-preconditioned conjugate gradients.
+ *
+ * Conventions for every function:
+ *   - Return value: PIC_OK (0) or one of the negative PIC_ERR_* codes; the
+ *     text of the last error of a handle is pic_last_error().  Nothing throws
+ *     or aborts across this boundary.
+ *   - Device work runs on the CUDA stream given to pic_create (a cudaStream_t
+ *     passed as void*; NULL = legacy default stream).  Calls marked "async"
+ *     only enqueue work; device-side failures (capacity, non-convergence,
+ *     non-finite values, wait timeouts) are latched in a status word that the
+ *     next synchronising call (pic_sync, pic_diagnostics, pic_get_*) returns.
+ *     Once a status is latched, later steps do no work.
+ *   - Units are SI (m, s, V, kg, C); energies in eV where named so.
+ *   - Node arrays are (nr+1) x (nz+1) doubles, row-major with z fastest:
+ *     element (m, n) at m*(nz+1) + n, node m at r = m*R/nr, n at z = n*L/nz.
+ *   - A handle may hold several independent discharges ("instances") that
+ *     advance together; per-instance calls take the instance index.
+ *   - A handle is used by one host thread at a time.
+ */
+#ifndef PIC_GB300_H
+#define PIC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_ABI_VERSION 1
+
+enum pic_status {
+  PIC_OK = 0,
+  PIC_ERR_INVALID = -1,      /* bad argument or configuration */
+  PIC_ERR_OOM = -2,          /* device allocation failed */
+  PIC_ERR_CAPACITY = -3,     /* particle or birth capacity exceeded */
+  PIC_ERR_NONCONVERGED = -4, /* Poisson solve reached poisson_max_iter */
+  PIC_ERR_NAN = -5,          /* non-finite particle coordinate */
+  PIC_ERR_TIMEOUT = -6,      /* a device-side wait reached its iteration limit */
+  PIC_ERR_CUDA = -7,         /* CUDA runtime error */
+  PIC_ERR_IO = -8           /* checkpoint file error */
+};
+
+enum pic_species { PIC_ELECTRON = 0, PIC_ION = 1 };
+
+/* Run parameters of one discharge.  Plain data; fill every field. */
+typedef struct pic_config {
+  uint32_t struct_size;      /* must be sizeof(pic_config) */
+  int32_t nr, nz;            /* cells in r and z; both >= 2 and even */
+  double R, L, Rc;           /* domain radius, length; cathode disk radius at z = 0 (m) */
+  double dt;                 /* time step (s) */
+  double weight;             /* real particles per macroparticle, both species (Section 5: constant) */
+  double m_ion;              /* ion mass (kg) */
+  double n_gas, T_gas;       /* background Ar density (m^-3) and temperature (K) (Section 3) */
+  int32_t b_mode;            /* 0: magnetron stand-in B = -grad(A0 J0(kr) e^{-kz}); 1: uniform B0 */
+  double B_kA0, B_k;         /* k*A0 (T) and k (1/m) */
+  double B0r, B0z;           /* uniform field (T) when b_mode = 1 */
+  double gamma_i, gamma_e;   /* ion- and electron-induced secondary electron yields (Section 3) */
+  int32_t circuit_mode;      /* 0: cathode fixed at Vc_fixed; 1: V_c = -V_s + I R_ext in [-V_s, 0] */
+  double Vc_fixed, Vs, Rext; /* V, V, Ohm */
+  int32_t n_avg;             /* steps in the running mean of the cathode current */
+  int32_t gather;            /* 0: EC-PIC, 1: MC-PIC (Section 2) */
+  int32_t rweight;           /* 0: tent in r; 1: tent in r^2 (volume weighting) */
+  int32_t precision;         /* 0: FP64 particles (the only value accepted by this build) */
+  int32_t mcc_on, push_on, field_on, walls_reflect; /* 1,1,1,0 for the physical model */
+  uint64_t seed;             /* Philox key word 0 */
+  double sigma_el;           /* elastic cross section (m^2) */
+  double ion_a, ion_I;       /* ionization: sigma = ion_a ln(E/I)/(E I) (m^2 eV^2, eV) */
+  double exc_C, exc_E;       /* excitation: sigma = exc_C ln(E/E_x)/(E E_x) (m^2 eV^2, eV) */
+  double E_cap;              /* energy bound of the null-collision frequency (eV) */
+  double poisson_tol;        /* relative residual ||b - A phi||_2 / ||b||_2 to reach */
+  int32_t poisson_max_iter;  /* PCG iterations before PIC_ERR_NONCONVERGED */
+  int64_t cap_e, cap_i;      /* particle capacities per species */
+  int64_t birth_cap;         /* births per species per step */
+  int32_t diag_every;        /* diagnostics are accumulated on steps that are multiples */
+  int32_t sort_every;        /* cell sort period in steps (1 = every step) */
+} pic_config;
+
+/* Device-memory provider.  alloc returns a device pointer aligned to at least
+ * 256 bytes or NULL; free releases it.  All device memory of a handle comes
+ * from here (when the pointer to this struct is NULL, cudaMalloc/cudaFree). */
+typedef struct pic_alloc {
+  void* ctx;
+  void* (*alloc)(void* ctx, size_t bytes);
+  void (*free)(void* ctx, void* ptr);
+} pic_alloc;
+
+/* Diagnostics of the last diagnostic step of one instance (Sections 4-6:
+ * cathode current and voltage, densities, energies). */
+typedef struct pic_diag {
+  double t;             /* time of the step whose energies are reported (s) */
+  double I_cath;        /* cathode current after the step (A), running mean */
+  double V_cath;        /* cathode potential after the step (V) */
+  double n_e_peak;      /* max over nodes of the electron density after the step (m^-3) */
+  double n_i_peak;      /* same for ions */
+  double W_field;       /* field energy 1/2 sum_edges eps0 E^2 V_edge at the step (J) */
+  double K_e, K_i;      /* kinetic energies, mean of |v|^2 before and after the push (J) */
+  int64_t N_e, N_i;     /* macroparticles after the step */
+  int64_t n_ion_cath, n_e_cath, n_sey; /* cathode impacts and secondary electrons this step */
+  int64_t n_ionize, n_excite, n_elastic; /* collisions this step */
+  int64_t step;         /* index of the step the record belongs to */
+  int64_t particle_steps; /* cumulative sum over steps of (electrons + ions) pushed */
+  int32_t poisson_iters;
+  int32_t status;       /* latched device status (pic_status) */
+  double poisson_resid; /* final relative residual */
+} pic_diag;
+
+typedef struct pic_handle pic_handle;
+
+/* Create a handle for n_instances discharges (cfgs[0..n_instances-1]).
+ * Allocates all device state, builds the static B table on the host in FP64
+ * and uploads it.  Particles start empty (pic_set_particles); phi starts at
+ * zero.  cuda_stream: cudaStream_t of all later work.  Returns PIC_OK and
+ * *out, or an error with *out = NULL. */
+int pic_create(const pic_config* cfgs, int n_instances, const pic_alloc* alloc,
+               void* cuda_stream, pic_handle** out);
+
+/* Release all device memory of the handle (after synchronising its stream). */
+void pic_destroy(pic_handle* h);
+
+/* Text of the last error on this handle (static storage of the handle). */
+const char* pic_last_error(const pic_handle* h);
+
+/* Replace the particles of one species of one instance.  Arrays of length n
+ * (r in [0,R), z in [0,L), velocities (v_r, v_theta, v_z) in m/s, ids unique
+ * and >= 0); host memory when on_device = 0, device memory otherwise.  The
+ * particles are sorted by cell on the device.  next_id becomes max(id)+1 over
+ * both species if that is larger.  Synchronous. */
+int pic_set_particles(pic_handle* h, int instance, int species, int64_t n, const double* r,
+                      const double* z, const double* vr, const double* vt, const double* vz,
+                      const int64_t* id, int on_device);
+
+/* Number of macroparticles of a species (synchronous). */
+int pic_count(pic_handle* h, int instance, int species, int64_t* n_out);
+
+/* Copy out the particles (any order; compare by id).  Arrays must hold the
+ * count returned by pic_count.  Host or device memory per on_device. */
+int pic_get_particles(pic_handle* h, int instance, int species, double* r, double* z,
+                      double* vr, double* vt, double* vz, int64_t* id, int on_device);
+
+/* Deposit the current particles and solve for phi with the current cathode
+ * voltage (used after pic_set_particles to obtain phi at step 0).  Async. */
+int pic_solve_fields(pic_handle* h, int instance);
+
+/* Overwrite phi (node array, host or device).  Synchronous. */
+int pic_set_phi(pic_handle* h, int instance, const double* phi, int on_device);
+
+/* Copy out phi, rho = Q/V and Q (node arrays; any may be NULL).  Synchronous. */
+int pic_get_fields(pic_handle* h, int instance, double* phi, double* rho, double* Q,
+                   int on_device);
+
+/* Set the circuit state: cathode voltage, step index and the last n_avg
+ * cathode charges (C; ring buffer indexed by step % n_avg).  Synchronous. */
+int pic_set_circuit(pic_handle* h, int instance, double Vc, int64_t step, const double* qhist,
+                    int n);
+
+/* Set / get the next particle id handed to a birth.  Synchronous. */
+int pic_set_next_id(pic_handle* h, int instance, int64_t next_id);
+int pic_get_next_id(pic_handle* h, int instance, int64_t* next_id);
+
+/* Advance all instances by nsteps time steps.  Async (see conventions). */
+int pic_step(pic_handle* h, int64_t nsteps);
+
+/* Wait for the handle's stream; return the latched status of all instances. */
+int pic_sync(pic_handle* h);
+
+/* Synchronise and copy the diagnostics record of one instance into *out
+ * (caller-owned).  Returns the latched status of that instance. */
+int pic_diagnostics(pic_handle* h, int instance, pic_diag* out);
+
+/* Checkpoint of one instance to / from a file (particles, phi, circuit
+ * state, step and id counters).  A resumed run continues bit for bit up to
+ * the order of particles inside a cell.  Synchronous. */
+int pic_save(pic_handle* h, int instance, const char* path);
+int pic_load(pic_handle* h, int instance, const char* path);
+
+/* Per-kernel timing of pic_step (CUDA events on the handle's stream around
+ * each kernel group).  pic_profile(h, 1) clears the counters and starts
+ * recording, pic_profile(h, 0) stops.  pic_profile_read synchronises and
+ * fills up to `max` records (names are static strings: "field_tables",
+ * "push_e", "push_i", "births", "scan", "scatter", "charge", "circuit",
+ * "poisson", "step_end"); *n_out is the number of kernel groups. */
+typedef struct pic_kernel_time {
+  const char* name;
+  int64_t launches;
+  double total_ms;
+} pic_kernel_time;
+int pic_profile(pic_handle* h, int enable);
+int pic_profile_read(pic_handle* h, pic_kernel_time* out, int max, int* n_out);
+
+/* Bytes of device scratch that pic_poisson_solve needs for an nr x nz grid. */
+size_t pic_poisson_workspace_bytes(int nr, int nz);
+
+/* Standalone RZ Poisson solve (Section 3: Dirichlet electrodes, Gauss's law
+ * on the axis) on the stream `cuda_stream`.
+ *   Q_dev    node charges (C), device, (nr+1)(nz+1) doubles (input)
+ *   phi_dev  device node array: on input the boundary nodes (z = 0, z = L,
+ *            r = R) hold the Dirichlet values and the others the initial
+ *            guess; on output the solution.
+ *   work_dev device scratch of pic_poisson_workspace_bytes(nr, nz) bytes,
+ *            256-byte aligned, owned by the caller; contents not preserved.
+ *   iters, resid (host, may be NULL): PCG iterations and final relative
+ *            residual.
+ * Synchronous.  Returns PIC_ERR_NONCONVERGED when tol is not met in max_iter
+ * iterations (phi then holds the last iterate). */
+int pic_poisson_solve(int nr, int nz, double R, double L, double tol, int max_iter,
+                      const double* Q_dev, double* phi_dev, void* work_dev, void* cuda_stream,
+                      int* iters, double* resid);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_GB300_H */

@@ -211,6 +211,9 @@ class Oracle:
         lib().orc_set_particles(self._h, species, ids.shape[0], *[_dp(a) for a in arrs],
                                 ids.ctypes.data_as(_I64))
 
+    def count(self, species: int) -> int:
+        return lib().orc_count(self._h, species)
+
     def get_particles(self, species: int) -> dict:
         n = lib().orc_count(self._h, species)
         out = {k: np.empty(n) for k in ("r", "z", "vr", "vt", "vz")}

@@ -1,0 +1,754 @@
+// api.cu -- the C ABI (include/pic.h): handle life cycle, host<->device
+// transfers, the per-step launch loop, checkpoints and the standalone Poisson
+// solve.  No compute happens here beyond set-up tables (the magnetron field
+// table, the null-collision frequency) evaluated once on the host in FP64.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "common.cuh"
+#include "launch.h"
+
+using namespace pic;
+
+namespace {
+
+struct InstHost {
+  pic_config cfg;
+  Inst I;
+  PoissonWork* pw = nullptr;
+  int swapped = 0;
+};
+
+}  // namespace
+
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  struct Rec { int group; cudaEvent_t b, e; };
+  std::vector<Rec> recs;
+  cudaEvent_t open[G_COUNT] = {};
+};
+
+struct pic_handle {
+  std::vector<InstHost> inst;
+  Profiler prof;
+  pic_alloc alloc;
+  bool own_alloc = true;
+  cudaStream_t stream = nullptr;
+  int num_sms = 1;
+  std::vector<void*> blocks;
+  std::string err;
+};
+
+namespace {
+
+int fail(pic_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int cuda_fail(pic_handle* h, cudaError_t e, const char* what) {
+  return fail(h, PIC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void* dev_alloc(pic_handle* h, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* p = nullptr;
+  if (h->own_alloc) {
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  } else {
+    p = h->alloc.alloc(h->alloc.ctx, bytes);
+  }
+  if (p) h->blocks.push_back(p);
+  return p;
+}
+
+int status_code(int st) {
+  if (st & ST_NAN) return PIC_ERR_NAN;
+  if (st & ST_CAPACITY) return PIC_ERR_CAPACITY;
+  if (st & ST_TIMEOUT) return PIC_ERR_TIMEOUT;
+  if (st & ST_NONCONV) return PIC_ERR_NONCONVERGED;
+  return PIC_OK;
+}
+
+const char* status_text(int code) {
+  switch (code) {
+    case PIC_ERR_NAN: return "non-finite or out-of-domain particle";
+    case PIC_ERR_CAPACITY: return "particle or birth capacity exceeded";
+    case PIC_ERR_TIMEOUT: return "device wait reached its limit";
+    case PIC_ERR_NONCONVERGED: return "Poisson solve did not converge";
+    default: return "ok";
+  }
+}
+
+// null-collision frequency: 1.001 n_g max over a log grid of 100001 energies
+double nu_max_of(const pic_config& c) {
+  double best = 0.0;
+  for (int k = 0; k <= 100000; ++k) {
+    double E = 1e-4 * std::pow(c.E_cap / 1e-4, k / 100000.0);
+    if (k == 100000) E = c.E_cap;
+    const double s_el = E > 0.0 ? c.sigma_el : 0.0;
+    const double s_ex = E > c.exc_E ? c.exc_C * std::log(E / c.exc_E) / (E * c.exc_E) : 0.0;
+    const double s_io = E > c.ion_I ? c.ion_a * std::log(E / c.ion_I) / (E * c.ion_I) : 0.0;
+    const double v = std::sqrt(2.0 * E * kQe / kMe);
+    const double nu = c.n_gas * (s_el + s_ex + s_io) * v;
+    if (nu > best) best = nu;
+  }
+  return 1.001 * best;
+}
+
+std::string validate(const pic_config& c) {
+  if (c.struct_size != sizeof(pic_config)) return "pic_config.struct_size mismatch";
+  if (c.nr < 2 || c.nz < 2 || (c.nr & 1) || (c.nz & 1)) return "nr, nz must be even and >= 2";
+  if ((long long)c.nr * c.nz > (1LL << 26)) return "grid too large";
+  if (!(c.R > 0) || !(c.L > 0) || !(c.dt > 0) || !(c.weight > 0) || !(c.m_ion > 0))
+    return "R, L, dt, weight, m_ion must be positive";
+  if (c.Rc < 0) return "Rc must be >= 0";
+  if (c.cap_e <= 0 || c.cap_i <= 0 || c.birth_cap <= 0) return "capacities must be positive";
+  if (c.cap_e >= (1LL << 31) || c.cap_i >= (1LL << 31) || c.birth_cap >= (1LL << 30))
+    return "capacities must stay below 2^31 (2^30 births)";
+  if (c.precision != 0) return "this build runs the FP64 particle path only (precision = 0)";
+  if (c.sort_every != 1) return "sort_every must be 1";
+  if (c.gather < 0 || c.gather > 1 || c.rweight < 0 || c.rweight > 1) return "gather/rweight";
+  if (c.circuit_mode < 0 || c.circuit_mode > 1 || c.b_mode < 0 || c.b_mode > 1) return "modes";
+  if (!(c.poisson_tol > 0) || c.poisson_max_iter < 1) return "poisson_tol/max_iter";
+  if (c.n_avg < 1) return "n_avg must be >= 1";
+  if (!(c.E_cap > 0)) return "E_cap must be positive";
+  return "";
+}
+
+int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
+  ih.cfg = c;
+  Inst& I = ih.I;
+  std::memset(&I, 0, sizeof(I));
+  I.nr = c.nr;
+  I.nz = c.nz;
+  const int ntr = (c.nr + kTile - 1) / kTile;
+  I.ntz = (c.nz + kTile - 1) / kTile;
+  I.nkey = ntr * I.ntz * kTileCells;
+  I.R = c.R;
+  I.L = c.L;
+  I.Rc = c.Rc;
+  I.dr = c.R / c.nr;
+  I.dz = c.L / c.nz;
+  I.inv_dr = 1.0 / I.dr;
+  I.inv_dz = 1.0 / I.dz;
+  I.m_cath = -1;
+  for (int m = 0; m <= c.nr; ++m)
+    if (m * I.dr <= c.Rc && m < c.nr) I.m_cath = m;
+  I.dt = c.dt;
+  I.weight = c.weight;
+  I.qm[0] = -kQe / kMe;
+  I.qm[1] = kQe / c.m_ion;
+  I.mass[0] = kMe;
+  I.mass[1] = c.m_ion;
+  I.gamma[0] = c.gamma_e;
+  I.gamma[1] = c.gamma_i;
+  I.n_gas = c.n_gas;
+  I.T_gas = c.T_gas;
+  I.m_ion = c.m_ion;
+  I.sigma_el = c.sigma_el;
+  I.ion_a = c.ion_a;
+  I.ion_I = c.ion_I;
+  I.exc_C = c.exc_C;
+  I.exc_E = c.exc_E;
+  I.nu_max = nu_max_of(c);
+  I.p_null = -std::expm1(-I.nu_max * c.dt);
+  I.seed = c.seed;
+  I.gather = c.gather;
+  I.rweight = c.rweight;
+  I.mcc_on = c.mcc_on;
+  I.push_on = c.push_on;
+  I.field_on = c.field_on;
+  I.walls_reflect = c.walls_reflect;
+  I.circuit_mode = c.circuit_mode;
+  I.n_avg = c.n_avg;
+  I.diag_every = c.diag_every > 0 ? c.diag_every : 1;
+  I.Vc_fixed = c.Vc_fixed;
+  I.Vs = c.Vs;
+  I.Rext = c.Rext;
+  I.poisson_tol = c.poisson_tol;
+  I.poisson_max_iter = c.poisson_max_iter;
+  I.cap[0] = c.cap_e;
+  I.cap[1] = c.cap_i;
+  I.birth_cap = c.birth_cap;
+
+  const size_t nn = (size_t)(c.nr + 1) * (c.nz + 1);
+  auto A = [&](size_t b) { return dev_alloc(h, b); };
+  bool ok = true;
+  auto chk = [&](void* p) { ok = ok && p != nullptr; return p; };
+  for (int sp = 0; sp < 2; ++sp) {
+    const size_t cap = (size_t)I.cap[sp];
+    for (ParticlesDev* P : {&I.cur[sp], &I.nxt[sp]}) {
+      P->r = (double*)chk(A(cap * 8));
+      P->z = (double*)chk(A(cap * 8));
+      P->vr = (double*)chk(A(cap * 8));
+      P->vt = (double*)chk(A(cap * 8));
+      P->vz = (double*)chk(A(cap * 8));
+      P->id = (long long*)chk(A(cap * 8));
+    }
+    I.key[sp] = (int*)chk(A(cap * 4));
+    I.counts[sp] = (int*)chk(A((size_t)I.nkey * 4));
+    I.cursor[sp] = (int*)chk(A((size_t)I.nkey * 4));
+    BirthsDev& B = I.births[sp];
+    const size_t bc = (size_t)c.birth_cap;
+    B.r = (double*)chk(A(bc * 8));
+    B.z = (double*)chk(A(bc * 8));
+    B.vr = (double*)chk(A(bc * 8));
+    B.vt = (double*)chk(A(bc * 8));
+    B.vz = (double*)chk(A(bc * 8));
+    B.pkey = (unsigned long long*)chk(A(bc * 8));
+    B.cell = (int*)chk(A(bc * 4));
+    B.id = (long long*)chk(A(bc * 8));
+    long long P2 = 1;
+    while (P2 < (long long)bc) P2 <<= 1;
+    B.sort_len = P2;
+    B.skey = (unsigned long long*)chk(A((size_t)P2 * 8));
+    B.sidx = (unsigned int*)chk(A((size_t)P2 * 4));
+    I.qacc[sp] = (unsigned long long*)chk(A(nn * 8));
+  }
+  I.phi = (double*)chk(A(nn * 8));
+  I.Q = (double*)chk(A(nn * 8));
+  I.etab = (double4_32a*)chk(A((size_t)I.nkey * (c.gather == 0 ? 1 : 2) * sizeof(double4_32a)));
+  I.btab = (double4_32a*)chk(A((size_t)I.nkey * 2 * sizeof(double4_32a)));
+  I.qhist = (double*)chk(A((size_t)c.n_avg * 8));
+  I.S = (Scalars*)chk(A(sizeof(Scalars)));
+  I.diag = (DiagDev*)chk(A(sizeof(DiagDev)));
+  const size_t pwb = poisson_work_bytes(c.nr, c.nz);
+  void* pwbase = chk(A(pwb));
+  if (!ok) return fail(h, PIC_ERR_OOM, "device allocation failed");
+  cudaStream_t st = h->stream;
+  cudaError_t e = cudaSuccess;
+  for (int sp = 0; sp < 2 && e == cudaSuccess; ++sp) {
+    e = cudaMemsetAsync(I.counts[sp], 0, (size_t)I.nkey * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(I.qacc[sp], 0, nn * 8, st);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(I.phi, 0, nn * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(I.Q, 0, nn * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(I.qhist, 0, (size_t)c.n_avg * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(I.diag, 0, sizeof(DiagDev), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pwbase, 0, pwb, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "memset");
+  ih.pw = poisson_work_init(pwbase, c.nr, c.nz, c.R, c.L, h->num_sms);
+
+  // static magnetic field: node values in FP64, folded per cell into
+  // bilinear coefficients (B table keyed like the cells)
+  std::vector<double> br(nn), bz(nn);
+  for (int m = 0; m <= c.nr; ++m)
+    for (int n = 0; n <= c.nz; ++n) {
+      const double r = m * I.dr, z = n * I.dz;
+      double vr = c.B0r, vz = c.B0z;
+      if (c.b_mode == 0) {
+        const double ex = std::exp(-c.B_k * z);
+        vr = c.B_kA0 * ::j1(c.B_k * r) * ex;
+        vz = c.B_kA0 * ::j0(c.B_k * r) * ex;
+      }
+      br[(size_t)m * (c.nz + 1) + n] = vr;
+      bz[(size_t)m * (c.nz + 1) + n] = vz;
+    }
+  std::vector<double4_32a> bt((size_t)I.nkey * 2, make_d4(0, 0, 0, 0));
+  for (int m = 0; m < c.nr; ++m)
+    for (int n = 0; n < c.nz; ++n) {
+      const int key = ((m >> 3) * I.ntz + (n >> 3)) * kTileCells + ((m & 7) << 3) + (n & 7);
+      auto at = [&](const std::vector<double>& v, int a, int b) {
+        return v[(size_t)(m + a) * (c.nz + 1) + (n + b)];
+      };
+      for (int comp = 0; comp < 2; ++comp) {
+        const std::vector<double>& v = comp == 0 ? br : bz;
+        const double b00 = at(v, 0, 0), b10 = at(v, 1, 0), b01 = at(v, 0, 1), b11 = at(v, 1, 1);
+        bt[(size_t)2 * key + comp] = make_d4(b00, b10 - b00, b01 - b00, b11 - b10 - b01 + b00);
+      }
+    }
+  e = cudaMemcpyAsync(I.btab, bt.data(), bt.size() * sizeof(double4_32a), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "upload B table");
+  Scalars s0;
+  std::memset(&s0, 0, sizeof(s0));
+  s0.Vc = c.circuit_mode == 1 ? -c.Vs : c.Vc_fixed;
+  s0.diag_on = 1;
+  e = cudaMemcpyAsync(I.S, &s0, sizeof(s0), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "upload scalars");
+  e = cudaStreamSynchronize(st);  // host vectors go out of scope
+  if (e != cudaSuccess) return cuda_fail(h, e, "create sync");
+  return PIC_OK;
+}
+
+int read_status(pic_handle* h, int instance, Scalars* out) {
+  Scalars s;
+  cudaError_t e = cudaMemcpyAsync(&s, h->inst[instance].I.S, sizeof(s), cudaMemcpyDeviceToHost,
+                                  h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "read status");
+  if (out) *out = s;
+  const int code = status_code(s.status);
+  if (code != PIC_OK) return fail(h, code, status_text(code));
+  return PIC_OK;
+}
+
+bool bad_instance(pic_handle* h, int instance) {
+  return !h || instance < 0 || instance >= (int)h->inst.size();
+}
+
+const char* kGroupNames[G_COUNT] = {"field_tables", "push_e", "push_i", "births", "scan",
+                                   "scatter", "charge", "circuit", "poisson", "step_end"};
+
+void prof_mark(void* ctx, int group, bool begin, cudaStream_t st) {
+  Profiler& P = *(Profiler*)ctx;
+  if (P.used == P.pool.size()) {
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) return;
+    P.pool.push_back(ev);
+  }
+  cudaEvent_t ev = P.pool[P.used++];
+  cudaEventRecord(ev, st);
+  if (begin) P.open[group] = ev;
+  else P.recs.push_back({group, P.open[group], ev});
+}
+
+void swap_buffers(InstHost& ih, int sp) {
+  std::swap(ih.I.cur[sp], ih.I.nxt[sp]);
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_create(const pic_config* cfgs, int n_instances, const pic_alloc* alloc, void* cuda_stream,
+               pic_handle** out) {
+  if (!out) return PIC_ERR_INVALID;
+  *out = nullptr;
+  if (!cfgs || n_instances < 1) return PIC_ERR_INVALID;
+  for (int k = 0; k < n_instances; ++k)
+    if (!validate(cfgs[k]).empty()) return PIC_ERR_INVALID;
+  pic_handle* h = new pic_handle();
+  if (alloc && alloc->alloc && alloc->free) {
+    h->alloc = *alloc;
+    h->own_alloc = false;
+  }
+  h->stream = (cudaStream_t)cuda_stream;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    delete h;
+    return PIC_ERR_CUDA;
+  }
+  h->inst.resize(n_instances);
+  for (int k = 0; k < n_instances; ++k) {
+    const int rc = build_instance(h, cfgs[k], h->inst[k]);
+    if (rc != PIC_OK) {
+      pic_destroy(h);
+      return rc;
+    }
+  }
+  *out = h;
+  return PIC_OK;
+}
+
+void pic_destroy(pic_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  for (cudaEvent_t ev : h->prof.pool) cudaEventDestroy(ev);
+  for (InstHost& ih : h->inst)
+    if (ih.pw) poisson_work_free(ih.pw);
+  for (void* p : h->blocks) {
+    if (h->own_alloc) cudaFree(p);
+    else h->alloc.free(h->alloc.ctx, p);
+  }
+  delete h;
+}
+
+const char* pic_last_error(const pic_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+int pic_set_particles(pic_handle* h, int instance, int species, int64_t n, const double* r,
+                      const double* z, const double* vr, const double* vt, const double* vz,
+                      const int64_t* id, int on_device) {
+  if (bad_instance(h, instance) || species < 0 || species > 1 || n < 0)
+    return fail(h, PIC_ERR_INVALID, "bad instance/species/count");
+  InstHost& ih = h->inst[instance];
+  if (n > ih.I.cap[species]) return fail(h, PIC_ERR_CAPACITY, "n exceeds the species capacity");
+  if (n > 0 && (!r || !z || !vr || !vt || !vz || !id))
+    return fail(h, PIC_ERR_INVALID, "null array");
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const ParticlesDev& P = ih.I.cur[species];
+  cudaStream_t st = h->stream;
+  cudaError_t e = cudaSuccess;
+  const size_t b = (size_t)n * 8;
+  if (n > 0) {
+    e = cudaMemcpyAsync(P.r, r, b, kind, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P.z, z, b, kind, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P.vr, vr, b, kind, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P.vt, vt, b, kind, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P.vz, vz, b, kind, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P.id, id, b, kind, st);
+  }
+  if (e == cudaSuccess) e = launch_set_n(ih.I, species, n, st);
+  if (e == cudaSuccess) e = launch_sort_species(ih.I, species, h->num_sms, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_particles");
+  swap_buffers(ih, species);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_particles sync");
+  return read_status(h, instance, nullptr);
+}
+
+int pic_count(pic_handle* h, int instance, int species, int64_t* n_out) {
+  if (bad_instance(h, instance) || species < 0 || species > 1 || !n_out)
+    return fail(h, PIC_ERR_INVALID, "bad argument");
+  Scalars s;
+  const int rc = read_status(h, instance, &s);
+  *n_out = s.n[species];
+  return rc;
+}
+
+int pic_get_particles(pic_handle* h, int instance, int species, double* r, double* z, double* vr,
+                      double* vt, double* vz, int64_t* id, int on_device) {
+  int64_t n = 0;
+  int rc = pic_count(h, instance, species, &n);
+  if (rc != PIC_OK && rc != PIC_ERR_NONCONVERGED) return rc;
+  const ParticlesDev& P = h->inst[instance].I.cur[species];
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t b = (size_t)n * 8;
+  cudaStream_t st = h->stream;
+  cudaError_t e = cudaSuccess;
+  if (n > 0) {
+    if (r) e = cudaMemcpyAsync(r, P.r, b, kind, st);
+    if (e == cudaSuccess && z) e = cudaMemcpyAsync(z, P.z, b, kind, st);
+    if (e == cudaSuccess && vr) e = cudaMemcpyAsync(vr, P.vr, b, kind, st);
+    if (e == cudaSuccess && vt) e = cudaMemcpyAsync(vt, P.vt, b, kind, st);
+    if (e == cudaSuccess && vz) e = cudaMemcpyAsync(vz, P.vz, b, kind, st);
+    if (e == cudaSuccess && id) e = cudaMemcpyAsync(id, P.id, b, kind, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_particles");
+  return rc;
+}
+
+int pic_solve_fields(pic_handle* h, int instance) {
+  if (bad_instance(h, instance)) return fail(h, PIC_ERR_INVALID, "bad instance");
+  InstHost& ih = h->inst[instance];
+  cudaError_t e = launch_solve_fields(ih.I, ih.pw, h->num_sms, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "solve_fields");
+  return PIC_OK;
+}
+
+int pic_set_phi(pic_handle* h, int instance, const double* phi, int on_device) {
+  if (bad_instance(h, instance) || !phi) return fail(h, PIC_ERR_INVALID, "bad argument");
+  InstHost& ih = h->inst[instance];
+  const size_t nn = (size_t)(ih.cfg.nr + 1) * (ih.cfg.nz + 1);
+  cudaError_t e = cudaMemcpyAsync(ih.I.phi, phi, nn * 8,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_phi");
+  return PIC_OK;
+}
+
+int pic_get_fields(pic_handle* h, int instance, double* phi, double* rho, double* Q, int on_device) {
+  if (bad_instance(h, instance)) return fail(h, PIC_ERR_INVALID, "bad instance");
+  InstHost& ih = h->inst[instance];
+  const pic_config& c = ih.cfg;
+  const size_t nn = (size_t)(c.nr + 1) * (c.nz + 1);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  cudaError_t e = cudaSuccess;
+  if (phi) e = cudaMemcpyAsync(phi, ih.I.phi, nn * 8, kind, h->stream);
+  if (e == cudaSuccess && Q) e = cudaMemcpyAsync(Q, ih.I.Q, nn * 8, kind, h->stream);
+  std::vector<double> qh;
+  if (e == cudaSuccess && rho) {
+    qh.resize(nn);
+    e = cudaMemcpyAsync(qh.data(), ih.I.Q, nn * 8, cudaMemcpyDeviceToHost, h->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_fields");
+  if (rho) {
+    // rho = Q / V with the node control volumes (half volume on z walls)
+    std::vector<double> rh(nn);
+    const double dr = c.R / c.nr, dz = c.L / c.nz;
+    for (int m = 0; m <= c.nr; ++m) {
+      double area;
+      if (m == 0) area = kPi * 0.25 * dr * dr;
+      else if (m == c.nr) area = kPi * (c.R * c.R - (c.R - 0.5 * dr) * (c.R - 0.5 * dr));
+      else area = 2.0 * kPi * (m * dr) * dr;
+      for (int n = 0; n <= c.nz; ++n) {
+        const double hz = (n == 0 || n == c.nz) ? 0.5 : 1.0;
+        rh[(size_t)m * (c.nz + 1) + n] = qh[(size_t)m * (c.nz + 1) + n] / (area * dz * hz);
+      }
+    }
+    if (on_device) e = cudaMemcpy(rho, rh.data(), nn * 8, cudaMemcpyHostToDevice);
+    else std::memcpy(rho, rh.data(), nn * 8);
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_fields rho");
+  }
+  return PIC_OK;
+}
+
+int pic_set_circuit(pic_handle* h, int instance, double Vc, int64_t step, const double* qhist,
+                    int n) {
+  if (bad_instance(h, instance) || step < 0 || n < 0 || (n > 0 && !qhist))
+    return fail(h, PIC_ERR_INVALID, "bad argument");
+  InstHost& ih = h->inst[instance];
+  Scalars s;
+  int rc = read_status(h, instance, &s);
+  (void)rc;
+  s.Vc = Vc;
+  s.step = step;
+  s.diag_on = (step % ih.I.diag_every) == 0;
+  std::vector<double> q((size_t)ih.cfg.n_avg, 0.0);
+  for (int k = 0; k < n && k < ih.cfg.n_avg; ++k) q[k] = qhist[k];
+  cudaError_t e = cudaMemcpyAsync(ih.I.S, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ih.I.qhist, q.data(), q.size() * 8, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_circuit");
+  return PIC_OK;
+}
+
+int pic_set_next_id(pic_handle* h, int instance, int64_t next_id) {
+  if (bad_instance(h, instance) || next_id < 0) return fail(h, PIC_ERR_INVALID, "bad argument");
+  Scalars s;
+  read_status(h, instance, &s);
+  s.next_id = next_id;
+  cudaError_t e = cudaMemcpyAsync(h->inst[instance].I.S, &s, sizeof(s), cudaMemcpyHostToDevice,
+                                  h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_next_id");
+  return PIC_OK;
+}
+
+int pic_get_next_id(pic_handle* h, int instance, int64_t* next_id) {
+  if (bad_instance(h, instance) || !next_id) return fail(h, PIC_ERR_INVALID, "bad argument");
+  Scalars s;
+  const int rc = read_status(h, instance, &s);
+  *next_id = s.next_id;
+  return rc;
+}
+
+int pic_step(pic_handle* h, int64_t nsteps) {
+  if (!h || nsteps < 0) return fail(h, PIC_ERR_INVALID, "bad argument");
+  StepMarks marks{prof_mark, &h->prof};
+  for (int64_t s = 0; s < nsteps; ++s) {
+    for (InstHost& ih : h->inst) {
+      cudaError_t e = launch_step(ih.I, ih.pw, h->num_sms, h->stream,
+                                  h->prof.on ? &marks : nullptr);
+      if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
+      swap_buffers(ih, 0);
+      swap_buffers(ih, 1);
+    }
+  }
+  return PIC_OK;
+}
+
+int pic_sync(pic_handle* h) {
+  if (!h) return PIC_ERR_INVALID;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sync");
+  for (int k = 0; k < (int)h->inst.size(); ++k) {
+    const int rc = read_status(h, k, nullptr);
+    if (rc != PIC_OK) return rc;
+  }
+  return PIC_OK;
+}
+
+int pic_diagnostics(pic_handle* h, int instance, pic_diag* out) {
+  if (bad_instance(h, instance) || !out) return fail(h, PIC_ERR_INVALID, "bad argument");
+  DiagDev d;
+  cudaError_t e = cudaMemcpyAsync(&d, h->inst[instance].I.diag, sizeof(d), cudaMemcpyDeviceToHost,
+                                  h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics");
+  out->t = d.t;
+  out->I_cath = d.I_cath;
+  out->V_cath = d.V_cath;
+  out->n_e_peak = d.n_e_peak;
+  out->n_i_peak = d.n_i_peak;
+  out->W_field = d.W_field;
+  out->K_e = d.K_e;
+  out->K_i = d.K_i;
+  out->N_e = d.N_e;
+  out->N_i = d.N_i;
+  out->n_ion_cath = d.n_ion_cath;
+  out->n_e_cath = d.n_e_cath;
+  out->n_sey = d.n_sey;
+  out->n_ionize = d.n_ionize;
+  out->n_excite = d.n_excite;
+  out->n_elastic = d.n_elastic;
+  out->step = d.step;
+  out->particle_steps = d.particle_steps;
+  out->poisson_iters = d.poisson_iters;
+  out->poisson_resid = d.poisson_resid;
+  Scalars s;
+  const int rc = read_status(h, instance, &s);
+  out->status = rc;
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// checkpoints: a flat little-endian file
+//   "PICCKPT1", pic_config, Scalars, qhist[n_avg], phi[nodes],
+//   then per species: n, r[n], z[n], vr[n], vt[n], vz[n], id[n]
+// ---------------------------------------------------------------------------
+int pic_save(pic_handle* h, int instance, const char* path) {
+  if (bad_instance(h, instance) || !path) return fail(h, PIC_ERR_INVALID, "bad argument");
+  InstHost& ih = h->inst[instance];
+  Scalars s;
+  int rc = read_status(h, instance, &s);
+  if (rc != PIC_OK) return rc;
+  const pic_config& c = ih.cfg;
+  const size_t nn = (size_t)(c.nr + 1) * (c.nz + 1);
+  std::vector<double> qh((size_t)c.n_avg), phi(nn);
+  cudaError_t e = cudaMemcpy(qh.data(), ih.I.qhist, qh.size() * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(phi.data(), ih.I.phi, nn * 8, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "save copy");
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(h, PIC_ERR_IO, std::string("cannot open ") + path);
+  bool ok = std::fwrite("PICCKPT1", 1, 8, f) == 8;
+  ok = ok && std::fwrite(&c, sizeof(c), 1, f) == 1;
+  ok = ok && std::fwrite(&s, sizeof(s), 1, f) == 1;
+  ok = ok && std::fwrite(qh.data(), 8, qh.size(), f) == qh.size();
+  ok = ok && std::fwrite(phi.data(), 8, nn, f) == nn;
+  for (int sp = 0; sp < 2 && ok; ++sp) {
+    const long long n = s.n[sp];
+    std::vector<double> buf((size_t)n);
+    std::vector<long long> ids((size_t)n);
+    ok = std::fwrite(&n, 8, 1, f) == 1;
+    const ParticlesDev& P = ih.I.cur[sp];
+    for (double* src : {P.r, P.z, P.vr, P.vt, P.vz}) {
+      if (!ok) break;
+      if (n > 0 && cudaMemcpy(buf.data(), src, (size_t)n * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+        ok = false;
+      ok = ok && std::fwrite(buf.data(), 8, (size_t)n, f) == (size_t)n;
+    }
+    if (ok && n > 0 && cudaMemcpy(ids.data(), P.id, (size_t)n * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      ok = false;
+    ok = ok && std::fwrite(ids.data(), 8, (size_t)n, f) == (size_t)n;
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? PIC_OK : fail(h, PIC_ERR_IO, "checkpoint write failed");
+}
+
+int pic_load(pic_handle* h, int instance, const char* path) {
+  if (bad_instance(h, instance) || !path) return fail(h, PIC_ERR_INVALID, "bad argument");
+  InstHost& ih = h->inst[instance];
+  const pic_config& c = ih.cfg;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(h, PIC_ERR_IO, std::string("cannot open ") + path);
+  char magic[8];
+  pic_config fc;
+  Scalars s;
+  const size_t nn = (size_t)(c.nr + 1) * (c.nz + 1);
+  std::vector<double> qh((size_t)c.n_avg), phi(nn);
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "PICCKPT1", 8) == 0;
+  ok = ok && std::fread(&fc, sizeof(fc), 1, f) == 1;
+  ok = ok && fc.nr == c.nr && fc.nz == c.nz && fc.n_avg == c.n_avg;
+  ok = ok && std::fread(&s, sizeof(s), 1, f) == 1;
+  ok = ok && std::fread(qh.data(), 8, qh.size(), f) == qh.size();
+  ok = ok && std::fread(phi.data(), 8, nn, f) == nn;
+  std::vector<double> arr[2][5];
+  std::vector<long long> ids[2];
+  long long n[2] = {0, 0};
+  for (int sp = 0; sp < 2 && ok; ++sp) {
+    ok = std::fread(&n[sp], 8, 1, f) == 1 && n[sp] >= 0 && n[sp] <= ih.I.cap[sp];
+    for (int k = 0; k < 5 && ok; ++k) {
+      arr[sp][k].resize((size_t)n[sp]);
+      ok = std::fread(arr[sp][k].data(), 8, (size_t)n[sp], f) == (size_t)n[sp];
+    }
+    if (ok) {
+      ids[sp].resize((size_t)n[sp]);
+      ok = std::fread(ids[sp].data(), 8, (size_t)n[sp], f) == (size_t)n[sp];
+    }
+  }
+  std::fclose(f);
+  if (!ok) return fail(h, PIC_ERR_IO, "checkpoint read failed or does not match the handle");
+  for (int sp = 0; sp < 2; ++sp) {
+    const int rc = pic_set_particles(h, instance, sp, n[sp], arr[sp][0].data(), arr[sp][1].data(),
+                                     arr[sp][2].data(), arr[sp][3].data(), arr[sp][4].data(),
+                                     (const int64_t*)ids[sp].data(), 0);
+    if (rc != PIC_OK) return rc;
+  }
+  Scalars cur;
+  read_status(h, instance, &cur);
+  s.n[0] = cur.n[0];
+  s.n[1] = cur.n[1];
+  cudaError_t e = cudaMemcpy(ih.I.S, &s, sizeof(s), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ih.I.qhist, qh.data(), qh.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ih.I.phi, phi.data(), nn * 8, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(h, e, "load copy");
+  return PIC_OK;
+}
+
+int pic_profile(pic_handle* h, int enable) {
+  if (!h) return PIC_ERR_INVALID;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "profile");
+  h->prof.on = enable != 0;
+  if (enable) {
+    h->prof.used = 0;
+    h->prof.recs.clear();
+  }
+  return PIC_OK;
+}
+
+int pic_profile_read(pic_handle* h, pic_kernel_time* out, int max, int* n_out) {
+  if (!h || !out || max < 0) return PIC_ERR_INVALID;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "profile read");
+  double tot[G_COUNT] = {};
+  long long cnt[G_COUNT] = {};
+  for (const Profiler::Rec& r : h->prof.recs) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, r.b, r.e) == cudaSuccess) {
+      tot[r.group] += ms;
+      cnt[r.group] += 1;
+    }
+  }
+  for (int g = 0; g < G_COUNT && g < max; ++g) {
+    out[g].name = kGroupNames[g];
+    out[g].launches = cnt[g];
+    out[g].total_ms = tot[g];
+  }
+  if (n_out) *n_out = G_COUNT;
+  return PIC_OK;
+}
+
+size_t pic_poisson_workspace_bytes(int nr, int nz) {
+  if (nr < 2 || nz < 2) return 0;
+  return poisson_work_bytes(nr, nz) + 256;
+}
+
+int pic_poisson_solve(int nr, int nz, double R, double L, double tol, int max_iter,
+                      const double* Q_dev, double* phi_dev, void* work_dev, void* cuda_stream,
+                      int* iters, double* resid) {
+  if (nr < 2 || nz < 2 || (nr & 1) || (nz & 1) || !(R > 0) || !(L > 0) || !(tol > 0) ||
+      max_iter < 1 || !Q_dev || !phi_dev || !work_dev || ((uintptr_t)work_dev & 255))
+    return PIC_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t wb = poisson_work_bytes(nr, nz);
+  cudaError_t e = cudaMemsetAsync(work_dev, 0, wb + 256, st);
+  if (e != cudaSuccess) return PIC_ERR_CUDA;
+  PoissonWork* pw = poisson_work_init(work_dev, nr, nz, R, L, sms);
+  char* tailp = (char*)work_dev + wb;
+  int* status = (int*)tailp;
+  int* it_dev = (int*)(tailp + 16);
+  double* res_dev = (double*)(tailp + 32);
+  e = launch_poisson(pw, Q_dev, phi_dev, tol, max_iter, status, it_dev, res_dev, st);
+  poisson_work_free(pw);
+  if (e != cudaSuccess) return PIC_ERR_CUDA;
+  int hs[2] = {0, 0};
+  double hr = 0.0;
+  e = cudaMemcpyAsync(hs, status, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs[1], it_dev, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hr, res_dev, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return PIC_ERR_CUDA;
+  if (iters) *iters = hs[1];
+  if (resid) *resid = hr;
+  return status_code(hs[0]);
+}
+
+}  // extern "C"

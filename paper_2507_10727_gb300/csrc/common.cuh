@@ -1,0 +1,225 @@
+// common.cuh -- device-side types and helpers of the GB300 PIC-MCC library.
+//
+// Layout decisions (all memory is HBM-resident for the whole run):
+//  * particles: structure of arrays per species, double buffered, sorted by a
+//    tile-major cell key (8 x 8 cell tiles) so that a CTA's chunk of
+//    consecutive particles covers a compact patch of the grid;
+//  * node arrays (phi, Q): (nr+1) x (nz+1), z fastest;
+//  * per-cell gather tables: the field and the magnetic field around a cell
+//    folded into polynomial coefficients in the in-cell offsets, so one cell
+//    lookup (contiguous 16-byte loads through L1) feeds the push;
+//  * charge: per-species node sums in 44-bit fixed point (u64), so that the
+//    deposit is exact, order independent and deterministic; weights are
+//    rounded to 2^-44 of a macroparticle and sum to exactly one.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pic {
+
+// CODATA 2018
+constexpr double kQe = 1.602176634e-19;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kBoltz = 1.380649e-23;
+constexpr double kPi = 3.14159265358979323846;
+
+constexpr int kTile = 8;                 // cells per tile side
+constexpr int kTileCells = kTile * kTile;
+constexpr int kFixBits = 44;             // fixed-point fraction bits of the deposit
+constexpr double kFixOne = 17592186044416.0;          // 2^44
+constexpr double kFixInv = 1.0 / 17592186044416.0;    // 2^-44
+
+// latched status bits (device side); translated to pic_status by the host
+enum : int {
+  ST_CAPACITY = 1,
+  ST_NONCONV = 2,
+  ST_NAN = 4,
+  ST_TIMEOUT = 8,
+};
+constexpr int ST_FATAL = ST_CAPACITY | ST_NONCONV | ST_NAN | ST_TIMEOUT;
+
+struct ParticlesDev {
+  double *r, *z, *vr, *vt, *vz;
+  long long* id;
+};
+
+struct BirthsDev {
+  double *r, *z, *vr, *vt, *vz;
+  unsigned long long* pkey;   // (parent id << 2) | kind
+  int* cell;                  // cell key of the birth position
+  long long* id;              // id assigned by the births kernel
+  unsigned long long* skey;   // sort scratch: keys (power-of-two length)
+  unsigned int* sidx;         // sort scratch: indices
+  long long sort_len;         // length of the scratch arrays
+};
+
+// Device-resident scalars of one instance.
+struct Scalars {
+  long long n[2];          // particles in the sorted arrays
+  long long n_next[2];     // after the current step's scatter
+  long long nbirth[2];     // births of the current step
+  long long step;          // index of the step being taken
+  long long next_id;
+  unsigned long long cnt_ion_cath, cnt_e_cath, cnt_sey;
+  unsigned long long cnt_ionize, cnt_excite, cnt_elastic;
+  double Vc;               // cathode potential used by the current field
+  double I;                // cathode current (running mean)
+  double K[2];             // kinetic energy accumulators of the step
+  double W;                // field energy of the step's phi
+  unsigned long long peak_bits[2];  // max density (bits of a positive double)
+  int status;
+  int diag_on;
+  int poisson_iters;
+  int pad0;
+  double poisson_resid;
+  long long pushed;        // cumulative particle-steps
+};
+
+struct DiagDev {           // mirrors pic_diag
+  double t, I_cath, V_cath, n_e_peak, n_i_peak, W_field, K_e, K_i;
+  long long N_e, N_i;
+  long long n_ion_cath, n_e_cath, n_sey, n_ionize, n_excite, n_elastic;
+  long long step;
+  long long particle_steps;
+  int poisson_iters;
+  int status;
+  double poisson_resid;
+};
+
+// Everything a kernel needs about one instance; passed by value.
+struct Inst {
+  // geometry
+  int nr, nz, ntz, nkey;   // ntz: tiles along z; nkey: number of cell keys
+  int m_cath;              // last radial node index of the cathode (r_m <= Rc)
+  double R, L, Rc, dr, dz, inv_dr, inv_dz;
+  double dt;
+  // species
+  double weight;
+  double qm[2], mass[2], gamma[2];
+  // collisions
+  double n_gas, T_gas, m_ion, sigma_el, ion_a, ion_I, exc_C, exc_E, nu_max, p_null;
+  unsigned long long seed;
+  // switches
+  int gather, rweight, mcc_on, push_on, field_on, walls_reflect, circuit_mode, n_avg;
+  int diag_every;
+  double Vc_fixed, Vs, Rext;
+  double poisson_tol;
+  int poisson_max_iter;
+  long long cap[2], birth_cap;
+  // device arrays
+  ParticlesDev cur[2], nxt[2];
+  int* key[2];
+  int* counts[2];
+  int* cursor[2];
+  BirthsDev births[2];
+  double* phi;
+  double* Q;
+  unsigned long long* qacc[2];
+  double4_32a* etab;           // EC: 1 per cell {Er0, dEr/dfz, Ez0, dEz/dwr}; MC: 2 per cell
+  double4_32a* btab;           // 2 per cell: {Br c0..c3}, {Bz c0..c3}
+  double* qhist;
+  Scalars* S;
+  DiagDev* diag;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x64(unsigned long long c0, unsigned long long c1,
+                                           unsigned long long c2, unsigned long long c3,
+                                           unsigned long long k0, unsigned long long k1,
+                                           unsigned long long out[4]) {
+  const unsigned long long M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const unsigned long long W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) { k0 += W0; k1 += W1; }
+    unsigned long long hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+    unsigned long long hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+    unsigned long long y0 = hi1 ^ c1 ^ k0, y2 = hi0 ^ c3 ^ k1;
+    c0 = y0; c1 = lo1; c2 = y2; c3 = lo0;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+__device__ __forceinline__ double u01(unsigned long long x) {
+  return (double)(x >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// four uniforms of stream k for particle id at step s of a species
+__device__ __forceinline__ void draws(const Inst& I, int sp, long long id, long long s, int k,
+                                      double u[4]) {
+  unsigned long long w[4];
+  philox4x64((unsigned long long)id, (unsigned long long)s, (unsigned long long)k, 0ULL, I.seed,
+             (unsigned long long)sp, w);
+  u[0] = u01(w[0]); u[1] = u01(w[1]); u[2] = u01(w[2]); u[3] = u01(w[3]);
+}
+
+// ---------------------------------------------------------------------------
+// grid helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void locate(double x, double inv_d, int ncell, int& k, double& f) {
+  double s = x * inv_d;
+  int i = (int)s;                       // x >= 0 for particles inside the domain
+  if (i > ncell - 1) i = ncell - 1;
+  k = i;
+  f = s - (double)i;
+}
+
+__device__ __forceinline__ int cell_key(const Inst& I, int m, int n) {
+  int tile = (m >> 3) * I.ntz + (n >> 3);
+  return tile * kTileCells + ((m & 7) << 3) + (n & 7);
+}
+
+__device__ __forceinline__ int node_index(const Inst& I, int m, int n) { return m * (I.nz + 1) + n; }
+
+// radial weight of node m+1 (tent in r, or in r^2 for volume weighting)
+__device__ __forceinline__ double rweight_upper(const Inst& I, double r, int m, double fr) {
+  if (I.rweight == 0) return fr;
+  // (r^2 - r_m^2) / (r_{m+1}^2 - r_m^2) = fr (2m + fr) / (2m + 1)
+  return fr * (2.0 * m + fr) / (2.0 * m + 1.0);
+}
+
+// Fixed-point corner weights of a unit charge at in-cell weights (wr, wz):
+// exact integers summing to 2^44.
+struct FixW { unsigned long long w00, w10, w01, w11; };
+__device__ __forceinline__ FixW fix_weights(double wr, double wz) {
+  double a = wr * kFixOne;               // exact scaling by a power of two
+  double b = wz * kFixOne;
+  unsigned long long i11 = (unsigned long long)__double2ll_rn(a * wz);
+  unsigned long long ir = (unsigned long long)__double2ll_rn(a);
+  unsigned long long iz = (unsigned long long)__double2ll_rn(b);
+  FixW f;
+  f.w11 = i11;
+  f.w10 = ir - i11;
+  f.w01 = iz - i11;
+  f.w00 = (1ULL << kFixBits) - ir - iz + i11;   // modular arithmetic keeps the sum exact
+  return f;
+}
+
+__device__ __forceinline__ double node_area(const Inst& I, int m) {
+  if (m == 0) return kPi * 0.25 * I.dr * I.dr;
+  if (m == I.nr) return kPi * (I.R * I.R - (I.R - 0.5 * I.dr) * (I.R - 0.5 * I.dr));
+  return 2.0 * kPi * (m * I.dr) * I.dr;
+}
+
+__device__ __forceinline__ double node_volume(const Inst& I, int m, int n) {
+  double h = (n == 0 || n == I.nz) ? 0.5 : 1.0;
+  return node_area(I, m) * I.dz * h;
+}
+
+__host__ __device__ __forceinline__ double4_32a make_d4(double x, double y, double z, double w) {
+  double4_32a v;
+  v.x = x; v.y = y; v.z = z; v.w = w;
+  return v;
+}
+
+__device__ __forceinline__ double global_time_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return (double)t;
+}
+
+}  // namespace pic

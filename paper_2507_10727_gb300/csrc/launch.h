@@ -1,0 +1,47 @@
+// launch.h -- host-side launchers of the kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace pic {
+
+struct PoissonWork;  // defined in poisson.cu
+
+// optional per-kernel-group event marks around the launches of a step
+enum StepGroup {
+  G_FIELD = 0, G_PUSH_E, G_PUSH_I, G_BIRTHS, G_SCAN, G_SCATTER, G_CHARGE, G_CIRCUIT,
+  G_POISSON, G_STEP_END, G_COUNT
+};
+struct StepMarks {
+  void (*mark)(void* ctx, int group, bool begin, cudaStream_t st);
+  void* ctx;
+};
+
+// one time step of one instance (all kernels of the step, in order)
+cudaError_t launch_step(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_t st,
+                        const StepMarks* marks);
+
+// sort the particles of species `sp` currently in cur[sp] into nxt[sp]
+// (keys, histogram, scan, scatter); the caller swaps cur/nxt afterwards
+cudaError_t launch_sort_species(const Inst& I, int sp, int num_sms, cudaStream_t st);
+
+// set the particle count of species sp (set-up)
+cudaError_t launch_set_n(const Inst& I, int sp, long long n, cudaStream_t st);
+
+// deposit the current particles, set the cathode values and solve phi
+cudaError_t launch_solve_fields(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_t st);
+
+// compute node charge Q from the fixed-point sums (and clear them)
+cudaError_t launch_charge(const Inst& I, cudaStream_t st);
+
+// Poisson workspace
+size_t poisson_work_bytes(int nr, int nz);
+PoissonWork* poisson_work_init(void* base, int nr, int nz, double R, double L, int num_sms);
+void poisson_work_free(PoissonWork* pw);
+// solve A phi = Q (+ Dirichlet values held in phi's boundary nodes)
+cudaError_t launch_poisson(PoissonWork* pw, const double* Q, double* phi, double tol, int max_iter,
+                           int* status_dev, int* iters_dev, double* resid_dev, cudaStream_t st);
+
+}  // namespace pic

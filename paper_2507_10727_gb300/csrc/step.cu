@@ -1,0 +1,831 @@
+// step.cu -- the per-step particle kernels of the RZ PIC-MCC method.
+//
+// Order inside one step (arXiv:2507.10727, Sections 2-4):
+//   k_field_tables    E from phi (edge-centred for EC-PIC, nodal for MC-PIC)
+//                     folded into per-cell gather tables; field energy
+//   k_push<e>, <i>    gather + Boris push + walls + secondary emission + MCC,
+//                     new cell key, histogram, charge deposit of the new
+//                     position into a shared-memory patch (no per-particle
+//                     global atomics), births appended to a birth buffer
+//   k_births          births sorted by (parent id, kind), ids assigned
+//   k_scan            exclusive scan of the cell histogram -> cursors
+//   k_scatter         counting-sort scatter into the other buffer
+//   k_charge          node charge Q from the fixed-point sums
+//   k_circuit         cathode current, V_c, cathode Dirichlet values
+//   (Poisson solve, poisson.cu)
+//   k_step_end        diagnostics record, counters, step index
+#include <cstdio>
+
+#include "common.cuh"
+#include "launch.h"
+
+namespace pic {
+
+constexpr int kPushThreads = 256;
+constexpr int kPPT = 8;                          // particles per thread per chunk
+constexpr int kChunk = kPushThreads * kPPT;      // particles per chunk
+constexpr int kHalo = 3;                         // cells a particle may move and still hit the patch
+constexpr int kPR = kTile + 2 * kHalo + 1;       // patch nodes in r
+constexpr int kPZ = 2 * kTile + 2 * kHalo + 1;   // patch nodes in z (two tiles along z)
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum of v added atomically to *dst (used for diagnostics only)
+__device__ void block_add(double v, double* dst) {
+  __shared__ double red[32];
+  v = warp_sum(v);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    double s = lane < nw ? red[lane] : 0.0;
+    s = warp_sum(s);
+    if (lane == 0 && s != 0.0) atomicAdd(dst, s);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Field gather tables (Section 2).
+//  EC-PIC: E_r stored on edges [r_{m+1/2}, z_n], interpolated NGP in r
+//  (the cell's own edge) and linear in z; E_z on [r_m, z_{n+1/2}], linear in
+//  r and NGP in z.  Table per cell: {E_r(lower z edge), E_r(upper) -
+//  E_r(lower), E_z(inner r edge), E_z(outer) - E_z(inner)}; with volume
+//  weighting the E_r entries are divided by r_{m+1/2} (dS/dr = 2r / (r_{m+1}^2
+//  - r_m^2) gives E_r a factor r / r_{m+1/2}).
+//  MC-PIC: nodal E (mean of the adjacent edges, one-sided on walls, E_r = 0
+//  on the axis) in bilinear coefficient form in the deposit's weights.
+// Field energy (diagnostic): 1/2 sum over edges of a_e (delta phi)^2.
+// ---------------------------------------------------------------------------
+__global__ void k_field_tables(Inst I) {
+  const Scalars* S = I.S;
+  if (S->status & ST_FATAL) return;
+  const int ncell = I.nr * I.nz;
+  const bool diag = S->diag_on != 0;
+  double wloc = 0.0;
+  const int nz1 = I.nz + 1;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+    const int m = c / I.nz, n = c - m * I.nz;
+    const double* ph = I.phi;
+    const double p00 = ph[m * nz1 + n], p01 = ph[m * nz1 + n + 1];
+    const double p10 = ph[(m + 1) * nz1 + n], p11 = ph[(m + 1) * nz1 + n + 1];
+    const int key = cell_key(I, m, n);
+    if (I.gather == 0) {
+      double4_32a t = make_d4(0.0, 0.0, 0.0, 0.0);
+      if (I.field_on) {
+        double er_lo = -(p10 - p00) * I.inv_dr, er_hi = -(p11 - p01) * I.inv_dr;
+        double ez_lo = -(p01 - p00) * I.inv_dz, ez_hi = -(p11 - p10) * I.inv_dz;
+        if (I.rweight == 1) {
+          double s = 1.0 / ((m + 0.5) * I.dr);
+          er_lo *= s;
+          er_hi *= s;
+        }
+        t = make_d4(er_lo, er_hi - er_lo, ez_lo, ez_hi - ez_lo);
+      }
+      I.etab[key] = t;
+    } else {
+      double er[2][2], ez[2][2];
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+          const int mm = m + a, nn = n + b;
+          double e;
+          if (mm == 0) e = 0.0;
+          else if (mm == I.nr) e = -(ph[mm * nz1 + nn] - ph[(mm - 1) * nz1 + nn]) * I.inv_dr;
+          else e = -(ph[(mm + 1) * nz1 + nn] - ph[(mm - 1) * nz1 + nn]) * (0.5 * I.inv_dr);
+          er[a][b] = e;
+          if (nn == 0) e = -(ph[mm * nz1 + 1] - ph[mm * nz1]) * I.inv_dz;
+          else if (nn == I.nz) e = -(ph[mm * nz1 + nn] - ph[mm * nz1 + nn - 1]) * I.inv_dz;
+          else e = -(ph[mm * nz1 + nn + 1] - ph[mm * nz1 + nn - 1]) * (0.5 * I.inv_dz);
+          ez[a][b] = e;
+        }
+      double4_32a tr = make_d4(0.0, 0.0, 0.0, 0.0), tz = tr;
+      if (I.field_on) {
+        tr = make_d4(er[0][0], er[1][0] - er[0][0], er[0][1] - er[0][0],
+                          er[1][1] - er[1][0] - er[0][1] + er[0][0]);
+        tz = make_d4(ez[0][0], ez[1][0] - ez[0][0], ez[0][1] - ez[0][0],
+                          ez[1][1] - ez[1][0] - ez[0][1] + ez[0][0]);
+      }
+      I.etab[2 * key] = tr;
+      I.etab[2 * key + 1] = tz;
+    }
+    if (diag) {
+      // edges owned by this cell: r-edge (m,n), z-edge (m,n); the last row /
+      // column also own r-edge (m,nz) and z-edge (nr,n)
+      const double c0 = 2.0 * kPi * kEps0;
+      const double ar = c0 * (m + 0.5) * I.dz;
+      const double az = kEps0 * node_area(I, m) / I.dz;
+      double d = p10 - p00;
+      wloc += 0.5 * ar * (n == 0 ? 0.5 : 1.0) * d * d;
+      d = p01 - p00;
+      wloc += 0.5 * az * d * d;
+      if (n == I.nz - 1) {
+        d = p11 - p01;
+        wloc += 0.5 * ar * 0.5 * d * d;
+      }
+      if (m == I.nr - 1) {
+        d = p11 - p10;
+        wloc += 0.5 * (kEps0 * node_area(I, I.nr) / I.dz) * d * d;
+      }
+    }
+  }
+  if (diag) block_add(wloc, &I.S->W);
+}
+
+// ---------------------------------------------------------------------------
+// births
+// ---------------------------------------------------------------------------
+__device__ void add_birth(const Inst& I, int sp, unsigned long long pkey, double r, double z,
+                          double vr, double vt, double vz) {
+  Scalars* S = I.S;
+  unsigned long long b = atomicAdd((unsigned long long*)&S->nbirth[sp], 1ULL);
+  if ((long long)b >= I.birth_cap) {
+    atomicOr(&S->status, ST_CAPACITY);
+    return;
+  }
+  const BirthsDev& B = I.births[sp];
+  B.r[b] = r; B.z[b] = z; B.vr[b] = vr; B.vt[b] = vt; B.vz[b] = vz;
+  B.pkey[b] = pkey;
+  int m, n;
+  double fr, fz;
+  locate(r, I.inv_dr, I.nr, m, fr);
+  locate(z, I.inv_dz, I.nz, n, fz);
+  const int key = cell_key(I, m, n);
+  B.cell[b] = key;
+  atomicAdd(&I.counts[sp][key], 1);
+  const FixW f = fix_weights(rweight_upper(I, r, m, fr), fz);
+  unsigned long long* q = I.qacc[sp];
+  atomicAdd(q + node_index(I, m, n), f.w00);
+  atomicAdd(q + node_index(I, m + 1, n), f.w10);
+  atomicAdd(q + node_index(I, m, n + 1), f.w01);
+  atomicAdd(q + node_index(I, m + 1, n + 1), f.w11);
+}
+
+// new direction: e rotated by polar angle chi (cos given) and azimuth phi,
+// in the frame (u, w) built from the coordinate axis of e's smallest component
+__device__ __forceinline__ void scatter_dir(const double e[3], double cos_chi, double phi,
+                                            double out[3]) {
+  int a = 0;
+  if (fabs(e[1]) < fabs(e[a])) a = 1;
+  if (fabs(e[2]) < fabs(e[a])) a = 2;
+  double ax[3] = {0.0, 0.0, 0.0};
+  ax[a] = 1.0;
+  double u[3] = {ax[1] * e[2] - ax[2] * e[1], ax[2] * e[0] - ax[0] * e[2],
+                 ax[0] * e[1] - ax[1] * e[0]};
+  const double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  u[0] /= un; u[1] /= un; u[2] /= un;
+  const double w[3] = {e[1] * u[2] - e[2] * u[1], e[2] * u[0] - e[0] * u[2],
+                       e[0] * u[1] - e[1] * u[0]};
+  const double sin_chi = sqrt(fmax(0.0, 1.0 - cos_chi * cos_chi));
+  double sp, cp;
+  sincos(phi, &sp, &cp);
+  for (int j = 0; j < 3; ++j) out[j] = cos_chi * e[j] + sin_chi * (cp * u[j] + sp * w[j]);
+}
+
+// Null-collision MCC for one electron (Section 3, reactions (1a)-(1c), [14]).
+// Returns true when the velocity changed.
+__device__ bool mcc_electron(const Inst& I, long long id, long long step, double r, double z,
+                             double& vr, double& vt, double& vz) {
+  double u[4];
+  draws(I, 0, id, step, 0, u);
+  if (!(u[0] < I.p_null)) return false;
+  const double v[3] = {vr, vt, vz};
+  const double vmag = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  const double E = 0.5 * kMe * vmag * vmag / kQe;
+  const double s_el = E > 0.0 ? I.sigma_el : 0.0;
+  const double s_ex = E > I.exc_E ? I.exc_C * log(E / I.exc_E) / (E * I.exc_E) : 0.0;
+  const double s_io = E > I.ion_I ? I.ion_a * log(E / I.ion_I) / (E * I.ion_I) : 0.0;
+  const double nu_el = I.n_gas * s_el * vmag, nu_ex = I.n_gas * s_ex * vmag;
+  const double nu_io = I.n_gas * s_io * vmag;
+  const double R = u[1] * I.nu_max;
+  const double inv = vmag > 0.0 ? 1.0 / vmag : 1.0;
+  const double e[3] = {v[0] * inv, v[1] * inv, v[2] * inv};
+  const double cos_chi = 1.0 - 2.0 * u[2], phi = 2.0 * kPi * u[3];
+  double Enew;
+  Scalars* S = I.S;
+  if (R < nu_el) {
+    Enew = E * (1.0 - 2.0 * kMe / I.m_ion * (1.0 - cos_chi));
+    atomicAdd(&S->cnt_elastic, 1ULL);
+  } else if (R < nu_el + nu_ex) {
+    Enew = E - I.exc_E;
+    atomicAdd(&S->cnt_excite, 1ULL);
+  } else if (R < nu_el + nu_ex + nu_io) {
+    double u2[4], g[4];
+    draws(I, 0, id, step, 1, u2);
+    const double Ex = E - I.ion_I;
+    Enew = u2[0] * Ex;
+    const double E2 = Ex - Enew;
+    double d2[3];
+    scatter_dir(e, 1.0 - 2.0 * u2[1], 2.0 * kPi * u2[2], d2);
+    const double v2 = sqrt(2.0 * E2 * kQe / kMe);
+    const unsigned long long key = ((unsigned long long)id << 2) | 0ULL;
+    add_birth(I, 0, key, r, z, v2 * d2[0], v2 * d2[1], v2 * d2[2]);
+    draws(I, 0, id, step, 4, g);
+    const double sig = sqrt(kBoltz * I.T_gas / I.m_ion);
+    const double rho1 = sqrt(-2.0 * log(1.0 - g[0])), th1 = 2.0 * kPi * g[1];
+    const double rho2 = sqrt(-2.0 * log(1.0 - g[2])), th2 = 2.0 * kPi * g[3];
+    double s1, c1, s2, c2;
+    sincos(th1, &s1, &c1);
+    sincos(th2, &s2, &c2);
+    add_birth(I, 1, key, r, z, sig * rho1 * c1, sig * rho1 * s1, sig * rho2 * c2);
+    atomicAdd(&S->cnt_ionize, 1ULL);
+  } else {
+    return false;
+  }
+  double d[3];
+  scatter_dir(e, cos_chi, phi, d);
+  const double vn = sqrt(2.0 * Enew * kQe / kMe);
+  vr = vn * d[0];
+  vt = vn * d[1];
+  vz = vn * d[2];
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// The push.  One CTA processes chunks of kChunk consecutive (cell-sorted)
+// particles; the chunk's charge goes into a shared patch of kPR x kPZ nodes
+// anchored at the tile of the chunk's first particle, flushed with one
+// atomic per touched node.  Particles whose new 4 nodes fall outside the
+// patch (fast movers, chunk tails in sparse regions) add to global memory.
+// ---------------------------------------------------------------------------
+template <int SP, int GATHER>
+__global__ void __launch_bounds__(kPushThreads) k_push(Inst I) {
+  Scalars* S = I.S;
+  if (S->status & ST_FATAL) return;
+  __shared__ unsigned long long patch[kPR * kPZ];
+  __shared__ int anchor[2];
+  const long long n = S->n[SP];
+  const long long step = S->step;
+  const bool diag = S->diag_on != 0;
+  const ParticlesDev P = I.cur[SP];
+  const double h = 0.5 * I.qm[SP] * I.dt;
+  const double dt = I.dt;
+  const int lane = threadIdx.x & 31;
+  double Kloc = 0.0;
+  for (int k = threadIdx.x; k < kPR * kPZ; k += blockDim.x) patch[k] = 0ULL;
+  for (long long c0 = (long long)blockIdx.x * kChunk; c0 < n; c0 += (long long)gridDim.x * kChunk) {
+    if (threadIdx.x == 0) {
+      int m, nn;
+      double f;
+      locate(P.r[c0], I.inv_dr, I.nr, m, f);
+      locate(P.z[c0], I.inv_dz, I.nz, nn, f);
+      anchor[0] = (m & ~(kTile - 1)) - kHalo;
+      anchor[1] = (nn & ~(kTile - 1)) - kHalo;
+    }
+    __syncthreads();
+    const int pm0 = anchor[0], pn0 = anchor[1];
+#pragma unroll 1
+    for (int j = 0; j < kPPT; ++j) {
+      const long long i = c0 + (long long)j * kPushThreads + threadIdx.x;
+      int newkey = -1;
+      if (i < n) {
+        double r = P.r[i], z = P.z[i], vr = P.vr[i], vt = P.vt[i], vz = P.vz[i];
+        const double v2old = vr * vr + vt * vt + vz * vz;
+        double x1 = r, y1 = 0.0, r1 = r, z1 = z;
+        if (I.push_on) {
+          int m, nn;
+          double fr, fz;
+          locate(r, I.inv_dr, I.nr, m, fr);
+          locate(z, I.inv_dz, I.nz, nn, fz);
+          const int ck = cell_key(I, m, nn);
+          // gather E
+          double Er, Ez;
+          if (GATHER == 0) {
+            const double4_32a t = I.etab[ck];
+            const double wr = rweight_upper(I, r, m, fr);
+            Er = t.x + t.y * fz;
+            if (I.rweight == 1) Er *= r;
+            Ez = t.z + t.w * wr;
+          } else {
+            const double wr = rweight_upper(I, r, m, fr);
+            const double4_32a a = I.etab[2 * ck];
+            const double4_32a b = I.etab[2 * ck + 1];
+            Er = a.x + wr * (a.y + fz * a.w) + fz * a.z;
+            Ez = b.x + wr * (b.y + fz * b.w) + fz * b.z;
+          }
+          // gather B (bilinear node table)
+          const double4_32a br = I.btab[2 * ck];
+          const double4_32a bz = I.btab[2 * ck + 1];
+          const double Br = br.x + fr * (br.y + fz * br.w) + fz * br.z;
+          const double Bz = bz.x + fr * (bz.y + fz * bz.w) + fz * bz.z;
+          // Boris: half kick, rotation about B, half kick
+          const double ax = vr + h * Er, ay = vt, az = vz + h * Ez;
+          const double tx = h * Br, tz = h * Bz;
+          const double f2 = 2.0 / (1.0 + tx * tx + tz * tz);
+          const double sx = f2 * tx, sz = f2 * tz;
+          const double px = ax + ay * tz;
+          const double py = ay + (az * tx - ax * tz);
+          const double pz = az - ay * tx;
+          const double vx = ax + py * sz + h * Er;
+          const double vy = ay + (pz * sx - px * sz);
+          const double vzn = az - py * sx + h * Ez;
+          // straight move, then rotate the frame onto the new radius
+          x1 = r + vx * dt;
+          y1 = vy * dt;
+          z1 = z + vzn * dt;
+          const double s2 = x1 * x1 + y1 * y1;
+          if (s2 > 0.0) {
+            const double inv = rsqrt(s2);
+            r1 = s2 * inv;
+            vr = (x1 * vx + y1 * vy) * inv;
+            vt = (x1 * vy - y1 * vx) * inv;
+          } else {
+            r1 = 0.0;
+            vr = vx;
+            vt = vy;
+          }
+          vz = vzn;
+        }
+        if (diag) Kloc += 0.5 * I.mass[SP] * I.weight * 0.5 * (v2old + vr * vr + vt * vt + vz * vz);
+        bool alive = true;
+        if (I.walls_reflect) {
+          if (z1 < 0.0) { z1 = -z1; vz = -vz; }
+          if (z1 >= I.L) { z1 = 2.0 * I.L - z1; vz = -vz; if (z1 >= I.L) z1 = nextafter(I.L, 0.0); }
+          if (r1 >= I.R) { r1 = 2.0 * I.R - r1; vr = -vr; if (r1 >= I.R) r1 = nextafter(I.R, 0.0); }
+        } else if (z1 < 0.0 || z1 >= I.L || r1 >= I.R) {
+          alive = false;
+          if (z1 < 0.0) {
+            const double tc = z / (z - z1);
+            const double xh = r + tc * (x1 - r), yh = tc * y1;
+            const double rhit = sqrt(xh * xh + yh * yh);
+            if (rhit <= I.Rc) {
+              // cathode impact (Section 3): tally; secondary electron with
+              // probability gamma, born at the impact point at rest
+              atomicAdd(SP == 1 ? &S->cnt_ion_cath : &S->cnt_e_cath, 1ULL);
+              if (I.gamma[SP] > 0.0) {
+                const long long id = P.id[i];
+                double u[4];
+                draws(I, SP, id, step, 2, u);
+                if (u[0] < I.gamma[SP]) {
+                  atomicAdd(&S->cnt_sey, 1ULL);
+                  add_birth(I, 0, ((unsigned long long)id << 2) | (SP == 1 ? 1ULL : 2ULL), rhit,
+                            0.0, 0.0, 0.0, 0.0);
+                }
+              }
+            }
+          }
+        }
+        if (alive) {
+          if (!(isfinite(r1) && isfinite(z1) && isfinite(vr) && isfinite(vt) && isfinite(vz))) {
+            atomicOr(&S->status, ST_NAN);
+            alive = false;
+          }
+        }
+        if (alive) {
+          if (SP == 0 && I.mcc_on) mcc_electron(I, P.id[i], step, r1, z1, vr, vt, vz);
+          int m1, n1;
+          double fr1, fz1;
+          locate(r1, I.inv_dr, I.nr, m1, fr1);
+          locate(z1, I.inv_dz, I.nz, n1, fz1);
+          newkey = cell_key(I, m1, n1);
+          P.r[i] = r1; P.z[i] = z1; P.vr[i] = vr; P.vt[i] = vt; P.vz[i] = vz;
+          // deposit x^{n+1} (Section 2: tent functions)
+          const FixW f = fix_weights(rweight_upper(I, r1, m1, fr1), fz1);
+          const int lm = m1 - pm0, ln = n1 - pn0;
+          if (lm >= 0 && lm + 1 < kPR && ln >= 0 && ln + 1 < kPZ) {
+            unsigned long long* p = patch + lm * kPZ + ln;
+            atomicAdd(p, f.w00);
+            atomicAdd(p + kPZ, f.w10);
+            atomicAdd(p + 1, f.w01);
+            atomicAdd(p + kPZ + 1, f.w11);
+          } else {
+            unsigned long long* q = I.qacc[SP];
+            atomicAdd(q + node_index(I, m1, n1), f.w00);
+            atomicAdd(q + node_index(I, m1 + 1, n1), f.w10);
+            atomicAdd(q + node_index(I, m1, n1 + 1), f.w01);
+            atomicAdd(q + node_index(I, m1 + 1, n1 + 1), f.w11);
+          }
+        }
+        I.key[SP][i] = newkey;
+      }
+      // histogram of new cells, aggregated over the lanes of a warp that
+      // share a cell (sorted input keeps most of a warp in one cell)
+      const unsigned peers = __match_any_sync(0xffffffffu, newkey);
+      if (newkey >= 0 && lane == __ffs(peers) - 1) atomicAdd(&I.counts[SP][newkey], __popc(peers));
+    }
+    __syncthreads();
+    // flush the patch
+    for (int k = threadIdx.x; k < kPR * kPZ; k += blockDim.x) {
+      const unsigned long long v = patch[k];
+      if (v != 0ULL) {
+        const int gm = pm0 + k / kPZ, gn = pn0 + k % kPZ;
+        atomicAdd(I.qacc[SP] + node_index(I, gm, gn), v);
+        patch[k] = 0ULL;
+      }
+    }
+    __syncthreads();
+  }
+  if (diag) block_add(Kloc, &I.S->K[SP]);
+}
+
+// ---------------------------------------------------------------------------
+// Births: sort each species' births by (parent id, kind) and hand out ids
+// next_id, next_id + 1, ... (electrons first, then ions).  One CTA; bitonic
+// sort in shared memory up to kSmemSort entries, in global scratch beyond.
+// ---------------------------------------------------------------------------
+constexpr int kSmemSort = 4096;
+
+__device__ void bitonic(unsigned long long* key, unsigned int* idx, int P) {
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const unsigned long long a = key[i], b = key[l];
+          if ((a > b) == up) {
+            key[i] = b;
+            key[l] = a;
+            const unsigned int t = idx[i];
+            idx[i] = idx[l];
+            idx[l] = t;
+          }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_births(Inst I) {
+  Scalars* S = I.S;
+  if (S->status & ST_FATAL) return;
+  __shared__ unsigned long long skey[kSmemSort];
+  __shared__ unsigned int sidx[kSmemSort];
+  long long base = S->next_id;
+  for (int sp = 0; sp < 2; ++sp) {
+    const long long nb = S->nbirth[sp] < I.birth_cap ? S->nbirth[sp] : I.birth_cap;
+    if (nb == 0) continue;
+    int P = 1;
+    while (P < nb) P <<= 1;
+    unsigned long long* key = skey;
+    unsigned int* idx = sidx;
+    if (P > kSmemSort) {
+      key = I.births[sp].skey;
+      idx = I.births[sp].sidx;
+    }
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+      key[i] = i < nb ? I.births[sp].pkey[i] : ~0ULL;
+      idx[i] = (unsigned int)i;
+    }
+    __syncthreads();
+    bitonic(key, idx, P);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) I.births[sp].id[idx[i]] = base + i;
+    __syncthreads();
+    base += nb;
+  }
+  if (threadIdx.x == 0) S->next_id = base;
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of the cell histogram of one species -> cursors; clears the
+// histogram; n_next = total (checked against the capacity).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_scan(Inst I, int sp0) {
+  Scalars* S = I.S;
+  if (S->status & ST_FATAL) return;
+  const int sp = sp0 + blockIdx.x;
+  int* counts = I.counts[sp];
+  int* cursor = I.cursor[sp];
+  __shared__ int wsum[32];
+  __shared__ long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int base = 0; base < I.nkey; base += blockDim.x * 4) {
+    const int i0 = base + threadIdx.x * 4;
+    int v[4];
+    for (int k = 0; k < 4; ++k) v[k] = i0 + k < I.nkey ? counts[i0 + k] : 0;
+    const int s = v[0] + v[1] + v[2] + v[3];
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      int x = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+      }
+      wsum[lane] = x;  // inclusive over warps
+    }
+    __syncthreads();
+    long long off = carry + (w > 0 ? wsum[w - 1] : 0) + (incl - s);
+    for (int k = 0; k < 4; ++k)
+      if (i0 + k < I.nkey) {
+        cursor[i0 + k] = (int)off;
+        counts[i0 + k] = 0;
+        off += v[k];
+      }
+    __syncthreads();
+    if (threadIdx.x == 0) carry += wsum[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    S->n_next[sp] = carry;
+    if (carry > I.cap[sp]) atomicOr(&S->status, ST_CAPACITY);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Counting-sort scatter cur -> nxt of the surviving particles and the
+// births (blockIdx.y = species).
+// ---------------------------------------------------------------------------
+__global__ void k_scatter(Inst I, int sp0) {
+  Scalars* S = I.S;
+  if (S->status & ST_FATAL) return;
+  const int sp = sp0 + blockIdx.y;
+  const long long n_old = S->n[sp];
+  const long long nb = S->nbirth[sp] < I.birth_cap ? S->nbirth[sp] : I.birth_cap;
+  const long long total = n_old + nb;
+  const ParticlesDev src = I.cur[sp], dst = I.nxt[sp];
+  const BirthsDev B = I.births[sp];
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = warp * 32; base < total; base += nwarp * 32) {
+    const long long i = base + lane;
+    int key = -1;
+    if (i < n_old) key = I.key[sp][i];
+    else if (i < total) key = B.cell[i - n_old];
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(peers) - 1;
+    int pos0 = 0;
+    if (lane == leader && key >= 0) pos0 = atomicAdd(&I.cursor[sp][key], __popc(peers));
+    pos0 = __shfl_sync(0xffffffffu, pos0, leader);
+    if (key >= 0) {
+      const int pos = pos0 + __popc(peers & ((1u << lane) - 1u));
+      if (i < n_old) {
+        dst.r[pos] = src.r[i]; dst.z[pos] = src.z[i];
+        dst.vr[pos] = src.vr[i]; dst.vt[pos] = src.vt[i]; dst.vz[pos] = src.vz[i];
+        dst.id[pos] = src.id[i];
+      } else {
+        const long long b = i - n_old;
+        dst.r[pos] = B.r[b]; dst.z[pos] = B.z[b];
+        dst.vr[pos] = B.vr[b]; dst.vt[pos] = B.vt[b]; dst.vz[pos] = B.vz[b];
+        dst.id[pos] = B.id[b];
+      }
+    }
+  }
+}
+
+// keys + histogram of particles loaded by pic_set_particles; range check
+__global__ void k_keys(Inst I, int sp) {
+  Scalars* S = I.S;
+  const long long n = S->n[sp];
+  const ParticlesDev P = I.cur[sp];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double r = P.r[i], z = P.z[i];
+    int key = -1;
+    if (r >= 0.0 && r < I.R && z >= 0.0 && z < I.L && isfinite(P.vr[i]) && isfinite(P.vt[i]) &&
+        isfinite(P.vz[i]) && P.id[i] >= 0) {
+      int m, nn;
+      double f;
+      locate(r, I.inv_dr, I.nr, m, f);
+      locate(z, I.inv_dz, I.nz, nn, f);
+      key = cell_key(I, m, nn);
+      atomicAdd(&I.counts[sp][key], 1);
+      atomicMax(&S->next_id, P.id[i] + 1);
+    } else {
+      atomicOr(&S->status, ST_NAN);
+    }
+    I.key[sp][i] = key;
+  }
+}
+
+// n = n_next after a set-up sort (no births)
+__global__ void k_commit_n(Inst I, int sp) {
+  if (threadIdx.x == 0 && !(I.S->status & ST_FATAL)) I.S->n[sp] = I.S->n_next[sp];
+}
+
+__global__ void k_set_n(Inst I, int sp, long long n) {
+  if (threadIdx.x == 0) {
+    I.S->n[sp] = n;
+    I.S->nbirth[sp] = 0;
+  }
+}
+
+// deposit every particle of the current arrays (global atomics; set-up only)
+__global__ void k_deposit_all(Inst I, int sp) {
+  const long long n = I.S->n[sp];
+  const ParticlesDev P = I.cur[sp];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    int m, nn;
+    double fr, fz;
+    locate(P.r[i], I.inv_dr, I.nr, m, fr);
+    locate(P.z[i], I.inv_dz, I.nz, nn, fz);
+    const FixW f = fix_weights(rweight_upper(I, P.r[i], m, fr), fz);
+    unsigned long long* q = I.qacc[sp];
+    atomicAdd(q + node_index(I, m, nn), f.w00);
+    atomicAdd(q + node_index(I, m + 1, nn), f.w10);
+    atomicAdd(q + node_index(I, m, nn + 1), f.w01);
+    atomicAdd(q + node_index(I, m + 1, nn + 1), f.w11);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Node charge Q = e w (sum_i - sum_e) 2^-44; peak densities on diagnostic steps
+// ---------------------------------------------------------------------------
+__global__ void k_charge(Inst I) {
+  Scalars* S = I.S;
+  const int nn = (I.nr + 1) * (I.nz + 1);
+  const bool diag = S->diag_on != 0;
+  const double scale = kQe * I.weight * kFixInv;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += gridDim.x * blockDim.x) {
+    const unsigned long long ue = I.qacc[0][k], ui = I.qacc[1][k];
+    I.qacc[0][k] = 0ULL;
+    I.qacc[1][k] = 0ULL;
+    I.Q[k] = (double)(long long)(ui - ue) * scale;
+    if (diag) {
+      const int m = k / (I.nz + 1), n = k - m * (I.nz + 1);
+      const double sv = I.weight * kFixInv / node_volume(I, m, n);
+      const double de = (double)ue * sv, di = (double)ui * sv;
+      atomicMax(&S->peak_bits[0], (unsigned long long)__double_as_longlong(de));
+      atomicMax(&S->peak_bits[1], (unsigned long long)__double_as_longlong(di));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// External circuit (Sections 3, 4, 6): cathode charge of the step, running
+// mean current over n_avg steps, V_c = -V_s + I R_ext clamped to [-V_s, 0];
+// writes the cathode nodes' Dirichlet value into phi.
+// ---------------------------------------------------------------------------
+__global__ void k_circuit(Inst I) {
+  Scalars* S = I.S;
+  if (S->status & ST_FATAL) return;
+  if (threadIdx.x == 0) {
+    const long long cnt_q = (long long)S->cnt_ion_cath + (long long)S->cnt_sey - (long long)S->cnt_e_cath;
+    const double qc = kQe * I.weight * (double)cnt_q;
+    const int na = I.n_avg > 0 ? I.n_avg : 1;
+    const long long st = S->step;
+    I.qhist[st % na] = qc;
+    const long long cnt = st + 1 < na ? st + 1 : na;
+    double qs = 0.0;
+    for (long long k = 0; k < cnt; ++k) qs += I.qhist[k];
+    const double cur = qs / ((double)cnt * I.dt);
+    double V = I.Vc_fixed;
+    if (I.circuit_mode == 1) {
+      V = -I.Vs + cur * I.Rext;
+      if (V < -I.Vs) V = -I.Vs;
+      if (V > 0.0) V = 0.0;
+    }
+    S->I = cur;
+    S->Vc = V;
+  }
+  __syncthreads();
+  const double V = S->Vc;
+  for (int m = threadIdx.x; m <= I.m_cath; m += blockDim.x) I.phi[m * (I.nz + 1)] = V;
+}
+
+__global__ void k_set_cathode(Inst I) {
+  const double V = I.S->Vc;
+  for (int m = threadIdx.x; m <= I.m_cath; m += blockDim.x) I.phi[m * (I.nz + 1)] = V;
+}
+
+// diagnostics record, counters for the next step, step index
+__global__ void k_step_end(Inst I) {
+  Scalars* S = I.S;
+  if (threadIdx.x != 0) return;
+  const long long nb0 = S->nbirth[0] < I.birth_cap ? S->nbirth[0] : I.birth_cap;
+  const long long nb1 = S->nbirth[1] < I.birth_cap ? S->nbirth[1] : I.birth_cap;
+  const bool ok = !(S->status & ST_FATAL);
+  if (S->diag_on) {
+    DiagDev* d = I.diag;
+    d->t = S->step * I.dt;
+    d->I_cath = S->I;
+    d->V_cath = S->Vc;
+    d->n_e_peak = __longlong_as_double((long long)S->peak_bits[0]);
+    d->n_i_peak = __longlong_as_double((long long)S->peak_bits[1]);
+    d->W_field = S->W;
+    d->K_e = S->K[0];
+    d->K_i = S->K[1];
+    d->N_e = ok ? S->n_next[0] : S->n[0];
+    d->N_i = ok ? S->n_next[1] : S->n[1];
+    d->n_ion_cath = (long long)S->cnt_ion_cath;
+    d->n_e_cath = (long long)S->cnt_e_cath;
+    d->n_sey = (long long)S->cnt_sey;
+    d->n_ionize = (long long)S->cnt_ionize;
+    d->n_excite = (long long)S->cnt_excite;
+    d->n_elastic = (long long)S->cnt_elastic;
+    d->step = S->step;
+    d->particle_steps = S->pushed + (ok ? S->n[0] + S->n[1] : 0);
+    d->poisson_iters = S->poisson_iters;
+    d->poisson_resid = S->poisson_resid;
+    d->status = S->status;
+  }
+  (void)nb0;
+  (void)nb1;
+  if (ok) {
+    S->pushed += S->n[0] + S->n[1];
+    S->n[0] = S->n_next[0];
+    S->n[1] = S->n_next[1];
+    S->step = S->step + 1;
+  }
+  S->nbirth[0] = S->nbirth[1] = 0;
+  S->cnt_ion_cath = S->cnt_e_cath = S->cnt_sey = 0ULL;
+  S->cnt_ionize = S->cnt_excite = S->cnt_elastic = 0ULL;
+  S->K[0] = S->K[1] = 0.0;
+  S->W = 0.0;
+  S->peak_bits[0] = S->peak_bits[1] = 0ULL;
+  S->diag_on = (S->step % (I.diag_every > 0 ? I.diag_every : 1)) == 0;
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static int grid_for(long long work, int threads, int num_sms, int per_sm) {
+  long long g = (work + threads - 1) / threads;
+  long long cap = (long long)num_sms * per_sm;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+cudaError_t launch_charge(const Inst& I, cudaStream_t st) {
+  const int nn = (I.nr + 1) * (I.nz + 1);
+  k_charge<<<grid_for(nn, 256, 1024, 1), 256, 0, st>>>(I);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_n(const Inst& I, int sp, long long n, cudaStream_t st) {
+  k_set_n<<<1, 32, 0, st>>>(I, sp, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort_species(const Inst& I, int sp, int num_sms, cudaStream_t st) {
+  // n is already in S->n[sp]; births are none
+  long long cap = I.cap[sp];
+  k_keys<<<grid_for(cap, 256, num_sms, 8), 256, 0, st>>>(I, sp);
+  k_scan<<<1, 1024, 0, st>>>(I, sp);
+  k_scatter<<<dim3(grid_for(cap, 256, num_sms, 8), 1), 256, 0, st>>>(I, sp);
+  k_commit_n<<<1, 32, 0, st>>>(I, sp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_fields(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_t st) {
+  for (int sp = 0; sp < 2; ++sp)
+    k_deposit_all<<<grid_for(I.cap[sp], 256, num_sms, 8), 256, 0, st>>>(I, sp);
+  cudaError_t e = launch_charge(I, st);
+  if (e != cudaSuccess) return e;
+  k_set_cathode<<<1, 256, 0, st>>>(I);
+  return launch_poisson(pw, I.Q, I.phi, I.poisson_tol, I.poisson_max_iter, &I.S->status,
+                        &I.S->poisson_iters, &I.S->poisson_resid, st);
+}
+
+cudaError_t launch_step(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_t st,
+                        const StepMarks* marks) {
+  auto mk = [&](int g, bool b) {
+    if (marks) marks->mark(marks->ctx, g, b, st);
+  };
+  const int ncell = I.nr * I.nz;
+  mk(G_FIELD, true);
+  k_field_tables<<<grid_for(ncell, 256, num_sms, 8), 256, 0, st>>>(I);
+  mk(G_FIELD, false);
+  const int pg = num_sms * 4;
+  mk(G_PUSH_E, true);
+  if (I.gather == 0) k_push<0, 0><<<pg, kPushThreads, 0, st>>>(I);
+  else k_push<0, 1><<<pg, kPushThreads, 0, st>>>(I);
+  mk(G_PUSH_E, false);
+  mk(G_PUSH_I, true);
+  if (I.gather == 0) k_push<1, 0><<<pg, kPushThreads, 0, st>>>(I);
+  else k_push<1, 1><<<pg, kPushThreads, 0, st>>>(I);
+  mk(G_PUSH_I, false);
+  mk(G_BIRTHS, true);
+  k_births<<<1, 1024, 0, st>>>(I);
+  mk(G_BIRTHS, false);
+  mk(G_SCAN, true);
+  k_scan<<<2, 1024, 0, st>>>(I, 0);
+  mk(G_SCAN, false);
+  mk(G_SCATTER, true);
+  k_scatter<<<dim3(num_sms * 8, 2), 256, 0, st>>>(I, 0);
+  mk(G_SCATTER, false);
+  mk(G_CHARGE, true);
+  cudaError_t e = launch_charge(I, st);
+  mk(G_CHARGE, false);
+  if (e != cudaSuccess) return e;
+  mk(G_CIRCUIT, true);
+  k_circuit<<<1, 256, 0, st>>>(I);
+  mk(G_CIRCUIT, false);
+  mk(G_POISSON, true);
+  e = launch_poisson(pw, I.Q, I.phi, I.poisson_tol, I.poisson_max_iter, &I.S->status,
+                     &I.S->poisson_iters, &I.S->poisson_resid, st);
+  mk(G_POISSON, false);
+  if (e != cudaSuccess) return e;
+  mk(G_STEP_END, true);
+  k_step_end<<<1, 32, 0, st>>>(I);
+  mk(G_STEP_END, false);
+  return cudaGetLastError();
+}
+
+}  // namespace pic

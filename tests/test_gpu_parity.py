@@ -1,0 +1,229 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle on
+identical seeded states, one step and several steps, element by element.
+
+Bar (FP64 mode): positions and velocities per species within
+||a - b||_inf / ||b||_inf <= 1e-12 with identical id sets; phi within 1e-10
+of the oracle's; integer outputs (particle counts, cathode impacts,
+secondary electrons, collision counts) equal.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import pic_inputs
+from parity import (FIELD_TOL, PARTICLE_TOL, busy_state, compare_species, field_err,
+                    sort_by_id)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2507_10727_gb300 as pg
+    import torch
+    assert torch.cuda.is_available()
+    return pg
+
+
+def _pair(pg, p, parts, set_phi=True):
+    p = pic_inputs.with_capacity(p, parts, factor=2.0)
+    orc = oracle.Oracle(p, parts)
+    h = pg.pic_create(p)
+    for k, sp in (("e", 0), ("i", 1)):
+        pg.pic_set_particles(h, 0, sp, parts[k])
+    if set_phi:
+        pg.pic_set_phi(h, 0, orc.fields()["phi"])
+    return p, orc, h
+
+
+def _check_step(pg, h, orc, check_phi=True):
+    de, do = pg.pic_diagnostics(h, 0), orc.diag()
+    for key in ("N_e", "N_i", "n_ion_cath", "n_e_cath", "n_sey", "n_ionize", "n_excite",
+                "n_elastic"):
+        assert de[key] == do[key], (key, de[key], do[key])
+    for sp in (0, 1):
+        err = compare_species(pg.pic_get_particles(h, 0, sp), orc.get_particles(sp))
+        assert err["pos"] <= PARTICLE_TOL and err["vel"] <= PARTICLE_TOL, (sp, err)
+    fg, fo = pg.pic_get_fields(h, 0), orc.fields()
+    assert field_err(fg["Q"], fo["Q"]) <= 1e-12
+    if check_phi:
+        assert field_err(fg["phi"], fo["phi"]) <= FIELD_TOL
+    for key in ("I_cath", "V_cath"):
+        assert de[key] == pytest.approx(do[key], rel=1e-12, abs=1e-12)
+    for key in ("K_e", "K_i", "W_field", "n_e_peak", "n_i_peak"):
+        assert de[key] == pytest.approx(do[key], rel=1e-10), key
+    return de
+
+
+@pytest.mark.parametrize("gather", [0, 1])
+@pytest.mark.parametrize("rweight", [0, 1])
+def test_one_step_busy_state(pg, gather, rweight):
+    p = pic_inputs.params_rz32(gather=gather)
+    p.update(rweight=rweight, gamma_i=0.5, gamma_e=0.3, poisson_tol=1e-13,
+             circuit_mode=1, Vs=400.0, Rext=100.0, n_avg=3)
+    p, parts = busy_state(p, ppc=16, seed=3 + gather + 2 * rweight)
+    p, orc, h = _pair(pg, p, parts)
+    orc.step(1)
+    pg.pic_step(h, 1)
+    d = _check_step(pg, h, orc)
+    # the state does exercise every branch
+    assert d["n_sey"] > 0 and d["n_ionize"] > 0 and d["n_excite"] > 0 and d["n_e_cath"] > 0
+    assert pg.pic_get_next_id(h, 0) == orc.next_id
+
+
+def test_ragged_grid_and_counts(pg):
+    # 20 x 36 cells: partial 8x8 tiles along both axes; particle counts not a
+    # multiple of the push chunk
+    p = pic_inputs.params_rz32(gather=0)
+    p.update(nr=20, nz=36, R=0.02, L=0.03, Rc=0.012, gamma_i=0.5, poisson_tol=1e-13)
+    p, parts = busy_state(p, ppc=7, seed=21)
+    p, orc, h = _pair(pg, p, parts)
+    for _ in range(3):
+        orc.step(1)
+        pg.pic_step(h, 1)
+        _check_step(pg, h, orc)
+
+
+@pytest.mark.parametrize("gather", [0, 1])
+def test_several_steps_seed_plasma(pg, gather):
+    p = pic_inputs.params_rz32(gather=gather)
+    p.update(poisson_tol=1e-13, circuit_mode=1, Vs=400.0, Rext=2000.0, n_avg=4, gamma_i=0.2)
+    p, parts = pic_inputs.seed_plasma(p, 32 * 32 * 8, seed=5, Te_eV=5.0)
+    p, orc, h = _pair(pg, p, parts)
+    for _ in range(6):
+        orc.step(1)
+        pg.pic_step(h, 1)
+        _check_step(pg, h, orc)
+
+
+def test_solve_fields_matches_oracle(pg):
+    p = pic_inputs.params_rz32()
+    p.update(poisson_tol=1e-13)
+    p, parts = busy_state(p, ppc=4, seed=8)
+    p, orc, h = _pair(pg, p, parts, set_phi=False)
+    pg.pic_solve_fields(h, 0)
+    pg.pic_sync(h)
+    fg, fo = pg.pic_get_fields(h, 0), orc.fields()
+    assert field_err(fg["Q"], fo["Q"]) <= 1e-12
+    assert field_err(fg["rho"], fo["rho"]) <= 1e-12
+    assert field_err(fg["phi"], fo["phi"]) <= FIELD_TOL
+
+
+@pytest.mark.parametrize("nr,nz", [(32, 32), (48, 20), (128, 128), (256, 256)])
+def test_poisson_standalone(pg, nr, nz):
+    import torch
+    p = pic_inputs.params_rz256()
+    p.update(nr=nr, nz=nz, R=0.05, L=0.05 * nz / nr)
+    rng = np.random.default_rng(nr + nz)
+    V = oracle.node_volume(p)
+    rho = rng.normal(size=(nr + 1, nz + 1)) * 1e-6
+    bc = np.zeros_like(rho)
+    dr = p["R"] / nr
+    mc = [m for m in range(nr) if m * dr <= 0.6 * p["R"]]
+    bc[mc, 0] = -321.0
+    bc[:, nz] = 5.0 * rng.random(nr + 1)
+    bc[nr, :] = 2.0
+    phi_o = oracle.poisson(p, rho, bc)
+    Q = torch.tensor(rho * V, device="cuda")
+    phi = torch.tensor(bc, device="cuda")
+    rc, it, res = pg.pic_poisson_solve(nr, nz, p["R"], p["L"], 1e-13, 500, Q, phi)
+    torch.cuda.synchronize()
+    assert rc == 0 and res <= 1e-13, (rc, it, res)
+    assert field_err(phi.cpu().numpy(), phi_o) <= FIELD_TOL
+    # Dirichlet nodes untouched
+    out = phi.cpu().numpy()
+    assert np.array_equal(out[:, 0], bc[:, 0]) and np.array_equal(out[nr, :], bc[nr, :])
+
+
+def test_determinism_and_checkpoint(pg, tmp_path):
+    p = pic_inputs.params_rz32()
+    p.update(circuit_mode=1, Vs=400.0, Rext=500.0, gamma_i=0.3)
+    p, parts = busy_state(p, ppc=8, seed=13)
+    p = pic_inputs.with_capacity(p, parts, factor=2.0)
+    runs = []
+    for _ in range(2):
+        h = pg.pic_create(p)
+        for k, sp in (("e", 0), ("i", 1)):
+            pg.pic_set_particles(h, 0, sp, parts[k])
+        pg.pic_solve_fields(h, 0)
+        pg.pic_step(h, 4)
+        pg.pic_save(h, 0, str(tmp_path / "ck.bin"))
+        pg.pic_step(h, 4)
+        runs.append((h, [sort_by_id(pg.pic_get_particles(h, 0, sp)) for sp in (0, 1)],
+                     pg.pic_get_fields(h, 0)["phi"], pg.pic_diagnostics(h, 0)))
+    (_, pa, fa, da), (_, pb, fb, db) = runs
+    for sp in (0, 1):
+        for k in pa[sp]:
+            assert np.array_equal(pa[sp][k], pb[sp][k]), (sp, k)
+    assert np.array_equal(fa, fb)
+    # resume from the checkpoint in a fresh handle: identical continuation
+    h2 = pg.pic_create(p)
+    pg.pic_load(h2, 0, str(tmp_path / "ck.bin"))
+    pg.pic_step(h2, 4)
+    for sp in (0, 1):
+        pc = sort_by_id(pg.pic_get_particles(h2, 0, sp))
+        for k in pc:
+            assert np.array_equal(pc[k], pa[sp][k]), (sp, k)
+    assert np.array_equal(pg.pic_get_fields(h2, 0)["phi"], fa)
+    dc = pg.pic_diagnostics(h2, 0)
+    assert dc["step"] == da["step"] and dc["V_cath"] == da["V_cath"]
+
+
+def test_edge_cases(pg):
+    p = pic_inputs.params_rz32()
+    p.update(cap_e=4096, cap_i=4096, birth_cap=1024)
+    empty = {k: np.zeros(0) for k in ("r", "z", "vr", "vt", "vz")} | {"id": np.zeros(0, np.int64)}
+    # empty plasma: steps run, fields are the vacuum solution
+    h = pg.pic_create(p)
+    pg.pic_solve_fields(h, 0)
+    pg.pic_step(h, 3)
+    d = pg.pic_diagnostics(h, 0)
+    assert d["N_e"] == 0 and d["N_i"] == 0 and d["status"] == 0
+    orc = oracle.Oracle(p, {"e": empty, "i": empty})
+    orc.step(3)
+    assert field_err(pg.pic_get_fields(h, 0)["phi"], orc.fields()["phi"]) <= FIELD_TOL
+    # every particle leaves in one step
+    n = 1000
+    gone = {"r": np.full(n, 0.01), "z": np.full(n, p["L"] * 0.999), "vr": np.zeros(n),
+            "vt": np.zeros(n), "vz": np.full(n, 1e7), "id": np.arange(n)}
+    h = pg.pic_create(p)
+    pg.pic_set_particles(h, 0, 0, gone)
+    pg.pic_step(h, 1)
+    assert pg.pic_count(h, 0, 0) == 0
+    # out-of-domain input is rejected
+    bad = dict(gone, r=np.full(n, 2 * p["R"]))
+    h = pg.pic_create(p)
+    with pytest.raises(pg.PicError) as ei:
+        pg.pic_set_particles(h, 0, 0, bad)
+    assert ei.value.code == -5
+    # more particles than the capacity
+    h = pg.pic_create(p)
+    big = {k: np.resize(v, 5000) for k, v in gone.items()}
+    big["id"] = np.arange(5000)
+    with pytest.raises(pg.PicError) as ei:
+        pg.pic_set_particles(h, 0, 0, big)
+    assert ei.value.code == -3
+
+
+def test_capacity_and_nonconvergence_latch(pg):
+    p = pic_inputs.params_rz32()
+    p, parts = busy_state(p, ppc=4, seed=2)
+    p = pic_inputs.with_capacity(p, parts, factor=1.0)
+    p["birth_cap"] = 1          # more than one birth in the first step
+    h = pg.pic_create(p)
+    for k, sp in (("e", 0), ("i", 1)):
+        pg.pic_set_particles(h, 0, sp, parts[k])
+    pg.pic_step(h, 2)
+    with pytest.raises(pg.PicError) as ei:
+        pg.pic_sync(h)
+    assert ei.value.code == -3
+    q = dict(p, birth_cap=100000, poisson_max_iter=1, poisson_tol=1e-15)
+    h = pg.pic_create(q)
+    for k, sp in (("e", 0), ("i", 1)):
+        pg.pic_set_particles(h, 0, sp, parts[k])
+    pg.pic_solve_fields(h, 0)
+    with pytest.raises(pg.PicError) as ei:
+        pg.pic_sync(h)
+    assert ei.value.code == -4
