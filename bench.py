@@ -73,6 +73,7 @@ def workload(args):
     n = int(args.n_per_species)
     p, parts = pic_inputs.grown_ring_state(p, n, seed=args.seed)
     p = pic_inputs.with_capacity(p, parts, factor=1.25, births=1 << 20)
+    p["diag_every"] = 10      # diagnostics reduction every 10 steps
     return p, parts
 
 
@@ -81,7 +82,7 @@ def config_block(p, n, args):
             "grid": [p["nr"], p["nz"]], "domain_m": [p["R"], p["L"]],
             "n_per_species": n, "gather": args.gather.upper() + "-PIC",
             "precision": "fp64", "circuit": {"Vs": p["Vs"], "Rext": p["Rext"]},
-            "dt": p["dt"], "poisson_tol": p["poisson_tol"],
+            "dt": p["dt"], "poisson_tol": p["poisson_tol"], "diag_every": p["diag_every"],
             "l2": "inputs larger than L2 (particle state 3.8 GB >> 129 MB)"}
 
 
@@ -270,7 +271,7 @@ def main():
     d2 = pg.pic_diagnostics(h, 0)
     prof_steps = max(1, prof["push_e"]["launches"])
     prof_ps = d2["particle_steps"] - d1["particle_steps"]
-    ne, ni = d2["N_e"], d2["N_i"]
+    ne, ni = pg.pic_count(h, 0, 0), pg.pic_count(h, 0, 1)
 
     peaks, peak_kind = measured_peaks()
     clocks = clk.summary()

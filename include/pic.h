@@ -118,7 +118,7 @@ typedef struct pic_diag {
   int64_t n_ion_cath, n_e_cath, n_sey; /* cathode impacts and secondary electrons this step */
   int64_t n_ionize, n_excite, n_elastic; /* collisions this step */
   int64_t step;         /* index of the step the record belongs to */
-  int64_t particle_steps; /* cumulative sum over steps of (electrons + ions) pushed */
+  int64_t particle_steps; /* particles pushed, summed over all steps so far (updated every step) */
   int32_t poisson_iters;
   int32_t status;       /* latched device status (pic_status) */
   double poisson_resid; /* final relative residual */

@@ -45,3 +45,4 @@ cudaError_t launch_poisson(PoissonWork* pw, const double* Q, double* phi, double
                            int* status_dev, int* iters_dev, double* resid_dev, cudaStream_t st);
 
 }  // namespace pic
+

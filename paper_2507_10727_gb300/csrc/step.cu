@@ -641,6 +641,7 @@ __global__ void k_charge(Inst I) {
   const int nn = (I.nr + 1) * (I.nz + 1);
   const bool diag = S->diag_on != 0;
   const double scale = kQe * I.weight * kFixInv;
+  double pe = 0.0, pi = 0.0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += gridDim.x * blockDim.x) {
     const unsigned long long ue = I.qacc[0][k], ui = I.qacc[1][k];
     I.qacc[0][k] = 0ULL;
@@ -649,9 +650,33 @@ __global__ void k_charge(Inst I) {
     if (diag) {
       const int m = k / (I.nz + 1), n = k - m * (I.nz + 1);
       const double sv = I.weight * kFixInv / node_volume(I, m, n);
-      const double de = (double)ue * sv, di = (double)ui * sv;
-      atomicMax(&S->peak_bits[0], (unsigned long long)__double_as_longlong(de));
-      atomicMax(&S->peak_bits[1], (unsigned long long)__double_as_longlong(di));
+      pe = fmax(pe, (double)ue * sv);
+      pi = fmax(pi, (double)ui * sv);
+    }
+  }
+  if (diag) {
+    // block maximum, then one atomic per block (positive doubles order like
+    // their bit patterns)
+    __shared__ double red[2][32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      pe = fmax(pe, __shfl_xor_sync(0xffffffffu, pe, o));
+      pi = fmax(pi, __shfl_xor_sync(0xffffffffu, pi, o));
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+      red[0][w] = pe;
+      red[1][w] = pi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0;
+      for (int j = 0; j < (int)(blockDim.x >> 5); ++j) {
+        a = fmax(a, red[0][j]);
+        b = fmax(b, red[1][j]);
+      }
+      if (a > 0.0) atomicMax(&S->peak_bits[0], (unsigned long long)__double_as_longlong(a));
+      if (b > 0.0) atomicMax(&S->peak_bits[1], (unsigned long long)__double_as_longlong(b));
     }
   }
 }
@@ -719,13 +744,13 @@ __global__ void k_step_end(Inst I) {
     d->n_excite = (long long)S->cnt_excite;
     d->n_elastic = (long long)S->cnt_elastic;
     d->step = S->step;
-    d->particle_steps = S->pushed + (ok ? S->n[0] + S->n[1] : 0);
     d->poisson_iters = S->poisson_iters;
     d->poisson_resid = S->poisson_resid;
     d->status = S->status;
   }
   (void)nb0;
   (void)nb1;
+  I.diag->particle_steps = S->pushed + (ok ? S->n[0] + S->n[1] : 0);  // every step
   if (ok) {
     S->pushed += S->n[0] + S->n[1];
     S->n[0] = S->n_next[0];
