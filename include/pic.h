@@ -226,6 +226,31 @@ int pic_poisson_solve(int nr, int nz, double R, double L, double tol, int max_it
                       const double* Q_dev, double* phi_dev, void* work_dev, void* cuda_stream,
                       int* iters, double* resid);
 
+/* Size in bytes of the device array that pic_poisson_solve_static uses as
+ * its scratch; it holds the workspace of grids up to 256 x 512 cells. */
+#define PIC_POISSON_STATIC_BYTES (6u * 1024u * 1024u)
+
+/* pic_poisson_solve for callers that cannot allocate device memory while
+ * they run -- e.g. an application whose memory pool already owns the GPU, or a
+ * loop that cannot afford the device-wide synchronisation of cudaMalloc.
+ * The paper has no counterpart: this is an allocation policy of this library.
+ * Same arguments and results as pic_poisson_solve, minus work_dev: the
+ * scratch is a file-scope device array of PIC_POISSON_STATIC_BYTES that every
+ * GPU which loads the library holds until the process exits.  Nothing is
+ * allocated: no cudaMalloc/cudaFree, no allocator of any framework.
+ *   - Grids whose pic_poisson_workspace_bytes(nr, nz) exceeds
+ *     PIC_POISSON_STATIC_BYTES - 256 are rejected with PIC_ERR_CAPACITY.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, once per device, with that device current);
+ *     make that first call before any stream capture.
+ *   - All calls on a device share the one array, which keeps the previous
+ *     call's contents (each call clears what must start at zero).  Calls that
+ *     overlap on the GPU race on it: serialise them (one stream, one thread).
+ * Synchronous. */
+int pic_poisson_solve_static(int nr, int nz, double R, double L, double tol, int max_iter,
+                             const double* Q_dev, double* phi_dev, void* cuda_stream, int* iters,
+                             double* resid);
+
 #ifdef __cplusplus
 }
 #endif

@@ -46,3 +46,11 @@ cudaError_t launch_poisson(PoissonWork* pw, const double* Q, double* phi, double
 
 }  // namespace pic
 
+namespace pic {
+// Poisson solve over a caller-provided workspace of poisson_work_bytes(nr, nz)
+// bytes at `base` (already cleared); allocates nothing.
+cudaError_t launch_poisson_in_place(void* base, int nr, int nz, double R, double L, int num_sms,
+                                    const double* Q, double* phi, double tol, int max_iter,
+                                    int* status_dev, int* iters_dev, double* resid_dev,
+                                    cudaStream_t st);
+}  // namespace pic

@@ -543,3 +543,74 @@ cudaError_t launch_poisson(PoissonWork* pw, const double* Q, double* phi, double
 }
 
 }  // namespace pic
+
+// ----------------------------------------------------------------------------
+// Variant for pic_poisson_solve_static: the workspace layout is built in a
+// struct on the host stack (no host or device allocation), over the caller's
+// scratch at `base`.  The layout is the one poisson_work_bytes() sizes.
+// ----------------------------------------------------------------------------
+namespace pic {
+
+cudaError_t launch_poisson_in_place(void* base, int nr, int nz, double R, double L, int num_sms,
+                                    const double* Q, double* phi, double tol, int max_iter,
+                                    int* status_dev, int* iters_dev, double* resid_dev,
+                                    cudaStream_t st) {
+  PoissonArgs a;
+  std::memset(&a, 0, sizeof(a));
+  PoissonWork& w = a.W;
+  w.nr = nr;
+  w.nz = nz;
+  w.dr = R / nr;
+  w.dz = L / nz;
+  char* p = (char*)base;
+  auto take = [&](size_t b) {
+    char* q = p;
+    p += (b + 255) & ~(size_t)255;
+    return (void*)q;
+  };
+  const size_t nn = (size_t)(nr + 1) * (nz + 1);
+  w.r = (double*)take(nn * sizeof(double));
+  w.p = (double*)take(nn * sizeof(double));
+  w.q = (double*)take(nn * sizeof(double));
+  w.z = (double*)take(nn * sizeof(double));
+  int lr = nr, lz = nz, l = 0;
+  w.tail = -1;
+  for (; l < kMaxLev; ++l) {
+    const size_t ln = (size_t)(lr + 1) * (lz + 1);
+    w.lnr[l] = lr;
+    w.lnz[l] = lz;
+    w.u[l] = (float*)take(ln * sizeof(float));
+    w.f[l] = (float*)take(ln * sizeof(float));
+    if (w.tail < 0 && ln <= (size_t)kTailNodes) w.tail = l;
+    if (!(lr % 2 == 0 && lz % 2 == 0 && lr >= 4 && lz >= 4)) break;
+    lr /= 2;
+    lz /= 2;
+  }
+  w.nlev = l + 1;
+  if (w.tail < 0) w.tail = w.nlev - 1;
+  w.partial = (double*)take(8 * 2048 * sizeof(double));
+  w.bar = (unsigned int*)take(256);
+  if ((size_t)(p - (char*)base) != poisson_work_bytes(nr, nz)) return cudaErrorInvalidValue;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_poisson, kPoisThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  long long want = ((long long)nr * (nz - 1) + kPoisThreads - 1) / kPoisThreads;
+  long long cap = (long long)num_sms * per_sm;
+  if (cap > 2048) cap = 2048;
+  if (want > cap) want = cap;
+  if (want < 1) want = 1;
+  w.nblocks = (int)want;
+  a.Q = Q;
+  a.phi = phi;
+  a.tol = tol;
+  a.max_iter = max_iter;
+  a.status = status_dev;
+  a.iters = iters_dev;
+  a.resid = resid_dev;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel((const void*)k_poisson, dim3(w.nblocks), dim3(kPoisThreads),
+                                     args, 0, st);
+}
+
+}  // namespace pic
