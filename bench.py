@@ -61,9 +61,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample", type=float, default=2e6,
+    ap.add_argument("--cpu-sample", type=float, default=8e6,
                     help="oracle sample size per species for the CPU baseline")
-    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--cpu-steps", type=int, default=8)
     return ap.parse_args()
 
 
