@@ -113,7 +113,7 @@ std::string validate(const pic_config& c) {
   if (c.cap_e <= 0 || c.cap_i <= 0 || c.birth_cap <= 0) return "capacities must be positive";
   if (c.cap_e >= (1LL << 31) || c.cap_i >= (1LL << 31) || c.birth_cap >= (1LL << 30))
     return "capacities must stay below 2^31 (2^30 births)";
-  if (c.precision != 0) return "this build runs the FP64 particle path only (precision = 0)";
+  if (c.precision != 0 && c.precision != 1) return "precision must be 0 (FP64) or 1 (FP32 particles)";
   if (c.sort_every != 1) return "sort_every must be 1";
   if (c.gather < 0 || c.gather > 1 || c.rweight < 0 || c.rweight > 1) return "gather/rweight";
   if (c.circuit_mode < 0 || c.circuit_mode > 1 || c.b_mode < 0 || c.b_mode > 1) return "modes";
@@ -160,6 +160,7 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
   I.exc_E = c.exc_E;
   I.nu_max = nu_max_of(c);
   I.p_null = -std::expm1(-I.nu_max * c.dt);
+  I.pnull_k = (unsigned long long)std::ceil(std::ldexp(I.p_null, 53));
   I.seed = c.seed;
   I.gather = c.gather;
   I.rweight = c.rweight;
@@ -183,40 +184,67 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
   auto A = [&](size_t b) { return dev_alloc(h, b); };
   bool ok = true;
   auto chk = [&](void* p) { ok = ok && p != nullptr; return p; };
+  const bool p32 = c.precision == 1;
+  I.prec32 = p32 ? 1 : 0;
+  I.hq32[0] = (float)(0.5 * I.qm[0] * c.dt);
+  I.hq32[1] = (float)(0.5 * I.qm[1] * c.dt);
+  I.kr32 = (float)(c.dt * I.inv_dr);
+  I.kz32 = (float)(c.dt * I.inv_dz);
   for (int sp = 0; sp < 2; ++sp) {
     const size_t cap = (size_t)I.cap[sp];
-    for (ParticlesDev* P : {&I.cur[sp], &I.nxt[sp]}) {
-      P->r = (double*)chk(A(cap * 8));
-      P->z = (double*)chk(A(cap * 8));
-      P->vr = (double*)chk(A(cap * 8));
-      P->vt = (double*)chk(A(cap * 8));
-      P->vz = (double*)chk(A(cap * 8));
-      P->id = (long long*)chk(A(cap * 8));
+    if (p32) {
+      for (Particles32* P : {&I.cur32[sp], &I.nxt32[sp]}) {
+        P->a = (float4*)chk(A(cap * 16));
+        P->b = (uint4*)chk(A(cap * 16));
+      }
+      I.qacc64[sp] = (double*)chk(A(nn * 8));
+    } else {
+      for (ParticlesDev* P : {&I.cur[sp], &I.nxt[sp]}) {
+        P->r = (double*)chk(A(cap * 8));
+        P->z = (double*)chk(A(cap * 8));
+        P->vr = (double*)chk(A(cap * 8));
+        P->vt = (double*)chk(A(cap * 8));
+        P->vz = (double*)chk(A(cap * 8));
+        P->id = (long long*)chk(A(cap * 8));
+      }
+      I.key[sp] = (int*)chk(A(cap * 4));
+      I.qacc[sp] = (unsigned long long*)chk(A(nn * 8));
     }
-    I.key[sp] = (int*)chk(A(cap * 4));
     I.counts[sp] = (int*)chk(A((size_t)I.nkey * 4));
     I.cursor[sp] = (int*)chk(A((size_t)I.nkey * 4));
     BirthsDev& B = I.births[sp];
     const size_t bc = (size_t)c.birth_cap;
-    B.r = (double*)chk(A(bc * 8));
-    B.z = (double*)chk(A(bc * 8));
-    B.vr = (double*)chk(A(bc * 8));
-    B.vt = (double*)chk(A(bc * 8));
-    B.vz = (double*)chk(A(bc * 8));
+    if (p32) {
+      B.a32 = (float4*)chk(A(bc * 16));
+      B.b32 = (uint4*)chk(A(bc * 16));
+    } else {
+      B.r = (double*)chk(A(bc * 8));
+      B.z = (double*)chk(A(bc * 8));
+      B.vr = (double*)chk(A(bc * 8));
+      B.vt = (double*)chk(A(bc * 8));
+      B.vz = (double*)chk(A(bc * 8));
+      B.cell = (int*)chk(A(bc * 4));
+      B.id = (long long*)chk(A(bc * 8));
+    }
     B.pkey = (unsigned long long*)chk(A(bc * 8));
-    B.cell = (int*)chk(A(bc * 4));
-    B.id = (long long*)chk(A(bc * 8));
     long long P2 = 1;
     while (P2 < (long long)bc) P2 <<= 1;
     B.sort_len = P2;
     B.skey = (unsigned long long*)chk(A((size_t)P2 * 8));
     B.sidx = (unsigned int*)chk(A((size_t)P2 * 4));
-    I.qacc[sp] = (unsigned long long*)chk(A(nn * 8));
   }
   I.phi = (double*)chk(A(nn * 8));
   I.Q = (double*)chk(A(nn * 8));
-  I.etab = (double4_32a*)chk(A((size_t)I.nkey * (c.gather == 0 ? 1 : 2) * sizeof(double4_32a)));
-  I.btab = (double4_32a*)chk(A((size_t)I.nkey * 2 * sizeof(double4_32a)));
+  if (p32) {
+    I.etab32 = (float4*)chk(A((size_t)I.nkey * (c.gather == 0 ? 1 : 2) * sizeof(float4)));
+    I.btab32 = (float4*)chk(A((size_t)I.nkey * 2 * sizeof(float4)));
+    long long cmax = I.cap[0] > I.cap[1] ? I.cap[0] : I.cap[1];
+    I.stage_len = cmax < (1LL << 22) ? cmax : (1LL << 22);
+    I.stage = (double*)chk(A((size_t)I.stage_len * 6 * 8));
+  } else {
+    I.etab = (double4_32a*)chk(A((size_t)I.nkey * (c.gather == 0 ? 1 : 2) * sizeof(double4_32a)));
+    I.btab = (double4_32a*)chk(A((size_t)I.nkey * 2 * sizeof(double4_32a)));
+  }
   I.qhist = (double*)chk(A((size_t)c.n_avg * 8));
   I.S = (Scalars*)chk(A(sizeof(Scalars)));
   I.diag = (DiagDev*)chk(A(sizeof(DiagDev)));
@@ -227,7 +255,7 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
   cudaError_t e = cudaSuccess;
   for (int sp = 0; sp < 2 && e == cudaSuccess; ++sp) {
     e = cudaMemsetAsync(I.counts[sp], 0, (size_t)I.nkey * 4, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(I.qacc[sp], 0, nn * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p32 ? (void*)I.qacc64[sp] : (void*)I.qacc[sp], 0, nn * 8, st);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(I.phi, 0, nn * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(I.Q, 0, nn * 8, st);
@@ -265,7 +293,15 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
         bt[(size_t)2 * key + comp] = make_d4(b00, b10 - b00, b01 - b00, b11 - b10 - b01 + b00);
       }
     }
-  e = cudaMemcpyAsync(I.btab, bt.data(), bt.size() * sizeof(double4_32a), cudaMemcpyHostToDevice, st);
+  std::vector<float4> bt32;
+  if (p32) {
+    bt32.resize(bt.size());
+    for (size_t k = 0; k < bt.size(); ++k)
+      bt32[k] = make_float4((float)bt[k].x, (float)bt[k].y, (float)bt[k].z, (float)bt[k].w);
+    e = cudaMemcpyAsync(I.btab32, bt32.data(), bt32.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
+  } else {
+    e = cudaMemcpyAsync(I.btab, bt.data(), bt.size() * sizeof(double4_32a), cudaMemcpyHostToDevice, st);
+  }
   if (e != cudaSuccess) return cuda_fail(h, e, "upload B table");
   Scalars s0;
   std::memset(&s0, 0, sizeof(s0));
@@ -312,6 +348,7 @@ void prof_mark(void* ctx, int group, bool begin, cudaStream_t st) {
 
 void swap_buffers(InstHost& ih, int sp) {
   std::swap(ih.I.cur[sp], ih.I.nxt[sp]);
+  std::swap(ih.I.cur32[sp], ih.I.nxt32[sp]);
 }
 
 }  // namespace
@@ -374,21 +411,47 @@ int pic_set_particles(pic_handle* h, int instance, int species, int64_t n, const
   if (n > ih.I.cap[species]) return fail(h, PIC_ERR_CAPACITY, "n exceeds the species capacity");
   if (n > 0 && (!r || !z || !vr || !vt || !vz || !id))
     return fail(h, PIC_ERR_INVALID, "null array");
-  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  const ParticlesDev& P = ih.I.cur[species];
   cudaStream_t st = h->stream;
   cudaError_t e = cudaSuccess;
-  const size_t b = (size_t)n * 8;
-  if (n > 0) {
-    e = cudaMemcpyAsync(P.r, r, b, kind, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(P.z, z, b, kind, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(P.vr, vr, b, kind, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(P.vt, vt, b, kind, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(P.vz, vz, b, kind, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(P.id, id, b, kind, st);
+  if (ih.I.prec32) {
+    e = launch_set_n(ih.I, species, n, st);
+    if (on_device) {
+      if (e == cudaSuccess && n > 0)
+        e = launch_pack32(ih.I, species, 0, n, r, z, vr, vt, vz, (const long long*)id, h->num_sms, st);
+    } else {
+      // host arrays: through the FP64 staging chunk
+      const long long L = ih.I.stage_len;
+      double* sg = ih.I.stage;
+      for (long long off = 0; off < n && e == cudaSuccess; off += L) {
+        const long long cnt = n - off < L ? n - off : L;
+        const size_t b = (size_t)cnt * 8;
+        const double* srcs[5] = {r + off, z + off, vr + off, vt + off, vz + off};
+        for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+          e = cudaMemcpyAsync(sg + (size_t)k * L, srcs[k], b, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(sg + (size_t)5 * L, id + off, b, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+          e = launch_pack32(ih.I, species, off, cnt, sg, sg + L, sg + 2 * L, sg + 3 * L, sg + 4 * L,
+                            (const long long*)(sg + 5 * L), h->num_sms, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // staging reused
+      }
+    }
+    if (e == cudaSuccess) e = launch_sort_species32(ih.I, species, h->num_sms, st);
+  } else {
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const ParticlesDev& P = ih.I.cur[species];
+    const size_t b = (size_t)n * 8;
+    if (n > 0) {
+      e = cudaMemcpyAsync(P.r, r, b, kind, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(P.z, z, b, kind, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(P.vr, vr, b, kind, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(P.vt, vt, b, kind, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(P.vz, vz, b, kind, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(P.id, id, b, kind, st);
+    }
+    if (e == cudaSuccess) e = launch_set_n(ih.I, species, n, st);
+    if (e == cudaSuccess) e = launch_sort_species(ih.I, species, h->num_sms, st);
   }
-  if (e == cudaSuccess) e = launch_set_n(ih.I, species, n, st);
-  if (e == cudaSuccess) e = launch_sort_species(ih.I, species, h->num_sms, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "set_particles");
   swap_buffers(ih, species);
   e = cudaStreamSynchronize(st);
@@ -410,18 +473,42 @@ int pic_get_particles(pic_handle* h, int instance, int species, double* r, doubl
   int64_t n = 0;
   int rc = pic_count(h, instance, species, &n);
   if (rc != PIC_OK && rc != PIC_ERR_NONCONVERGED) return rc;
-  const ParticlesDev& P = h->inst[instance].I.cur[species];
-  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  const size_t b = (size_t)n * 8;
+  const Inst& I = h->inst[instance].I;
   cudaStream_t st = h->stream;
   cudaError_t e = cudaSuccess;
-  if (n > 0) {
-    if (r) e = cudaMemcpyAsync(r, P.r, b, kind, st);
-    if (e == cudaSuccess && z) e = cudaMemcpyAsync(z, P.z, b, kind, st);
-    if (e == cudaSuccess && vr) e = cudaMemcpyAsync(vr, P.vr, b, kind, st);
-    if (e == cudaSuccess && vt) e = cudaMemcpyAsync(vt, P.vt, b, kind, st);
-    if (e == cudaSuccess && vz) e = cudaMemcpyAsync(vz, P.vz, b, kind, st);
-    if (e == cudaSuccess && id) e = cudaMemcpyAsync(id, P.id, b, kind, st);
+  if (I.prec32) {
+    if (on_device) {
+      if (n > 0)
+        e = launch_unpack32(I, species, 0, n, r, z, vr, vt, vz, (long long*)id, h->num_sms, st);
+    } else {
+      const long long L = I.stage_len;
+      double* sg = I.stage;
+      for (long long off = 0; off < n && e == cudaSuccess; off += L) {
+        const long long cnt = n - off < L ? n - off : L;
+        const size_t b = (size_t)cnt * 8;
+        e = launch_unpack32(I, species, off, cnt, sg, sg + L, sg + 2 * L, sg + 3 * L, sg + 4 * L,
+                            (long long*)(sg + 5 * L), h->num_sms, st);
+        double* dsts[5] = {r, z, vr, vt, vz};
+        for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+          if (dsts[k])
+            e = cudaMemcpyAsync(dsts[k] + off, sg + (size_t)k * L, b, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && id)
+          e = cudaMemcpyAsync(id + off, sg + (size_t)5 * L, b, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      }
+    }
+  } else {
+    const ParticlesDev& P = I.cur[species];
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const size_t b = (size_t)n * 8;
+    if (n > 0) {
+      if (r) e = cudaMemcpyAsync(r, P.r, b, kind, st);
+      if (e == cudaSuccess && z) e = cudaMemcpyAsync(z, P.z, b, kind, st);
+      if (e == cudaSuccess && vr) e = cudaMemcpyAsync(vr, P.vr, b, kind, st);
+      if (e == cudaSuccess && vt) e = cudaMemcpyAsync(vt, P.vt, b, kind, st);
+      if (e == cudaSuccess && vz) e = cudaMemcpyAsync(vz, P.vz, b, kind, st);
+      if (e == cudaSuccess && id) e = cudaMemcpyAsync(id, P.id, b, kind, st);
+    }
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(h, e, "get_particles");
@@ -611,9 +698,21 @@ int pic_save(pic_handle* h, int instance, const char* path) {
   ok = ok && std::fwrite(phi.data(), 8, nn, f) == nn;
   for (int sp = 0; sp < 2 && ok; ++sp) {
     const long long n = s.n[sp];
+    ok = std::fwrite(&n, 8, 1, f) == 1;
+    if (ih.I.prec32) {
+      // raw FP32 records: the checkpoint restores the state bit for bit
+      std::vector<float4> ra((size_t)n);
+      std::vector<uint4> rb((size_t)n);
+      if (ok && n > 0 &&
+          (cudaMemcpy(ra.data(), ih.I.cur32[sp].a, (size_t)n * 16, cudaMemcpyDeviceToHost) != cudaSuccess ||
+           cudaMemcpy(rb.data(), ih.I.cur32[sp].b, (size_t)n * 16, cudaMemcpyDeviceToHost) != cudaSuccess))
+        ok = false;
+      ok = ok && std::fwrite(ra.data(), 16, (size_t)n, f) == (size_t)n;
+      ok = ok && std::fwrite(rb.data(), 16, (size_t)n, f) == (size_t)n;
+      continue;
+    }
     std::vector<double> buf((size_t)n);
     std::vector<long long> ids((size_t)n);
-    ok = std::fwrite(&n, 8, 1, f) == 1;
     const ParticlesDev& P = ih.I.cur[sp];
     for (double* src : {P.r, P.z, P.vr, P.vt, P.vz}) {
       if (!ok) break;
@@ -642,15 +741,24 @@ int pic_load(pic_handle* h, int instance, const char* path) {
   std::vector<double> qh((size_t)c.n_avg), phi(nn);
   bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "PICCKPT1", 8) == 0;
   ok = ok && std::fread(&fc, sizeof(fc), 1, f) == 1;
-  ok = ok && fc.nr == c.nr && fc.nz == c.nz && fc.n_avg == c.n_avg;
+  ok = ok && fc.nr == c.nr && fc.nz == c.nz && fc.n_avg == c.n_avg && fc.precision == c.precision;
   ok = ok && std::fread(&s, sizeof(s), 1, f) == 1;
   ok = ok && std::fread(qh.data(), 8, qh.size(), f) == qh.size();
   ok = ok && std::fread(phi.data(), 8, nn, f) == nn;
   std::vector<double> arr[2][5];
   std::vector<long long> ids[2];
+  std::vector<float4> ra[2];
+  std::vector<uint4> rb[2];
   long long n[2] = {0, 0};
   for (int sp = 0; sp < 2 && ok; ++sp) {
     ok = std::fread(&n[sp], 8, 1, f) == 1 && n[sp] >= 0 && n[sp] <= ih.I.cap[sp];
+    if (ok && ih.I.prec32) {
+      ra[sp].resize((size_t)n[sp]);
+      rb[sp].resize((size_t)n[sp]);
+      ok = std::fread(ra[sp].data(), 16, (size_t)n[sp], f) == (size_t)n[sp];
+      ok = ok && std::fread(rb[sp].data(), 16, (size_t)n[sp], f) == (size_t)n[sp];
+      continue;
+    }
     for (int k = 0; k < 5 && ok; ++k) {
       arr[sp][k].resize((size_t)n[sp]);
       ok = std::fread(arr[sp][k].data(), 8, (size_t)n[sp], f) == (size_t)n[sp];
@@ -663,6 +771,16 @@ int pic_load(pic_handle* h, int instance, const char* path) {
   std::fclose(f);
   if (!ok) return fail(h, PIC_ERR_IO, "checkpoint read failed or does not match the handle");
   for (int sp = 0; sp < 2; ++sp) {
+    if (ih.I.prec32) {
+      cudaError_t e0 = cudaSuccess;
+      if (n[sp] > 0) {
+        e0 = cudaMemcpy(ih.I.cur32[sp].a, ra[sp].data(), (size_t)n[sp] * 16, cudaMemcpyHostToDevice);
+        if (e0 == cudaSuccess)
+          e0 = cudaMemcpy(ih.I.cur32[sp].b, rb[sp].data(), (size_t)n[sp] * 16, cudaMemcpyHostToDevice);
+      }
+      if (e0 != cudaSuccess) return cuda_fail(h, e0, "load copy");
+      continue;
+    }
     const int rc = pic_set_particles(h, instance, sp, n[sp], arr[sp][0].data(), arr[sp][1].data(),
                                      arr[sp][2].data(), arr[sp][3].data(), arr[sp][4].data(),
                                      (const int64_t*)ids[sp].data(), 0);
@@ -670,8 +788,8 @@ int pic_load(pic_handle* h, int instance, const char* path) {
   }
   Scalars cur;
   read_status(h, instance, &cur);
-  s.n[0] = cur.n[0];
-  s.n[1] = cur.n[1];
+  s.n[0] = ih.I.prec32 ? n[0] : cur.n[0];
+  s.n[1] = ih.I.prec32 ? n[1] : cur.n[1];
   cudaError_t e = cudaMemcpy(ih.I.S, &s, sizeof(s), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ih.I.qhist, qh.data(), qh.size() * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ih.I.phi, phi.data(), nn * 8, cudaMemcpyHostToDevice);

@@ -45,7 +45,17 @@ struct ParticlesDev {
   long long* id;
 };
 
+// FP32 particle mode: 32 bytes per particle in two 16-byte records,
+// a = {dr, dz, v_r, v_theta} (dr, dz: FP32 offsets in [0,1) inside the cell),
+// b = {v_z (bits), cell key, id low word, id high word}; key -1 = removed.
+struct Particles32 {
+  float4* a;
+  uint4* b;
+};
+
 struct BirthsDev {
+  float4* a32;                // FP32 mode records (cell key in b32.y, id in b32.z/w)
+  uint4* b32;
   double *r, *z, *vr, *vt, *vz;
   unsigned long long* pkey;   // (parent id << 2) | kind
   int* cell;                  // cell key of the birth position
@@ -100,6 +110,7 @@ struct Inst {
   double qm[2], mass[2], gamma[2];
   // collisions
   double n_gas, T_gas, m_ion, sigma_el, ion_a, ion_I, exc_C, exc_E, nu_max, p_null;
+  unsigned long long pnull_k;   // ceil(p_null 2^53): U < p_null  <=>  (word >> 11) < pnull_k
   unsigned long long seed;
   // switches
   int gather, rweight, mcc_on, push_on, field_on, walls_reflect, circuit_mode, n_avg;
@@ -108,6 +119,16 @@ struct Inst {
   double poisson_tol;
   int poisson_max_iter;
   long long cap[2], birth_cap;
+  // FP32 particle mode
+  int prec32;
+  float hq32[2];           // q dt / 2m per species
+  float kr32, kz32;        // dt / dr, dt / dz
+  Particles32 cur32[2], nxt32[2];
+  double* qacc64[2];       // FP32 mode: FP64 node sums of deposited macro-charges
+  float4* etab32;          // FP32 gather tables (layout as etab / btab)
+  float4* btab32;
+  double* stage;           // FP64 staging of pic_set/get_particles in FP32 mode
+  long long stage_len;     // particles per staging chunk
   // device arrays
   ParticlesDev cur[2], nxt[2];
   int* key[2];
@@ -183,20 +204,25 @@ __device__ __forceinline__ double rweight_upper(const Inst& I, double r, int m, 
 }
 
 // Fixed-point corner weights of a unit charge at in-cell weights (wr, wz):
-// exact integers summing to 2^44.
+// exact integers summing to 2^44.  w11 = round(ir iz / 2^44) from the 88-bit
+// integer product, so only two FP64 -> integer conversions are needed.
 struct FixW { unsigned long long w00, w10, w01, w11; };
 __device__ __forceinline__ FixW fix_weights(double wr, double wz) {
-  double a = wr * kFixOne;               // exact scaling by a power of two
-  double b = wz * kFixOne;
-  unsigned long long i11 = (unsigned long long)__double2ll_rn(a * wz);
-  unsigned long long ir = (unsigned long long)__double2ll_rn(a);
-  unsigned long long iz = (unsigned long long)__double2ll_rn(b);
+  const unsigned long long ir = (unsigned long long)__double2ll_rn(wr * kFixOne);  // exact scaling
+  const unsigned long long iz = (unsigned long long)__double2ll_rn(wz * kFixOne);
+  const unsigned long long lo = ir * iz, hi = __umul64hi(ir, iz);
+  const unsigned long long i11 = ((hi << (64 - kFixBits)) | (lo >> kFixBits)) + ((lo >> (kFixBits - 1)) & 1ULL);
   FixW f;
   f.w11 = i11;
   f.w10 = ir - i11;
   f.w01 = iz - i11;
   f.w00 = (1ULL << kFixBits) - ir - iz + i11;   // modular arithmetic keeps the sum exact
   return f;
+}
+
+// finite test on the exponent bits (integer pipe)
+__device__ __forceinline__ bool finite64(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
 }
 
 __device__ __forceinline__ double node_area(const Inst& I, int m) {

@@ -33,6 +33,23 @@ cudaError_t launch_set_n(const Inst& I, int sp, long long n, cudaStream_t st);
 // deposit the current particles, set the cathode values and solve phi
 cudaError_t launch_solve_fields(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_t st);
 
+// pieces shared with the FP32 path
+cudaError_t launch_scan(const Inst& I, int sp0, int nsp, cudaStream_t st);
+cudaError_t launch_commit_n(const Inst& I, int sp, cudaStream_t st);
+
+// FP32 particle path (step32.cu)
+cudaError_t launch_pack32(const Inst& I, int sp, long long offset, long long count, const double* r,
+                          const double* z, const double* vr, const double* vt, const double* vz,
+                          const long long* id, int num_sms, cudaStream_t st);
+cudaError_t launch_unpack32(const Inst& I, int sp, long long offset, long long count, double* r,
+                            double* z, double* vr, double* vt, double* vz, long long* id,
+                            int num_sms, cudaStream_t st);
+cudaError_t launch_sort_species32(const Inst& I, int sp, int num_sms, cudaStream_t st);
+cudaError_t launch_deposit_all32(const Inst& I, int num_sms, cudaStream_t st);
+cudaError_t launch_push32(const Inst& I, int sp, int num_sms, cudaStream_t st);
+cudaError_t launch_births32(const Inst& I, cudaStream_t st);
+cudaError_t launch_scatter32(const Inst& I, int num_sms, cudaStream_t st);
+
 // compute node charge Q from the fixed-point sums (and clear them)
 cudaError_t launch_charge(const Inst& I, cudaStream_t st);
 

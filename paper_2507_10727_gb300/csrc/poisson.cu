@@ -77,17 +77,22 @@ size_t poisson_work_bytes(int nr, int nz) {
 // ----------------------------------------------------------------------------
 // device pieces
 // ----------------------------------------------------------------------------
+// Grid barrier with a time limit.  The arrival counter and the generation word
+// sit in different 128-byte lines so that the waiting blocks' polling does not
+// contend with the arrivals.
+constexpr int kBarGen = 32;   // bar[0]: arrivals, bar[kBarGen]: generation
+
 __device__ __forceinline__ bool barrier_grid(unsigned int* bar, int* status) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = bar + 1;
+    volatile unsigned int* vgen = bar + kBarGen;
     const unsigned int g = *vgen;
     __threadfence();
     const unsigned int arrived = atomicAdd(bar, 1u);
     if (arrived == gridDim.x - 1) {
       atomicExch(bar, 0u);
       __threadfence();
-      atomicAdd(bar + 1, 1u);
+      atomicAdd(bar + kBarGen, 1u);
     } else {
       const double t0 = global_time_ns();
       unsigned int spins = 0;
@@ -209,42 +214,74 @@ __device__ void prolong_from(const Lev& F, const Lev& C, int tid, int nthr) {
   }
 }
 
-// levels >= l0 inside one CTA (block-level synchronisation only)
-__device__ void vcycle_tail(const PoissonWork& W, int l0) {
+// Levels >= l0 inside one CTA (block-level synchronisation only).
+constexpr int kTailSmemFloats = 2 * 5800;   // u and f of levels with <= kTailNodes nodes
+
+__device__ void vcycle_levels(Lev* T, int l0, int nlev) {
   const int tid = threadIdx.x, nthr = blockDim.x;
-  for (int l = l0; l < W.nlev - 1; ++l) {
-    const Lev F = lev(W, l), C = lev(W, l + 1);
-    smooth(F, 0, tid, nthr);
+  for (int l = l0; l < nlev - 1; ++l) {
+    smooth(T[l], 0, tid, nthr);
     __syncthreads();
-    smooth(F, 1, tid, nthr);
+    smooth(T[l], 1, tid, nthr);
     __syncthreads();
-    restrict_to(F, C, tid, nthr);
+    restrict_to(T[l], T[l + 1], tid, nthr);
     __syncthreads();
   }
   {
-    const Lev C = lev(W, W.nlev - 1);
-    for (int s = 0; s < 16; ++s) {
+    const Lev& C = T[nlev - 1];
+    for (int s = 0; s < 8; ++s) {
       smooth(C, 0, tid, nthr);
       __syncthreads();
       smooth(C, 1, tid, nthr);
       __syncthreads();
     }
-    for (int s = 0; s < 16; ++s) {
+    for (int s = 0; s < 8; ++s) {
       smooth(C, 1, tid, nthr);
       __syncthreads();
       smooth(C, 0, tid, nthr);
       __syncthreads();
     }
   }
-  for (int l = W.nlev - 2; l >= l0; --l) {
-    const Lev F = lev(W, l), C = lev(W, l + 1);
-    prolong_from(F, C, tid, nthr);
+  for (int l = nlev - 2; l >= l0; --l) {
+    prolong_from(T[l], T[l + 1], tid, nthr);
     __syncthreads();
-    smooth(F, 1, tid, nthr);
+    smooth(T[l], 1, tid, nthr);
     __syncthreads();
-    smooth(F, 0, tid, nthr);
+    smooth(T[l], 0, tid, nthr);
     __syncthreads();
   }
+}
+
+// The tail in shared memory when it fits in `buf` (f of level l0 loaded, u
+// of level l0 written back), else in the global level arrays.
+__device__ void vcycle_tail(const PoissonWork& W, int l0, float* buf) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  Lev T[kMaxLev];
+  int total = 0;
+  for (int l = l0; l < W.nlev; ++l) {
+    T[l] = lev(W, l);
+    total += 2 * (T[l].nr + 1) * (T[l].nz + 1);
+  }
+  if (total > kTailSmemFloats) {
+    vcycle_levels(T, l0, W.nlev);
+    return;
+  }
+  float* p = buf;
+  for (int l = l0; l < W.nlev; ++l) {
+    const int nn = (T[l].nr + 1) * (T[l].nz + 1);
+    T[l].u = p;
+    T[l].f = p + nn;
+    p += 2 * nn;
+  }
+  for (int k = tid; k < total; k += nthr) buf[k] = 0.0f;
+  __syncthreads();
+  const int nn0 = (T[l0].nr + 1) * (T[l0].nz + 1);
+  const float* fg = W.f[l0];
+  for (int k = tid; k < nn0; k += nthr) T[l0].f[k] = fg[k];
+  __syncthreads();
+  vcycle_levels(T, l0, W.nlev);
+  float* ug = W.u[l0];
+  for (int k = tid; k < nn0; k += nthr) ug[k] = T[l0].u[k];
 }
 
 __device__ __forceinline__ double warp_sum64(double v) {
@@ -301,6 +338,7 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A) {
   double* phi = A.phi;
   int parity = 0;
   double vals[3];
+  __shared__ float tail_buf[kTailSmemFloats];
 
   // residual r = Q - A phi (Dirichlet values in phi), ||b||^2, ||r||^2
   double bb = 0.0, rr = 0.0;
@@ -356,7 +394,7 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A) {
       restrict_to(F, C, gtid, gthr);
       if (!barrier_grid(W.bar, A.status)) return;
     }
-    if (blockIdx.x == 0) vcycle_tail(W, W.tail);
+    if (blockIdx.x == 0) vcycle_tail(W, W.tail, tail_buf);
     if (!barrier_grid(W.bar, A.status)) return;
     for (int l = W.tail - 1; l >= 0; --l) {
       const Lev F = lev(W, l), C = lev(W, l + 1);

@@ -17,6 +17,7 @@
 #include <cstdio>
 
 #include "common.cuh"
+#include "device_util.cuh"
 #include "launch.h"
 
 namespace pic {
@@ -27,28 +28,6 @@ constexpr int kChunk = kPushThreads * kPPT;      // particles per chunk
 constexpr int kHalo = 3;                         // cells a particle may move and still hit the patch
 constexpr int kPR = kTile + 2 * kHalo + 1;       // patch nodes in r
 constexpr int kPZ = 2 * kTile + 2 * kHalo + 1;   // patch nodes in z (two tiles along z)
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// block-wide sum of v added atomically to *dst (used for diagnostics only)
-__device__ void block_add(double v, double* dst) {
-  __shared__ double red[32];
-  v = warp_sum(v);
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    int nw = (blockDim.x + 31) >> 5;
-    double s = lane < nw ? red[lane] : 0.0;
-    s = warp_sum(s);
-    if (lane == 0 && s != 0.0) atomicAdd(dst, s);
-  }
-  __syncthreads();
-}
 
 // ---------------------------------------------------------------------------
 // Field gather tables (Section 2).
@@ -87,7 +66,8 @@ __global__ void k_field_tables(Inst I) {
         }
         t = make_d4(er_lo, er_hi - er_lo, ez_lo, ez_hi - ez_lo);
       }
-      I.etab[key] = t;
+      if (I.prec32) I.etab32[key] = make_float4((float)t.x, (float)t.y, (float)t.z, (float)t.w);
+      else I.etab[key] = t;
     } else {
       double er[2][2], ez[2][2];
       for (int a = 0; a < 2; ++a)
@@ -110,8 +90,13 @@ __global__ void k_field_tables(Inst I) {
         tz = make_d4(ez[0][0], ez[1][0] - ez[0][0], ez[0][1] - ez[0][0],
                           ez[1][1] - ez[1][0] - ez[0][1] + ez[0][0]);
       }
-      I.etab[2 * key] = tr;
-      I.etab[2 * key + 1] = tz;
+      if (I.prec32) {
+        I.etab32[2 * key] = make_float4((float)tr.x, (float)tr.y, (float)tr.z, (float)tr.w);
+        I.etab32[2 * key + 1] = make_float4((float)tz.x, (float)tz.y, (float)tz.z, (float)tz.w);
+      } else {
+        I.etab[2 * key] = tr;
+        I.etab[2 * key + 1] = tz;
+      }
     }
     if (diag) {
       // edges owned by this cell: r-edge (m,n), z-edge (m,n); the last row /
@@ -165,34 +150,16 @@ __device__ void add_birth(const Inst& I, int sp, unsigned long long pkey, double
   atomicAdd(q + node_index(I, m + 1, n + 1), f.w11);
 }
 
-// new direction: e rotated by polar angle chi (cos given) and azimuth phi,
-// in the frame (u, w) built from the coordinate axis of e's smallest component
-__device__ __forceinline__ void scatter_dir(const double e[3], double cos_chi, double phi,
-                                            double out[3]) {
-  int a = 0;
-  if (fabs(e[1]) < fabs(e[a])) a = 1;
-  if (fabs(e[2]) < fabs(e[a])) a = 2;
-  double ax[3] = {0.0, 0.0, 0.0};
-  ax[a] = 1.0;
-  double u[3] = {ax[1] * e[2] - ax[2] * e[1], ax[2] * e[0] - ax[0] * e[2],
-                 ax[0] * e[1] - ax[1] * e[0]};
-  const double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-  u[0] /= un; u[1] /= un; u[2] /= un;
-  const double w[3] = {e[1] * u[2] - e[2] * u[1], e[2] * u[0] - e[0] * u[2],
-                       e[0] * u[1] - e[1] * u[0]};
-  const double sin_chi = sqrt(fmax(0.0, 1.0 - cos_chi * cos_chi));
-  double sp, cp;
-  sincos(phi, &sp, &cp);
-  for (int j = 0; j < 3; ++j) out[j] = cos_chi * e[j] + sin_chi * (cp * u[j] + sp * w[j]);
-}
-
 // Null-collision MCC for one electron (Section 3, reactions (1a)-(1c), [14]).
 // Returns true when the velocity changed.
 __device__ bool mcc_electron(const Inst& I, long long id, long long step, double r, double z,
                              double& vr, double& vt, double& vz) {
+  unsigned long long w[4];
+  philox4x64((unsigned long long)id, (unsigned long long)step, 0ULL, 0ULL, I.seed, 0ULL, w);
+  // candidate test U1 < p_null done exactly on the integer word
+  if ((w[0] >> 11) >= I.pnull_k) return false;
   double u[4];
-  draws(I, 0, id, step, 0, u);
-  if (!(u[0] < I.p_null)) return false;
+  u[0] = u01(w[0]); u[1] = u01(w[1]); u[2] = u01(w[2]); u[3] = u01(w[3]);
   const double v[3] = {vr, vt, vz};
   const double vmag = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
   const double E = 0.5 * kMe * vmag * vmag / kQe;
@@ -253,7 +220,7 @@ __device__ bool mcc_electron(const Inst& I, long long id, long long step, double
 // patch (fast movers, chunk tails in sparse regions) add to global memory.
 // ---------------------------------------------------------------------------
 template <int SP, int GATHER>
-__global__ void __launch_bounds__(kPushThreads) k_push(Inst I) {
+__global__ void __launch_bounds__(kPushThreads, 3) k_push(Inst I) {
   Scalars* S = I.S;
   if (S->status & ST_FATAL) return;
   __shared__ unsigned long long patch[kPR * kPZ];
@@ -370,7 +337,8 @@ __global__ void __launch_bounds__(kPushThreads) k_push(Inst I) {
           }
         }
         if (alive) {
-          if (!(isfinite(r1) && isfinite(z1) && isfinite(vr) && isfinite(vt) && isfinite(vz))) {
+          // a non-finite velocity component makes the new position non-finite
+          if (!(finite64(r1) && finite64(z1))) {
             atomicOr(&S->status, ST_NAN);
             alive = false;
           }
@@ -428,27 +396,6 @@ __global__ void __launch_bounds__(kPushThreads) k_push(Inst I) {
 // sort in shared memory up to kSmemSort entries, in global scratch beyond.
 // ---------------------------------------------------------------------------
 constexpr int kSmemSort = 4096;
-
-__device__ void bitonic(unsigned long long* key, unsigned int* idx, int P) {
-  for (int k = 2; k <= P; k <<= 1)
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const int l = i ^ j;
-        if (l > i) {
-          const bool up = (i & k) == 0;
-          const unsigned long long a = key[i], b = key[l];
-          if ((a > b) == up) {
-            key[i] = b;
-            key[l] = a;
-            const unsigned int t = idx[i];
-            idx[i] = idx[l];
-            idx[l] = t;
-          }
-        }
-      }
-      __syncthreads();
-    }
-}
 
 __global__ void __launch_bounds__(1024) k_births(Inst I) {
   Scalars* S = I.S;
@@ -577,29 +524,46 @@ __global__ void k_scatter(Inst I, int sp0) {
   }
 }
 
-// keys + histogram of particles loaded by pic_set_particles; range check
+// keys + histogram of particles loaded by pic_set_particles; range check.
+// Histogram increments are aggregated over the lanes of a warp that share a
+// cell, and the id maximum over the warp, to keep atomics off hot addresses.
 __global__ void k_keys(Inst I, int sp) {
   Scalars* S = I.S;
   const long long n = S->n[sp];
   const ParticlesDev P = I.cur[sp];
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const double r = P.r[i], z = P.z[i];
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+  long long idmax = -1;
+  bool bad = false;
+  for (long long base = warp * 32; base < n; base += nwarp * 32) {
+    const long long i = base + lane;
     int key = -1;
-    if (r >= 0.0 && r < I.R && z >= 0.0 && z < I.L && isfinite(P.vr[i]) && isfinite(P.vt[i]) &&
-        isfinite(P.vz[i]) && P.id[i] >= 0) {
-      int m, nn;
-      double f;
-      locate(r, I.inv_dr, I.nr, m, f);
-      locate(z, I.inv_dz, I.nz, nn, f);
-      key = cell_key(I, m, nn);
-      atomicAdd(&I.counts[sp][key], 1);
-      atomicMax(&S->next_id, P.id[i] + 1);
-    } else {
-      atomicOr(&S->status, ST_NAN);
+    if (i < n) {
+      const double r = P.r[i], z = P.z[i];
+      if (r >= 0.0 && r < I.R && z >= 0.0 && z < I.L && finite64(P.vr[i]) && finite64(P.vt[i]) &&
+          finite64(P.vz[i]) && P.id[i] >= 0) {
+        int m, nn;
+        double f;
+        locate(r, I.inv_dr, I.nr, m, f);
+        locate(z, I.inv_dz, I.nz, nn, f);
+        key = cell_key(I, m, nn);
+        idmax = P.id[i] > idmax ? P.id[i] : idmax;
+      } else {
+        bad = true;
+      }
+      I.key[sp][i] = key;
     }
-    I.key[sp][i] = key;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&I.counts[sp][key], __popc(peers));
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long other = __shfl_xor_sync(0xffffffffu, idmax, o);
+    idmax = other > idmax ? other : idmax;
+  }
+  if (lane == 0 && idmax >= 0) atomicMax(&S->next_id, idmax + 1);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&S->status, ST_NAN);
 }
 
 // n = n_next after a set-up sort (no births)
@@ -643,15 +607,26 @@ __global__ void k_charge(Inst I) {
   const double scale = kQe * I.weight * kFixInv;
   double pe = 0.0, pi = 0.0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += gridDim.x * blockDim.x) {
-    const unsigned long long ue = I.qacc[0][k], ui = I.qacc[1][k];
-    I.qacc[0][k] = 0ULL;
-    I.qacc[1][k] = 0ULL;
-    I.Q[k] = (double)(long long)(ui - ue) * scale;
+    double se, si;   // deposited macroparticles of each species at the node
+    if (I.prec32) {
+      se = I.qacc64[0][k];
+      si = I.qacc64[1][k];
+      I.qacc64[0][k] = 0.0;
+      I.qacc64[1][k] = 0.0;
+      I.Q[k] = (si - se) * (kQe * I.weight);
+    } else {
+      const unsigned long long ue = I.qacc[0][k], ui = I.qacc[1][k];
+      I.qacc[0][k] = 0ULL;
+      I.qacc[1][k] = 0ULL;
+      I.Q[k] = (double)(long long)(ui - ue) * scale;
+      se = (double)ue * kFixInv;
+      si = (double)ui * kFixInv;
+    }
     if (diag) {
       const int m = k / (I.nz + 1), n = k - m * (I.nz + 1);
-      const double sv = I.weight * kFixInv / node_volume(I, m, n);
-      pe = fmax(pe, (double)ue * sv);
-      pi = fmax(pi, (double)ui * sv);
+      const double sv = I.weight / node_volume(I, m, n);
+      pe = fmax(pe, se * sv);
+      pi = fmax(pi, si * sv);
     }
   }
   if (diag) {
@@ -769,6 +744,19 @@ __global__ void k_step_end(Inst I) {
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
+// one wave of a persistent kernel: resident blocks per SM x SMs (cached per kernel)
+template <typename K>
+static int resident_grid(K kernel, int threads, int num_sms) {
+  static int per = 0;
+  if (per == 0) {
+    int p = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kernel, threads, 0) != cudaSuccess || p < 1)
+      p = 1;
+    per = p;
+  }
+  return per * num_sms;
+}
+
 static int grid_for(long long work, int threads, int num_sms, int per_sm) {
   long long g = (work + threads - 1) / threads;
   long long cap = (long long)num_sms * per_sm;
@@ -798,9 +786,24 @@ cudaError_t launch_sort_species(const Inst& I, int sp, int num_sms, cudaStream_t
   return cudaGetLastError();
 }
 
+cudaError_t launch_scan(const Inst& I, int sp0, int nsp, cudaStream_t st) {
+  k_scan<<<nsp, 1024, 0, st>>>(I, sp0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_commit_n(const Inst& I, int sp, cudaStream_t st) {
+  k_commit_n<<<1, 32, 0, st>>>(I, sp);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_solve_fields(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_t st) {
-  for (int sp = 0; sp < 2; ++sp)
-    k_deposit_all<<<grid_for(I.cap[sp], 256, num_sms, 8), 256, 0, st>>>(I, sp);
+  if (I.prec32) {
+    cudaError_t e0 = launch_deposit_all32(I, num_sms, st);
+    if (e0 != cudaSuccess) return e0;
+  } else {
+    for (int sp = 0; sp < 2; ++sp)
+      k_deposit_all<<<grid_for(I.cap[sp], 256, num_sms, 8), 256, 0, st>>>(I, sp);
+  }
   cudaError_t e = launch_charge(I, st);
   if (e != cudaSuccess) return e;
   k_set_cathode<<<1, 256, 0, st>>>(I);
@@ -817,23 +820,30 @@ cudaError_t launch_step(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_
   mk(G_FIELD, true);
   k_field_tables<<<grid_for(ncell, 256, num_sms, 8), 256, 0, st>>>(I);
   mk(G_FIELD, false);
-  const int pg = num_sms * 4;
   mk(G_PUSH_E, true);
-  if (I.gather == 0) k_push<0, 0><<<pg, kPushThreads, 0, st>>>(I);
-  else k_push<0, 1><<<pg, kPushThreads, 0, st>>>(I);
+  if (I.prec32) launch_push32(I, 0, num_sms, st);
+  else if (I.gather == 0)
+    k_push<0, 0><<<resident_grid(k_push<0, 0>, kPushThreads, num_sms), kPushThreads, 0, st>>>(I);
+  else
+    k_push<0, 1><<<resident_grid(k_push<0, 1>, kPushThreads, num_sms), kPushThreads, 0, st>>>(I);
   mk(G_PUSH_E, false);
   mk(G_PUSH_I, true);
-  if (I.gather == 0) k_push<1, 0><<<pg, kPushThreads, 0, st>>>(I);
-  else k_push<1, 1><<<pg, kPushThreads, 0, st>>>(I);
+  if (I.prec32) launch_push32(I, 1, num_sms, st);
+  else if (I.gather == 0)
+    k_push<1, 0><<<resident_grid(k_push<1, 0>, kPushThreads, num_sms), kPushThreads, 0, st>>>(I);
+  else
+    k_push<1, 1><<<resident_grid(k_push<1, 1>, kPushThreads, num_sms), kPushThreads, 0, st>>>(I);
   mk(G_PUSH_I, false);
   mk(G_BIRTHS, true);
-  k_births<<<1, 1024, 0, st>>>(I);
+  if (I.prec32) launch_births32(I, st);
+  else k_births<<<1, 1024, 0, st>>>(I);
   mk(G_BIRTHS, false);
   mk(G_SCAN, true);
   k_scan<<<2, 1024, 0, st>>>(I, 0);
   mk(G_SCAN, false);
   mk(G_SCATTER, true);
-  k_scatter<<<dim3(num_sms * 8, 2), 256, 0, st>>>(I, 0);
+  if (I.prec32) launch_scatter32(I, num_sms, st);
+  else k_scatter<<<dim3(num_sms * 8, 2), 256, 0, st>>>(I, 0);
   mk(G_SCATTER, false);
   mk(G_CHARGE, true);
   cudaError_t e = launch_charge(I, st);

@@ -1,0 +1,570 @@
+// step32.cu -- FP32 particle path (precision mode 1) of the RZ PIC-MCC step.
+//
+// Same method and step order as the FP64 path (step.cu); what changes is the
+// arithmetic of the particle loop:
+//  * a particle is 32 bytes: {dr, dz, v_r, v_theta} + {v_z, cell key, id}; the
+//    position is the cell index plus FP32 offsets in [0,1) of the cell, so its
+//    resolution is 2^-24 of a cell everywhere in the domain;
+//  * gather, Boris, move and MCC run in FP32; the move is done in local cell
+//    units, and the new radius relative to the old cell uses the cancellation-
+//    free form  r' - m = (x' - m) + y'^2 / (r' + x')  (x' > 0);
+//  * the deposit accumulates FP32 weights in a shared-memory patch and flushes
+//    it into FP64 node sums; the Poisson residuals, the circuit and the
+//    energy / charge reductions stay FP64 (the shared kernels of step.cu and
+//    poisson.cu).
+#include "common.cuh"
+#include "device_util.cuh"
+#include "launch.h"
+
+namespace pic {
+
+constexpr int kPush32Threads = 256;
+constexpr int kPPT32 = 8;
+constexpr int kChunk32 = kPush32Threads * kPPT32;
+constexpr int kHalo32 = 3;
+constexpr int kPR32 = kTile + 2 * kHalo32 + 1;
+constexpr int kPZ32 = 2 * kTile + 2 * kHalo32 + 1;
+constexpr float kHalfMeOverE = (float)(0.5 * kMe / kQe);   // E[eV] = kHalfMeOverE v^2
+constexpr float kTwoEOverMe = (float)(2.0 * kQe / kMe);    // v^2 = kTwoEOverMe E[eV]
+
+__device__ __forceinline__ void key_to_mn(const Inst& I, int key, int& m, int& n) {
+  const int tile = key >> 6, within = key & 63;
+  const int tm = tile / I.ntz, tn = tile - tm * I.ntz;
+  m = (tm << 3) + (within >> 3);
+  n = (tn << 3) + (within & 7);
+}
+
+__device__ __forceinline__ float rweight_upper32(const Inst& I, float dr, int m) {
+  if (I.rweight == 0) return dr;
+  return dr * (2.0f * (float)m + dr) / (2.0f * (float)m + 1.0f);
+}
+
+__device__ __forceinline__ float u01f(unsigned long long x) {
+  return (float)(x >> 40) * (1.0f / 16777216.0f);
+}
+
+__device__ __forceinline__ long long id_of(const uint4& b) {
+  return (long long)(((unsigned long long)b.w << 32) | (unsigned long long)b.z);
+}
+
+// global deposit of one macroparticle (FP32 weights into FP64 node sums)
+__device__ __forceinline__ void deposit_global32(const Inst& I, int sp, int m, int n, float wr,
+                                                 float wz) {
+  double* q = I.qacc64[sp];
+  const int i = node_index(I, m, n), nz1 = I.nz + 1;
+  atomicAdd(q + i, (double)((1.0f - wr) * (1.0f - wz)));
+  atomicAdd(q + i + nz1, (double)(wr * (1.0f - wz)));
+  atomicAdd(q + i + 1, (double)((1.0f - wr) * wz));
+  atomicAdd(q + i + nz1 + 1, (double)(wr * wz));
+}
+
+__device__ void add_birth32(const Inst& I, int sp, unsigned long long pkey, int m, float dr, int n,
+                            float dz, float vr, float vt, float vz) {
+  Scalars* S = I.S;
+  const unsigned long long b = atomicAdd((unsigned long long*)&S->nbirth[sp], 1ULL);
+  if ((long long)b >= I.birth_cap) {
+    atomicOr(&S->status, ST_CAPACITY);
+    return;
+  }
+  const int key = cell_key(I, m, n);
+  const BirthsDev& B = I.births[sp];
+  B.a32[b] = make_float4(dr, dz, vr, vt);
+  B.b32[b] = make_uint4(__float_as_uint(vz), (unsigned)key, 0u, 0u);
+  B.pkey[b] = pkey;
+  atomicAdd(&I.counts[sp][key], 1);
+  deposit_global32(I, sp, m, n, rweight_upper32(I, dr, m), dz);
+}
+
+__device__ __forceinline__ void scatter_dir32(const float e[3], float cos_chi, float phi,
+                                              float out[3]) {
+  int a = 0;
+  if (fabsf(e[1]) < fabsf(e[a])) a = 1;
+  if (fabsf(e[2]) < fabsf(e[a])) a = 2;
+  float ax[3] = {0.0f, 0.0f, 0.0f};
+  ax[a] = 1.0f;
+  float u[3] = {ax[1] * e[2] - ax[2] * e[1], ax[2] * e[0] - ax[0] * e[2],
+                ax[0] * e[1] - ax[1] * e[0]};
+  const float un = rsqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  u[0] *= un; u[1] *= un; u[2] *= un;
+  const float w[3] = {e[1] * u[2] - e[2] * u[1], e[2] * u[0] - e[0] * u[2],
+                      e[0] * u[1] - e[1] * u[0]};
+  const float sin_chi = sqrtf(fmaxf(0.0f, 1.0f - cos_chi * cos_chi));
+  float sp, cp;
+  sincosf(phi, &sp, &cp);
+  for (int j = 0; j < 3; ++j) out[j] = cos_chi * e[j] + sin_chi * (cp * u[j] + sp * w[j]);
+}
+
+// null-collision MCC of one electron in FP32 (candidate test exact on the
+// 64-bit Philox word, as in FP64 mode)
+__device__ void mcc_electron32(const Inst& I, long long id, long long step, int m, float dr, int n,
+                               float dz, float& vr, float& vt, float& vz) {
+  unsigned long long w[4];
+  philox4x64((unsigned long long)id, (unsigned long long)step, 0ULL, 0ULL, I.seed, 0ULL, w);
+  if ((w[0] >> 11) >= I.pnull_k) return;
+  const float v2 = vr * vr + vt * vt + vz * vz;
+  const float vmag = sqrtf(v2);
+  const float E = kHalfMeOverE * v2;
+  const float exE = (float)I.exc_E, ioI = (float)I.ion_I;
+  const float s_el = E > 0.0f ? (float)I.sigma_el : 0.0f;
+  const float s_ex = E > exE ? (float)I.exc_C * logf(E / exE) / (E * exE) : 0.0f;
+  const float s_io = E > ioI ? (float)I.ion_a * logf(E / ioI) / (E * ioI) : 0.0f;
+  const float ng = (float)I.n_gas;
+  const float nu_el = ng * s_el * vmag, nu_ex = ng * s_ex * vmag, nu_io = ng * s_io * vmag;
+  const float R = u01f(w[1]) * (float)I.nu_max;
+  const float inv = vmag > 0.0f ? 1.0f / vmag : 1.0f;
+  const float e[3] = {vr * inv, vt * inv, vz * inv};
+  const float cos_chi = 1.0f - 2.0f * u01f(w[2]);
+  const float phi = 2.0f * (float)kPi * u01f(w[3]);
+  float Enew;
+  Scalars* S = I.S;
+  if (R < nu_el) {
+    Enew = E * (1.0f - 2.0f * (float)(kMe / I.m_ion) * (1.0f - cos_chi));
+    atomicAdd(&S->cnt_elastic, 1ULL);
+  } else if (R < nu_el + nu_ex) {
+    Enew = E - exE;
+    atomicAdd(&S->cnt_excite, 1ULL);
+  } else if (R < nu_el + nu_ex + nu_io) {
+    unsigned long long w2[4], g[4];
+    philox4x64((unsigned long long)id, (unsigned long long)step, 1ULL, 0ULL, I.seed, 0ULL, w2);
+    const float Ex = E - ioI;
+    Enew = u01f(w2[0]) * Ex;
+    const float E2 = Ex - Enew;
+    float d2[3];
+    scatter_dir32(e, 1.0f - 2.0f * u01f(w2[1]), 2.0f * (float)kPi * u01f(w2[2]), d2);
+    const float v2n = sqrtf(kTwoEOverMe * E2);
+    const unsigned long long key = ((unsigned long long)id << 2) | 0ULL;
+    add_birth32(I, 0, key, m, dr, n, dz, v2n * d2[0], v2n * d2[1], v2n * d2[2]);
+    philox4x64((unsigned long long)id, (unsigned long long)step, 4ULL, 0ULL, I.seed, 0ULL, g);
+    const float sig = (float)sqrt(kBoltz * I.T_gas / I.m_ion);
+    const float rho1 = sqrtf(-2.0f * logf(1.0f - u01f(g[0]))), th1 = 2.0f * (float)kPi * u01f(g[1]);
+    const float rho2 = sqrtf(-2.0f * logf(1.0f - u01f(g[2]))), th2 = 2.0f * (float)kPi * u01f(g[3]);
+    float s1, c1, s2, c2;
+    sincosf(th1, &s1, &c1);
+    sincosf(th2, &s2, &c2);
+    add_birth32(I, 1, key, m, dr, n, dz, sig * rho1 * c1, sig * rho1 * s1, sig * rho2 * c2);
+    atomicAdd(&S->cnt_ionize, 1ULL);
+  } else {
+    return;
+  }
+  float d[3];
+  scatter_dir32(e, cos_chi, phi, d);
+  const float vn = sqrtf(kTwoEOverMe * fmaxf(Enew, 0.0f));
+  vr = vn * d[0];
+  vt = vn * d[1];
+  vz = vn * d[2];
+}
+
+// ---------------------------------------------------------------------------
+// The FP32 push: gather + Boris + move + walls + SEY + MCC + deposit, state
+// rewritten in place with the new cell key (read by the scatter).
+// ---------------------------------------------------------------------------
+template <int SP, int GATHER>
+__global__ void __launch_bounds__(kPush32Threads, 4) k_push32(Inst I) {
+  Scalars* S = I.S;
+  if (S->status & ST_FATAL) return;
+  __shared__ float patch[kPR32 * kPZ32];
+  __shared__ int anchor[2];
+  const long long n = S->n[SP];
+  const long long step = S->step;
+  const bool diag = S->diag_on != 0;
+  const Particles32 P = I.cur32[SP];
+  const float h = I.hq32[SP], kr = I.kr32, kz = I.kz32;
+  const float rc_cells = (float)(I.Rc * I.inv_dr);
+  const int lane = threadIdx.x & 31;
+  double Kloc = 0.0;
+  for (int k = threadIdx.x; k < kPR32 * kPZ32; k += blockDim.x) patch[k] = 0.0f;
+  for (long long c0 = (long long)blockIdx.x * kChunk32; c0 < n;
+       c0 += (long long)gridDim.x * kChunk32) {
+    if (threadIdx.x == 0) {
+      int m, nn;
+      key_to_mn(I, (int)P.b[c0].y, m, nn);
+      anchor[0] = (m & ~(kTile - 1)) - kHalo32;
+      anchor[1] = (nn & ~(kTile - 1)) - kHalo32;
+    }
+    __syncthreads();
+    const int pm0 = anchor[0], pn0 = anchor[1];
+#pragma unroll 1
+    for (int j = 0; j < kPPT32; ++j) {
+      const long long i = c0 + (long long)j * kPush32Threads + threadIdx.x;
+      int newkey = -1;
+      if (i < n) {
+        const float4 a = P.a[i];
+        const uint4 b = P.b[i];
+        int m, nn;
+        key_to_mn(I, (int)b.y, m, nn);
+        const float dr = a.x, dz = a.y;
+        float vr = a.z, vt = a.w, vz = __uint_as_float(b.x);
+        const float v2old = vr * vr + vt * vt + vz * vz;
+        float rho = dr, zeta = dz, X = (float)m + dr, y = 0.0f;
+        if (I.push_on) {
+          const int ck = (int)b.y;
+          const float wr = rweight_upper32(I, dr, m);
+          float Er, Ez;
+          if (GATHER == 0) {
+            const float4 t = I.etab32[ck];
+            Er = t.x + t.y * dz;
+            if (I.rweight == 1) Er *= ((float)m + dr) * (float)I.dr;
+            Ez = t.z + t.w * wr;
+          } else {
+            const float4 ta = I.etab32[2 * ck];
+            const float4 tb = I.etab32[2 * ck + 1];
+            Er = ta.x + wr * (ta.y + dz * ta.w) + dz * ta.z;
+            Ez = tb.x + wr * (tb.y + dz * tb.w) + dz * tb.z;
+          }
+          const float4 br = I.btab32[2 * ck];
+          const float4 bz = I.btab32[2 * ck + 1];
+          const float Br = br.x + dr * (br.y + dz * br.w) + dz * br.z;
+          const float Bz = bz.x + dr * (bz.y + dz * bz.w) + dz * bz.z;
+          const float ax = vr + h * Er, ay = vt, az = vz + h * Ez;
+          const float tx = h * Br, tz = h * Bz;
+          const float f2 = 2.0f / (1.0f + tx * tx + tz * tz);
+          const float sx = f2 * tx, sz = f2 * tz;
+          const float px = ax + ay * tz;
+          const float py = ay + (az * tx - ax * tz);
+          const float pz = az - ay * tx;
+          const float vx = ax + py * sz + h * Er;
+          const float vy = ay + (pz * sx - px * sz);
+          const float vzn = az - py * sx + h * Ez;
+          // move in cell units relative to the old cell
+          const float xl = dr + vx * kr;
+          y = vy * kr;
+          X = (float)m + xl;
+          const float R2 = X * X + y * y;
+          const float Rn = sqrtf(R2);
+          rho = X > 0.0f ? xl + y * y / (Rn + X) : Rn - (float)m;
+          if (Rn > 0.0f) {
+            const float inv = 1.0f / Rn;
+            vr = (X * vx + y * vy) * inv;
+            vt = (X * vy - y * vx) * inv;
+          } else {
+            vr = vx;
+            vt = vy;
+          }
+          vz = vzn;
+          zeta = dz + vzn * kz;
+        }
+        if (diag)
+          Kloc += 0.5 * I.mass[SP] * I.weight * 0.5 *
+                  ((double)v2old + (double)(vr * vr + vt * vt + vz * vz));
+        bool alive = true;
+        int m1, n1;
+        float dr1, dz1;
+        if (I.walls_reflect) {
+          float rc = (float)m + rho, zc = (float)nn + zeta;
+          if (zc < 0.0f) { zc = -zc; vz = -vz; }
+          if (zc >= (float)I.nz) { zc = 2.0f * I.nz - zc; vz = -vz; if (zc >= (float)I.nz) zc = nextafterf((float)I.nz, 0.0f); }
+          if (rc >= (float)I.nr) { rc = 2.0f * I.nr - rc; vr = -vr; if (rc >= (float)I.nr) rc = nextafterf((float)I.nr, 0.0f); }
+          m1 = (int)floorf(rc);
+          n1 = (int)floorf(zc);
+          dr1 = rc - (float)m1;
+          dz1 = zc - (float)n1;
+        } else {
+          const float fm = floorf(rho), fn = floorf(zeta);
+          m1 = m + (int)fm;
+          n1 = nn + (int)fn;
+          dr1 = rho - fm;
+          dz1 = zeta - fn;
+        }
+        if (dr1 >= 1.0f) { dr1 = 0.0f; ++m1; }
+        if (dz1 >= 1.0f) { dz1 = 0.0f; ++n1; }
+        if (m1 < 0) { m1 = 0; dr1 = 0.0f; }
+        if (!(isfinite(rho) && isfinite(zeta))) {
+          atomicOr(&S->status, ST_NAN);
+          alive = false;
+        } else if (!I.walls_reflect && (n1 < 0 || n1 >= I.nz || m1 >= I.nr)) {
+          alive = false;
+          if (n1 < 0) {
+            const float zo = (float)nn + dz, zn = (float)nn + zeta;
+            const float tc = zo / (zo - zn);
+            const float Xo = (float)m + dr;
+            const float xh = Xo + tc * (X - Xo), yh = tc * y;
+            const float rhit = sqrtf(xh * xh + yh * yh);   // cells
+            if (rhit <= rc_cells) {
+              atomicAdd(SP == 1 ? &S->cnt_ion_cath : &S->cnt_e_cath, 1ULL);
+              if (I.gamma[SP] > 0.0) {
+                const long long id = id_of(b);
+                double u[4];
+                draws(I, SP, id, step, 2, u);
+                if (u[0] < I.gamma[SP]) {
+                  atomicAdd(&S->cnt_sey, 1ULL);
+                  int mh = (int)floorf(rhit);
+                  float drh = rhit - (float)mh;
+                  if (mh > I.nr - 1) { mh = I.nr - 1; drh = 1.0f; }
+                  add_birth32(I, 0, ((unsigned long long)id << 2) | (SP == 1 ? 1ULL : 2ULL), mh,
+                              drh, 0, 0.0f, 0.0f, 0.0f, 0.0f);
+                }
+              }
+            }
+          }
+        }
+        if (alive) {
+          if (SP == 0 && I.mcc_on) mcc_electron32(I, id_of(b), step, m1, dr1, n1, dz1, vr, vt, vz);
+          newkey = cell_key(I, m1, n1);
+          P.a[i] = make_float4(dr1, dz1, vr, vt);
+          P.b[i] = make_uint4(__float_as_uint(vz), (unsigned)newkey, b.z, b.w);
+          const float wr1 = rweight_upper32(I, dr1, m1), wz1 = dz1;
+          const int lm = m1 - pm0, ln = n1 - pn0;
+          if (lm >= 0 && lm + 1 < kPR32 && ln >= 0 && ln + 1 < kPZ32) {
+            float* p = patch + lm * kPZ32 + ln;
+            atomicAdd(p, (1.0f - wr1) * (1.0f - wz1));
+            atomicAdd(p + kPZ32, wr1 * (1.0f - wz1));
+            atomicAdd(p + 1, (1.0f - wr1) * wz1);
+            atomicAdd(p + kPZ32 + 1, wr1 * wz1);
+          } else {
+            deposit_global32(I, SP, m1, n1, wr1, wz1);
+          }
+        } else {
+          reinterpret_cast<unsigned int*>(P.b + i)[1] = 0xffffffffu;   // key = -1
+        }
+      }
+      const unsigned peers = __match_any_sync(0xffffffffu, newkey);
+      if (newkey >= 0 && lane == __ffs(peers) - 1) atomicAdd(&I.counts[SP][newkey], __popc(peers));
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kPR32 * kPZ32; k += blockDim.x) {
+      const float v = patch[k];
+      if (v != 0.0f) {
+        const int gm = pm0 + k / kPZ32, gn = pn0 + k % kPZ32;
+        atomicAdd(I.qacc64[SP] + node_index(I, gm, gn), (double)v);
+        patch[k] = 0.0f;
+      }
+    }
+    __syncthreads();
+  }
+  if (diag) block_add(Kloc, &I.S->K[SP]);
+}
+
+// births: sort by (parent id, kind), ids into the records' id words
+constexpr int kSmemSort32 = 4096;
+
+__global__ void __launch_bounds__(1024) k_births32(Inst I) {
+  Scalars* S = I.S;
+  if (S->status & ST_FATAL) return;
+  __shared__ unsigned long long skey[kSmemSort32];
+  __shared__ unsigned int sidx[kSmemSort32];
+  long long base = S->next_id;
+  for (int sp = 0; sp < 2; ++sp) {
+    const long long nb = S->nbirth[sp] < I.birth_cap ? S->nbirth[sp] : I.birth_cap;
+    if (nb == 0) continue;
+    int P = 1;
+    while (P < nb) P <<= 1;
+    unsigned long long* key = skey;
+    unsigned int* idx = sidx;
+    if (P > kSmemSort32) {
+      key = I.births[sp].skey;
+      idx = I.births[sp].sidx;
+    }
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+      key[i] = i < nb ? I.births[sp].pkey[i] : ~0ULL;
+      idx[i] = (unsigned int)i;
+    }
+    __syncthreads();
+    bitonic(key, idx, P);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+      const unsigned long long id = (unsigned long long)(base + i);
+      uint4* rec = I.births[sp].b32 + idx[i];
+      reinterpret_cast<unsigned int*>(rec)[2] = (unsigned int)(id & 0xffffffffULL);
+      reinterpret_cast<unsigned int*>(rec)[3] = (unsigned int)(id >> 32);
+    }
+    __syncthreads();
+    base += nb;
+  }
+  if (threadIdx.x == 0) S->next_id = base;
+}
+
+__global__ void k_scatter32(Inst I, int sp0) {
+  Scalars* S = I.S;
+  if (S->status & ST_FATAL) return;
+  const int sp = sp0 + blockIdx.y;
+  const long long n_old = S->n[sp];
+  const long long nb = S->nbirth[sp] < I.birth_cap ? S->nbirth[sp] : I.birth_cap;
+  const long long total = n_old + nb;
+  const Particles32 src = I.cur32[sp], dst = I.nxt32[sp];
+  const BirthsDev B = I.births[sp];
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = warp * 32; base < total; base += nwarp * 32) {
+    const long long i = base + lane;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint4 b = make_uint4(0u, 0xffffffffu, 0u, 0u);
+    if (i < n_old) {
+      a = src.a[i];
+      b = src.b[i];
+    } else if (i < total) {
+      a = B.a32[i - n_old];
+      b = B.b32[i - n_old];
+    }
+    const int key = (int)b.y;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(peers) - 1;
+    int pos0 = 0;
+    if (lane == leader && key >= 0) pos0 = atomicAdd(&I.cursor[sp][key], __popc(peers));
+    pos0 = __shfl_sync(0xffffffffu, pos0, leader);
+    if (key >= 0) {
+      const int pos = pos0 + __popc(peers & ((1u << lane) - 1u));
+      dst.a[pos] = a;
+      dst.b[pos] = b;
+    }
+  }
+}
+
+// FP64 SoA (r, z, v, id) -> FP32 records at [offset, offset + count) of cur32,
+// keys counted; out-of-domain input removed and flagged
+__global__ void k_pack32(Inst I, int sp, long long offset, long long count, const double* r,
+                         const double* z, const double* vr, const double* vt, const double* vz,
+                         const long long* id) {
+  Scalars* S = I.S;
+  const Particles32 P = I.cur32[sp];
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+  long long idmax = -1;
+  bool bad = false;
+  for (long long base = warp * 32; base < count; base += nwarp * 32) {
+    const long long k = base + lane;
+    int key = -1;
+    if (k < count) {
+      const double rr = r[k], zz = z[k];
+      const long long pid = id[k];
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+      uint4 b = make_uint4(0u, 0xffffffffu, 0u, 0u);
+      if (rr >= 0.0 && rr < I.R && zz >= 0.0 && zz < I.L && finite64(vr[k]) && finite64(vt[k]) &&
+          finite64(vz[k]) && pid >= 0) {
+        int m, nn;
+        double fr, fz;
+        locate(rr, I.inv_dr, I.nr, m, fr);
+        locate(zz, I.inv_dz, I.nz, nn, fz);
+        float dr = (float)fr, dz = (float)fz;
+        if (dr >= 1.0f) dr = nextafterf(1.0f, 0.0f);
+        if (dz >= 1.0f) dz = nextafterf(1.0f, 0.0f);
+        key = cell_key(I, m, nn);
+        a = make_float4(dr, dz, (float)vr[k], (float)vt[k]);
+        b = make_uint4(__float_as_uint((float)vz[k]), (unsigned)key,
+                       (unsigned)((unsigned long long)pid & 0xffffffffULL),
+                       (unsigned)((unsigned long long)pid >> 32));
+        idmax = pid > idmax ? pid : idmax;
+      } else {
+        bad = true;
+      }
+      P.a[offset + k] = a;
+      P.b[offset + k] = b;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&I.counts[sp][key], __popc(peers));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long other = __shfl_xor_sync(0xffffffffu, idmax, o);
+    idmax = other > idmax ? other : idmax;
+  }
+  if (lane == 0 && idmax >= 0) atomicMax(&S->next_id, idmax + 1);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&S->status, ST_NAN);
+}
+
+// FP32 records [offset, offset + count) of cur32 -> FP64 SoA
+__global__ void k_unpack32(Inst I, int sp, long long offset, long long count, double* r, double* z,
+                           double* vr, double* vt, double* vz, long long* id) {
+  const Particles32 P = I.cur32[sp];
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < count;
+       k += (long long)gridDim.x * blockDim.x) {
+    const float4 a = P.a[offset + k];
+    const uint4 b = P.b[offset + k];
+    int m, nn;
+    key_to_mn(I, (int)b.y, m, nn);
+    if (r) r[k] = ((double)m + (double)a.x) * I.dr;
+    if (z) z[k] = ((double)nn + (double)a.y) * I.dz;
+    if (vr) vr[k] = (double)a.z;
+    if (vt) vt[k] = (double)a.w;
+    if (vz) vz[k] = (double)__uint_as_float(b.x);
+    if (id) id[k] = id_of(b);
+  }
+}
+
+__global__ void k_deposit_all32(Inst I, int sp) {
+  const long long n = I.S->n[sp];
+  const Particles32 P = I.cur32[sp];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float4 a = P.a[i];
+    int m, nn;
+    key_to_mn(I, (int)P.b[i].y, m, nn);
+    deposit_global32(I, sp, m, nn, rweight_upper32(I, a.x, m), a.y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static int grid32(long long work, int threads, int num_sms, int per_sm) {
+  long long g = (work + threads - 1) / threads;
+  const long long cap = (long long)num_sms * per_sm;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+cudaError_t launch_pack32(const Inst& I, int sp, long long offset, long long count, const double* r,
+                          const double* z, const double* vr, const double* vt, const double* vz,
+                          const long long* id, int num_sms, cudaStream_t st) {
+  k_pack32<<<grid32(count, 256, num_sms, 8), 256, 0, st>>>(I, sp, offset, count, r, z, vr, vt, vz,
+                                                             id);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack32(const Inst& I, int sp, long long offset, long long count, double* r,
+                            double* z, double* vr, double* vt, double* vz, long long* id,
+                            int num_sms, cudaStream_t st) {
+  k_unpack32<<<grid32(count, 256, num_sms, 8), 256, 0, st>>>(I, sp, offset, count, r, z, vr, vt, vz,
+                                                               id);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort_species32(const Inst& I, int sp, int num_sms, cudaStream_t st) {
+  launch_scan(I, sp, 1, st);
+  k_scatter32<<<dim3(grid32(I.cap[sp], 256, num_sms, 8), 1), 256, 0, st>>>(I, sp);
+  return launch_commit_n(I, sp, st);
+}
+
+cudaError_t launch_deposit_all32(const Inst& I, int num_sms, cudaStream_t st) {
+  for (int sp = 0; sp < 2; ++sp)
+    k_deposit_all32<<<grid32(I.cap[sp], 256, num_sms, 8), 256, 0, st>>>(I, sp);
+  return cudaGetLastError();
+}
+
+// one wave of the persistent push: resident blocks per SM x SMs (cached per kernel)
+template <typename K>
+static int one_wave(K kernel, int num_sms) {
+  static int per = 0;
+  if (per == 0) {
+    int p = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kernel, kPush32Threads, 0) != cudaSuccess ||
+        p < 1)
+      p = 1;
+    per = p;
+  }
+  return per * num_sms;
+}
+
+cudaError_t launch_push32(const Inst& I, int sp, int num_sms, cudaStream_t st) {
+  if (sp == 0) {
+    if (I.gather == 0) k_push32<0, 0><<<one_wave(k_push32<0, 0>, num_sms), kPush32Threads, 0, st>>>(I);
+    else k_push32<0, 1><<<one_wave(k_push32<0, 1>, num_sms), kPush32Threads, 0, st>>>(I);
+  } else {
+    if (I.gather == 0) k_push32<1, 0><<<one_wave(k_push32<1, 0>, num_sms), kPush32Threads, 0, st>>>(I);
+    else k_push32<1, 1><<<one_wave(k_push32<1, 1>, num_sms), kPush32Threads, 0, st>>>(I);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_births32(const Inst& I, cudaStream_t st) {
+  k_births32<<<1, 1024, 0, st>>>(I);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter32(const Inst& I, int num_sms, cudaStream_t st) {
+  k_scatter32<<<dim3(num_sms * 8, 2), 256, 0, st>>>(I, 0);
+  return cudaGetLastError();
+}
+
+}  // namespace pic

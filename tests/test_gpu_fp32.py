@@ -1,0 +1,169 @@
+"""GPU parity of the FP32 particle mode against the FP64 oracle.
+
+Bar (FP32 mode): positions and velocities within ||a - b||_inf / ||b||_inf <=
+1e-5 per species, phi and Q within 1e-5.  A discrete decision taken in FP32
+(a collision process chosen by U nu_max against cumulative frequencies, a wall
+crossing) can fall on the other side of a threshold than in FP64; such
+particles are counted as flips and excluded from the norms, and at most
+ceil(1e-5 N) of them are allowed.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import pic_inputs
+from parity import busy_state, field_err, sort_by_id
+
+pytestmark = pytest.mark.gpu
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def pg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2507_10727_gb300 as pg
+    return pg
+
+
+def compare32(a: dict, b: dict):
+    """GPU FP32 particles `a` vs oracle FP64 particles `b` (dicts of arrays)."""
+    ia, ib = set(a["id"].tolist()), set(b["id"].tolist())
+    flips = len(ia ^ ib)
+    common = np.array(sorted(ia & ib), dtype=np.int64)
+    a, b = sort_by_id(a), sort_by_id(b)
+    sa = np.isin(a["id"], common)
+    sb = np.isin(b["id"], common)
+    A = {k: v[sa] for k, v in a.items()}
+    B = {k: v[sb] for k, v in b.items()}
+    va = np.stack([A["vr"], A["vt"], A["vz"]])
+    vb = np.stack([B["vr"], B["vt"], B["vz"]])
+    vmax = max(np.abs(vb).max(), 1e-300) if vb.size else 1.0
+    # a particle whose velocity differs grossly took another collision branch
+    branch = np.abs(va - vb).max(axis=0) > 1e-3 * vmax
+    flips += int(branch.sum())
+    keep = ~branch
+    if keep.sum() == 0:
+        return {"pos": 0.0, "vel": 0.0}, flips
+    pa, pb = np.stack([A["r"], A["z"]])[:, keep], np.stack([B["r"], B["z"]])[:, keep]
+    return ({"pos": float(np.abs(pa - pb).max() / np.abs(pb).max()),
+             "vel": float(np.abs(va[:, keep] - vb[:, keep]).max() / vmax)}, flips)
+
+
+def _pair32(pg, p, parts):
+    p = pic_inputs.with_capacity(p, parts, factor=2.0)
+    orc = oracle.Oracle(p, parts)
+    h = pg.pic_create(dict(p, precision=1))
+    for k, sp in (("e", 0), ("i", 1)):
+        pg.pic_set_particles(h, 0, sp, parts[k])
+    pg.pic_set_phi(h, 0, orc.fields()["phi"])
+    return p, orc, h
+
+
+def _check(pg, h, orc):
+    n_total = 0
+    flips_total = 0
+    for sp in (0, 1):
+        a, b = pg.pic_get_particles(h, 0, sp), orc.get_particles(sp)
+        err, flips = compare32(a, b)
+        n_total += b["id"].shape[0]
+        flips_total += flips
+        assert err["pos"] <= TOL32 and err["vel"] <= TOL32, (sp, err)
+    assert flips_total <= math.ceil(1e-5 * n_total), flips_total
+    fg, fo = pg.pic_get_fields(h, 0), orc.fields()
+    assert field_err(fg["Q"], fo["Q"]) <= TOL32
+    assert field_err(fg["phi"], fo["phi"]) <= TOL32
+    return flips_total
+
+
+@pytest.mark.parametrize("gather", [0, 1])
+@pytest.mark.parametrize("rweight", [0, 1])
+def test_fp32_one_step_busy_state(pg, gather, rweight):
+    p = pic_inputs.params_rz32(gather=gather)
+    p.update(rweight=rweight, gamma_i=0.5, gamma_e=0.3, poisson_tol=1e-12, circuit_mode=1,
+             Vs=400.0, Rext=100.0, n_avg=3)
+    p, parts = busy_state(p, ppc=16, seed=31 + gather + 2 * rweight)
+    p, orc, h = _pair32(pg, p, parts)
+    orc.step(1)
+    pg.pic_step(h, 1)
+    flips = _check(pg, h, orc)
+    d, do = pg.pic_diagnostics(h, 0), orc.diag()
+    if flips == 0:
+        for key in ("N_e", "N_i", "n_ion_cath", "n_e_cath", "n_sey", "n_ionize", "n_excite",
+                    "n_elastic"):
+            assert d[key] == do[key], key
+    assert d["n_ionize"] > 0 and d["n_sey"] > 0
+
+
+def test_fp32_several_steps(pg):
+    p = pic_inputs.params_rz32(gather=0)
+    p.update(poisson_tol=1e-12, circuit_mode=1, Vs=400.0, Rext=2000.0, n_avg=4, gamma_i=0.2)
+    p, parts = pic_inputs.seed_plasma(p, 32 * 32 * 8, seed=5, Te_eV=5.0)
+    p, orc, h = _pair32(pg, p, parts)
+    for _ in range(6):
+        orc.step(1)
+        pg.pic_step(h, 1)
+    _check(pg, h, orc)
+
+
+def test_fp32_set_get_roundtrip(pg):
+    p = pic_inputs.params_rz32()
+    p, parts = pic_inputs.seed_plasma(p, 50000, seed=9)
+    p = pic_inputs.with_capacity(p, parts)
+    h = pg.pic_create(dict(p, precision=1))
+    pg.pic_set_particles(h, 0, 0, parts["e"])
+    got = sort_by_id(pg.pic_get_particles(h, 0, 0))
+    ref = sort_by_id(parts["e"])
+    assert np.array_equal(got["id"], ref["id"])
+    dr = p["R"] / p["nr"]
+    assert np.abs(got["r"] - ref["r"]).max() <= 2.0 ** -23 * dr
+    assert np.abs(got["z"] - ref["z"]).max() <= 2.0 ** -23 * p["L"] / p["nz"]
+    for k in ("vr", "vt", "vz"):
+        np.testing.assert_allclose(got[k], ref[k], rtol=2.0 ** -23)
+
+
+def test_fp32_checkpoint_resume(pg, tmp_path):
+    p = pic_inputs.params_rz32()
+    p.update(circuit_mode=1, Vs=400.0, Rext=500.0, gamma_i=0.3, precision=1)
+    p, parts = busy_state(p, ppc=8, seed=17)
+    p = pic_inputs.with_capacity(p, parts, factor=2.0)
+    h = pg.pic_create(p)
+    for k, sp in (("e", 0), ("i", 1)):
+        pg.pic_set_particles(h, 0, sp, parts[k])
+    pg.pic_solve_fields(h, 0)
+    pg.pic_step(h, 3)
+    pg.pic_save(h, 0, str(tmp_path / "ck32.bin"))
+    pg.pic_step(h, 3)
+    ref = [sort_by_id(pg.pic_get_particles(h, 0, sp)) for sp in (0, 1)]
+    h2 = pg.pic_create(p)
+    pg.pic_load(h2, 0, str(tmp_path / "ck32.bin"))
+    pg.pic_step(h2, 3)
+    for sp in (0, 1):
+        got = sort_by_id(pg.pic_get_particles(h2, 0, sp))
+        assert np.array_equal(got["id"], ref[sp]["id"])
+        for k in ("r", "z", "vr", "vt", "vz"):
+            scale = np.abs(ref[sp][k]).max()
+            assert np.abs(got[k] - ref[sp][k]).max() <= 1e-5 * scale, (sp, k)
+    assert pg.pic_diagnostics(h2, 0)["step"] == pg.pic_diagnostics(h, 0)["step"]
+
+
+def test_fp32_diagnostics_vs_fp64_oracle(pg):
+    """Diagnostics of 20 FP32 steps against the FP64 oracle from the same
+    state; the errors are printed (they are quoted in the design notes)."""
+    p = pic_inputs.params_rz32(gather=0)
+    p.update(poisson_tol=1e-12, circuit_mode=1, Vs=400.0, Rext=200.0, n_avg=5)
+    p, parts = pic_inputs.seed_plasma(p, 32 * 32 * 16, seed=23, Te_eV=3.0)
+    p, orc, h = _pair32(pg, p, parts)
+    errs = {k: 0.0 for k in ("I_cath", "V_cath", "n_e_peak", "n_i_peak", "W_field", "K_e", "K_i")}
+    for _ in range(20):
+        orc.step(1)
+        pg.pic_step(h, 1)
+        d, do = pg.pic_diagnostics(h, 0), orc.diag()
+        for k in errs:
+            den = max(abs(do[k]), 1e-30)
+            errs[k] = max(errs[k], abs(d[k] - do[k]) / den)
+    print("FP32 diagnostics, max relative error over 20 steps:", errs)
+    for k, v in errs.items():
+        assert v <= 1e-4, (k, v)
