@@ -45,6 +45,8 @@ FLOPS_PER_PARTICLE = {0: 78.0, 1: 86.0}   # EC, MC
 # Algorithmic HBM bytes of one particle-step: read and write r, z, v_r,
 # v_theta, v_z, id once (FP64).
 BYTES_PER_PARTICLE = 96.0
+# FP32 mode: read and write the two 16-byte records of a particle once.
+BYTES_PER_PARTICLE_FP32 = 64.0
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA pipes-lanes per SM per clock x 2
 # flop x 2.07 GHz = 1.26 TFLOP/s (nominal 1.25); scaled to the measured clock.
 FP64_FLOP_PER_CLK = 152 * 2 * 2
@@ -58,12 +60,17 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--n-per-species", type=float, default=4e7)
     ap.add_argument("--gather", default="ec", choices=["ec", "mc"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+                    help="particle arithmetic: fp64 (plain method) or fp32 (precision mode)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=float, default=8e6,
                     help="oracle sample size per species for the CPU baseline")
     ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--workload", default="rz256", choices=["rz256", "sweep16"],
+                    help="rz256: one 256x256 discharge; sweep16: the 16-discharge "
+                         "SEY x R_ext ensemble on 128x128 grids")
     return ap.parse_args()
 
 
@@ -74,14 +81,15 @@ def workload(args):
     p, parts = pic_inputs.grown_ring_state(p, n, seed=args.seed)
     p = pic_inputs.with_capacity(p, parts, factor=1.25, births=1 << 20)
     p["diag_every"] = 10      # diagnostics reduction every 10 steps
+    p["precision"] = 1 if args.precision == "fp32" else 0
     return p, parts
 
 
 def config_block(p, n, args):
-    return {"workload": f"rz256_ring_{n:.0e}_per_species".replace("+", ""),
+    return {"workload": f"rz256_ring_{n:.0e}_per_species_{args.precision}".replace("+", ""),
             "grid": [p["nr"], p["nz"]], "domain_m": [p["R"], p["L"]],
             "n_per_species": n, "gather": args.gather.upper() + "-PIC",
-            "precision": "fp64", "circuit": {"Vs": p["Vs"], "Rext": p["Rext"]},
+            "precision": args.precision, "circuit": {"Vs": p["Vs"], "Rext": p["Rext"]},
             "dt": p["dt"], "poisson_tol": p["poisson_tol"], "diag_every": p["diag_every"],
             "l2": "inputs larger than L2 (particle state 3.8 GB >> 129 MB)"}
 
@@ -202,6 +210,90 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+# ensemble workload: 16 discharges (gamma x R_ext sweep), uneven loads
+# ---------------------------------------------------------------------------
+def sweep_workload(args):
+    g = 0 if args.gather == "ec" else 1
+    plist = pic_inputs.params_rz128_sweep(gather=g, seed=args.seed)
+    rng = np.random.default_rng(args.seed + 5)
+    sizes = [int(1e6 * 8.0 ** (k / 15.0)) for k in range(16)]
+    rng.shuffle(sizes)
+    out = []
+    for k, p in enumerate(plist):
+        p, parts = pic_inputs.grown_ring_state(p, sizes[k], seed=args.seed + 31 * k)
+        p = pic_inputs.with_capacity(p, parts, factor=1.25, births=1 << 18)
+        p["diag_every"] = 10
+        p["precision"] = 1 if args.precision == "fp32" else 0
+        out.append((p, parts))
+    return out
+
+
+def run_sweep(args, torch, pg):
+    insts = sweep_workload(args)
+    ntot = sum(2 * parts["e"]["r"].shape[0] for _, parts in insts)
+    warm = max(args.warmup, 5)           # includes the 4 autotuning steps
+
+    def load(h, k, parts):
+        for key, sp in (("e", 0), ("i", 1)):
+            pg.pic_set_particles(h, k, sp, parts[key])
+        pg.pic_solve_fields(h, k)
+
+    def timed(h_list, steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ps0 = sum(pg.pic_diagnostics(h, k)["particle_steps"] for h, k in h_list)
+        torch.cuda.synchronize()
+        ev0.record()
+        for h in dict.fromkeys(h for h, _ in h_list):
+            pg.pic_step(h, steps)
+        ev1.record()
+        torch.cuda.synchronize()
+        ps1 = sum(pg.pic_diagnostics(h, k)["particle_steps"] for h, k in h_list)
+        return ev0.elapsed_time(ev1), ps1 - ps0
+
+    ens = pg.pic_create([p for p, _ in insts])
+    for k, (_, parts) in enumerate(insts):
+        load(ens, k, parts)
+    pg.pic_step(ens, warm)
+    pg.pic_sync(ens)
+    ms_e, ps_e = timed([(ens, k) for k in range(len(insts))], args.steps)
+    pg.pic_profile(ens, True)
+    pg.pic_step(ens, min(args.steps, 5))
+    prof = pg.pic_profile_read(ens)
+    pg.pic_profile(ens, False)
+    nprof = max(1, prof["push_e"]["launches"])
+    tuned = pg.pic_tuned_chunk(ens)
+    graph = pg.pic_uses_graph(ens)
+    pg.pic_destroy(ens)
+    # the same 16 discharges as 16 sequential single-discharge runs
+    singles = []
+    for p, parts in insts:
+        h = pg.pic_create(p)
+        load(h, 0, parts)
+        pg.pic_step(h, args.warmup)
+        singles.append(h)
+    pg.pic_sync(singles[0])
+    ms_s, ps_s = timed([(h, 0) for h in singles], args.steps)
+    for h in singles:
+        pg.pic_destroy(h)
+    value = ps_e / (ms_e / 1e3)
+    seq = ps_s / (ms_s / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": warm, "ms_per_step": ms_e / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+            "config": {"workload": f"sweep16_rz128_{args.precision}",
+                       "instances": len(insts), "grid": [128, 128], "domain_m": [0.05, 0.05],
+                       "particles_per_species": [parts["e"]["r"].shape[0] for _, parts in insts],
+                       "total_particles": ntot,
+                       "gamma_x_Rext": [[p["gamma_i"], p["Rext"]] for p, _ in insts],
+                       "l2": "inputs larger than L2"},
+            "sequential_16_value": seq, "ensemble_over_sequential": value / seq,
+            "autotuned_particles_per_thread": tuned, "cuda_graph": graph,
+            "per_kernel_ms_per_step": {k: v["total_ms"] / nprof for k, v in prof.items()}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def main():
@@ -228,6 +320,12 @@ def main():
         __graft_entry__.build()
     barrier()
     import paper_2507_10727_gb300 as pg
+
+    # a side stream: pic_step captures one step into a CUDA graph and replays it
+    side = torch.cuda.Stream()
+    torch.cuda.set_stream(side)
+    if args.workload == "sweep16":
+        return run_sweep(args, torch, pg)
 
     p, parts = workload(args)
     n = int(args.n_per_species)
@@ -283,16 +381,26 @@ def main():
     g = 0 if args.gather == "ec" else 1
     achieved = FLOPS_PER_PARTICLE[g] * dom_n / (dom_ms / 1e3) / 1e12
     achieved_bw = BYTES_PER_PARTICLE * dom_n / (dom_ms / 1e3) / 1e9
-    roofline = {"bound": "alu", "kernel": f"k_push ({dom})", "achieved": achieved,
-                "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                "traffic": None,
-                "peak_note": f"FP64 pipes: 152 SMs x 4 flop/clk at the median loaded SM clock "
-                             f"{sm_mhz:.0f} MHz (1.25 TFLOP/s nominal at 2.07 GHz)",
-                "hbm_view": {"achieved_gbs": achieved_bw, "peak_gbs": peaks.get("hbm_gbs"),
-                             "frac": achieved_bw / peaks.get("hbm_gbs", 6800.0),
-                             "peak_kind": peak_kind, "bytes_per_particle": BYTES_PER_PARTICLE},
-                "flops_per_particle": FLOPS_PER_PARTICLE[g],
-                "per_kernel_ms_per_step": {k: v["total_ms"] / prof_steps for k, v in prof.items()}}
+    per_kernel = {k: v["total_ms"] / prof_steps for k, v in prof.items()}
+    if args.precision == "fp64":
+        roofline = {"bound": "alu", "kernel": f"k_push ({dom})", "achieved": achieved,
+                    "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                    "traffic": None,
+                    "peak_note": f"FP64 pipes: 152 SMs x 4 flop/clk at the median loaded SM "
+                                 f"clock {sm_mhz:.0f} MHz (1.25 TFLOP/s nominal at 2.07 GHz)",
+                    "hbm_view": {"achieved_gbs": achieved_bw, "peak_gbs": peaks.get("hbm_gbs"),
+                                 "frac": achieved_bw / peaks.get("hbm_gbs", 6800.0),
+                                 "peak_kind": peak_kind,
+                                 "bytes_per_particle": BYTES_PER_PARTICLE},
+                    "flops_per_particle": FLOPS_PER_PARTICLE[g],
+                    "per_kernel_ms_per_step": per_kernel}
+    else:
+        bw32 = BYTES_PER_PARTICLE_FP32 * dom_n / (dom_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": f"k_push32 ({dom})", "achieved": bw32,
+                    "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                    "frac": bw32 / peaks.get("hbm_gbs", 6800.0), "traffic": None,
+                    "peak_kind": peak_kind, "bytes_per_particle": BYTES_PER_PARTICLE_FP32,
+                    "per_kernel_ms_per_step": per_kernel}
 
     # end to end through the C ABI with host buffers: upload the state from
     # pinned host memory, then each step pic_step + a diagnostics read-back
@@ -337,12 +445,12 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": config_block(p, n, args),
-                "gpu_launches": args.steps * 10,
+                "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+                "data": "synthetic", "config": config_block(p, n, args),
+                "gpu_launches": args.steps * 10, "cuda_graph": pg.pic_uses_graph(h),
                 "poisson": {"iters_last_step": d1["poisson_iters"],
                             "resid_last_step": d1["poisson_resid"],
-                            "ms_per_step": roofline["per_kernel_ms_per_step"]["poisson"]},
+                            "ms_per_step": per_kernel["poisson"]},
                 "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     pg.pic_destroy(h)

@@ -126,7 +126,8 @@ typedef struct pic_diag {
 
 typedef struct pic_handle pic_handle;
 
-/* Create a handle for n_instances discharges (cfgs[0..n_instances-1]).
+/* Create a handle for n_instances discharges (cfgs[0..n_instances-1]; at most
+ * 64, all with the same gather and precision).
  * Allocates all device state, builds the static B table on the host in FP64
  * and uploads it.  Particles start empty (pic_set_particles); phi starts at
  * zero.  cuda_stream: cudaStream_t of all later work.  Returns PIC_OK and
@@ -177,8 +178,22 @@ int pic_set_circuit(pic_handle* h, int instance, double Vc, int64_t step, const 
 int pic_set_next_id(pic_handle* h, int instance, int64_t next_id);
 int pic_get_next_id(pic_handle* h, int instance, int64_t* next_id);
 
-/* Advance all instances by nsteps time steps.  Async (see conventions). */
+/* Advance all instances by nsteps time steps.  Async (see conventions).
+ * On a stream other than the legacy default stream the first call captures
+ * one step of all instances into a CUDA graph and later steps replay it
+ * (eager launches while pic_profile is on, or if capture is unavailable). */
 int pic_step(pic_handle* h, int64_t nsteps);
+
+/* 1 when pic_step replays a captured CUDA graph on this handle, else 0. */
+int pic_uses_graph(pic_handle* h);
+
+/* Ensembles (n_instances > 1): the particle pushes of all instances run as
+ * persistent kernels over a device queue of (instance, chunk) work items, the
+ * Poisson solves of all instances in one grouped launch.  The first four
+ * steps of a handle each try one chunk size (2, 4, 8, 16 particles per
+ * thread) and the fastest is kept: *particles_per_thread receives it, or 0
+ * while tuning is unfinished (single-instance handles: the fixed size). */
+int pic_tuned_chunk(pic_handle* h, int* particles_per_thread);
 
 /* Wait for the handle's stream; return the latched status of all instances. */
 int pic_sync(pic_handle* h);

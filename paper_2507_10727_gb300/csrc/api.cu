@@ -37,6 +37,16 @@ struct Profiler {
 struct pic_handle {
   std::vector<InstHost> inst;
   Profiler prof;
+  cudaGraphExec_t graph = nullptr;   // one step of every instance, captured once
+  bool graph_failed = false;
+  // ensemble (n_instances > 1): batched push over a work queue, grouped Poisson
+  Inst* d_insts = nullptr;
+  WorkQueue* d_queue = nullptr;
+  void* d_pargs = nullptr;
+  std::vector<PoissonWork*> pws;
+  int ppt = 8;                       // particles per thread per work item (autotuned)
+  int tune_next = 0;                 // next autotuner candidate; -1 = done
+  float tune_ms[4] = {0, 0, 0, 0};
   pic_alloc alloc;
   bool own_alloc = true;
   cudaStream_t stream = nullptr;
@@ -193,13 +203,13 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
   for (int sp = 0; sp < 2; ++sp) {
     const size_t cap = (size_t)I.cap[sp];
     if (p32) {
-      for (Particles32* P : {&I.cur32[sp], &I.nxt32[sp]}) {
+      for (Particles32* P : {&I.buf32[sp][0], &I.buf32[sp][1]}) {
         P->a = (float4*)chk(A(cap * 16));
         P->b = (uint4*)chk(A(cap * 16));
       }
       I.qacc64[sp] = (double*)chk(A(nn * 8));
     } else {
-      for (ParticlesDev* P : {&I.cur[sp], &I.nxt[sp]}) {
+      for (ParticlesDev* P : {&I.buf[sp][0], &I.buf[sp][1]}) {
         P->r = (double*)chk(A(cap * 8));
         P->z = (double*)chk(A(cap * 8));
         P->vr = (double*)chk(A(cap * 8));
@@ -346,9 +356,11 @@ void prof_mark(void* ctx, int group, bool begin, cudaStream_t st) {
   else P.recs.push_back({group, P.open[group], ev});
 }
 
-void swap_buffers(InstHost& ih, int sp) {
-  std::swap(ih.I.cur[sp], ih.I.nxt[sp]);
-  std::swap(ih.I.cur32[sp], ih.I.nxt32[sp]);
+// index of the current particle buffer of a species (device-side parity)
+int current_buffer(pic_handle* h, int instance, int sp) {
+  Scalars s;
+  read_status(h, instance, &s);
+  return s.flip[sp] & 1;
 }
 
 }  // namespace
@@ -375,12 +387,43 @@ int pic_create(const pic_config* cfgs, int n_instances, const pic_alloc* alloc, 
     delete h;
     return PIC_ERR_CUDA;
   }
+  if (n_instances > kMaxInstances) {
+    delete h;
+    return PIC_ERR_INVALID;
+  }
+  for (int k = 1; k < n_instances; ++k)
+    if (cfgs[k].gather != cfgs[0].gather || cfgs[k].precision != cfgs[0].precision) {
+      delete h;
+      return PIC_ERR_INVALID;   // one kernel variant serves all instances of a handle
+    }
   h->inst.resize(n_instances);
   for (int k = 0; k < n_instances; ++k) {
     const int rc = build_instance(h, cfgs[k], h->inst[k]);
     if (rc != PIC_OK) {
       pic_destroy(h);
       return rc;
+    }
+  }
+  if (n_instances > 1) {
+    h->d_insts = (Inst*)dev_alloc(h, sizeof(Inst) * n_instances);
+    h->d_queue = (WorkQueue*)dev_alloc(h, sizeof(WorkQueue));
+    h->d_pargs = dev_alloc(h, poisson_args_bytes() * n_instances);
+    if (!h->d_insts || !h->d_queue || !h->d_pargs) {
+      pic_destroy(h);
+      return PIC_ERR_OOM;
+    }
+    std::vector<Inst> hi(n_instances);
+    for (int k = 0; k < n_instances; ++k) {
+      hi[k] = h->inst[k].I;
+      h->pws.push_back(h->inst[k].pw);
+    }
+    cudaError_t e = cudaMemcpyAsync(h->d_insts, hi.data(), sizeof(Inst) * n_instances,
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_queue, 0, sizeof(WorkQueue), h->stream);
+    if (e == cudaSuccess) e = poisson_group_upload(h->pws.data(), hi.data(), n_instances, h->d_pargs, h->stream);
+    if (e != cudaSuccess) {
+      pic_destroy(h);
+      return PIC_ERR_CUDA;
     }
   }
   *out = h;
@@ -390,6 +433,7 @@ int pic_create(const pic_config* cfgs, int n_instances, const pic_alloc* alloc, 
 void pic_destroy(pic_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
   for (cudaEvent_t ev : h->prof.pool) cudaEventDestroy(ev);
   for (InstHost& ih : h->inst)
     if (ih.pw) poisson_work_free(ih.pw);
@@ -439,7 +483,7 @@ int pic_set_particles(pic_handle* h, int instance, int species, int64_t n, const
     if (e == cudaSuccess) e = launch_sort_species32(ih.I, species, h->num_sms, st);
   } else {
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    const ParticlesDev& P = ih.I.cur[species];
+    const ParticlesDev& P = ih.I.buf[species][current_buffer(h, instance, species)];
     const size_t b = (size_t)n * 8;
     if (n > 0) {
       e = cudaMemcpyAsync(P.r, r, b, kind, st);
@@ -453,7 +497,6 @@ int pic_set_particles(pic_handle* h, int instance, int species, int64_t n, const
     if (e == cudaSuccess) e = launch_sort_species(ih.I, species, h->num_sms, st);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "set_particles");
-  swap_buffers(ih, species);
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(h, e, "set_particles sync");
   return read_status(h, instance, nullptr);
@@ -498,7 +541,7 @@ int pic_get_particles(pic_handle* h, int instance, int species, double* r, doubl
       }
     }
   } else {
-    const ParticlesDev& P = I.cur[species];
+    const ParticlesDev& P = I.buf[species][current_buffer(h, instance, species)];
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     const size_t b = (size_t)n * 8;
     if (n > 0) {
@@ -613,20 +656,147 @@ int pic_get_next_id(pic_handle* h, int instance, int64_t* next_id) {
   return rc;
 }
 
-int pic_step(pic_handle* h, int64_t nsteps) {
-  if (!h || nsteps < 0) return fail(h, PIC_ERR_INVALID, "bad argument");
-  StepMarks marks{prof_mark, &h->prof};
-  for (int64_t s = 0; s < nsteps; ++s) {
-    for (InstHost& ih : h->inst) {
-      cudaError_t e = launch_step(ih.I, ih.pw, h->num_sms, h->stream,
-                                  h->prof.on ? &marks : nullptr);
-      if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
-      swap_buffers(ih, 0);
-      swap_buffers(ih, 1);
-    }
+// One step of an ensemble: field tables per instance, both species pushed by
+// persistent CTAs over a queue of (instance, chunk) items, the rest of the
+// particle step per instance, all Poisson solves in one grouped launch.
+static const int kTuneCandidates[4] = {2, 4, 8, 16};
+
+static cudaError_t launch_ensemble_step(pic_handle* h, const StepMarks* marks) {
+  auto mk = [&](int g, bool b) {
+    if (marks) marks->mark(marks->ctx, g, b, h->stream);
+  };
+  const int n = (int)h->inst.size();
+  const Inst& I0 = h->inst[0].I;
+  cudaStream_t st = h->stream;
+  cudaError_t e = cudaSuccess;
+  mk(G_FIELD, true);
+  for (InstHost& ih : h->inst)
+    if (e == cudaSuccess) e = launch_field_tables(ih.I, h->num_sms, st);
+  mk(G_FIELD, false);
+  const int threads = 256;
+  if (e == cudaSuccess) e = launch_queue_setup(h->d_insts, h->d_queue, n, (long long)h->ppt * threads, st);
+  for (int sp = 0; sp < 2 && e == cudaSuccess; ++sp) {
+    mk(sp == 0 ? G_PUSH_E : G_PUSH_I, true);
+    e = I0.prec32 ? launch_push32_batched(h->d_insts, h->d_queue, sp, I0.gather, h->ppt, h->num_sms, st)
+                  : launch_push64_batched(h->d_insts, h->d_queue, sp, I0.gather, h->ppt, h->num_sms, st);
+    mk(sp == 0 ? G_PUSH_E : G_PUSH_I, false);
+  }
+  mk(G_SCATTER, true);
+  for (InstHost& ih : h->inst)
+    if (e == cudaSuccess) e = launch_post_push(ih.I, h->num_sms, st);
+  mk(G_SCATTER, false);
+  mk(G_POISSON, true);
+  if (e == cudaSuccess) e = launch_poisson_group(h->pws.data(), nullptr, n, h->d_pargs, h->num_sms, st);
+  mk(G_POISSON, false);
+  mk(G_STEP_END, true);
+  for (InstHost& ih : h->inst)
+    if (e == cudaSuccess) e = launch_step_end(ih.I, st);
+  mk(G_STEP_END, false);
+  return e;
+}
+
+// Online autotuner of the ensemble push: the first steps of a handle run one
+// candidate chunk size each (timed with events around the two batched
+// pushes); the fastest is kept for the rest of the run.
+static int autotune_step(pic_handle* h) {
+  const int c = h->tune_next;
+  h->ppt = kTuneCandidates[c];
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  struct Ctx { cudaEvent_t a, b; } ctx{a, b};
+  StepMarks marks{[](void* p, int g, bool begin, cudaStream_t st) {
+                    Ctx* x = (Ctx*)p;
+                    if (g == G_PUSH_E && begin) cudaEventRecord(x->a, st);
+                    if (g == G_PUSH_I && !begin) cudaEventRecord(x->b, st);
+                  },
+                  &ctx};
+  const cudaError_t e = launch_ensemble_step(h, &marks);
+  float ms = 0.0f;
+  if (e == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e != cudaSuccess) return cuda_fail(h, e, "ensemble step");
+  h->tune_ms[c] = ms;
+  if (++h->tune_next == 4) {
+    int best = 0;
+    for (int k = 1; k < 4; ++k)
+      if (h->tune_ms[k] < h->tune_ms[best]) best = k;
+    h->ppt = kTuneCandidates[best];
+    h->tune_next = -1;
   }
   return PIC_OK;
 }
+
+static cudaError_t launch_all(pic_handle* h, const StepMarks* marks) {
+  if (h->inst.size() > 1) return launch_ensemble_step(h, marks);
+  cudaError_t e = cudaSuccess;
+  for (InstHost& ih : h->inst)
+    if (e == cudaSuccess) e = launch_step(ih.I, ih.pw, h->num_sms, h->stream, marks);
+  return e;
+}
+
+// Capture one time step of every instance into a CUDA graph.  Every step
+// launches the same kernels with the same arguments (buffer parity, counts and
+// the step index live on the device), so the graph is replayed as is.
+static void build_graph(pic_handle* h) {
+  cudaStreamCaptureStatus cs;
+  if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    h->graph_failed = true;
+    return;
+  }
+  if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    h->graph_failed = true;
+    return;
+  }
+  bool ok = launch_all(h, nullptr) == cudaSuccess;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  ok = ok && e == cudaSuccess && g != nullptr;
+  cudaGraphExec_t ex = nullptr;
+  if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  if (ok) h->graph = ex;
+  else h->graph_failed = true;
+}
+
+int pic_step(pic_handle* h, int64_t nsteps) {
+  if (!h || nsteps < 0) return fail(h, PIC_ERR_INVALID, "bad argument");
+  if (nsteps == 0) return PIC_OK;
+  // ensembles: the first steps tune the batched push's chunk size
+  while (h->inst.size() > 1 && h->tune_next >= 0 && nsteps > 0) {
+    const int rc = autotune_step(h);
+    if (rc != PIC_OK) return rc;
+    --nsteps;
+  }
+  if (nsteps == 0) return PIC_OK;
+  // graphs need a capturable stream; profiling needs the per-kernel events
+  const bool use_graph = !h->prof.on && h->stream != nullptr && !h->graph_failed;
+  if (use_graph && !h->graph) build_graph(h);
+  if (use_graph && h->graph) {
+    for (int64_t s = 0; s < nsteps; ++s) {
+      const cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+    }
+    return PIC_OK;
+  }
+  StepMarks marks{prof_mark, &h->prof};
+  for (int64_t s = 0; s < nsteps; ++s) {
+    const cudaError_t e = launch_all(h, h->prof.on ? &marks : nullptr);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
+  }
+  return PIC_OK;
+}
+
+int pic_tuned_chunk(pic_handle* h, int* particles_per_thread) {
+  if (!h || !particles_per_thread) return PIC_ERR_INVALID;
+  *particles_per_thread = h->tune_next < 0 || h->inst.size() == 1 ? h->ppt : 0;
+  return PIC_OK;
+}
+
+int pic_uses_graph(pic_handle* h) { return h && h->graph ? 1 : 0; }
 
 int pic_sync(pic_handle* h) {
   if (!h) return PIC_ERR_INVALID;
@@ -704,8 +874,8 @@ int pic_save(pic_handle* h, int instance, const char* path) {
       std::vector<float4> ra((size_t)n);
       std::vector<uint4> rb((size_t)n);
       if (ok && n > 0 &&
-          (cudaMemcpy(ra.data(), ih.I.cur32[sp].a, (size_t)n * 16, cudaMemcpyDeviceToHost) != cudaSuccess ||
-           cudaMemcpy(rb.data(), ih.I.cur32[sp].b, (size_t)n * 16, cudaMemcpyDeviceToHost) != cudaSuccess))
+          (cudaMemcpy(ra.data(), ih.I.buf32[sp][s.flip[sp] & 1].a, (size_t)n * 16, cudaMemcpyDeviceToHost) != cudaSuccess ||
+           cudaMemcpy(rb.data(), ih.I.buf32[sp][s.flip[sp] & 1].b, (size_t)n * 16, cudaMemcpyDeviceToHost) != cudaSuccess))
         ok = false;
       ok = ok && std::fwrite(ra.data(), 16, (size_t)n, f) == (size_t)n;
       ok = ok && std::fwrite(rb.data(), 16, (size_t)n, f) == (size_t)n;
@@ -713,7 +883,7 @@ int pic_save(pic_handle* h, int instance, const char* path) {
     }
     std::vector<double> buf((size_t)n);
     std::vector<long long> ids((size_t)n);
-    const ParticlesDev& P = ih.I.cur[sp];
+    const ParticlesDev& P = ih.I.buf[sp][s.flip[sp] & 1];
     for (double* src : {P.r, P.z, P.vr, P.vt, P.vz}) {
       if (!ok) break;
       if (n > 0 && cudaMemcpy(buf.data(), src, (size_t)n * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -773,10 +943,11 @@ int pic_load(pic_handle* h, int instance, const char* path) {
   for (int sp = 0; sp < 2; ++sp) {
     if (ih.I.prec32) {
       cudaError_t e0 = cudaSuccess;
+      const int fl = current_buffer(h, instance, sp);
       if (n[sp] > 0) {
-        e0 = cudaMemcpy(ih.I.cur32[sp].a, ra[sp].data(), (size_t)n[sp] * 16, cudaMemcpyHostToDevice);
+        e0 = cudaMemcpy(ih.I.buf32[sp][fl].a, ra[sp].data(), (size_t)n[sp] * 16, cudaMemcpyHostToDevice);
         if (e0 == cudaSuccess)
-          e0 = cudaMemcpy(ih.I.cur32[sp].b, rb[sp].data(), (size_t)n[sp] * 16, cudaMemcpyHostToDevice);
+          e0 = cudaMemcpy(ih.I.buf32[sp][fl].b, rb[sp].data(), (size_t)n[sp] * 16, cudaMemcpyHostToDevice);
       }
       if (e0 != cudaSuccess) return cuda_fail(h, e0, "load copy");
       continue;
@@ -790,6 +961,8 @@ int pic_load(pic_handle* h, int instance, const char* path) {
   read_status(h, instance, &cur);
   s.n[0] = ih.I.prec32 ? n[0] : cur.n[0];
   s.n[1] = ih.I.prec32 ? n[1] : cur.n[1];
+  s.flip[0] = cur.flip[0];   // the particles were placed in this handle's current buffers
+  s.flip[1] = cur.flip[1];
   cudaError_t e = cudaMemcpy(ih.I.S, &s, sizeof(s), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ih.I.qhist, qh.data(), qh.size() * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ih.I.phi, phi.data(), nn * 8, cudaMemcpyHostToDevice);

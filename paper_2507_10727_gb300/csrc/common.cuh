@@ -47,7 +47,8 @@ struct ParticlesDev {
 
 // FP32 particle mode: 32 bytes per particle in two 16-byte records,
 // a = {dr, dz, v_r, v_theta} (dr, dz: FP32 offsets in [0,1) inside the cell),
-// b = {v_z (bits), cell key, id low word, id high word}; key -1 = removed.
+// b = {v_z (bits), cell (m << 16 | n), id low word, id high word}; a cell
+// word of all ones marks a removed particle.
 struct Particles32 {
   float4* a;
   uint4* b;
@@ -85,6 +86,8 @@ struct Scalars {
   int pad0;
   double poisson_resid;
   long long pushed;        // cumulative particle-steps
+  int flip[2];             // which of the two particle buffers of a species is current
+  int pad1[2];
 };
 
 struct DiagDev {           // mirrors pic_diag
@@ -96,6 +99,16 @@ struct DiagDev {           // mirrors pic_diag
   int poisson_iters;
   int status;
   double poisson_resid;
+};
+
+// Work queue of the batched (ensemble) push: items are (instance, chunk)
+// pairs in instance-major order, prefix[sp][k] = first item of instance k.
+constexpr int kMaxInstances = 64;
+struct WorkQueue {
+  unsigned int next[2];
+  int n_inst;
+  int pad;
+  int prefix[2][kMaxInstances + 1];
 };
 
 // Everything a kernel needs about one instance; passed by value.
@@ -123,14 +136,14 @@ struct Inst {
   int prec32;
   float hq32[2];           // q dt / 2m per species
   float kr32, kz32;        // dt / dr, dt / dz
-  Particles32 cur32[2], nxt32[2];
+  Particles32 buf32[2][2];  // [species][buffer]; current = buf32[sp][S->flip[sp]]
   double* qacc64[2];       // FP32 mode: FP64 node sums of deposited macro-charges
   float4* etab32;          // FP32 gather tables (layout as etab / btab)
   float4* btab32;
   double* stage;           // FP64 staging of pic_set/get_particles in FP32 mode
   long long stage_len;     // particles per staging chunk
   // device arrays
-  ParticlesDev cur[2], nxt[2];
+  ParticlesDev buf[2][2];   // [species][buffer]; current = buf[sp][S->flip[sp]]
   int* key[2];
   int* counts[2];
   int* cursor[2];

@@ -48,6 +48,39 @@ static __device__ __forceinline__ void scatter_dir(const double e[3], double cos
   for (int j = 0; j < 3; ++j) out[j] = cos_chi * e[j] + sin_chi * (cp * u[j] + sp * w[j]);
 }
 
+// Contiguous-run reduction over the lanes of a warp: lanes with equal `key`
+// next to each other form a run; on return the last lane of every run holds
+// the run's sums of the four values (fixed order, so deterministic) and the
+// function returns true there.  All 32 lanes must call it.
+template <typename T>
+__device__ __forceinline__ bool run_sum4(int key, T& a, T& b, T& c, T& d) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int prev = __shfl_up_sync(full, key, 1);
+  const int next = __shfl_down_sync(full, key, 1);
+  const bool head = lane == 0 || prev != key;
+  const bool tail = lane == 31 || next != key;
+  if (__all_sync(full, head)) return tail;          // no two neighbours share a key
+  int start = head ? lane : 0;                        // first lane of this lane's run
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(full, start, o);
+    if (lane >= o && t > start) start = t;
+  }
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T ta = __shfl_up_sync(full, a, o), tb = __shfl_up_sync(full, b, o);
+    const T tc = __shfl_up_sync(full, c, o), td = __shfl_up_sync(full, d, o);
+    if (lane - o >= start) {
+      a += ta;
+      b += tb;
+      c += tc;
+      d += td;
+    }
+  }
+  return tail;
+}
+
 // Bitonic sort of P (a power of two) keys with their indices, one CTA.
 static __device__ void bitonic(unsigned long long* key, unsigned int* idx, int P) {
   for (int k = 2; k <= P; k <<= 1)

@@ -33,6 +33,24 @@ cudaError_t launch_set_n(const Inst& I, int sp, long long n, cudaStream_t st);
 // deposit the current particles, set the cathode values and solve phi
 cudaError_t launch_solve_fields(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_t st);
 
+// ensemble pieces: field tables, batched pushes over a work queue, the
+// per-instance rest of the step
+cudaError_t launch_field_tables(const Inst& I, int num_sms, cudaStream_t st);
+cudaError_t launch_queue_setup(const Inst* d_insts, WorkQueue* q, int n_inst, long long chunk,
+                               cudaStream_t st);
+cudaError_t launch_push64_batched(const Inst* d_insts, WorkQueue* q, int sp, int gather, int ppt,
+                                  int num_sms, cudaStream_t st);
+cudaError_t launch_push32_batched(const Inst* d_insts, WorkQueue* q, int sp, int gather, int ppt,
+                                  int num_sms, cudaStream_t st);
+cudaError_t launch_post_push(const Inst& I, int num_sms, cudaStream_t st);
+cudaError_t launch_step_end(const Inst& I, cudaStream_t st);
+// all instances' Poisson solves in one cooperative launch (block groups)
+cudaError_t launch_poisson_group(PoissonWork* const* pws, const Inst* insts, int n_inst,
+                                 void* d_args, int num_sms, cudaStream_t st);
+size_t poisson_args_bytes();
+cudaError_t poisson_group_upload(PoissonWork* const* pws, const Inst* insts, int n_inst,
+                                 void* d_args, cudaStream_t st);
+
 // pieces shared with the FP32 path
 cudaError_t launch_scan(const Inst& I, int sp0, int nsp, cudaStream_t st);
 cudaError_t launch_commit_n(const Inst& I, int sp, cudaStream_t st);

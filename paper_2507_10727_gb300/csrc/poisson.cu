@@ -17,10 +17,15 @@
 // the transpose of bilinear prolongation).  Because the outer iteration and
 // its stopping test (relative residual ||b - A phi||_2 <= tol ||b||_2) are
 // FP64, the converged phi does not depend on the preconditioner's precision.
-// Coarse levels (<= kTailNodes nodes) run inside one CTA; finer levels use
-// the whole grid with a time-bounded grid barrier.
+//
+// Layout of the work: the couplings of every level are tabulated per radial
+// index in shared memory at the start of the launch; the coarse levels that
+// fit in shared memory run inside one CTA ("tail"); the finer levels use the
+// whole grid with a time-bounded grid barrier.  Nodes are visited as (row,
+// 32-wide segment) items per warp, so no per-node integer division is needed.
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "common.cuh"
 #include "launch.h"
@@ -29,14 +34,20 @@ namespace pic {
 
 constexpr int kMaxLev = 16;
 constexpr int kPoisThreads = 512;
-constexpr int kTailNodes = 4225;        // 65 x 65
 constexpr double kBarrierLimitNs = 2.0e9;
+constexpr size_t kSmemBudget = 200 * 1024;   // dynamic shared memory per block
+constexpr int kTailMaxNodes = 65 * 65;       // finest level handled inside one CTA
+constexpr int kCoarseSweeps = 4;             // symmetric sweep pairs on the coarsest level
 
 struct PoissonWork {
   int nr, nz, nlev, tail;
   double dr, dz;
   int nblocks;
+  int smem_bytes;          // dynamic shared memory per block
   int lnr[kMaxLev], lnz[kMaxLev];
+  int coef_off[kMaxLev];   // offset of level l in the per-level coupling tables
+  int ncoef;               // entries of each coupling table
+  int tail_floats;         // shared-memory floats of the tail levels (u and f)
   float* u[kMaxLev];
   float* f[kMaxLev];
   double *r, *p, *q, *z;
@@ -55,23 +66,78 @@ struct PoissonArgs {
   double* resid;
 };
 
-size_t poisson_work_bytes(int nr, int nz) {
-  size_t bytes = 0;
-  auto add = [&](size_t b) { bytes += (b + 255) & ~(size_t)255; };
-  const size_t nn = (size_t)(nr + 1) * (nz + 1);
-  for (int k = 0; k < 4; ++k) add(nn * sizeof(double));
-  int lr = nr, lz = nz;
-  for (int l = 0; l < kMaxLev; ++l) {
-    const size_t ln = (size_t)(lr + 1) * (lz + 1);
-    add(ln * sizeof(float));
-    add(ln * sizeof(float));
+static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static int level_count(int nr, int nz, int* lnr, int* lnz) {
+  int lr = nr, lz = nz, l = 0;
+  for (; l < kMaxLev; ++l) {
+    lnr[l] = lr;
+    lnz[l] = lz;
     if (!(lr % 2 == 0 && lz % 2 == 0 && lr >= 4 && lz >= 4)) break;
     lr /= 2;
     lz /= 2;
   }
-  add(8 * 2048 * sizeof(double));  // partial sums: 2 parities x 4 slots x blocks
-  add(256);                        // barrier words
+  return l + 1;
+}
+
+size_t poisson_work_bytes(int nr, int nz) {
+  size_t bytes = 0;
+  const size_t nn = (size_t)(nr + 1) * (nz + 1);
+  for (int k = 0; k < 4; ++k) bytes += round256(nn * sizeof(double));
+  int lnr[kMaxLev], lnz[kMaxLev];
+  const int nlev = level_count(nr, nz, lnr, lnz);
+  for (int l = 0; l < nlev; ++l) {
+    const size_t ln = (size_t)(lnr[l] + 1) * (lnz[l] + 1);
+    bytes += 2 * round256(ln * sizeof(float));
+  }
+  bytes += round256(8 * 2048 * sizeof(double));  // partial sums: 2 parities x 4 slots x blocks
+  bytes += 256;                                  // barrier words
   return bytes;
+}
+
+// Layout of the workspace at `base` (poisson_work_bytes bytes) and of the
+// shared memory: FP64 level-0 tables, three FP32 tables, then the tail levels.
+static void layout(PoissonWork& w, void* base, int nr, int nz, double R, double L) {
+  std::memset(&w, 0, sizeof(w));
+  w.nr = nr;
+  w.nz = nz;
+  w.dr = R / nr;
+  w.dz = L / nz;
+  char* p = (char*)base;
+  auto take = [&](size_t b) {
+    char* q = p;
+    p += round256(b);
+    return (void*)q;
+  };
+  const size_t nn = (size_t)(nr + 1) * (nz + 1);
+  w.r = (double*)take(nn * sizeof(double));
+  w.p = (double*)take(nn * sizeof(double));
+  w.q = (double*)take(nn * sizeof(double));
+  w.z = (double*)take(nn * sizeof(double));
+  w.nlev = level_count(nr, nz, w.lnr, w.lnz);
+  int off = 0;
+  for (int l = 0; l < w.nlev; ++l) {
+    const size_t ln = (size_t)(w.lnr[l] + 1) * (w.lnz[l] + 1);
+    w.u[l] = (float*)take(ln * sizeof(float));
+    w.f[l] = (float*)take(ln * sizeof(float));
+    w.coef_off[l] = off;
+    off += w.lnr[l] + 1;
+  }
+  w.ncoef = off;
+  w.partial = (double*)take(8 * 2048 * sizeof(double));
+  w.bar = (unsigned int*)take(256);
+  const size_t tables = 2 * (size_t)(nr + 1) * sizeof(double) + 3 * (size_t)w.ncoef * sizeof(float);
+  w.tail = w.nlev - 1;
+  w.tail_floats = 2 * (w.lnr[w.nlev - 1] + 1) * (w.lnz[w.nlev - 1] + 1);
+  for (int l = w.nlev - 1; l >= 0; --l) {
+    size_t fl = 0;
+    for (int k = l; k < w.nlev; ++k) fl += 2 * (size_t)(w.lnr[k] + 1) * (w.lnz[k] + 1);
+    if (tables + fl * sizeof(float) > kSmemBudget) break;
+    if (l < w.nlev - 1 && (size_t)(w.lnr[l] + 1) * (w.lnz[l] + 1) > (size_t)kTailMaxNodes) break;
+    w.tail = l;
+    w.tail_floats = (int)fl;
+  }
+  w.smem_bytes = (int)(tables + (size_t)w.tail_floats * sizeof(float));
 }
 
 // ----------------------------------------------------------------------------
@@ -82,14 +148,14 @@ size_t poisson_work_bytes(int nr, int nz) {
 // contend with the arrivals.
 constexpr int kBarGen = 32;   // bar[0]: arrivals, bar[kBarGen]: generation
 
-__device__ __forceinline__ bool barrier_grid(unsigned int* bar, int* status) {
+__device__ __forceinline__ bool barrier_grid(unsigned int* bar, int* status, int nb) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned int* vgen = bar + kBarGen;
     const unsigned int g = *vgen;
     __threadfence();
     const unsigned int arrived = atomicAdd(bar, 1u);
-    if (arrived == gridDim.x - 1) {
+    if (arrived == (unsigned)nb - 1u) {
       atomicExch(bar, 0u);
       __threadfence();
       atomicAdd(bar + kBarGen, 1u);
@@ -109,101 +175,104 @@ __device__ __forceinline__ bool barrier_grid(unsigned int* bar, int* status) {
   return (*(volatile int*)status & ST_TIMEOUT) == 0;
 }
 
-// physical couplings (FP64) at the finest level
-__device__ __forceinline__ double ar64(const PoissonWork& W, int m) {
-  return 2.0 * kPi * kEps0 * (m + 0.5) * W.dz;
-}
-__device__ __forceinline__ double az64(const PoissonWork& W, int m) {
-  const double area = m == 0 ? kPi * 0.25 * W.dr * W.dr : 2.0 * kPi * (m * W.dr) * W.dr;
-  return kEps0 * area / W.dz;
-}
-// scaled couplings (operator / (2 pi eps0)) of level l, FP32
-__device__ __forceinline__ float ar32(float dzl, int m) { return dzl * ((float)m + 0.5f); }
-__device__ __forceinline__ float az32(float drl, float dzl, int m) {
-  return m == 0 ? drl * drl / (8.0f * dzl) : (float)m * drl * drl / dzl;
-}
-
+// One level: node arrays and its coupling tables per radial index m, scaled
+// by 1/(2 pi eps0): az = a_z(m), ar = a_r(m) (between m and m+1), idg = 1 /
+// diagonal.
 struct Lev {
   int nr, nz;
-  float dr, dz;
   float* u;
   float* f;
+  const float* az;
+  const float* ar;
+  const float* idg;
 };
 
-__device__ __forceinline__ Lev lev(const PoissonWork& W, int l) {
+struct Tables {
+  const double* az0;   // level 0, FP64, physical units
+  const double* ar0;
+  const float* az;
+  const float* ar;
+  const float* idg;
+};
+
+__device__ __forceinline__ Lev lev(const PoissonWork& W, const Tables& T, int l, float* u, float* f) {
   Lev L;
   L.nr = W.lnr[l];
   L.nz = W.lnz[l];
-  L.dr = (float)(W.dr * (double)(1 << l));
-  L.dz = (float)(W.dz * (double)(1 << l));
-  L.u = W.u[l];
-  L.f = W.f[l];
+  L.u = u;
+  L.f = f;
+  L.az = T.az + W.coef_off[l];
+  L.ar = T.ar + W.coef_off[l];
+  L.idg = T.idg + W.coef_off[l];
   return L;
 }
 
-// red-black Gauss-Seidel half sweep over free nodes of `color`
-__device__ void smooth(const Lev& L, int color, int tid, int nthr) {
-  const int nzf = L.nz - 1;          // free nodes per radial line
-  const int nfree = L.nr * nzf;
-  const int nz1 = L.nz + 1;
-  for (int k = tid; k < nfree; k += nthr) {
-    const int m = k / nzf, n = 1 + (k - m * nzf);
-    if (((m + n) & 1) != color) continue;
+// Nodes are visited as warp items (row m, 32-wide segment of n):
+//   full sweep:    n = 1 + 32 seg + lane
+//   colour sweep:  the nodes of row m with (m + n) % 2 == colour,
+//                  n = 2 (32 seg + lane) + 1 (odd n) or + 2 (even n)
+__device__ __forceinline__ int segs_full(int nz) { return (nz - 1 + 31) >> 5; }
+__device__ __forceinline__ int segs_color(int nz) { return (nz / 2 + 32) >> 5; }
+
+__device__ void smooth(const Lev L, int color, int wid, int nw, int lane) {
+  const int ns = segs_color(L.nz), nz1 = L.nz + 1;
+  const int items = L.nr * ns;
+  for (int it = wid; it < items; it += nw) {
+    const int m = it / ns, s = it - m * ns;
+    const int odd = (color + m) & 1;
+    const int n = 2 * (s * 32 + lane) + (odd ? 1 : 2);
+    if (n > L.nz - 1) continue;
     const int i = m * nz1 + n;
-    const float az = az32(L.dr, L.dz, m);
-    const float arp = ar32(L.dz, m);
-    const float arm = m > 0 ? ar32(L.dz, m - 1) : 0.0f;
-    float s = L.f[i] + az * (L.u[i - 1] + L.u[i + 1]) + arp * L.u[i + nz1];
-    if (m > 0) s += arm * L.u[i - nz1];
-    L.u[i] = s / (2.0f * az + arp + arm);
+    float sum = L.f[i] + L.az[m] * (L.u[i - 1] + L.u[i + 1]) + L.ar[m] * L.u[i + nz1];
+    if (m > 0) sum += L.ar[m - 1] * L.u[i - nz1];
+    L.u[i] = sum * L.idg[m];
   }
 }
 
-__device__ __forceinline__ float resid_at(const Lev& L, int m, int n) {
-  // residual of a free node (zero outside the free set)
+__device__ __forceinline__ float resid_at(const Lev L, int m, int n) {
   if (m < 0 || m >= L.nr || n < 1 || n >= L.nz) return 0.0f;
-  const int nz1 = L.nz + 1;
-  const int i = m * nz1 + n;
-  const float az = az32(L.dr, L.dz, m);
-  const float arp = ar32(L.dz, m);
-  const float arm = m > 0 ? ar32(L.dz, m - 1) : 0.0f;
-  float a = (2.0f * az + arp + arm) * L.u[i] - az * (L.u[i - 1] + L.u[i + 1]) - arp * L.u[i + nz1];
+  const int nz1 = L.nz + 1, i = m * nz1 + n;
+  const float arm = m > 0 ? L.ar[m - 1] : 0.0f;
+  const float diag = 2.0f * L.az[m] + L.ar[m] + arm;
+  float a = diag * L.u[i] - L.az[m] * (L.u[i - 1] + L.u[i + 1]) - L.ar[m] * L.u[i + nz1];
   if (m > 0) a -= arm * L.u[i - nz1];
   return L.f[i] - a;
 }
 
 // coarse f = P^T (fine residual), coarse u = 0
-__device__ void restrict_to(const Lev& F, const Lev& C, int tid, int nthr) {
-  const int nzf = C.nz - 1;
-  const int nfree = C.nr * nzf;
-  const int nz1 = C.nz + 1;
-  for (int k = tid; k < nfree; k += nthr) {
-    const int M = k / nzf, N = 1 + (k - M * nzf);
-    float s = 0.0f;
+__device__ void restrict_to(const Lev F, const Lev C, int wid, int nw, int lane) {
+  const int ns = segs_full(C.nz), nz1 = C.nz + 1;
+  const int items = C.nr * ns;
+  for (int it = wid; it < items; it += nw) {
+    const int M = it / ns, s = it - M * ns;
+    const int N = 1 + s * 32 + lane;
+    if (N > C.nz - 1) continue;
+    float acc = 0.0f;
 #pragma unroll
     for (int di = -1; di <= 1; ++di) {
       const float wi = di == 0 ? 1.0f : 0.5f;
 #pragma unroll
       for (int dj = -1; dj <= 1; ++dj) {
         const float wj = dj == 0 ? 1.0f : 0.5f;
-        s += wi * wj * resid_at(F, 2 * M + di, 2 * N + dj);
+        acc += wi * wj * resid_at(F, 2 * M + di, 2 * N + dj);
       }
     }
-    C.f[M * nz1 + N] = s;
+    C.f[M * nz1 + N] = acc;
     C.u[M * nz1 + N] = 0.0f;
   }
 }
 
 // fine u += bilinear interpolation of coarse u (zero on coarse Dirichlet nodes)
-__device__ void prolong_from(const Lev& F, const Lev& C, int tid, int nthr) {
-  const int nzf = F.nz - 1;
-  const int nfree = F.nr * nzf;
-  const int fz1 = F.nz + 1, cz1 = C.nz + 1;
-  for (int k = tid; k < nfree; k += nthr) {
-    const int m = k / nzf, n = 1 + (k - m * nzf);
+__device__ void prolong_from(const Lev F, const Lev C, int wid, int nw, int lane) {
+  const int ns = segs_full(F.nz), fz1 = F.nz + 1, cz1 = C.nz + 1;
+  const int items = F.nr * ns;
+  for (int it = wid; it < items; it += nw) {
+    const int m = it / ns, s = it - m * ns;
+    const int n = 1 + s * 32 + lane;
+    if (n > F.nz - 1) continue;
     const int cm = m >> 1, cn = n >> 1;
-    float v;
     const float* u = C.u;
+    float v;
     if ((m & 1) == 0 && (n & 1) == 0) v = u[cm * cz1 + cn];
     else if ((n & 1) == 0) v = 0.5f * (u[cm * cz1 + cn] + u[(cm + 1) * cz1 + cn]);
     else if ((m & 1) == 0) v = 0.5f * (u[cm * cz1 + cn] + u[cm * cz1 + cn + 1]);
@@ -214,74 +283,86 @@ __device__ void prolong_from(const Lev& F, const Lev& C, int tid, int nthr) {
   }
 }
 
-// Levels >= l0 inside one CTA (block-level synchronisation only).
-constexpr int kTailSmemFloats = 2 * 5800;   // u and f of levels with <= kTailNodes nodes
+// Levels >= l0 inside this CTA, in shared memory: f of level l0 is loaded
+// from global memory (u starts at zero), u of level l0 is written back.  Level
+// descriptors are rebuilt from the shared buffer's offsets where they are
+// used, so the sweeps address shared memory directly.
+__device__ __forceinline__ Lev tail_lev(const PoissonWork& W, const Tables& T, int l0, int l,
+                                        float* buf) {
+  int off = 0;
+  for (int k = l0; k < l; ++k) off += 2 * (W.lnr[k] + 1) * (W.lnz[k] + 1);
+  const int nn = (W.lnr[l] + 1) * (W.lnz[l] + 1);
+  return lev(W, T, l, buf + off, buf + off + nn);
+}
 
-__device__ void vcycle_levels(Lev* T, int l0, int nlev) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  for (int l = l0; l < nlev - 1; ++l) {
-    smooth(T[l], 0, tid, nthr);
+__device__ void vcycle_tail(const PoissonWork& W, const Tables& T, int l0, float* buf) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = threadIdx.x; k < W.tail_floats; k += blockDim.x) buf[k] = 0.0f;
+  __syncthreads();
+  const int nn0 = (W.lnr[l0] + 1) * (W.lnz[l0] + 1);
+  {
+    const Lev L0 = tail_lev(W, T, l0, l0, buf);
+    const float* fg = W.f[l0];
+    // eight independent loads in flight per thread
+    int k = threadIdx.x;
+    for (; k + 7 * (int)blockDim.x < nn0; k += 8 * blockDim.x) {
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = fg[k + j * blockDim.x];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) L0.f[k + j * blockDim.x] = v[j];
+    }
+    for (; k < nn0; k += blockDim.x) L0.f[k] = fg[k];
+  }
+  __syncthreads();
+  for (int l = l0; l < W.nlev - 1; ++l) {
+    const Lev F = tail_lev(W, T, l0, l, buf), C = tail_lev(W, T, l0, l + 1, buf);
+    smooth(F, 0, wid, nw, lane);
     __syncthreads();
-    smooth(T[l], 1, tid, nthr);
+    smooth(F, 1, wid, nw, lane);
     __syncthreads();
-    restrict_to(T[l], T[l + 1], tid, nthr);
+    restrict_to(F, C, wid, nw, lane);
+    __syncthreads();
+  }
+  if (wid == 0) {
+    // coarsest level: one warp, symmetric Gauss-Seidel sweeps
+    const Lev C = tail_lev(W, T, l0, W.nlev - 1, buf);
+    for (int s = 0; s < kCoarseSweeps; ++s) {
+      smooth(C, 0, 0, 1, lane);
+      __syncwarp();
+      smooth(C, 1, 0, 1, lane);
+      __syncwarp();
+    }
+    for (int s = 0; s < kCoarseSweeps; ++s) {
+      smooth(C, 1, 0, 1, lane);
+      __syncwarp();
+      smooth(C, 0, 0, 1, lane);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int l = W.nlev - 2; l >= l0; --l) {
+    const Lev F = tail_lev(W, T, l0, l, buf), C = tail_lev(W, T, l0, l + 1, buf);
+    prolong_from(F, C, wid, nw, lane);
+    __syncthreads();
+    smooth(F, 1, wid, nw, lane);
+    __syncthreads();
+    smooth(F, 0, wid, nw, lane);
     __syncthreads();
   }
   {
-    const Lev& C = T[nlev - 1];
-    for (int s = 0; s < 8; ++s) {
-      smooth(C, 0, tid, nthr);
-      __syncthreads();
-      smooth(C, 1, tid, nthr);
-      __syncthreads();
+    const Lev L0 = tail_lev(W, T, l0, l0, buf);
+    float* ug = W.u[l0];
+    int k = threadIdx.x;
+    for (; k + 7 * (int)blockDim.x < nn0; k += 8 * blockDim.x) {
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = L0.u[k + j * blockDim.x];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) ug[k + j * blockDim.x] = v[j];
     }
-    for (int s = 0; s < 8; ++s) {
-      smooth(C, 1, tid, nthr);
-      __syncthreads();
-      smooth(C, 0, tid, nthr);
-      __syncthreads();
-    }
+    for (; k < nn0; k += blockDim.x) ug[k] = L0.u[k];
   }
-  for (int l = nlev - 2; l >= l0; --l) {
-    prolong_from(T[l], T[l + 1], tid, nthr);
-    __syncthreads();
-    smooth(T[l], 1, tid, nthr);
-    __syncthreads();
-    smooth(T[l], 0, tid, nthr);
-    __syncthreads();
-  }
-}
-
-// The tail in shared memory when it fits in `buf` (f of level l0 loaded, u
-// of level l0 written back), else in the global level arrays.
-__device__ void vcycle_tail(const PoissonWork& W, int l0, float* buf) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  Lev T[kMaxLev];
-  int total = 0;
-  for (int l = l0; l < W.nlev; ++l) {
-    T[l] = lev(W, l);
-    total += 2 * (T[l].nr + 1) * (T[l].nz + 1);
-  }
-  if (total > kTailSmemFloats) {
-    vcycle_levels(T, l0, W.nlev);
-    return;
-  }
-  float* p = buf;
-  for (int l = l0; l < W.nlev; ++l) {
-    const int nn = (T[l].nr + 1) * (T[l].nz + 1);
-    T[l].u = p;
-    T[l].f = p + nn;
-    p += 2 * nn;
-  }
-  for (int k = tid; k < total; k += nthr) buf[k] = 0.0f;
-  __syncthreads();
-  const int nn0 = (T[l0].nr + 1) * (T[l0].nz + 1);
-  const float* fg = W.f[l0];
-  for (int k = tid; k < nn0; k += nthr) T[l0].f[k] = fg[k];
-  __syncthreads();
-  vcycle_levels(T, l0, W.nlev);
-  float* ug = W.u[l0];
-  for (int k = tid; k < nn0; k += nthr) ug[k] = T[l0].u[k];
 }
 
 __device__ __forceinline__ double warp_sum64(double v) {
@@ -292,7 +373,8 @@ __device__ __forceinline__ double warp_sum64(double v) {
 
 // Block partial sums of up to 3 values written to partial[slot][block]; after
 // a grid barrier every block reads them back in block order (deterministic).
-__device__ void block_partials(double* partial, int parity, int nvals, const double* v) {
+__device__ void block_partials(double* partial, int parity, int nvals, const double* v, int lb,
+                               int nb) {
   __shared__ double red[3][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int j = 0; j < nvals; ++j) {
@@ -305,20 +387,20 @@ __device__ void block_partials(double* partial, int parity, int nvals, const dou
     for (int j = 0; j < nvals; ++j) {
       double s = lane < nw ? red[j][lane] : 0.0;
       s = warp_sum64(s);
-      if (lane == 0) partial[(parity * 4 + j) * gridDim.x + blockIdx.x] = s;
+      if (lane == 0) partial[(parity * 4 + j) * nb + lb] = s;
     }
   }
   __syncthreads();
 }
 
-__device__ void read_partials(const double* partial, int parity, int nvals, double* out) {
+__device__ void read_partials(const double* partial, int parity, int nvals, double* out, int nb) {
   __shared__ double res[3];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (w == 0) {
     for (int j = 0; j < nvals; ++j) {
       double s = 0.0;
-      const volatile double* p = partial + (parity * 4 + j) * gridDim.x;
-      for (int b = lane; b < (int)gridDim.x; b += 32) s += p[b];
+      const volatile double* p = partial + (parity * 4 + j) * nb;
+      for (int b = lane; b < nb; b += 32) s += p[b];
       s = warp_sum64(s);
       if (lane == 0) res[j] = s;
     }
@@ -328,166 +410,233 @@ __device__ void read_partials(const double* partial, int parity, int nvals, doub
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A) {
+// (A x) at a free fine node, x holding the Dirichlet values on the boundary
+__device__ __forceinline__ double apply64(const Tables& T, const double* x, int m, int i, int nz1) {
+  double a = T.az0[m] * (2.0 * x[i] - x[i - 1] - x[i + 1]) + T.ar0[m] * (x[i] - x[i + nz1]);
+  if (m > 0) a += T.ar0[m - 1] * (x[i] - x[i - nz1]);
+  return a;
+}
+
+// One solve per block group: `group` == nullptr -> the whole grid solves A0;
+// otherwise block b works on group[b / bpi] with bpi blocks per solve (the
+// ensemble's discharges solved side by side in one launch).
+__global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const PoissonArgs* group,
+                                                          int bpi) {
+  __shared__ PoissonArgs sA;
+  int lb, nb;
+  {
+    const PoissonArgs* src = &A0;
+    if (group) {
+      const int inst = blockIdx.x / bpi;
+      lb = blockIdx.x - inst * bpi;
+      nb = bpi;
+      src = group + inst;
+    } else {
+      lb = blockIdx.x;
+      nb = gridDim.x;
+    }
+    const unsigned* s4 = reinterpret_cast<const unsigned*>(src);
+    unsigned* d4 = reinterpret_cast<unsigned*>(&sA);
+    for (int k = threadIdx.x; k < (int)(sizeof(PoissonArgs) / 4); k += blockDim.x) d4[k] = s4[k];
+    __syncthreads();
+  }
+  const PoissonArgs& A = sA;
   const PoissonWork& W = A.W;
   if (*(volatile int*)A.status & (ST_FATAL)) return;
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int gthr = gridDim.x * blockDim.x;
+  extern __shared__ __align__(16) unsigned char smem[];
   const int nr = W.nr, nz = W.nz, nz1 = nz + 1;
-  const int nzf = nz - 1, nfree = nr * nzf;
+  const int lane = threadIdx.x & 31;
+  const int gw = (lb * blockDim.x + threadIdx.x) >> 5;
+  const int ngw = (nb * blockDim.x) >> 5;
+  const int nsf = (nz - 1 + 31) >> 5;            // segments of a fine row
+  const int items0 = nr * nsf;
+  const long long nfree = (long long)nr * (nz - 1);
   double* phi = A.phi;
+
+  // ---- coupling tables of every level in shared memory ----------------------
+  double* az0 = (double*)smem;
+  double* ar0 = az0 + (nr + 1);
+  float* taz = (float*)(ar0 + (nr + 1));
+  float* tar = taz + W.ncoef;
+  float* tidg = tar + W.ncoef;
+  float* tailbuf = tidg + W.ncoef;
+  for (int m = threadIdx.x; m <= nr; m += blockDim.x) {
+    const double c = 2.0 * kPi * kEps0;
+    az0[m] = m == 0 ? c * W.dr * W.dr / (8.0 * W.dz) : c * m * W.dr * W.dr / W.dz;
+    ar0[m] = c * (m + 0.5) * W.dz;
+  }
+  for (int l = 0; l < W.nlev; ++l) {
+    const float drl = (float)(W.dr * (double)(1 << l)), dzl = (float)(W.dz * (double)(1 << l));
+    const int o = W.coef_off[l], lr = W.lnr[l];
+    for (int m = threadIdx.x; m <= lr; m += blockDim.x) {
+      const float az = m == 0 ? drl * drl / (8.0f * dzl) : (float)m * drl * drl / dzl;
+      const float arp = dzl * ((float)m + 0.5f);
+      const float arm = m > 0 ? dzl * ((float)m - 0.5f) : 0.0f;
+      taz[o + m] = az;
+      tar[o + m] = arp;
+      tidg[o + m] = 1.0f / (2.0f * az + arp + arm);
+    }
+  }
+  __syncthreads();
+  const Tables T{az0, ar0, taz, tar, tidg};
+
   int parity = 0;
   double vals[3];
-  __shared__ float tail_buf[kTailSmemFloats];
-
-  // residual r = Q - A phi (Dirichlet values in phi), ||b||^2, ||r||^2
+  // ---- r = Q - A phi (Dirichlet values in phi), ||b||^2, ||r||^2 ------------
   double bb = 0.0, rr = 0.0;
-  for (int k = gtid; k < nfree; k += gthr) {
-    const int m = k / nzf, n = 1 + (k - m * nzf);
+  for (int it = gw; it < items0; it += ngw) {
+    const int m = it / nsf, n = 1 + (it - m * nsf) * 32 + lane;
+    if (n > nz - 1) continue;
     const int i = m * nz1 + n;
-    const double az = az64(W, m), arp = ar64(W, m), arm = m > 0 ? ar64(W, m - 1) : 0.0;
-    double a = az * (2.0 * phi[i] - phi[i - 1] - phi[i + 1]) + arp * (phi[i] - phi[i + nz1]);
-    if (m > 0) a += arm * (phi[i] - phi[i - nz1]);
     double b = A.Q[i];
-    if (n == 1) b += az * phi[i - 1];
-    if (n == nz - 1) b += az * phi[i + 1];
-    if (m == nr - 1) b += arp * phi[i + nz1];
-    const double r = A.Q[i] - a;
+    if (n == 1) b += az0[m] * phi[i - 1];
+    if (n == nz - 1) b += az0[m] * phi[i + 1];
+    if (m == nr - 1) b += ar0[m] * phi[i + nz1];
+    const double r = A.Q[i] - apply64(T, phi, m, i, nz1);
     W.r[i] = r;
     bb += b * b;
     rr += r * r;
   }
   vals[0] = bb;
   vals[1] = rr;
-  block_partials(W.partial, parity, 2, vals);
-  if (!barrier_grid(W.bar, A.status)) return;
-  read_partials(W.partial, parity, 2, vals);
+  block_partials(W.partial, parity, 2, vals, lb, nb);
+  if (!barrier_grid(W.bar, A.status, nb)) return;
+  read_partials(W.partial, parity, 2, vals, nb);
   parity ^= 1;
   bb = vals[0];
   rr = vals[1];
   const double tol2bb = A.tol * A.tol * bb;
+  // the preconditioner works on r scaled to O(1) (FP32 range), unscaled after
+  const double ref = bb > 0.0 ? bb : rr;
+  const double scale = ref > 0.0 ? 1.0 / sqrt(ref / (double)nfree) : 1.0;
+  const double unscale = 1.0 / (2.0 * kPi * kEps0 * scale);
+  const Lev L0 = lev(W, T, 0, W.u[0], W.f[0]);
+
   int it = 0;
   bool converged = rr <= tol2bb;
   double rz = 0.0, alpha = 0.0;
   bool first = true;
   int restarts = 0;
-
+  if (!converged) {
+    // f0 = scale r; the first red half sweep from u0 = 0 is u0 = f0 / diag
+    for (int itm = gw; itm < items0; itm += ngw) {
+      const int m = itm / nsf, n = 1 + (itm - m * nsf) * 32 + lane;
+      if (n > nz - 1) continue;
+      const int i = m * nz1 + n;
+      const float f = (float)(W.r[i] * scale);
+      L0.f[i] = f;
+      L0.u[i] = ((m + n) & 1) == 0 ? f * L0.idg[m] : 0.0f;
+    }
+    if (!barrier_grid(W.bar, A.status, nb)) return;
+  }
   while (!converged && it < A.max_iter) {
-    // ---- z = M^{-1} r : scale, V-cycle in FP32, unscale -------------------
-    const double scale = rr > 0.0 ? 1.0 / sqrt(rr / (double)nfree) : 1.0;
-    {
-      const Lev L0 = lev(W, 0);
-      for (int k = gtid; k < nfree; k += gthr) {
-        const int m = k / nzf, n = 1 + (k - m * nzf);
-        const int i = m * nz1 + n;
-        L0.f[i] = (float)(W.r[i] * scale);
-        L0.u[i] = 0.0f;
-      }
-      if (!barrier_grid(W.bar, A.status)) return;
-    }
+    // ---- V-cycle, grid levels down (red of level 0 already done) -----------
     for (int l = 0; l < W.tail; ++l) {
-      const Lev F = lev(W, l), C = lev(W, l + 1);
-      smooth(F, 0, gtid, gthr);
-      if (!barrier_grid(W.bar, A.status)) return;
-      smooth(F, 1, gtid, gthr);
-      if (!barrier_grid(W.bar, A.status)) return;
-      restrict_to(F, C, gtid, gthr);
-      if (!barrier_grid(W.bar, A.status)) return;
-    }
-    if (blockIdx.x == 0) vcycle_tail(W, W.tail, tail_buf);
-    if (!barrier_grid(W.bar, A.status)) return;
-    for (int l = W.tail - 1; l >= 0; --l) {
-      const Lev F = lev(W, l), C = lev(W, l + 1);
-      prolong_from(F, C, gtid, gthr);
-      if (!barrier_grid(W.bar, A.status)) return;
-      smooth(F, 1, gtid, gthr);
-      if (!barrier_grid(W.bar, A.status)) return;
-      smooth(F, 0, gtid, gthr);
-      if (!barrier_grid(W.bar, A.status)) return;
-    }
-    {
-      const Lev L0 = lev(W, 0);
-      const double unscale = 1.0 / (2.0 * kPi * kEps0 * scale);
-      double rz_loc = 0.0, zq_loc = 0.0;
-      for (int k = gtid; k < nfree; k += gthr) {
-        const int m = k / nzf, n = 1 + (k - m * nzf);
-        const int i = m * nz1 + n;
-        const double zi = (double)L0.u[i] * unscale;
-        W.z[i] = zi;
-        rz_loc += W.r[i] * zi;
-        if (!first) zq_loc += zi * W.q[i];
+      const Lev F = lev(W, T, l, W.u[l], W.f[l]);
+      const Lev C = lev(W, T, l + 1, W.u[l + 1], W.f[l + 1]);
+      if (l > 0) {
+        smooth(F, 0, gw, ngw, lane);
+        if (!barrier_grid(W.bar, A.status, nb)) return;
       }
-      vals[0] = rz_loc;
-      vals[1] = zq_loc;
-      block_partials(W.partial, parity, 2, vals);
-      if (!barrier_grid(W.bar, A.status)) return;
-      read_partials(W.partial, parity, 2, vals);
-      parity ^= 1;
+      smooth(F, 1, gw, ngw, lane);
+      if (!barrier_grid(W.bar, A.status, nb)) return;
+      restrict_to(F, C, gw, ngw, lane);
+      if (!barrier_grid(W.bar, A.status, nb)) return;
     }
-    // ---- direction: p = z + beta p (flexible Polak-Ribiere beta) ----------
+    if (lb == 0) vcycle_tail(W, T, W.tail, tailbuf);
+    if (!barrier_grid(W.bar, A.status, nb)) return;
+    for (int l = W.tail - 1; l >= 0; --l) {
+      const Lev F = lev(W, T, l, W.u[l], W.f[l]);
+      const Lev C = lev(W, T, l + 1, W.u[l + 1], W.f[l + 1]);
+      prolong_from(F, C, gw, ngw, lane);
+      if (!barrier_grid(W.bar, A.status, nb)) return;
+      smooth(F, 1, gw, ngw, lane);
+      if (!barrier_grid(W.bar, A.status, nb)) return;
+      smooth(F, 0, gw, ngw, lane);
+      if (!barrier_grid(W.bar, A.status, nb)) return;
+    }
+    // ---- z = M^{-1} r, r.z and z.q_old ------------------------------------
+    double rz_loc = 0.0, zq_loc = 0.0;
+    for (int itm = gw; itm < items0; itm += ngw) {
+      const int m = itm / nsf, n = 1 + (itm - m * nsf) * 32 + lane;
+      if (n > nz - 1) continue;
+      const int i = m * nz1 + n;
+      const double zi = (double)L0.u[i] * unscale;
+      W.z[i] = zi;
+      rz_loc += W.r[i] * zi;
+      if (!first) zq_loc += zi * W.q[i];
+    }
+    vals[0] = rz_loc;
+    vals[1] = zq_loc;
+    block_partials(W.partial, parity, 2, vals, lb, nb);
+    if (!barrier_grid(W.bar, A.status, nb)) return;
+    read_partials(W.partial, parity, 2, vals, nb);
+    parity ^= 1;
+    // ---- p = z + beta p, q = A z + beta q (flexible Polak-Ribiere beta) ---
     const double beta = first ? 0.0 : -alpha * vals[1] / rz;
     rz = vals[0];
     first = false;
-    for (int k = gtid; k < nfree; k += gthr) {
-      const int m = k / nzf, n = 1 + (k - m * nzf);
-      const int i = m * nz1 + n;
-      W.p[i] = W.z[i] + beta * W.p[i];
-    }
-    if (!barrier_grid(W.bar, A.status)) return;
-    // ---- q = A p, alpha = rz / (p.q) --------------------------------------
     double pq = 0.0;
-    for (int k = gtid; k < nfree; k += gthr) {
-      const int m = k / nzf, n = 1 + (k - m * nzf);
+    for (int itm = gw; itm < items0; itm += ngw) {
+      const int m = itm / nsf, n = 1 + (itm - m * nsf) * 32 + lane;
+      if (n > nz - 1) continue;
       const int i = m * nz1 + n;
-      const double az = az64(W, m), arp = ar64(W, m), arm = m > 0 ? ar64(W, m - 1) : 0.0;
-      const double pi = W.p[i];
-      const double pl = n > 1 ? W.p[i - 1] : 0.0, pu = n < nz - 1 ? W.p[i + 1] : 0.0;
-      const double po = m < nr - 1 ? W.p[i + nz1] : 0.0, pn = m > 0 ? W.p[i - nz1] : 0.0;
-      double a = az * (2.0 * pi - pl - pu) + arp * (pi - po);
-      if (m > 0) a += arm * (pi - pn);
-      W.q[i] = a;
-      pq += pi * a;
+      const double zi = W.z[i];
+      const double zl = n > 1 ? W.z[i - 1] : 0.0, zu = n < nz - 1 ? W.z[i + 1] : 0.0;
+      const double zo = m < nr - 1 ? W.z[i + nz1] : 0.0;
+      double a = az0[m] * (2.0 * zi - zl - zu) + ar0[m] * (zi - zo);
+      if (m > 0) a += ar0[m - 1] * (zi - W.z[i - nz1]);
+      const double pi = zi + beta * W.p[i];
+      const double qi = a + beta * W.q[i];
+      W.p[i] = pi;
+      W.q[i] = qi;
+      pq += pi * qi;
     }
     vals[0] = pq;
-    block_partials(W.partial, parity, 1, vals);
-    if (!barrier_grid(W.bar, A.status)) return;
-    read_partials(W.partial, parity, 1, vals);
+    block_partials(W.partial, parity, 1, vals, lb, nb);
+    if (!barrier_grid(W.bar, A.status, nb)) return;
+    read_partials(W.partial, parity, 1, vals, nb);
     parity ^= 1;
     alpha = vals[0] != 0.0 ? rz / vals[0] : 0.0;
-    // ---- phi += alpha p, r -= alpha q --------------------------------------
+    // ---- phi += alpha p, r -= alpha q, next V-cycle's f0 and red sweep ----
     double rl = 0.0;
-    for (int k = gtid; k < nfree; k += gthr) {
-      const int m = k / nzf, n = 1 + (k - m * nzf);
+    for (int itm = gw; itm < items0; itm += ngw) {
+      const int m = itm / nsf, n = 1 + (itm - m * nsf) * 32 + lane;
+      if (n > nz - 1) continue;
       const int i = m * nz1 + n;
       phi[i] += alpha * W.p[i];
       const double r = W.r[i] - alpha * W.q[i];
       W.r[i] = r;
       rl += r * r;
+      const float f = (float)(r * scale);
+      L0.f[i] = f;
+      L0.u[i] = ((m + n) & 1) == 0 ? f * L0.idg[m] : 0.0f;
     }
     vals[0] = rl;
-    block_partials(W.partial, parity, 1, vals);
-    if (!barrier_grid(W.bar, A.status)) return;
-    read_partials(W.partial, parity, 1, vals);
+    block_partials(W.partial, parity, 1, vals, lb, nb);
+    if (!barrier_grid(W.bar, A.status, nb)) return;
+    read_partials(W.partial, parity, 1, vals, nb);
     parity ^= 1;
     rr = vals[0];
     ++it;
     if (rr <= tol2bb) {
-      // confirm with the true residual b - A phi
+      // confirm with the true residual b - A phi (also the restart's input)
       double rt = 0.0;
-      for (int k = gtid; k < nfree; k += gthr) {
-        const int m = k / nzf, n = 1 + (k - m * nzf);
+      for (int itm = gw; itm < items0; itm += ngw) {
+        const int m = itm / nsf, n = 1 + (itm - m * nsf) * 32 + lane;
+        if (n > nz - 1) continue;
         const int i = m * nz1 + n;
-        const double az = az64(W, m), arp = ar64(W, m), arm = m > 0 ? ar64(W, m - 1) : 0.0;
-        double a = az * (2.0 * phi[i] - phi[i - 1] - phi[i + 1]) + arp * (phi[i] - phi[i + nz1]);
-        if (m > 0) a += arm * (phi[i] - phi[i - nz1]);
-        const double r = A.Q[i] - a;
+        const double r = A.Q[i] - apply64(T, phi, m, i, nz1);
         W.r[i] = r;
         rt += r * r;
+        const float f = (float)(r * scale);
+        L0.f[i] = f;
+        L0.u[i] = ((m + n) & 1) == 0 ? f * L0.idg[m] : 0.0f;
       }
       vals[0] = rt;
-      block_partials(W.partial, parity, 1, vals);
-      if (!barrier_grid(W.bar, A.status)) return;
-      read_partials(W.partial, parity, 1, vals);
+      block_partials(W.partial, parity, 1, vals, lb, nb);
+      if (!barrier_grid(W.bar, A.status, nb)) return;
+      read_partials(W.partial, parity, 1, vals, nb);
       parity ^= 1;
       rr = vals[0];
       if (rr <= tol2bb || restarts >= 3) {
@@ -498,7 +647,7 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A) {
       first = true;  // restart the Krylov space from the true residual
     }
   }
-  if (gtid == 0) {
+  if (lb == 0 && threadIdx.x == 0) {
     *A.iters = it;
     *A.resid = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
     if (!converged) atomicOr(A.status, ST_NONCONV);
@@ -508,57 +657,29 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A) {
 // ----------------------------------------------------------------------------
 // host side
 // ----------------------------------------------------------------------------
-struct PoissonWorkHost {
-  PoissonWork w;
-  double tol;
-  int max_iter;
-};
-
-PoissonWork* poisson_work_init(void* base, int nr, int nz, double R, double L, int num_sms) {
-  PoissonWork* pw = new PoissonWork();
-  std::memset(pw, 0, sizeof(*pw));
-  pw->nr = nr;
-  pw->nz = nz;
-  pw->dr = R / nr;
-  pw->dz = L / nz;
-  char* p = (char*)base;
-  auto take = [&](size_t b) {
-    char* q = p;
-    p += (b + 255) & ~(size_t)255;
-    return (void*)q;
-  };
-  const size_t nn = (size_t)(nr + 1) * (nz + 1);
-  pw->r = (double*)take(nn * sizeof(double));
-  pw->p = (double*)take(nn * sizeof(double));
-  pw->q = (double*)take(nn * sizeof(double));
-  pw->z = (double*)take(nn * sizeof(double));
-  int lr = nr, lz = nz, l = 0;
-  pw->tail = -1;
-  for (; l < kMaxLev; ++l) {
-    const size_t ln = (size_t)(lr + 1) * (lz + 1);
-    pw->lnr[l] = lr;
-    pw->lnz[l] = lz;
-    pw->u[l] = (float*)take(ln * sizeof(float));
-    pw->f[l] = (float*)take(ln * sizeof(float));
-    if (pw->tail < 0 && ln <= (size_t)kTailNodes) pw->tail = l;
-    if (!(lr % 2 == 0 && lz % 2 == 0 && lr >= 4 && lz >= 4)) break;
-    lr /= 2;
-    lz /= 2;
+static int poisson_blocks(const PoissonWork& w, int num_sms) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_poisson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+    attr_set = true;
   }
-  pw->nlev = l + 1;
-  if (pw->tail < 0) pw->tail = pw->nlev - 1;
-  pw->partial = (double*)take(8 * 2048 * sizeof(double));
-  pw->bar = (unsigned int*)take(256);
-  // blocks: enough for the free nodes at ~1 per thread, at most one wave
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_poisson, kPoisThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_poisson, kPoisThreads, w.smem_bytes);
   if (per_sm < 1) per_sm = 1;
-  long long want = ((long long)nr * (nz - 1) + kPoisThreads - 1) / kPoisThreads;
+  // about one row segment per warp, at most one wave
+  const long long items = (long long)w.nr * ((w.nz - 1 + 31) / 32);
+  long long want = (items + kPoisThreads / 32 - 1) / (kPoisThreads / 32);
   long long cap = (long long)num_sms * per_sm;
   if (cap > 2048) cap = 2048;
   if (want > cap) want = cap;
   if (want < 1) want = 1;
-  pw->nblocks = (int)want;
+  return (int)want;
+}
+
+PoissonWork* poisson_work_init(void* base, int nr, int nz, double R, double L, int num_sms) {
+  PoissonWork* pw = new PoissonWork();
+  layout(*pw, base, nr, nz, R, L);
+  pw->nblocks = poisson_blocks(*pw, num_sms);
   return pw;
 }
 
@@ -575,80 +696,79 @@ cudaError_t launch_poisson(PoissonWork* pw, const double* Q, double* phi, double
   a.status = status_dev;
   a.iters = iters_dev;
   a.resid = resid_dev;
-  void* args[] = {&a};
+  const PoissonArgs* none = nullptr;
+  int one = 1;
+  void* args[] = {&a, &none, &one};
   return cudaLaunchCooperativeKernel((const void*)k_poisson, dim3(pw->nblocks), dim3(kPoisThreads),
-                                     args, 0, st);
+                                     args, (size_t)pw->smem_bytes, st);
 }
 
-}  // namespace pic
+size_t poisson_args_bytes() { return sizeof(PoissonArgs); }
+
+// Argument records of the grouped launch, written once (the pointers they hold
+// do not change over a handle's life) to d_args: n_inst * poisson_args_bytes().
+cudaError_t poisson_group_upload(PoissonWork* const* pws, const Inst* insts, int n_inst,
+                                 void* d_args, cudaStream_t st) {
+  std::vector<PoissonArgs> host((size_t)n_inst);
+  for (int k = 0; k < n_inst; ++k) {
+    PoissonArgs& a = host[k];
+    std::memset(&a, 0, sizeof(a));
+    a.W = *pws[k];
+    a.Q = insts[k].Q;
+    a.phi = insts[k].phi;
+    a.tol = insts[k].poisson_tol;
+    a.max_iter = insts[k].poisson_max_iter;
+    a.status = &insts[k].S->status;
+    a.iters = &insts[k].S->poisson_iters;
+    a.resid = &insts[k].S->poisson_resid;
+  }
+  cudaError_t e = cudaMemcpyAsync(d_args, host.data(), host.size() * sizeof(PoissonArgs),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+// All instances' solves in one cooperative launch, bpi blocks per instance.
+cudaError_t launch_poisson_group(PoissonWork* const* pws, const Inst* insts, int n_inst,
+                                 void* d_args, int num_sms, cudaStream_t st) {
+  (void)insts;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_poisson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+    attr_set = true;
+  }
+  int smem = 0, want = 1;
+  for (int k = 0; k < n_inst; ++k) {
+    smem = pws[k]->smem_bytes > smem ? pws[k]->smem_bytes : smem;
+    want = pws[k]->nblocks > want ? pws[k]->nblocks : want;
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_poisson, kPoisThreads, smem);
+  if (per_sm < 1) per_sm = 1;
+  int bpi = (num_sms * per_sm) / n_inst;
+  if (bpi > want) bpi = want;
+  if (bpi < 1) return cudaErrorInvalidConfiguration;
+  PoissonArgs a0;
+  std::memset(&a0, 0, sizeof(a0));
+  const PoissonArgs* g = (const PoissonArgs*)d_args;
+  void* args[] = {&a0, &g, &bpi};
+  return cudaLaunchCooperativeKernel((const void*)k_poisson, dim3(n_inst * bpi), dim3(kPoisThreads),
+                                     args, (size_t)smem, st);
+}
 
 // ----------------------------------------------------------------------------
 // Variant for pic_poisson_solve_static: the workspace layout is built in a
 // struct on the host stack (no host or device allocation), over the caller's
 // scratch at `base`.  The layout is the one poisson_work_bytes() sizes.
 // ----------------------------------------------------------------------------
-namespace pic {
-
 cudaError_t launch_poisson_in_place(void* base, int nr, int nz, double R, double L, int num_sms,
                                     const double* Q, double* phi, double tol, int max_iter,
                                     int* status_dev, int* iters_dev, double* resid_dev,
                                     cudaStream_t st) {
-  PoissonArgs a;
-  std::memset(&a, 0, sizeof(a));
-  PoissonWork& w = a.W;
-  w.nr = nr;
-  w.nz = nz;
-  w.dr = R / nr;
-  w.dz = L / nz;
-  char* p = (char*)base;
-  auto take = [&](size_t b) {
-    char* q = p;
-    p += (b + 255) & ~(size_t)255;
-    return (void*)q;
-  };
-  const size_t nn = (size_t)(nr + 1) * (nz + 1);
-  w.r = (double*)take(nn * sizeof(double));
-  w.p = (double*)take(nn * sizeof(double));
-  w.q = (double*)take(nn * sizeof(double));
-  w.z = (double*)take(nn * sizeof(double));
-  int lr = nr, lz = nz, l = 0;
-  w.tail = -1;
-  for (; l < kMaxLev; ++l) {
-    const size_t ln = (size_t)(lr + 1) * (lz + 1);
-    w.lnr[l] = lr;
-    w.lnz[l] = lz;
-    w.u[l] = (float*)take(ln * sizeof(float));
-    w.f[l] = (float*)take(ln * sizeof(float));
-    if (w.tail < 0 && ln <= (size_t)kTailNodes) w.tail = l;
-    if (!(lr % 2 == 0 && lz % 2 == 0 && lr >= 4 && lz >= 4)) break;
-    lr /= 2;
-    lz /= 2;
-  }
-  w.nlev = l + 1;
-  if (w.tail < 0) w.tail = w.nlev - 1;
-  w.partial = (double*)take(8 * 2048 * sizeof(double));
-  w.bar = (unsigned int*)take(256);
-  if ((size_t)(p - (char*)base) != poisson_work_bytes(nr, nz)) return cudaErrorInvalidValue;
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_poisson, kPoisThreads, 0);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  long long want = ((long long)nr * (nz - 1) + kPoisThreads - 1) / kPoisThreads;
-  long long cap = (long long)num_sms * per_sm;
-  if (cap > 2048) cap = 2048;
-  if (want > cap) want = cap;
-  if (want < 1) want = 1;
-  w.nblocks = (int)want;
-  a.Q = Q;
-  a.phi = phi;
-  a.tol = tol;
-  a.max_iter = max_iter;
-  a.status = status_dev;
-  a.iters = iters_dev;
-  a.resid = resid_dev;
-  void* args[] = {&a};
-  return cudaLaunchCooperativeKernel((const void*)k_poisson, dim3(w.nblocks), dim3(kPoisThreads),
-                                     args, 0, st);
+  PoissonWork w;
+  layout(w, base, nr, nz, R, L);
+  w.nblocks = poisson_blocks(w, num_sms);
+  return launch_poisson(&w, Q, phi, tol, max_iter, status_dev, iters_dev, resid_dev, st);
 }
 
 }  // namespace pic

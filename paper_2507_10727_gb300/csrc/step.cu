@@ -219,22 +219,23 @@ __device__ bool mcc_electron(const Inst& I, long long id, long long step, double
 // atomic per touched node.  Particles whose new 4 nodes fall outside the
 // patch (fast movers, chunk tails in sparse regions) add to global memory.
 // ---------------------------------------------------------------------------
+// Push the chunk of `ppt * blockDim.x` particles of species SP starting at c0
+// (the whole CTA takes part).  `patch` is the CTA's zeroed shared deposit
+// patch; it is flushed and zeroed again before return.  Returns this thread's
+// share of the kinetic energy (diagnostic steps only).
 template <int SP, int GATHER>
-__global__ void __launch_bounds__(kPushThreads, 3) k_push(Inst I) {
+__device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned long long* patch,
+                               int* anchor) {
   Scalars* S = I.S;
-  if (S->status & ST_FATAL) return;
-  __shared__ unsigned long long patch[kPR * kPZ];
-  __shared__ int anchor[2];
   const long long n = S->n[SP];
   const long long step = S->step;
   const bool diag = S->diag_on != 0;
-  const ParticlesDev P = I.cur[SP];
+  const ParticlesDev P = I.buf[SP][S->flip[SP]];
   const double h = 0.5 * I.qm[SP] * I.dt;
   const double dt = I.dt;
   const int lane = threadIdx.x & 31;
   double Kloc = 0.0;
-  for (int k = threadIdx.x; k < kPR * kPZ; k += blockDim.x) patch[k] = 0ULL;
-  for (long long c0 = (long long)blockIdx.x * kChunk; c0 < n; c0 += (long long)gridDim.x * kChunk) {
+  {
     if (threadIdx.x == 0) {
       int m, nn;
       double f;
@@ -246,8 +247,8 @@ __global__ void __launch_bounds__(kPushThreads, 3) k_push(Inst I) {
     __syncthreads();
     const int pm0 = anchor[0], pn0 = anchor[1];
 #pragma unroll 1
-    for (int j = 0; j < kPPT; ++j) {
-      const long long i = c0 + (long long)j * kPushThreads + threadIdx.x;
+    for (int j = 0; j < ppt; ++j) {
+      const long long i = c0 + (long long)j * blockDim.x + threadIdx.x;
       int newkey = -1;
       if (i < n) {
         double r = P.r[i], z = P.z[i], vr = P.vr[i], vt = P.vt[i], vz = P.vz[i];
@@ -387,7 +388,70 @@ __global__ void __launch_bounds__(kPushThreads, 3) k_push(Inst I) {
     }
     __syncthreads();
   }
-  if (diag) block_add(Kloc, &I.S->K[SP]);
+  return diag ? Kloc : 0.0;
+}
+
+template <int SP, int GATHER>
+__global__ void __launch_bounds__(kPushThreads, 3) k_push(Inst I) {
+  Scalars* S = I.S;
+  __shared__ unsigned long long patch[kPR * kPZ];
+  __shared__ int anchor[2];
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = *(volatile int*)&S->status & ST_FATAL;
+  __syncthreads();
+  if (s_skip) return;   // the whole CTA, so that no barrier is left short
+  for (int k = threadIdx.x; k < kPR * kPZ; k += blockDim.x) patch[k] = 0ULL;
+  const long long n = S->n[SP];
+  double Kloc = 0.0;
+  for (long long c0 = (long long)blockIdx.x * kChunk; c0 < n; c0 += (long long)gridDim.x * kChunk)
+    Kloc += push_chunk64<SP, GATHER>(I, c0, kPPT, patch, anchor);
+  if (S->diag_on) block_add(Kloc, &S->K[SP]);
+}
+
+// Ensemble: persistent CTAs take (instance, chunk) items from a device queue
+// (instance-major order), so discharges of any size keep every SM busy.
+template <int SP, int GATHER>
+__global__ void __launch_bounds__(kPushThreads, 3) k_push_batched(const Inst* insts, WorkQueue* q,
+                                                                  int ppt) {
+  __shared__ unsigned long long patch[kPR * kPZ];
+  __shared__ int anchor[2];
+  __shared__ Inst sI;
+  __shared__ int s_inst;
+  __shared__ long long s_c0;
+  __shared__ int s_skip;
+  for (int k = threadIdx.x; k < kPR * kPZ; k += blockDim.x) patch[k] = 0ULL;
+  int cur = -1;
+  double Kloc = 0.0;
+  const long long chunk = (long long)ppt * blockDim.x;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int item = (int)atomicAdd(&q->next[SP], 1u);
+      int inst = -1;
+      for (int k = 0; k < q->n_inst; ++k)
+        if (item >= q->prefix[SP][k] && item < q->prefix[SP][k + 1]) inst = k;
+      s_inst = inst;
+      s_c0 = inst >= 0 ? (long long)(item - q->prefix[SP][inst]) * chunk : 0;
+      // one reading of the status word for the whole CTA (it may change
+      // while the kernel runs; the chunk's barriers need a uniform decision)
+      s_skip = inst >= 0 ? (*(volatile int*)&insts[inst].S->status & ST_FATAL) : 0;
+    }
+    __syncthreads();
+    const int inst = s_inst;
+    // a CTA may find the queue empty on its first fetch (cur == -1 == inst)
+    if (inst != cur || inst < 0) {
+      if (cur >= 0 && sI.S->diag_on) block_add(Kloc, &sI.S->K[SP]);
+      Kloc = 0.0;
+      if (inst < 0) break;
+      // stage the instance's parameters in shared memory
+      const unsigned* src = reinterpret_cast<const unsigned*>(insts + inst);
+      unsigned* dst = reinterpret_cast<unsigned*>(&sI);
+      for (int k = threadIdx.x; k < (int)(sizeof(Inst) / 4); k += blockDim.x) dst[k] = src[k];
+      __syncthreads();
+      cur = inst;
+    }
+    if (!s_skip) Kloc += push_chunk64<SP, GATHER>(sI, s_c0, ppt, patch, anchor);
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -493,7 +557,8 @@ __global__ void k_scatter(Inst I, int sp0) {
   const long long n_old = S->n[sp];
   const long long nb = S->nbirth[sp] < I.birth_cap ? S->nbirth[sp] : I.birth_cap;
   const long long total = n_old + nb;
-  const ParticlesDev src = I.cur[sp], dst = I.nxt[sp];
+  const int fl = S->flip[sp];
+  const ParticlesDev src = I.buf[sp][fl], dst = I.buf[sp][fl ^ 1];
   const BirthsDev B = I.births[sp];
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -530,7 +595,7 @@ __global__ void k_scatter(Inst I, int sp0) {
 __global__ void k_keys(Inst I, int sp) {
   Scalars* S = I.S;
   const long long n = S->n[sp];
-  const ParticlesDev P = I.cur[sp];
+  const ParticlesDev P = I.buf[sp][S->flip[sp]];
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -568,7 +633,10 @@ __global__ void k_keys(Inst I, int sp) {
 
 // n = n_next after a set-up sort (no births)
 __global__ void k_commit_n(Inst I, int sp) {
-  if (threadIdx.x == 0 && !(I.S->status & ST_FATAL)) I.S->n[sp] = I.S->n_next[sp];
+  if (threadIdx.x == 0 && !(I.S->status & ST_FATAL)) {
+    I.S->n[sp] = I.S->n_next[sp];
+    I.S->flip[sp] ^= 1;
+  }
 }
 
 __global__ void k_set_n(Inst I, int sp, long long n) {
@@ -581,7 +649,7 @@ __global__ void k_set_n(Inst I, int sp, long long n) {
 // deposit every particle of the current arrays (global atomics; set-up only)
 __global__ void k_deposit_all(Inst I, int sp) {
   const long long n = I.S->n[sp];
-  const ParticlesDev P = I.cur[sp];
+  const ParticlesDev P = I.buf[sp][I.S->flip[sp]];
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     int m, nn;
@@ -727,6 +795,8 @@ __global__ void k_step_end(Inst I) {
   (void)nb1;
   I.diag->particle_steps = S->pushed + (ok ? S->n[0] + S->n[1] : 0);  // every step
   if (ok) {
+    S->flip[0] ^= 1;   // the scatter wrote the other buffer
+    S->flip[1] ^= 1;
     S->pushed += S->n[0] + S->n[1];
     S->n[0] = S->n_next[0];
     S->n[1] = S->n_next[1];
@@ -739,6 +809,24 @@ __global__ void k_step_end(Inst I) {
   S->W = 0.0;
   S->peak_bits[0] = S->peak_bits[1] = 0ULL;
   S->diag_on = (S->step % (I.diag_every > 0 ? I.diag_every : 1)) == 0;
+}
+
+// Fill the batched push's queue: chunks of `chunk` particles per instance
+// and species (none for an instance whose status is latched).
+__global__ void k_queue_setup(const Inst* insts, WorkQueue* q, int n_inst, long long chunk) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  q->n_inst = n_inst;
+  for (int sp = 0; sp < 2; ++sp) {
+    int acc = 0;
+    q->prefix[sp][0] = 0;
+    for (int k = 0; k < n_inst; ++k) {
+      const Scalars* S = insts[k].S;
+      const long long n = (S->status & ST_FATAL) ? 0 : S->n[sp];
+      acc += (int)((n + chunk - 1) / chunk);
+      q->prefix[sp][k + 1] = acc;
+    }
+    q->next[sp] = 0u;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -763,6 +851,25 @@ static int grid_for(long long work, int threads, int num_sms, int per_sm) {
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (int)g;
+}
+
+cudaError_t launch_queue_setup(const Inst* d_insts, WorkQueue* q, int n_inst, long long chunk,
+                               cudaStream_t st) {
+  k_queue_setup<<<1, 32, 0, st>>>(d_insts, q, n_inst, chunk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_push64_batched(const Inst* d_insts, WorkQueue* q, int sp, int gather, int ppt,
+                                  int num_sms, cudaStream_t st) {
+  if (sp == 0 && gather == 0)
+    k_push_batched<0, 0><<<resident_grid(k_push_batched<0, 0>, kPushThreads, num_sms), kPushThreads, 0, st>>>(d_insts, q, ppt);
+  else if (sp == 0)
+    k_push_batched<0, 1><<<resident_grid(k_push_batched<0, 1>, kPushThreads, num_sms), kPushThreads, 0, st>>>(d_insts, q, ppt);
+  else if (gather == 0)
+    k_push_batched<1, 0><<<resident_grid(k_push_batched<1, 0>, kPushThreads, num_sms), kPushThreads, 0, st>>>(d_insts, q, ppt);
+  else
+    k_push_batched<1, 1><<<resident_grid(k_push_batched<1, 1>, kPushThreads, num_sms), kPushThreads, 0, st>>>(d_insts, q, ppt);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_charge(const Inst& I, cudaStream_t st) {
@@ -809,6 +916,29 @@ cudaError_t launch_solve_fields(const Inst& I, PoissonWork* pw, int num_sms, cud
   k_set_cathode<<<1, 256, 0, st>>>(I);
   return launch_poisson(pw, I.Q, I.phi, I.poisson_tol, I.poisson_max_iter, &I.S->status,
                         &I.S->poisson_iters, &I.S->poisson_resid, st);
+}
+
+cudaError_t launch_field_tables(const Inst& I, int num_sms, cudaStream_t st) {
+  k_field_tables<<<grid_for(I.nr * I.nz, 256, num_sms, 8), 256, 0, st>>>(I);
+  return cudaGetLastError();
+}
+
+// births, scan, scatter, charge and circuit of one instance (after its push)
+cudaError_t launch_post_push(const Inst& I, int num_sms, cudaStream_t st) {
+  if (I.prec32) launch_births32(I, st);
+  else k_births<<<1, 1024, 0, st>>>(I);
+  k_scan<<<2, 1024, 0, st>>>(I, 0);
+  if (I.prec32) launch_scatter32(I, num_sms, st);
+  else k_scatter<<<dim3(num_sms * 8, 2), 256, 0, st>>>(I, 0);
+  cudaError_t e = launch_charge(I, st);
+  if (e != cudaSuccess) return e;
+  k_circuit<<<1, 256, 0, st>>>(I);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_end(const Inst& I, cudaStream_t st) {
+  k_step_end<<<1, 32, 0, st>>>(I);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_step(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_t st,

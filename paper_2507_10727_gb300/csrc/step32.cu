@@ -27,12 +27,14 @@ constexpr int kPZ32 = 2 * kTile + 2 * kHalo32 + 1;
 constexpr float kHalfMeOverE = (float)(0.5 * kMe / kQe);   // E[eV] = kHalfMeOverE v^2
 constexpr float kTwoEOverMe = (float)(2.0 * kQe / kMe);    // v^2 = kTwoEOverMe E[eV]
 
-__device__ __forceinline__ void key_to_mn(const Inst& I, int key, int& m, int& n) {
-  const int tile = key >> 6, within = key & 63;
-  const int tm = tile / I.ntz, tn = tile - tm * I.ntz;
-  m = (tm << 3) + (within >> 3);
-  n = (tn << 3) + (within & 7);
+// The record's cell word holds (m << 16) | n; all ones marks a removed
+// particle.  The sort key (8 x 8 tile-major) is derived from it.
+constexpr unsigned kDead = 0xffffffffu;
+__device__ __forceinline__ void cell_mn(unsigned c, int& m, int& n) {
+  m = (int)(c >> 16);
+  n = (int)(c & 0xffffu);
 }
+__device__ __forceinline__ unsigned pack_mn(int m, int n) { return ((unsigned)m << 16) | (unsigned)n; }
 
 __device__ __forceinline__ float rweight_upper32(const Inst& I, float dr, int m) {
   if (I.rweight == 0) return dr;
@@ -69,7 +71,7 @@ __device__ void add_birth32(const Inst& I, int sp, unsigned long long pkey, int 
   const int key = cell_key(I, m, n);
   const BirthsDev& B = I.births[sp];
   B.a32[b] = make_float4(dr, dz, vr, vt);
-  B.b32[b] = make_uint4(__float_as_uint(vz), (unsigned)key, 0u, 0u);
+  B.b32[b] = make_uint4(__float_as_uint(vz), pack_mn(m, n), 0u, 0u);
   B.pkey[b] = pkey;
   atomicAdd(&I.counts[sp][key], 1);
   deposit_global32(I, sp, m, n, rweight_upper32(I, dr, m), dz);
@@ -158,46 +160,44 @@ __device__ void mcc_electron32(const Inst& I, long long id, long long step, int 
 // The FP32 push: gather + Boris + move + walls + SEY + MCC + deposit, state
 // rewritten in place with the new cell key (read by the scatter).
 // ---------------------------------------------------------------------------
+// Push the chunk of `ppt * blockDim.x` particles starting at c0 (whole CTA);
+// `patch` is the CTA's zeroed deposit patch, flushed and zeroed on return.
 template <int SP, int GATHER>
-__global__ void __launch_bounds__(kPush32Threads, 4) k_push32(Inst I) {
+__device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patch, int* anchor) {
   Scalars* S = I.S;
-  if (S->status & ST_FATAL) return;
-  __shared__ float patch[kPR32 * kPZ32];
-  __shared__ int anchor[2];
   const long long n = S->n[SP];
   const long long step = S->step;
   const bool diag = S->diag_on != 0;
-  const Particles32 P = I.cur32[SP];
+  const Particles32 P = I.buf32[SP][S->flip[SP]];
   const float h = I.hq32[SP], kr = I.kr32, kz = I.kz32;
   const float rc_cells = (float)(I.Rc * I.inv_dr);
   const int lane = threadIdx.x & 31;
   double Kloc = 0.0;
-  for (int k = threadIdx.x; k < kPR32 * kPZ32; k += blockDim.x) patch[k] = 0.0f;
-  for (long long c0 = (long long)blockIdx.x * kChunk32; c0 < n;
-       c0 += (long long)gridDim.x * kChunk32) {
+  {
     if (threadIdx.x == 0) {
       int m, nn;
-      key_to_mn(I, (int)P.b[c0].y, m, nn);
+      cell_mn(P.b[c0].y, m, nn);
       anchor[0] = (m & ~(kTile - 1)) - kHalo32;
       anchor[1] = (nn & ~(kTile - 1)) - kHalo32;
     }
     __syncthreads();
     const int pm0 = anchor[0], pn0 = anchor[1];
 #pragma unroll 1
-    for (int j = 0; j < kPPT32; ++j) {
-      const long long i = c0 + (long long)j * kPush32Threads + threadIdx.x;
-      int newkey = -1;
+    for (int j = 0; j < ppt; ++j) {
+      const long long i = c0 + (long long)j * blockDim.x + threadIdx.x;
+      int newkey = -1, dm = 0, dn = 0;
+      float w00 = 0.0f, w10 = 0.0f, w01 = 0.0f, w11 = 0.0f;
       if (i < n) {
         const float4 a = P.a[i];
         const uint4 b = P.b[i];
         int m, nn;
-        key_to_mn(I, (int)b.y, m, nn);
+        cell_mn(b.y, m, nn);
         const float dr = a.x, dz = a.y;
         float vr = a.z, vt = a.w, vz = __uint_as_float(b.x);
         const float v2old = vr * vr + vt * vt + vz * vz;
         float rho = dr, zeta = dz, X = (float)m + dr, y = 0.0f;
         if (I.push_on) {
-          const int ck = (int)b.y;
+          const int ck = cell_key(I, m, nn);
           const float wr = rweight_upper32(I, dr, m);
           float Er, Ez;
           if (GATHER == 0) {
@@ -301,20 +301,35 @@ __global__ void __launch_bounds__(kPush32Threads, 4) k_push32(Inst I) {
           if (SP == 0 && I.mcc_on) mcc_electron32(I, id_of(b), step, m1, dr1, n1, dz1, vr, vt, vz);
           newkey = cell_key(I, m1, n1);
           P.a[i] = make_float4(dr1, dz1, vr, vt);
-          P.b[i] = make_uint4(__float_as_uint(vz), (unsigned)newkey, b.z, b.w);
+          P.b[i] = make_uint4(__float_as_uint(vz), pack_mn(m1, n1), b.z, b.w);
           const float wr1 = rweight_upper32(I, dr1, m1), wz1 = dz1;
-          const int lm = m1 - pm0, ln = n1 - pn0;
-          if (lm >= 0 && lm + 1 < kPR32 && ln >= 0 && ln + 1 < kPZ32) {
-            float* p = patch + lm * kPZ32 + ln;
-            atomicAdd(p, (1.0f - wr1) * (1.0f - wz1));
-            atomicAdd(p + kPZ32, wr1 * (1.0f - wz1));
-            atomicAdd(p + 1, (1.0f - wr1) * wz1);
-            atomicAdd(p + kPZ32 + 1, wr1 * wz1);
-          } else {
-            deposit_global32(I, SP, m1, n1, wr1, wz1);
-          }
+          w00 = (1.0f - wr1) * (1.0f - wz1);
+          w10 = wr1 * (1.0f - wz1);
+          w01 = (1.0f - wr1) * wz1;
+          w11 = wr1 * wz1;
+          dm = m1;
+          dn = n1;
         } else {
-          reinterpret_cast<unsigned int*>(P.b + i)[1] = 0xffffffffu;   // key = -1
+          reinterpret_cast<unsigned int*>(P.b + i)[1] = kDead;
+        }
+      }
+      // deposit: sum the weights of neighbouring lanes in the same cell, then
+      // one shared-memory (or global) atomic per node and run
+      if (run_sum4(newkey, w00, w10, w01, w11) && newkey >= 0) {
+        const int lm = dm - pm0, ln = dn - pn0;
+        if (lm >= 0 && lm + 1 < kPR32 && ln >= 0 && ln + 1 < kPZ32) {
+          float* p = patch + lm * kPZ32 + ln;
+          atomicAdd(p, w00);
+          atomicAdd(p + kPZ32, w10);
+          atomicAdd(p + 1, w01);
+          atomicAdd(p + kPZ32 + 1, w11);
+        } else {
+          double* q = I.qacc64[SP];
+          const int gi = node_index(I, dm, dn), nz1 = I.nz + 1;
+          atomicAdd(q + gi, (double)w00);
+          atomicAdd(q + gi + nz1, (double)w10);
+          atomicAdd(q + gi + 1, (double)w01);
+          atomicAdd(q + gi + nz1 + 1, (double)w11);
         }
       }
       const unsigned peers = __match_any_sync(0xffffffffu, newkey);
@@ -331,7 +346,68 @@ __global__ void __launch_bounds__(kPush32Threads, 4) k_push32(Inst I) {
     }
     __syncthreads();
   }
-  if (diag) block_add(Kloc, &I.S->K[SP]);
+  return diag ? Kloc : 0.0;
+}
+
+template <int SP, int GATHER>
+__global__ void __launch_bounds__(kPush32Threads, 4) k_push32(Inst I) {
+  Scalars* S = I.S;
+  __shared__ float patch[kPR32 * kPZ32];
+  __shared__ int anchor[2];
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = *(volatile int*)&S->status & ST_FATAL;
+  __syncthreads();
+  if (s_skip) return;   // the whole CTA, so that no barrier is left short
+  for (int k = threadIdx.x; k < kPR32 * kPZ32; k += blockDim.x) patch[k] = 0.0f;
+  const long long n = S->n[SP];
+  double Kloc = 0.0;
+  for (long long c0 = (long long)blockIdx.x * kChunk32; c0 < n; c0 += (long long)gridDim.x * kChunk32)
+    Kloc += push_chunk32<SP, GATHER>(I, c0, kPPT32, patch, anchor);
+  if (S->diag_on) block_add(Kloc, &S->K[SP]);
+}
+
+// Ensemble: persistent CTAs take (instance, chunk) items from a device queue.
+template <int SP, int GATHER>
+__global__ void __launch_bounds__(kPush32Threads, 4) k_push32_batched(const Inst* insts,
+                                                                      WorkQueue* q, int ppt) {
+  __shared__ float patch[kPR32 * kPZ32];
+  __shared__ int anchor[2];
+  __shared__ Inst sI;
+  __shared__ int s_inst;
+  __shared__ long long s_c0;
+  __shared__ int s_skip;
+  for (int k = threadIdx.x; k < kPR32 * kPZ32; k += blockDim.x) patch[k] = 0.0f;
+  int cur = -1;
+  double Kloc = 0.0;
+  const long long chunk = (long long)ppt * blockDim.x;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int item = (int)atomicAdd(&q->next[SP], 1u);
+      int inst = -1;
+      for (int k = 0; k < q->n_inst; ++k)
+        if (item >= q->prefix[SP][k] && item < q->prefix[SP][k + 1]) inst = k;
+      s_inst = inst;
+      s_c0 = inst >= 0 ? (long long)(item - q->prefix[SP][inst]) * chunk : 0;
+      // one reading of the status word for the whole CTA (it may change
+      // while the kernel runs; the chunk's barriers need a uniform decision)
+      s_skip = inst >= 0 ? (*(volatile int*)&insts[inst].S->status & ST_FATAL) : 0;
+    }
+    __syncthreads();
+    const int inst = s_inst;
+    // a CTA may find the queue empty on its first fetch (cur == -1 == inst)
+    if (inst != cur || inst < 0) {
+      if (cur >= 0 && sI.S->diag_on) block_add(Kloc, &sI.S->K[SP]);
+      Kloc = 0.0;
+      if (inst < 0) break;
+      const unsigned* src = reinterpret_cast<const unsigned*>(insts + inst);
+      unsigned* dst = reinterpret_cast<unsigned*>(&sI);
+      for (int k = threadIdx.x; k < (int)(sizeof(Inst) / 4); k += blockDim.x) dst[k] = src[k];
+      __syncthreads();
+      cur = inst;
+    }
+    if (!s_skip) Kloc += push_chunk32<SP, GATHER>(sI, s_c0, ppt, patch, anchor);
+    __syncthreads();
+  }
 }
 
 // births: sort by (parent id, kind), ids into the records' id words
@@ -379,7 +455,8 @@ __global__ void k_scatter32(Inst I, int sp0) {
   const long long n_old = S->n[sp];
   const long long nb = S->nbirth[sp] < I.birth_cap ? S->nbirth[sp] : I.birth_cap;
   const long long total = n_old + nb;
-  const Particles32 src = I.cur32[sp], dst = I.nxt32[sp];
+  const int fl = S->flip[sp];
+  const Particles32 src = I.buf32[sp][fl], dst = I.buf32[sp][fl ^ 1];
   const BirthsDev B = I.births[sp];
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -387,7 +464,7 @@ __global__ void k_scatter32(Inst I, int sp0) {
   for (long long base = warp * 32; base < total; base += nwarp * 32) {
     const long long i = base + lane;
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-    uint4 b = make_uint4(0u, 0xffffffffu, 0u, 0u);
+    uint4 b = make_uint4(0u, kDead, 0u, 0u);
     if (i < n_old) {
       a = src.a[i];
       b = src.b[i];
@@ -395,7 +472,12 @@ __global__ void k_scatter32(Inst I, int sp0) {
       a = B.a32[i - n_old];
       b = B.b32[i - n_old];
     }
-    const int key = (int)b.y;
+    int key = -1;
+    if (b.y != kDead) {
+      int m, nn;
+      cell_mn(b.y, m, nn);
+      key = cell_key(I, m, nn);
+    }
     const unsigned peers = __match_any_sync(0xffffffffu, key);
     const int leader = __ffs(peers) - 1;
     int pos0 = 0;
@@ -415,7 +497,7 @@ __global__ void k_pack32(Inst I, int sp, long long offset, long long count, cons
                          const double* z, const double* vr, const double* vt, const double* vz,
                          const long long* id) {
   Scalars* S = I.S;
-  const Particles32 P = I.cur32[sp];
+  const Particles32 P = I.buf32[sp][S->flip[sp]];
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -428,7 +510,7 @@ __global__ void k_pack32(Inst I, int sp, long long offset, long long count, cons
       const double rr = r[k], zz = z[k];
       const long long pid = id[k];
       float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-      uint4 b = make_uint4(0u, 0xffffffffu, 0u, 0u);
+      uint4 b = make_uint4(0u, kDead, 0u, 0u);
       if (rr >= 0.0 && rr < I.R && zz >= 0.0 && zz < I.L && finite64(vr[k]) && finite64(vt[k]) &&
           finite64(vz[k]) && pid >= 0) {
         int m, nn;
@@ -440,7 +522,7 @@ __global__ void k_pack32(Inst I, int sp, long long offset, long long count, cons
         if (dz >= 1.0f) dz = nextafterf(1.0f, 0.0f);
         key = cell_key(I, m, nn);
         a = make_float4(dr, dz, (float)vr[k], (float)vt[k]);
-        b = make_uint4(__float_as_uint((float)vz[k]), (unsigned)key,
+        b = make_uint4(__float_as_uint((float)vz[k]), pack_mn(m, nn),
                        (unsigned)((unsigned long long)pid & 0xffffffffULL),
                        (unsigned)((unsigned long long)pid >> 32));
         idmax = pid > idmax ? pid : idmax;
@@ -465,13 +547,13 @@ __global__ void k_pack32(Inst I, int sp, long long offset, long long count, cons
 // FP32 records [offset, offset + count) of cur32 -> FP64 SoA
 __global__ void k_unpack32(Inst I, int sp, long long offset, long long count, double* r, double* z,
                            double* vr, double* vt, double* vz, long long* id) {
-  const Particles32 P = I.cur32[sp];
+  const Particles32 P = I.buf32[sp][I.S->flip[sp]];
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < count;
        k += (long long)gridDim.x * blockDim.x) {
     const float4 a = P.a[offset + k];
     const uint4 b = P.b[offset + k];
     int m, nn;
-    key_to_mn(I, (int)b.y, m, nn);
+    cell_mn(b.y, m, nn);
     if (r) r[k] = ((double)m + (double)a.x) * I.dr;
     if (z) z[k] = ((double)nn + (double)a.y) * I.dz;
     if (vr) vr[k] = (double)a.z;
@@ -483,12 +565,12 @@ __global__ void k_unpack32(Inst I, int sp, long long offset, long long count, do
 
 __global__ void k_deposit_all32(Inst I, int sp) {
   const long long n = I.S->n[sp];
-  const Particles32 P = I.cur32[sp];
+  const Particles32 P = I.buf32[sp][I.S->flip[sp]];
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const float4 a = P.a[i];
     int m, nn;
-    key_to_mn(I, (int)P.b[i].y, m, nn);
+    cell_mn(P.b[i].y, m, nn);
     deposit_global32(I, sp, m, nn, rweight_upper32(I, a.x, m), a.y);
   }
 }
@@ -554,6 +636,32 @@ cudaError_t launch_push32(const Inst& I, int sp, int num_sms, cudaStream_t st) {
     if (I.gather == 0) k_push32<1, 0><<<one_wave(k_push32<1, 0>, num_sms), kPush32Threads, 0, st>>>(I);
     else k_push32<1, 1><<<one_wave(k_push32<1, 1>, num_sms), kPush32Threads, 0, st>>>(I);
   }
+  return cudaGetLastError();
+}
+
+template <typename K>
+static int one_wave_batched(K kernel, int num_sms) {
+  static int per = 0;
+  if (per == 0) {
+    int p = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kernel, kPush32Threads, 0) != cudaSuccess ||
+        p < 1)
+      p = 1;
+    per = p;
+  }
+  return per * num_sms;
+}
+
+cudaError_t launch_push32_batched(const Inst* d_insts, WorkQueue* q, int sp, int gather, int ppt,
+                                  int num_sms, cudaStream_t st) {
+  if (sp == 0 && gather == 0)
+    k_push32_batched<0, 0><<<one_wave_batched(k_push32_batched<0, 0>, num_sms), kPush32Threads, 0, st>>>(d_insts, q, ppt);
+  else if (sp == 0)
+    k_push32_batched<0, 1><<<one_wave_batched(k_push32_batched<0, 1>, num_sms), kPush32Threads, 0, st>>>(d_insts, q, ppt);
+  else if (gather == 0)
+    k_push32_batched<1, 0><<<one_wave_batched(k_push32_batched<1, 0>, num_sms), kPush32Threads, 0, st>>>(d_insts, q, ppt);
+  else
+    k_push32_batched<1, 1><<<one_wave_batched(k_push32_batched<1, 1>, num_sms), kPush32Threads, 0, st>>>(d_insts, q, ppt);
   return cudaGetLastError();
 }
 

@@ -119,6 +119,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         L.pic_set_next_id.argtypes = [vp, C.c_int, C.c_int64]
         L.pic_get_next_id.argtypes = [vp, C.c_int, _I64]
         L.pic_step.argtypes = [vp, C.c_int64]
+        L.pic_uses_graph.argtypes = [vp]
+        L.pic_tuned_chunk.argtypes = [vp, C.POINTER(C.c_int)]
         L.pic_sync.argtypes = [vp]
         L.pic_diagnostics.argtypes = [vp, C.c_int, C.POINTER(PicDiag)]
         L.pic_save.argtypes = [vp, C.c_int, C.c_char_p]
@@ -298,6 +300,16 @@ def pic_get_next_id(h: Handle, instance: int = 0) -> int:
 
 def pic_step(h: Handle, nsteps: int = 1):
     _check(h, load_library().pic_step(h.ptr, nsteps))
+
+
+def pic_uses_graph(h: Handle) -> bool:
+    return bool(load_library().pic_uses_graph(h.ptr))
+
+
+def pic_tuned_chunk(h: Handle) -> int:
+    v = C.c_int()
+    _check(h, load_library().pic_tuned_chunk(h.ptr, C.byref(v)))
+    return v.value
 
 
 def pic_sync(h: Handle):

@@ -1,0 +1,115 @@
+"""The batched ensemble (one handle, several independent discharges) against
+the same discharges run one by one.
+
+In FP64 mode every result of a step is independent of the order in which the
+particles are processed (the deposit is an exact integer sum, births are
+ordered by parent id), so the ensemble must reproduce the single-instance runs
+bit for bit -- including while the autotuner switches chunk sizes and after
+the step is captured into a CUDA graph.  The single-instance path is itself
+checked against the oracle in test_gpu_parity.py; instance 0's first step is
+checked against the oracle here as well.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import pic_inputs
+from parity import PARTICLE_TOL, busy_state, compare_species, sort_by_id
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2507_10727_gb300 as pg
+    return pg
+
+
+def _instances(precision=0):
+    out = []
+    for k, (gamma, rext, ppc) in enumerate([(0.05, 50.0, 3), (0.1, 100.0, 9), (0.2, 200.0, 5),
+                                            (0.3, 400.0, 14)]):
+        p = pic_inputs.params_rz32(gather=0, precision=precision)
+        p.update(nr=32, nz=48, R=0.02, L=0.03, Rc=0.015, gamma_i=gamma, circuit_mode=1,
+                 Vs=400.0, Rext=rext, n_avg=4, seed=7 + k, poisson_tol=1e-12)
+        p, parts = busy_state(p, ppc=ppc, seed=100 + k)
+        p = pic_inputs.with_capacity(p, parts, factor=2.0)
+        out.append((p, parts))
+    return out
+
+
+def _load(pg, h, k, parts):
+    for key, sp in (("e", 0), ("i", 1)):
+        pg.pic_set_particles(h, k, sp, parts[key])
+
+
+@pytest.mark.parametrize("side_stream", [False, True])
+def test_ensemble_equals_individual_runs(pg, side_stream):
+    import torch
+    insts = _instances()
+    steps = 7
+    stream = torch.cuda.Stream() if side_stream else torch.cuda.current_stream()
+    with torch.cuda.stream(stream):
+        ens = pg.pic_create([p for p, _ in insts])
+        for k, (p, parts) in enumerate(insts):
+            _load(pg, ens, k, parts)
+            pg.pic_solve_fields(ens, k)
+        pg.pic_step(ens, steps)
+        pg.pic_sync(ens)
+        assert pg.pic_tuned_chunk(ens) in (2, 4, 8, 16)
+        if side_stream:
+            assert pg.pic_uses_graph(ens)
+        for k, (p, parts) in enumerate(insts):
+            one = pg.pic_create(p)
+            _load(pg, one, 0, parts)
+            pg.pic_solve_fields(one, 0)
+            pg.pic_step(one, steps)
+            for sp in (0, 1):
+                a = sort_by_id(pg.pic_get_particles(ens, k, sp))
+                b = sort_by_id(pg.pic_get_particles(one, 0, sp))
+                for q in a:
+                    assert np.array_equal(a[q], b[q]), (k, sp, q)
+            fa, fb = pg.pic_get_fields(ens, k), pg.pic_get_fields(one, 0)
+            assert np.array_equal(fa["phi"], fb["phi"])
+            da, db = pg.pic_diagnostics(ens, k), pg.pic_diagnostics(one, 0)
+            for key in ("N_e", "N_i", "V_cath", "I_cath", "n_sey", "n_ionize", "step"):
+                assert da[key] == db[key], (k, key)
+    stream.synchronize()
+
+
+def test_ensemble_first_step_matches_oracle(pg):
+    insts = _instances()
+    ens = pg.pic_create([p for p, _ in insts])
+    orcs = []
+    for k, (p, parts) in enumerate(insts):
+        _load(pg, ens, k, parts)
+        orc = oracle.Oracle(p, parts)
+        pg.pic_set_phi(ens, k, orc.fields()["phi"])
+        orcs.append(orc)
+    pg.pic_step(ens, 1)
+    for k, orc in enumerate(orcs):
+        orc.step(1)
+        for sp in (0, 1):
+            err = compare_species(pg.pic_get_particles(ens, k, sp), orc.get_particles(sp))
+            assert err["pos"] <= PARTICLE_TOL and err["vel"] <= PARTICLE_TOL, (k, sp, err)
+
+
+def test_ensemble_fp32_runs_and_tracks_fp64(pg):
+    insts64 = _instances(0)
+    insts32 = _instances(1)
+    e64 = pg.pic_create([p for p, _ in insts64])
+    e32 = pg.pic_create([p for p, _ in insts32])
+    for k in range(len(insts64)):
+        _load(pg, e64, k, insts64[k][1])
+        _load(pg, e32, k, insts32[k][1])
+        pg.pic_solve_fields(e64, k)
+        pg.pic_solve_fields(e32, k)
+    pg.pic_step(e64, 5)
+    pg.pic_step(e32, 5)
+    for k in range(len(insts64)):
+        a, b = pg.pic_diagnostics(e32, k), pg.pic_diagnostics(e64, k)
+        assert a["status"] == 0
+        assert abs(a["N_e"] - b["N_e"]) <= max(2, 1e-4 * b["N_e"])
+        assert a["W_field"] == pytest.approx(b["W_field"], rel=1e-3)

@@ -227,3 +227,21 @@ def test_capacity_and_nonconvergence_latch(pg):
     with pytest.raises(pg.PicError) as ei:
         pg.pic_sync(h)
     assert ei.value.code == -4
+
+
+def test_graph_replay_matches_oracle(pg):
+    """On a side stream pic_step captures one step into a CUDA graph and
+    replays it; the replayed steps match the oracle like eager ones."""
+    import torch
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        p = pic_inputs.params_rz32(gather=0)
+        p.update(gamma_i=0.5, poisson_tol=1e-13, circuit_mode=1, Vs=400.0, Rext=100.0, n_avg=3)
+        p, parts = busy_state(p, ppc=8, seed=41)
+        p, orc, h = _pair(pg, p, parts)
+        for _ in range(3):
+            orc.step(1)
+            pg.pic_step(h, 1)
+            assert pg.pic_uses_graph(h)
+            _check_step(pg, h, orc)
+    side.synchronize()
