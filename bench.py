@@ -68,9 +68,17 @@ def parse():
     ap.add_argument("--cpu-sample", type=float, default=8e6,
                     help="oracle sample size per species for the CPU baseline")
     ap.add_argument("--cpu-steps", type=int, default=8)
-    ap.add_argument("--workload", default="rz256", choices=["rz256", "sweep16"],
+    ap.add_argument("--workload", default="rz256", choices=["rz256", "sweep16", "learned"],
                     help="rz256: one 256x256 discharge; sweep16: the 16-discharge "
-                         "SEY x R_ext ensemble on 128x128 grids")
+                         "SEY x R_ext ensemble on 128x128 grids; learned: the 256x512 "
+                         "discharge with and without the learned Poisson warm start")
+    ap.add_argument("--unet-mode", type=int, default=1, choices=[0, 1],
+                    help="learned: 0 = network maps (rho, r, V) to phi; 1 = network maps the "
+                         "previous solution's residual to the change of phi")
+    ap.add_argument("--snapshots", type=int, default=512,
+                    help="learned: recorded steps (one snapshot per step)")
+    ap.add_argument("--train-iters", type=int, default=1000)
+    ap.add_argument("--train-batch", type=int, default=8)
     return ap.parse_args()
 
 
@@ -294,6 +302,81 @@ def run_sweep(args, torch, pg):
 
 
 # ---------------------------------------------------------------------------
+# learned warm start workload: 256 x 512 cells, 10 cm long, 5e7 per species
+# ---------------------------------------------------------------------------
+def run_learned(args, torch, pg):
+    g = 0 if args.gather == "ec" else 1
+    n = int(args.n_per_species) if args.n_per_species != 4e7 else int(5e7)
+    p = pic_inputs.params_rz256x512(gather=g, seed=args.seed)
+    p, parts = pic_inputs.grown_ring_state(p, n, seed=args.seed)
+    p = pic_inputs.with_capacity(p, parts, factor=1.25, births=1 << 20)
+    p["diag_every"] = 10
+    p["precision"] = 1 if args.precision == "fp32" else 0
+    h = pg.pic_create(p)
+    for k, sp in (("e", 0), ("i", 1)):
+        pg.pic_set_particles(h, 0, sp, parts[k])
+    del parts
+    pg.pic_solve_fields(h, 0)
+    pg.pic_unet_create(h, args.seed + 1, args.train_batch, args.unet_mode)
+    # training data: one snapshot per step of the run itself
+    pg.pic_unet_snapshots(h, args.snapshots, 1)
+    t0 = time.perf_counter()
+    pg.pic_step(h, args.snapshots)
+    pg.pic_sync(h)
+    t_rec = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss0, loss1 = pg.pic_unet_train(h, args.train_iters, args.train_batch, 2e-3, args.seed + 7)
+    t_train = time.perf_counter() - t0
+
+    def measure(on: bool):
+        pg.pic_unet_warm_start(h, on)
+        pg.pic_step(h, args.warmup)
+        pg.pic_sync(h)
+        s0, d0 = pg.pic_unet_stats(h), pg.pic_diagnostics(h, 0)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        pg.pic_step(h, args.steps)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        s1, d1 = pg.pic_unet_stats(h), pg.pic_diagnostics(h, 0)
+        pg.pic_profile(h, True)
+        pg.pic_step(h, 10)
+        prof = pg.pic_profile_read(h)
+        pg.pic_profile(h, False)
+        nprof = max(1, prof["push_e"]["launches"])
+        return {"value": (d1["particle_steps"] - d0["particle_steps"]) / (ms / 1e3),
+                "ms_per_step": ms / args.steps,
+                "poisson_iters_per_step": (s1["poisson_iters"] - s0["poisson_iters"]) / args.steps,
+                "starts": {k: s1[k] - s0[k] for k in ("starts_previous", "starts_network",
+                                                       "starts_zero")},
+                "poisson_ms_per_step": prof["poisson"]["total_ms"] / nprof,
+                "warm_start_ms_per_step": prof["warm_start"]["total_ms"] / nprof,
+                "cuda_graph": pg.pic_uses_graph(h)}
+
+    plain = measure(False)
+    warm = measure(True)
+    line = {"metric": METRIC, "value": warm["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": warm["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+            "config": {"workload": f"learned_rz256x512_{n:.0e}_per_species_mode{args.unet_mode}_"
+                                   f"{args.precision}".replace("+", ""),
+                       "grid": [p["nr"], p["nz"]], "domain_m": [p["R"], p["L"]],
+                       "n_per_species": n, "unet_mode": args.unet_mode,
+                       "snapshots": args.snapshots, "train_iters": args.train_iters,
+                       "train_batch": args.train_batch, "poisson_tol": p["poisson_tol"],
+                       "l2": "inputs larger than L2"},
+            "plain": plain, "warm": warm,
+            "training": {"loss_first": loss0, "loss_last": loss1, "seconds": t_train,
+                         "record_seconds": t_rec, "stats": pg.pic_unet_stats(h)}}
+    print(json.dumps(line), flush=True)
+    pg.pic_destroy(h)
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def main():
@@ -326,6 +409,8 @@ def main():
     torch.cuda.set_stream(side)
     if args.workload == "sweep16":
         return run_sweep(args, torch, pg)
+    if args.workload == "learned":
+        return run_learned(args, torch, pg)
 
     p, parts = workload(args)
     n = int(args.n_per_species)

@@ -80,7 +80,8 @@ typedef struct pic_config {
   int32_t n_avg;             /* steps in the running mean of the cathode current */
   int32_t gather;            /* 0: EC-PIC, 1: MC-PIC (Section 2) */
   int32_t rweight;           /* 0: tent in r; 1: tent in r^2 (volume weighting) */
-  int32_t precision;         /* 0: FP64 particles (the only value accepted by this build) */
+  int32_t precision;         /* 0: FP64 particles; 1: FP32 particles (cell index + FP32 offsets,
+                                FP32 push/deposit, FP64 field solve, circuit and reductions) */
   int32_t mcc_on, push_on, field_on, walls_reflect; /* 1,1,1,0 for the physical model */
   uint64_t seed;             /* Philox key word 0 */
   double sigma_el;           /* elastic cross section (m^2) */
@@ -213,7 +214,8 @@ int pic_load(pic_handle* h, int instance, const char* path);
  * recording, pic_profile(h, 0) stops.  pic_profile_read synchronises and
  * fills up to `max` records (names are static strings: "field_tables",
  * "push_e", "push_i", "births", "scan", "scatter", "charge", "circuit",
- * "poisson", "step_end"); *n_out is the number of kernel groups. */
+ * "poisson", "step_end", "warm_start"); *n_out is the number of kernel
+ * groups. */
 typedef struct pic_kernel_time {
   const char* name;
   int64_t launches;
@@ -221,6 +223,93 @@ typedef struct pic_kernel_time {
 } pic_kernel_time;
 int pic_profile(pic_handle* h, int enable);
 int pic_profile_read(pic_handle* h, pic_kernel_time* out, int max, int* n_out);
+
+/* ---------------------------------------------------------------------------
+ * Learned warm start of the Poisson solve (single-instance handles).
+ *
+ * A small U-Net, trained on the GPU on snapshots the simulation records,
+ * proposes where each Poisson solve starts.  Network: 4 levels of
+ * ((nr >> l) + 1) x ((nz >> l) + 1) nodes, channels 16, 32, 64, 64; two 3x3
+ * convolutions (zero padding, ReLU) per level and stage; even nodes down,
+ * bilinear node interpolation up, [up, skip] concatenation; 1x1 head.
+ * 302,849 parameters, FP32 master copy, BF16 tensor-core arithmetic with FP32
+ * accumulation.  Parameter vector order: for each layer enc0a, enc0b, enc1a,
+ * enc1b, enc2a, enc2b, enc3a, enc3b, dec2a, dec2b, dec1a, dec1b, dec0a, dec0b,
+ * head: weights (cout, cin, kh, kw) row-major, then biases.
+ *
+ * Two readings of what the network maps (chosen at pic_unet_create):
+ *   mode 0 (potential):  x0 = rho / in_norm (rho = Q / V), x1 = r / R,
+ *                        x2 = Dirichlet value / V_ref on z = 0, z = L, r = R
+ *                        (0 elsewhere)  ->  phi / V_ref;
+ *                        V_ref = |V_s| (circuit_mode 1) or |Vc_fixed|.
+ *   mode 1 (correction): x0 = res / in_norm with res = Q - A phi_prev (this
+ *                        step's charge and electrode values against the
+ *                        previous solution), x1 = r / R, x2 = 1 on Dirichlet
+ *                        nodes  ->  (phi - phi_prev) / out_norm.
+ * in_norm (and out_norm in mode 1) are the RMS of the recorded fields, fixed
+ * by the first pic_unet_train call.
+ *
+ * With the warm start on, the network's candidate (mode 0: V_ref y; mode 1:
+ * phi_prev + out_norm y, on the free nodes) is smoothed by two red-black
+ * Gauss-Seidel sweeps of the FP64 operator, and the solve starts from
+ * whichever of {phi_prev, candidate, zero} has the smallest residual
+ * ||Q - A x||_2.  The solve still runs to poisson_tol: only the iteration
+ * count (and time) changes, never the tolerance phi is solved to.
+ * ------------------------------------------------------------------------- */
+
+/* Number of network parameters (302849). */
+int pic_unet_param_count(int64_t* n);
+
+/* Attach a network to a single-instance handle (nr, nz divisible by 8).
+ * He-normal weights from `seed`, zero biases; max_batch = largest batch of
+ * pic_unet_loss_grad / pic_unet_train; mode 0 or 1 (see above).  Allocates
+ * through the handle's allocator.  Synchronous.  PIC_ERR_INVALID for
+ * ensembles, other grids, another mode or a second call. */
+int pic_unet_create(pic_handle* h, uint64_t seed, int max_batch, int mode);
+
+/* Set / get the FP32 parameter vector (host, n = pic_unet_param_count). */
+int pic_unet_set_params(pic_handle* h, const float* params, int64_t n);
+int pic_unet_get_params(pic_handle* h, float* params, int64_t n);
+
+/* Forward pass on `batch` inputs and, when y != NULL, the mean squared error
+ * against y and its gradient with respect to every parameter.  Host arrays:
+ *   x    (batch, 3, nr+1, nz+1) network inputs (already normalised)
+ *   y    (batch, nr+1, nz+1) targets, or NULL (forward only)
+ *   out  (batch, nr+1, nz+1) network output, or NULL
+ *   grad parameter-vector gradient, or NULL; loss: mean squared error, or NULL.
+ * Parameters are not changed.  Synchronous. */
+int pic_unet_loss_grad(pic_handle* h, int batch, const float* x, const float* y, float* out,
+                       float* grad, double* loss);
+
+/* Record the training pairs of every `every`-th step into a device ring of
+ * `capacity` snapshots of two FP32 node fields (8 (nr+1)(nz+1) bytes per
+ * snapshot): mode 0 (rho, phi) after the solve; mode 1 (res, phi - phi_prev)
+ * around it.  Recording continues in later pic_step calls.  Synchronous. */
+int pic_unet_snapshots(pic_handle* h, int64_t capacity, int every);
+
+/* `iters` Adam steps (beta 0.9, 0.999) of learning rate lr on batches of
+ * `batch` snapshots drawn from the ring by a hash of (seed, iteration,
+ * index); targets as the mode defines.  *loss_first and *loss_last (may be NULL)
+ * receive the training loss of the first and the last batch.  Synchronous. */
+int pic_unet_train(pic_handle* h, int iters, int batch, float lr, uint64_t seed,
+                   double* loss_first, double* loss_last);
+
+/* Turn the warm start of later pic_step solves on (1) or off (0). */
+int pic_unet_warm_start(pic_handle* h, int on);
+
+/* Counters since pic_unet_create (synchronous). */
+typedef struct pic_unet_stats {
+  int64_t snapshots;           /* snapshots recorded */
+  int64_t starts_previous;     /* solves started from the previous phi */
+  int64_t starts_network;      /* solves started from the network's guess */
+  int64_t starts_zero;         /* solves started from zero */
+  int64_t poisson_iters;       /* PCG iterations summed over steps */
+  double in_norm;              /* input scale of channel 0 (0 until trained) */
+  double out_norm;             /* output scale (mode 0: V_ref; mode 1: 0 until trained) */
+  int32_t last_start;          /* 0 previous, 1 network, 2 zero */
+  int32_t pad;
+} pic_unet_stats;
+int pic_unet_stats_read(pic_handle* h, pic_unet_stats* out);
 
 /* Bytes of device scratch that pic_poisson_solve needs for an nr x nz grid. */
 size_t pic_poisson_workspace_bytes(int nr, int nz);

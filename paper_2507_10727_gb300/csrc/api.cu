@@ -11,6 +11,7 @@
 #include "../../include/pic.h"
 #include "common.cuh"
 #include "launch.h"
+#include "unet.h"
 
 using namespace pic;
 
@@ -47,6 +48,7 @@ struct pic_handle {
   int ppt = 8;                       // particles per thread per work item (autotuned)
   int tune_next = 0;                 // next autotuner candidate; -1 = done
   float tune_ms[4] = {0, 0, 0, 0};
+  UNet* unet = nullptr;              // learned warm start (single instance)
   pic_alloc alloc;
   bool own_alloc = true;
   cudaStream_t stream = nullptr;
@@ -341,7 +343,8 @@ bool bad_instance(pic_handle* h, int instance) {
 }
 
 const char* kGroupNames[G_COUNT] = {"field_tables", "push_e", "push_i", "births", "scan",
-                                   "scatter", "charge", "circuit", "poisson", "step_end"};
+                                   "scatter", "charge", "circuit", "poisson", "step_end",
+                                   "warm_start"};
 
 void prof_mark(void* ctx, int group, bool begin, cudaStream_t st) {
   Profiler& P = *(Profiler*)ctx;
@@ -437,6 +440,7 @@ void pic_destroy(pic_handle* h) {
   for (cudaEvent_t ev : h->prof.pool) cudaEventDestroy(ev);
   for (InstHost& ih : h->inst)
     if (ih.pw) poisson_work_free(ih.pw);
+  if (h->unet) unet_destroy(h->unet);
   for (void* p : h->blocks) {
     if (h->own_alloc) cudaFree(p);
     else h->alloc.free(h->alloc.ctx, p);
@@ -728,12 +732,37 @@ static int autotune_step(pic_handle* h) {
   return PIC_OK;
 }
 
+// launches around the Poisson solve of a single-instance step: the learned
+// warm start before it, snapshot recording and iteration counts after it
+static cudaError_t hook_pre_poisson(void* ctx, const Inst& I, PoissonWork* pw, cudaStream_t st) {
+  return launch_pre_solve(((pic_handle*)ctx)->unet, I, pw, st);
+}
+static cudaError_t hook_post_poisson(void* ctx, const Inst& I, cudaStream_t st) {
+  return launch_after_solve(((pic_handle*)ctx)->unet, I, st);
+}
+
 static cudaError_t launch_all(pic_handle* h, const StepMarks* marks) {
   if (h->inst.size() > 1) return launch_ensemble_step(h, marks);
+  StepHooks hooks{nullptr, nullptr, h};
+  if (h->unet) {
+    hooks.post_poisson = hook_post_poisson;
+    if (unet_pre_solve_needed(h->unet)) hooks.pre_poisson = hook_pre_poisson;
+  }
   cudaError_t e = cudaSuccess;
   for (InstHost& ih : h->inst)
-    if (e == cudaSuccess) e = launch_step(ih.I, ih.pw, h->num_sms, h->stream, marks);
+    if (e == cudaSuccess)
+      e = launch_step(ih.I, ih.pw, h->num_sms, h->stream, marks, h->unet ? &hooks : nullptr);
   return e;
+}
+
+// the step's launch sequence changed: capture a new graph at the next step
+static void drop_graph(pic_handle* h) {
+  if (h->graph) {
+    cudaStreamSynchronize(h->stream);
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  h->graph_failed = false;
 }
 
 // Capture one time step of every instance into a CUDA graph.  Every step
@@ -967,6 +996,122 @@ int pic_load(pic_handle* h, int instance, const char* path) {
   if (e == cudaSuccess) e = cudaMemcpy(ih.I.qhist, qh.data(), qh.size() * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ih.I.phi, phi.data(), nn * 8, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(h, e, "load copy");
+  return PIC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// learned warm start
+// ---------------------------------------------------------------------------
+static void* unet_alloc_cb(void* ctx, size_t bytes) { return dev_alloc((pic_handle*)ctx, bytes); }
+
+static int need_unet(pic_handle* h) {
+  if (!h) return PIC_ERR_INVALID;
+  if (!h->unet) return fail(h, PIC_ERR_INVALID, "no network on this handle (pic_unet_create)");
+  return PIC_OK;
+}
+
+int pic_unet_param_count(int64_t* n) {
+  if (!n) return PIC_ERR_INVALID;
+  *n = unet_param_count();
+  return PIC_OK;
+}
+
+int pic_unet_create(pic_handle* h, uint64_t seed, int max_batch, int mode) {
+  if (!h) return PIC_ERR_INVALID;
+  if (h->unet) return fail(h, PIC_ERR_INVALID, "the handle already has a network");
+  if (h->inst.size() != 1) return fail(h, PIC_ERR_INVALID, "warm start needs a single-instance handle");
+  const pic_config& c = h->inst[0].cfg;
+  if (c.nr % 8 || c.nz % 8 || max_batch < 1 || mode < 0 || mode > 1)
+    return fail(h, PIC_ERR_INVALID, "nr and nz must be multiples of 8, max_batch >= 1, mode 0 or 1");
+  const double vref = c.circuit_mode == 1 ? std::fabs(c.Vs) : std::fabs(c.Vc_fixed);
+  UNet* u = unet_create(c.nr, c.nz, max_batch, mode, seed, vref > 0.0 ? vref : 1.0, unet_alloc_cb,
+                        h, h->stream);
+  if (!u) return fail(h, PIC_ERR_OOM, "network allocation or set-up failed");
+  h->unet = u;
+  drop_graph(h);
+  return PIC_OK;
+}
+
+int pic_unet_set_params(pic_handle* h, const float* params, int64_t n) {
+  const int rc = need_unet(h);
+  if (rc != PIC_OK) return rc;
+  if (!params || n != unet_param_count()) return fail(h, PIC_ERR_INVALID, "parameter count");
+  const cudaError_t e = unet_set_params(h->unet, params, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "unet_set_params");
+  return PIC_OK;
+}
+
+int pic_unet_get_params(pic_handle* h, float* params, int64_t n) {
+  const int rc = need_unet(h);
+  if (rc != PIC_OK) return rc;
+  if (!params || n != unet_param_count()) return fail(h, PIC_ERR_INVALID, "parameter count");
+  const cudaError_t e = unet_get_params(h->unet, params, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "unet_get_params");
+  return PIC_OK;
+}
+
+int pic_unet_loss_grad(pic_handle* h, int batch, const float* x, const float* y, float* out,
+                       float* grad, double* loss) {
+  const int rc = need_unet(h);
+  if (rc != PIC_OK) return rc;
+  if (!x || batch < 1 || batch > unet_bmax(h->unet)) return fail(h, PIC_ERR_INVALID, "batch or x");
+  const cudaError_t e = unet_loss_grad(h->unet, batch, x, y, out, grad, loss, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "unet_loss_grad");
+  return PIC_OK;
+}
+
+int pic_unet_snapshots(pic_handle* h, int64_t capacity, int every) {
+  const int rc = need_unet(h);
+  if (rc != PIC_OK) return rc;
+  if (capacity < 1 || every < 1) return fail(h, PIC_ERR_INVALID, "capacity, every >= 1");
+  if (unet_recording(h->unet)) return fail(h, PIC_ERR_INVALID, "snapshot ring already set");
+  const cudaError_t e = unet_snapshots(h->unet, capacity, every, unet_alloc_cb, h);
+  if (e != cudaSuccess) return fail(h, PIC_ERR_OOM, "snapshot ring allocation failed");
+  drop_graph(h);
+  return PIC_OK;
+}
+
+int pic_unet_train(pic_handle* h, int iters, int batch, float lr, uint64_t seed,
+                   double* loss_first, double* loss_last) {
+  const int rc = need_unet(h);
+  if (rc != PIC_OK) return rc;
+  if (iters < 1 || batch < 1 || batch > unet_bmax(h->unet) || !(lr > 0.0f))
+    return fail(h, PIC_ERR_INVALID, "iters, batch or lr");
+  if (!unet_recording(h->unet)) return fail(h, PIC_ERR_INVALID, "no snapshots (pic_unet_snapshots)");
+  const cudaError_t e = unet_train(h->unet, iters, batch, lr, seed, loss_first, loss_last, h->stream);
+  if (e == cudaErrorInvalidValue) return fail(h, PIC_ERR_INVALID, "no snapshot recorded yet");
+  if (e != cudaSuccess) return cuda_fail(h, e, "unet_train");
+  return PIC_OK;
+}
+
+int pic_unet_warm_start(pic_handle* h, int on) {
+  const int rc = need_unet(h);
+  if (rc != PIC_OK) return rc;
+  if (unet_warm(h->unet) != (on != 0)) {
+    unet_set_warm(h->unet, on != 0);
+    drop_graph(h);
+  }
+  return PIC_OK;
+}
+
+int pic_unet_stats_read(pic_handle* h, pic_unet_stats* out) {
+  const int rc = need_unet(h);
+  if (rc != PIC_OK) return rc;
+  if (!out) return fail(h, PIC_ERR_INVALID, "null out");
+  UDev d;
+  cudaError_t e = cudaMemcpyAsync(&d, unet_dev(h->unet), sizeof(UDev), cudaMemcpyDeviceToHost,
+                                  h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "unet stats");
+  out->snapshots = d.snap_count;
+  out->starts_previous = d.n_choice[0];
+  out->starts_network = d.n_choice[1];
+  out->starts_zero = d.n_choice[2];
+  out->poisson_iters = d.iters_total;
+  out->in_norm = d.in_norm;
+  out->out_norm = d.out_norm;
+  out->last_start = d.choice;
+  out->pad = 0;
   return PIC_OK;
 }
 

@@ -12,16 +12,24 @@ struct PoissonWork;  // defined in poisson.cu
 // optional per-kernel-group event marks around the launches of a step
 enum StepGroup {
   G_FIELD = 0, G_PUSH_E, G_PUSH_I, G_BIRTHS, G_SCAN, G_SCATTER, G_CHARGE, G_CIRCUIT,
-  G_POISSON, G_STEP_END, G_COUNT
+  G_POISSON, G_STEP_END, G_WARM, G_COUNT
 };
 struct StepMarks {
   void (*mark)(void* ctx, int group, bool begin, cudaStream_t st);
   void* ctx;
 };
 
+// optional launches around the Poisson solve of a step (the learned warm
+// start before it, snapshot recording after it)
+struct StepHooks {
+  cudaError_t (*pre_poisson)(void* ctx, const Inst& I, PoissonWork* pw, cudaStream_t st);
+  cudaError_t (*post_poisson)(void* ctx, const Inst& I, cudaStream_t st);
+  void* ctx;
+};
+
 // one time step of one instance (all kernels of the step, in order)
 cudaError_t launch_step(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_t st,
-                        const StepMarks* marks);
+                        const StepMarks* marks, const StepHooks* hooks = nullptr);
 
 // sort the particles of species `sp` currently in cur[sp] into nxt[sp]
 // (keys, histogram, scan, scatter); the caller swaps cur/nxt afterwards

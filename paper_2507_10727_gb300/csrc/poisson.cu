@@ -29,6 +29,7 @@
 
 #include "common.cuh"
 #include "launch.h"
+#include "unet.h"
 
 namespace pic {
 
@@ -205,6 +206,14 @@ __device__ __forceinline__ Lev lev(const PoissonWork& W, const Tables& T, int l,
   L.ar = T.ar + W.coef_off[l];
   L.idg = T.idg + W.coef_off[l];
   return L;
+}
+
+// Fine-level couplings of the volume-scaled RZ operator at radial index m:
+// az (along z, between n and n +- 1) and ar (between m and m + 1).
+__device__ __forceinline__ void fine_coef(const PoissonWork& W, int m, double& az, double& ar) {
+  const double c = 2.0 * kPi * kEps0;
+  az = m == 0 ? c * W.dr * W.dr / (8.0 * W.dz) : c * m * W.dr * W.dr / W.dz;
+  ar = c * (m + 0.5) * W.dz;
 }
 
 // Nodes are visited as warp items (row m, 32-wide segment of n):
@@ -460,11 +469,7 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
   float* tar = taz + W.ncoef;
   float* tidg = tar + W.ncoef;
   float* tailbuf = tidg + W.ncoef;
-  for (int m = threadIdx.x; m <= nr; m += blockDim.x) {
-    const double c = 2.0 * kPi * kEps0;
-    az0[m] = m == 0 ? c * W.dr * W.dr / (8.0 * W.dz) : c * m * W.dr * W.dr / W.dz;
-    ar0[m] = c * (m + 0.5) * W.dz;
-  }
+  for (int m = threadIdx.x; m <= nr; m += blockDim.x) fine_coef(W, m, az0[m], ar0[m]);
   for (int l = 0; l < W.nlev; ++l) {
     const float drl = (float)(W.dr * (double)(1 << l)), dzl = (float)(W.dz * (double)(1 << l));
     const int o = W.coef_off[l], lr = W.lnr[l];
@@ -652,6 +657,171 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
     *A.resid = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
     if (!converged) atomicOr(A.status, ST_NONCONV);
   }
+}
+
+// ----------------------------------------------------------------------------
+// Pieces of the learned warm start, on the fine FP64 operator of the solve.
+// Start selection: the residual norms ||Q - A x||^2 of three starting points
+// -- x = phi as it stands (the previous solution with this step's Dirichlet
+// values), x = the candidate from the network, x = 0 -- all with the
+// Dirichlet values of phi on the boundary; the smallest wins (ties keep the
+// earlier candidate) and is copied into phi's free nodes.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ bool free_node(int m, int n, int nr, int nz) {
+  return m < nr && n >= 1 && n <= nz - 1;
+}
+
+__device__ __forceinline__ double start_value(int k, const double* phi, const double* cand, int m,
+                                              int n, int i, int nr, int nz) {
+  if (k == 0 || !free_node(m, n, nr, nz)) return phi[i];
+  return k == 1 ? cand[i] : 0.0;
+}
+
+__global__ void __launch_bounds__(256) k_guess_norms(PoissonWork W, const double* Q, const double* phi,
+                                                     const double* cand, double* partial) {
+  __shared__ double red[3][8];
+  const int nr = W.nr, nz = W.nz, nz1 = nz + 1;
+  const long long nfree = (long long)nr * (nz - 1);
+  double loc[3] = {0.0, 0.0, 0.0};
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nfree;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(e / (nz - 1)), n = 1 + (int)(e - (long long)m * (nz - 1));
+    const int i = m * nz1 + n;
+    double az, ar, azm = 0.0, arm = 0.0;
+    fine_coef(W, m, az, ar);
+    if (m > 0) fine_coef(W, m - 1, azm, arm);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double xi = start_value(k, phi, cand, m, n, i, nr, nz);
+      const double xl = start_value(k, phi, cand, m, n - 1, i - 1, nr, nz);
+      const double xu = start_value(k, phi, cand, m, n + 1, i + 1, nr, nz);
+      const double xo = start_value(k, phi, cand, m + 1, n, i + nz1, nr, nz);
+      double a = az * (2.0 * xi - xl - xu) + ar * (xi - xo);
+      if (m > 0) a += arm * (xi - start_value(k, phi, cand, m - 1, n, i - nz1, nr, nz));
+      const double r = Q[i] - a;
+      loc[k] += r * r;
+    }
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double s = warp_sum64(loc[k]);
+    if (lane == 0) red[k][w] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double s = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[threadIdx.x][q];
+    partial[(long long)threadIdx.x * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_guess_pick(const double* partial, int nblk, UDev* ud, const int* status) {
+  __shared__ double tot[3];
+  if (threadIdx.x < 3) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[(long long)threadIdx.x * nblk + b];
+    tot[threadIdx.x] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (*status & ST_FATAL) {
+      ud->choice = 0;
+      return;
+    }
+    int best = 0;
+    for (int k = 1; k < 3; ++k)
+      if (tot[k] < tot[best]) best = k;   // NaN norms never win
+    ud->choice = best;
+    ud->n_choice[best] += 1;
+  }
+}
+
+__global__ void k_guess_apply(int nr, int nz, double* phi, const double* cand, const UDev* ud) {
+  const int choice = ud->choice;
+  if (choice == 0) return;
+  const int nz1 = nz + 1;
+  const long long nfree = (long long)nr * (nz - 1);
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nfree;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(e / (nz - 1)), n = 1 + (int)(e - (long long)m * (nz - 1));
+    const int i = m * nz1 + n;
+    phi[i] = choice == 1 ? cand[i] : 0.0;
+  }
+}
+
+// res = Q - A phi on free nodes, 0 on Dirichlet nodes
+__global__ void k_residual32(PoissonWork W, const double* Q, const double* phi, float* res) {
+  const int nr = W.nr, nz = W.nz, nz1 = nz + 1;
+  const long long nn = (long long)(nr + 1) * nz1;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nn;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(i / nz1), n = (int)(i - (long long)m * nz1);
+    if (!free_node(m, n, nr, nz)) {
+      res[i] = 0.0f;
+      continue;
+    }
+    double az, ar, azm = 0.0, arm = 0.0;
+    fine_coef(W, m, az, ar);
+    if (m > 0) fine_coef(W, m - 1, azm, arm);
+    double a = az * (2.0 * phi[i] - phi[i - 1] - phi[i + 1]) + ar * (phi[i] - phi[i + nz1]);
+    if (m > 0) a += arm * (phi[i] - phi[i - nz1]);
+    res[i] = (float)(Q[i] - a);
+  }
+}
+
+// one colour of a red-black Gauss-Seidel sweep on A x = Q
+__global__ void k_gs_color(PoissonWork W, const double* Q, double* x, int color) {
+  const int nr = W.nr, nz = W.nz, nz1 = nz + 1;
+  const long long nfree = (long long)nr * (nz - 1);
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nfree;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(e / (nz - 1)), n = 1 + (int)(e - (long long)m * (nz - 1));
+    if (((m + n) & 1) != color) continue;
+    const int i = m * nz1 + n;
+    double az, ar, azm = 0.0, arm = 0.0;
+    fine_coef(W, m, az, ar);
+    if (m > 0) fine_coef(W, m - 1, azm, arm);
+    double s = Q[i] + az * (x[i - 1] + x[i + 1]) + ar * x[i + nz1];
+    if (m > 0) s += arm * x[i - nz1];
+    x[i] = s / (2.0 * az + ar + arm);
+  }
+}
+
+int guess_blocks(int nr, int nz) {
+  const long long nfree = (long long)nr * (nz - 1);
+  long long b = (nfree + 255) / 256;
+  if (b > 592) b = 592;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+cudaError_t launch_residual32(PoissonWork* pw, const double* Q, const double* phi, float* res,
+                              cudaStream_t st) {
+  const long long nn = (long long)(pw->nr + 1) * (pw->nz + 1);
+  long long b = (nn + 255) / 256;
+  if (b > 592) b = 592;
+  k_residual32<<<(int)b, 256, 0, st>>>(*pw, Q, phi, res);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gs_sweeps(PoissonWork* pw, const double* Q, double* x, int sweeps,
+                             cudaStream_t st) {
+  const int nb = guess_blocks(pw->nr, pw->nz);
+  for (int s = 0; s < sweeps; ++s) {
+    k_gs_color<<<nb, 256, 0, st>>>(*pw, Q, x, 0);
+    k_gs_color<<<nb, 256, 0, st>>>(*pw, Q, x, 1);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_guess_select(PoissonWork* pw, const double* Q, double* phi, const double* cand,
+                                double* partial, int nblk, UDev* ud, const int* status,
+                                cudaStream_t st) {
+  k_guess_norms<<<nblk, 256, 0, st>>>(*pw, Q, phi, cand, partial);
+  k_guess_pick<<<1, 32, 0, st>>>(partial, nblk, ud, status);
+  k_guess_apply<<<nblk, 256, 0, st>>>(pw->nr, pw->nz, phi, cand, ud);
+  return cudaGetLastError();
 }
 
 // ----------------------------------------------------------------------------

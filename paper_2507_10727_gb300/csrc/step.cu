@@ -942,7 +942,7 @@ cudaError_t launch_step_end(const Inst& I, cudaStream_t st) {
 }
 
 cudaError_t launch_step(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_t st,
-                        const StepMarks* marks) {
+                        const StepMarks* marks, const StepHooks* hooks) {
   auto mk = [&](int g, bool b) {
     if (marks) marks->mark(marks->ctx, g, b, st);
   };
@@ -982,11 +982,21 @@ cudaError_t launch_step(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_
   mk(G_CIRCUIT, true);
   k_circuit<<<1, 256, 0, st>>>(I);
   mk(G_CIRCUIT, false);
+  if (hooks && hooks->pre_poisson) {
+    mk(G_WARM, true);
+    e = hooks->pre_poisson(hooks->ctx, I, pw, st);
+    mk(G_WARM, false);
+    if (e != cudaSuccess) return e;
+  }
   mk(G_POISSON, true);
   e = launch_poisson(pw, I.Q, I.phi, I.poisson_tol, I.poisson_max_iter, &I.S->status,
                      &I.S->poisson_iters, &I.S->poisson_resid, st);
   mk(G_POISSON, false);
   if (e != cudaSuccess) return e;
+  if (hooks && hooks->post_poisson) {
+    e = hooks->post_poisson(hooks->ctx, I, st);
+    if (e != cudaSuccess) return e;
+  }
   mk(G_STEP_END, true);
   k_step_end<<<1, 32, 0, st>>>(I);
   mk(G_STEP_END, false);

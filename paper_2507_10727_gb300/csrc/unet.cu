@@ -1,0 +1,1287 @@
+// unet.cu -- the learned Poisson warm start: a BF16 U-Net on the node grid,
+// its forward and backward passes, Adam training on snapshots the simulation
+// records, and the per-step guess (north-star pattern "learned warm start";
+// the paper's solver is the judge: the guess only changes where the solve
+// starts, never where it ends).
+//
+// Convolutions are implicit GEMMs on the tensor cores (BF16 operands, FP32
+// accumulation): a CTA owns an 8 x 16 tile of output nodes; the input halo
+// (10 x 18 nodes x 16 channels) and the 9 taps' weights of one 16-channel
+// input chunk are staged in shared memory with cp.async, and each warp forms
+// one row of 16 outputs by ldmatrix + mma.m16n8k16 over the 9 taps.  The data
+// gradient is the same kernel run on flipped, transposed weights; the weight
+// gradient contracts over nodes (9 warps = 9 taps, split-K over tiles with a
+// deterministic reduction).
+#include <cmath>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "launch.h"
+#include "unet.h"
+
+namespace pic {
+
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+constexpr int kLev = 4;
+constexpr int kCh[kLev] = {16, 32, 64, 64};
+constexpr int kInReal = 3;
+constexpr int kInPad = 16;
+constexpr int kNumConv = 14;
+constexpr int kHead = 14;
+constexpr int kNumLayers = 15;
+
+constexpr int kTH = 8, kTW = 16;              // output tile: rows x columns
+constexpr int kPH = kTH + 2, kPW = kTW + 2;   // input halo patch
+constexpr int kPS = 24;                       // bf16 per staged row (16 + 8 pad = 48 bytes)
+constexpr int kConvThreads = 256;             // 8 warps = 8 tile rows
+constexpr int kWgThreads = 288;               // 9 warps = 9 taps
+constexpr int kMaxSplit = 608;                // 4 x 152 weight-gradient CTAs
+constexpr int kHeadVals = 18;                 // loss, d bias, d w[16]
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+// 16-byte async copy global -> shared; bytes < 16 zero-fills the rest
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3,
+                                        const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3,
+                                          const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(smem_u32(p)));
+}
+// D += A (16x16, row) * B (16x8, col), BF16 in, FP32 accumulate
+__device__ __forceinline__ void mma_bf16(float* d, unsigned a0, unsigned a1, unsigned a2,
+                                         unsigned a3, unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  // splitmix64 finaliser (Steele, Lea, Flood 2014)
+  x += 0x9E3779B97F4A7C15ULL;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+  return x ^ (x >> 31);
+}
+
+// ---------------------------------------------------------------------------
+// 3x3 convolution (forward; also the data gradient on flipped weights)
+// ---------------------------------------------------------------------------
+struct ConvArgs {
+  const bf16* x;      // input buffer; logical node (i, j) at buffer node (i, j) * x_step
+  long long x_bs;     // batch stride (elements)
+  int x_cs, x_c0, x_step, x_w;   // channel stride, channel offset, node step, buffer row length
+  const bf16* w;      // packed weights [cin / 16][9][cout][16]
+  const float* bias;  // cout entries or null
+  int cin, cout;      // cin multiple of 16
+  bf16* y;
+  long long y_bs;
+  int y_cs, y_c0, y_step, y_w;
+  int H, W, B;        // logical node grid of the convolution, batch
+  int relu, accumulate;
+};
+
+template <int COB>
+__global__ void __launch_bounds__(kConvThreads) k_conv3(ConvArgs a) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  bf16* patch = reinterpret_cast<bf16*>(sm_raw);
+  bf16* wsm = patch + kPH * kPW * kPS;
+  const int tw = (a.W + kTW - 1) / kTW, th = (a.H + kTH - 1) / kTH;
+  int t = blockIdx.x;
+  const int b = t / (tw * th);
+  t -= b * tw * th;
+  const int i0 = (t / tw) * kTH, j0 = (t % tw) * kTW;
+  const int co0 = blockIdx.y * COB;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bf16* xb = a.x + (long long)b * a.x_bs;
+  float acc[COB / 8][4];
+#pragma unroll
+  for (int q = 0; q < COB / 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.0f;
+  const int nkc = a.cin >> 4;
+  for (int kc = 0; kc < nkc; ++kc) {
+    for (int e = threadIdx.x; e < kPH * kPW * 2; e += blockDim.x) {
+      const int p = e >> 1, half = e & 1;
+      const int pi = p / kPW, pj = p - pi * kPW;
+      const int gi = i0 + pi - 1, gj = j0 + pj - 1;
+      const bool ok = gi >= 0 && gi < a.H && gj >= 0 && gj < a.W;
+      const bf16* src = ok ? xb + ((long long)gi * a.x_step * a.x_w + (long long)gj * a.x_step) * a.x_cs +
+                                 a.x_c0 + kc * 16 + half * 8
+                           : a.x;
+      cp_async16(patch + p * kPS + half * 8, src, ok ? 16 : 0);
+    }
+    for (int e = threadIdx.x; e < 9 * COB * 2; e += blockDim.x) {
+      const int row = e >> 1, half = e & 1;
+      const int tap = row / COB, c = row - tap * COB;
+      const bf16* src = a.w + (((long long)kc * 9 + tap) * a.cout + co0 + c) * 16 + half * 8;
+      cp_async16(wsm + row * kPS + half * 8, src, 16);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int dr = tap / 3, dc = tap - dr * 3;
+      unsigned a0, a1, a2, a3;
+      {
+        // A (16 nodes x 16 channels): matrices (nodes 0-7 | 8-15) x (k 0-7 | 8-15)
+        const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8;
+        const int kof = (lane >> 4) * 8;
+        ldsm_x4(a0, a1, a2, a3, patch + ((warp + dr) * kPW + mrow + dc) * kPS + kof);
+      }
+#pragma unroll
+      for (int nt = 0; nt < COB / 8; nt += 2) {
+        // B (16 channels x 16 outputs, stored output-major): two 8-wide n tiles
+        const int nrow = (lane & 7) + (lane >> 4) * 8;
+        const int kb = ((lane >> 3) & 1) * 8;
+        unsigned b0, b1, b2, b3;
+        ldsm_x4(b0, b1, b2, b3, wsm + (tap * COB + nt * 8 + nrow) * kPS + kb);
+        mma_bf16(acc[nt], a0, a1, a2, a3, b0, b1);
+        mma_bf16(acc[nt + 1], a0, a1, a2, a3, b2, b3);
+      }
+    }
+    __syncthreads();
+  }
+  const int gi = i0 + warp;
+  if (gi >= a.H) return;
+  bf16* yb = a.y + (long long)b * a.y_bs;
+#pragma unroll
+  for (int nt = 0; nt < COB / 8; ++nt) {
+    const int co = co0 + nt * 8 + (lane & 3) * 2;
+    const float bb0 = a.bias ? a.bias[co] : 0.0f, bb1 = a.bias ? a.bias[co + 1] : 0.0f;
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+      const int gj = j0 + (lane >> 2) + hf * 8;
+      if (gj >= a.W) continue;
+      float v0 = acc[nt][hf * 2] + bb0, v1 = acc[nt][hf * 2 + 1] + bb1;
+      __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(
+          yb + ((long long)gi * a.y_step * a.y_w + (long long)gj * a.y_step) * a.y_cs + a.y_c0 + co);
+      if (a.accumulate) {
+        const float2 o = __bfloat1622float2(*dst);
+        v0 += o.x;
+        v1 += o.y;
+      }
+      if (a.relu) {
+        v0 = fmaxf(v0, 0.0f);
+        v1 = fmaxf(v1, 0.0f);
+      }
+      *dst = __floats2bfloat162_rn(v0, v1);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// weight gradient: dW[co][ci][tap] = sum over nodes of dZ[node][co] *
+// X[node + tap][ci]; CTA (ci chunk, split s) runs over tiles s, s + S, ...
+// ---------------------------------------------------------------------------
+struct WgArgs {
+  const bf16* x;
+  long long x_bs;
+  int x_cs, x_c0, x_step, x_w;
+  const bf16* dz;     // output gradient (after the ReLU mask), node step 1, row length W
+  long long dz_bs;
+  int dz_cs, dz_c0;
+  int cin, H, W, B;   // cin: padded (multiple of 16)
+  float* pw;          // [S][cin / 16][9][COUT][16]
+  float* pb;          // [S][COUT]
+};
+
+template <int COUT>
+__global__ void __launch_bounds__(kWgThreads) k_conv3_wgrad(WgArgs a) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  constexpr int DS = COUT + 8;
+  bf16* dzs = reinterpret_cast<bf16*>(sm_raw);   // [128 nodes][DS]
+  bf16* patch = dzs + kTH * kTW * DS;              // [kPH * kPW][kPS]
+  const int kc = blockIdx.x, s = blockIdx.y, S = gridDim.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int dr = warp / 3, dc = warp - dr * 3;
+  const int tw = (a.W + kTW - 1) / kTW, th = (a.H + kTH - 1) / kTH;
+  const int T = a.B * tw * th;
+  float acc[COUT / 16][2][4];
+#pragma unroll
+  for (int mt = 0; mt < COUT / 16; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) acc[mt][nt][0] = acc[mt][nt][1] = acc[mt][nt][2] = acc[mt][nt][3] = 0.0f;
+  float bsum = 0.0f;
+  for (int t = s; t < T; t += S) {
+    const int b = t / (tw * th);
+    const int r = t - b * tw * th;
+    const int i0 = (r / tw) * kTH, j0 = (r % tw) * kTW;
+    const bf16* dzb = a.dz + (long long)b * a.dz_bs;
+    for (int e = threadIdx.x; e < kTH * kTW * (COUT / 8); e += blockDim.x) {
+      const int p = e / (COUT / 8), c8 = e - p * (COUT / 8);
+      const int gi = i0 + p / kTW, gj = j0 + p % kTW;
+      const bool ok = gi < a.H && gj < a.W;
+      const bf16* src = ok ? dzb + ((long long)gi * a.W + gj) * a.dz_cs + a.dz_c0 + c8 * 8 : a.dz;
+      cp_async16(dzs + p * DS + c8 * 8, src, ok ? 16 : 0);
+    }
+    const bf16* xb = a.x + (long long)b * a.x_bs;
+    for (int e = threadIdx.x; e < kPH * kPW * 2; e += blockDim.x) {
+      const int p = e >> 1, half = e & 1;
+      const int pi = p / kPW, pj = p - pi * kPW;
+      const int gi = i0 + pi - 1, gj = j0 + pj - 1;
+      const bool ok = gi >= 0 && gi < a.H && gj >= 0 && gj < a.W;
+      const bf16* src = ok ? xb + ((long long)gi * a.x_step * a.x_w + (long long)gj * a.x_step) * a.x_cs +
+                                 a.x_c0 + kc * 16 + half * 8
+                           : a.x;
+      cp_async16(patch + p * kPS + half * 8, src, ok ? 16 : 0);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    if (kc == 0 && threadIdx.x < COUT)
+      for (int p = 0; p < kTH * kTW; ++p) bsum += __bfloat162float(dzs[p * DS + threadIdx.x]);
+#pragma unroll 1
+    for (int ks = 0; ks < kTH; ++ks) {
+      // B (16 nodes x 16 input channels) from the halo patch, shifted by the tap
+      unsigned b0, b1, b2, b3;
+      {
+        const int pxl = (lane & 7) + ((lane >> 3) & 1) * 8;
+        const int cio = (lane >> 4) * 8;
+        ldsm_x4_t(b0, b1, b2, b3, patch + ((ks + dr) * kPW + pxl + dc) * kPS + cio);
+      }
+#pragma unroll
+      for (int mt = 0; mt < COUT / 16; ++mt) {
+        // A (16 output channels x 16 nodes) = dZ^T
+        const int pxl = (lane & 7) + (lane >> 4) * 8;
+        const int coo = ((lane >> 3) & 1) * 8;
+        unsigned a0, a1, a2, a3;
+        ldsm_x4_t(a0, a1, a2, a3, dzs + (ks * kTW + pxl) * DS + mt * 16 + coo);
+        mma_bf16(acc[mt][0], a0, a1, a2, a3, b0, b1);
+        mma_bf16(acc[mt][1], a0, a1, a2, a3, b2, b3);
+      }
+    }
+    __syncthreads();
+  }
+  float* pw = a.pw + (((long long)s * (a.cin >> 4) + kc) * 9 + warp) * COUT * 16;
+#pragma unroll
+  for (int mt = 0; mt < COUT / 16; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const int co = mt * 16 + (lane >> 2), ci = nt * 8 + (lane & 3) * 2;
+      pw[co * 16 + ci] = acc[mt][nt][0];
+      pw[co * 16 + ci + 1] = acc[mt][nt][1];
+      pw[(co + 8) * 16 + ci] = acc[mt][nt][2];
+      pw[(co + 8) * 16 + ci + 1] = acc[mt][nt][3];
+    }
+  if (kc == 0 && threadIdx.x < COUT) a.pb[(long long)s * COUT + threadIdx.x] = bsum;
+}
+
+// sum the split partials (in split order) into the layer's weight/bias gradient
+__global__ void k_wgrad_reduce(const float* pw, const float* pb, int S, int cin, int cin_pad,
+                               int cout, float* gw, float* gb) {
+  const int nW = cout * cin * 9;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nW + cout; idx += gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    if (idx < nW) {
+      const int co = idx / (cin * 9), rr = idx - co * cin * 9;
+      const int ci = rr / 9, tap = rr - ci * 9;
+      const int kc = ci >> 4, k = ci & 15;
+      for (int sp = 0; sp < S; ++sp)
+        s += pw[(((long long)sp * (cin_pad >> 4) + kc) * 9 + tap) * cout * 16 + co * 16 + k];
+      gw[idx] = s;
+    } else {
+      const int co = idx - nW;
+      for (int sp = 0; sp < S; ++sp) s += pb[(long long)sp * cout + co];
+      gb[co] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// element-wise pieces
+// ---------------------------------------------------------------------------
+// g <- g * (y > 0) on a channel slice (ReLU backward), 8 channels per item
+__global__ void k_relu_mask(bf16* g, int g_cs, int g_c0, const bf16* y, int y_cs, int y_c0, int C,
+                            long long npx) {
+  const int c8n = C >> 3;
+  const long long total = npx * c8n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long p = e / c8n;
+    const int c8 = (int)(e - p * c8n);
+    uint4* gp = reinterpret_cast<uint4*>(g + p * g_cs + g_c0 + c8 * 8);
+    const uint4 yv = *reinterpret_cast<const uint4*>(y + p * y_cs + y_c0 + c8 * 8);
+    uint4 gv = *gp;
+    unsigned* gw = &gv.x;
+    const unsigned* yw = &yv.x;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const unsigned lo = yw[q] & 0xFFFFu, hi = yw[q] >> 16;
+      const bool plo = (lo & 0x8000u) == 0 && (lo & 0x7FFFu) != 0;
+      const bool phi = (hi & 0x8000u) == 0 && (hi & 0x7FFFu) != 0;
+      gw[q] &= (plo ? 0x0000FFFFu : 0u) | (phi ? 0xFFFF0000u : 0u);
+    }
+    *gp = gv;
+  }
+}
+
+__device__ __forceinline__ void load8(const bf16* p, float* v) {
+  const uint4 u = *reinterpret_cast<const uint4*>(p);
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float2 f = __bfloat1622float2(h[q]);
+    v[2 * q] = f.x;
+    v[2 * q + 1] = f.y;
+  }
+}
+__device__ __forceinline__ void store8(bf16* p, const float* v) {
+  uint4 u;
+  __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) h[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+  *reinterpret_cast<uint4*>(p) = u;
+}
+
+// bilinear node up-sampling: coarse node (I, J) sits on fine node (2I, 2J)
+__global__ void k_up(const bf16* src, int s_cs, int s_c0, int Hc, int Wc, bf16* dst, int d_cs,
+                     int d_c0, int Hf, int Wf, int C, int B) {
+  const int c8n = C >> 3;
+  const long long total = (long long)B * Hf * Wf * c8n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int c8 = (int)(e % c8n);
+    const long long p = e / c8n;
+    const int b = (int)(p / ((long long)Hf * Wf));
+    const int q = (int)(p - (long long)b * Hf * Wf);
+    const int i = q / Wf, j = q - i * Wf;
+    const int I = i >> 1, J = j >> 1, oi = i & 1, oj = j & 1;
+    const bf16* cb = src + (long long)b * Hc * Wc * s_cs + s_c0 + c8 * 8;
+    float v[8], t[8];
+    load8(cb + ((long long)I * Wc + J) * s_cs, v);
+    if (oi) {
+      load8(cb + ((long long)(I + 1) * Wc + J) * s_cs, t);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] += t[k];
+    }
+    if (oj) {
+      load8(cb + ((long long)I * Wc + J + 1) * s_cs, t);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] += t[k];
+    }
+    if (oi && oj) {
+      load8(cb + ((long long)(I + 1) * Wc + J + 1) * s_cs, t);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] += t[k];
+    }
+    const float sc = (oi && oj) ? 0.25f : (oi || oj) ? 0.5f : 1.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] *= sc;
+    store8(dst + (p * d_cs) + d_c0 + c8 * 8, v);
+  }
+}
+
+// transpose of k_up: coarse gradient = sum over the fine nodes it feeds
+__global__ void k_up_t(const bf16* gf, int f_cs, int f_c0, int Hf, int Wf, bf16* gc, int c_cs,
+                       int c_c0, int Hc, int Wc, int C, int B) {
+  const int c8n = C >> 3;
+  const long long total = (long long)B * Hc * Wc * c8n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int c8 = (int)(e % c8n);
+    const long long p = e / c8n;
+    const int b = (int)(p / ((long long)Hc * Wc));
+    const int q = (int)(p - (long long)b * Hc * Wc);
+    const int I = q / Wc, J = q - I * Wc;
+    const bf16* fb = gf + (long long)b * Hf * Wf * f_cs + f_c0 + c8 * 8;
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0}, t[8];
+    for (int di = -1; di <= 1; ++di) {
+      const int i = 2 * I + di;
+      if (i < 0 || i >= Hf) continue;
+      const float wi = di == 0 ? 1.0f : 0.5f;
+      for (int dj = -1; dj <= 1; ++dj) {
+        const int j = 2 * J + dj;
+        if (j < 0 || j >= Wf) continue;
+        const float w = wi * (dj == 0 ? 1.0f : 0.5f);
+        load8(fb + ((long long)i * Wf + j) * f_cs, t);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] += w * t[k];
+      }
+    }
+    store8(gc + p * c_cs + c_c0 + c8 * 8, acc);
+  }
+}
+
+// 1x1 head (16 -> 1), FP32
+__global__ void k_head_fwd(const bf16* h, const float* w, const float* bias, float* out, long long npx) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npx;
+       p += (long long)gridDim.x * blockDim.x) {
+    float v[16];
+    load8(h + p * 16, v);
+    load8(h + p * 16 + 8, v + 8);
+    float s = bias[0];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) s += w[c] * v[c];
+    out[p] = s;
+  }
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// MSE loss and the head's backward: d out = 2 (out - y) / N, d h = w d out;
+// block partial sums of (sum d^2, d bias, d w[16]) in FP64
+__global__ void __launch_bounds__(256) k_head_bwd(const bf16* h, const float* w, const float* out,
+                                                  const float* y, bf16* gh, long long npx,
+                                                  double inv_n, double* partial) {
+  __shared__ double red[kHeadVals][8];
+  double loc[kHeadVals];
+#pragma unroll
+  for (int k = 0; k < kHeadVals; ++k) loc[k] = 0.0;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npx;
+       p += (long long)gridDim.x * blockDim.x) {
+    const double d = (double)out[p] - (double)y[p];
+    const double g = 2.0 * d * inv_n;
+    loc[0] += d * d;
+    loc[1] += g;
+    float v[16], o[16];
+    load8(h + p * 16, v);
+    load8(h + p * 16 + 8, v + 8);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      loc[2 + c] += g * (double)v[c];
+      o[c] = (float)((double)w[c] * g);
+    }
+    store8(gh + p * 16, o);
+    store8(gh + p * 16 + 8, o + 8);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kHeadVals; ++k) {
+    const double s = warp_sum_d(loc[k]);
+    if (lane == 0) red[k][wid] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < kHeadVals) {
+    double s = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[threadIdx.x][q];
+    partial[(long long)blockIdx.x * kHeadVals + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_head_final(const double* partial, int nblk, double inv_n, double* loss,
+                             float* gw, float* gb) {
+  const int k = threadIdx.x;
+  if (k >= kHeadVals) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partial[(long long)b * kHeadVals + k];
+  if (k == 0) *loss = s * inv_n;
+  else if (k == 1) gb[0] = (float)s;
+  else gw[k - 2] = (float)s;
+}
+
+// network input from host arrays in the (B, 3, H, W) layout
+__global__ void k_pack_input(const float* xs, int B, int H, int W, bf16* x_in) {
+  const long long npx = (long long)H * W, total = (long long)B * npx;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e / npx, q = e - b * npx;
+    float v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = c < kInReal ? xs[(b * kInReal + c) * npx + q] : 0.0f;
+    store8(x_in + e * 16, v);
+    store8(x_in + e * 16 + 8, v + 8);
+  }
+}
+
+__device__ __forceinline__ bool dirichlet_node(int m, int n, int nr, int nz) {
+  return n == 0 || n == nz || m == nr;
+}
+
+// training batch: B snapshots drawn by hash of (seed, iteration, b).
+// Slot fields: mode 0 (rho, phi), mode 1 (res, phi - phi_prev).
+__global__ void k_train_input(const float* f0, const float* f1, long long avail, int B,
+                              unsigned long long seed, long long iter, int nr, int nz, int mode,
+                              const UDev* ud, bf16* x_in, float* y) {
+  const int W = nz + 1;
+  const long long npx = (long long)(nr + 1) * W, total = (long long)B * npx;
+  const float inv_in = (float)(1.0 / ud->in_norm), inv_out = (float)(1.0 / ud->out_norm);
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e / npx, q = e - b * npx;
+    const unsigned long long hsh =
+        mix64(seed ^ mix64((unsigned long long)iter * 0x100000001B3ULL + (unsigned long long)b));
+    const long long slot = (long long)(hsh % (unsigned long long)avail);
+    const int m = (int)(q / W), n = (int)(q - (long long)m * W);
+    const float a = f0[slot * npx + q], t = f1[slot * npx + q];
+    const bool dir = dirichlet_node(m, n, nr, nz);
+    float v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = 0.0f;
+    v[0] = a * inv_in;
+    v[1] = (float)m / (float)nr;
+    v[2] = mode == 0 ? (dir ? t * inv_out : 0.0f) : (dir ? 1.0f : 0.0f);
+    store8(x_in + e * 16, v);
+    store8(x_in + e * 16 + 8, v + 8);
+    y[e] = t * inv_out;
+  }
+}
+
+// network input from the live state (batch 1): mode 0 from rho = Q / V and
+// phi's Dirichlet values, mode 1 from the residual of the previous solution
+__global__ void k_step_input(Inst I, const UDev* ud, int mode, const float* res, bf16* x_in) {
+  const int W = I.nz + 1;
+  const long long npx = (long long)(I.nr + 1) * W;
+  if (I.S->status & ST_FATAL) return;
+  const double inv_in = 1.0 / ud->in_norm, inv_out = 1.0 / ud->out_norm;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(q / W), n = (int)(q - (long long)m * W);
+    const bool dir = dirichlet_node(m, n, I.nr, I.nz);
+    float v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = 0.0f;
+    if (mode == 0) {
+      v[0] = (float)(I.Q[q] / node_volume(I, m, n) * inv_in);
+      v[2] = dir ? (float)(I.phi[q] * inv_out) : 0.0f;
+    } else {
+      v[0] = (float)(res[q] * inv_in);
+      v[2] = dir ? 1.0f : 0.0f;
+    }
+    v[1] = (float)m / (float)I.nr;
+    store8(x_in + q * 16, v);
+    store8(x_in + q * 16 + 8, v + 8);
+  }
+}
+
+// candidate start from the network output (Dirichlet values of phi)
+__global__ void k_make_cand(int nr, int nz, const double* phi, const float* net, const UDev* ud,
+                            int mode, double* cand) {
+  const int W = nz + 1;
+  const long long npx = (long long)(nr + 1) * W;
+  const double s = ud->out_norm;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(q / W), n = (int)(q - (long long)m * W);
+    if (dirichlet_node(m, n, nr, nz)) cand[q] = phi[q];
+    else cand[q] = (mode == 0 ? 0.0 : phi[q]) + s * (double)net[q];
+  }
+}
+
+// mode 0 recording (after the solve): rho and phi
+__global__ void k_snap_record(Inst I, const UDev* ud, float* f0, float* f1, long long cap,
+                              int every) {
+  const Scalars* S = I.S;
+  if ((S->status & ST_FATAL) || (S->step % every) != 0) return;
+  const int W = I.nz + 1;
+  const long long npx = (long long)(I.nr + 1) * W;
+  const long long slot = ud->snap_count % cap;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(q / W), n = (int)(q - (long long)m * W);
+    f0[slot * npx + q] = (float)(I.Q[q] / node_volume(I, m, n));
+    f1[slot * npx + q] = (float)I.phi[q];
+  }
+}
+
+// mode 1 recording, before the solve: the residual of the previous solution
+// into the slot, the previous solution kept in FP64
+__global__ void k_snap_pre(Inst I, const UDev* ud, const float* res, float* f0, double* phi_prev,
+                           long long cap, int every) {
+  const Scalars* S = I.S;
+  if ((S->status & ST_FATAL) || (S->step % every) != 0) return;
+  const long long npx = (long long)(I.nr + 1) * (I.nz + 1);
+  const long long slot = ud->snap_count % cap;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
+       q += (long long)gridDim.x * blockDim.x) {
+    f0[slot * npx + q] = res[q];
+    phi_prev[q] = I.phi[q];
+  }
+}
+
+// mode 1 recording, after the solve: the change of phi
+__global__ void k_snap_post(Inst I, const UDev* ud, float* f1, const double* phi_prev,
+                            long long cap, int every) {
+  const Scalars* S = I.S;
+  if ((S->status & ST_FATAL) || (S->step % every) != 0) return;
+  const long long npx = (long long)(I.nr + 1) * (I.nz + 1);
+  const long long slot = ud->snap_count % cap;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
+       q += (long long)gridDim.x * blockDim.x)
+    f1[slot * npx + q] = (float)(I.phi[q] - phi_prev[q]);
+}
+
+__global__ void k_after_solve(Inst I, UDev* ud, int every, int record) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const Scalars* S = I.S;
+  if (S->status & ST_FATAL) return;
+  ud->iters_total += S->poisson_iters;
+  if (record && (S->step % every) == 0) ud->snap_count += 1;
+}
+
+// mean square of a recorded field over the stored snapshots (input and
+// output scales, set by the first training call)
+__global__ void k_ms_partial(const float* f, long long n, double* partial) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const double v = f[k];
+    s += v * v;
+  }
+  s = warp_sum_d(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    partial[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_norm_set(const double* partial, int nblk, long long n, double* target) {
+  if (threadIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partial[b];
+  const double rms = n > 0 ? sqrt(s / (double)n) : 0.0;
+  *target = rms > 0.0 ? rms : 1.0;
+}
+
+__global__ void k_adam(float* p, const float* g, float* m, float* v, long long n, float lr_t,
+                       float b1, float b2, float eps) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr_t * mi / (sqrtf(vi) + eps);
+  }
+}
+
+// packed BF16 weights of every conv layer: forward [cin_pad/16][9][cout][16]
+// and data-gradient (flipped taps, in/out swapped) [cout/16][9][cin_pad][16]
+struct PackTable {
+  int cin[kNumConv], cin_pad[kNumConv], cout[kNumConv];
+  long long w_off[kNumConv], wf_off[kNumConv], wd_off[kNumConv];
+};
+
+__global__ void k_pack_all(PackTable t, const float* p, bf16* wf, bf16* wd) {
+  const int L = blockIdx.y;
+  const int cin = t.cin[L], cinp = t.cin_pad[L], cout = t.cout[L];
+  const float* W = p + t.w_off[L];
+  const long long nf = (long long)cinp * 9 * cout;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nf;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e & 15);
+    long long r = e >> 4;
+    const int co = (int)(r % cout);
+    r /= cout;
+    const int tap = (int)(r % 9);
+    const int kc = (int)(r / 9);
+    const int ci = kc * 16 + k;
+    wf[t.wf_off[L] + e] = __float2bfloat16_rn(ci < cin ? W[((long long)co * cin + ci) * 9 + tap] : 0.0f);
+  }
+  if (t.wd_off[L] < 0) return;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nf;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e & 15);
+    long long r = e >> 4;
+    const int ci = (int)(r % cinp);
+    r /= cinp;
+    const int tapd = (int)(r % 9);
+    const int kc = (int)(r / 9);
+    const int co = kc * 16 + k;
+    wd[t.wd_off[L] + e] =
+        __float2bfloat16_rn(ci < cin ? W[((long long)co * cin + ci) * 9 + (8 - tapd)] : 0.0f);
+  }
+}
+
+int grid1(long long n, int threads) {
+  long long g = (n + threads - 1) / threads;
+  if (g > 4096) g = 4096;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct ULayerInfo {
+  int cin, cin_pad, cout;
+  long long w_off, b_off, wf_off, wd_off;
+};
+
+struct UNet {
+  int nr, nz, bmax;
+  int H[kLev], W[kLev];
+  double v_ref;
+  ULayerInfo L[kNumLayers];
+  PackTable pack;
+  long long np = 0, nwf = 0, nwd = 0;
+  float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+  bf16 *wf = nullptr, *wd = nullptr;
+  bf16* x_in = nullptr;
+  bf16 *ea[kLev] = {}, *cat[kLev - 1] = {}, *h3 = nullptr, *da[kLev - 1] = {}, *db[kLev - 1] = {};
+  bf16 *g_ea[kLev] = {}, *g_cat[kLev - 1] = {}, *g_h3 = nullptr, *g_da[kLev - 1] = {},
+       *g_db[kLev - 1] = {};
+  float *out = nullptr, *y = nullptr, *xs = nullptr;
+  float* part = nullptr;       // weight-gradient partials
+  double* red = nullptr;       // head partials
+  int red_blocks = 0;
+  double* d_loss = nullptr;    // per-iteration losses of a training call
+  long long d_loss_len = 0;
+  UDev* ud = nullptr;
+  double* gpart = nullptr;     // guess-selection partials
+  int gblk = 0;
+  int mode = 0;
+  double* cand = nullptr;      // candidate start (FP64 node array)
+  float* res = nullptr;        // residual of the previous solution (mode 1)
+  double* phi_prev = nullptr;  // previous solution (mode-1 recording)
+  float *snap_f0 = nullptr, *snap_f1 = nullptr;
+  long long snap_cap = 0;
+  int snap_every = 1;
+  bool warm = false;
+  long long adam_t = 0;
+  UAllocFn alloc = nullptr;
+  void* actx = nullptr;
+  long long npx(int l) const { return (long long)H[l] * W[l]; }
+};
+
+namespace {
+
+void* ua(UNet* u, size_t bytes) { return u->alloc(u->actx, bytes); }
+
+int cob_for(int cout) {
+  if (cout % 64 == 0) return 64;
+  if (cout % 48 == 0) return 48;
+  if (cout % 32 == 0) return 32;
+  return 16;
+}
+
+size_t conv_smem(int cob) { return (size_t)(kPH * kPW * kPS + 9 * cob * kPS) * sizeof(bf16); }
+
+cudaError_t run_conv(const ConvArgs& a, cudaStream_t st) {
+  const int cob = cob_for(a.cout);
+  const int tiles = ((a.W + kTW - 1) / kTW) * ((a.H + kTH - 1) / kTH) * a.B;
+  const dim3 grid(tiles, a.cout / cob);
+  const size_t sm = conv_smem(cob);
+  switch (cob) {
+    case 64: k_conv3<64><<<grid, kConvThreads, sm, st>>>(a); break;
+    case 48: k_conv3<48><<<grid, kConvThreads, sm, st>>>(a); break;
+    case 32: k_conv3<32><<<grid, kConvThreads, sm, st>>>(a); break;
+    default: k_conv3<16><<<grid, kConvThreads, sm, st>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+// forward conv of layer L
+cudaError_t conv_fwd(UNet* u, int Lx, const bf16* x, long long x_bs, int x_cs, int x_c0, int x_step,
+                     int x_w, bf16* y, long long y_bs, int y_cs, int y_c0, int H, int W, int B,
+                     cudaStream_t st) {
+  const ULayerInfo& L = u->L[Lx];
+  ConvArgs a;
+  a.x = x; a.x_bs = x_bs; a.x_cs = x_cs; a.x_c0 = x_c0; a.x_step = x_step; a.x_w = x_w;
+  a.w = u->wf + L.wf_off; a.bias = u->p + L.b_off; a.cin = L.cin_pad; a.cout = L.cout;
+  a.y = y; a.y_bs = y_bs; a.y_cs = y_cs; a.y_c0 = y_c0; a.y_step = 1; a.y_w = W;
+  a.H = H; a.W = W; a.B = B; a.relu = 1; a.accumulate = 0;
+  return run_conv(a, st);
+}
+
+// data gradient of layer L: dz (node step 1) -> dx (node step dx_step)
+cudaError_t conv_dgrad(UNet* u, int Lx, const bf16* dz, long long dz_bs, int dz_cs, int dz_c0,
+                       bf16* dx, long long dx_bs, int dx_cs, int dx_c0, int dx_step, int dx_w,
+                       int H, int W, int B, bool accumulate, cudaStream_t st) {
+  const ULayerInfo& L = u->L[Lx];
+  ConvArgs a;
+  a.x = dz; a.x_bs = dz_bs; a.x_cs = dz_cs; a.x_c0 = dz_c0; a.x_step = 1; a.x_w = W;
+  a.w = u->wd + L.wd_off; a.bias = nullptr; a.cin = L.cout; a.cout = L.cin_pad;
+  a.y = dx; a.y_bs = dx_bs; a.y_cs = dx_cs; a.y_c0 = dx_c0; a.y_step = dx_step; a.y_w = dx_w;
+  a.H = H; a.W = W; a.B = B; a.relu = 0; a.accumulate = accumulate ? 1 : 0;
+  return run_conv(a, st);
+}
+
+cudaError_t conv_wgrad(UNet* u, int Lx, const bf16* x, long long x_bs, int x_cs, int x_c0,
+                       int x_step, int x_w, const bf16* dz, long long dz_bs, int dz_cs, int dz_c0,
+                       int H, int W, int B, cudaStream_t st) {
+  const ULayerInfo& L = u->L[Lx];
+  WgArgs a;
+  a.x = x; a.x_bs = x_bs; a.x_cs = x_cs; a.x_c0 = x_c0; a.x_step = x_step; a.x_w = x_w;
+  a.dz = dz; a.dz_bs = dz_bs; a.dz_cs = dz_cs; a.dz_c0 = dz_c0;
+  a.cin = L.cin_pad; a.H = H; a.W = W; a.B = B;
+  a.pw = u->part;
+  a.pb = u->part + (long long)kMaxSplit * 9 * 16 * 64;
+  const int nkc = L.cin_pad >> 4;
+  const int T = B * ((W + kTW - 1) / kTW) * ((H + kTH - 1) / kTH);
+  int S = kMaxSplit / nkc;
+  if (S > T) S = T;
+  if (S < 1) S = 1;
+  const dim3 grid(nkc, S);
+  const size_t sm = (size_t)(kTH * kTW * (L.cout + 8) + kPH * kPW * kPS) * sizeof(bf16);
+  switch (L.cout) {
+    case 64: k_conv3_wgrad<64><<<grid, kWgThreads, sm, st>>>(a); break;
+    case 32: k_conv3_wgrad<32><<<grid, kWgThreads, sm, st>>>(a); break;
+    default: k_conv3_wgrad<16><<<grid, kWgThreads, sm, st>>>(a); break;
+  }
+  const long long n = (long long)L.cout * L.cin * 9 + L.cout;
+  k_wgrad_reduce<<<grid1(n, 256), 256, 0, st>>>(a.pw, a.pb, S, L.cin, L.cin_pad, L.cout,
+                                                u->g + L.w_off, u->g + L.b_off);
+  return cudaGetLastError();
+}
+
+cudaError_t relu_mask(bf16* g, int g_cs, int g_c0, const bf16* y, int y_cs, int y_c0, int C,
+                      long long npx, cudaStream_t st) {
+  k_relu_mask<<<grid1(npx * (C / 8), 256), 256, 0, st>>>(g, g_cs, g_c0, y, y_cs, y_c0, C, npx);
+  return cudaGetLastError();
+}
+
+// channel counts of the level buffers
+int cat_cs(int l) { return kCh[l + 1] + kCh[l]; }
+
+cudaError_t forward(UNet* u, int B, cudaStream_t st) {
+  const int* H = u->H;
+  const int* W = u->W;
+  cudaError_t e;
+  // encoder
+  e = conv_fwd(u, 0, u->x_in, u->npx(0) * kInPad, kInPad, 0, 1, W[0], u->ea[0], u->npx(0) * kCh[0],
+               kCh[0], 0, H[0], W[0], B, st);
+  if (e) return e;
+  e = conv_fwd(u, 1, u->ea[0], u->npx(0) * kCh[0], kCh[0], 0, 1, W[0], u->cat[0],
+               u->npx(0) * cat_cs(0), cat_cs(0), kCh[1], H[0], W[0], B, st);
+  if (e) return e;
+  for (int l = 1; l < kLev; ++l) {
+    e = conv_fwd(u, 2 * l, u->cat[l - 1], u->npx(l - 1) * cat_cs(l - 1), cat_cs(l - 1), kCh[l], 2,
+                 W[l - 1], u->ea[l], u->npx(l) * kCh[l], kCh[l], 0, H[l], W[l], B, st);
+    if (e) return e;
+    if (l < kLev - 1)
+      e = conv_fwd(u, 2 * l + 1, u->ea[l], u->npx(l) * kCh[l], kCh[l], 0, 1, W[l], u->cat[l],
+                   u->npx(l) * cat_cs(l), cat_cs(l), kCh[l + 1], H[l], W[l], B, st);
+    else
+      e = conv_fwd(u, 2 * l + 1, u->ea[l], u->npx(l) * kCh[l], kCh[l], 0, 1, W[l], u->h3,
+                   u->npx(l) * kCh[l], kCh[l], 0, H[l], W[l], B, st);
+    if (e) return e;
+  }
+  // decoder
+  const bf16* src = u->h3;
+  int src_c = kCh[kLev - 1];
+  for (int l = kLev - 2; l >= 0; --l) {
+    const long long n = (long long)B * u->npx(l) * (src_c / 8);
+    k_up<<<grid1(n, 256), 256, 0, st>>>(src, src_c, 0, H[l + 1], W[l + 1], u->cat[l], cat_cs(l), 0,
+                                        H[l], W[l], src_c, B);
+    const int la = 8 + 2 * (kLev - 2 - l), lb = la + 1;
+    e = conv_fwd(u, la, u->cat[l], u->npx(l) * cat_cs(l), cat_cs(l), 0, 1, W[l], u->da[l],
+                 u->npx(l) * kCh[l], kCh[l], 0, H[l], W[l], B, st);
+    if (e) return e;
+    e = conv_fwd(u, lb, u->da[l], u->npx(l) * kCh[l], kCh[l], 0, 1, W[l], u->db[l],
+                 u->npx(l) * kCh[l], kCh[l], 0, H[l], W[l], B, st);
+    if (e) return e;
+    src = u->db[l];
+    src_c = kCh[l];
+  }
+  const ULayerInfo& Lh = u->L[kHead];
+  const long long n0 = (long long)B * u->npx(0);
+  k_head_fwd<<<grid1(n0, 256), 256, 0, st>>>(u->db[0], u->p + Lh.w_off, u->p + Lh.b_off, u->out, n0);
+  return cudaGetLastError();
+}
+
+// backward from the MSE loss against u->y; the loss lands in *d_loss
+cudaError_t backward(UNet* u, int B, double* d_loss, cudaStream_t st) {
+  const int* H = u->H;
+  const int* W = u->W;
+  cudaError_t e;
+  const ULayerInfo& Lh = u->L[kHead];
+  const long long n0 = (long long)B * u->npx(0);
+  const double inv_n = 1.0 / (double)n0;
+  k_head_bwd<<<u->red_blocks, 256, 0, st>>>(u->db[0], u->p + Lh.w_off, u->out, u->y, u->g_db[0],
+                                            n0, inv_n, u->red);
+  k_head_final<<<1, 32, 0, st>>>(u->red, u->red_blocks, inv_n, d_loss, u->g + Lh.w_off,
+                                 u->g + Lh.b_off);
+  // decoder, level 0 first
+  for (int l = 0; l < kLev - 1; ++l) {
+    const int la = 8 + 2 * (kLev - 2 - l), lb = la + 1;
+    const long long np = (long long)B * u->npx(l);
+    const long long bs = u->npx(l) * kCh[l];
+    e = relu_mask(u->g_db[l], kCh[l], 0, u->db[l], kCh[l], 0, kCh[l], np, st);
+    if (e) return e;
+    e = conv_wgrad(u, lb, u->da[l], bs, kCh[l], 0, 1, W[l], u->g_db[l], bs, kCh[l], 0, H[l], W[l], B, st);
+    if (e) return e;
+    e = conv_dgrad(u, lb, u->g_db[l], bs, kCh[l], 0, u->g_da[l], bs, kCh[l], 0, 1, W[l], H[l], W[l],
+                   B, false, st);
+    if (e) return e;
+    e = relu_mask(u->g_da[l], kCh[l], 0, u->da[l], kCh[l], 0, kCh[l], np, st);
+    if (e) return e;
+    const long long cbs = u->npx(l) * cat_cs(l);
+    e = conv_wgrad(u, la, u->cat[l], cbs, cat_cs(l), 0, 1, W[l], u->g_da[l], bs, kCh[l], 0, H[l],
+                   W[l], B, st);
+    if (e) return e;
+    e = conv_dgrad(u, la, u->g_da[l], bs, kCh[l], 0, u->g_cat[l], cbs, cat_cs(l), 0, 1, W[l], H[l],
+                   W[l], B, false, st);
+    if (e) return e;
+    // up-sampling transpose into the coarse source's gradient
+    bf16* gsrc = l + 1 < kLev - 1 ? u->g_db[l + 1] : u->g_h3;
+    const int C = kCh[l + 1];
+    const long long n = (long long)B * u->npx(l + 1) * (C / 8);
+    k_up_t<<<grid1(n, 256), 256, 0, st>>>(u->g_cat[l], cat_cs(l), 0, H[l], W[l], gsrc, C, 0,
+                                          H[l + 1], W[l + 1], C, B);
+  }
+  // encoder, bottom level first
+  for (int l = kLev - 1; l >= 0; --l) {
+    const long long np = (long long)B * u->npx(l);
+    const long long bs = u->npx(l) * kCh[l];
+    bf16 *yo, *go;
+    int o_cs, o_c0;
+    if (l == kLev - 1) {
+      yo = u->h3; go = u->g_h3; o_cs = kCh[l]; o_c0 = 0;
+    } else {
+      yo = u->cat[l]; go = u->g_cat[l]; o_cs = cat_cs(l); o_c0 = kCh[l + 1];
+    }
+    const long long obs = u->npx(l) * o_cs;
+    e = relu_mask(go, o_cs, o_c0, yo, o_cs, o_c0, kCh[l], np, st);
+    if (e) return e;
+    e = conv_wgrad(u, 2 * l + 1, u->ea[l], bs, kCh[l], 0, 1, W[l], go, obs, o_cs, o_c0, H[l], W[l],
+                   B, st);
+    if (e) return e;
+    e = conv_dgrad(u, 2 * l + 1, go, obs, o_cs, o_c0, u->g_ea[l], bs, kCh[l], 0, 1, W[l], H[l], W[l],
+                   B, false, st);
+    if (e) return e;
+    e = relu_mask(u->g_ea[l], kCh[l], 0, u->ea[l], kCh[l], 0, kCh[l], np, st);
+    if (e) return e;
+    if (l == 0) {
+      e = conv_wgrad(u, 0, u->x_in, u->npx(0) * kInPad, kInPad, 0, 1, W[0], u->g_ea[0], bs, kCh[0], 0,
+                     H[0], W[0], B, st);
+      if (e) return e;
+    } else {
+      const long long pbs = u->npx(l - 1) * cat_cs(l - 1);
+      e = conv_wgrad(u, 2 * l, u->cat[l - 1], pbs, cat_cs(l - 1), kCh[l], 2, W[l - 1], u->g_ea[l], bs,
+                     kCh[l], 0, H[l], W[l], B, st);
+      if (e) return e;
+      e = conv_dgrad(u, 2 * l, u->g_ea[l], bs, kCh[l], 0, u->g_cat[l - 1], pbs, cat_cs(l - 1), kCh[l],
+                     2, W[l - 1], H[l], W[l], B, true, st);
+      if (e) return e;
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t pack_weights(UNet* u, cudaStream_t st) {
+  k_pack_all<<<dim3(64, kNumConv), 256, 0, st>>>(u->pack, u->p, u->wf, u->wd);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+long long unet_param_count() {
+  long long n = 0;
+  int ci[kNumConv], co[kNumConv];
+  for (int l = 0; l < kLev; ++l) {
+    ci[2 * l] = l == 0 ? kInReal : kCh[l - 1];
+    co[2 * l] = kCh[l];
+    ci[2 * l + 1] = kCh[l];
+    co[2 * l + 1] = kCh[l];
+  }
+  for (int l = kLev - 2, k = 8; l >= 0; --l, k += 2) {
+    ci[k] = kCh[l + 1] + kCh[l];
+    co[k] = kCh[l];
+    ci[k + 1] = kCh[l];
+    co[k + 1] = kCh[l];
+  }
+  for (int k = 0; k < kNumConv; ++k) n += (long long)co[k] * ci[k] * 9 + co[k];
+  return n + kCh[0] + 1;
+}
+
+UNet* unet_create(int nr, int nz, int bmax, int mode, unsigned long long seed, double v_ref,
+                  UAllocFn alloc, void* ctx, cudaStream_t st) {
+  if (nr % 8 || nz % 8 || nr < 8 || nz < 8 || bmax < 1 || !alloc || mode < 0 || mode > 1)
+    return nullptr;
+  UNet* u = new UNet();
+  u->mode = mode;
+  u->nr = nr;
+  u->nz = nz;
+  u->bmax = bmax;
+  u->v_ref = v_ref > 0.0 ? v_ref : 1.0;
+  u->alloc = alloc;
+  u->actx = ctx;
+  for (int l = 0; l < kLev; ++l) {
+    u->H[l] = (nr >> l) + 1;
+    u->W[l] = (nz >> l) + 1;
+  }
+  // layer table in the reference order
+  int ci[kNumLayers], co[kNumLayers];
+  for (int l = 0; l < kLev; ++l) {
+    ci[2 * l] = l == 0 ? kInReal : kCh[l - 1];
+    co[2 * l] = kCh[l];
+    ci[2 * l + 1] = kCh[l];
+    co[2 * l + 1] = kCh[l];
+  }
+  for (int l = kLev - 2, k = 8; l >= 0; --l, k += 2) {
+    ci[k] = kCh[l + 1] + kCh[l];
+    co[k] = kCh[l];
+    ci[k + 1] = kCh[l];
+    co[k + 1] = kCh[l];
+  }
+  ci[kHead] = kCh[0];
+  co[kHead] = 1;
+  long long off = 0, of = 0, od = 0;
+  for (int k = 0; k < kNumLayers; ++k) {
+    ULayerInfo& L = u->L[k];
+    L.cin = ci[k];
+    L.cin_pad = (ci[k] + 15) / 16 * 16;
+    L.cout = co[k];
+    L.w_off = off;
+    off += (long long)co[k] * ci[k] * (k == kHead ? 1 : 9);
+    L.b_off = off;
+    off += co[k];
+    L.wf_off = L.wd_off = -1;
+    if (k < kNumConv) {
+      L.wf_off = of;
+      of += (long long)L.cin_pad * 9 * L.cout;
+      if (k != 0) {
+        L.wd_off = od;
+        od += (long long)L.cin_pad * 9 * L.cout;
+      }
+      u->pack.cin[k] = L.cin;
+      u->pack.cin_pad[k] = L.cin_pad;
+      u->pack.cout[k] = L.cout;
+      u->pack.w_off[k] = L.w_off;
+      u->pack.wf_off[k] = L.wf_off;
+      u->pack.wd_off[k] = L.wd_off;
+    }
+  }
+  u->np = off;
+  u->nwf = of;
+  u->nwd = od;
+  bool ok = true;
+  auto A = [&](size_t b) {
+    void* p = ua(u, b);
+    ok = ok && p;
+    return p;
+  };
+  u->p = (float*)A(u->np * 4);
+  u->g = (float*)A(u->np * 4);
+  u->m = (float*)A(u->np * 4);
+  u->v = (float*)A(u->np * 4);
+  u->wf = (bf16*)A(u->nwf * 2);
+  u->wd = (bf16*)A(u->nwd * 2);
+  const long long B = bmax;
+  u->x_in = (bf16*)A(B * u->npx(0) * kInPad * 2);
+  for (int l = 0; l < kLev; ++l) {
+    u->ea[l] = (bf16*)A(B * u->npx(l) * kCh[l] * 2);
+    u->g_ea[l] = (bf16*)A(B * u->npx(l) * kCh[l] * 2);
+  }
+  for (int l = 0; l < kLev - 1; ++l) {
+    u->cat[l] = (bf16*)A(B * u->npx(l) * cat_cs(l) * 2);
+    u->g_cat[l] = (bf16*)A(B * u->npx(l) * cat_cs(l) * 2);
+    u->da[l] = (bf16*)A(B * u->npx(l) * kCh[l] * 2);
+    u->g_da[l] = (bf16*)A(B * u->npx(l) * kCh[l] * 2);
+    u->db[l] = (bf16*)A(B * u->npx(l) * kCh[l] * 2);
+    u->g_db[l] = (bf16*)A(B * u->npx(l) * kCh[l] * 2);
+  }
+  u->h3 = (bf16*)A(B * u->npx(kLev - 1) * kCh[kLev - 1] * 2);
+  u->g_h3 = (bf16*)A(B * u->npx(kLev - 1) * kCh[kLev - 1] * 2);
+  u->out = (float*)A(B * u->npx(0) * 4);
+  u->y = (float*)A(B * u->npx(0) * 4);
+  u->xs = (float*)A(B * u->npx(0) * kInReal * 4);
+  u->part = (float*)A(((size_t)kMaxSplit * 9 * 16 * 64 + (size_t)kMaxSplit * 64) * 4);
+  u->red_blocks = 296;
+  u->red = (double*)A((size_t)u->red_blocks * kHeadVals * 8);
+  u->d_loss_len = 1;
+  u->d_loss = (double*)A(8);
+  u->ud = (UDev*)A(sizeof(UDev));
+  u->gblk = guess_blocks(nr, nz);
+  u->gpart = (double*)A((size_t)u->gblk * 3 * 8);
+  u->cand = (double*)A(u->npx(0) * 8);
+  u->res = (float*)A(u->npx(0) * 4);
+  u->phi_prev = (double*)A(u->npx(0) * 8);
+  if (!ok) {
+    delete u;
+    return nullptr;
+  }
+  // He-normal weights, zero biases (std::mt19937_64 + normal_distribution)
+  std::vector<float> hp((size_t)u->np, 0.0f);
+  std::mt19937_64 rng(seed);
+  for (int k = 0; k < kNumLayers; ++k) {
+    const ULayerInfo& L = u->L[k];
+    const int taps = k == kHead ? 1 : 9;
+    std::normal_distribution<double> nd(0.0, std::sqrt(2.0 / (double)(L.cin * taps)));
+    for (long long q = 0; q < (long long)L.cout * L.cin * taps; ++q) hp[L.w_off + q] = (float)nd(rng);
+  }
+  UDev ud0;
+  std::memset(&ud0, 0, sizeof(ud0));
+  ud0.out_norm = mode == 0 ? u->v_ref : 0.0;
+  cudaError_t e = cudaMemcpyAsync(u->p, hp.data(), u->np * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(u->m, 0, u->np * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(u->v, 0, u->np * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(u->g, 0, u->np * 4, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(u->ud, &ud0, sizeof(UDev), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = pack_weights(u, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_conv3<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem(64));
+    cudaFuncSetAttribute(k_conv3<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem(48));
+    attr = true;
+  }
+  if (e != cudaSuccess) {
+    delete u;
+    return nullptr;
+  }
+  return u;
+}
+
+void unet_destroy(UNet* u) { delete u; }
+int unet_mode(const UNet* u) { return u->mode; }
+int unet_bmax(const UNet* u) { return u->bmax; }
+UDev* unet_dev(UNet* u) { return u->ud; }
+
+cudaError_t unet_set_params(UNet* u, const float* host, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(u->p, host, u->np * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = pack_weights(u, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+cudaError_t unet_get_params(UNet* u, float* host, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(host, u->p, u->np * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+cudaError_t unet_loss_grad(UNet* u, int B, const float* x, const float* y, float* out, float* grad,
+                           double* loss, cudaStream_t st) {
+  if (B < 1 || B > u->bmax) return cudaErrorInvalidValue;
+  const long long n0 = (long long)B * u->npx(0);
+  cudaError_t e = cudaMemcpyAsync(u->xs, x, n0 * kInReal * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && y) e = cudaMemcpyAsync(u->y, y, n0 * 4, cudaMemcpyHostToDevice, st);
+  if (e) return e;
+  k_pack_input<<<grid1(n0, 256), 256, 0, st>>>(u->xs, B, u->H[0], u->W[0], u->x_in);
+  e = forward(u, B, st);
+  if (e == cudaSuccess && y) e = backward(u, B, u->d_loss, st);
+  if (e == cudaSuccess && out) e = cudaMemcpyAsync(out, u->out, n0 * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && y && grad) e = cudaMemcpyAsync(grad, u->g, u->np * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && y && loss) e = cudaMemcpyAsync(loss, u->d_loss, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+cudaError_t unet_snapshots(UNet* u, long long cap, int every, UAllocFn alloc, void* ctx) {
+  if (cap < 1 || every < 1) return cudaErrorInvalidValue;
+  const size_t bytes = (size_t)cap * u->npx(0) * 4;
+  float* a = (float*)alloc(ctx, bytes);
+  float* b = (float*)alloc(ctx, bytes);
+  if (!a || !b) return cudaErrorMemoryAllocation;
+  u->snap_f0 = a;
+  u->snap_f1 = b;
+  u->snap_cap = cap;
+  u->snap_every = every;
+  return cudaSuccess;
+}
+
+bool unet_recording(const UNet* u) { return u->snap_cap > 0; }
+
+bool unet_pre_solve_needed(const UNet* u) { return u->warm || (u->mode == 1 && u->snap_cap > 0); }
+
+cudaError_t launch_pre_solve(UNet* u, const Inst& I, PoissonWork* pw, cudaStream_t st) {
+  const int g0 = grid1(u->npx(0), 256);
+  cudaError_t e = cudaSuccess;
+  if (u->mode == 1) {
+    e = launch_residual32(pw, I.Q, I.phi, u->res, st);
+    if (e) return e;
+    if (u->snap_cap > 0)
+      k_snap_pre<<<g0, 256, 0, st>>>(I, u->ud, u->res, u->snap_f0, u->phi_prev, u->snap_cap,
+                                     u->snap_every);
+  }
+  if (!u->warm) return cudaGetLastError();
+  k_step_input<<<g0, 256, 0, st>>>(I, u->ud, u->mode, u->res, u->x_in);
+  e = forward(u, 1, st);
+  if (e) return e;
+  k_make_cand<<<g0, 256, 0, st>>>(u->nr, u->nz, I.phi, u->out, u->ud, u->mode, u->cand);
+  e = launch_gs_sweeps(pw, I.Q, u->cand, 2, st);
+  if (e) return e;
+  return launch_guess_select(pw, I.Q, I.phi, u->cand, u->gpart, u->gblk, u->ud, &I.S->status, st);
+}
+
+cudaError_t launch_after_solve(UNet* u, const Inst& I, cudaStream_t st) {
+  const int g0 = grid1(u->npx(0), 256);
+  if (u->snap_cap > 0) {
+    if (u->mode == 0)
+      k_snap_record<<<g0, 256, 0, st>>>(I, u->ud, u->snap_f0, u->snap_f1, u->snap_cap, u->snap_every);
+    else
+      k_snap_post<<<g0, 256, 0, st>>>(I, u->ud, u->snap_f1, u->phi_prev, u->snap_cap, u->snap_every);
+  }
+  k_after_solve<<<1, 32, 0, st>>>(I, u->ud, u->snap_every, u->snap_cap > 0 ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t unet_train(UNet* u, int iters, int batch, float lr, unsigned long long seed,
+                       double* loss_first, double* loss_last, cudaStream_t st) {
+  if (iters < 1 || batch < 1 || batch > u->bmax || u->snap_cap <= 0) return cudaErrorInvalidValue;
+  UDev ud;
+  cudaError_t e = cudaMemcpyAsync(&ud, u->ud, sizeof(UDev), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e) return e;
+  const long long avail = ud.snap_count < u->snap_cap ? ud.snap_count : u->snap_cap;
+  if (avail < 1) return cudaErrorInvalidValue;
+  if (ud.in_norm <= 0.0) {
+    const long long n = avail * u->npx(0);
+    const int nb = 592;
+    k_ms_partial<<<nb, 256, 0, st>>>(u->snap_f0, n, u->red);
+    k_norm_set<<<1, 32, 0, st>>>(u->red, nb, n, &u->ud->in_norm);
+    if (u->mode == 1) {
+      k_ms_partial<<<nb, 256, 0, st>>>(u->snap_f1, n, u->red);
+      k_norm_set<<<1, 32, 0, st>>>(u->red, nb, n, &u->ud->out_norm);
+    }
+  }
+  if (u->d_loss_len < iters) {
+    double* d = (double*)ua(u, (size_t)iters * 8);
+    if (!d) return cudaErrorMemoryAllocation;
+    u->d_loss = d;
+    u->d_loss_len = iters;
+  }
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const long long n0 = (long long)batch * u->npx(0);
+  for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+    k_train_input<<<grid1(n0, 256), 256, 0, st>>>(u->snap_f0, u->snap_f1, avail, batch, seed, it,
+                                                  u->nr, u->nz, u->mode, u->ud, u->x_in, u->y);
+    e = forward(u, batch, st);
+    if (e == cudaSuccess) e = backward(u, batch, u->d_loss + it, st);
+    if (e != cudaSuccess) break;
+    ++u->adam_t;
+    const double t = (double)u->adam_t;
+    const float lr_t = (float)(lr * std::sqrt(1.0 - std::pow((double)b2, t)) / (1.0 - std::pow((double)b1, t)));
+    k_adam<<<grid1(u->np, 256), 256, 0, st>>>(u->p, u->g, u->m, u->v, u->np, lr_t, b1, b2, eps);
+    e = pack_weights(u, st);
+  }
+  double l0 = 0.0, l1 = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&l0, u->d_loss, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&l1, u->d_loss + (iters - 1), 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (loss_first) *loss_first = l0;
+  if (loss_last) *loss_last = l1;
+  return e;
+}
+
+void unet_set_warm(UNet* u, bool on) { u->warm = on; }
+bool unet_warm(const UNet* u) { return u->warm; }
+
+}  // namespace pic

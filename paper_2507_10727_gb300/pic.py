@@ -78,6 +78,16 @@ class PicDiag(C.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class PicUnetStats(C.Structure):
+    _fields_ = [("snapshots", C.c_int64), ("starts_previous", C.c_int64),
+                ("starts_network", C.c_int64), ("starts_zero", C.c_int64),
+                ("poisson_iters", C.c_int64), ("in_norm", C.c_double), ("out_norm", C.c_double),
+                ("last_start", C.c_int32), ("pad", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
 class PicKernelTime(C.Structure):
     _fields_ = [("name", C.c_char_p), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
@@ -128,6 +138,15 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         L.pic_profile.argtypes = [vp, C.c_int]
         L.pic_profile_read.argtypes = [vp, C.POINTER(PicKernelTime), C.c_int,
                                        C.POINTER(C.c_int)]
+        L.pic_unet_param_count.argtypes = [_I64]
+        L.pic_unet_create.argtypes = [vp, C.c_uint64, C.c_int, C.c_int]
+        L.pic_unet_set_params.argtypes = [vp, vp, C.c_int64]
+        L.pic_unet_get_params.argtypes = [vp, vp, C.c_int64]
+        L.pic_unet_loss_grad.argtypes = [vp, C.c_int, vp, vp, vp, vp, _D]
+        L.pic_unet_snapshots.argtypes = [vp, C.c_int64, C.c_int]
+        L.pic_unet_train.argtypes = [vp, C.c_int, C.c_int, C.c_float, C.c_uint64, _D, _D]
+        L.pic_unet_warm_start.argtypes = [vp, C.c_int]
+        L.pic_unet_stats_read.argtypes = [vp, C.POINTER(PicUnetStats)]
         L.pic_poisson_workspace_bytes.argtypes = [C.c_int, C.c_int]
         L.pic_poisson_workspace_bytes.restype = C.c_size_t
         L.pic_poisson_solve.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
@@ -362,3 +381,67 @@ def pic_poisson_solve(nr: int, nz: int, R: float, L: float, tol: float, max_iter
     if rc != PIC_OK and rc != -4:
         raise PicError(rc, "pic_poisson_solve failed")
     return rc, it.value, res.value
+
+
+# ---------------------------------------------------------------------------
+# learned warm start
+# ---------------------------------------------------------------------------
+def pic_unet_param_count() -> int:
+    n = C.c_int64()
+    rc = load_library().pic_unet_param_count(C.byref(n))
+    if rc != PIC_OK:
+        raise PicError(rc, "pic_unet_param_count")
+    return n.value
+
+
+def pic_unet_create(h: Handle, seed: int = 0, max_batch: int = 1, mode: int = 0):
+    _check(h, load_library().pic_unet_create(h.ptr, seed, max_batch, mode))
+
+
+def pic_unet_set_params(h: Handle, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(h, load_library().pic_unet_set_params(h.ptr, p.ctypes.data, p.size))
+
+
+def pic_unet_get_params(h: Handle) -> np.ndarray:
+    p = np.empty(pic_unet_param_count(), dtype=np.float32)
+    _check(h, load_library().pic_unet_get_params(h.ptr, p.ctypes.data, p.size))
+    return p
+
+
+def pic_unet_loss_grad(h: Handle, x, y=None):
+    """x: (B, 3, nr+1, nz+1), y: (B, nr+1, nz+1) or None.  Returns
+    (out (B, nr+1, nz+1), grad or None, loss or None) as FP32 numpy / float."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    B, _, H, W = x.shape
+    out = np.empty((B, H, W), dtype=np.float32)
+    yp = gp = 0
+    grad = None
+    loss = C.c_double()
+    if y is not None:
+        y = np.ascontiguousarray(y, dtype=np.float32).reshape(B, H, W)
+        grad = np.empty(pic_unet_param_count(), dtype=np.float32)
+        yp, gp = y.ctypes.data, grad.ctypes.data
+    _check(h, load_library().pic_unet_loss_grad(h.ptr, B, x.ctypes.data, yp or None,
+                                                out.ctypes.data, gp or None, C.byref(loss)))
+    return out, grad, (loss.value if y is not None else None)
+
+
+def pic_unet_snapshots(h: Handle, capacity: int, every: int = 1):
+    _check(h, load_library().pic_unet_snapshots(h.ptr, capacity, every))
+
+
+def pic_unet_train(h: Handle, iters: int, batch: int, lr: float, seed: int = 0):
+    a, b = C.c_double(), C.c_double()
+    _check(h, load_library().pic_unet_train(h.ptr, iters, batch, lr, seed, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def pic_unet_warm_start(h: Handle, on: bool = True):
+    _check(h, load_library().pic_unet_warm_start(h.ptr, 1 if on else 0))
+
+
+def pic_unet_stats(h: Handle) -> dict:
+    s = PicUnetStats()
+    _check(h, load_library().pic_unet_stats_read(h.ptr, C.byref(s)))
+    return s.as_dict()

@@ -79,3 +79,9 @@ def test_binding_fails_loudly_without_library(tmp_path):
             pic.load_library(str(tmp_path / "missing.so"))
     finally:
         pic._lib = saved
+
+
+def test_network_parameter_count_matches_reference(lib):
+    import paper_2507_10727_gb300 as pg
+    from oracle import unet
+    assert pg.pic_unet_param_count() == unet.n_params(unet.init_params(0))
