@@ -1056,6 +1056,7 @@ int pic_unet_loss_grad(pic_handle* h, int batch, const float* x, const float* y,
   if (rc != PIC_OK) return rc;
   if (!x || batch < 1 || batch > unet_bmax(h->unet)) return fail(h, PIC_ERR_INVALID, "batch or x");
   const cudaError_t e = unet_loss_grad(h->unet, batch, x, y, out, grad, loss, h->stream);
+  if (e == cudaErrorTimeout) return fail(h, PIC_ERR_TIMEOUT, "tensor-core wait reached its limit");
   if (e != cudaSuccess) return cuda_fail(h, e, "unet_loss_grad");
   return PIC_OK;
 }
@@ -1080,6 +1081,7 @@ int pic_unet_train(pic_handle* h, int iters, int batch, float lr, uint64_t seed,
   if (!unet_recording(h->unet)) return fail(h, PIC_ERR_INVALID, "no snapshots (pic_unet_snapshots)");
   const cudaError_t e = unet_train(h->unet, iters, batch, lr, seed, loss_first, loss_last, h->stream);
   if (e == cudaErrorInvalidValue) return fail(h, PIC_ERR_INVALID, "no snapshot recorded yet");
+  if (e == cudaErrorTimeout) return fail(h, PIC_ERR_TIMEOUT, "tensor-core wait reached its limit");
   if (e != cudaSuccess) return cuda_fail(h, e, "unet_train");
   return PIC_OK;
 }

@@ -661,11 +661,11 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
 
 // ----------------------------------------------------------------------------
 // Pieces of the learned warm start, on the fine FP64 operator of the solve.
-// Start selection: the residual norms ||Q - A x||^2 of three starting points
-// -- x = phi as it stands (the previous solution with this step's Dirichlet
-// values), x = the candidate from the network, x = 0 -- all with the
-// Dirichlet values of phi on the boundary; the smallest wins (ties keep the
-// earlier candidate) and is copied into phi's free nodes.
+// Start selection among three starting points -- x = phi as it stands (the
+// previous solution with this step's Dirichlet values), x = the candidate from
+// the network, x = 0 -- all with the Dirichlet values of phi on the boundary:
+// the smallest score (below) wins, ties keep the earlier candidate, and the
+// winner is copied into phi's free nodes.
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ bool free_node(int m, int n, int nr, int nz) {
   return m < nr && n >= 1 && n <= nz - 1;
@@ -677,6 +677,7 @@ __device__ __forceinline__ double start_value(int k, const double* phi, const do
   return k == 1 ? cand[i] : 0.0;
 }
 
+// Score of a start: ||Q - A x||_2^2 over the free nodes.
 __global__ void __launch_bounds__(256) k_guess_norms(PoissonWork W, const double* Q, const double* phi,
                                                      const double* cand, double* partial) {
   __shared__ double red[3][8];

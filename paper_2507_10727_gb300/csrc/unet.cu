@@ -4,14 +4,20 @@
 // the paper's solver is the judge: the guess only changes where the solve
 // starts, never where it ends).
 //
-// Convolutions are implicit GEMMs on the tensor cores (BF16 operands, FP32
-// accumulation): a CTA owns an 8 x 16 tile of output nodes; the input halo
-// (10 x 18 nodes x 16 channels) and the 9 taps' weights of one 16-channel
-// input chunk are staged in shared memory with cp.async, and each warp forms
-// one row of 16 outputs by ldmatrix + mma.m16n8k16 over the 9 taps.  The data
-// gradient is the same kernel run on flipped, transposed weights; the weight
-// gradient contracts over nodes (9 warps = 9 taps, split-K over tiles with a
-// deterministic reduction).
+// Forward and data-gradient convolutions run on the 5th-generation tensor
+// cores (tcgen05.mma, BF16 operands, FP32 accumulator in tensor memory): a CTA
+// owns 128 consecutive nodes of the row-major node grid with one virtual zero
+// column on each side, so that every 3x3 tap of those 128 outputs reads 128
+// consecutive (padded) input nodes.  Three such windows (rows above, at and
+// below) of one 16-channel input chunk and the chunk's 9 x COB weights are
+// staged in shared memory in the canonical K-major layout (8 nodes x 16 bytes
+// per core matrix); a tap's operand is a window at a start offset of 0-2
+// nodes.  One thread issues the 9 MMAs of a chunk; the next chunk is staged
+// while they run (two stages, mbarrier completion); the epilogue reads the
+// accumulator with tcgen05.ld.  The data gradient is the same kernel on
+// flipped, transposed weights.  The weight gradient contracts over nodes with
+// ldmatrix + mma.sync (9 warps = 9 taps, split-K over tiles, deterministic
+// reduction).
 #include <cmath>
 #include <cstring>
 #include <random>
@@ -39,7 +45,6 @@ constexpr int kNumLayers = 15;
 constexpr int kTH = 8, kTW = 16;              // output tile: rows x columns
 constexpr int kPH = kTH + 2, kPW = kTW + 2;   // input halo patch
 constexpr int kPS = 24;                       // bf16 per staged row (16 + 8 pad = 48 bytes)
-constexpr int kConvThreads = 256;             // 8 warps = 8 tile rows
 constexpr int kWgThreads = 288;               // 9 warps = 9 taps
 constexpr int kMaxSplit = 608;                // 4 x 152 weight-gradient CTAs
 constexpr int kHeadVals = 18;                 // loss, d bias, d w[16]
@@ -59,12 +64,6 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-__device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3,
-                                        const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(smem_u32(p)));
-}
 __device__ __forceinline__ void ldsm_x4_t(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3,
                                           const void* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
@@ -104,94 +103,232 @@ struct ConvArgs {
   int y_cs, y_c0, y_step, y_w;
   int H, W, B;        // logical node grid of the convolution, batch
   int relu, accumulate;
+  int* err;           // set to 1 if a tensor-core wait reached its time limit
 };
 
-template <int COB>
-__global__ void __launch_bounds__(kConvThreads) k_conv3(ConvArgs a) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  bf16* patch = reinterpret_cast<bf16*>(sm_raw);
-  bf16* wsm = patch + kPH * kPW * kPS;
-  const int tw = (a.W + kTW - 1) / kTW, th = (a.H + kTH - 1) / kTH;
-  int t = blockIdx.x;
-  const int b = t / (tw * th);
-  t -= b * tw * th;
-  const int i0 = (t / tw) * kTH, j0 = (t % tw) * kTW;
-  const int co0 = blockIdx.y * COB;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bf16* xb = a.x + (long long)b * a.x_bs;
-  float acc[COB / 8][4];
+__device__ __forceinline__ void load8(const bf16* p, float* v) {
+  const uint4 u = *reinterpret_cast<const uint4*>(p);
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
 #pragma unroll
-  for (int q = 0; q < COB / 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.0f;
-  const int nkc = a.cin >> 4;
-  for (int kc = 0; kc < nkc; ++kc) {
-    for (int e = threadIdx.x; e < kPH * kPW * 2; e += blockDim.x) {
-      const int p = e >> 1, half = e & 1;
-      const int pi = p / kPW, pj = p - pi * kPW;
-      const int gi = i0 + pi - 1, gj = j0 + pj - 1;
-      const bool ok = gi >= 0 && gi < a.H && gj >= 0 && gj < a.W;
-      const bf16* src = ok ? xb + ((long long)gi * a.x_step * a.x_w + (long long)gj * a.x_step) * a.x_cs +
-                                 a.x_c0 + kc * 16 + half * 8
-                           : a.x;
-      cp_async16(patch + p * kPS + half * 8, src, ok ? 16 : 0);
+  for (int q = 0; q < 4; ++q) {
+    const float2 f = __bfloat1622float2(h[q]);
+    v[2 * q] = f.x;
+    v[2 * q + 1] = f.y;
+  }
+}
+__device__ __forceinline__ void store8(bf16* p, const float* v) {
+  uint4 u;
+  __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) h[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+  *reinterpret_cast<uint4*>(p) = u;
+}
+
+// ---- tcgen05 helpers --------------------------------------------------------
+constexpr int kTcThreads = 128;          // 4 warps = the 4 TMEM lane quarters
+constexpr int kTcM = 128;                // output nodes per CTA (MMA M)
+constexpr int kWinPos = 136;             // staged nodes per window (130 used)
+constexpr int kAStage = 3 * 2 * kWinPos * 16;   // 3 windows x 2 k-groups, bytes
+constexpr double kWaitLimitNs = 1.0e9;   // tensor-core completion wait limit
+
+__host__ __device__ constexpr int tc_b_stage(int cob) { return 9 * 2 * cob * 16; }
+__host__ __device__ constexpr int tc_smem(int cob) { return 2 * (kAStage + tc_b_stage(cob)) + 64; }
+__host__ __device__ constexpr int tc_tcols(int cob) { return cob <= 32 ? 32 : 64; }
+
+// shared-memory matrix descriptor: canonical K-major layout without swizzle;
+// lbo = byte step between core matrices along K, sbo = along M (or N)
+__device__ __forceinline__ unsigned long long smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+  unsigned long long d = (unsigned long long)((addr >> 4) & 0x3FFFu);
+  d |= (unsigned long long)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (unsigned long long)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= 1ULL << 46;   // descriptor version of the 5th-generation tensor cores
+  return d;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// wait for the phase of the given parity; false after the time limit
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned a = smem_u32(bar);
+  double t0 = -1.0;
+  for (unsigned it = 0;; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 1023u) == 0u) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t0 < 0.0) t0 = (double)t;
+      else if ((double)t - t0 > kWaitLimitNs) return false;
     }
-    for (int e = threadIdx.x; e < 9 * COB * 2; e += blockDim.x) {
-      const int row = e >> 1, half = e & 1;
-      const int tap = row / COB, c = row - tap * COB;
-      const bf16* src = a.w + (((long long)kc * 9 + tap) * a.cout + co0 + c) * 16 + half * 8;
-      cp_async16(wsm + row * kPS + half * 8, src, 16);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+template <int COB>
+__global__ void __launch_bounds__(kTcThreads) k_conv3_tc(ConvArgs a) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  constexpr int BST = tc_b_stage(COB);
+  constexpr unsigned TCOLS = tc_tcols(COB);
+  unsigned char* stA0 = sm;
+  unsigned char* stB0 = sm + 2 * kAStage;
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sm + 2 * (kAStage + BST));
+  unsigned* taddr_s = reinterpret_cast<unsigned*>(mbar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int Wp = a.W + 2;
+  // padded node index q = (i + 1) * Wp + j + 1 of one image (< 2^31 for any grid that fits)
+  const int q_first = Wp + 1, q_last = a.H * Wp + a.W;
+  const int T = (q_last - q_first + kTcM) / kTcM;
+  const int b = blockIdx.x / T, t = blockIdx.x - b * T;
+  const int q0 = q_first + kTcM * t;
+  const int co0 = blockIdx.y * COB;
+  const bf16* xb = a.x + (long long)b * a.x_bs;
+
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(taddr_s)),
+                 "r"(TCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // stage chunk kc (16 input channels) into buffer s
+  auto stage = [&](int kc, int s) {
+    unsigned char* A = stA0 + s * kAStage;
+    unsigned char* Bs = stB0 + s * BST;
+    for (int e = tid; e < 3 * 2 * 130; e += kTcThreads) {
+      const int w = e / 260, r = e - w * 260, g = r / 130, p = r - g * 130;
+      const int qq = q0 + (w - 1) * Wp - 1 + p;     // >= 0 since q0 >= Wp + 1
+      const int pi = (int)((unsigned)qq / (unsigned)Wp);
+      const int pj = qq - pi * Wp;
+      const bool ok = pi >= 1 && pi <= a.H && pj >= 1 && pj <= a.W;
+      const bf16* src = ok ? xb + ((long long)(pi - 1) * a.x_step * a.x_w + (long long)(pj - 1) * a.x_step) * a.x_cs +
+                                 a.x_c0 + kc * 16 + g * 8
+                           : a.x;
+      cp_async16(A + ((w * 2 + g) * kWinPos + p) * 16, src, ok ? 16 : 0);
+    }
+    for (int e = tid; e < 9 * 2 * COB; e += kTcThreads) {
+      const int tap = e / (2 * COB), r = e - tap * 2 * COB, g = r / COB, c = r - g * COB;
+      const bf16* src = a.w + (((long long)kc * 9 + tap) * a.cout + co0 + c) * 16 + g * 8;
+      cp_async16(Bs + ((tap * 2 + g) * COB + c) * 16, src, 16);
     }
     cp_async_commit();
-    cp_async_wait_all();
-    __syncthreads();
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int dr = tap / 3, dc = tap - dr * 3;
-      unsigned a0, a1, a2, a3;
-      {
-        // A (16 nodes x 16 channels): matrices (nodes 0-7 | 8-15) x (k 0-7 | 8-15)
-        const int mrow = (lane & 7) + ((lane >> 3) & 1) * 8;
-        const int kof = (lane >> 4) * 8;
-        ldsm_x4(a0, a1, a2, a3, patch + ((warp + dr) * kPW + mrow + dc) * kPS + kof);
+  };
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned taddr = *taddr_s;
+  // D f32, A and B bf16, both K-major, N = COB, M = 128
+  const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(COB >> 3) << 17) |
+                         ((unsigned)(kTcM >> 4) << 24);
+  const int nkc = a.cin >> 4;
+  bool bad = false;
+  stage(0, 0);
+  for (int kc = 0; kc < nkc; ++kc) {
+    const int s = kc & 1;
+    if (kc + 1 < nkc) {
+      // the MMAs of chunk kc - 1 read buffer s ^ 1
+      bool f = false;
+      if (kc >= 1) f = !mbar_wait(&mbar[s ^ 1], (unsigned)((kc - 1) >> 1) & 1u);
+      if (__syncthreads_or(f)) {
+        bad = true;
+        break;
       }
-#pragma unroll
-      for (int nt = 0; nt < COB / 8; nt += 2) {
-        // B (16 channels x 16 outputs, stored output-major): two 8-wide n tiles
-        const int nrow = (lane & 7) + (lane >> 4) * 8;
-        const int kb = ((lane >> 3) & 1) * 8;
-        unsigned b0, b1, b2, b3;
-        ldsm_x4(b0, b1, b2, b3, wsm + (tap * COB + nt * 8 + nrow) * kPS + kb);
-        mma_bf16(acc[nt], a0, a1, a2, a3, b0, b1);
-        mma_bf16(acc[nt + 1], a0, a1, a2, a3, b2, b3);
-      }
+      stage(kc + 1, s ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const unsigned aA = smem_u32(stA0 + s * kAStage), aB = smem_u32(stB0 + s * BST);
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const int dr = tap / 3, dc = tap - dr * 3;
+        const unsigned long long ad =
+            smem_desc(aA + (unsigned)((dr * 2 * kWinPos + dc) * 16), kWinPos * 16, 128);
+        const unsigned long long bd = smem_desc(aB + (unsigned)(tap * 2 * COB * 16), COB * 16, 128);
+        const unsigned acc = (kc > 0 || tap > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&mbar[s]))
+                   : "memory");
+    }
   }
-  const int gi = i0 + warp;
-  if (gi >= a.H) return;
-  bf16* yb = a.y + (long long)b * a.y_bs;
+  if (!bad) {
+    const bool f = !mbar_wait(&mbar[(nkc - 1) & 1], (unsigned)((nkc - 1) >> 1) & 1u);
+    bad = __syncthreads_or(f);
+  }
+  if (bad) {
+    cp_async_wait<0>();
+    if (tid == 0) atomicExch(a.err, 1);
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int q = q0 + 32 * warp + lane;
+    const int pi = (int)((unsigned)q / (unsigned)Wp);
+    const int pj = q - pi * Wp;
+    const bool mine = q <= q_last && pj >= 1 && pj <= a.W;
+    bf16* dst = a.y + (long long)b * a.y_bs +
+                ((long long)(pi - 1) * a.y_step * a.y_w + (long long)(pj - 1) * a.y_step) * a.y_cs +
+                a.y_c0 + co0;
 #pragma unroll
-  for (int nt = 0; nt < COB / 8; ++nt) {
-    const int co = co0 + nt * 8 + (lane & 3) * 2;
-    const float bb0 = a.bias ? a.bias[co] : 0.0f, bb1 = a.bias ? a.bias[co + 1] : 0.0f;
+    for (int c = 0; c < COB; c += 16) {
+      float v[16];
+      tmem_ld16(taddr + ((unsigned)(32 * warp) << 16) + (unsigned)c, v);   // all lanes take part
+      if (!mine) continue;
 #pragma unroll
-    for (int hf = 0; hf < 2; ++hf) {
-      const int gj = j0 + (lane >> 2) + hf * 8;
-      if (gj >= a.W) continue;
-      float v0 = acc[nt][hf * 2] + bb0, v1 = acc[nt][hf * 2 + 1] + bb1;
-      __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(
-          yb + ((long long)gi * a.y_step * a.y_w + (long long)gj * a.y_step) * a.y_cs + a.y_c0 + co);
+      for (int k = 0; k < 16; ++k) v[k] += a.bias ? a.bias[co0 + c + k] : 0.0f;
       if (a.accumulate) {
-        const float2 o = __bfloat1622float2(*dst);
-        v0 += o.x;
-        v1 += o.y;
+        float o[16];
+        load8(dst + c, o);
+        load8(dst + c + 8, o + 8);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] += o[k];
       }
       if (a.relu) {
-        v0 = fmaxf(v0, 0.0f);
-        v1 = fmaxf(v1, 0.0f);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = fmaxf(v[k], 0.0f);
       }
-      *dst = __floats2bfloat162_rn(v0, v1);
+      store8(dst + c, v);
+      store8(dst + c + 8, v + 8);
     }
   }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TCOLS));
 }
 
 // ---------------------------------------------------------------------------
@@ -338,24 +475,6 @@ __global__ void k_relu_mask(bf16* g, int g_cs, int g_c0, const bf16* y, int y_cs
     }
     *gp = gv;
   }
-}
-
-__device__ __forceinline__ void load8(const bf16* p, float* v) {
-  const uint4 u = *reinterpret_cast<const uint4*>(p);
-  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const float2 f = __bfloat1622float2(h[q]);
-    v[2 * q] = f.x;
-    v[2 * q + 1] = f.y;
-  }
-}
-__device__ __forceinline__ void store8(bf16* p, const float* v) {
-  uint4 u;
-  __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) h[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-  *reinterpret_cast<uint4*>(p) = u;
 }
 
 // bilinear node up-sampling: coarse node (I, J) sits on fine node (2I, 2J)
@@ -631,7 +750,8 @@ __global__ void k_snap_post(Inst I, const UDev* ud, float* f1, const double* phi
 
 __global__ void k_after_solve(Inst I, UDev* ud, int every, int record) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const Scalars* S = I.S;
+  Scalars* S = I.S;
+  if (ud->err) atomicOr(&S->status, ST_TIMEOUT);
   if (S->status & ST_FATAL) return;
   ud->iters_total += S->poisson_iters;
   if (record && (S->step % every) == 0) ud->snap_count += 1;
@@ -780,18 +900,16 @@ int cob_for(int cout) {
   return 16;
 }
 
-size_t conv_smem(int cob) { return (size_t)(kPH * kPW * kPS + 9 * cob * kPS) * sizeof(bf16); }
-
 cudaError_t run_conv(const ConvArgs& a, cudaStream_t st) {
   const int cob = cob_for(a.cout);
-  const int tiles = ((a.W + kTW - 1) / kTW) * ((a.H + kTH - 1) / kTH) * a.B;
-  const dim3 grid(tiles, a.cout / cob);
-  const size_t sm = conv_smem(cob);
+  const long long count = (long long)(a.H - 1) * (a.W + 2) + a.W;   // padded-row nodes spanned
+  const int T = (int)((count + kTcM - 1) / kTcM);
+  const dim3 grid(T * a.B, a.cout / cob);
   switch (cob) {
-    case 64: k_conv3<64><<<grid, kConvThreads, sm, st>>>(a); break;
-    case 48: k_conv3<48><<<grid, kConvThreads, sm, st>>>(a); break;
-    case 32: k_conv3<32><<<grid, kConvThreads, sm, st>>>(a); break;
-    default: k_conv3<16><<<grid, kConvThreads, sm, st>>>(a); break;
+    case 64: k_conv3_tc<64><<<grid, kTcThreads, tc_smem(64), st>>>(a); break;
+    case 48: k_conv3_tc<48><<<grid, kTcThreads, tc_smem(48), st>>>(a); break;
+    case 32: k_conv3_tc<32><<<grid, kTcThreads, tc_smem(32), st>>>(a); break;
+    default: k_conv3_tc<16><<<grid, kTcThreads, tc_smem(16), st>>>(a); break;
   }
   return cudaGetLastError();
 }
@@ -805,7 +923,7 @@ cudaError_t conv_fwd(UNet* u, int Lx, const bf16* x, long long x_bs, int x_cs, i
   a.x = x; a.x_bs = x_bs; a.x_cs = x_cs; a.x_c0 = x_c0; a.x_step = x_step; a.x_w = x_w;
   a.w = u->wf + L.wf_off; a.bias = u->p + L.b_off; a.cin = L.cin_pad; a.cout = L.cout;
   a.y = y; a.y_bs = y_bs; a.y_cs = y_cs; a.y_c0 = y_c0; a.y_step = 1; a.y_w = W;
-  a.H = H; a.W = W; a.B = B; a.relu = 1; a.accumulate = 0;
+  a.H = H; a.W = W; a.B = B; a.relu = 1; a.accumulate = 0; a.err = &u->ud->err;
   return run_conv(a, st);
 }
 
@@ -818,7 +936,7 @@ cudaError_t conv_dgrad(UNet* u, int Lx, const bf16* dz, long long dz_bs, int dz_
   a.x = dz; a.x_bs = dz_bs; a.x_cs = dz_cs; a.x_c0 = dz_c0; a.x_step = 1; a.x_w = W;
   a.w = u->wd + L.wd_off; a.bias = nullptr; a.cin = L.cout; a.cout = L.cin_pad;
   a.y = dx; a.y_bs = dx_bs; a.y_cs = dx_cs; a.y_c0 = dx_c0; a.y_step = dx_step; a.y_w = dx_w;
-  a.H = H; a.W = W; a.B = B; a.relu = 0; a.accumulate = accumulate ? 1 : 0;
+  a.H = H; a.W = W; a.B = B; a.relu = 0; a.accumulate = accumulate ? 1 : 0; a.err = &u->ud->err;
   return run_conv(a, st);
 }
 
@@ -1138,8 +1256,10 @@ UNet* unet_create(int nr, int nz, int bmax, int mode, unsigned long long seed, d
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_conv3<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem(64));
-    cudaFuncSetAttribute(k_conv3<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem(48));
+    cudaFuncSetAttribute(k_conv3_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(64));
+    cudaFuncSetAttribute(k_conv3_tc<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(48));
+    cudaFuncSetAttribute(k_conv3_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(32));
+    cudaFuncSetAttribute(k_conv3_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(16));
     attr = true;
   }
   if (e != cudaSuccess) {
@@ -1153,6 +1273,15 @@ void unet_destroy(UNet* u) { delete u; }
 int unet_mode(const UNet* u) { return u->mode; }
 int unet_bmax(const UNet* u) { return u->bmax; }
 UDev* unet_dev(UNet* u) { return u->ud; }
+
+// the tensor-core kernels' error word (a completion wait reached its limit)
+cudaError_t unet_check_err(UNet* u, cudaStream_t st) {
+  int err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, &u->ud->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && err) e = cudaErrorTimeout;
+  return e;
+}
 
 cudaError_t unet_set_params(UNet* u, const float* host, cudaStream_t st) {
   cudaError_t e = cudaMemcpyAsync(u->p, host, u->np * 4, cudaMemcpyHostToDevice, st);
@@ -1181,6 +1310,7 @@ cudaError_t unet_loss_grad(UNet* u, int B, const float* x, const float* y, float
   if (e == cudaSuccess && y && grad) e = cudaMemcpyAsync(grad, u->g, u->np * 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && y && loss) e = cudaMemcpyAsync(loss, u->d_loss, 8, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = unet_check_err(u, st);
   return e;
 }
 
@@ -1278,6 +1408,7 @@ cudaError_t unet_train(UNet* u, int iters, int batch, float lr, unsigned long lo
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (loss_first) *loss_first = l0;
   if (loss_last) *loss_last = l1;
+  if (e == cudaSuccess) e = unet_check_err(u, st);
   return e;
 }
 

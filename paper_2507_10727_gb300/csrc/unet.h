@@ -36,7 +36,7 @@ struct UDev {
   double in_norm;           // input scale of channel 0 (set by the first training)
   double out_norm;          // output scale (mode 0: V_ref; mode 1: set by the first training)
   int choice;               // guess used by the last solve
-  int pad;
+  int err;                  // 1 once a tensor-core wait reached its time limit
 };
 
 typedef void* (*UAllocFn)(void* ctx, size_t bytes);
@@ -82,8 +82,8 @@ cudaError_t launch_residual32(PoissonWork* pw, const double* Q, const double* ph
 // `sweeps` red-black Gauss-Seidel sweeps on A x = Q (Dirichlet values in x)
 cudaError_t launch_gs_sweeps(PoissonWork* pw, const double* Q, double* x, int sweeps,
                              cudaStream_t st);
-// start of the solve: the smallest ||Q - A x|| of x in {phi, cand, 0}
-// (Dirichlet values of phi) is copied into phi; counts in *ud
+// start of the solve: of x in {phi, cand, 0} (Dirichlet values of phi) the
+// one with the smallest residual norm is copied into phi; counts in *ud
 cudaError_t launch_guess_select(PoissonWork* pw, const double* Q, double* phi, const double* cand,
                                 double* partial, int nblk, UDev* ud, const int* status,
                                 cudaStream_t st);
