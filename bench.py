@@ -50,6 +50,8 @@ BYTES_PER_PARTICLE_FP32 = 64.0
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA pipes-lanes per SM per clock x 2
 # flop x 2.07 GHz = 1.26 TFLOP/s (nominal 1.25); scaled to the measured clock.
 FP64_FLOP_PER_CLK = 152 * 2 * 2
+# steps a new handle spends tuning the push's chunk size (pic_tuned_chunk)
+AUTOTUNE_STEPS = 4
 
 
 def parse():
@@ -239,7 +241,7 @@ def sweep_workload(args):
 def run_sweep(args, torch, pg):
     insts = sweep_workload(args)
     ntot = sum(2 * parts["e"]["r"].shape[0] for _, parts in insts)
-    warm = max(args.warmup, 5)           # includes the 4 autotuning steps
+    warm = AUTOTUNE_STEPS + args.warmup
 
     def load(h, k, parts):
         for key, sp in (("e", 0), ("i", 1)):
@@ -268,7 +270,7 @@ def run_sweep(args, torch, pg):
     pg.pic_step(ens, min(args.steps, 5))
     prof = pg.pic_profile_read(ens)
     pg.pic_profile(ens, False)
-    nprof = max(1, prof["push_e"]["launches"])
+    nprof = max(1, prof["push"]["launches"])
     tuned = pg.pic_tuned_chunk(ens)
     graph = pg.pic_uses_graph(ens)
     pg.pic_destroy(ens)
@@ -277,7 +279,7 @@ def run_sweep(args, torch, pg):
     for p, parts in insts:
         h = pg.pic_create(p)
         load(h, 0, parts)
-        pg.pic_step(h, args.warmup)
+        pg.pic_step(h, AUTOTUNE_STEPS + args.warmup)
         singles.append(h)
     pg.pic_sync(singles[0])
     ms_s, ps_s = timed([(h, 0) for h in singles], args.steps)
@@ -346,7 +348,7 @@ def run_learned(args, torch, pg):
         pg.pic_step(h, 10)
         prof = pg.pic_profile_read(h)
         pg.pic_profile(h, False)
-        nprof = max(1, prof["push_e"]["launches"])
+        nprof = max(1, prof["push"]["launches"])
         return {"value": (d1["particle_steps"] - d0["particle_steps"]) / (ms / 1e3),
                 "ms_per_step": ms / args.steps,
                 "poisson_iters_per_step": (s1["poisson_iters"] - s0["poisson_iters"]) / args.steps,
@@ -418,6 +420,8 @@ def main():
     for k, sp in (("e", 0), ("i", 1)):
         pg.pic_set_particles(h, 0, sp, parts[k])
     pg.pic_solve_fields(h, 0)
+    # the first 4 steps of a handle tune the push's chunk size (eager, untimed)
+    pg.pic_step(h, AUTOTUNE_STEPS)
     pg.pic_step(h, args.warmup)
     pg.pic_sync(h)
     d0 = pg.pic_diagnostics(h, 0)
@@ -452,7 +456,7 @@ def main():
     prof = pg.pic_profile_read(h)
     pg.pic_profile(h, False)
     d2 = pg.pic_diagnostics(h, 0)
-    prof_steps = max(1, prof["push_e"]["launches"])
+    prof_steps = max(1, prof["push"]["launches"])
     prof_ps = d2["particle_steps"] - d1["particle_steps"]
     ne, ni = pg.pic_count(h, 0, 0), pg.pic_count(h, 0, 1)
 
@@ -460,15 +464,15 @@ def main():
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     fp64_peak = FP64_FLOP_PER_CLK * sm_mhz * 1e6 / 1e12       # TFLOP/s at the loaded clock
-    dom = "push_e" if prof["push_e"]["total_ms"] >= prof["push_i"]["total_ms"] else "push_i"
-    dom_ms = prof[dom]["total_ms"] / prof_steps
-    dom_n = (ne if dom == "push_e" else ni)
+    # the dominant kernel: the push of both species (one launch per step)
+    push_ms = prof["push"]["total_ms"] / prof_steps
+    n_pushed = ne + ni
     g = 0 if args.gather == "ec" else 1
-    achieved = FLOPS_PER_PARTICLE[g] * dom_n / (dom_ms / 1e3) / 1e12
-    achieved_bw = BYTES_PER_PARTICLE * dom_n / (dom_ms / 1e3) / 1e9
+    achieved = FLOPS_PER_PARTICLE[g] * n_pushed / (push_ms / 1e3) / 1e12
+    achieved_bw = BYTES_PER_PARTICLE * n_pushed / (push_ms / 1e3) / 1e9
     per_kernel = {k: v["total_ms"] / prof_steps for k, v in prof.items()}
     if args.precision == "fp64":
-        roofline = {"bound": "alu", "kernel": f"k_push ({dom})", "achieved": achieved,
+        roofline = {"bound": "alu", "kernel": "k_push_all (both species)", "achieved": achieved,
                     "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
                     "traffic": None,
                     "peak_note": f"FP64 pipes: 152 SMs x 4 flop/clk at the median loaded SM "
@@ -478,13 +482,15 @@ def main():
                                  "peak_kind": peak_kind,
                                  "bytes_per_particle": BYTES_PER_PARTICLE},
                     "flops_per_particle": FLOPS_PER_PARTICLE[g],
+                    "particles_per_launch": n_pushed,
                     "per_kernel_ms_per_step": per_kernel}
     else:
-        bw32 = BYTES_PER_PARTICLE_FP32 * dom_n / (dom_ms / 1e3) / 1e9
-        roofline = {"bound": "hbm", "kernel": f"k_push32 ({dom})", "achieved": bw32,
+        bw32 = BYTES_PER_PARTICLE_FP32 * n_pushed / (push_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "k_push32_all (both species)", "achieved": bw32,
                     "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
                     "frac": bw32 / peaks.get("hbm_gbs", 6800.0), "traffic": None,
                     "peak_kind": peak_kind, "bytes_per_particle": BYTES_PER_PARTICLE_FP32,
+                    "particles_per_launch": n_pushed,
                     "per_kernel_ms_per_step": per_kernel}
 
     # end to end through the C ABI with host buffers: upload the state from
@@ -533,6 +539,7 @@ def main():
                 "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
                 "data": "synthetic", "config": config_block(p, n, args),
                 "gpu_launches": args.steps * 10, "cuda_graph": pg.pic_uses_graph(h),
+                "autotune_steps": AUTOTUNE_STEPS, "push_particles_per_thread": pg.pic_tuned_chunk(h),
                 "poisson": {"iters_last_step": d1["poisson_iters"],
                             "resid_last_step": d1["poisson_resid"],
                             "ms_per_step": per_kernel["poisson"]},

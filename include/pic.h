@@ -179,21 +179,24 @@ int pic_set_circuit(pic_handle* h, int instance, double Vc, int64_t step, const 
 int pic_set_next_id(pic_handle* h, int instance, int64_t next_id);
 int pic_get_next_id(pic_handle* h, int instance, int64_t* next_id);
 
-/* Advance all instances by nsteps time steps.  Async (see conventions).
- * On a stream other than the legacy default stream the first call captures
- * one step of all instances into a CUDA graph and later steps replay it
- * (eager launches while pic_profile is on, or if capture is unavailable). */
+/* Advance all instances by nsteps time steps.  Async (see conventions), except
+ * for the first four steps of a handle, which tune the push (see
+ * pic_tuned_chunk) and wait for their own completion.  After them, on a stream
+ * other than the legacy default stream, one step of all instances is captured
+ * into a CUDA graph and replayed (eager launches while pic_profile is on, or
+ * if capture is unavailable). */
 int pic_step(pic_handle* h, int64_t nsteps);
 
 /* 1 when pic_step replays a captured CUDA graph on this handle, else 0. */
 int pic_uses_graph(pic_handle* h);
 
-/* Ensembles (n_instances > 1): the particle pushes of all instances run as
- * persistent kernels over a device queue of (instance, chunk) work items, the
- * Poisson solves of all instances in one grouped launch.  The first four
- * steps of a handle each try one chunk size (2, 4, 8, 16 particles per
- * thread) and the fastest is kept: *particles_per_thread receives it, or 0
- * while tuning is unfinished (single-instance handles: the fixed size). */
+/* The push of both species of every instance is one persistent kernel over a
+ * device queue of (instance, species, chunk) work items, electron and ion
+ * chunks interleaved; ensembles (n_instances > 1) also solve all Poisson
+ * problems in one grouped launch.  The first four steps of a handle each try
+ * one chunk size (2, 4, 8, 16 particles per thread) with eager launches and
+ * the fastest is kept: *particles_per_thread receives it, or 0 while tuning
+ * is unfinished. */
 int pic_tuned_chunk(pic_handle* h, int* particles_per_thread);
 
 /* Wait for the handle's stream; return the latched status of all instances. */
@@ -213,9 +216,8 @@ int pic_load(pic_handle* h, int instance, const char* path);
  * each kernel group).  pic_profile(h, 1) clears the counters and starts
  * recording, pic_profile(h, 0) stops.  pic_profile_read synchronises and
  * fills up to `max` records (names are static strings: "field_tables",
- * "push_e", "push_i", "births", "scan", "scatter", "charge", "circuit",
- * "poisson", "step_end", "warm_start"); *n_out is the number of kernel
- * groups. */
+ * "push", "births", "scan", "scatter", "charge", "circuit", "poisson",
+ * "step_end", "warm_start"); *n_out is the number of kernel groups. */
 typedef struct pic_kernel_time {
   const char* name;
   int64_t launches;

@@ -342,9 +342,8 @@ bool bad_instance(pic_handle* h, int instance) {
   return !h || instance < 0 || instance >= (int)h->inst.size();
 }
 
-const char* kGroupNames[G_COUNT] = {"field_tables", "push_e", "push_i", "births", "scan",
-                                   "scatter", "charge", "circuit", "poisson", "step_end",
-                                   "warm_start"};
+const char* kGroupNames[G_COUNT] = {"field_tables", "push", "births", "scan", "scatter",
+                                   "charge", "circuit", "poisson", "step_end", "warm_start"};
 
 void prof_mark(void* ctx, int group, bool begin, cudaStream_t st) {
   Profiler& P = *(Profiler*)ctx;
@@ -407,7 +406,7 @@ int pic_create(const pic_config* cfgs, int n_instances, const pic_alloc* alloc, 
       return rc;
     }
   }
-  if (n_instances > 1) {
+  {
     h->d_insts = (Inst*)dev_alloc(h, sizeof(Inst) * n_instances);
     h->d_queue = (WorkQueue*)dev_alloc(h, sizeof(WorkQueue));
     h->d_pargs = dev_alloc(h, poisson_args_bytes() * n_instances);
@@ -678,13 +677,11 @@ static cudaError_t launch_ensemble_step(pic_handle* h, const StepMarks* marks) {
     if (e == cudaSuccess) e = launch_field_tables(ih.I, h->num_sms, st);
   mk(G_FIELD, false);
   const int threads = 256;
+  mk(G_PUSH, true);
   if (e == cudaSuccess) e = launch_queue_setup(h->d_insts, h->d_queue, n, (long long)h->ppt * threads, st);
-  for (int sp = 0; sp < 2 && e == cudaSuccess; ++sp) {
-    mk(sp == 0 ? G_PUSH_E : G_PUSH_I, true);
-    e = I0.prec32 ? launch_push32_batched(h->d_insts, h->d_queue, sp, I0.gather, h->ppt, h->num_sms, st)
-                  : launch_push64_batched(h->d_insts, h->d_queue, sp, I0.gather, h->ppt, h->num_sms, st);
-    mk(sp == 0 ? G_PUSH_E : G_PUSH_I, false);
-  }
+  if (e == cudaSuccess)
+    e = launch_push_all(h->d_insts, h->d_queue, I0.prec32, I0.gather, h->ppt, h->num_sms, st);
+  mk(G_PUSH, false);
   mk(G_SCATTER, true);
   for (InstHost& ih : h->inst)
     if (e == cudaSuccess) e = launch_post_push(ih.I, h->num_sms, st);
@@ -697,39 +694,6 @@ static cudaError_t launch_ensemble_step(pic_handle* h, const StepMarks* marks) {
     if (e == cudaSuccess) e = launch_step_end(ih.I, st);
   mk(G_STEP_END, false);
   return e;
-}
-
-// Online autotuner of the ensemble push: the first steps of a handle run one
-// candidate chunk size each (timed with events around the two batched
-// pushes); the fastest is kept for the rest of the run.
-static int autotune_step(pic_handle* h) {
-  const int c = h->tune_next;
-  h->ppt = kTuneCandidates[c];
-  cudaEvent_t a, b;
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
-  struct Ctx { cudaEvent_t a, b; } ctx{a, b};
-  StepMarks marks{[](void* p, int g, bool begin, cudaStream_t st) {
-                    Ctx* x = (Ctx*)p;
-                    if (g == G_PUSH_E && begin) cudaEventRecord(x->a, st);
-                    if (g == G_PUSH_I && !begin) cudaEventRecord(x->b, st);
-                  },
-                  &ctx};
-  const cudaError_t e = launch_ensemble_step(h, &marks);
-  float ms = 0.0f;
-  if (e == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  if (e != cudaSuccess) return cuda_fail(h, e, "ensemble step");
-  h->tune_ms[c] = ms;
-  if (++h->tune_next == 4) {
-    int best = 0;
-    for (int k = 1; k < 4; ++k)
-      if (h->tune_ms[k] < h->tune_ms[best]) best = k;
-    h->ppt = kTuneCandidates[best];
-    h->tune_next = -1;
-  }
-  return PIC_OK;
 }
 
 // launches around the Poisson solve of a single-instance step: the learned
@@ -751,8 +715,42 @@ static cudaError_t launch_all(pic_handle* h, const StepMarks* marks) {
   cudaError_t e = cudaSuccess;
   for (InstHost& ih : h->inst)
     if (e == cudaSuccess)
-      e = launch_step(ih.I, ih.pw, h->num_sms, h->stream, marks, h->unet ? &hooks : nullptr);
+      e = launch_step(ih.I, ih.pw, h->num_sms, h->stream, marks, h->unet ? &hooks : nullptr,
+                      h->d_insts, h->d_queue, h->ppt);
   return e;
+}
+
+// Online autotuner of the push: the first steps of a handle run one
+// candidate chunk size each (timed with events around the push); the fastest
+// is kept for the rest of the run.
+static int autotune_step(pic_handle* h) {
+  const int c = h->tune_next;
+  h->ppt = kTuneCandidates[c];
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  struct Ctx { cudaEvent_t a, b; } ctx{a, b};
+  StepMarks marks{[](void* p, int g, bool begin, cudaStream_t st) {
+                    Ctx* x = (Ctx*)p;
+                    if (g == G_PUSH && begin) cudaEventRecord(x->a, st);
+                    if (g == G_PUSH && !begin) cudaEventRecord(x->b, st);
+                  },
+                  &ctx};
+  const cudaError_t e = launch_all(h, &marks);
+  float ms = 0.0f;
+  if (e == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e != cudaSuccess) return cuda_fail(h, e, "step");
+  h->tune_ms[c] = ms;
+  if (++h->tune_next == 4) {
+    int best = 0;
+    for (int k = 1; k < 4; ++k)
+      if (h->tune_ms[k] < h->tune_ms[best]) best = k;
+    h->ppt = kTuneCandidates[best];
+    h->tune_next = -1;
+  }
+  return PIC_OK;
 }
 
 // the step's launch sequence changed: capture a new graph at the next step
@@ -794,8 +792,8 @@ static void build_graph(pic_handle* h) {
 int pic_step(pic_handle* h, int64_t nsteps) {
   if (!h || nsteps < 0) return fail(h, PIC_ERR_INVALID, "bad argument");
   if (nsteps == 0) return PIC_OK;
-  // ensembles: the first steps tune the batched push's chunk size
-  while (h->inst.size() > 1 && h->tune_next >= 0 && nsteps > 0) {
+  // the first steps of a handle tune the push's chunk size
+  while (h->tune_next >= 0 && nsteps > 0) {
     const int rc = autotune_step(h);
     if (rc != PIC_OK) return rc;
     --nsteps;
@@ -821,7 +819,7 @@ int pic_step(pic_handle* h, int64_t nsteps) {
 
 int pic_tuned_chunk(pic_handle* h, int* particles_per_thread) {
   if (!h || !particles_per_thread) return PIC_ERR_INVALID;
-  *particles_per_thread = h->tune_next < 0 || h->inst.size() == 1 ? h->ppt : 0;
+  *particles_per_thread = h->tune_next < 0 ? h->ppt : 0;
   return PIC_OK;
 }
 

@@ -101,15 +101,39 @@ struct DiagDev {           // mirrors pic_diag
   double poisson_resid;
 };
 
-// Work queue of the batched (ensemble) push: items are (instance, chunk)
-// pairs in instance-major order, prefix[sp][k] = first item of instance k.
+// Work queue of the push: items are (instance, species, chunk) triples.  Per
+// instance the electron and ion chunks alternate while both species have
+// some left (the electron push is bound by its random-number arithmetic, the
+// ion push by memory traffic; interleaving runs both at once on every SM),
+// then the rest of the larger species follows.
 constexpr int kMaxInstances = 64;
 struct WorkQueue {
-  unsigned int next[2];
+  unsigned int next;                 // next item to hand out
   int n_inst;
-  int pad;
-  int prefix[2][kMaxInstances + 1];
+  int prefix[kMaxInstances + 1];     // first item of instance k
+  int nch[kMaxInstances][2];         // chunks per species of instance k
 };
+
+// item -> (instance, species, chunk index); false past the last item
+__device__ __forceinline__ bool queue_item(const WorkQueue* q, int item, int& inst, int& sp,
+                                           int& chunk) {
+  int k = -1;
+  for (int j = 0; j < q->n_inst; ++j)
+    if (item >= q->prefix[j] && item < q->prefix[j + 1]) k = j;
+  if (k < 0) return false;
+  const int local = item - q->prefix[k];
+  const int ce = q->nch[k][0], ci = q->nch[k][1];
+  const int m = ce < ci ? ce : ci;
+  if (local < 2 * m) {
+    sp = local & 1;
+    chunk = local >> 1;
+  } else {
+    sp = ce > ci ? 0 : 1;
+    chunk = m + (local - 2 * m);
+  }
+  inst = k;
+  return true;
+}
 
 // Everything a kernel needs about one instance; passed by value.
 struct Inst {

@@ -11,8 +11,8 @@ struct PoissonWork;  // defined in poisson.cu
 
 // optional per-kernel-group event marks around the launches of a step
 enum StepGroup {
-  G_FIELD = 0, G_PUSH_E, G_PUSH_I, G_BIRTHS, G_SCAN, G_SCATTER, G_CHARGE, G_CIRCUIT,
-  G_POISSON, G_STEP_END, G_WARM, G_COUNT
+  G_FIELD = 0, G_PUSH, G_BIRTHS, G_SCAN, G_SCATTER, G_CHARGE, G_CIRCUIT, G_POISSON,
+  G_STEP_END, G_WARM, G_COUNT
 };
 struct StepMarks {
   void (*mark)(void* ctx, int group, bool begin, cudaStream_t st);
@@ -27,9 +27,11 @@ struct StepHooks {
   void* ctx;
 };
 
-// one time step of one instance (all kernels of the step, in order)
+// one time step of one instance (all kernels of the step, in order); the push
+// runs over the work queue q with the device copy d_inst of I
 cudaError_t launch_step(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_t st,
-                        const StepMarks* marks, const StepHooks* hooks = nullptr);
+                        const StepMarks* marks, const StepHooks* hooks, const Inst* d_inst,
+                        WorkQueue* q, int ppt);
 
 // sort the particles of species `sp` currently in cur[sp] into nxt[sp]
 // (keys, histogram, scan, scatter); the caller swaps cur/nxt afterwards
@@ -46,10 +48,11 @@ cudaError_t launch_solve_fields(const Inst& I, PoissonWork* pw, int num_sms, cud
 cudaError_t launch_field_tables(const Inst& I, int num_sms, cudaStream_t st);
 cudaError_t launch_queue_setup(const Inst* d_insts, WorkQueue* q, int n_inst, long long chunk,
                                cudaStream_t st);
-cudaError_t launch_push64_batched(const Inst* d_insts, WorkQueue* q, int sp, int gather, int ppt,
-                                  int num_sms, cudaStream_t st);
-cudaError_t launch_push32_batched(const Inst* d_insts, WorkQueue* q, int sp, int gather, int ppt,
-                                  int num_sms, cudaStream_t st);
+// the push of both species of every instance over the work queue
+cudaError_t launch_push_all(const Inst* d_insts, WorkQueue* q, int prec32, int gather, int ppt,
+                            int num_sms, cudaStream_t st);
+cudaError_t launch_push32_all(const Inst* d_insts, WorkQueue* q, int gather, int ppt, int num_sms,
+                              cudaStream_t st);
 cudaError_t launch_post_push(const Inst& I, int num_sms, cudaStream_t st);
 cudaError_t launch_step_end(const Inst& I, cudaStream_t st);
 // all instances' Poisson solves in one cooperative launch (block groups)
@@ -72,7 +75,6 @@ cudaError_t launch_unpack32(const Inst& I, int sp, long long offset, long long c
                             int num_sms, cudaStream_t st);
 cudaError_t launch_sort_species32(const Inst& I, int sp, int num_sms, cudaStream_t st);
 cudaError_t launch_deposit_all32(const Inst& I, int num_sms, cudaStream_t st);
-cudaError_t launch_push32(const Inst& I, int sp, int num_sms, cudaStream_t st);
 cudaError_t launch_births32(const Inst& I, cudaStream_t st);
 cudaError_t launch_scatter32(const Inst& I, int num_sms, cudaStream_t st);
 

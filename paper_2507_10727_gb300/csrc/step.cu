@@ -391,46 +391,29 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
   return diag ? Kloc : 0.0;
 }
 
-template <int SP, int GATHER>
-__global__ void __launch_bounds__(kPushThreads, 3) k_push(Inst I) {
-  Scalars* S = I.S;
-  __shared__ unsigned long long patch[kPR * kPZ];
-  __shared__ int anchor[2];
-  __shared__ int s_skip;
-  if (threadIdx.x == 0) s_skip = *(volatile int*)&S->status & ST_FATAL;
-  __syncthreads();
-  if (s_skip) return;   // the whole CTA, so that no barrier is left short
-  for (int k = threadIdx.x; k < kPR * kPZ; k += blockDim.x) patch[k] = 0ULL;
-  const long long n = S->n[SP];
-  double Kloc = 0.0;
-  for (long long c0 = (long long)blockIdx.x * kChunk; c0 < n; c0 += (long long)gridDim.x * kChunk)
-    Kloc += push_chunk64<SP, GATHER>(I, c0, kPPT, patch, anchor);
-  if (S->diag_on) block_add(Kloc, &S->K[SP]);
-}
-
-// Ensemble: persistent CTAs take (instance, chunk) items from a device queue
-// (instance-major order), so discharges of any size keep every SM busy.
-template <int SP, int GATHER>
-__global__ void __launch_bounds__(kPushThreads, 3) k_push_batched(const Inst* insts, WorkQueue* q,
-                                                                  int ppt) {
+// The push of both species of every instance: persistent CTAs take (instance,
+// species, chunk) items from the work queue; an instance's parameters are
+// staged in shared memory when a CTA moves to it.
+template <int GATHER>
+__global__ void __launch_bounds__(kPushThreads, 3) k_push_all(const Inst* insts, WorkQueue* q,
+                                                               int ppt) {
   __shared__ unsigned long long patch[kPR * kPZ];
   __shared__ int anchor[2];
   __shared__ Inst sI;
-  __shared__ int s_inst;
+  __shared__ int s_inst, s_sp, s_skip;
   __shared__ long long s_c0;
-  __shared__ int s_skip;
   for (int k = threadIdx.x; k < kPR * kPZ; k += blockDim.x) patch[k] = 0ULL;
   int cur = -1;
-  double Kloc = 0.0;
+  double K0 = 0.0, K1 = 0.0;
   const long long chunk = (long long)ppt * blockDim.x;
   for (;;) {
     if (threadIdx.x == 0) {
-      const int item = (int)atomicAdd(&q->next[SP], 1u);
-      int inst = -1;
-      for (int k = 0; k < q->n_inst; ++k)
-        if (item >= q->prefix[SP][k] && item < q->prefix[SP][k + 1]) inst = k;
+      const int item = (int)atomicAdd(&q->next, 1u);
+      int inst = -1, sp = 0, c = 0;
+      if (!queue_item(q, item, inst, sp, c)) inst = -1;
       s_inst = inst;
-      s_c0 = inst >= 0 ? (long long)(item - q->prefix[SP][inst]) * chunk : 0;
+      s_sp = sp;
+      s_c0 = (long long)c * chunk;
       // one reading of the status word for the whole CTA (it may change
       // while the kernel runs; the chunk's barriers need a uniform decision)
       s_skip = inst >= 0 ? (*(volatile int*)&insts[inst].S->status & ST_FATAL) : 0;
@@ -439,17 +422,22 @@ __global__ void __launch_bounds__(kPushThreads, 3) k_push_batched(const Inst* in
     const int inst = s_inst;
     // a CTA may find the queue empty on its first fetch (cur == -1 == inst)
     if (inst != cur || inst < 0) {
-      if (cur >= 0 && sI.S->diag_on) block_add(Kloc, &sI.S->K[SP]);
-      Kloc = 0.0;
+      if (cur >= 0 && sI.S->diag_on) {
+        block_add(K0, &sI.S->K[0]);
+        block_add(K1, &sI.S->K[1]);
+      }
+      K0 = K1 = 0.0;
       if (inst < 0) break;
-      // stage the instance's parameters in shared memory
       const unsigned* src = reinterpret_cast<const unsigned*>(insts + inst);
       unsigned* dst = reinterpret_cast<unsigned*>(&sI);
       for (int k = threadIdx.x; k < (int)(sizeof(Inst) / 4); k += blockDim.x) dst[k] = src[k];
       __syncthreads();
       cur = inst;
     }
-    if (!s_skip) Kloc += push_chunk64<SP, GATHER>(sI, s_c0, ppt, patch, anchor);
+    if (!s_skip) {
+      if (s_sp == 0) K0 += push_chunk64<0, GATHER>(sI, s_c0, ppt, patch, anchor);
+      else K1 += push_chunk64<1, GATHER>(sI, s_c0, ppt, patch, anchor);
+    }
     __syncthreads();
   }
 }
@@ -811,38 +799,45 @@ __global__ void k_step_end(Inst I) {
   S->diag_on = (S->step % (I.diag_every > 0 ? I.diag_every : 1)) == 0;
 }
 
-// Fill the batched push's queue: chunks of `chunk` particles per instance
-// and species (none for an instance whose status is latched).
+// Fill the push queue: chunks of `chunk` particles per instance and species
+// (none for an instance whose status is latched).
 __global__ void k_queue_setup(const Inst* insts, WorkQueue* q, int n_inst, long long chunk) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   q->n_inst = n_inst;
-  for (int sp = 0; sp < 2; ++sp) {
-    int acc = 0;
-    q->prefix[sp][0] = 0;
-    for (int k = 0; k < n_inst; ++k) {
-      const Scalars* S = insts[k].S;
-      const long long n = (S->status & ST_FATAL) ? 0 : S->n[sp];
-      acc += (int)((n + chunk - 1) / chunk);
-      q->prefix[sp][k + 1] = acc;
+  int acc = 0;
+  q->prefix[0] = 0;
+  for (int k = 0; k < n_inst; ++k) {
+    const Scalars* S = insts[k].S;
+    const bool dead = (S->status & ST_FATAL) != 0;
+    for (int sp = 0; sp < 2; ++sp) {
+      const long long n = dead ? 0 : S->n[sp];
+      q->nch[k][sp] = (int)((n + chunk - 1) / chunk);
+      acc += q->nch[k][sp];
     }
-    q->next[sp] = 0u;
+    q->prefix[k + 1] = acc;
   }
+  q->next = 0u;
 }
 
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-// one wave of a persistent kernel: resident blocks per SM x SMs (cached per kernel)
-template <typename K>
-static int resident_grid(K kernel, int threads, int num_sms) {
-  static int per = 0;
-  if (per == 0) {
-    int p = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kernel, threads, 0) != cudaSuccess || p < 1)
-      p = 1;
-    per = p;
+// one wave of a persistent kernel: resident blocks per SM x SMs (cached per
+// kernel function)
+int resident_blocks(const void* fn, int threads, int num_sms) {
+  static const void* keys[16];
+  static int vals[16];
+  static int used = 0;
+  for (int k = 0; k < used; ++k)
+    if (keys[k] == fn) return vals[k] * num_sms;
+  int p = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, fn, threads, 0) != cudaSuccess || p < 1) p = 1;
+  if (used < 16) {
+    keys[used] = fn;
+    vals[used] = p;
+    ++used;
   }
-  return per * num_sms;
+  return p * num_sms;
 }
 
 static int grid_for(long long work, int threads, int num_sms, int per_sm) {
@@ -859,16 +854,13 @@ cudaError_t launch_queue_setup(const Inst* d_insts, WorkQueue* q, int n_inst, lo
   return cudaGetLastError();
 }
 
-cudaError_t launch_push64_batched(const Inst* d_insts, WorkQueue* q, int sp, int gather, int ppt,
-                                  int num_sms, cudaStream_t st) {
-  if (sp == 0 && gather == 0)
-    k_push_batched<0, 0><<<resident_grid(k_push_batched<0, 0>, kPushThreads, num_sms), kPushThreads, 0, st>>>(d_insts, q, ppt);
-  else if (sp == 0)
-    k_push_batched<0, 1><<<resident_grid(k_push_batched<0, 1>, kPushThreads, num_sms), kPushThreads, 0, st>>>(d_insts, q, ppt);
-  else if (gather == 0)
-    k_push_batched<1, 0><<<resident_grid(k_push_batched<1, 0>, kPushThreads, num_sms), kPushThreads, 0, st>>>(d_insts, q, ppt);
+cudaError_t launch_push_all(const Inst* d_insts, WorkQueue* q, int prec32, int gather, int ppt,
+                            int num_sms, cudaStream_t st) {
+  if (prec32) return launch_push32_all(d_insts, q, gather, ppt, num_sms, st);
+  if (gather == 0)
+    k_push_all<0><<<resident_blocks((const void*)k_push_all<0>, kPushThreads, num_sms), kPushThreads, 0, st>>>(d_insts, q, ppt);
   else
-    k_push_batched<1, 1><<<resident_grid(k_push_batched<1, 1>, kPushThreads, num_sms), kPushThreads, 0, st>>>(d_insts, q, ppt);
+    k_push_all<1><<<resident_blocks((const void*)k_push_all<1>, kPushThreads, num_sms), kPushThreads, 0, st>>>(d_insts, q, ppt);
   return cudaGetLastError();
 }
 
@@ -942,7 +934,8 @@ cudaError_t launch_step_end(const Inst& I, cudaStream_t st) {
 }
 
 cudaError_t launch_step(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_t st,
-                        const StepMarks* marks, const StepHooks* hooks) {
+                        const StepMarks* marks, const StepHooks* hooks, const Inst* d_inst,
+                        WorkQueue* q, int ppt) {
   auto mk = [&](int g, bool b) {
     if (marks) marks->mark(marks->ctx, g, b, st);
   };
@@ -950,20 +943,11 @@ cudaError_t launch_step(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_
   mk(G_FIELD, true);
   k_field_tables<<<grid_for(ncell, 256, num_sms, 8), 256, 0, st>>>(I);
   mk(G_FIELD, false);
-  mk(G_PUSH_E, true);
-  if (I.prec32) launch_push32(I, 0, num_sms, st);
-  else if (I.gather == 0)
-    k_push<0, 0><<<resident_grid(k_push<0, 0>, kPushThreads, num_sms), kPushThreads, 0, st>>>(I);
-  else
-    k_push<0, 1><<<resident_grid(k_push<0, 1>, kPushThreads, num_sms), kPushThreads, 0, st>>>(I);
-  mk(G_PUSH_E, false);
-  mk(G_PUSH_I, true);
-  if (I.prec32) launch_push32(I, 1, num_sms, st);
-  else if (I.gather == 0)
-    k_push<1, 0><<<resident_grid(k_push<1, 0>, kPushThreads, num_sms), kPushThreads, 0, st>>>(I);
-  else
-    k_push<1, 1><<<resident_grid(k_push<1, 1>, kPushThreads, num_sms), kPushThreads, 0, st>>>(I);
-  mk(G_PUSH_I, false);
+  mk(G_PUSH, true);
+  cudaError_t e0 = launch_queue_setup(d_inst, q, 1, (long long)ppt * kPushThreads, st);
+  if (e0 == cudaSuccess) e0 = launch_push_all(d_inst, q, I.prec32, I.gather, ppt, num_sms, st);
+  mk(G_PUSH, false);
+  if (e0 != cudaSuccess) return e0;
   mk(G_BIRTHS, true);
   if (I.prec32) launch_births32(I, st);
   else k_births<<<1, 1024, 0, st>>>(I);

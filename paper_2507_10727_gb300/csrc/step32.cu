@@ -349,55 +349,38 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
   return diag ? Kloc : 0.0;
 }
 
-template <int SP, int GATHER>
-__global__ void __launch_bounds__(kPush32Threads, 4) k_push32(Inst I) {
-  Scalars* S = I.S;
-  __shared__ float patch[kPR32 * kPZ32];
-  __shared__ int anchor[2];
-  __shared__ int s_skip;
-  if (threadIdx.x == 0) s_skip = *(volatile int*)&S->status & ST_FATAL;
-  __syncthreads();
-  if (s_skip) return;   // the whole CTA, so that no barrier is left short
-  for (int k = threadIdx.x; k < kPR32 * kPZ32; k += blockDim.x) patch[k] = 0.0f;
-  const long long n = S->n[SP];
-  double Kloc = 0.0;
-  for (long long c0 = (long long)blockIdx.x * kChunk32; c0 < n; c0 += (long long)gridDim.x * kChunk32)
-    Kloc += push_chunk32<SP, GATHER>(I, c0, kPPT32, patch, anchor);
-  if (S->diag_on) block_add(Kloc, &S->K[SP]);
-}
-
-// Ensemble: persistent CTAs take (instance, chunk) items from a device queue.
-template <int SP, int GATHER>
-__global__ void __launch_bounds__(kPush32Threads, 4) k_push32_batched(const Inst* insts,
-                                                                      WorkQueue* q, int ppt) {
+// The FP32 push of both species of every instance over the work queue (see
+// k_push_all in step.cu).
+template <int GATHER>
+__global__ void __launch_bounds__(kPush32Threads, 4) k_push32_all(const Inst* insts, WorkQueue* q,
+                                                                   int ppt) {
   __shared__ float patch[kPR32 * kPZ32];
   __shared__ int anchor[2];
   __shared__ Inst sI;
-  __shared__ int s_inst;
+  __shared__ int s_inst, s_sp, s_skip;
   __shared__ long long s_c0;
-  __shared__ int s_skip;
   for (int k = threadIdx.x; k < kPR32 * kPZ32; k += blockDim.x) patch[k] = 0.0f;
   int cur = -1;
-  double Kloc = 0.0;
+  double K0 = 0.0, K1 = 0.0;
   const long long chunk = (long long)ppt * blockDim.x;
   for (;;) {
     if (threadIdx.x == 0) {
-      const int item = (int)atomicAdd(&q->next[SP], 1u);
-      int inst = -1;
-      for (int k = 0; k < q->n_inst; ++k)
-        if (item >= q->prefix[SP][k] && item < q->prefix[SP][k + 1]) inst = k;
+      const int item = (int)atomicAdd(&q->next, 1u);
+      int inst = -1, sp = 0, c = 0;
+      if (!queue_item(q, item, inst, sp, c)) inst = -1;
       s_inst = inst;
-      s_c0 = inst >= 0 ? (long long)(item - q->prefix[SP][inst]) * chunk : 0;
-      // one reading of the status word for the whole CTA (it may change
-      // while the kernel runs; the chunk's barriers need a uniform decision)
+      s_sp = sp;
+      s_c0 = (long long)c * chunk;
       s_skip = inst >= 0 ? (*(volatile int*)&insts[inst].S->status & ST_FATAL) : 0;
     }
     __syncthreads();
     const int inst = s_inst;
-    // a CTA may find the queue empty on its first fetch (cur == -1 == inst)
     if (inst != cur || inst < 0) {
-      if (cur >= 0 && sI.S->diag_on) block_add(Kloc, &sI.S->K[SP]);
-      Kloc = 0.0;
+      if (cur >= 0 && sI.S->diag_on) {
+        block_add(K0, &sI.S->K[0]);
+        block_add(K1, &sI.S->K[1]);
+      }
+      K0 = K1 = 0.0;
       if (inst < 0) break;
       const unsigned* src = reinterpret_cast<const unsigned*>(insts + inst);
       unsigned* dst = reinterpret_cast<unsigned*>(&sI);
@@ -405,7 +388,10 @@ __global__ void __launch_bounds__(kPush32Threads, 4) k_push32_batched(const Inst
       __syncthreads();
       cur = inst;
     }
-    if (!s_skip) Kloc += push_chunk32<SP, GATHER>(sI, s_c0, ppt, patch, anchor);
+    if (!s_skip) {
+      if (s_sp == 0) K0 += push_chunk32<0, GATHER>(sI, s_c0, ppt, patch, anchor);
+      else K1 += push_chunk32<1, GATHER>(sI, s_c0, ppt, patch, anchor);
+    }
     __syncthreads();
   }
 }
@@ -615,53 +601,14 @@ cudaError_t launch_deposit_all32(const Inst& I, int num_sms, cudaStream_t st) {
 }
 
 // one wave of the persistent push: resident blocks per SM x SMs (cached per kernel)
-template <typename K>
-static int one_wave(K kernel, int num_sms) {
-  static int per = 0;
-  if (per == 0) {
-    int p = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kernel, kPush32Threads, 0) != cudaSuccess ||
-        p < 1)
-      p = 1;
-    per = p;
-  }
-  return per * num_sms;
-}
+int resident_blocks(const void* fn, int threads, int num_sms);   // step.cu
 
-cudaError_t launch_push32(const Inst& I, int sp, int num_sms, cudaStream_t st) {
-  if (sp == 0) {
-    if (I.gather == 0) k_push32<0, 0><<<one_wave(k_push32<0, 0>, num_sms), kPush32Threads, 0, st>>>(I);
-    else k_push32<0, 1><<<one_wave(k_push32<0, 1>, num_sms), kPush32Threads, 0, st>>>(I);
-  } else {
-    if (I.gather == 0) k_push32<1, 0><<<one_wave(k_push32<1, 0>, num_sms), kPush32Threads, 0, st>>>(I);
-    else k_push32<1, 1><<<one_wave(k_push32<1, 1>, num_sms), kPush32Threads, 0, st>>>(I);
-  }
-  return cudaGetLastError();
-}
-
-template <typename K>
-static int one_wave_batched(K kernel, int num_sms) {
-  static int per = 0;
-  if (per == 0) {
-    int p = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kernel, kPush32Threads, 0) != cudaSuccess ||
-        p < 1)
-      p = 1;
-    per = p;
-  }
-  return per * num_sms;
-}
-
-cudaError_t launch_push32_batched(const Inst* d_insts, WorkQueue* q, int sp, int gather, int ppt,
-                                  int num_sms, cudaStream_t st) {
-  if (sp == 0 && gather == 0)
-    k_push32_batched<0, 0><<<one_wave_batched(k_push32_batched<0, 0>, num_sms), kPush32Threads, 0, st>>>(d_insts, q, ppt);
-  else if (sp == 0)
-    k_push32_batched<0, 1><<<one_wave_batched(k_push32_batched<0, 1>, num_sms), kPush32Threads, 0, st>>>(d_insts, q, ppt);
-  else if (gather == 0)
-    k_push32_batched<1, 0><<<one_wave_batched(k_push32_batched<1, 0>, num_sms), kPush32Threads, 0, st>>>(d_insts, q, ppt);
+cudaError_t launch_push32_all(const Inst* d_insts, WorkQueue* q, int gather, int ppt, int num_sms,
+                              cudaStream_t st) {
+  if (gather == 0)
+    k_push32_all<0><<<resident_blocks((const void*)k_push32_all<0>, kPush32Threads, num_sms), kPush32Threads, 0, st>>>(d_insts, q, ppt);
   else
-    k_push32_batched<1, 1><<<one_wave_batched(k_push32_batched<1, 1>, num_sms), kPush32Threads, 0, st>>>(d_insts, q, ppt);
+    k_push32_all<1><<<resident_blocks((const void*)k_push32_all<1>, kPush32Threads, num_sms), kPush32Threads, 0, st>>>(d_insts, q, ppt);
   return cudaGetLastError();
 }
 

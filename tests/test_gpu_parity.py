@@ -239,9 +239,12 @@ def test_graph_replay_matches_oracle(pg):
         p.update(gamma_i=0.5, poisson_tol=1e-13, circuit_mode=1, Vs=400.0, Rext=100.0, n_avg=3)
         p, parts = busy_state(p, ppc=8, seed=41)
         p, orc, h = _pair(pg, p, parts)
-        for _ in range(3):
+        # the first four steps tune the push's chunk size (eager launches),
+        # later ones replay the captured step
+        for k in range(6):
             orc.step(1)
             pg.pic_step(h, 1)
-            assert pg.pic_uses_graph(h)
+            assert pg.pic_uses_graph(h) == (k >= 4)
             _check_step(pg, h, orc)
+        assert pg.pic_tuned_chunk(h) in (2, 4, 8, 16)
     side.synchronize()
