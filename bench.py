@@ -70,10 +70,11 @@ def parse():
     ap.add_argument("--cpu-sample", type=float, default=8e6,
                     help="oracle sample size per species for the CPU baseline")
     ap.add_argument("--cpu-steps", type=int, default=8)
-    ap.add_argument("--workload", default="rz256", choices=["rz256", "sweep16", "learned"],
+    ap.add_argument("--workload", default="rz256", choices=["rz256", "sweep16", "learned", "unet"],
                     help="rz256: one 256x256 discharge; sweep16: the 16-discharge "
                          "SEY x R_ext ensemble on 128x128 grids; learned: the 256x512 "
-                         "discharge with and without the learned Poisson warm start")
+                         "discharge with and without the learned Poisson warm start; unet: "
+                         "the warm-start network alone on the 257x513 node grid")
     ap.add_argument("--unet-mode", type=int, default=1, choices=[0, 1],
                     help="learned: 0 = network maps (rho, r, V) to phi; 1 = network maps the "
                          "previous solution's residual to the change of phi")
@@ -379,6 +380,50 @@ def run_learned(args, torch, pg):
 
 
 # ---------------------------------------------------------------------------
+# the warm-start network alone: forward (batch 1) and training pass (batch 8)
+# on the 257 x 513 node grid, through the C ABI (host inputs)
+# ---------------------------------------------------------------------------
+def run_unet(args, torch, pg):
+    p = pic_inputs.params_rz256x512(seed=args.seed)
+    p.update(cap_e=4096, cap_i=4096, birth_cap=1024)
+    h = pg.pic_create(p)
+    pg.pic_unet_create(h, args.seed + 1, 8, args.unet_mode)
+    H, W = p["nr"] + 1, p["nz"] + 1
+    rng = np.random.default_rng(args.seed)
+    x = rng.normal(size=(8, 3, H, W)).astype(np.float32)
+    y = rng.normal(size=(8, H, W)).astype(np.float32)
+    out = {}
+    for name, B, yy in (("forward_b1", 1, None), ("forward_backward_b8", 8, y)):
+        for _ in range(args.warmup):
+            pg.pic_unet_loss_grad(h, x[:B], None if yy is None else yy[:B])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pg.pic_unet_loss_grad(h, x[:B], None if yy is None else yy[:B])
+        torch.cuda.synchronize()
+        out[name + "_ms"] = (time.perf_counter() - t0) / args.steps * 1e3
+    gflop_fwd = 0.0
+    C = (16, 32, 64, 64)
+    for l in range(4):
+        n = ((p["nr"] >> l) + 1) * ((p["nz"] >> l) + 1)
+        cin_a = 16 if l == 0 else C[l - 1]
+        gflop_fwd += 2 * 9 * n * (cin_a * C[l] + C[l] * C[l]) / 1e9
+        if l < 3:
+            gflop_fwd += 2 * 9 * n * ((C[l + 1] + C[l]) * C[l] + C[l] * C[l]) / 1e9
+    line = {"metric": "U-Net forward time, 257x513 nodes, batch 1 (through the C ABI)",
+            "value": out["forward_b1_ms"], "unit": "ms", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": False, "dtype": "bf16",
+            "data": "synthetic", "config": {"workload": "unet_257x513", "mode": args.unet_mode,
+                                            "params": pg.pic_unet_param_count()},
+            "forward_backward_b8_ms": out["forward_backward_b8_ms"],
+            "forward_gflop": gflop_fwd,
+            "note": "host-to-device copy of the inputs and device-to-host copy of the output "
+                    "are inside each timed call"}
+    print(json.dumps(line), flush=True)
+    pg.pic_destroy(h)
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def main():
@@ -413,6 +458,8 @@ def main():
         return run_sweep(args, torch, pg)
     if args.workload == "learned":
         return run_learned(args, torch, pg)
+    if args.workload == "unet":
+        return run_unet(args, torch, pg)
 
     p, parts = workload(args)
     n = int(args.n_per_species)
