@@ -106,6 +106,23 @@ def config_block(p, n, args):
 
 
 # ---------------------------------------------------------------------------
+# replicas (N > 1): one independent discharge per rank
+# ---------------------------------------------------------------------------
+def aggregate_replicas(t: float, psteps: float, world: int, device: str):
+    """Whole-job numbers of N replicas: the timed region is the slowest rank's,
+    the work is the sum of all ranks' particle-steps."""
+    if world <= 1:
+        return t, psteps
+    import torch
+    import torch.distributed as dist
+    tmax = torch.tensor([t], device=device, dtype=torch.float64)
+    tot = torch.tensor([float(psteps)], device=device, dtype=torch.float64)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    return float(tmax.item()), float(tot.item())
+
+
+# ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
 class ClockSampler:
@@ -489,12 +506,7 @@ def main():
     d1 = pg.pic_diagnostics(h, 0)
     psteps = d1["particle_steps"] - d0["particle_steps"]
     t = ms / 1e3
-    if world > 1:
-        tt = torch.tensor([t, float(psteps)], device="cuda", dtype=torch.float64)
-        tmax = tt[:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
-        t, psteps = float(tmax.item()), float(tt[1].item())
+    t, psteps = aggregate_replicas(t, psteps, world, "cuda")
     value = psteps / t
 
     # per-kernel CUDA-event times over a second timed pass of the same step
