@@ -244,15 +244,18 @@ int pic_profile_read(pic_handle* h, pic_kernel_time* out, int max, int* n_out);
  *                        x2 = Dirichlet value / V_ref on z = 0, z = L, r = R
  *                        (0 elsewhere)  ->  phi / V_ref;
  *                        V_ref = |V_s| (circuit_mode 1) or |Vc_fixed|.
- *   mode 1 (correction): x0 = res / in_norm with res = Q - A phi_prev (this
+ *   mode 1 (correction): x0 = res / s with res = Q - A phi_prev (this
  *                        step's charge and electrode values against the
- *                        previous solution), x1 = r / R, x2 = 1 on Dirichlet
- *                        nodes  ->  (phi - phi_prev) / out_norm.
+ *                        previous solution) and s the RMS of res over the
+ *                        nodes of that step, x1 = r / R, x2 = 1 on Dirichlet
+ *                        nodes  ->  (phi - phi_prev) / (s K), K = out_norm /
+ *                        in_norm (the change of phi is linear in res, so each
+ *                        snapshot is scaled to unit size).
  * in_norm (and out_norm in mode 1) are the RMS of the recorded fields, fixed
  * by the first pic_unet_train call.
  *
  * With the warm start on, the network's candidate (mode 0: V_ref y; mode 1:
- * phi_prev + out_norm y, on the free nodes) is smoothed by two red-black
+ * phi_prev + s K y, on the free nodes) is smoothed by two red-black
  * Gauss-Seidel sweeps of the FP64 operator, and the solve starts from
  * whichever of {phi_prev, candidate, zero} has the smallest residual
  * ||Q - A x||_2.  The solve still runs to poisson_tol: only the iteration

@@ -428,21 +428,28 @@ __global__ void __launch_bounds__(kWgThreads) k_conv3_wgrad(WgArgs a) {
   if (kc == 0 && threadIdx.x < COUT) a.pb[(long long)s * COUT + threadIdx.x] = bsum;
 }
 
-// sum the split partials (in split order) into the layer's weight/bias gradient
+// sum the split partials (in split order) into the layer's weight/bias
+// gradient; threads run along the partials' own layout (kc, tap, co, k), so
+// neighbouring threads read neighbouring words
 __global__ void k_wgrad_reduce(const float* pw, const float* pb, int S, int cin, int cin_pad,
                                int cout, float* gw, float* gb) {
-  const int nW = cout * cin * 9;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nW + cout; idx += gridDim.x * blockDim.x) {
+  const long long per = (long long)(cin_pad >> 4) * 9 * cout * 16;   // one split's partials
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < per + cout;
+       e += (long long)gridDim.x * blockDim.x) {
     float s = 0.0f;
-    if (idx < nW) {
-      const int co = idx / (cin * 9), rr = idx - co * cin * 9;
-      const int ci = rr / 9, tap = rr - ci * 9;
-      const int kc = ci >> 4, k = ci & 15;
-      for (int sp = 0; sp < S; ++sp)
-        s += pw[(((long long)sp * (cin_pad >> 4) + kc) * 9 + tap) * cout * 16 + co * 16 + k];
-      gw[idx] = s;
+    if (e < per) {
+      const int k = (int)(e & 15);
+      long long r = e >> 4;
+      const int co = (int)(r % cout);
+      r /= cout;
+      const int tap = (int)(r % 9);
+      const int kc = (int)(r / 9);
+      const int ci = kc * 16 + k;
+      if (ci >= cin) continue;
+      for (int sp = 0; sp < S; ++sp) s += pw[(long long)sp * per + e];
+      gw[((long long)co * cin + ci) * 9 + tap] = s;
     } else {
-      const int co = idx - nW;
+      const int co = (int)(e - per);
       for (int sp = 0; sp < S; ++sp) s += pb[(long long)sp * cout + co];
       gb[co] = s;
     }
@@ -637,12 +644,12 @@ __device__ __forceinline__ bool dirichlet_node(int m, int n, int nr, int nz) {
 
 // training batch: B snapshots drawn by hash of (seed, iteration, b).
 // Slot fields: mode 0 (rho, phi), mode 1 (res, phi - phi_prev).
-__global__ void k_train_input(const float* f0, const float* f1, long long avail, int B,
-                              unsigned long long seed, long long iter, int nr, int nz, int mode,
-                              const UDev* ud, bf16* x_in, float* y) {
+__global__ void k_train_input(const float* f0, const float* f1, const float* slot_scale,
+                              long long avail, int B, unsigned long long seed, long long iter,
+                              int nr, int nz, int mode, const UDev* ud, bf16* x_in, float* y) {
   const int W = nz + 1;
   const long long npx = (long long)(nr + 1) * W, total = (long long)B * npx;
-  const float inv_in = (float)(1.0 / ud->in_norm), inv_out = (float)(1.0 / ud->out_norm);
+  const double K = ud->out_norm / ud->in_norm;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const long long b = e / npx, q = e - b * npx;
@@ -652,6 +659,10 @@ __global__ void k_train_input(const float* f0, const float* f1, long long avail,
     const int m = (int)(q / W), n = (int)(q - (long long)m * W);
     const float a = f0[slot * npx + q], t = f1[slot * npx + q];
     const bool dir = dirichlet_node(m, n, nr, nz);
+    // mode 0: global scales; mode 1: the snapshot's own residual RMS
+    const double sc = mode == 0 ? 1.0 : (double)slot_scale[slot];
+    const float inv_in = (float)(1.0 / (mode == 0 ? ud->in_norm : sc));
+    const float inv_out = (float)(1.0 / (mode == 0 ? ud->out_norm : sc * K));
     float v[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) v[c] = 0.0f;
@@ -670,7 +681,8 @@ __global__ void k_step_input(Inst I, const UDev* ud, int mode, const float* res,
   const int W = I.nz + 1;
   const long long npx = (long long)(I.nr + 1) * W;
   if (I.S->status & ST_FATAL) return;
-  const double inv_in = 1.0 / ud->in_norm, inv_out = 1.0 / ud->out_norm;
+  const double inv_in = 1.0 / (mode == 0 ? ud->in_norm : ud->cur_scale);
+  const double inv_out = 1.0 / ud->out_norm;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
        q += (long long)gridDim.x * blockDim.x) {
     const int m = (int)(q / W), n = (int)(q - (long long)m * W);
@@ -696,7 +708,7 @@ __global__ void k_make_cand(int nr, int nz, const double* phi, const float* net,
                             int mode, double* cand) {
   const int W = nz + 1;
   const long long npx = (long long)(nr + 1) * W;
-  const double s = ud->out_norm;
+  const double s = mode == 0 ? ud->out_norm : ud->cur_scale * (ud->out_norm / ud->in_norm);
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
        q += (long long)gridDim.x * blockDim.x) {
     const int m = (int)(q / W), n = (int)(q - (long long)m * W);
@@ -746,6 +758,43 @@ __global__ void k_snap_post(Inst I, const UDev* ud, float* f1, const double* phi
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
        q += (long long)gridDim.x * blockDim.x)
     f1[slot * npx + q] = (float)(I.phi[q] - phi_prev[q]);
+}
+
+// RMS of n floats by one CTA (1024 threads), FP64 accumulation, fixed order;
+// zero RMS is stored as 1 (an all-zero input stays zero after scaling)
+__device__ void cta_rms(const float* f, long long n, double* out_d, float* out_f) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (long long k = threadIdx.x; k < n; k += blockDim.x) {
+    const double v = f[k];
+    s += v * v;
+  }
+  s = warp_sum_d(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    double r = n > 0 ? sqrt(t / (double)n) : 0.0;
+    if (!(r > 0.0)) r = 1.0;
+    if (out_d) *out_d = r;
+    if (out_f) *out_f = (float)r;
+  }
+}
+
+// mode-1 recording: RMS of the residual just stored in the current slot
+__global__ void __launch_bounds__(1024) k_slot_rms(Inst I, const UDev* ud, const float* f0,
+                                                   float* slot_scale, long long cap, int every) {
+  const Scalars* S = I.S;
+  if ((S->status & ST_FATAL) || (S->step % every) != 0) return;
+  const long long npx = (long long)(I.nr + 1) * (I.nz + 1);
+  const long long slot = ud->snap_count % cap;
+  cta_rms(f0 + slot * npx, npx, nullptr, slot_scale + slot);
+}
+
+// mode-1 warm start: RMS of the live residual
+__global__ void __launch_bounds__(1024) k_live_rms(const float* res, long long npx, UDev* ud) {
+  cta_rms(res, npx, &ud->cur_scale, nullptr);
 }
 
 __global__ void k_after_solve(Inst I, UDev* ud, int every, int record) {
@@ -880,6 +929,7 @@ struct UNet {
   float* res = nullptr;        // residual of the previous solution (mode 1)
   double* phi_prev = nullptr;  // previous solution (mode-1 recording)
   float *snap_f0 = nullptr, *snap_f1 = nullptr;
+  float* slot_scale = nullptr;  // mode 1: residual RMS of each snapshot
   long long snap_cap = 0;
   int snap_every = 1;
   bool warm = false;
@@ -962,7 +1012,7 @@ cudaError_t conv_wgrad(UNet* u, int Lx, const bf16* x, long long x_bs, int x_cs,
     case 32: k_conv3_wgrad<32><<<grid, kWgThreads, sm, st>>>(a); break;
     default: k_conv3_wgrad<16><<<grid, kWgThreads, sm, st>>>(a); break;
   }
-  const long long n = (long long)L.cout * L.cin * 9 + L.cout;
+  const long long n = (long long)(L.cin_pad >> 4) * 9 * L.cout * 16 + L.cout;
   k_wgrad_reduce<<<grid1(n, 256), 256, 0, st>>>(a.pw, a.pb, S, L.cin, L.cin_pad, L.cout,
                                                 u->g + L.w_off, u->g + L.b_off);
   return cudaGetLastError();
@@ -1319,9 +1369,11 @@ cudaError_t unet_snapshots(UNet* u, long long cap, int every, UAllocFn alloc, vo
   const size_t bytes = (size_t)cap * u->npx(0) * 4;
   float* a = (float*)alloc(ctx, bytes);
   float* b = (float*)alloc(ctx, bytes);
-  if (!a || !b) return cudaErrorMemoryAllocation;
+  float* c = (float*)alloc(ctx, (size_t)cap * 4);
+  if (!a || !b || !c) return cudaErrorMemoryAllocation;
   u->snap_f0 = a;
   u->snap_f1 = b;
+  u->slot_scale = c;
   u->snap_cap = cap;
   u->snap_every = every;
   return cudaSuccess;
@@ -1337,9 +1389,13 @@ cudaError_t launch_pre_solve(UNet* u, const Inst& I, PoissonWork* pw, cudaStream
   if (u->mode == 1) {
     e = launch_residual32(pw, I.Q, I.phi, u->res, st);
     if (e) return e;
-    if (u->snap_cap > 0)
+    if (u->snap_cap > 0) {
       k_snap_pre<<<g0, 256, 0, st>>>(I, u->ud, u->res, u->snap_f0, u->phi_prev, u->snap_cap,
                                      u->snap_every);
+      k_slot_rms<<<1, 1024, 0, st>>>(I, u->ud, u->snap_f0, u->slot_scale, u->snap_cap,
+                                     u->snap_every);
+    }
+    if (u->warm) k_live_rms<<<1, 1024, 0, st>>>(u->res, u->npx(0), u->ud);
   }
   if (!u->warm) return cudaGetLastError();
   k_step_input<<<g0, 256, 0, st>>>(I, u->ud, u->mode, u->res, u->x_in);
@@ -1391,8 +1447,9 @@ cudaError_t unet_train(UNet* u, int iters, int batch, float lr, unsigned long lo
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const long long n0 = (long long)batch * u->npx(0);
   for (int it = 0; it < iters && e == cudaSuccess; ++it) {
-    k_train_input<<<grid1(n0, 256), 256, 0, st>>>(u->snap_f0, u->snap_f1, avail, batch, seed, it,
-                                                  u->nr, u->nz, u->mode, u->ud, u->x_in, u->y);
+    k_train_input<<<grid1(n0, 256), 256, 0, st>>>(u->snap_f0, u->snap_f1, u->slot_scale, avail,
+                                                  batch, seed, it, u->nr, u->nz, u->mode, u->ud,
+                                                  u->x_in, u->y);
     e = forward(u, batch, st);
     if (e == cudaSuccess) e = backward(u, batch, u->d_loss + it, st);
     if (e != cudaSuccess) break;

@@ -9,10 +9,14 @@
 // then biases for each layer).  Two input/output readings:
 //   mode 0 (potential):  x = (rho / in_norm, r / R, Dirichlet value / V_ref)
 //                        -> phi / V_ref
-//   mode 1 (correction): x = (res / in_norm, r / R, Dirichlet mask)
-//                        -> (phi - phi_prev) / out_norm,
+//   mode 1 (correction): x = (res / s, r / R, Dirichlet mask)
+//                        -> (phi - phi_prev) / (s K),
 //                        res = Q - A phi_prev (this step's charge and
-//                        electrode values against the previous solution)
+//                        electrode values against the previous solution),
+//                        s = RMS of res of the same step (the change of phi
+//                        is linear in res, so every snapshot is scaled to
+//                        unit size), K = out_norm / in_norm (RMS over the
+//                        recorded snapshots)
 // The guess (mode 0: V_ref * y; mode 1: phi_prev + out_norm * y on the free
 // nodes) is smoothed by two red-black Gauss-Seidel sweeps of the FP64 fine
 // operator, then competes with phi_prev and zero by residual norm.
@@ -37,6 +41,7 @@ struct UDev {
   double out_norm;          // output scale (mode 0: V_ref; mode 1: set by the first training)
   int choice;               // guess used by the last solve
   int err;                  // 1 once a tensor-core wait reached its time limit
+  double cur_scale;         // mode 1: RMS of the live residual of this step
 };
 
 typedef void* (*UAllocFn)(void* ctx, size_t bytes);
