@@ -250,6 +250,8 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
     for (int j = 0; j < ppt; ++j) {
       const long long i = c0 + (long long)j * blockDim.x + threadIdx.x;
       int newkey = -1;
+      unsigned long long w00 = 0ULL, w10 = 0ULL, w01 = 0ULL, w11 = 0ULL;
+      int dm = 0, dn = 0;
       if (i < n) {
         double r = P.r[i], z = P.z[i], vr = P.vr[i], vt = P.vt[i], vz = P.vz[i];
         const double v2old = vr * vr + vt * vt + vz * vz;
@@ -352,24 +354,34 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
           locate(z1, I.inv_dz, I.nz, n1, fz1);
           newkey = cell_key(I, m1, n1);
           P.r[i] = r1; P.z[i] = z1; P.vr[i] = vr; P.vt[i] = vt; P.vz[i] = vz;
-          // deposit x^{n+1} (Section 2: tent functions)
+          // deposit weights of x^{n+1} (Section 2: tent functions)
           const FixW f = fix_weights(rweight_upper(I, r1, m1, fr1), fz1);
-          const int lm = m1 - pm0, ln = n1 - pn0;
-          if (lm >= 0 && lm + 1 < kPR && ln >= 0 && ln + 1 < kPZ) {
-            unsigned long long* p = patch + lm * kPZ + ln;
-            atomicAdd(p, f.w00);
-            atomicAdd(p + kPZ, f.w10);
-            atomicAdd(p + 1, f.w01);
-            atomicAdd(p + kPZ + 1, f.w11);
-          } else {
-            unsigned long long* q = I.qacc[SP];
-            atomicAdd(q + node_index(I, m1, n1), f.w00);
-            atomicAdd(q + node_index(I, m1 + 1, n1), f.w10);
-            atomicAdd(q + node_index(I, m1, n1 + 1), f.w01);
-            atomicAdd(q + node_index(I, m1 + 1, n1 + 1), f.w11);
-          }
+          w00 = f.w00;
+          w10 = f.w10;
+          w01 = f.w01;
+          w11 = f.w11;
+          dm = m1;
+          dn = n1;
         }
         I.key[SP][i] = newkey;
+      }
+      // deposit: integer sums of neighbouring lanes in the same cell (exact,
+      // order free), then one shared-memory (or global) atomic per node and run
+      if (run_sum4(newkey, w00, w10, w01, w11) && newkey >= 0) {
+        const int lm = dm - pm0, ln = dn - pn0;
+        if (lm >= 0 && lm + 1 < kPR && ln >= 0 && ln + 1 < kPZ) {
+          unsigned long long* p = patch + lm * kPZ + ln;
+          atomicAdd(p, w00);
+          atomicAdd(p + kPZ, w10);
+          atomicAdd(p + 1, w01);
+          atomicAdd(p + kPZ + 1, w11);
+        } else {
+          unsigned long long* q = I.qacc[SP];
+          atomicAdd(q + node_index(I, dm, dn), w00);
+          atomicAdd(q + node_index(I, dm + 1, dn), w10);
+          atomicAdd(q + node_index(I, dm, dn + 1), w01);
+          atomicAdd(q + node_index(I, dm + 1, dn + 1), w11);
+        }
       }
       // histogram of new cells, aggregated over the lanes of a warp that
       // share a cell (sorted input keeps most of a warp in one cell)
@@ -395,7 +407,7 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
 // species, chunk) items from the work queue; an instance's parameters are
 // staged in shared memory when a CTA moves to it.
 template <int GATHER>
-__global__ void __launch_bounds__(kPushThreads, 3) k_push_all(const Inst* insts, WorkQueue* q,
+__global__ void __launch_bounds__(kPushThreads, 2) k_push_all(const Inst* insts, WorkQueue* q,
                                                                int ppt) {
   __shared__ unsigned long long patch[kPR * kPZ];
   __shared__ int anchor[2];

@@ -17,7 +17,7 @@
 //                        is linear in res, so every snapshot is scaled to
 //                        unit size), K = out_norm / in_norm (RMS over the
 //                        recorded snapshots)
-// The guess (mode 0: V_ref * y; mode 1: phi_prev + out_norm * y on the free
+// The guess (mode 0: V_ref * y; mode 1: phi_prev + s K y on the free
 // nodes) is smoothed by two red-black Gauss-Seidel sweeps of the FP64 fine
 // operator, then competes with phi_prev and zero by residual norm.
 #pragma once
