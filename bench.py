@@ -47,6 +47,11 @@ FLOPS_PER_PARTICLE = {0: 78.0, 1: 86.0}   # EC, MC
 BYTES_PER_PARTICLE = 96.0
 # FP32 mode: read and write the two 16-byte records of a particle once.
 BYTES_PER_PARTICLE_FP32 = 64.0
+# DRAM traffic of one push launch per particle pushed, from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) on this workload at full size
+# (profiles/traffic_push_rz256_ring_4e7.md); None until measured on the
+# kernel as it stands.
+TRAFFIC_PER_PARTICLE = {"fp64": 89.2, "fp32": 64.1}
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA pipes-lanes per SM per clock x 2
 # flop x 2.07 GHz = 1.26 TFLOP/s (nominal 1.25); scaled to the measured clock.
 FP64_FLOP_PER_CLK = 152 * 2 * 2
@@ -533,7 +538,8 @@ def main():
     if args.precision == "fp64":
         roofline = {"bound": "alu", "kernel": "k_push_all (both species)", "achieved": achieved,
                     "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                    "traffic": None,
+                    "traffic": (TRAFFIC_PER_PARTICLE["fp64"] * n_pushed
+                                if TRAFFIC_PER_PARTICLE["fp64"] else None),
                     "peak_note": f"FP64 pipes: 152 SMs x 4 flop/clk at the median loaded SM "
                                  f"clock {sm_mhz:.0f} MHz (1.25 TFLOP/s nominal at 2.07 GHz)",
                     "hbm_view": {"achieved_gbs": achieved_bw, "peak_gbs": peaks.get("hbm_gbs"),
@@ -547,7 +553,9 @@ def main():
         bw32 = BYTES_PER_PARTICLE_FP32 * n_pushed / (push_ms / 1e3) / 1e9
         roofline = {"bound": "hbm", "kernel": "k_push32_all (both species)", "achieved": bw32,
                     "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
-                    "frac": bw32 / peaks.get("hbm_gbs", 6800.0), "traffic": None,
+                    "frac": bw32 / peaks.get("hbm_gbs", 6800.0),
+                    "traffic": (TRAFFIC_PER_PARTICLE["fp32"] * n_pushed
+                                if TRAFFIC_PER_PARTICLE["fp32"] else None),
                     "peak_kind": peak_kind, "bytes_per_particle": BYTES_PER_PARTICLE_FP32,
                     "particles_per_launch": n_pushed,
                     "per_kernel_ms_per_step": per_kernel}
