@@ -182,14 +182,28 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
     }
     __syncthreads();
     const int pm0 = anchor[0], pn0 = anchor[1];
+    // the next particle's two records are loaded while this one is pushed
+    long long i = c0 + threadIdx.x;
+    float4 a_nx = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    uint4 b_nx = make_uint4(0u, 0u, 0u, 0u);
+    if (i < n) {
+      a_nx = P.a[i];
+      b_nx = P.b[i];
+    }
 #pragma unroll 1
-    for (int j = 0; j < ppt; ++j) {
-      const long long i = c0 + (long long)j * blockDim.x + threadIdx.x;
+    for (int j = 0; j < ppt; ++j, i += blockDim.x) {
       int newkey = -1, dm = 0, dn = 0;
       float w00 = 0.0f, w10 = 0.0f, w01 = 0.0f, w11 = 0.0f;
+      const float4 a = a_nx;
+      const uint4 b = b_nx;
+      {
+        const long long i2 = i + blockDim.x;
+        if (j + 1 < ppt && i2 < n) {
+          a_nx = P.a[i2];
+          b_nx = P.b[i2];
+        }
+      }
       if (i < n) {
-        const float4 a = P.a[i];
-        const uint4 b = P.b[i];
         int m, nn;
         cell_mn(b.y, m, nn);
         const float dr = a.x, dz = a.y;
