@@ -75,7 +75,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=float, default=8e6,
                     help="oracle sample size per species for the CPU baseline")
     ap.add_argument("--cpu-steps", type=int, default=8)
-    ap.add_argument("--workload", default="rz256", choices=["rz256", "sweep16", "learned", "unet"],
+    ap.add_argument("--workload", default="rz256",
+                    choices=["rz256", "sweep16", "learned", "unet", "precision"],
                     help="rz256: one 256x256 discharge; sweep16: the 16-discharge "
                          "SEY x R_ext ensemble on 128x128 grids; learned: the 256x512 "
                          "discharge with and without the learned Poisson warm start; unet: "
@@ -87,6 +88,10 @@ def parse():
                     help="learned: recorded steps (one snapshot per step)")
     ap.add_argument("--train-iters", type=int, default=1000)
     ap.add_argument("--train-batch", type=int, default=8)
+    ap.add_argument("--energy-steps", type=int, default=100000,
+                    help="precision: steps of the closed-system energy runs")
+    ap.add_argument("--steady-steps", type=int, default=20000,
+                    help="precision: steps of the FP64 / FP32 discharge comparison")
     return ap.parse_args()
 
 
@@ -446,6 +451,71 @@ def run_unet(args, torch, pg):
 
 
 # ---------------------------------------------------------------------------
+# precision mode on the 32 x 32 discharge: energy drift of a closed system and
+# time-averaged diagnostics of the discharge, FP32 against FP64
+# ---------------------------------------------------------------------------
+def _run_series(pg, p, parts, steps, every):
+    h = pg.pic_create(p)
+    for k, sp in (("e", 0), ("i", 1)):
+        pg.pic_set_particles(h, 0, sp, parts[k])
+    pg.pic_solve_fields(h, 0)
+    out = []
+    for _ in range(steps // every):
+        pg.pic_step(h, every)
+        out.append(pg.pic_diagnostics(h, 0))
+    pg.pic_destroy(h)
+    return out
+
+
+def run_precision(args, torch, pg):
+    res = {"energy": {}, "steady": {}}
+    t0 = time.perf_counter()
+    # closed system: no collisions, reflecting walls, all electrodes at 0 V
+    for gname, g in (("EC", 0), ("MC", 1)):
+        for prec in ("fp64", "fp32"):
+            p = pic_inputs.params_rz32(gather=g, precision=1 if prec == "fp32" else 0, seed=args.seed)
+            p.update(mcc_on=0, walls_reflect=1, circuit_mode=0, Vc_fixed=0.0, diag_every=100)
+            p, parts = pic_inputs.seed_plasma(p, 32 * 32 * 64, n0=1e15, seed=args.seed + 1)
+            p = pic_inputs.with_capacity(p, parts, factor=1.1)
+            ser = _run_series(pg, p, parts, args.energy_steps, 100)
+            tot = np.array([d["W_field"] + d["K_e"] + d["K_i"] for d in ser])
+            rel = tot / tot[0] - 1.0
+            res["energy"][f"{gname}_{prec}"] = {
+                "steps": args.energy_steps, "rel_change_end": float(rel[-1]),
+                "max_abs_rel_change": float(np.abs(rel).max()),
+                "rel_change_per_1e5_steps": float(rel[-1] * 1e5 / args.energy_steps)}
+    # the cfg-1 discharge: -400 V cathode, collisions, secondary emission
+    keys = ("I_cath", "n_e_peak", "n_i_peak", "W_field", "K_e", "K_i", "N_e", "N_i")
+    means = {}
+    for prec in ("fp64", "fp32"):
+        acc = {k: [] for k in keys}
+        for seed in (args.seed, args.seed + 1):
+            p = pic_inputs.params_rz32(gather=0, precision=1 if prec == "fp32" else 0, seed=seed)
+            p.update(diag_every=50)
+            p, parts = pic_inputs.seed_plasma(p, 32 * 32 * 64, n0=1e15, seed=seed + 10)
+            p = pic_inputs.with_capacity(p, parts, factor=4.0, births=1 << 16)
+            ser = _run_series(pg, p, parts, args.steady_steps, 50)
+            tail = ser[len(ser) // 2:]
+            for k in keys:
+                acc[k].append(float(np.mean([d[k] for d in tail])))
+        means[prec] = {k: float(np.mean(v)) for k, v in acc.items()}
+        res["steady"][prec] = {"per_seed": acc}
+    res["steady"]["fp32_vs_fp64_rel_diff"] = {
+        k: (means["fp32"][k] - means["fp64"][k]) / abs(means["fp64"][k]) if means["fp64"][k] else 0.0
+        for k in keys}
+    res["steady"]["seed_spread_fp64_rel"] = {
+        k: (abs(res["steady"]["fp64"]["per_seed"][k][0] - res["steady"]["fp64"]["per_seed"][k][1]) /
+            abs(means["fp64"][k]) if means["fp64"][k] else 0.0) for k in keys}
+    line = {"metric": "precision mode on the 32x32 discharge (FP32 vs FP64)", "value": None,
+            "unit": None, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "rz32_precision", "energy_steps": args.energy_steps,
+                       "steady_steps": args.steady_steps, "steady_average": "second half, every 50 steps",
+                       "seeds": [args.seed, args.seed + 1]},
+            "seconds": time.perf_counter() - t0, **res}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def main():
@@ -482,6 +552,8 @@ def main():
         return run_learned(args, torch, pg)
     if args.workload == "unet":
         return run_unet(args, torch, pg)
+    if args.workload == "precision":
+        return run_precision(args, torch, pg)
 
     p, parts = workload(args)
     n = int(args.n_per_species)
