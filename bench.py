@@ -192,6 +192,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def gpu_uuid(torch, local: int = 0) -> str:
+    props = torch.cuda.get_device_properties(local)
+    return f"GPU-{props.uuid}" if hasattr(props, "uuid") else str(local)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -293,7 +298,8 @@ def run_sweep(args, torch, pg):
         load(ens, k, parts)
     pg.pic_step(ens, warm)
     pg.pic_sync(ens)
-    ms_e, ps_e = timed([(ens, k) for k in range(len(insts))], args.steps)
+    with ClockSampler(gpu_uuid(torch)) as clk:
+        ms_e, ps_e = timed([(ens, k) for k in range(len(insts))], args.steps)
     pg.pic_profile(ens, True)
     pg.pic_step(ens, min(args.steps, 5))
     prof = pg.pic_profile_read(ens)
@@ -325,6 +331,7 @@ def run_sweep(args, torch, pg):
                        "total_particles": ntot,
                        "gamma_x_Rext": [[p["gamma_i"], p["Rext"]] for p, _ in insts],
                        "l2": "inputs larger than L2"},
+            "clocks": clk.summary(),
             "sequential_16_value": seq, "ensemble_over_sequential": value / seq,
             "autotuned_particles_per_thread": tuned, "cuda_graph": graph,
             "per_kernel_ms_per_step": {k: v["total_ms"] / nprof for k, v in prof.items()}}
@@ -366,10 +373,11 @@ def run_learned(args, torch, pg):
         s0, d0 = pg.pic_unet_stats(h), pg.pic_diagnostics(h, 0)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
-        ev0.record()
-        pg.pic_step(h, args.steps)
-        ev1.record()
-        torch.cuda.synchronize()
+        with ClockSampler(gpu_uuid(torch)) as clk:
+            ev0.record()
+            pg.pic_step(h, args.steps)
+            ev1.record()
+            torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1)
         s1, d1 = pg.pic_unet_stats(h), pg.pic_diagnostics(h, 0)
         pg.pic_profile(h, True)
@@ -384,7 +392,7 @@ def run_learned(args, torch, pg):
                                                        "starts_zero")},
                 "poisson_ms_per_step": prof["poisson"]["total_ms"] / nprof,
                 "warm_start_ms_per_step": prof["warm_start"]["total_ms"] / nprof,
-                "cuda_graph": pg.pic_uses_graph(h)}
+                "cuda_graph": pg.pic_uses_graph(h), "clocks": clk.summary()}
 
     plain = measure(False)
     warm = measure(True)
@@ -569,9 +577,7 @@ def main():
 
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    props = torch.cuda.get_device_properties(local)
-    gpu_id = f"GPU-{props.uuid}" if hasattr(props, "uuid") else str(local)
-    with ClockSampler(gpu_id) as clk:
+    with ClockSampler(gpu_uuid(torch, local)) as clk:
         barrier()
         torch.cuda.synchronize()
         ev0.record(stream)
