@@ -388,8 +388,15 @@ void orc_sigma(const orc_config* c, double E, double out[3]) {
   out[2] = E > c->ion_I ? c->ion_a * log(E / c->ion_I) / (E * c->ion_I) : 0.0;
 }
 
-/* Null-collision frequency (MCC [14]): nu_max = 1.001 n_g max_E sigma_T(E) v(E)
- * over a log grid of 100001 energies in [1e-4 eV, E_cap]. */
+/* Stepwise ionization from the metastable (1d), threshold 4.20 eV (Section 3);
+ * same Lotz form as (1c), one outer-shell electron. */
+double orc_sigma_meta(const orc_config* c, double E) {
+  return E > c->meta_I ? c->meta_a * log(E / c->meta_I) / (E * c->meta_I) : 0.0;
+}
+
+/* Null-collision frequency (MCC [14]): nu_max = 1.001 max_E nu_T(E) with
+ * nu_T = (n_g sigma_T(E) + n_meta sigma_1d(E)) v(E), over a log grid of 100001
+ * energies in [1e-4 eV, E_cap]. */
 double orc_nu_max(const orc_config* c) {
   double best = 0.0;
   for (int k = 0; k <= 100000; ++k) {
@@ -398,7 +405,7 @@ double orc_nu_max(const orc_config* c) {
     double s[3];
     orc_sigma(c, E, s);
     double v = sqrt(2.0 * E * QE / ME);
-    double nu = c->n_gas * (s[0] + s[1] + s[2]) * v;
+    double nu = (c->n_gas * (s[0] + s[1] + s[2]) + c->n_meta * orc_sigma_meta(c, E)) * v;
     if (nu > best) best = nu;
   }
   return 1.001 * best;
@@ -613,11 +620,40 @@ static void b_at(const orc_sim* s, double r, double z, double* Br, double* Bz) {
         w01 * s->Bnz[nidx(c, m, n + 1)] + w11 * s->Bnz[nidx(c, m + 1, n + 1)];
 }
 
-/* MCC for one electron (Section 3: MCC [14], reactions (1a)-(1c)); null
+/* An ionizing collision of electron k (reactions (1c) and (1d)): the electron
+ * loses the threshold I and shares E - I uniformly with a new electron
+ * (isotropic); the ion is born with a Maxwellian at the gas temperature.
+ * Returns the primary's new energy. */
+static double ionize(orc_sim* s, int64_t k, double E, double I, const double e[3], blist* be,
+                     blist* bi) {
+  const orc_config* c = &s->c;
+  pstore* p = &s->sp[0];
+  double u2[4], g[4];
+  draws(c, 0, p->id[k], s->step, 1, u2);
+  double Ex = E - I;
+  double Enew = u2[0] * Ex;
+  double E2 = Ex - Enew;
+  double d2[3];
+  scatter_dir(e, 1.0 - 2.0 * u2[1], 2.0 * PI * u2[2], d2);
+  double v2 = sqrt(2.0 * E2 * QE / ME);
+  uint64_t key = ((uint64_t)p->id[k] << 2) | 0u;
+  bl_push(be, key, p->r[k], p->z[k], v2 * d2[0], v2 * d2[1], v2 * d2[2]);
+  /* ion: Maxwellian at T_gas by Box-Muller */
+  draws(c, 0, p->id[k], s->step, 4, g);
+  double sig = sqrt(KBOLTZ * c->T_gas / c->m_ion);
+  double rho1 = sqrt(-2.0 * log(1.0 - g[0])), th1 = 2.0 * PI * g[1];
+  double rho2 = sqrt(-2.0 * log(1.0 - g[2])), th2 = 2.0 * PI * g[3];
+  bl_push(bi, key, p->r[k], p->z[k], sig * rho1 * cos(th1), sig * rho1 * sin(th1),
+          sig * rho2 * cos(th2));
+  return Enew;
+}
+
+/* MCC for one electron (Section 3: MCC [14], reactions (1a)-(1d)); null
  * collision with probability 1 - exp(-nu_max dt) of a candidate, the process
- * chosen by U nu_max against the cumulative n_g sigma_k v.  Reading: isotropic
- * scattering; elastic loss E' = E (1 - 2 m/M (1 - cos chi)); excitation loses
- * 11.55 eV; ionization loses 15.76 eV and shares the rest uniformly; the ion
+ * chosen by U nu_max against the cumulative frequencies n_g sigma_k v (1a-1c)
+ * and n_meta sigma_1d v (1d).  Reading: isotropic scattering; elastic loss
+ * E' = E (1 - 2 m/M (1 - cos chi)); excitation loses 11.55 eV; ionization
+ * loses 15.76 eV (1c) or 4.20 eV (1d) and shares the rest uniformly; the ion
  * is born at rest-frame gas temperature. */
 static void mcc_electron(orc_sim* s, int64_t k, blist* be, blist* bi) {
   const orc_config* c = &s->c;
@@ -632,6 +668,7 @@ static void mcc_electron(orc_sim* s, int64_t k, blist* be, blist* bi) {
   orc_sigma(c, E, sg);
   double nu_el = c->n_gas * sg[0] * vmag, nu_ex = c->n_gas * sg[1] * vmag;
   double nu_io = c->n_gas * sg[2] * vmag;
+  double nu_md = c->n_meta * orc_sigma_meta(c, E) * vmag;
   double R = u[1] * s->nu_max;
   double e[3] = {v[0] / (vmag > 0 ? vmag : 1), v[1] / (vmag > 0 ? vmag : 1),
                  v[2] / (vmag > 0 ? vmag : 1)};
@@ -644,24 +681,11 @@ static void mcc_electron(orc_sim* s, int64_t k, blist* be, blist* bi) {
     Enew = E - c->exc_E;
     s->d.n_excite++;
   } else if (R < nu_el + nu_ex + nu_io) {
-    double u2[4], g[4];
-    draws(c, 0, p->id[k], s->step, 1, u2);
-    double Ex = E - c->ion_I;
-    Enew = u2[0] * Ex;
-    double E2 = Ex - Enew;
-    double d2[3];
-    scatter_dir(e, 1.0 - 2.0 * u2[1], 2.0 * PI * u2[2], d2);
-    double v2 = sqrt(2.0 * E2 * QE / ME);
-    uint64_t key = ((uint64_t)p->id[k] << 2) | 0u;
-    bl_push(be, key, p->r[k], p->z[k], v2 * d2[0], v2 * d2[1], v2 * d2[2]);
-    /* ion: Maxwellian at T_gas by Box-Muller */
-    draws(c, 0, p->id[k], s->step, 4, g);
-    double sig = sqrt(KBOLTZ * c->T_gas / c->m_ion);
-    double rho1 = sqrt(-2.0 * log(1.0 - g[0])), th1 = 2.0 * PI * g[1];
-    double rho2 = sqrt(-2.0 * log(1.0 - g[2])), th2 = 2.0 * PI * g[3];
-    bl_push(bi, key, p->r[k], p->z[k], sig * rho1 * cos(th1), sig * rho1 * sin(th1),
-            sig * rho2 * cos(th2));
+    Enew = ionize(s, k, E, c->ion_I, e, be, bi);
     s->d.n_ionize++;
+  } else if (R < nu_el + nu_ex + nu_io + nu_md) {
+    Enew = ionize(s, k, E, c->meta_I, e, be, bi);
+    s->d.n_ionize_meta++;
   } else {
     return; /* null collision */
   }

@@ -54,12 +54,15 @@ typedef struct orc_config {
   int32_t mcc_on, push_on, field_on, walls_reflect;
   uint64_t seed;
   double sigma_el, ion_a, ion_I, exc_C, exc_E, E_cap;
+  double n_meta;           /* metastable Ar* density (m^-3), constant background */
+  double meta_a, meta_I;   /* reaction (1d): sigma = meta_a ln(E/meta_I)/(E meta_I) */
 } orc_config;
 
 typedef struct orc_diag {
   double t, I_cath, V_cath, n_e_peak, n_i_peak, W_field, K_e, K_i;
   int64_t N_e, N_i;
   int64_t n_ion_cath, n_e_cath, n_sey, n_ionize, n_excite, n_elastic;
+  int64_t n_ionize_meta;   /* reaction (1d) events */
 } orc_diag;
 
 typedef struct orc_sim orc_sim;
@@ -76,6 +79,7 @@ int orc_poisson(const orc_config* c, const double* rho, const double* phi_bc, do
 void orc_efield_at(const orc_config* c, const double* phi, double r, double z,
                    double* Er, double* Ez);
 void orc_sigma(const orc_config* c, double E_eV, double out[3]);
+double orc_sigma_meta(const orc_config* c, double E_eV);
 double orc_nu_max(const orc_config* c);
 double orc_field_energy(const orc_config* c, const double* phi);
 

@@ -31,6 +31,7 @@ class OracleConfig(C.Structure):
         ("seed", C.c_uint64),
         ("sigma_el", C.c_double), ("ion_a", C.c_double), ("ion_I", C.c_double),
         ("exc_C", C.c_double), ("exc_E", C.c_double), ("E_cap", C.c_double),
+        ("n_meta", C.c_double), ("meta_a", C.c_double), ("meta_I", C.c_double),
     ]
 
     @classmethod
@@ -46,7 +47,7 @@ class OracleDiag(C.Structure):
                 ("t", "I_cath", "V_cath", "n_e_peak", "n_i_peak", "W_field", "K_e", "K_i")] + \
                [(n, C.c_int64) for n in
                 ("N_e", "N_i", "n_ion_cath", "n_e_cath", "n_sey", "n_ionize", "n_excite",
-                 "n_elastic")]
+                 "n_elastic", "n_ionize_meta")]
 
     def as_dict(self) -> dict:
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -72,6 +73,8 @@ def lib():
         L.orc_poisson.argtypes = [cfgp, _D, _D, _D]
         L.orc_efield_at.argtypes = [cfgp, _D, C.c_double, C.c_double, _D, _D]
         L.orc_sigma.argtypes = [cfgp, C.c_double, _D]
+        L.orc_sigma_meta.argtypes = [cfgp, C.c_double]
+        L.orc_sigma_meta.restype = C.c_double
         L.orc_nu_max.argtypes = [cfgp]
         L.orc_nu_max.restype = C.c_double
         L.orc_field_energy.argtypes = [cfgp, _D]
@@ -168,6 +171,11 @@ def sigma(p: dict, E: float) -> np.ndarray:
     out = np.zeros(3)
     lib().orc_sigma(C.byref(cfg), E, _dp(out))
     return out
+
+
+def sigma_meta(p: dict, E: float) -> float:
+    cfg = OracleConfig.from_params(p)
+    return lib().orc_sigma_meta(C.byref(cfg), E)
 
 
 def nu_max(p: dict) -> float:

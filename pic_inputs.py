@@ -54,7 +54,10 @@ def base_params() -> dict:
 
     Cross-section stand-ins: elastic 1e-19 m^2 (constant); excitation with
     threshold 11.55 eV (reaction 1b) and ionization with threshold 15.76 eV
-    (reaction 1c) of the Lotz single-shell form.  The magnetron field is the
+    (reaction 1c) of the Lotz single-shell form; stepwise ionization from the
+    metastable Ar* (reaction 1d, threshold 4.20 eV, one outer electron) off a
+    constant Ar* background of density n_meta (0 unless a workload sets it;
+    the paper's runs use 2.5e17 m^-3).  The magnetron field is the
     vacuum field B = -grad(A0 J0(kr) exp(-kz)) with k = 3.83 / 2 cm and
     k A0 = 0.04 T, so that B_r vanishes at the cathode edge r = 2 cm.
     """
@@ -70,6 +73,7 @@ def base_params() -> dict:
         seed=0,
         sigma_el=1e-19, ion_a=4.0e-18 * 6.0, ion_I=15.76,
         exc_C=3.63e-18, exc_E=11.55, E_cap=800.0,
+        n_meta=0.0, meta_a=4.0e-18, meta_I=4.20,
         poisson_tol=1e-10, poisson_max_iter=200,
         cap_e=0, cap_i=0, birth_cap=0, diag_every=1,
         sort_every=1,

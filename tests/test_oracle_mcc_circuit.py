@@ -247,3 +247,69 @@ def test_birth_ids_follow_parent_order():
     by_id = np.argsort(e["id"][born])
     np.testing.assert_allclose(e["r"][born][by_id], r_hits[order], rtol=1e-15)
     assert (e["z"][born] == 0.0).all() and (e["vr"][born] == 0.0).all()
+
+
+# ---- reaction (1d): stepwise ionization from the metastable Ar* (Section 3) ----
+def test_metastable_cross_section_closed_forms():
+    p = pic_inputs.params_rz32()
+    I = p["meta_I"]
+    assert I == 4.20 and oracle.sigma_meta(p, 4.19) == 0.0 and oracle.sigma_meta(p, I) == 0.0
+    # Lotz form a ln(E/I)/(E I): maximum at E = e I with value a / (e I^2)
+    Epk = math.e * I
+    assert oracle.sigma_meta(p, Epk) == pytest.approx(p["meta_a"] / (math.e * I * I), rel=1e-12)
+    assert oracle.sigma_meta(p, Epk * 1.01) < oracle.sigma_meta(p, Epk)
+    assert oracle.sigma_meta(p, 100.0) == pytest.approx(
+        p["meta_a"] * math.log(100.0 / I) / (100.0 * I), rel=1e-12)
+
+
+def test_nu_max_bounds_every_energy_with_metastables():
+    p = pic_inputs.params_rz32()
+    p["n_meta"] = 2.5e17
+    numax = oracle.nu_max(p)
+    Es = np.concatenate([np.geomspace(1e-3, p["E_cap"], 3000), [p["E_cap"]]])
+    nus = np.array([(p["n_gas"] * oracle.sigma(p, E).sum() + p["n_meta"] * oracle.sigma_meta(p, E))
+                    * math.sqrt(2 * E * E_CHARGE / M_ELECTRON) for E in Es])
+    assert (nus <= numax).all()
+    assert numax <= 1.0011 * nus.max()
+    p0 = dict(p, n_meta=0.0)
+    assert numax > oracle.nu_max(p0)
+
+
+def test_metastable_ionization_counts_binomial():
+    # only the metastable process: no ground-state gas, a dense Ar* background
+    E0 = 30.0
+    p = _mcc_params(n_gas=0.0, n_meta=3e20)
+    n = 300000
+    parts = {"e": _mono_electrons(n, E0, p, seed=5), "i": _empty()}
+    orc = oracle.Oracle(p, parts, solve=False)
+    orc.step(1)
+    d = orc.diag()
+    assert d["n_elastic"] == d["n_excite"] == d["n_ionize"] == 0
+    numax = oracle.nu_max(p)
+    pnull = -math.expm1(-numax * p["dt"])
+    v = math.sqrt(2 * E0 * E_CHARGE / M_ELECTRON)
+    prob = pnull * p["n_meta"] * oracle.sigma_meta(p, E0) * v / numax
+    mean, sd = n * prob, math.sqrt(n * prob * (1 - prob))
+    assert d["n_ionize_meta"] > 100
+    assert abs(d["n_ionize_meta"] - mean) <= 4.5 * sd + 1, (d["n_ionize_meta"], mean, sd)
+
+
+def test_metastable_ionization_energy_bookkeeping():
+    E0 = 30.0
+    p = _mcc_params(n_gas=0.0, n_meta=3e20)
+    n = 200000
+    e0 = _mono_electrons(n, E0, p, seed=7)
+    orc = oracle.Oracle(p, {"e": e0, "i": _empty()}, solve=False)
+    orc.step(1)
+    d = orc.diag()
+    e1, ions = orc.get_particles(0), orc.get_particles(1)
+    old = e1["id"] < n
+    E_new = 0.5 * M_ELECTRON * (e1["vr"][old] ** 2 + e1["vt"][old] ** 2 + e1["vz"][old] ** 2) / E_CHARGE
+    prim = E_new <= E0 - p["meta_I"] + 1e-9
+    assert prim.sum() == d["n_ionize_meta"] == (~old).sum() == ions["id"].shape[0]
+    E_sec = 0.5 * M_ELECTRON * (e1["vr"][~old] ** 2 + e1["vt"][~old] ** 2 + e1["vz"][~old] ** 2) / E_CHARGE
+    # each event removes exactly the 4.20 eV threshold
+    assert E_new[prim].sum() + E_sec.sum() == pytest.approx(
+        d["n_ionize_meta"] * (E0 - p["meta_I"]), rel=1e-12)
+    # electrons that did not collide keep E0
+    assert np.abs(E_new[~prim] - E0).max() < 1e-9 * E0
