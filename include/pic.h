@@ -94,6 +94,9 @@ typedef struct pic_config {
   int64_t birth_cap;         /* births per species per step */
   int32_t diag_every;        /* diagnostics are accumulated on steps that are multiples */
   int32_t sort_every;        /* cell sort period in steps (1 = every step) */
+  double n_meta;             /* metastable Ar* density (m^-3), a constant background; 0 = off */
+  double meta_a, meta_I;     /* stepwise ionization (1d) from Ar*: sigma = meta_a ln(E/meta_I)/(E meta_I)
+                                (m^2 eV^2, eV; Section 3: threshold 4.20 eV) */
 } pic_config;
 
 /* Device-memory provider.  alloc returns a device pointer aligned to at least
@@ -123,6 +126,7 @@ typedef struct pic_diag {
   int32_t poisson_iters;
   int32_t status;       /* latched device status (pic_status) */
   double poisson_resid; /* final relative residual */
+  int64_t n_ionize_meta; /* stepwise ionizations from Ar* (1d) this step */
 } pic_diag;
 
 typedef struct pic_handle pic_handle;

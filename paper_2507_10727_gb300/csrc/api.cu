@@ -99,7 +99,8 @@ const char* status_text(int code) {
   }
 }
 
-// null-collision frequency: 1.001 n_g max over a log grid of 100001 energies
+// null-collision frequency: 1.001 max over a log grid of 100001 energies of
+// (n_g sigma_T + n_meta sigma_1d) v
 double nu_max_of(const pic_config& c) {
   double best = 0.0;
   for (int k = 0; k <= 100000; ++k) {
@@ -108,8 +109,10 @@ double nu_max_of(const pic_config& c) {
     const double s_el = E > 0.0 ? c.sigma_el : 0.0;
     const double s_ex = E > c.exc_E ? c.exc_C * std::log(E / c.exc_E) / (E * c.exc_E) : 0.0;
     const double s_io = E > c.ion_I ? c.ion_a * std::log(E / c.ion_I) / (E * c.ion_I) : 0.0;
+    const double s_md =
+        E > c.meta_I ? c.meta_a * std::log(E / c.meta_I) / (E * c.meta_I) : 0.0;
     const double v = std::sqrt(2.0 * E * kQe / kMe);
-    const double nu = c.n_gas * (s_el + s_ex + s_io) * v;
+    const double nu = (c.n_gas * (s_el + s_ex + s_io) + c.n_meta * s_md) * v;
     if (nu > best) best = nu;
   }
   return 1.001 * best;
@@ -132,6 +135,8 @@ std::string validate(const pic_config& c) {
   if (!(c.poisson_tol > 0) || c.poisson_max_iter < 1) return "poisson_tol/max_iter";
   if (c.n_avg < 1) return "n_avg must be >= 1";
   if (!(c.E_cap > 0)) return "E_cap must be positive";
+  if (!(c.n_meta >= 0.0)) return "n_meta must be >= 0";
+  if (c.n_meta > 0.0 && !(c.meta_I > 0.0 && c.meta_a >= 0.0)) return "meta_I > 0, meta_a >= 0";
   return "";
 }
 
@@ -168,6 +173,9 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
   I.sigma_el = c.sigma_el;
   I.ion_a = c.ion_a;
   I.ion_I = c.ion_I;
+  I.n_meta = c.n_meta;
+  I.meta_a = c.meta_a;
+  I.meta_I = c.meta_I;
   I.exc_C = c.exc_C;
   I.exc_E = c.exc_E;
   I.nu_max = nu_max_of(c);
@@ -859,6 +867,7 @@ int pic_diagnostics(pic_handle* h, int instance, pic_diag* out) {
   out->n_ionize = d.n_ionize;
   out->n_excite = d.n_excite;
   out->n_elastic = d.n_elastic;
+  out->n_ionize_meta = d.n_ionize_meta;
   out->step = d.step;
   out->particle_steps = d.particle_steps;
   out->poisson_iters = d.poisson_iters;

@@ -88,6 +88,7 @@ struct Scalars {
   long long pushed;        // cumulative particle-steps
   int flip[2];             // which of the two particle buffers of a species is current
   int pad1[2];
+  unsigned long long cnt_ionize_meta;   // stepwise ionizations from Ar* (1d) this step
 };
 
 struct DiagDev {           // mirrors pic_diag
@@ -99,6 +100,7 @@ struct DiagDev {           // mirrors pic_diag
   int poisson_iters;
   int status;
   double poisson_resid;
+  long long n_ionize_meta;
 };
 
 // Work queue of the push: items are (instance, species, chunk) triples.  Per
@@ -147,6 +149,7 @@ struct Inst {
   double qm[2], mass[2], gamma[2];
   // collisions
   double n_gas, T_gas, m_ion, sigma_el, ion_a, ion_I, exc_C, exc_E, nu_max, p_null;
+  double n_meta, meta_a, meta_I;   // reaction (1d) off a constant Ar* background
   unsigned long long pnull_k;   // ceil(p_null 2^53): U < p_null  <=>  (word >> 11) < pnull_k
   unsigned long long seed;
   // switches

@@ -150,8 +150,34 @@ __device__ void add_birth(const Inst& I, int sp, unsigned long long pkey, double
   atomicAdd(q + node_index(I, m + 1, n + 1), f.w11);
 }
 
-// Null-collision MCC for one electron (Section 3, reactions (1a)-(1c), [14]).
+// Null-collision MCC for one electron (Section 3, reactions (1a)-(1d), [14]).
 // Returns true when the velocity changed.
+// An ionizing collision ((1c) or (1d), threshold Ith): the electron keeps a
+// uniform share of E - Ith, a new electron (isotropic) the rest; the ion is born
+// with a Maxwellian at the gas temperature.  Returns the primary's new energy.
+__device__ double ionize64(const Inst& I, long long id, long long step, double r, double z,
+                           double E, double Ith, const double e[3]) {
+  double u2[4], g[4];
+  draws(I, 0, id, step, 1, u2);
+  const double Ex = E - Ith;
+  const double Enew = u2[0] * Ex;
+  const double E2 = Ex - Enew;
+  double d2[3];
+  scatter_dir(e, 1.0 - 2.0 * u2[1], 2.0 * kPi * u2[2], d2);
+  const double v2 = sqrt(2.0 * E2 * kQe / kMe);
+  const unsigned long long key = ((unsigned long long)id << 2) | 0ULL;
+  add_birth(I, 0, key, r, z, v2 * d2[0], v2 * d2[1], v2 * d2[2]);
+  draws(I, 0, id, step, 4, g);
+  const double sig = sqrt(kBoltz * I.T_gas / I.m_ion);
+  const double rho1 = sqrt(-2.0 * log(1.0 - g[0])), th1 = 2.0 * kPi * g[1];
+  const double rho2 = sqrt(-2.0 * log(1.0 - g[2])), th2 = 2.0 * kPi * g[3];
+  double s1, c1, s2, c2;
+  sincos(th1, &s1, &c1);
+  sincos(th2, &s2, &c2);
+  add_birth(I, 1, key, r, z, sig * rho1 * c1, sig * rho1 * s1, sig * rho2 * c2);
+  return Enew;
+}
+
 __device__ bool mcc_electron(const Inst& I, long long id, long long step, double r, double z,
                              double& vr, double& vt, double& vz) {
   unsigned long long w[4];
@@ -166,8 +192,10 @@ __device__ bool mcc_electron(const Inst& I, long long id, long long step, double
   const double s_el = E > 0.0 ? I.sigma_el : 0.0;
   const double s_ex = E > I.exc_E ? I.exc_C * log(E / I.exc_E) / (E * I.exc_E) : 0.0;
   const double s_io = E > I.ion_I ? I.ion_a * log(E / I.ion_I) / (E * I.ion_I) : 0.0;
+  const double s_md = E > I.meta_I ? I.meta_a * log(E / I.meta_I) / (E * I.meta_I) : 0.0;
   const double nu_el = I.n_gas * s_el * vmag, nu_ex = I.n_gas * s_ex * vmag;
   const double nu_io = I.n_gas * s_io * vmag;
+  const double nu_md = I.n_meta * s_md * vmag;
   const double R = u[1] * I.nu_max;
   const double inv = vmag > 0.0 ? 1.0 / vmag : 1.0;
   const double e[3] = {v[0] * inv, v[1] * inv, v[2] * inv};
@@ -181,25 +209,11 @@ __device__ bool mcc_electron(const Inst& I, long long id, long long step, double
     Enew = E - I.exc_E;
     atomicAdd(&S->cnt_excite, 1ULL);
   } else if (R < nu_el + nu_ex + nu_io) {
-    double u2[4], g[4];
-    draws(I, 0, id, step, 1, u2);
-    const double Ex = E - I.ion_I;
-    Enew = u2[0] * Ex;
-    const double E2 = Ex - Enew;
-    double d2[3];
-    scatter_dir(e, 1.0 - 2.0 * u2[1], 2.0 * kPi * u2[2], d2);
-    const double v2 = sqrt(2.0 * E2 * kQe / kMe);
-    const unsigned long long key = ((unsigned long long)id << 2) | 0ULL;
-    add_birth(I, 0, key, r, z, v2 * d2[0], v2 * d2[1], v2 * d2[2]);
-    draws(I, 0, id, step, 4, g);
-    const double sig = sqrt(kBoltz * I.T_gas / I.m_ion);
-    const double rho1 = sqrt(-2.0 * log(1.0 - g[0])), th1 = 2.0 * kPi * g[1];
-    const double rho2 = sqrt(-2.0 * log(1.0 - g[2])), th2 = 2.0 * kPi * g[3];
-    double s1, c1, s2, c2;
-    sincos(th1, &s1, &c1);
-    sincos(th2, &s2, &c2);
-    add_birth(I, 1, key, r, z, sig * rho1 * c1, sig * rho1 * s1, sig * rho2 * c2);
+    Enew = ionize64(I, id, step, r, z, E, I.ion_I, e);
     atomicAdd(&S->cnt_ionize, 1ULL);
+  } else if (R < nu_el + nu_ex + nu_io + nu_md) {
+    Enew = ionize64(I, id, step, r, z, E, I.meta_I, e);
+    atomicAdd(&S->cnt_ionize_meta, 1ULL);
   } else {
     return false;
   }
@@ -786,6 +800,7 @@ __global__ void k_step_end(Inst I) {
     d->n_ionize = (long long)S->cnt_ionize;
     d->n_excite = (long long)S->cnt_excite;
     d->n_elastic = (long long)S->cnt_elastic;
+    d->n_ionize_meta = (long long)S->cnt_ionize_meta;
     d->step = S->step;
     d->poisson_iters = S->poisson_iters;
     d->poisson_resid = S->poisson_resid;
@@ -805,6 +820,7 @@ __global__ void k_step_end(Inst I) {
   S->nbirth[0] = S->nbirth[1] = 0;
   S->cnt_ion_cath = S->cnt_e_cath = S->cnt_sey = 0ULL;
   S->cnt_ionize = S->cnt_excite = S->cnt_elastic = 0ULL;
+  S->cnt_ionize_meta = 0ULL;
   S->K[0] = S->K[1] = 0.0;
   S->W = 0.0;
   S->peak_bits[0] = S->peak_bits[1] = 0ULL;

@@ -98,6 +98,30 @@ __device__ __forceinline__ void scatter_dir32(const float e[3], float cos_chi, f
 
 // null-collision MCC of one electron in FP32 (candidate test exact on the
 // 64-bit Philox word, as in FP64 mode)
+// FP32 ionizing collision ((1c) or (1d), threshold Ith): see ionize64
+__device__ float ionize32(const Inst& I, long long id, long long step, int m, float dr, int n,
+                          float dz, float E, float Ith, const float e[3]) {
+  unsigned long long w2[4], g[4];
+  philox4x64((unsigned long long)id, (unsigned long long)step, 1ULL, 0ULL, I.seed, 0ULL, w2);
+  const float Ex = E - Ith;
+  const float Enew = u01f(w2[0]) * Ex;
+  const float E2 = Ex - Enew;
+  float d2[3];
+  scatter_dir32(e, 1.0f - 2.0f * u01f(w2[1]), 2.0f * (float)kPi * u01f(w2[2]), d2);
+  const float v2n = sqrtf(kTwoEOverMe * E2);
+  const unsigned long long key = ((unsigned long long)id << 2) | 0ULL;
+  add_birth32(I, 0, key, m, dr, n, dz, v2n * d2[0], v2n * d2[1], v2n * d2[2]);
+  philox4x64((unsigned long long)id, (unsigned long long)step, 4ULL, 0ULL, I.seed, 0ULL, g);
+  const float sig = (float)sqrt(kBoltz * I.T_gas / I.m_ion);
+  const float rho1 = sqrtf(-2.0f * logf(1.0f - u01f(g[0]))), th1 = 2.0f * (float)kPi * u01f(g[1]);
+  const float rho2 = sqrtf(-2.0f * logf(1.0f - u01f(g[2]))), th2 = 2.0f * (float)kPi * u01f(g[3]);
+  float s1, c1, s2, c2;
+  sincosf(th1, &s1, &c1);
+  sincosf(th2, &s2, &c2);
+  add_birth32(I, 1, key, m, dr, n, dz, sig * rho1 * c1, sig * rho1 * s1, sig * rho2 * c2);
+  return Enew;
+}
+
 __device__ void mcc_electron32(const Inst& I, long long id, long long step, int m, float dr, int n,
                                float dz, float& vr, float& vt, float& vz) {
   unsigned long long w[4];
@@ -106,12 +130,14 @@ __device__ void mcc_electron32(const Inst& I, long long id, long long step, int 
   const float v2 = vr * vr + vt * vt + vz * vz;
   const float vmag = sqrtf(v2);
   const float E = kHalfMeOverE * v2;
-  const float exE = (float)I.exc_E, ioI = (float)I.ion_I;
+  const float exE = (float)I.exc_E, ioI = (float)I.ion_I, mdI = (float)I.meta_I;
   const float s_el = E > 0.0f ? (float)I.sigma_el : 0.0f;
   const float s_ex = E > exE ? (float)I.exc_C * logf(E / exE) / (E * exE) : 0.0f;
   const float s_io = E > ioI ? (float)I.ion_a * logf(E / ioI) / (E * ioI) : 0.0f;
+  const float s_md = E > mdI ? (float)I.meta_a * logf(E / mdI) / (E * mdI) : 0.0f;
   const float ng = (float)I.n_gas;
   const float nu_el = ng * s_el * vmag, nu_ex = ng * s_ex * vmag, nu_io = ng * s_io * vmag;
+  const float nu_md = (float)I.n_meta * s_md * vmag;
   const float R = u01f(w[1]) * (float)I.nu_max;
   const float inv = vmag > 0.0f ? 1.0f / vmag : 1.0f;
   const float e[3] = {vr * inv, vt * inv, vz * inv};
@@ -126,25 +152,11 @@ __device__ void mcc_electron32(const Inst& I, long long id, long long step, int 
     Enew = E - exE;
     atomicAdd(&S->cnt_excite, 1ULL);
   } else if (R < nu_el + nu_ex + nu_io) {
-    unsigned long long w2[4], g[4];
-    philox4x64((unsigned long long)id, (unsigned long long)step, 1ULL, 0ULL, I.seed, 0ULL, w2);
-    const float Ex = E - ioI;
-    Enew = u01f(w2[0]) * Ex;
-    const float E2 = Ex - Enew;
-    float d2[3];
-    scatter_dir32(e, 1.0f - 2.0f * u01f(w2[1]), 2.0f * (float)kPi * u01f(w2[2]), d2);
-    const float v2n = sqrtf(kTwoEOverMe * E2);
-    const unsigned long long key = ((unsigned long long)id << 2) | 0ULL;
-    add_birth32(I, 0, key, m, dr, n, dz, v2n * d2[0], v2n * d2[1], v2n * d2[2]);
-    philox4x64((unsigned long long)id, (unsigned long long)step, 4ULL, 0ULL, I.seed, 0ULL, g);
-    const float sig = (float)sqrt(kBoltz * I.T_gas / I.m_ion);
-    const float rho1 = sqrtf(-2.0f * logf(1.0f - u01f(g[0]))), th1 = 2.0f * (float)kPi * u01f(g[1]);
-    const float rho2 = sqrtf(-2.0f * logf(1.0f - u01f(g[2]))), th2 = 2.0f * (float)kPi * u01f(g[3]);
-    float s1, c1, s2, c2;
-    sincosf(th1, &s1, &c1);
-    sincosf(th2, &s2, &c2);
-    add_birth32(I, 1, key, m, dr, n, dz, sig * rho1 * c1, sig * rho1 * s1, sig * rho2 * c2);
+    Enew = ionize32(I, id, step, m, dr, n, dz, E, ioI, e);
     atomicAdd(&S->cnt_ionize, 1ULL);
+  } else if (R < nu_el + nu_ex + nu_io + nu_md) {
+    Enew = ionize32(I, id, step, m, dr, n, dz, E, mdI, e);
+    atomicAdd(&S->cnt_ionize_meta, 1ULL);
   } else {
     return;
   }

@@ -52,6 +52,7 @@ class PicConfig(C.Structure):
         ("poisson_tol", C.c_double), ("poisson_max_iter", C.c_int32),
         ("cap_e", C.c_int64), ("cap_i", C.c_int64), ("birth_cap", C.c_int64),
         ("diag_every", C.c_int32), ("sort_every", C.c_int32),
+        ("n_meta", C.c_double), ("meta_a", C.c_double), ("meta_I", C.c_double),
     ]
 
     @classmethod
@@ -72,7 +73,7 @@ class PicDiag(C.Structure):
                 ("N_e", "N_i", "n_ion_cath", "n_e_cath", "n_sey", "n_ionize", "n_excite",
                  "n_elastic", "step", "particle_steps")] + \
                [("poisson_iters", C.c_int32), ("status", C.c_int32),
-                ("poisson_resid", C.c_double)]
+                ("poisson_resid", C.c_double), ("n_ionize_meta", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {n: getattr(self, n) for n, _ in self._fields_}

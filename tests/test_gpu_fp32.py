@@ -97,6 +97,24 @@ def test_fp32_one_step_busy_state(pg, gather, rweight):
     assert d["n_ionize"] > 0 and d["n_sey"] > 0
 
 
+def test_fp32_metastable_ionization(pg):
+    """Reaction (1d) in FP32 mode against the FP64 oracle (dense Ar* so that
+    the step has tens of events)."""
+    p = pic_inputs.params_rz32(gather=0)
+    p.update(n_meta=3e20, gamma_i=0.2, gamma_e=0.1, poisson_tol=1e-12)
+    p, parts = busy_state(p, ppc=16, seed=47)
+    p, orc, h = _pair32(pg, p, parts)
+    orc.step(1)
+    pg.pic_step(h, 1)
+    flips = _check(pg, h, orc)
+    d, do = pg.pic_diagnostics(h, 0), orc.diag()
+    assert do["n_ionize_meta"] > 0
+    if flips == 0:
+        assert d["n_ionize_meta"] == do["n_ionize_meta"]
+    else:
+        assert abs(d["n_ionize_meta"] - do["n_ionize_meta"]) <= flips
+
+
 def test_fp32_several_steps(pg):
     p = pic_inputs.params_rz32(gather=0)
     p.update(poisson_tol=1e-12, circuit_mode=1, Vs=400.0, Rext=2000.0, n_avg=4, gamma_i=0.2)

@@ -41,7 +41,7 @@ def _pair(pg, p, parts, set_phi=True):
 def _check_step(pg, h, orc, check_phi=True):
     de, do = pg.pic_diagnostics(h, 0), orc.diag()
     for key in ("N_e", "N_i", "n_ion_cath", "n_e_cath", "n_sey", "n_ionize", "n_excite",
-                "n_elastic"):
+                "n_elastic", "n_ionize_meta"):
         assert de[key] == do[key], (key, de[key], do[key])
     for sp in (0, 1):
         err = compare_species(pg.pic_get_particles(h, 0, sp), orc.get_particles(sp))
@@ -71,6 +71,23 @@ def test_one_step_busy_state(pg, gather, rweight):
     # the state does exercise every branch
     assert d["n_sey"] > 0 and d["n_ionize"] > 0 and d["n_excite"] > 0 and d["n_e_cath"] > 0
     assert pg.pic_get_next_id(h, 0) == orc.next_id
+
+
+@pytest.mark.parametrize("gather", [0, 1])
+def test_metastable_ionization_and_electron_sey(pg, gather):
+    """Reaction (1d) off an Ar* background (dense here, 3e20 m^-3, so that a
+    step has tens of events) and electron-induced secondary emission at the
+    paper's gamma_e = 0.1 (Section 3)."""
+    p = pic_inputs.params_rz32(gather=gather)
+    p.update(n_meta=3e20, gamma_i=0.2, gamma_e=0.1, poisson_tol=1e-13, circuit_mode=1,
+             Vs=400.0, Rext=100.0, n_avg=3)
+    p, parts = busy_state(p, ppc=16, seed=31 + gather)
+    p, orc, h = _pair(pg, p, parts)
+    for _ in range(2):
+        orc.step(1)
+        pg.pic_step(h, 1)
+        d = _check_step(pg, h, orc)
+    assert d["n_ionize_meta"] > 0 and d["n_e_cath"] > 0
 
 
 def test_ragged_grid_and_counts(pg):
