@@ -198,7 +198,7 @@ int pic_uses_graph(pic_handle* h);
  * device queue of (instance, species, chunk) work items, electron and ion
  * chunks interleaved; ensembles (n_instances > 1) also solve all Poisson
  * problems in one grouped launch.  The first four steps of a handle each try
- * one chunk size (2, 4, 8, 16 particles per thread) with eager launches and
+ * one chunk size (4, 8, 16, 32 particles per thread) with eager launches and
  * the fastest is kept: *particles_per_thread receives it, or 0 while tuning
  * is unfinished. */
 int pic_tuned_chunk(pic_handle* h, int* particles_per_thread);

@@ -670,7 +670,7 @@ int pic_get_next_id(pic_handle* h, int instance, int64_t* next_id) {
 // One step of an ensemble: field tables per instance, both species pushed by
 // persistent CTAs over a queue of (instance, chunk) items, the rest of the
 // particle step per instance, all Poisson solves in one grouped launch.
-static const int kTuneCandidates[4] = {2, 4, 8, 16};
+static const int kTuneCandidates[4] = {4, 8, 16, 32};
 
 static cudaError_t launch_ensemble_step(pic_handle* h, const StepMarks* marks) {
   auto mk = [&](int g, bool b) {

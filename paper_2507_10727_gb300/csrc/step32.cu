@@ -341,9 +341,24 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
           reinterpret_cast<unsigned int*>(P.b + i)[1] = kDead;
         }
       }
-      // deposit: sum the weights of neighbouring lanes in the same cell, then
-      // one shared-memory (or global) atomic per node and run
-      if (run_sum4(newkey, w00, w10, w01, w11) && newkey >= 0) {
+      // deposit: sum the weights of lanes in the same cell (one exact integer
+      // warp reduction of 2^-26 fixed-point weights when the whole warp is in
+      // one cell, runs of neighbouring lanes otherwise), then one shared-memory
+      // (or global) atomic per node and group
+      const unsigned full = 0xffffffffu;
+      const bool one_cell = __all_sync(full, newkey == __shfl_sync(full, newkey, 0));
+      bool tail;
+      if (one_cell) {
+        const float kf = 67108864.0f, ki = 1.0f / 67108864.0f;
+        w00 = (float)__reduce_add_sync(full, __float2uint_rn(w00 * kf)) * ki;
+        w10 = (float)__reduce_add_sync(full, __float2uint_rn(w10 * kf)) * ki;
+        w01 = (float)__reduce_add_sync(full, __float2uint_rn(w01 * kf)) * ki;
+        w11 = (float)__reduce_add_sync(full, __float2uint_rn(w11 * kf)) * ki;
+        tail = lane == 0;
+      } else {
+        tail = run_sum4(newkey, w00, w10, w01, w11);
+      }
+      if (tail && newkey >= 0) {
         const int lm = dm - pm0, ln = dn - pn0;
         if (lm >= 0 && lm + 1 < kPR32 && ln >= 0 && ln + 1 < kPZ32) {
           float* p = patch + lm * kPZ32 + ln;
@@ -360,8 +375,12 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
           atomicAdd(q + gi + nz1 + 1, (double)w11);
         }
       }
-      const unsigned peers = __match_any_sync(0xffffffffu, newkey);
-      if (newkey >= 0 && lane == __ffs(peers) - 1) atomicAdd(&I.counts[SP][newkey], __popc(peers));
+      if (one_cell) {
+        if (lane == 0 && newkey >= 0) atomicAdd(&I.counts[SP][newkey], 32);
+      } else {
+        const unsigned peers = __match_any_sync(full, newkey);
+        if (newkey >= 0 && lane == __ffs(peers) - 1) atomicAdd(&I.counts[SP][newkey], __popc(peers));
+      }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < kPR32 * kPZ32; k += blockDim.x) {

@@ -58,7 +58,7 @@ def test_ensemble_equals_individual_runs(pg, side_stream):
             pg.pic_solve_fields(ens, k)
         pg.pic_step(ens, steps)
         pg.pic_sync(ens)
-        assert pg.pic_tuned_chunk(ens) in (2, 4, 8, 16)
+        assert pg.pic_tuned_chunk(ens) in (4, 8, 16, 32)
         if side_stream:
             assert pg.pic_uses_graph(ens)
         for k, (p, parts) in enumerate(insts):

@@ -263,5 +263,5 @@ def test_graph_replay_matches_oracle(pg):
             pg.pic_step(h, 1)
             assert pg.pic_uses_graph(h) == (k >= 4)
             _check_step(pg, h, orc)
-        assert pg.pic_tuned_chunk(h) in (2, 4, 8, 16)
+        assert pg.pic_tuned_chunk(h) in (4, 8, 16, 32)
     side.synchronize()
