@@ -113,3 +113,34 @@ def test_ensemble_fp32_runs_and_tracks_fp64(pg):
         assert a["status"] == 0
         assert abs(a["N_e"] - b["N_e"]) <= max(2, 1e-4 * b["N_e"])
         assert a["W_field"] == pytest.approx(b["W_field"], rel=1e-3)
+
+
+def test_mixed_grid_ensemble_equals_individual_runs(pg):
+    """Instances of different grids (different multigrid hierarchies and
+    single-CTA tails in the grouped Poisson launch) and particle counts."""
+    insts = []
+    for k, (nr, nz, ppc) in enumerate([(32, 48, 4), (64, 32, 6), (20, 36, 9)]):
+        p = pic_inputs.params_rz32(gather=0)
+        p.update(nr=nr, nz=nz, R=0.02, L=0.02 * nz / nr, Rc=0.6 * 0.02, gamma_i=0.2,
+                 circuit_mode=1, Vs=400.0, Rext=100.0 * (k + 1), n_avg=4, seed=11 + k,
+                 poisson_tol=1e-12)
+        p, parts = busy_state(p, ppc=ppc, seed=200 + k)
+        p = pic_inputs.with_capacity(p, parts, factor=2.0)
+        insts.append((p, parts))
+    steps = 6
+    ens = pg.pic_create([p for p, _ in insts])
+    for k, (p, parts) in enumerate(insts):
+        _load(pg, ens, k, parts)
+        pg.pic_solve_fields(ens, k)
+    pg.pic_step(ens, steps)
+    for k, (p, parts) in enumerate(insts):
+        one = pg.pic_create(p)
+        _load(pg, one, 0, parts)
+        pg.pic_solve_fields(one, 0)
+        pg.pic_step(one, steps)
+        for sp in (0, 1):
+            a = sort_by_id(pg.pic_get_particles(ens, k, sp))
+            b = sort_by_id(pg.pic_get_particles(one, 0, sp))
+            for q in a:
+                assert np.array_equal(a[q], b[q]), (k, sp, q)
+        assert np.array_equal(pg.pic_get_fields(ens, k)["phi"], pg.pic_get_fields(one, 0)["phi"])
