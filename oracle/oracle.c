@@ -604,6 +604,40 @@ void orc_set_circuit(orc_sim* s, double Vc, int64_t step, const double* qhist, i
 void orc_set_next_id(orc_sim* s, int64_t next_id) { s->next_id = next_id; }
 int64_t orc_get_next_id(const orc_sim* s) { return s->next_id; }
 int64_t orc_get_step(const orc_sim* s) { return s->step; }
+
+/* Particle re-weighting (Section 6, the large-grid EC/MC runs): when the
+ * particles per cell grow too large, two thirds of the particles are removed
+ * and the weight of the rest is tripled.  Reading: the paper does not say
+ * which particles go; each particle is kept independently with probability
+ * 1/factor, decided by its own counter-based draw (stream 5 of the particle's
+ * id at the current step), so the kept set does not depend on storage order
+ * and total charge, density profile and velocity distribution are preserved
+ * in expectation.  The kept particles are unchanged and keep their order. */
+int64_t orc_reweight(orc_sim* s, int factor) {
+  if (factor < 1) return -1;
+  int64_t kept = 0;
+  for (int sp = 0; sp < 2; ++sp) {
+    pstore* p = &s->sp[sp];
+    int64_t out = 0;
+    for (int64_t k = 0; k < p->n; ++k) {
+      uint64_t ctr[4] = {(uint64_t)p->id[k], (uint64_t)s->step, 5, 0};
+      uint64_t key[2] = {s->c.seed, (uint64_t)sp};
+      uint64_t w[4];
+      orc_philox4x64(ctr, key, w);
+      if (w[0] % (uint64_t)factor != 0) continue;
+      p->r[out] = p->r[k]; p->z[out] = p->z[k];
+      p->vr[out] = p->vr[k]; p->vt[out] = p->vt[k]; p->vz[out] = p->vz[k];
+      p->id[out] = p->id[k];
+      ++out;
+    }
+    p->n = out;
+    kept += out;
+  }
+  s->c.weight *= (double)factor;
+  return kept;
+}
+
+double orc_get_weight(const orc_sim* s) { return s->c.weight; }
 void orc_get_diag(const orc_sim* s, orc_diag* d) { *d = s->d; }
 
 /* B at a particle: bilinear interpolation of the node table. */
@@ -694,6 +728,25 @@ static void mcc_electron(orc_sim* s, int64_t k, blist* be, blist* bi) {
   p->vr[k] = vn * d[0];
   p->vt[k] = vn * d[1];
   p->vz[k] = vn * d[2];
+}
+
+/* Largest number of macroparticles of a species in one cell (the quantity
+ * Section 6 watches before re-weighting). */
+static int64_t max_per_cell(const orc_sim* s, int sp) {
+  const orc_config* c = &s->c;
+  int64_t* cnt = (int64_t*)calloc((size_t)c->nr * c->nz, sizeof(int64_t));
+  const pstore* p = &s->sp[sp];
+  int64_t best = 0;
+  for (int64_t k = 0; k < p->n; ++k) {
+    int m, n;
+    double f;
+    locate(p->r[k], dr_of(c), c->nr, &m, &f);
+    locate(p->z[k], dz_of(c), c->nz, &n, &f);
+    int64_t v = ++cnt[(size_t)m * c->nz + n];
+    if (v > best) best = v;
+  }
+  free(cnt);
+  return best;
 }
 
 int orc_step(orc_sim* s, int64_t nsteps) {
@@ -812,6 +865,8 @@ int orc_step(orc_sim* s, int64_t nsteps) {
     s->d.n_ion_cath = n_ion_cath;
     s->d.n_e_cath = n_e_cath;
     s->d.n_sey = n_sey;
+    s->d.ppc_max_e = max_per_cell(s, 0);
+    s->d.ppc_max_i = max_per_cell(s, 1);
     s->step++;
   }
   return 0;

@@ -25,6 +25,9 @@
  *   orc_efield_at          MC zero axial self-force, EC force = -dW/dx
  *   MCC inside orc_step    collision counts vs nu_k dt, exact energy losses
  *   circuit inside orc_step  prescribed-charge drive; Table 1 cases 1-2
+ *   orc_reweight           kept fraction within binomial bounds, kept records
+ *                          unchanged, independent of particle order, charge
+ *                          and density profile conserved in expectation
  */
 #ifndef PIC_ORACLE_H
 #define PIC_ORACLE_H
@@ -63,6 +66,7 @@ typedef struct orc_diag {
   int64_t N_e, N_i;
   int64_t n_ion_cath, n_e_cath, n_sey, n_ionize, n_excite, n_elastic;
   int64_t n_ionize_meta;   /* reaction (1d) events */
+  int64_t ppc_max_e, ppc_max_i;  /* most macroparticles in one cell after the step */
 } orc_diag;
 
 typedef struct orc_sim orc_sim;
@@ -99,6 +103,11 @@ void orc_get_diag(const orc_sim* s, orc_diag* d);
 void orc_set_next_id(orc_sim* s, int64_t next_id);
 int64_t orc_get_next_id(const orc_sim* s);
 int64_t orc_get_step(const orc_sim* s);
+/* Particle re-weighting (Section 6): keep each particle with probability
+ * 1/factor and multiply the macroparticle weight by factor.  Returns the
+ * particles kept (both species), or -1 for factor < 1. */
+int64_t orc_reweight(orc_sim* s, int factor);
+double orc_get_weight(const orc_sim* s);
 void orc_destroy(orc_sim* s);
 
 #ifdef __cplusplus

@@ -47,7 +47,7 @@ class OracleDiag(C.Structure):
                 ("t", "I_cath", "V_cath", "n_e_peak", "n_i_peak", "W_field", "K_e", "K_i")] + \
                [(n, C.c_int64) for n in
                 ("N_e", "N_i", "n_ion_cath", "n_e_cath", "n_sey", "n_ionize", "n_excite",
-                 "n_elastic", "n_ionize_meta")]
+                 "n_elastic", "n_ionize_meta", "ppc_max_e", "ppc_max_i")]
 
     def as_dict(self) -> dict:
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -96,6 +96,10 @@ def lib():
         L.orc_get_next_id.restype = C.c_int64
         L.orc_get_step.argtypes = [C.c_void_p]
         L.orc_get_step.restype = C.c_int64
+        L.orc_reweight.argtypes = [C.c_void_p, C.c_int]
+        L.orc_reweight.restype = C.c_int64
+        L.orc_get_weight.argtypes = [C.c_void_p]
+        L.orc_get_weight.restype = C.c_double
         L.orc_destroy.argtypes = [C.c_void_p]
         _lib = L
     return _lib
@@ -267,3 +271,15 @@ class Oracle:
     @property
     def step_index(self) -> int:
         return lib().orc_get_step(self._h)
+
+    def reweight(self, factor: int) -> int:
+        """Keep each particle with probability 1/factor, weight x factor
+        (Section 6); returns the particles kept."""
+        kept = lib().orc_reweight(self._h, factor)
+        if kept < 0:
+            raise ValueError("factor must be >= 1")
+        return kept
+
+    @property
+    def weight(self) -> float:
+        return lib().orc_get_weight(self._h)
