@@ -127,6 +127,8 @@ typedef struct pic_diag {
   int32_t status;       /* latched device status (pic_status) */
   double poisson_resid; /* final relative residual */
   int64_t n_ionize_meta; /* stepwise ionizations from Ar* (1d) this step */
+  int64_t ppc_max_e, ppc_max_i; /* most macroparticles in one cell after the step */
+  double weight;        /* current macroparticle weight (changed by pic_reweight) */
 } pic_diag;
 
 typedef struct pic_handle pic_handle;
@@ -210,9 +212,21 @@ int pic_sync(pic_handle* h);
  * (caller-owned).  Returns the latched status of that instance. */
 int pic_diagnostics(pic_handle* h, int instance, pic_diag* out);
 
+/* Particle re-weighting of one instance between steps (Section 6: at high
+ * density, two thirds of the particles removed and the weight of the rest
+ * tripled).  Each particle of both species is kept with probability
+ * 1/factor: particle `id` of species s stays iff word 0 of Philox4x64-10 with
+ * counter (id, step, 5, 0) and key (seed, s) is divisible by factor, `step`
+ * being the index of the next step.  The kept particles are unchanged; the
+ * macroparticle weight (charge, current, energies and densities from the
+ * next step on) is multiplied by factor; phi stays until the next solve.
+ * Synchronous; drops the captured step graph.  factor 1 is a no-op;
+ * factor < 1 returns PIC_ERR_INVALID. */
+int pic_reweight(pic_handle* h, int instance, int factor);
+
 /* Checkpoint of one instance to / from a file (particles, phi, circuit
- * state, step and id counters).  A resumed run continues bit for bit up to
- * the order of particles inside a cell.  Synchronous. */
+ * state, step and id counters, weight).  A resumed run continues bit for bit
+ * up to the order of particles inside a cell.  Synchronous. */
 int pic_save(pic_handle* h, int instance, const char* path);
 int pic_load(pic_handle* h, int instance, const char* path);
 

@@ -868,6 +868,9 @@ int pic_diagnostics(pic_handle* h, int instance, pic_diag* out) {
   out->n_excite = d.n_excite;
   out->n_elastic = d.n_elastic;
   out->n_ionize_meta = d.n_ionize_meta;
+  out->ppc_max_e = d.ppc_max[0];
+  out->ppc_max_i = d.ppc_max[1];
+  out->weight = h->inst[instance].I.weight;
   out->step = d.step;
   out->particle_steps = d.particle_steps;
   out->poisson_iters = d.poisson_iters;
@@ -878,9 +881,40 @@ int pic_diagnostics(pic_handle* h, int instance, pic_diag* out) {
   return rc;
 }
 
+// New macroparticle weight of one instance: host copies, the device copy
+// read by the push, and the captured step (its kernels hold the weight by
+// value).
+static int set_weight(pic_handle* h, int instance, double w) {
+  InstHost& ih = h->inst[instance];
+  ih.cfg.weight = w;
+  ih.I.weight = w;
+  drop_graph(h);
+  cudaError_t e = cudaMemcpyAsync(h->d_insts + instance, &ih.I, sizeof(Inst), cudaMemcpyHostToDevice,
+                                  h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "weight upload");
+  return PIC_OK;
+}
+
+int pic_reweight(pic_handle* h, int instance, int factor) {
+  if (bad_instance(h, instance) || factor < 1) return fail(h, PIC_ERR_INVALID, "bad argument");
+  if (factor == 1) return read_status(h, instance, nullptr);
+  InstHost& ih = h->inst[instance];
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "reweight sync");
+  int rc = read_status(h, instance, nullptr);
+  if (rc != PIC_OK && rc != PIC_ERR_NONCONVERGED) return rc;
+  e = launch_thin(ih.I, factor, h->num_sms, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "reweight");
+  rc = set_weight(h, instance, ih.I.weight * (double)factor);
+  if (rc != PIC_OK) return rc;
+  return read_status(h, instance, nullptr);
+}
+
 // ---------------------------------------------------------------------------
 // checkpoints: a flat little-endian file
-//   "PICCKPT1", pic_config, Scalars, qhist[n_avg], phi[nodes],
+//   "PICCKPT2", pic_config, Scalars, qhist[n_avg], phi[nodes],
 //   then per species: n, r[n], z[n], vr[n], vt[n], vz[n], id[n]
 // ---------------------------------------------------------------------------
 int pic_save(pic_handle* h, int instance, const char* path) {
@@ -897,7 +931,7 @@ int pic_save(pic_handle* h, int instance, const char* path) {
   if (e != cudaSuccess) return cuda_fail(h, e, "save copy");
   FILE* f = std::fopen(path, "wb");
   if (!f) return fail(h, PIC_ERR_IO, std::string("cannot open ") + path);
-  bool ok = std::fwrite("PICCKPT1", 1, 8, f) == 8;
+  bool ok = std::fwrite("PICCKPT2", 1, 8, f) == 8;
   ok = ok && std::fwrite(&c, sizeof(c), 1, f) == 1;
   ok = ok && std::fwrite(&s, sizeof(s), 1, f) == 1;
   ok = ok && std::fwrite(qh.data(), 8, qh.size(), f) == qh.size();
@@ -945,7 +979,7 @@ int pic_load(pic_handle* h, int instance, const char* path) {
   Scalars s;
   const size_t nn = (size_t)(c.nr + 1) * (c.nz + 1);
   std::vector<double> qh((size_t)c.n_avg), phi(nn);
-  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "PICCKPT1", 8) == 0;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "PICCKPT2", 8) == 0;
   ok = ok && std::fread(&fc, sizeof(fc), 1, f) == 1;
   ok = ok && fc.nr == c.nr && fc.nz == c.nz && fc.n_avg == c.n_avg && fc.precision == c.precision;
   ok = ok && std::fread(&s, sizeof(s), 1, f) == 1;
@@ -1003,6 +1037,8 @@ int pic_load(pic_handle* h, int instance, const char* path) {
   if (e == cudaSuccess) e = cudaMemcpy(ih.I.qhist, qh.data(), qh.size() * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ih.I.phi, phi.data(), nn * 8, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(h, e, "load copy");
+  // the checkpoint's weight (it differs from the handle's after re-weighting)
+  if (fc.weight != ih.I.weight) return set_weight(h, instance, fc.weight);
   return PIC_OK;
 }
 

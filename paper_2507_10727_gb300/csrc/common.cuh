@@ -89,6 +89,7 @@ struct Scalars {
   int flip[2];             // which of the two particle buffers of a species is current
   int pad1[2];
   unsigned long long cnt_ionize_meta;   // stepwise ionizations from Ar* (1d) this step
+  long long ppc_max[2];    // most particles in one cell, from the last sort's histogram
 };
 
 struct DiagDev {           // mirrors pic_diag
@@ -101,6 +102,7 @@ struct DiagDev {           // mirrors pic_diag
   int status;
   double poisson_resid;
   long long n_ionize_meta;
+  long long ppc_max[2];
 };
 
 // Work queue of the push: items are (instance, species, chunk) triples.  Per

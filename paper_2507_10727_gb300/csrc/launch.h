@@ -37,6 +37,12 @@ cudaError_t launch_step(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_
 // (keys, histogram, scan, scatter); the caller swaps cur/nxt afterwards
 cudaError_t launch_sort_species(const Inst& I, int sp, int num_sms, cudaStream_t st);
 
+// re-weighting between steps: keep each particle with probability 1/factor
+// (per-id draw, stream 5 of the current step), both species, re-sorted; the
+// caller multiplies the weight
+cudaError_t launch_thin(const Inst& I, int factor, int num_sms, cudaStream_t st);
+cudaError_t launch_thin32(const Inst& I, int sp, int factor, int num_sms, cudaStream_t st);
+
 // set the particle count of species sp (set-up)
 cudaError_t launch_set_n(const Inst& I, int sp, long long n, cudaStream_t st);
 

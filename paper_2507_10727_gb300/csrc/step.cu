@@ -520,10 +520,12 @@ __global__ void __launch_bounds__(1024) k_scan(Inst I, int sp0) {
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int vmax = 0;   // most particles in one cell
   for (int base = 0; base < I.nkey; base += blockDim.x * 4) {
     const int i0 = base + threadIdx.x * 4;
     int v[4];
     for (int k = 0; k < 4; ++k) v[k] = i0 + k < I.nkey ? counts[i0 + k] : 0;
+    vmax = max(vmax, max(max(v[0], v[1]), max(v[2], v[3])));
     const int s = v[0] + v[1] + v[2] + v[3];
     int incl = s;
 #pragma unroll
@@ -554,7 +556,13 @@ __global__ void __launch_bounds__(1024) k_scan(Inst I, int sp0) {
     if (threadIdx.x == 0) carry += wsum[31];
     __syncthreads();
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  if (lane == 0) wsum[w] = vmax;   // free after the last loop's barrier
+  __syncthreads();
   if (threadIdx.x == 0) {
+    for (int j = 1; j < (int)(blockDim.x >> 5); ++j) vmax = max(vmax, wsum[j]);
+    S->ppc_max[sp] = vmax;
     S->n_next[sp] = carry;
     if (carry > I.cap[sp]) atomicOr(&S->status, ST_CAPACITY);
   }
@@ -643,6 +651,44 @@ __global__ void k_keys(Inst I, int sp) {
   }
   if (lane == 0 && idmax >= 0) atomicMax(&S->next_id, idmax + 1);
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&S->status, ST_NAN);
+}
+
+// Re-weighting (Section 6): particle `id` of species sp stays iff word 0 of
+// its stream-5 draw at the current step is divisible by `factor`; kept
+// particles get their cell key and are counted, the others key -1 (the
+// scatter drops them).
+__device__ __forceinline__ bool thin_keep(const Inst& I, int sp, long long id, long long s,
+                                          int factor) {
+  unsigned long long w[4];
+  philox4x64((unsigned long long)id, (unsigned long long)s, 5ULL, 0ULL, I.seed,
+             (unsigned long long)sp, w);
+  return w[0] % (unsigned long long)factor == 0ULL;
+}
+
+__global__ void k_thin(Inst I, int sp, int factor) {
+  Scalars* S = I.S;
+  if (S->status & ST_FATAL) return;
+  const long long n = S->n[sp], s = S->step;
+  const ParticlesDev P = I.buf[sp][S->flip[sp]];
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = warp * 32; base < n; base += nwarp * 32) {
+    const long long i = base + lane;
+    int key = -1;
+    if (i < n) {
+      if (thin_keep(I, sp, P.id[i], s, factor)) {
+        int m, nn;
+        double f;
+        locate(P.r[i], I.inv_dr, I.nr, m, f);
+        locate(P.z[i], I.inv_dz, I.nz, nn, f);
+        key = cell_key(I, m, nn);
+      }
+      I.key[sp][i] = key;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&I.counts[sp][key], __popc(peers));
+  }
 }
 
 // n = n_next after a set-up sort (no births)
@@ -801,6 +847,8 @@ __global__ void k_step_end(Inst I) {
     d->n_excite = (long long)S->cnt_excite;
     d->n_elastic = (long long)S->cnt_elastic;
     d->n_ionize_meta = (long long)S->cnt_ionize_meta;
+    d->ppc_max[0] = S->ppc_max[0];
+    d->ppc_max[1] = S->ppc_max[1];
     d->step = S->step;
     d->poisson_iters = S->poisson_iters;
     d->poisson_resid = S->poisson_resid;
@@ -910,6 +958,22 @@ cudaError_t launch_sort_species(const Inst& I, int sp, int num_sms, cudaStream_t
   k_scan<<<1, 1024, 0, st>>>(I, sp);
   k_scatter<<<dim3(grid_for(cap, 256, num_sms, 8), 1), 256, 0, st>>>(I, sp);
   k_commit_n<<<1, 32, 0, st>>>(I, sp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_thin(const Inst& I, int factor, int num_sms, cudaStream_t st) {
+  for (int sp = 0; sp < 2; ++sp) {
+    if (I.prec32) {
+      launch_thin32(I, sp, factor, num_sms, st);
+      launch_sort_species32(I, sp, num_sms, st);
+    } else {
+      const long long cap = I.cap[sp];
+      k_thin<<<grid_for(cap, 256, num_sms, 8), 256, 0, st>>>(I, sp, factor);
+      k_scan<<<1, 1024, 0, st>>>(I, sp);
+      k_scatter<<<dim3(grid_for(cap, 256, num_sms, 8), 1), 256, 0, st>>>(I, sp);
+      k_commit_n<<<1, 32, 0, st>>>(I, sp);
+    }
+  }
   return cudaGetLastError();
 }
 

@@ -577,6 +577,38 @@ __global__ void k_pack32(Inst I, int sp, long long offset, long long count, cons
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&S->status, ST_NAN);
 }
 
+// Re-weighting in FP32 mode: the same per-id draw as the FP64 path; dropped
+// records are marked dead in place, kept ones counted for the sort.
+__global__ void k_thin32(Inst I, int sp, int factor) {
+  Scalars* S = I.S;
+  if (S->status & ST_FATAL) return;
+  const long long n = S->n[sp], s = S->step;
+  const Particles32 P = I.buf32[sp][S->flip[sp]];
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = warp * 32; base < n; base += nwarp * 32) {
+    const long long i = base + lane;
+    int key = -1;
+    if (i < n) {
+      uint4 b = P.b[i];
+      unsigned long long w[4];
+      philox4x64((unsigned long long)id_of(b), (unsigned long long)s, 5ULL, 0ULL, I.seed,
+                 (unsigned long long)sp, w);
+      if (w[0] % (unsigned long long)factor == 0ULL) {
+        int m, nn;
+        cell_mn(b.y, m, nn);
+        key = cell_key(I, m, nn);
+      } else {
+        b.y = kDead;
+        P.b[i] = b;
+      }
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&I.counts[sp][key], __popc(peers));
+  }
+}
+
 // FP32 records [offset, offset + count) of cur32 -> FP64 SoA
 __global__ void k_unpack32(Inst I, int sp, long long offset, long long count, double* r, double* z,
                            double* vr, double* vt, double* vz, long long* id) {
@@ -639,6 +671,11 @@ cudaError_t launch_sort_species32(const Inst& I, int sp, int num_sms, cudaStream
   launch_scan(I, sp, 1, st);
   k_scatter32<<<dim3(grid32(I.cap[sp], 256, num_sms, 8), 1), 256, 0, st>>>(I, sp);
   return launch_commit_n(I, sp, st);
+}
+
+cudaError_t launch_thin32(const Inst& I, int sp, int factor, int num_sms, cudaStream_t st) {
+  k_thin32<<<grid32(I.cap[sp], 256, num_sms, 8), 256, 0, st>>>(I, sp, factor);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_deposit_all32(const Inst& I, int num_sms, cudaStream_t st) {

@@ -73,7 +73,8 @@ class PicDiag(C.Structure):
                 ("N_e", "N_i", "n_ion_cath", "n_e_cath", "n_sey", "n_ionize", "n_excite",
                  "n_elastic", "step", "particle_steps")] + \
                [("poisson_iters", C.c_int32), ("status", C.c_int32),
-                ("poisson_resid", C.c_double), ("n_ionize_meta", C.c_int64)]
+                ("poisson_resid", C.c_double), ("n_ionize_meta", C.c_int64),
+                ("ppc_max_e", C.c_int64), ("ppc_max_i", C.c_int64), ("weight", C.c_double)]
 
     def as_dict(self) -> dict:
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -134,6 +135,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         L.pic_tuned_chunk.argtypes = [vp, C.POINTER(C.c_int)]
         L.pic_sync.argtypes = [vp]
         L.pic_diagnostics.argtypes = [vp, C.c_int, C.POINTER(PicDiag)]
+        L.pic_reweight.argtypes = [vp, C.c_int, C.c_int]
         L.pic_save.argtypes = [vp, C.c_int, C.c_char_p]
         L.pic_load.argtypes = [vp, C.c_int, C.c_char_p]
         L.pic_profile.argtypes = [vp, C.c_int]
@@ -342,6 +344,10 @@ def pic_diagnostics(h: Handle, instance: int = 0, check: bool = True) -> dict:
     if check:
         _check(h, rc)
     return d.as_dict()
+
+
+def pic_reweight(h: Handle, instance: int, factor: int = 3):
+    _check(h, load_library().pic_reweight(h.ptr, instance, factor))
 
 
 def pic_save(h: Handle, instance: int, path: str):

@@ -185,3 +185,24 @@ def test_fp32_diagnostics_vs_fp64_oracle(pg):
     print("FP32 diagnostics, max relative error over 20 steps:", errs)
     for k, v in errs.items():
         assert v <= 1e-4, (k, v)
+
+
+def test_fp32_reweight_keeps_the_oracles_particles(pg):
+    """Re-weighting in FP32 mode draws from the particle ids alone, so it keeps
+    exactly the oracle's set; the step after it matches at the FP32 bar with
+    the tripled weight (charge Q included)."""
+    p = pic_inputs.params_rz32()
+    p.update(gamma_i=0.3, poisson_tol=1e-12, circuit_mode=1, Vs=400.0, Rext=100.0, n_avg=3)
+    p, parts = busy_state(p, ppc=24, seed=43)
+    p, orc, h = _pair32(pg, p, parts)
+    pg.pic_reweight(h, 0, 3)
+    orc.reweight(3)
+    for sp in (0, 1):
+        a = sort_by_id(pg.pic_get_particles(h, 0, sp))
+        b = sort_by_id(orc.get_particles(sp))
+        assert np.array_equal(a["id"], b["id"]), sp
+    orc.step(1)
+    pg.pic_step(h, 1)
+    _check(pg, h, orc)
+    assert pg.pic_diagnostics(h, 0)["weight"] == orc.weight == 3 * p["weight"]
+    pg.pic_destroy(h)

@@ -41,7 +41,7 @@ def _pair(pg, p, parts, set_phi=True):
 def _check_step(pg, h, orc, check_phi=True):
     de, do = pg.pic_diagnostics(h, 0), orc.diag()
     for key in ("N_e", "N_i", "n_ion_cath", "n_e_cath", "n_sey", "n_ionize", "n_excite",
-                "n_elastic", "n_ionize_meta"):
+                "n_elastic", "n_ionize_meta", "ppc_max_e", "ppc_max_i"):
         assert de[key] == do[key], (key, de[key], do[key])
     for sp in (0, 1):
         err = compare_species(pg.pic_get_particles(h, 0, sp), orc.get_particles(sp))
@@ -265,3 +265,82 @@ def test_graph_replay_matches_oracle(pg):
             _check_step(pg, h, orc)
         assert pg.pic_tuned_chunk(h) in (4, 8, 16, 32)
     side.synchronize()
+
+
+@pytest.mark.parametrize("gather", [0, 1])
+def test_reweight_matches_oracle(pg, gather, tmp_path):
+    """Re-weighting between steps (Section 6): the same particles kept as the
+    oracle's (per-id draw), weight x 3, then steps that match the oracle's
+    with the new weight; a checkpoint taken after it restores the weight."""
+    p = pic_inputs.params_rz32(gather=gather)
+    p.update(gamma_i=0.3, gamma_e=0.1, poisson_tol=1e-13, circuit_mode=1, Vs=400.0,
+             Rext=100.0, n_avg=3)
+    p, parts = busy_state(p, ppc=24, seed=41 + gather)
+    p, orc, h = _pair(pg, p, parts)
+    for _ in range(2):
+        orc.step(1)
+        pg.pic_step(h, 1)
+    d0 = _check_step(pg, h, orc)
+    assert d0["ppc_max_e"] > 0 and d0["ppc_max_i"] > 0
+    n_before = [pg.pic_count(h, 0, sp) for sp in (0, 1)]
+    pg.pic_reweight(h, 0, 3)
+    orc.reweight(3)
+    for sp in (0, 1):
+        a = sort_by_id(pg.pic_get_particles(h, 0, sp))
+        b = sort_by_id(orc.get_particles(sp))
+        assert np.array_equal(a["id"], b["id"]), sp
+        # binomial(n, 1/3) at 5 sigma
+        n = n_before[sp]
+        assert abs(a["id"].size - n / 3) < 5 * np.sqrt(n * 2 / 9)
+    pg.pic_save(h, 0, str(tmp_path / "rw.bin"))
+    for _ in range(3):
+        orc.step(1)
+        pg.pic_step(h, 1)
+        d = _check_step(pg, h, orc)
+    assert d["weight"] == orc.weight == 3 * p["weight"]
+    # resume from the checkpoint in a fresh handle created with the old weight
+    h2 = pg.pic_create(p)
+    pg.pic_load(h2, 0, str(tmp_path / "rw.bin"))
+    pg.pic_step(h2, 3)
+    d2 = pg.pic_diagnostics(h2, 0)
+    assert d2["weight"] == 3 * p["weight"]
+    for sp in (0, 1):
+        a = sort_by_id(pg.pic_get_particles(h2, 0, sp))
+        b = sort_by_id(pg.pic_get_particles(h, 0, sp))
+        for k in a:
+            assert np.array_equal(a[k], b[k]), (sp, k)
+    assert d2["I_cath"] == d["I_cath"]
+    assert d2["K_e"] == pytest.approx(d["K_e"], rel=1e-12)   # atomic summation order
+    pg.pic_destroy(h2)
+    pg.pic_destroy(h)
+
+
+def test_reweight_factor_checks_and_graph(pg):
+    """Argument checks; on a side stream the captured step is dropped by the
+    re-weighting and captured again, and the replayed steps match the oracle
+    with the new weight."""
+    import torch
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        p = pic_inputs.params_rz32()
+        p.update(gamma_i=0.3, poisson_tol=1e-13, circuit_mode=1, Vs=400.0, Rext=100.0, n_avg=3)
+        p, parts = busy_state(p, ppc=12, seed=5)
+        p, orc, h = _pair(pg, p, parts)
+        with pytest.raises(pg.PicError):
+            pg.pic_reweight(h, 0, 0)
+        n0 = pg.pic_count(h, 0, 0)
+        pg.pic_reweight(h, 0, 1)
+        assert pg.pic_count(h, 0, 0) == n0
+        for _ in range(5):
+            orc.step(1)
+            pg.pic_step(h, 1)
+        assert pg.pic_uses_graph(h) == 1
+        pg.pic_reweight(h, 0, 2)
+        orc.reweight(2)
+        assert pg.pic_uses_graph(h) == 0
+        for _ in range(2):
+            orc.step(1)
+            pg.pic_step(h, 1)
+            assert pg.pic_uses_graph(h) == 1
+            _check_step(pg, h, orc)
+        pg.pic_destroy(h)
