@@ -150,14 +150,21 @@ static double ez_edge(const orc_config* c, const double* phi, int m, int n) {
   return -(phi[nidx(c, m, n + 1)] - phi[nidx(c, m, n)]) / dz_of(c);
 }
 /* Reading: nodal E is the mean of the two adjacent edge values, the single
- * adjacent edge on a wall, and E_r = 0 on the axis by symmetry. */
+ * adjacent edge on a conducting wall, zero normal component on an insulating
+ * (Neumann) wall -- the boundary condition itself -- and E_r = 0 on the axis
+ * by symmetry. */
+static int cathode_node(const orc_config* c, int m);
 static double er_node(const orc_config* c, const double* phi, int m, int n) {
   if (m == 0) return 0.0;
-  if (m == c->nr) return er_edge(c, phi, m - 1, n);
+  if (m == c->nr) return c->wall_neumann ? 0.0 : er_edge(c, phi, m - 1, n);
   return 0.5 * (er_edge(c, phi, m - 1, n) + er_edge(c, phi, m, n));
 }
 static double ez_node(const orc_config* c, const double* phi, int m, int n) {
-  if (n == 0) return ez_edge(c, phi, m, 0);
+  if (n == 0) {
+    int insulating = m == c->nr ? (c->gap_neumann && c->wall_neumann)
+                                : (c->gap_neumann && !cathode_node(c, m));
+    return insulating ? 0.0 : ez_edge(c, phi, m, 0);
+  }
   if (n == c->nz) return ez_edge(c, phi, m, c->nz - 1);
   return 0.5 * (ez_edge(c, phi, m, n - 1) + ez_edge(c, phi, m, n));
 }
@@ -191,18 +198,21 @@ void orc_efield_at(const orc_config* c, const double* phi, double r, double z, d
 
 /* ------------------------------------------------------------------------ */
 /* Poisson problem (Section 3: anode grounded, cathode at the circuit       */
-/* voltage, Gauss's law on the axis).  Reading: finite-volume form on the   */
-/* nodes,                                                                   */
-/*  eps0 [ r_{m+1/2}(phi_{m+1}-phi_m) - r_{m-1/2}(phi_m-phi_{m-1}) ]/(r_m dr^2)*/
-/*  + eps0 (phi_{n+1} - 2 phi_n + phi_{n-1})/dz^2 = -rho        (m >= 1)    */
-/*  eps0 4 (phi_1 - phi_0)/dr^2 + (same z part) = -rho          (axis)      */
-/* Every row is multiplied by the node's control volume V_m; the coupling   */
-/* between two nodes is then the same from both sides:                      */
-/*   r-neighbours m, m+1:  a_r(m) = eps0 2 pi r_{m+1/2} dz / dr             */
-/*   z-neighbours n, n+1:  a_z(m) = eps0 V_m / dz^2  (V_m = area(m) dz)     */
-/* (check on the axis: V_0 4/dr^2 = pi dz = 2 pi (dr/2) dz / dr).  The      */
-/* system A phi = V rho + (Dirichlet couplings) is symmetric positive       */
-/* definite.  Unknowns: m = 0..nr-1, n = 1..nz-1; the rest is Dirichlet.    */
+/* voltage, the insulating "block" a Neumann boundary, Gauss's law on the   */
+/* axis).  Reading: finite volumes on the nodes.  Node (m,n) owns the part  */
+/* of the box [r_m -+ dr/2] x [z_n -+ dz/2] inside the domain (area(m) in r,*/
+/* half height on z = 0 and z = L).  Integrating -div(eps0 grad phi) = rho  */
+/* over it, with the flux through a face between two nodes approximated by  */
+/* eps0 (face area) (phi_k - phi_j) / spacing and no flux through the       */
+/* domain's outer surface, gives  sum_j a_kj (phi_k - phi_j) = V_k rho_k    */
+/* with the symmetric couplings                                             */
+/*   r-neighbours m, m+1:  a_r(m) h(n),  a_r(m) = eps0 2 pi r_{m+1/2} dz/dr, */
+/*                         h = 1/2 on z = 0 and z = L, else 1              */
+/*   z-neighbours n, n+1:  a_z(m) = eps0 area(m) / dz                       */
+/* (on the axis the first line is Gauss's law on the disk r < dr/2).  Nodes */
+/* on a conductor are Dirichlet (given values), the rest are unknowns; the  */
+/* couplings to Dirichlet neighbours move to the right-hand side, so the    */
+/* system is symmetric positive definite (the anode is always Dirichlet).   */
 /* ------------------------------------------------------------------------ */
 static double a_r(const orc_config* c, int m) {
   return EPS0 * 2.0 * PI * ((m + 0.5) * dr_of(c)) * dz_of(c) / dr_of(c);
@@ -210,29 +220,63 @@ static double a_r(const orc_config* c, int m) {
 static double a_z(const orc_config* c, int m) {
   return EPS0 * node_area(c, m) * dz_of(c) / (dz_of(c) * dz_of(c));
 }
+static double h_of(const orc_config* c, int n) { return (n == 0 || n == c->nz) ? 0.5 : 1.0; }
+
+/* Cathode nodes: z = 0, r_m <= Rc, m < nr (Section 3 and Table 1's
+ * benchmark geometry). */
+static int cathode_node(const orc_config* c, int m) { return m * dr_of(c) <= c->Rc && m < c->nr; }
+
+/* Unknown (not on a conductor).  Conductors: the anode z = L; the cathode;
+ * the rest of z = 0 unless gap_neumann; the wall r = R unless wall_neumann. */
+static int node_free(const orc_config* c, int m, int n) {
+  if (n == c->nz) return 0;
+  if (m == c->nr && !c->wall_neumann) return 0;
+  if (n == 0) return c->gap_neumann && !cathode_node(c, m);
+  return 1;
+}
 
 typedef struct chol {
   int nfree, bw;
+  int* idx;  /* unknown number of node (m,n), -1 for Dirichlet nodes */
   double* L; /* L(k, k-j) at L[k*(bw+1) + j] */
 } chol;
 
-static int fidx(const orc_config* c, int m, int n) { return m * (c->nz - 1) + (n - 1); }
+/* the four neighbours of a node and their couplings (0 outside the grid) */
+static int neighbours(const orc_config* c, int m, int n, int nb[4][2], double a[4]) {
+  int k = 0;
+  if (m > 0) { nb[k][0] = m - 1; nb[k][1] = n; a[k++] = a_r(c, m - 1) * h_of(c, n); }
+  if (m < c->nr) { nb[k][0] = m + 1; nb[k][1] = n; a[k++] = a_r(c, m) * h_of(c, n); }
+  if (n > 0) { nb[k][0] = m; nb[k][1] = n - 1; a[k++] = a_z(c, m); }
+  if (n < c->nz) { nb[k][0] = m; nb[k][1] = n + 1; a[k++] = a_z(c, m); }
+  return k;
+}
 
 static int chol_build(const orc_config* c, chol* f) {
-  int nfree = c->nr * (c->nz - 1), bw = c->nz - 1;
+  size_t nn = (size_t)(c->nr + 1) * (c->nz + 1);
+  f->idx = (int*)malloc(sizeof(int) * nn);
+  int nfree = 0;
+  for (int m = 0; m <= c->nr; ++m)
+    for (int n = 0; n <= c->nz; ++n) f->idx[nidx(c, m, n)] = node_free(c, m, n) ? nfree++ : -1;
+  /* unknowns are numbered m-major, so a neighbour is at most nz+1 away */
+  int bw = c->nz + 1;
   f->nfree = nfree;
   f->bw = bw;
-  f->L = (double*)calloc((size_t)nfree * (bw + 1), sizeof(double));
-  if (!f->L) return -1;
+  f->L = (double*)calloc((size_t)(nfree > 0 ? nfree : 1) * (bw + 1), sizeof(double));
+  if (!f->L || !f->idx) return -1;
   /* assemble the lower band of A */
-  for (int m = 0; m < c->nr; ++m)
-    for (int n = 1; n < c->nz; ++n) {
-      int k = fidx(c, m, n);
-      double diag = a_z(c, m) * 2.0 + a_r(c, m);
-      if (m > 0) diag += a_r(c, m - 1);
+  for (int m = 0; m <= c->nr; ++m)
+    for (int n = 0; n <= c->nz; ++n) {
+      int k = f->idx[nidx(c, m, n)];
+      if (k < 0) continue;
+      int nb[4][2];
+      double a[4], diag = 0.0;
+      int cnt = neighbours(c, m, n, nb, a);
+      for (int j = 0; j < cnt; ++j) {
+        diag += a[j];
+        int kj = f->idx[nidx(c, nb[j][0], nb[j][1])];
+        if (kj >= 0 && kj < k) f->L[(size_t)k * (bw + 1) + (k - kj)] = -a[j];
+      }
       f->L[(size_t)k * (bw + 1) + 0] = diag;
-      if (n > 1) f->L[(size_t)k * (bw + 1) + 1] = -a_z(c, m);
-      if (m > 0) f->L[(size_t)k * (bw + 1) + bw] = -a_r(c, m - 1);
     }
   /* in-place banded Cholesky A = L L^T */
   for (int k = 0; k < nfree; ++k) {
@@ -253,6 +297,11 @@ static int chol_build(const orc_config* c, chol* f) {
   return 0;
 }
 
+static void chol_free(chol* f) {
+  free(f->L);
+  free(f->idx);
+}
+
 static void chol_solve(const chol* f, double* x /* in: b, out: solution */) {
   int bw = f->bw, N = f->nfree;
   for (int k = 0; k < N; ++k) {
@@ -270,23 +319,27 @@ static void chol_solve(const chol* f, double* x /* in: b, out: solution */) {
 }
 
 /* Solve with the factor: rho on nodes, Dirichlet values taken from phi_bc on
- * the boundary nodes (z = 0, z = L, r = R); result written to phi (all nodes). */
+ * the conductor nodes; result written to phi (all nodes). */
 static void poisson_with(const orc_config* c, const chol* f, const double* rho,
                          const double* phi_bc, double* phi) {
-  double* x = (double*)malloc(sizeof(double) * (size_t)f->nfree);
-  for (int m = 0; m < c->nr; ++m)
-    for (int n = 1; n < c->nz; ++n) {
+  double* x = (double*)malloc(sizeof(double) * (size_t)(f->nfree > 0 ? f->nfree : 1));
+  for (int m = 0; m <= c->nr; ++m)
+    for (int n = 0; n <= c->nz; ++n) {
+      int k = f->idx[nidx(c, m, n)];
+      if (k < 0) continue;
       double b = orc_node_volume(c, m, n) * rho[nidx(c, m, n)];
-      if (n == 1) b += a_z(c, m) * phi_bc[nidx(c, m, 0)];
-      if (n == c->nz - 1) b += a_z(c, m) * phi_bc[nidx(c, m, c->nz)];
-      if (m == c->nr - 1) b += a_r(c, m) * phi_bc[nidx(c, c->nr, n)];
-      x[fidx(c, m, n)] = b;
+      int nb[4][2];
+      double a[4];
+      int cnt = neighbours(c, m, n, nb, a);
+      for (int j = 0; j < cnt; ++j)
+        if (f->idx[nidx(c, nb[j][0], nb[j][1])] < 0) b += a[j] * phi_bc[nidx(c, nb[j][0], nb[j][1])];
+      x[k] = b;
     }
   chol_solve(f, x);
   for (int m = 0; m <= c->nr; ++m)
     for (int n = 0; n <= c->nz; ++n) {
-      int dirichlet = (n == 0 || n == c->nz || m == c->nr);
-      phi[nidx(c, m, n)] = dirichlet ? phi_bc[nidx(c, m, n)] : x[fidx(c, m, n)];
+      int k = f->idx[nidx(c, m, n)];
+      phi[nidx(c, m, n)] = k < 0 ? phi_bc[nidx(c, m, n)] : x[k];
     }
   free(x);
 }
@@ -295,7 +348,7 @@ int orc_poisson(const orc_config* c, const double* rho, const double* phi_bc, do
   chol f;
   int rc = chol_build(c, &f);
   if (rc == 0) poisson_with(c, &f, rho, phi_bc, phi);
-  free(f.L);
+  chol_free(&f);
   return rc;
 }
 
@@ -518,7 +571,7 @@ void orc_destroy(orc_sim* s) {
     free(s->sp[k].vz); free(s->sp[k].id); free(s->Qs[k]);
   }
   free(s->phi); free(s->rho); free(s->Q); free(s->Bnr); free(s->Bnz);
-  free(s->f.L); free(s->qhist); free(s);
+  chol_free(&s->f); free(s->qhist); free(s);
 }
 
 int orc_set_particles(orc_sim* s, int sp, int64_t n, const double* r, const double* z,
@@ -564,15 +617,16 @@ static void deposit_all(orc_sim* s) {
     }
 }
 
-/* Dirichlet data: the cathode (z = 0, r_m <= Rc) at V_c; the rest of z = 0,
- * the anode z = L and the wall r = R grounded (Section 3, with the cathode
- * disk of the benchmark configuration). */
+/* Dirichlet data: the cathode (z = 0, r_m <= Rc) at V_c; the other
+ * conductor nodes (anode z = L; the rest of z = 0 and the wall r = R unless
+ * insulating) grounded (Section 3, with the cathode disk of the benchmark
+ * configuration). */
 static void solve_phi(orc_sim* s) {
   const orc_config* c = &s->c;
   size_t nn = (size_t)(c->nr + 1) * (c->nz + 1);
   double* bc = (double*)calloc(nn, sizeof(double));
   for (int m = 0; m <= c->nr; ++m)
-    if (m * dr_of(c) <= c->Rc && m < c->nr) bc[nidx(c, m, 0)] = s->Vc;
+    if (cathode_node(c, m)) bc[nidx(c, m, 0)] = s->Vc;
   poisson_with(c, &s->f, s->rho, bc, s->phi);
   free(bc);
 }

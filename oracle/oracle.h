@@ -21,7 +21,9 @@
  *                          near the J1 root at the cathode edge
  *   orc_deposit            total charge, single-particle split, r^2 moment
  *   orc_poisson            exact quadratic solution, 2nd-order convergence,
- *                          Gauss law
+ *                          Gauss law; insulating boundaries: exact quadratic
+ *                          solutions with zero normal derivative, mirror image
+ *                          of the all-insulating z = 0 plane
  *   orc_efield_at          MC zero axial self-force, EC force = -dW/dx
  *   MCC inside orc_step    collision counts vs nu_k dt, exact energy losses
  *   circuit inside orc_step  prescribed-charge drive; Table 1 cases 1-2
@@ -59,6 +61,8 @@ typedef struct orc_config {
   double sigma_el, ion_a, ion_I, exc_C, exc_E, E_cap;
   double n_meta;           /* metastable Ar* density (m^-3), constant background */
   double meta_a, meta_I;   /* reaction (1d): sigma = meta_a ln(E/meta_I)/(E meta_I) */
+  int32_t gap_neumann;     /* 1: z = 0 outside the cathode is the insulating block */
+  int32_t wall_neumann;    /* 1: the wall r = R is insulating too */
 } orc_config;
 
 typedef struct orc_diag {

@@ -32,6 +32,7 @@ class OracleConfig(C.Structure):
         ("sigma_el", C.c_double), ("ion_a", C.c_double), ("ion_I", C.c_double),
         ("exc_C", C.c_double), ("exc_E", C.c_double), ("E_cap", C.c_double),
         ("n_meta", C.c_double), ("meta_a", C.c_double), ("meta_I", C.c_double),
+        ("gap_neumann", C.c_int32), ("wall_neumann", C.c_int32),
     ]
 
     @classmethod

@@ -74,6 +74,7 @@ def base_params() -> dict:
         sigma_el=1e-19, ion_a=4.0e-18 * 6.0, ion_I=15.76,
         exc_C=3.63e-18, exc_E=11.55, E_cap=800.0,
         n_meta=0.0, meta_a=4.0e-18, meta_I=4.20,
+        gap_neumann=0, wall_neumann=0,
         poisson_tol=1e-10, poisson_max_iter=200,
         cap_e=0, cap_i=0, birth_cap=0, diag_every=1,
         sort_every=1,
