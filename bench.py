@@ -81,6 +81,11 @@ def parse():
                          "SEY x R_ext ensemble on 128x128 grids; learned: the 256x512 "
                          "discharge with and without the learned Poisson warm start; unet: "
                          "the warm-start network alone on the 257x513 node grid")
+    ap.add_argument("--geometry", default="rz256", choices=["rz256", "paper"],
+                    help="rz256 workload's chamber: rz256 = 5 x 5 cm, cathode disk r <= 2 cm, "
+                         "other walls grounded; paper = the 3 x 3 cm chamber of Section 3 "
+                         "(cathode to 0.85 L_r, insulating block on the rest of z = 0, "
+                         "10 mTorr), same 256 x 256 grid and particle count")
     ap.add_argument("--unet-mode", type=int, default=1, choices=[0, 1],
                     help="learned: 0 = network maps (rho, r, V) to phi; 1 = network maps the "
                          "previous solution's residual to the change of phi")
@@ -97,7 +102,10 @@ def parse():
 
 def workload(args):
     g = 0 if args.gather == "ec" else 1
-    p = pic_inputs.params_rz256(gather=g, seed=args.seed)
+    if args.geometry == "paper":
+        p = pic_inputs.params_paper(gather=g, seed=args.seed, cells=256)
+    else:
+        p = pic_inputs.params_rz256(gather=g, seed=args.seed)
     n = int(args.n_per_species)
     p, parts = pic_inputs.grown_ring_state(p, n, seed=args.seed)
     p = pic_inputs.with_capacity(p, parts, factor=1.25, births=1 << 20)
@@ -107,11 +115,14 @@ def workload(args):
 
 
 def config_block(p, n, args):
-    return {"workload": f"rz256_ring_{n:.0e}_per_species_{args.precision}".replace("+", ""),
+    name = "rz256" if args.geometry == "rz256" else "paper256_insulating_block"
+    return {"workload": f"{name}_ring_{n:.0e}_per_species_{args.precision}".replace("+", ""),
             "grid": [p["nr"], p["nz"]], "domain_m": [p["R"], p["L"]],
             "n_per_species": n, "gather": args.gather.upper() + "-PIC",
             "precision": args.precision, "circuit": {"Vs": p["Vs"], "Rext": p["Rext"]},
             "dt": p["dt"], "poisson_tol": p["poisson_tol"], "diag_every": p["diag_every"],
+            "insulating_boundary": {"z0_outside_cathode": p["gap_neumann"],
+                                    "wall_r_R": p["wall_neumann"]},
             "l2": "inputs larger than L2 (particle state 3.8 GB >> 129 MB)"}
 
 

@@ -97,6 +97,10 @@ typedef struct pic_config {
   double n_meta;             /* metastable Ar* density (m^-3), a constant background; 0 = off */
   double meta_a, meta_I;     /* stepwise ionization (1d) from Ar*: sigma = meta_a ln(E/meta_I)/(E meta_I)
                                 (m^2 eV^2, eV; Section 3: threshold 4.20 eV) */
+  int32_t gap_neumann;       /* 1: the plane z = 0 outside the cathode is the insulating block
+                                (Section 3: Neumann boundary, no normal field; its nodes are
+                                unknowns of the Poisson solve); 0: grounded conductor */
+  int32_t wall_neumann;      /* 1: the wall r = R is insulating as well; 0: grounded */
 } pic_config;
 
 /* Device-memory provider.  alloc returns a device pointer aligned to at least
@@ -336,6 +340,19 @@ int pic_unet_stats_read(pic_handle* h, pic_unet_stats* out);
 
 /* Bytes of device scratch that pic_poisson_solve needs for an nr x nz grid. */
 size_t pic_poisson_workspace_bytes(int nr, int nz);
+
+/* pic_poisson_solve with insulating (Neumann) boundary parts: the nodes of
+ * row z = 0 from radial index first_insulating_z0 on (nr + 1: none) and,
+ * when wall_insulating is 1, the wall r = R (n = 1 .. nz - 1, and the corner
+ * r = R, z = 0 when row 0 is insulating there too) are unknowns with zero
+ * normal flux; every other boundary node holds its Dirichlet value from
+ * phi_dev.  Other arguments, ownership and errors as pic_poisson_solve;
+ * PIC_ERR_INVALID also for first_insulating_z0 outside [0, nr + 1] or
+ * wall_insulating not 0/1. */
+int pic_poisson_solve_mixed(int nr, int nz, double R, double L, int first_insulating_z0,
+                            int wall_insulating, double tol, int max_iter, const double* Q_dev,
+                            double* phi_dev, void* work_dev, void* cuda_stream, int* iters,
+                            double* resid);
 
 /* Standalone RZ Poisson solve (Section 3: Dirichlet electrodes, Gauss's law
  * on the axis) on the stream `cuda_stream`.

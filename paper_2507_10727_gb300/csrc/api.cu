@@ -137,6 +137,8 @@ std::string validate(const pic_config& c) {
   if (!(c.E_cap > 0)) return "E_cap must be positive";
   if (!(c.n_meta >= 0.0)) return "n_meta must be >= 0";
   if (c.n_meta > 0.0 && !(c.meta_I > 0.0 && c.meta_a >= 0.0)) return "meta_I > 0, meta_a >= 0";
+  if ((c.gap_neumann != 0 && c.gap_neumann != 1) || (c.wall_neumann != 0 && c.wall_neumann != 1))
+    return "gap_neumann, wall_neumann must be 0 or 1";
   return "";
 }
 
@@ -159,6 +161,8 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
   I.m_cath = -1;
   for (int m = 0; m <= c.nr; ++m)
     if (m * I.dr <= c.Rc && m < c.nr) I.m_cath = m;
+  I.bc_g = c.gap_neumann ? I.m_cath + 1 : c.nr + 1;
+  I.bc_wall = c.wall_neumann ? 1 : 0;
   I.dt = c.dt;
   I.weight = c.weight;
   I.qm[0] = -kQe / kMe;
@@ -283,7 +287,7 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
   if (e == cudaSuccess) e = cudaMemsetAsync(I.diag, 0, sizeof(DiagDev), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(pwbase, 0, pwb, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "memset");
-  ih.pw = poisson_work_init(pwbase, c.nr, c.nz, c.R, c.L, h->num_sms);
+  ih.pw = poisson_work_init(pwbase, c.nr, c.nz, c.R, c.L, I.bc_g, I.bc_wall, h->num_sms);
 
   // static magnetic field: node values in FP64, folded per cell into
   // bilinear coefficients (B table keyed like the cells)
@@ -1070,6 +1074,7 @@ int pic_unet_create(pic_handle* h, uint64_t seed, int max_batch, int mode) {
   UNet* u = unet_create(c.nr, c.nz, max_batch, mode, seed, vref > 0.0 ? vref : 1.0, unet_alloc_cb,
                         h, h->stream);
   if (!u) return fail(h, PIC_ERR_OOM, "network allocation or set-up failed");
+  unet_set_boundary(u, h->inst[0].I.bc_g, h->inst[0].I.bc_wall);
   h->unet = u;
   drop_graph(h);
   return PIC_OK;
@@ -1202,8 +1207,18 @@ size_t pic_poisson_workspace_bytes(int nr, int nz) {
 int pic_poisson_solve(int nr, int nz, double R, double L, double tol, int max_iter,
                       const double* Q_dev, double* phi_dev, void* work_dev, void* cuda_stream,
                       int* iters, double* resid) {
+  return pic_poisson_solve_mixed(nr, nz, R, L, nr + 1, 0, tol, max_iter, Q_dev, phi_dev, work_dev,
+                                 cuda_stream, iters, resid);
+}
+
+int pic_poisson_solve_mixed(int nr, int nz, double R, double L, int first_insulating_z0,
+                            int wall_insulating, double tol, int max_iter, const double* Q_dev,
+                            double* phi_dev, void* work_dev, void* cuda_stream, int* iters,
+                            double* resid) {
   if (nr < 2 || nz < 2 || (nr & 1) || (nz & 1) || !(R > 0) || !(L > 0) || !(tol > 0) ||
-      max_iter < 1 || !Q_dev || !phi_dev || !work_dev || ((uintptr_t)work_dev & 255))
+      max_iter < 1 || !Q_dev || !phi_dev || !work_dev || ((uintptr_t)work_dev & 255) ||
+      first_insulating_z0 < 0 || first_insulating_z0 > nr + 1 ||
+      (wall_insulating != 0 && wall_insulating != 1))
     return PIC_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   int dev = 0, sms = 1;
@@ -1212,7 +1227,8 @@ int pic_poisson_solve(int nr, int nz, double R, double L, double tol, int max_it
   const size_t wb = poisson_work_bytes(nr, nz);
   cudaError_t e = cudaMemsetAsync(work_dev, 0, wb + 256, st);
   if (e != cudaSuccess) return PIC_ERR_CUDA;
-  PoissonWork* pw = poisson_work_init(work_dev, nr, nz, R, L, sms);
+  PoissonWork* pw = poisson_work_init(work_dev, nr, nz, R, L, first_insulating_z0, wall_insulating,
+                                      sms);
   char* tailp = (char*)work_dev + wb;
   int* status = (int*)tailp;
   int* it_dev = (int*)(tailp + 16);

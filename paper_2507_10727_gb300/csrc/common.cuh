@@ -156,6 +156,8 @@ struct Inst {
   unsigned long long seed;
   // switches
   int gather, rweight, mcc_on, push_on, field_on, walls_reflect, circuit_mode, n_avg;
+  int bc_g;                // first insulating node of row z = 0 (nr + 1: none)
+  int bc_wall;             // 1: the wall r = R is insulating
   int diag_every;
   double Vc_fixed, Vs, Rext;
   double poisson_tol;
@@ -265,6 +267,16 @@ __device__ __forceinline__ FixW fix_weights(double wr, double wz) {
 // finite test on the exponent bits (integer pipe)
 __device__ __forceinline__ bool finite64(double x) {
   return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+
+// Field boundary (Section 3).  Conductors (Dirichlet nodes): the anode row
+// n = nz, the cathode nodes of row 0, and -- unless insulating -- the rest of
+// row 0 and the wall m = nr.  Insulating parts (the Neumann block) are
+// unknowns: row 0 from node g on (g = nr + 1: none), the wall when `wall`.
+__host__ __device__ __forceinline__ bool field_free(int m, int n, int nr, int nz, int g, int wall) {
+  if (n < 0 || n >= nz || m < 0 || m > nr) return false;
+  if (n == 0) return m >= g && (m < nr || wall != 0);
+  return m < nr || wall != 0;
 }
 
 __device__ __forceinline__ double node_area(const Inst& I, int m) {

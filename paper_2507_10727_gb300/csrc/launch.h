@@ -89,7 +89,10 @@ cudaError_t launch_charge(const Inst& I, cudaStream_t st);
 
 // Poisson workspace
 size_t poisson_work_bytes(int nr, int nz);
-PoissonWork* poisson_work_init(void* base, int nr, int nz, double R, double L, int num_sms);
+// g: first free (insulating) node of row z = 0 (nr + 1: none); wall: 1 when
+// the wall r = R is insulating
+PoissonWork* poisson_work_init(void* base, int nr, int nz, double R, double L, int g, int wall,
+                               int num_sms);
 void poisson_work_free(PoissonWork* pw);
 // solve A phi = Q (+ Dirichlet values held in phi's boundary nodes)
 cudaError_t launch_poisson(PoissonWork* pw, const double* Q, double* phi, double tol, int max_iter,
@@ -100,8 +103,8 @@ cudaError_t launch_poisson(PoissonWork* pw, const double* Q, double* phi, double
 namespace pic {
 // Poisson solve over a caller-provided workspace of poisson_work_bytes(nr, nz)
 // bytes at `base` (already cleared); allocates nothing.
-cudaError_t launch_poisson_in_place(void* base, int nr, int nz, double R, double L, int num_sms,
-                                    const double* Q, double* phi, double tol, int max_iter,
-                                    int* status_dev, int* iters_dev, double* resid_dev,
-                                    cudaStream_t st);
+cudaError_t launch_poisson_in_place(void* base, int nr, int nz, double R, double L, int g, int wall,
+                                    int num_sms, const double* Q, double* phi, double tol,
+                                    int max_iter, int* status_dev, int* iters_dev,
+                                    double* resid_dev, cudaStream_t st);
 }  // namespace pic

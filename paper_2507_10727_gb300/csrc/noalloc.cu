@@ -74,7 +74,7 @@ extern "C" int pic_poisson_solve_static(int nr, int nz, double R, double L, doub
   int* status = (int*)tail;
   int* it_dev = (int*)(tail + 16);
   double* res_dev = (double*)(tail + 32);
-  if (pic::launch_poisson_in_place(base, nr, nz, R, L, sms, Q_dev, phi_dev, tol, max_iter, status,
+  if (pic::launch_poisson_in_place(base, nr, nz, R, L, nr + 1, 0, sms, Q_dev, phi_dev, tol, max_iter, status,
                                    it_dev, res_dev, st) != cudaSuccess)
     return PIC_ERR_CUDA;
   int hs[2] = {0, 0};

@@ -1,13 +1,21 @@
-// poisson.cu -- RZ Poisson solve (arXiv:2507.10727, Section 3: anode and
-// walls grounded, cathode at the circuit voltage, Gauss's law on the axis).
+// poisson.cu -- RZ Poisson solve (arXiv:2507.10727, Section 3: anode
+// grounded, cathode at the circuit voltage, the insulating block a Neumann
+// boundary, Gauss's law on the axis).
 //
 // Discretisation (the paper gives none; finite-volume reading): for a free
-// node (m, n), m = 0..nr-1, n = 1..nz-1, the equation times the node's
-// control volume reads  sum_j a_kj (phi_k - phi_j) = Q_k  with
-//   a_r(m) = 2 pi eps0 (m + 1/2) dz           between (m,n) and (m+1,n)
+// node (m, n) the equation times the node's control volume (its part of the
+// box r_m -+ dr/2, z_n -+ dz/2 inside the domain) reads
+// sum_j a_kj (phi_k - phi_j) = Q_k  with
+//   a_r(m) h(n) = 2 pi eps0 (m + 1/2) dz h(n)  between (m,n) and (m+1,n),
+//                 h = 1/2 on z = 0 (half-height faces), else 1
 //   a_z(m) = eps0 area(m) / dz                between (m,n) and (m,n+1)
-//   area(m) = 2 pi m dr^2 (m >= 1), pi dr^2 / 4 (axis: Gauss on the disk dr/2)
-// which is symmetric positive definite on the free nodes.
+//   area(m) = 2 pi m dr^2 (0 < m < nr), pi dr^2 / 4 (axis: Gauss on the disk
+//   dr/2), pi (nr - 1/4) dr^2 (half annulus at r = R)
+// and no flux through the domain's surface, which is symmetric positive
+// definite on the free nodes.  Free nodes: the interior m = 0..nr-1,
+// n = 1..nz-1, plus the insulating boundary "line" (row 0 from node g on,
+// then the wall column m = nr when it is insulating); the rest of the
+// boundary holds Dirichlet values.
 //
 // Solver: one cooperative persistent kernel.  Flexible preconditioned
 // conjugate gradients with iterates, residuals and dot products in FP64
@@ -46,6 +54,8 @@ struct PoissonWork {
   int nblocks;
   int smem_bytes;          // dynamic shared memory per block
   int lnr[kMaxLev], lnz[kMaxLev];
+  int bc_g[kMaxLev];       // first free node of row 0 per level (lnr + 1: none)
+  int bc_wall;             // 1: the wall column m = nr is free (insulating)
   int coef_off[kMaxLev];   // offset of level l in the per-level coupling tables
   int ncoef;               // entries of each coupling table
   int tail_floats;         // shared-memory floats of the tail levels (u and f)
@@ -98,10 +108,12 @@ size_t poisson_work_bytes(int nr, int nz) {
 
 // Layout of the workspace at `base` (poisson_work_bytes bytes) and of the
 // shared memory: FP64 level-0 tables, three FP32 tables, then the tail levels.
-static void layout(PoissonWork& w, void* base, int nr, int nz, double R, double L) {
+static void layout(PoissonWork& w, void* base, int nr, int nz, double R, double L, int g,
+                   int wall) {
   std::memset(&w, 0, sizeof(w));
   w.nr = nr;
   w.nz = nz;
+  w.bc_wall = wall ? 1 : 0;
   w.dr = R / nr;
   w.dz = L / nz;
   char* p = (char*)base;
@@ -116,6 +128,9 @@ static void layout(PoissonWork& w, void* base, int nr, int nz, double R, double 
   w.q = (double*)take(nn * sizeof(double));
   w.z = (double*)take(nn * sizeof(double));
   w.nlev = level_count(nr, nz, w.lnr, w.lnz);
+  // a coarse row-0 node is free when the fine node at the same place is
+  w.bc_g[0] = g < 0 ? 0 : (g > nr + 1 ? nr + 1 : g);
+  for (int l = 1; l < w.nlev; ++l) w.bc_g[l] = (w.bc_g[l - 1] + 1) / 2;
   int off = 0;
   for (int l = 0; l < w.nlev; ++l) {
     const size_t ln = (size_t)(w.lnr[l] + 1) * (w.lnz[l] + 1);
@@ -181,6 +196,7 @@ __device__ __forceinline__ bool barrier_grid(unsigned int* bar, int* status, int
 // diagonal.
 struct Lev {
   int nr, nz;
+  int g, wall;   // insulating boundary nodes (row 0 from g on, the wall column)
   float* u;
   float* f;
   const float* az;
@@ -200,6 +216,8 @@ __device__ __forceinline__ Lev lev(const PoissonWork& W, const Tables& T, int l,
   Lev L;
   L.nr = W.lnr[l];
   L.nz = W.lnz[l];
+  L.g = W.bc_g[l];
+  L.wall = W.bc_wall;
   L.u = u;
   L.f = f;
   L.az = T.az + W.coef_off[l];
@@ -212,8 +230,57 @@ __device__ __forceinline__ Lev lev(const PoissonWork& W, const Tables& T, int l,
 // az (along z, between n and n +- 1) and ar (between m and m + 1).
 __device__ __forceinline__ void fine_coef(const PoissonWork& W, int m, double& az, double& ar) {
   const double c = 2.0 * kPi * kEps0;
-  az = m == 0 ? c * W.dr * W.dr / (8.0 * W.dz) : c * m * W.dr * W.dr / W.dz;
+  az = m == 0       ? c * W.dr * W.dr / (8.0 * W.dz)
+       : m == W.nr ? c * (m - 0.25) * W.dr * W.dr / (2.0 * W.dz)
+                   : c * m * W.dr * W.dr / W.dz;
   ar = c * (m + 0.5) * W.dz;
+}
+
+// Insulating boundary nodes of a level, numbered j = 0, 1, ...: row 0 from
+// node g to nr - 1 (to nr when the wall is insulating too), then the wall
+// column m = nr, n = 1 .. nz - 1.
+__host__ __device__ __forceinline__ int line_gap(int nr, int g, int wall) {
+  const int last = wall ? nr : nr - 1;
+  return last >= g ? last - g + 1 : 0;
+}
+__host__ __device__ __forceinline__ int line_count(int nr, int nz, int g, int wall) {
+  return line_gap(nr, g, wall) + (wall ? nz - 1 : 0);
+}
+__device__ __forceinline__ void line_node(int j, int nr, int g, int ngap, int& m, int& n) {
+  if (j < ngap) {
+    m = g + j;
+    n = 0;
+  } else {
+    m = nr;
+    n = 1 + (j - ngap);
+  }
+}
+
+// Gauss-Seidel pieces at an insulating boundary node: s = sum of couplings
+// times neighbour values (neighbours inside the grid; r-couplings halved on
+// row 0), diag = sum of couplings.  Values on Dirichlet nodes are zero in the
+// multigrid arrays (corrections).
+__device__ __forceinline__ float line_sum(const Lev& L, int m, int n, float& diag) {
+  const int nz1 = L.nz + 1, i = m * nz1 + n;
+  const float h = n == 0 ? 0.5f : 1.0f;
+  const float az = L.az[m];
+  float s = az * L.u[i + 1];
+  diag = az;
+  if (n > 0) {
+    s += az * L.u[i - 1];
+    diag += az;
+  }
+  if (m < L.nr) {
+    const float c = h * L.ar[m];
+    s += c * L.u[i + nz1];
+    diag += c;
+  }
+  if (m > 0) {
+    const float c = h * L.ar[m - 1];
+    s += c * L.u[i - nz1];
+    diag += c;
+  }
+  return s;
 }
 
 // Nodes are visited as warp items (row m, 32-wide segment of n):
@@ -226,20 +293,41 @@ __device__ __forceinline__ int segs_color(int nz) { return (nz / 2 + 32) >> 5; }
 __device__ void smooth(const Lev L, int color, int wid, int nw, int lane) {
   const int ns = segs_color(L.nz), nz1 = L.nz + 1;
   const int items = L.nr * ns;
-  for (int it = wid; it < items; it += nw) {
-    const int m = it / ns, s = it - m * ns;
-    const int odd = (color + m) & 1;
-    const int n = 2 * (s * 32 + lane) + (odd ? 1 : 2);
-    if (n > L.nz - 1) continue;
-    const int i = m * nz1 + n;
-    float sum = L.f[i] + L.az[m] * (L.u[i - 1] + L.u[i + 1]) + L.ar[m] * L.u[i + nz1];
-    if (m > 0) sum += L.ar[m - 1] * L.u[i - nz1];
-    L.u[i] = sum * L.idg[m];
+  const int ngap = line_gap(L.nr, L.g, L.wall);
+  const int nline = ngap + (L.wall ? L.nz - 1 : 0);
+  const int total = items + ((nline + 31) >> 5);
+  for (int it = wid; it < total; it += nw) {
+    if (it < items) {
+      const int m = it / ns, s = it - m * ns;
+      const int odd = (color + m) & 1;
+      const int n = 2 * (s * 32 + lane) + (odd ? 1 : 2);
+      if (n > L.nz - 1) continue;
+      const int i = m * nz1 + n;
+      float sum = L.f[i] + L.az[m] * (L.u[i - 1] + L.u[i + 1]) + L.ar[m] * L.u[i + nz1];
+      if (m > 0) sum += L.ar[m - 1] * L.u[i - nz1];
+      L.u[i] = sum * L.idg[m];
+    } else {
+      const int j = (it - items) * 32 + lane;
+      if (j >= nline) continue;
+      int m, n;
+      line_node(j, L.nr, L.g, ngap, m, n);
+      if (((m + n) & 1) != color) continue;
+      float diag;
+      const float sum = line_sum(L, m, n, diag);
+      const int i = m * nz1 + n;
+      L.u[i] = (L.f[i] + sum) / diag;
+    }
   }
 }
 
 __device__ __forceinline__ float resid_at(const Lev L, int m, int n) {
-  if (m < 0 || m >= L.nr || n < 1 || n >= L.nz) return 0.0f;
+  if (m < 0 || m >= L.nr || n < 1 || n >= L.nz) {
+    if (!field_free(m, n, L.nr, L.nz, L.g, L.wall)) return 0.0f;
+    float diag;
+    const float s = line_sum(L, m, n, diag);
+    const int i = m * (L.nz + 1) + n;
+    return L.f[i] - (diag * L.u[i] - s);
+  }
   const int nz1 = L.nz + 1, i = m * nz1 + n;
   const float arm = m > 0 ? L.ar[m - 1] : 0.0f;
   const float diag = 2.0f * L.az[m] + L.ar[m] + arm;
@@ -252,10 +340,20 @@ __device__ __forceinline__ float resid_at(const Lev L, int m, int n) {
 __device__ void restrict_to(const Lev F, const Lev C, int wid, int nw, int lane) {
   const int ns = segs_full(C.nz), nz1 = C.nz + 1;
   const int items = C.nr * ns;
-  for (int it = wid; it < items; it += nw) {
-    const int M = it / ns, s = it - M * ns;
-    const int N = 1 + s * 32 + lane;
-    if (N > C.nz - 1) continue;
+  const int ngap = line_gap(C.nr, C.g, C.wall);
+  const int nline = ngap + (C.wall ? C.nz - 1 : 0);
+  const int total = items + ((nline + 31) >> 5);
+  for (int it = wid; it < total; it += nw) {
+    int M, N;
+    if (it < items) {
+      M = it / ns;
+      N = 1 + (it - M * ns) * 32 + lane;
+      if (N > C.nz - 1) continue;
+    } else {
+      const int j = (it - items) * 32 + lane;
+      if (j >= nline) continue;
+      line_node(j, C.nr, C.g, ngap, M, N);
+    }
     float acc = 0.0f;
 #pragma unroll
     for (int di = -1; di <= 1; ++di) {
@@ -275,10 +373,20 @@ __device__ void restrict_to(const Lev F, const Lev C, int wid, int nw, int lane)
 __device__ void prolong_from(const Lev F, const Lev C, int wid, int nw, int lane) {
   const int ns = segs_full(F.nz), fz1 = F.nz + 1, cz1 = C.nz + 1;
   const int items = F.nr * ns;
-  for (int it = wid; it < items; it += nw) {
-    const int m = it / ns, s = it - m * ns;
-    const int n = 1 + s * 32 + lane;
-    if (n > F.nz - 1) continue;
+  const int ngap = line_gap(F.nr, F.g, F.wall);
+  const int nline = ngap + (F.wall ? F.nz - 1 : 0);
+  const int total = items + ((nline + 31) >> 5);
+  for (int it = wid; it < total; it += nw) {
+    int m, n;
+    if (it < items) {
+      m = it / ns;
+      n = 1 + (it - m * ns) * 32 + lane;
+      if (n > F.nz - 1) continue;
+    } else {
+      const int j = (it - items) * 32 + lane;
+      if (j >= nline) continue;
+      line_node(j, F.nr, F.g, ngap, m, n);
+    }
     const int cm = m >> 1, cn = n >> 1;
     const float* u = C.u;
     float v;
@@ -426,6 +534,38 @@ __device__ __forceinline__ double apply64(const Tables& T, const double* x, int 
   return a;
 }
 
+// (A x) at an insulating boundary node of the fine level; with `masked`
+// the neighbours that are Dirichlet nodes count as zero (x a correction),
+// else x holds their values.  Optionally adds the Dirichlet couplings
+// (a_kj x_j over Dirichlet neighbours j) to *bd.
+__device__ __forceinline__ double line_apply64(const Tables& T, const double* x, int m, int n,
+                                               int nr, int nz, int g, int wall, bool masked,
+                                               double* bd) {
+  const int nz1 = nz + 1, i = m * nz1 + n;
+  const double h = n == 0 ? 0.5 : 1.0, xi = x[i];
+  double a = 0.0;
+  auto nb = [&](int mm, int nn, int j, double c) {
+    const bool fr = field_free(mm, nn, nr, nz, g, wall);
+    const double xj = (masked && !fr) ? 0.0 : x[j];
+    a += c * (xi - xj);
+    if (bd && !fr) *bd += c * x[j];
+  };
+  nb(m, n + 1, i + 1, T.az0[m]);
+  if (n > 0) nb(m, n - 1, i - 1, T.az0[m]);
+  if (m < nr) nb(m + 1, n, i + nz1, h * T.ar0[m]);
+  if (m > 0) nb(m - 1, n, i - nz1, h * T.ar0[m - 1]);
+  return a;
+}
+
+// diagonal of the FP32 operator at an insulating boundary node
+__device__ __forceinline__ float line_diag(const Lev& L, int m, int n) {
+  const float h = n == 0 ? 0.5f : 1.0f;
+  float d = L.az[m] * (n > 0 ? 2.0f : 1.0f);
+  if (m < L.nr) d += h * L.ar[m];
+  if (m > 0) d += h * L.ar[m - 1];
+  return d;
+}
+
 // One solve per block group: `group` == nullptr -> the whole grid solves A0;
 // otherwise block b works on group[b / bpi] with bpi blocks per solve (the
 // ensemble's discharges solved side by side in one launch).
@@ -459,8 +599,25 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
   const int ngw = (nb * blockDim.x) >> 5;
   const int nsf = (nz - 1 + 31) >> 5;            // segments of a fine row
   const int items0 = nr * nsf;
-  const long long nfree = (long long)nr * (nz - 1);
+  // insulating boundary nodes follow the interior rows as extra warp items
+  const int g0 = W.bc_g[0], wall = W.bc_wall;
+  const int ngap0 = line_gap(nr, g0, wall);
+  const int nline0 = ngap0 + (wall ? nz - 1 : 0);
+  const int itemsT = items0 + ((nline0 + 31) >> 5);
+  const long long nfree = (long long)nr * (nz - 1) + nline0;
   double* phi = A.phi;
+  // node of warp item `it` for this lane; false when the lane has none
+  auto node_of = [&](int it, int& m, int& n) -> bool {
+    if (it < items0) {
+      m = it / nsf;
+      n = 1 + (it - m * nsf) * 32 + lane;
+      return n <= nz - 1;
+    }
+    const int j = (it - items0) * 32 + lane;
+    if (j >= nline0) return false;
+    line_node(j, nr, g0, ngap0, m, n);
+    return true;
+  };
 
   // ---- coupling tables of every level in shared memory ----------------------
   double* az0 = (double*)smem;
@@ -474,7 +631,9 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
     const float drl = (float)(W.dr * (double)(1 << l)), dzl = (float)(W.dz * (double)(1 << l));
     const int o = W.coef_off[l], lr = W.lnr[l];
     for (int m = threadIdx.x; m <= lr; m += blockDim.x) {
-      const float az = m == 0 ? drl * drl / (8.0f * dzl) : (float)m * drl * drl / dzl;
+      const float az = m == 0    ? drl * drl / (8.0f * dzl)
+                       : m == lr ? ((float)m - 0.25f) * drl * drl / (2.0f * dzl)
+                                 : (float)m * drl * drl / dzl;
       const float arp = dzl * ((float)m + 0.5f);
       const float arm = m > 0 ? dzl * ((float)m - 0.5f) : 0.0f;
       taz[o + m] = az;
@@ -489,15 +648,20 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
   double vals[3];
   // ---- r = Q - A phi (Dirichlet values in phi), ||b||^2, ||r||^2 ------------
   double bb = 0.0, rr = 0.0;
-  for (int it = gw; it < items0; it += ngw) {
-    const int m = it / nsf, n = 1 + (it - m * nsf) * 32 + lane;
-    if (n > nz - 1) continue;
+  for (int it = gw; it < itemsT; it += ngw) {
+    int m, n;
+    if (!node_of(it, m, n)) continue;
     const int i = m * nz1 + n;
-    double b = A.Q[i];
-    if (n == 1) b += az0[m] * phi[i - 1];
-    if (n == nz - 1) b += az0[m] * phi[i + 1];
-    if (m == nr - 1) b += ar0[m] * phi[i + nz1];
-    const double r = A.Q[i] - apply64(T, phi, m, i, nz1);
+    double b = A.Q[i], a;
+    if (it < items0) {
+      if (n == 1 && !field_free(m, 0, nr, nz, g0, wall)) b += az0[m] * phi[i - 1];
+      if (n == nz - 1) b += az0[m] * phi[i + 1];
+      if (m == nr - 1 && !wall) b += ar0[m] * phi[i + nz1];
+      a = apply64(T, phi, m, i, nz1);
+    } else {
+      a = line_apply64(T, phi, m, n, nr, nz, g0, wall, false, &b);
+    }
+    const double r = A.Q[i] - a;
     W.r[i] = r;
     bb += b * b;
     rr += r * r;
@@ -524,13 +688,14 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
   int restarts = 0;
   if (!converged) {
     // f0 = scale r; the first red half sweep from u0 = 0 is u0 = f0 / diag
-    for (int itm = gw; itm < items0; itm += ngw) {
-      const int m = itm / nsf, n = 1 + (itm - m * nsf) * 32 + lane;
-      if (n > nz - 1) continue;
+    for (int itm = gw; itm < itemsT; itm += ngw) {
+      int m, n;
+      if (!node_of(itm, m, n)) continue;
       const int i = m * nz1 + n;
       const float f = (float)(W.r[i] * scale);
       L0.f[i] = f;
-      L0.u[i] = ((m + n) & 1) == 0 ? f * L0.idg[m] : 0.0f;
+      const float idg = itm < items0 ? L0.idg[m] : 1.0f / line_diag(L0, m, n);
+      L0.u[i] = ((m + n) & 1) == 0 ? f * idg : 0.0f;
     }
     if (!barrier_grid(W.bar, A.status, nb)) return;
   }
@@ -562,9 +727,9 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
     }
     // ---- z = M^{-1} r, r.z and z.q_old ------------------------------------
     double rz_loc = 0.0, zq_loc = 0.0;
-    for (int itm = gw; itm < items0; itm += ngw) {
-      const int m = itm / nsf, n = 1 + (itm - m * nsf) * 32 + lane;
-      if (n > nz - 1) continue;
+    for (int itm = gw; itm < itemsT; itm += ngw) {
+      int m, n;
+      if (!node_of(itm, m, n)) continue;
       const int i = m * nz1 + n;
       const double zi = (double)L0.u[i] * unscale;
       W.z[i] = zi;
@@ -582,15 +747,21 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
     rz = vals[0];
     first = false;
     double pq = 0.0;
-    for (int itm = gw; itm < items0; itm += ngw) {
-      const int m = itm / nsf, n = 1 + (itm - m * nsf) * 32 + lane;
-      if (n > nz - 1) continue;
+    for (int itm = gw; itm < itemsT; itm += ngw) {
+      int m, n;
+      if (!node_of(itm, m, n)) continue;
       const int i = m * nz1 + n;
       const double zi = W.z[i];
-      const double zl = n > 1 ? W.z[i - 1] : 0.0, zu = n < nz - 1 ? W.z[i + 1] : 0.0;
-      const double zo = m < nr - 1 ? W.z[i + nz1] : 0.0;
-      double a = az0[m] * (2.0 * zi - zl - zu) + ar0[m] * (zi - zo);
-      if (m > 0) a += ar0[m - 1] * (zi - W.z[i - nz1]);
+      double a;
+      if (itm < items0) {
+        const double zl = (n > 1 || m >= g0) ? W.z[i - 1] : 0.0;
+        const double zu = n < nz - 1 ? W.z[i + 1] : 0.0;
+        const double zo = (m < nr - 1 || wall) ? W.z[i + nz1] : 0.0;
+        a = az0[m] * (2.0 * zi - zl - zu) + ar0[m] * (zi - zo);
+        if (m > 0) a += ar0[m - 1] * (zi - W.z[i - nz1]);
+      } else {
+        a = line_apply64(T, W.z, m, n, nr, nz, g0, wall, true, nullptr);
+      }
       const double pi = zi + beta * W.p[i];
       const double qi = a + beta * W.q[i];
       W.p[i] = pi;
@@ -605,9 +776,9 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
     alpha = vals[0] != 0.0 ? rz / vals[0] : 0.0;
     // ---- phi += alpha p, r -= alpha q, next V-cycle's f0 and red sweep ----
     double rl = 0.0;
-    for (int itm = gw; itm < items0; itm += ngw) {
-      const int m = itm / nsf, n = 1 + (itm - m * nsf) * 32 + lane;
-      if (n > nz - 1) continue;
+    for (int itm = gw; itm < itemsT; itm += ngw) {
+      int m, n;
+      if (!node_of(itm, m, n)) continue;
       const int i = m * nz1 + n;
       phi[i] += alpha * W.p[i];
       const double r = W.r[i] - alpha * W.q[i];
@@ -615,7 +786,8 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
       rl += r * r;
       const float f = (float)(r * scale);
       L0.f[i] = f;
-      L0.u[i] = ((m + n) & 1) == 0 ? f * L0.idg[m] : 0.0f;
+      const float idg = itm < items0 ? L0.idg[m] : 1.0f / line_diag(L0, m, n);
+      L0.u[i] = ((m + n) & 1) == 0 ? f * idg : 0.0f;
     }
     vals[0] = rl;
     block_partials(W.partial, parity, 1, vals, lb, nb);
@@ -627,16 +799,20 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
     if (rr <= tol2bb) {
       // confirm with the true residual b - A phi (also the restart's input)
       double rt = 0.0;
-      for (int itm = gw; itm < items0; itm += ngw) {
-        const int m = itm / nsf, n = 1 + (itm - m * nsf) * 32 + lane;
-        if (n > nz - 1) continue;
+      for (int itm = gw; itm < itemsT; itm += ngw) {
+        int m, n;
+        if (!node_of(itm, m, n)) continue;
         const int i = m * nz1 + n;
-        const double r = A.Q[i] - apply64(T, phi, m, i, nz1);
+        const double a = itm < items0
+                             ? apply64(T, phi, m, i, nz1)
+                             : line_apply64(T, phi, m, n, nr, nz, g0, wall, false, nullptr);
+        const double r = A.Q[i] - a;
         W.r[i] = r;
         rt += r * r;
         const float f = (float)(r * scale);
         L0.f[i] = f;
-        L0.u[i] = ((m + n) & 1) == 0 ? f * L0.idg[m] : 0.0f;
+        const float idg = itm < items0 ? L0.idg[m] : 1.0f / line_diag(L0, m, n);
+        L0.u[i] = ((m + n) & 1) == 0 ? f * idg : 0.0f;
       }
       vals[0] = rt;
       block_partials(W.partial, parity, 1, vals, lb, nb);
@@ -667,13 +843,26 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
 // the smallest score (below) wins, ties keep the earlier candidate, and the
 // winner is copied into phi's free nodes.
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ bool free_node(int m, int n, int nr, int nz) {
-  return m < nr && n >= 1 && n <= nz - 1;
+__device__ __forceinline__ bool free_node(const PoissonWork& W, int m, int n) {
+  return field_free(m, n, W.nr, W.nz, W.bc_g[0], W.bc_wall);
 }
 
-__device__ __forceinline__ double start_value(int k, const double* phi, const double* cand, int m,
-                                              int n, int i, int nr, int nz) {
-  if (k == 0 || !free_node(m, n, nr, nz)) return phi[i];
+// couplings of fine node (m, n) to (m-1, n), (m+1, n), (m, n-1), (m, n+1);
+// 0 for neighbours outside the grid, r-couplings halved on row 0
+__device__ __forceinline__ void node_coup(const PoissonWork& W, int m, int n, double c[4]) {
+  double az, ar, azm, arm = 0.0;
+  fine_coef(W, m, az, ar);
+  if (m > 0) fine_coef(W, m - 1, azm, arm);
+  const double h = n == 0 ? 0.5 : 1.0;
+  c[0] = m > 0 ? h * arm : 0.0;
+  c[1] = m < W.nr ? h * ar : 0.0;
+  c[2] = n > 0 ? az : 0.0;
+  c[3] = n < W.nz ? az : 0.0;
+}
+
+__device__ __forceinline__ double start_value(int k, const double* phi, const double* cand,
+                                              bool fr, int i) {
+  if (k == 0 || !fr) return phi[i];
   return k == 1 ? cand[i] : 0.0;
 }
 
@@ -682,23 +871,26 @@ __global__ void __launch_bounds__(256) k_guess_norms(PoissonWork W, const double
                                                      const double* cand, double* partial) {
   __shared__ double red[3][8];
   const int nr = W.nr, nz = W.nz, nz1 = nz + 1;
-  const long long nfree = (long long)nr * (nz - 1);
+  const long long nn = (long long)(nr + 1) * nz1;
+  const int dm[4] = {-1, 1, 0, 0}, dn[4] = {0, 0, -1, 1};
   double loc[3] = {0.0, 0.0, 0.0};
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nfree;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn;
        e += (long long)gridDim.x * blockDim.x) {
-    const int m = (int)(e / (nz - 1)), n = 1 + (int)(e - (long long)m * (nz - 1));
-    const int i = m * nz1 + n;
-    double az, ar, azm = 0.0, arm = 0.0;
-    fine_coef(W, m, az, ar);
-    if (m > 0) fine_coef(W, m - 1, azm, arm);
+    const int m = (int)(e / nz1), n = (int)(e - (long long)m * nz1);
+    if (!free_node(W, m, n)) continue;
+    const int i = (int)e;
+    double c[4];
+    node_coup(W, m, n, c);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const double xi = start_value(k, phi, cand, m, n, i, nr, nz);
-      const double xl = start_value(k, phi, cand, m, n - 1, i - 1, nr, nz);
-      const double xu = start_value(k, phi, cand, m, n + 1, i + 1, nr, nz);
-      const double xo = start_value(k, phi, cand, m + 1, n, i + nz1, nr, nz);
-      double a = az * (2.0 * xi - xl - xu) + ar * (xi - xo);
-      if (m > 0) a += arm * (xi - start_value(k, phi, cand, m - 1, n, i - nz1, nr, nz));
+      const double xi = start_value(k, phi, cand, true, i);
+      double a = 0.0;
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        if (c[d] == 0.0) continue;
+        const int mm = m + dm[d], nn2 = n + dn[d];
+        a += c[d] * (xi - start_value(k, phi, cand, free_node(W, mm, nn2), mm * nz1 + nn2));
+      }
       const double r = Q[i] - a;
       loc[k] += r * r;
     }
@@ -738,16 +930,15 @@ __global__ void k_guess_pick(const double* partial, int nblk, UDev* ud, const in
   }
 }
 
-__global__ void k_guess_apply(int nr, int nz, double* phi, const double* cand, const UDev* ud) {
+__global__ void k_guess_apply(PoissonWork W, double* phi, const double* cand, const UDev* ud) {
   const int choice = ud->choice;
   if (choice == 0) return;
-  const int nz1 = nz + 1;
-  const long long nfree = (long long)nr * (nz - 1);
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nfree;
+  const int nz1 = W.nz + 1;
+  const long long nn = (long long)(W.nr + 1) * nz1;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn;
        e += (long long)gridDim.x * blockDim.x) {
-    const int m = (int)(e / (nz - 1)), n = 1 + (int)(e - (long long)m * (nz - 1));
-    const int i = m * nz1 + n;
-    phi[i] = choice == 1 ? cand[i] : 0.0;
+    const int m = (int)(e / nz1), n = (int)(e - (long long)m * nz1);
+    if (free_node(W, m, n)) phi[e] = choice == 1 ? cand[e] : 0.0;
   }
 }
 
@@ -755,18 +946,20 @@ __global__ void k_guess_apply(int nr, int nz, double* phi, const double* cand, c
 __global__ void k_residual32(PoissonWork W, const double* Q, const double* phi, float* res) {
   const int nr = W.nr, nz = W.nz, nz1 = nz + 1;
   const long long nn = (long long)(nr + 1) * nz1;
+  const int off[4] = {-nz1, nz1, -1, 1};
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nn;
        i += (long long)gridDim.x * blockDim.x) {
     const int m = (int)(i / nz1), n = (int)(i - (long long)m * nz1);
-    if (!free_node(m, n, nr, nz)) {
+    if (!free_node(W, m, n)) {
       res[i] = 0.0f;
       continue;
     }
-    double az, ar, azm = 0.0, arm = 0.0;
-    fine_coef(W, m, az, ar);
-    if (m > 0) fine_coef(W, m - 1, azm, arm);
-    double a = az * (2.0 * phi[i] - phi[i - 1] - phi[i + 1]) + ar * (phi[i] - phi[i + nz1]);
-    if (m > 0) a += arm * (phi[i] - phi[i - nz1]);
+    double c[4];
+    node_coup(W, m, n, c);
+    double a = 0.0;
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+      if (c[d] != 0.0) a += c[d] * (phi[i] - phi[i + off[d]]);
     res[i] = (float)(Q[i] - a);
   }
 }
@@ -774,24 +967,28 @@ __global__ void k_residual32(PoissonWork W, const double* Q, const double* phi, 
 // one colour of a red-black Gauss-Seidel sweep on A x = Q
 __global__ void k_gs_color(PoissonWork W, const double* Q, double* x, int color) {
   const int nr = W.nr, nz = W.nz, nz1 = nz + 1;
-  const long long nfree = (long long)nr * (nz - 1);
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nfree;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int m = (int)(e / (nz - 1)), n = 1 + (int)(e - (long long)m * (nz - 1));
-    if (((m + n) & 1) != color) continue;
-    const int i = m * nz1 + n;
-    double az, ar, azm = 0.0, arm = 0.0;
-    fine_coef(W, m, az, ar);
-    if (m > 0) fine_coef(W, m - 1, azm, arm);
-    double s = Q[i] + az * (x[i - 1] + x[i + 1]) + ar * x[i + nz1];
-    if (m > 0) s += arm * x[i - nz1];
-    x[i] = s / (2.0 * az + ar + arm);
+  const long long nn = (long long)(nr + 1) * nz1;
+  const int off[4] = {-nz1, nz1, -1, 1};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nn;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(i / nz1), n = (int)(i - (long long)m * nz1);
+    if (((m + n) & 1) != color || !free_node(W, m, n)) continue;
+    double c[4];
+    node_coup(W, m, n, c);
+    double s = Q[i], d = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (c[k] != 0.0) {
+        s += c[k] * x[i + off[k]];
+        d += c[k];
+      }
+    x[i] = s / d;
   }
 }
 
 int guess_blocks(int nr, int nz) {
-  const long long nfree = (long long)nr * (nz - 1);
-  long long b = (nfree + 255) / 256;
+  const long long nn = (long long)(nr + 1) * (nz + 1);
+  long long b = (nn + 255) / 256;
   if (b > 592) b = 592;
   if (b < 1) b = 1;
   return (int)b;
@@ -821,7 +1018,7 @@ cudaError_t launch_guess_select(PoissonWork* pw, const double* Q, double* phi, c
                                 cudaStream_t st) {
   k_guess_norms<<<nblk, 256, 0, st>>>(*pw, Q, phi, cand, partial);
   k_guess_pick<<<1, 32, 0, st>>>(partial, nblk, ud, status);
-  k_guess_apply<<<nblk, 256, 0, st>>>(pw->nr, pw->nz, phi, cand, ud);
+  k_guess_apply<<<nblk, 256, 0, st>>>(*pw, phi, cand, ud);
   return cudaGetLastError();
 }
 
@@ -847,9 +1044,10 @@ static int poisson_blocks(const PoissonWork& w, int num_sms) {
   return (int)want;
 }
 
-PoissonWork* poisson_work_init(void* base, int nr, int nz, double R, double L, int num_sms) {
+PoissonWork* poisson_work_init(void* base, int nr, int nz, double R, double L, int g, int wall,
+                               int num_sms) {
   PoissonWork* pw = new PoissonWork();
-  layout(*pw, base, nr, nz, R, L);
+  layout(*pw, base, nr, nz, R, L, g, wall);
   pw->nblocks = poisson_blocks(*pw, num_sms);
   return pw;
 }
@@ -932,12 +1130,12 @@ cudaError_t launch_poisson_group(PoissonWork* const* pws, const Inst* insts, int
 // struct on the host stack (no host or device allocation), over the caller's
 // scratch at `base`.  The layout is the one poisson_work_bytes() sizes.
 // ----------------------------------------------------------------------------
-cudaError_t launch_poisson_in_place(void* base, int nr, int nz, double R, double L, int num_sms,
-                                    const double* Q, double* phi, double tol, int max_iter,
-                                    int* status_dev, int* iters_dev, double* resid_dev,
-                                    cudaStream_t st) {
+cudaError_t launch_poisson_in_place(void* base, int nr, int nz, double R, double L, int g, int wall,
+                                    int num_sms, const double* Q, double* phi, double tol,
+                                    int max_iter, int* status_dev, int* iters_dev,
+                                    double* resid_dev, cudaStream_t st) {
   PoissonWork w;
-  layout(w, base, nr, nz, R, L);
+  layout(w, base, nr, nz, R, L, g, wall);
   w.nblocks = poisson_blocks(w, num_sms);
   return launch_poisson(&w, Q, phi, tol, max_iter, status_dev, iters_dev, resid_dev, st);
 }

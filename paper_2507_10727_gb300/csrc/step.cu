@@ -37,8 +37,9 @@ constexpr int kPZ = 2 * kTile + 2 * kHalo + 1;   // patch nodes in z (two tiles 
 //  E_r(lower), E_z(inner r edge), E_z(outer) - E_z(inner)}; with volume
 //  weighting the E_r entries are divided by r_{m+1/2} (dS/dr = 2r / (r_{m+1}^2
 //  - r_m^2) gives E_r a factor r / r_{m+1/2}).
-//  MC-PIC: nodal E (mean of the adjacent edges, one-sided on walls, E_r = 0
-//  on the axis) in bilinear coefficient form in the deposit's weights.
+//  MC-PIC: nodal E (mean of the adjacent edges, one-sided on conducting
+//  walls, no normal component on insulating ones, E_r = 0 on the axis) in
+//  bilinear coefficient form in the deposit's weights.
 // Field energy (diagnostic): 1/2 sum over edges of a_e (delta phi)^2.
 // ---------------------------------------------------------------------------
 __global__ void k_field_tables(Inst I) {
@@ -75,10 +76,14 @@ __global__ void k_field_tables(Inst I) {
           const int mm = m + a, nn = n + b;
           double e;
           if (mm == 0) e = 0.0;
-          else if (mm == I.nr) e = -(ph[mm * nz1 + nn] - ph[(mm - 1) * nz1 + nn]) * I.inv_dr;
+          else if (mm == I.nr)
+            e = I.bc_wall ? 0.0 : -(ph[mm * nz1 + nn] - ph[(mm - 1) * nz1 + nn]) * I.inv_dr;
           else e = -(ph[(mm + 1) * nz1 + nn] - ph[(mm - 1) * nz1 + nn]) * (0.5 * I.inv_dr);
           er[a][b] = e;
-          if (nn == 0) e = -(ph[mm * nz1 + 1] - ph[mm * nz1]) * I.inv_dz;
+          if (nn == 0)
+            e = field_free(mm, 0, I.nr, I.nz, I.bc_g, I.bc_wall)
+                    ? 0.0
+                    : -(ph[mm * nz1 + 1] - ph[mm * nz1]) * I.inv_dz;
           else if (nn == I.nz) e = -(ph[mm * nz1 + nn] - ph[mm * nz1 + nn - 1]) * I.inv_dz;
           else e = -(ph[mm * nz1 + nn + 1] - ph[mm * nz1 + nn - 1]) * (0.5 * I.inv_dz);
           ez[a][b] = e;

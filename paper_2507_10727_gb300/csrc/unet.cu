@@ -638,15 +638,18 @@ __global__ void k_pack_input(const float* xs, int B, int H, int W, bf16* x_in) {
   }
 }
 
-__device__ __forceinline__ bool dirichlet_node(int m, int n, int nr, int nz) {
-  return n == 0 || n == nz || m == nr;
+// conductor nodes (Dirichlet values) of the field boundary; g, wall as in
+// field_free
+__device__ __forceinline__ bool dirichlet_node(int m, int n, int nr, int nz, int g, int wall) {
+  return !field_free(m, n, nr, nz, g, wall);
 }
 
 // training batch: B snapshots drawn by hash of (seed, iteration, b).
 // Slot fields: mode 0 (rho, phi), mode 1 (res, phi - phi_prev).
 __global__ void k_train_input(const float* f0, const float* f1, const float* slot_scale,
                               long long avail, int B, unsigned long long seed, long long iter,
-                              int nr, int nz, int mode, const UDev* ud, bf16* x_in, float* y) {
+                              int nr, int nz, int g, int wall, int mode, const UDev* ud,
+                              bf16* x_in, float* y) {
   const int W = nz + 1;
   const long long npx = (long long)(nr + 1) * W, total = (long long)B * npx;
   const double K = ud->out_norm / ud->in_norm;
@@ -658,7 +661,7 @@ __global__ void k_train_input(const float* f0, const float* f1, const float* slo
     const long long slot = (long long)(hsh % (unsigned long long)avail);
     const int m = (int)(q / W), n = (int)(q - (long long)m * W);
     const float a = f0[slot * npx + q], t = f1[slot * npx + q];
-    const bool dir = dirichlet_node(m, n, nr, nz);
+    const bool dir = dirichlet_node(m, n, nr, nz, g, wall);
     // mode 0: global scales; mode 1: the snapshot's own residual RMS
     const double sc = mode == 0 ? 1.0 : (double)slot_scale[slot];
     const float inv_in = (float)(1.0 / (mode == 0 ? ud->in_norm : sc));
@@ -686,7 +689,7 @@ __global__ void k_step_input(Inst I, const UDev* ud, int mode, const float* res,
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
        q += (long long)gridDim.x * blockDim.x) {
     const int m = (int)(q / W), n = (int)(q - (long long)m * W);
-    const bool dir = dirichlet_node(m, n, I.nr, I.nz);
+    const bool dir = dirichlet_node(m, n, I.nr, I.nz, I.bc_g, I.bc_wall);
     float v[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) v[c] = 0.0f;
@@ -704,15 +707,15 @@ __global__ void k_step_input(Inst I, const UDev* ud, int mode, const float* res,
 }
 
 // candidate start from the network output (Dirichlet values of phi)
-__global__ void k_make_cand(int nr, int nz, const double* phi, const float* net, const UDev* ud,
-                            int mode, double* cand) {
+__global__ void k_make_cand(int nr, int nz, int g, int wall, const double* phi, const float* net,
+                            const UDev* ud, int mode, double* cand) {
   const int W = nz + 1;
   const long long npx = (long long)(nr + 1) * W;
   const double s = mode == 0 ? ud->out_norm : ud->cur_scale * (ud->out_norm / ud->in_norm);
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
        q += (long long)gridDim.x * blockDim.x) {
     const int m = (int)(q / W), n = (int)(q - (long long)m * W);
-    if (dirichlet_node(m, n, nr, nz)) cand[q] = phi[q];
+    if (dirichlet_node(m, n, nr, nz, g, wall)) cand[q] = phi[q];
     else cand[q] = (mode == 0 ? 0.0 : phi[q]) + s * (double)net[q];
   }
 }
@@ -932,6 +935,7 @@ struct UNet {
   float* slot_scale = nullptr;  // mode 1: residual RMS of each snapshot
   long long snap_cap = 0;
   int snap_every = 1;
+  int bc_g = 0, bc_wall = 0;   // insulating boundary nodes (field_free), set at creation
   bool warm = false;
   long long adam_t = 0;
   UAllocFn alloc = nullptr;
@@ -1188,6 +1192,7 @@ UNet* unet_create(int nr, int nz, int bmax, int mode, unsigned long long seed, d
   u->nz = nz;
   u->bmax = bmax;
   u->v_ref = v_ref > 0.0 ? v_ref : 1.0;
+  u->bc_g = nr + 1;
   u->alloc = alloc;
   u->actx = ctx;
   for (int l = 0; l < kLev; ++l) {
@@ -1320,6 +1325,11 @@ UNet* unet_create(int nr, int nz, int bmax, int mode, unsigned long long seed, d
 }
 
 void unet_destroy(UNet* u) { delete u; }
+void unet_set_boundary(UNet* u, int g, int wall) {
+  u->bc_g = g;
+  u->bc_wall = wall ? 1 : 0;
+}
+
 int unet_mode(const UNet* u) { return u->mode; }
 int unet_bmax(const UNet* u) { return u->bmax; }
 UDev* unet_dev(UNet* u) { return u->ud; }
@@ -1401,7 +1411,8 @@ cudaError_t launch_pre_solve(UNet* u, const Inst& I, PoissonWork* pw, cudaStream
   k_step_input<<<g0, 256, 0, st>>>(I, u->ud, u->mode, u->res, u->x_in);
   e = forward(u, 1, st);
   if (e) return e;
-  k_make_cand<<<g0, 256, 0, st>>>(u->nr, u->nz, I.phi, u->out, u->ud, u->mode, u->cand);
+  k_make_cand<<<g0, 256, 0, st>>>(u->nr, u->nz, I.bc_g, I.bc_wall, I.phi, u->out, u->ud, u->mode,
+                                  u->cand);
   e = launch_gs_sweeps(pw, I.Q, u->cand, 2, st);
   if (e) return e;
   return launch_guess_select(pw, I.Q, I.phi, u->cand, u->gpart, u->gblk, u->ud, &I.S->status, st);
@@ -1448,8 +1459,8 @@ cudaError_t unet_train(UNet* u, int iters, int batch, float lr, unsigned long lo
   const long long n0 = (long long)batch * u->npx(0);
   for (int it = 0; it < iters && e == cudaSuccess; ++it) {
     k_train_input<<<grid1(n0, 256), 256, 0, st>>>(u->snap_f0, u->snap_f1, u->slot_scale, avail,
-                                                  batch, seed, it, u->nr, u->nz, u->mode, u->ud,
-                                                  u->x_in, u->y);
+                                                  batch, seed, it, u->nr, u->nz, u->bc_g,
+                                                  u->bc_wall, u->mode, u->ud, u->x_in, u->y);
     e = forward(u, batch, st);
     if (e == cudaSuccess) e = backward(u, batch, u->d_loss + it, st);
     if (e != cudaSuccess) break;

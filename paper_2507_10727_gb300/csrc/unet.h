@@ -51,6 +51,9 @@ long long unet_param_count();
 UNet* unet_create(int nr, int nz, int bmax, int mode, unsigned long long seed, double v_ref,
                   UAllocFn alloc, void* ctx, cudaStream_t st);
 int unet_mode(const UNet* u);
+// insulating boundary nodes of the field (field_free's g and wall): they are
+// unknowns of the solve, not Dirichlet inputs of the network
+void unet_set_boundary(UNet* u, int g, int wall);
 void unet_destroy(UNet* u);
 int unet_bmax(const UNet* u);
 UDev* unet_dev(UNet* u);

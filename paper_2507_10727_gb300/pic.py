@@ -53,6 +53,7 @@ class PicConfig(C.Structure):
         ("cap_e", C.c_int64), ("cap_i", C.c_int64), ("birth_cap", C.c_int64),
         ("diag_every", C.c_int32), ("sort_every", C.c_int32),
         ("n_meta", C.c_double), ("meta_a", C.c_double), ("meta_I", C.c_double),
+        ("gap_neumann", C.c_int32), ("wall_neumann", C.c_int32),
     ]
 
     @classmethod
@@ -154,6 +155,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         L.pic_poisson_workspace_bytes.restype = C.c_size_t
         L.pic_poisson_solve.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                         C.c_int, vp, vp, vp, vp, C.POINTER(C.c_int), _D]
+        L.pic_poisson_solve_mixed.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
+                                              C.c_int, C.c_double, C.c_int, vp, vp, vp, vp,
+                                              C.POINTER(C.c_int), _D]
         _lib = L
     return _lib
 
@@ -375,16 +379,25 @@ def pic_poisson_workspace_bytes(nr: int, nz: int) -> int:
 
 
 def pic_poisson_solve(nr: int, nz: int, R: float, L: float, tol: float, max_iter: int, Q, phi,
-                      work=None, stream=None):
-    """Solve in place on CUDA tensors Q, phi ((nr+1) x (nz+1) float64)."""
+                      work=None, stream=None, first_insulating_z0=None, wall_insulating=0):
+    """Solve in place on CUDA tensors Q, phi ((nr+1) x (nz+1) float64).  With
+    ``first_insulating_z0`` or ``wall_insulating`` set, pic_poisson_solve_mixed
+    (insulating boundary parts) is called."""
     torch = _torch()
     if work is None:
         work = torch.empty(pic_poisson_workspace_bytes(nr, nz), dtype=torch.uint8, device=Q.device)
     it = C.c_int()
     res = C.c_double()
-    rc = load_library().pic_poisson_solve(nr, nz, R, L, tol, max_iter, Q.data_ptr(), phi.data_ptr(),
-                                          work.data_ptr(), _stream_ptr(stream), C.byref(it),
-                                          C.byref(res))
+    if first_insulating_z0 is None and not wall_insulating:
+        rc = load_library().pic_poisson_solve(nr, nz, R, L, tol, max_iter, Q.data_ptr(),
+                                              phi.data_ptr(), work.data_ptr(), _stream_ptr(stream),
+                                              C.byref(it), C.byref(res))
+    else:
+        g = nr + 1 if first_insulating_z0 is None else first_insulating_z0
+        rc = load_library().pic_poisson_solve_mixed(nr, nz, R, L, g, int(wall_insulating), tol,
+                                                    max_iter, Q.data_ptr(), phi.data_ptr(),
+                                                    work.data_ptr(), _stream_ptr(stream),
+                                                    C.byref(it), C.byref(res))
     if rc != PIC_OK and rc != -4:
         raise PicError(rc, "pic_poisson_solve failed")
     return rc, it.value, res.value

@@ -106,6 +106,24 @@ def params_rz256x512(gather: int = 0, precision: int = 0, seed: int = 0) -> dict
     return p
 
 
+def params_paper(gather: int = 0, precision: int = 0, seed: int = 0, cells: int = 256,
+                 gamma_i: float = 0.1, Rext: float = 3000.0) -> dict:
+    """The paper's chamber (Section 3): 3 cm x 3 cm, cathode r <= 0.85 L_r on
+    z = 0, the rest of z = 0 the insulating block (Neumann), anode z = L and
+    wall r = R grounded, 10 mTorr, V_ext = -300 V through R_ext (3000 or
+    1000 Ohm), ion SEY 0.1 / 0.2, electron SEY 0.1, Ar* background
+    2.5e17 m^-3.  The magnet field stand-in puts the racetrack (B_z = 0) at
+    r = 1.2 cm (k r = 2.405), between the paper's inner magnet (6.5 mm) and
+    outer magnet (1.7 cm).  `cells` x `cells` grid; 20 ps steps."""
+    p = base_params()
+    p.update(nr=cells, nz=cells, R=0.03, L=0.03, Rc=0.85 * 0.03, dt=2e-11,
+             n_gas=gas_density(10.0, 300.0), gap_neumann=1, wall_neumann=0,
+             circuit_mode=1, Vc_fixed=-300.0, Vs=300.0, Rext=Rext, n_avg=100,
+             gamma_i=gamma_i, gamma_e=0.1, n_meta=2.5e17, B_k=2.405 / 0.012,
+             E_cap=600.0, gather=gather, precision=precision, seed=seed)
+    return p
+
+
 def params_rz128_sweep(gather: int = 0, precision: int = 0, seed: int = 0) -> list[dict]:
     """16 independent 128 x 128 discharges: gamma in {.05,.1,.2,.3} x R_ext in {50,100,200,400} Ohm."""
     out = []

@@ -206,3 +206,15 @@ def test_fp32_reweight_keeps_the_oracles_particles(pg):
     _check(pg, h, orc)
     assert pg.pic_diagnostics(h, 0)["weight"] == orc.weight == 3 * p["weight"]
     pg.pic_destroy(h)
+
+
+def test_fp32_insulating_block(pg):
+    p = pic_inputs.params_rz32()
+    p.update(gap_neumann=1, wall_neumann=1, Rc=0.6 * p["R"], gamma_i=0.3, poisson_tol=1e-12,
+             circuit_mode=1, Vs=400.0, Rext=100.0, n_avg=3)
+    p, parts = busy_state(p, ppc=16, seed=57)
+    p, orc, h = _pair32(pg, p, parts)
+    orc.step(1)
+    pg.pic_step(h, 1)
+    _check(pg, h, orc)
+    pg.pic_destroy(h)

@@ -344,3 +344,62 @@ def test_reweight_factor_checks_and_graph(pg):
             assert pg.pic_uses_graph(h) == 1
             _check_step(pg, h, orc)
         pg.pic_destroy(h)
+
+
+@pytest.mark.parametrize("nr,nz,gap,wall", [(32, 32, 1, 0), (32, 32, 1, 1), (48, 20, 0, 1),
+                                            (128, 128, 1, 1), (256, 256, 1, 0)])
+def test_poisson_insulating_boundaries(pg, nr, nz, gap, wall):
+    """Standalone solve with the insulating block (Section 3: Neumann) on
+    z = 0 outside the cathode and / or on the wall r = R, against the oracle's
+    direct solve of the same finite-volume system."""
+    import torch
+    p = pic_inputs.params_rz256()
+    p.update(nr=nr, nz=nz, R=0.05, L=0.05 * nz / nr, Rc=0.6 * 0.05, gap_neumann=gap,
+             wall_neumann=wall)
+    rng = np.random.default_rng(nr + 3 * nz + gap + 2 * wall)
+    V = oracle.node_volume(p)
+    rho = rng.normal(size=(nr + 1, nz + 1)) * 1e-6
+    bc = np.zeros_like(rho)
+    dr = p["R"] / nr
+    mc = [m for m in range(nr) if m * dr <= p["Rc"]]
+    bc[mc, 0] = -321.0
+    bc[:, nz] = 5.0 * rng.random(nr + 1)
+    bc[nr, :] = 2.0
+    phi_o = oracle.poisson(p, rho, bc)
+    g = len(mc) if gap else nr + 1
+    Q = torch.tensor(rho * V, device="cuda")
+    phi = torch.tensor(bc, device="cuda")
+    rc, it, res = pg.pic_poisson_solve(nr, nz, p["R"], p["L"], 1e-13, 500, Q, phi,
+                                       first_insulating_z0=g, wall_insulating=wall)
+    torch.cuda.synchronize()
+    assert rc == 0 and res <= 1e-13, (rc, it, res)
+    out = phi.cpu().numpy()
+    assert field_err(out, phi_o) <= FIELD_TOL
+    # conductor nodes untouched; insulating nodes solved (they differ from bc)
+    assert np.array_equal(out[mc, 0], bc[mc, 0]) and np.array_equal(out[:, nz], bc[:, nz])
+    if gap:
+        assert not np.array_equal(out[len(mc):nr, 0], bc[len(mc):nr, 0])
+    if wall:
+        assert not np.array_equal(out[nr, 1:nz], bc[nr, 1:nz])
+    else:
+        assert np.array_equal(out[nr, :], bc[nr, :])
+
+
+@pytest.mark.parametrize("gather", [0, 1])
+@pytest.mark.parametrize("wall", [0, 1])
+def test_insulating_block_steps_match_oracle(pg, gather, wall):
+    """Full steps with the paper's boundary (Section 3): the z = 0 plane beside
+    the cathode insulating (and the wall r = R in the second reading)."""
+    p = pic_inputs.params_rz32(gather=gather)
+    p.update(gap_neumann=1, wall_neumann=wall, Rc=0.6 * p["R"], gamma_i=0.3, gamma_e=0.1,
+             poisson_tol=1e-13, circuit_mode=1, Vs=400.0, Rext=100.0, n_avg=3)
+    p, parts = busy_state(p, ppc=16, seed=51 + gather + 2 * wall)
+    p, orc, h = _pair(pg, p, parts)
+    for _ in range(3):
+        orc.step(1)
+        pg.pic_step(h, 1)
+        _check_step(pg, h, orc)
+    phi = pg.pic_get_fields(h, 0)["phi"]
+    m_gap = int(0.6 * p["nr"]) + 2
+    assert phi[m_gap, 0] != 0.0          # the block floats
+    pg.pic_destroy(h)

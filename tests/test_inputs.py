@@ -37,3 +37,20 @@ def test_grown_ring_state_shape():
     ring = ((r > 0.0115) & (r < 0.0135) & (z > 0.0015) & (z < 0.0025)).sum() / V(0.0115, 0.0135, 0.0015, 0.0025)
     floor = ((r > 0.03) & (r < 0.045) & (z > 0.02) & (z < 0.045)).sum() / V(0.03, 0.045, 0.02, 0.045)
     assert 6.0 < ring / floor < 14.0
+
+
+def test_paper_chamber_preset():
+    """Section 3's chamber: 3 x 3 cm, cathode to 0.85 L_r, the rest of z = 0
+    insulating, 10 mTorr (n = p / k T), V_ext -300 V; the field stand-in's
+    racetrack (B_z = 0) lies between the inner (6.5 mm) and outer (1.7 cm)
+    magnets."""
+    import oracle
+    p = pic_inputs.params_paper()
+    assert p["R"] == p["L"] == 0.03 and p["Rc"] == pytest.approx(0.0255)
+    assert p["gap_neumann"] == 1 and p["wall_neumann"] == 0
+    assert p["n_gas"] == pytest.approx(10e-3 * 133.322368421 / (1.380649e-23 * 300.0))
+    assert p["Vs"] == 300.0 and p["gamma_e"] == 0.1
+    rs = np.linspace(0.0065, 0.017, 2001)
+    bz = np.array([oracle.bfield(p, r, 0.0)[1] for r in rs])
+    r0 = rs[np.argmin(np.abs(bz))]
+    assert 0.0065 < r0 < 0.017 and abs(r0 - 0.012) < 1e-4
