@@ -290,12 +290,15 @@ __device__ __forceinline__ float line_sum(const Lev& L, int m, int n, float& dia
 __device__ __forceinline__ int segs_full(int nz) { return (nz - 1 + 31) >> 5; }
 __device__ __forceinline__ int segs_color(int nz) { return (nz / 2 + 32) >> 5; }
 
+// LINES: the problem has insulating boundary nodes (else the interior loops
+// alone, the all-conductor case)
+template <bool LINES>
 __device__ void smooth(const Lev L, int color, int wid, int nw, int lane) {
   const int ns = segs_color(L.nz), nz1 = L.nz + 1;
   const int items = L.nr * ns;
-  const int ngap = line_gap(L.nr, L.g, L.wall);
-  const int nline = ngap + (L.wall ? L.nz - 1 : 0);
-  const int total = items + ((nline + 31) >> 5);
+  const int ngap = LINES ? line_gap(L.nr, L.g, L.wall) : 0;
+  const int nline = LINES ? ngap + (L.wall ? L.nz - 1 : 0) : 0;
+  const int total = LINES ? items + ((nline + 31) >> 5) : items;
   for (int it = wid; it < total; it += nw) {
     if (it < items) {
       const int m = it / ns, s = it - m * ns;
@@ -306,7 +309,7 @@ __device__ void smooth(const Lev L, int color, int wid, int nw, int lane) {
       float sum = L.f[i] + L.az[m] * (L.u[i - 1] + L.u[i + 1]) + L.ar[m] * L.u[i + nz1];
       if (m > 0) sum += L.ar[m - 1] * L.u[i - nz1];
       L.u[i] = sum * L.idg[m];
-    } else {
+    } else if constexpr (LINES) {
       const int j = (it - items) * 32 + lane;
       if (j >= nline) continue;
       int m, n;
@@ -320,13 +323,18 @@ __device__ void smooth(const Lev L, int color, int wid, int nw, int lane) {
   }
 }
 
+template <bool LINES>
 __device__ __forceinline__ float resid_at(const Lev L, int m, int n) {
   if (m < 0 || m >= L.nr || n < 1 || n >= L.nz) {
-    if (!field_free(m, n, L.nr, L.nz, L.g, L.wall)) return 0.0f;
-    float diag;
-    const float s = line_sum(L, m, n, diag);
-    const int i = m * (L.nz + 1) + n;
-    return L.f[i] - (diag * L.u[i] - s);
+    if constexpr (LINES) {
+      if (!field_free(m, n, L.nr, L.nz, L.g, L.wall)) return 0.0f;
+      float diag;
+      const float s = line_sum(L, m, n, diag);
+      const int i = m * (L.nz + 1) + n;
+      return L.f[i] - (diag * L.u[i] - s);
+    } else {
+      return 0.0f;
+    }
   }
   const int nz1 = L.nz + 1, i = m * nz1 + n;
   const float arm = m > 0 ? L.ar[m - 1] : 0.0f;
@@ -337,15 +345,16 @@ __device__ __forceinline__ float resid_at(const Lev L, int m, int n) {
 }
 
 // coarse f = P^T (fine residual), coarse u = 0
+template <bool LINES>
 __device__ void restrict_to(const Lev F, const Lev C, int wid, int nw, int lane) {
   const int ns = segs_full(C.nz), nz1 = C.nz + 1;
   const int items = C.nr * ns;
-  const int ngap = line_gap(C.nr, C.g, C.wall);
-  const int nline = ngap + (C.wall ? C.nz - 1 : 0);
-  const int total = items + ((nline + 31) >> 5);
+  const int ngap = LINES ? line_gap(C.nr, C.g, C.wall) : 0;
+  const int nline = LINES ? ngap + (C.wall ? C.nz - 1 : 0) : 0;
+  const int total = LINES ? items + ((nline + 31) >> 5) : items;
   for (int it = wid; it < total; it += nw) {
     int M, N;
-    if (it < items) {
+    if (!LINES || it < items) {
       M = it / ns;
       N = 1 + (it - M * ns) * 32 + lane;
       if (N > C.nz - 1) continue;
@@ -361,7 +370,7 @@ __device__ void restrict_to(const Lev F, const Lev C, int wid, int nw, int lane)
 #pragma unroll
       for (int dj = -1; dj <= 1; ++dj) {
         const float wj = dj == 0 ? 1.0f : 0.5f;
-        acc += wi * wj * resid_at(F, 2 * M + di, 2 * N + dj);
+        acc += wi * wj * resid_at<LINES>(F, 2 * M + di, 2 * N + dj);
       }
     }
     C.f[M * nz1 + N] = acc;
@@ -370,15 +379,16 @@ __device__ void restrict_to(const Lev F, const Lev C, int wid, int nw, int lane)
 }
 
 // fine u += bilinear interpolation of coarse u (zero on coarse Dirichlet nodes)
+template <bool LINES>
 __device__ void prolong_from(const Lev F, const Lev C, int wid, int nw, int lane) {
   const int ns = segs_full(F.nz), fz1 = F.nz + 1, cz1 = C.nz + 1;
   const int items = F.nr * ns;
-  const int ngap = line_gap(F.nr, F.g, F.wall);
-  const int nline = ngap + (F.wall ? F.nz - 1 : 0);
-  const int total = items + ((nline + 31) >> 5);
+  const int ngap = LINES ? line_gap(F.nr, F.g, F.wall) : 0;
+  const int nline = LINES ? ngap + (F.wall ? F.nz - 1 : 0) : 0;
+  const int total = LINES ? items + ((nline + 31) >> 5) : items;
   for (int it = wid; it < total; it += nw) {
     int m, n;
-    if (it < items) {
+    if (!LINES || it < items) {
       m = it / ns;
       n = 1 + (it - m * ns) * 32 + lane;
       if (n > F.nz - 1) continue;
@@ -412,6 +422,7 @@ __device__ __forceinline__ Lev tail_lev(const PoissonWork& W, const Tables& T, i
   return lev(W, T, l, buf + off, buf + off + nn);
 }
 
+template <bool LINES>
 __device__ void vcycle_tail(const PoissonWork& W, const Tables& T, int l0, float* buf) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int k = threadIdx.x; k < W.tail_floats; k += blockDim.x) buf[k] = 0.0f;
@@ -434,37 +445,37 @@ __device__ void vcycle_tail(const PoissonWork& W, const Tables& T, int l0, float
   __syncthreads();
   for (int l = l0; l < W.nlev - 1; ++l) {
     const Lev F = tail_lev(W, T, l0, l, buf), C = tail_lev(W, T, l0, l + 1, buf);
-    smooth(F, 0, wid, nw, lane);
+    smooth<LINES>(F, 0, wid, nw, lane);
     __syncthreads();
-    smooth(F, 1, wid, nw, lane);
+    smooth<LINES>(F, 1, wid, nw, lane);
     __syncthreads();
-    restrict_to(F, C, wid, nw, lane);
+    restrict_to<LINES>(F, C, wid, nw, lane);
     __syncthreads();
   }
   if (wid == 0) {
     // coarsest level: one warp, symmetric Gauss-Seidel sweeps
     const Lev C = tail_lev(W, T, l0, W.nlev - 1, buf);
     for (int s = 0; s < kCoarseSweeps; ++s) {
-      smooth(C, 0, 0, 1, lane);
+      smooth<LINES>(C, 0, 0, 1, lane);
       __syncwarp();
-      smooth(C, 1, 0, 1, lane);
+      smooth<LINES>(C, 1, 0, 1, lane);
       __syncwarp();
     }
     for (int s = 0; s < kCoarseSweeps; ++s) {
-      smooth(C, 1, 0, 1, lane);
+      smooth<LINES>(C, 1, 0, 1, lane);
       __syncwarp();
-      smooth(C, 0, 0, 1, lane);
+      smooth<LINES>(C, 0, 0, 1, lane);
       __syncwarp();
     }
   }
   __syncthreads();
   for (int l = W.nlev - 2; l >= l0; --l) {
     const Lev F = tail_lev(W, T, l0, l, buf), C = tail_lev(W, T, l0, l + 1, buf);
-    prolong_from(F, C, wid, nw, lane);
+    prolong_from<LINES>(F, C, wid, nw, lane);
     __syncthreads();
-    smooth(F, 1, wid, nw, lane);
+    smooth<LINES>(F, 1, wid, nw, lane);
     __syncthreads();
-    smooth(F, 0, wid, nw, lane);
+    smooth<LINES>(F, 0, wid, nw, lane);
     __syncthreads();
   }
   {
@@ -569,6 +580,7 @@ __device__ __forceinline__ float line_diag(const Lev& L, int m, int n) {
 // One solve per block group: `group` == nullptr -> the whole grid solves A0;
 // otherwise block b works on group[b / bpi] with bpi blocks per solve (the
 // ensemble's discharges solved side by side in one launch).
+template <bool LINES>
 __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const PoissonArgs* group,
                                                           int bpi) {
   __shared__ PoissonArgs sA;
@@ -601,14 +613,15 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
   const int items0 = nr * nsf;
   // insulating boundary nodes follow the interior rows as extra warp items
   const int g0 = W.bc_g[0], wall = W.bc_wall;
-  const int ngap0 = line_gap(nr, g0, wall);
-  const int nline0 = ngap0 + (wall ? nz - 1 : 0);
-  const int itemsT = items0 + ((nline0 + 31) >> 5);
+  const int ngap0 = LINES ? line_gap(nr, g0, wall) : 0;
+  const int nline0 = LINES ? ngap0 + (wall ? nz - 1 : 0) : 0;
+  const int itemsT = LINES ? items0 + ((nline0 + 31) >> 5) : items0;
+  auto interior = [&](int it) -> bool { return !LINES || it < items0; };
   const long long nfree = (long long)nr * (nz - 1) + nline0;
   double* phi = A.phi;
   // node of warp item `it` for this lane; false when the lane has none
   auto node_of = [&](int it, int& m, int& n) -> bool {
-    if (it < items0) {
+    if (interior(it)) {
       m = it / nsf;
       n = 1 + (it - m * nsf) * 32 + lane;
       return n <= nz - 1;
@@ -653,10 +666,10 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
     if (!node_of(it, m, n)) continue;
     const int i = m * nz1 + n;
     double b = A.Q[i], a;
-    if (it < items0) {
-      if (n == 1 && !field_free(m, 0, nr, nz, g0, wall)) b += az0[m] * phi[i - 1];
+    if (interior(it)) {
+      if (n == 1 && (!LINES || !field_free(m, 0, nr, nz, g0, wall))) b += az0[m] * phi[i - 1];
       if (n == nz - 1) b += az0[m] * phi[i + 1];
-      if (m == nr - 1 && !wall) b += ar0[m] * phi[i + nz1];
+      if (m == nr - 1 && (!LINES || !wall)) b += ar0[m] * phi[i + nz1];
       a = apply64(T, phi, m, i, nz1);
     } else {
       a = line_apply64(T, phi, m, n, nr, nz, g0, wall, false, &b);
@@ -694,7 +707,7 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
       const int i = m * nz1 + n;
       const float f = (float)(W.r[i] * scale);
       L0.f[i] = f;
-      const float idg = itm < items0 ? L0.idg[m] : 1.0f / line_diag(L0, m, n);
+      const float idg = interior(itm) ? L0.idg[m] : 1.0f / line_diag(L0, m, n);
       L0.u[i] = ((m + n) & 1) == 0 ? f * idg : 0.0f;
     }
     if (!barrier_grid(W.bar, A.status, nb)) return;
@@ -705,24 +718,24 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
       const Lev F = lev(W, T, l, W.u[l], W.f[l]);
       const Lev C = lev(W, T, l + 1, W.u[l + 1], W.f[l + 1]);
       if (l > 0) {
-        smooth(F, 0, gw, ngw, lane);
+        smooth<LINES>(F, 0, gw, ngw, lane);
         if (!barrier_grid(W.bar, A.status, nb)) return;
       }
-      smooth(F, 1, gw, ngw, lane);
+      smooth<LINES>(F, 1, gw, ngw, lane);
       if (!barrier_grid(W.bar, A.status, nb)) return;
-      restrict_to(F, C, gw, ngw, lane);
+      restrict_to<LINES>(F, C, gw, ngw, lane);
       if (!barrier_grid(W.bar, A.status, nb)) return;
     }
-    if (lb == 0) vcycle_tail(W, T, W.tail, tailbuf);
+    if (lb == 0) vcycle_tail<LINES>(W, T, W.tail, tailbuf);
     if (!barrier_grid(W.bar, A.status, nb)) return;
     for (int l = W.tail - 1; l >= 0; --l) {
       const Lev F = lev(W, T, l, W.u[l], W.f[l]);
       const Lev C = lev(W, T, l + 1, W.u[l + 1], W.f[l + 1]);
-      prolong_from(F, C, gw, ngw, lane);
+      prolong_from<LINES>(F, C, gw, ngw, lane);
       if (!barrier_grid(W.bar, A.status, nb)) return;
-      smooth(F, 1, gw, ngw, lane);
+      smooth<LINES>(F, 1, gw, ngw, lane);
       if (!barrier_grid(W.bar, A.status, nb)) return;
-      smooth(F, 0, gw, ngw, lane);
+      smooth<LINES>(F, 0, gw, ngw, lane);
       if (!barrier_grid(W.bar, A.status, nb)) return;
     }
     // ---- z = M^{-1} r, r.z and z.q_old ------------------------------------
@@ -753,10 +766,10 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
       const int i = m * nz1 + n;
       const double zi = W.z[i];
       double a;
-      if (itm < items0) {
-        const double zl = (n > 1 || m >= g0) ? W.z[i - 1] : 0.0;
+      if (interior(itm)) {
+        const double zl = (n > 1 || (LINES && m >= g0)) ? W.z[i - 1] : 0.0;
         const double zu = n < nz - 1 ? W.z[i + 1] : 0.0;
-        const double zo = (m < nr - 1 || wall) ? W.z[i + nz1] : 0.0;
+        const double zo = (m < nr - 1 || (LINES && wall)) ? W.z[i + nz1] : 0.0;
         a = az0[m] * (2.0 * zi - zl - zu) + ar0[m] * (zi - zo);
         if (m > 0) a += ar0[m - 1] * (zi - W.z[i - nz1]);
       } else {
@@ -786,7 +799,7 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
       rl += r * r;
       const float f = (float)(r * scale);
       L0.f[i] = f;
-      const float idg = itm < items0 ? L0.idg[m] : 1.0f / line_diag(L0, m, n);
+      const float idg = interior(itm) ? L0.idg[m] : 1.0f / line_diag(L0, m, n);
       L0.u[i] = ((m + n) & 1) == 0 ? f * idg : 0.0f;
     }
     vals[0] = rl;
@@ -803,7 +816,7 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
         int m, n;
         if (!node_of(itm, m, n)) continue;
         const int i = m * nz1 + n;
-        const double a = itm < items0
+        const double a = interior(itm)
                              ? apply64(T, phi, m, i, nz1)
                              : line_apply64(T, phi, m, n, nr, nz, g0, wall, false, nullptr);
         const double r = A.Q[i] - a;
@@ -811,7 +824,7 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
         rt += r * r;
         const float f = (float)(r * scale);
         L0.f[i] = f;
-        const float idg = itm < items0 ? L0.idg[m] : 1.0f / line_diag(L0, m, n);
+        const float idg = interior(itm) ? L0.idg[m] : 1.0f / line_diag(L0, m, n);
         L0.u[i] = ((m + n) & 1) == 0 ? f * idg : 0.0f;
       }
       vals[0] = rt;
@@ -1025,14 +1038,27 @@ cudaError_t launch_guess_select(PoissonWork* pw, const double* Q, double* phi, c
 // ----------------------------------------------------------------------------
 // host side
 // ----------------------------------------------------------------------------
-static int poisson_blocks(const PoissonWork& w, int num_sms) {
+// the kernel variant of a problem: with insulating boundary nodes or without
+static bool has_lines(const PoissonWork& w) {
+  return line_count(w.nr, w.nz, w.bc_g[0], w.bc_wall) > 0;
+}
+
+static const void* poisson_kernel(bool lines) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_poisson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+    cudaFuncSetAttribute(k_poisson<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kSmemBudget);
+    cudaFuncSetAttribute(k_poisson<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kSmemBudget);
     attr_set = true;
   }
+  return lines ? (const void*)k_poisson<true> : (const void*)k_poisson<false>;
+}
+
+static int poisson_blocks(const PoissonWork& w, int num_sms) {
+  const void* kern = poisson_kernel(has_lines(w));
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_poisson, kPoisThreads, w.smem_bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPoisThreads, w.smem_bytes);
   if (per_sm < 1) per_sm = 1;
   // about one row segment per warp, at most one wave
   const long long items = (long long)w.nr * ((w.nz - 1 + 31) / 32);
@@ -1068,8 +1094,8 @@ cudaError_t launch_poisson(PoissonWork* pw, const double* Q, double* phi, double
   const PoissonArgs* none = nullptr;
   int one = 1;
   void* args[] = {&a, &none, &one};
-  return cudaLaunchCooperativeKernel((const void*)k_poisson, dim3(pw->nblocks), dim3(kPoisThreads),
-                                     args, (size_t)pw->smem_bytes, st);
+  return cudaLaunchCooperativeKernel(poisson_kernel(has_lines(*pw)), dim3(pw->nblocks),
+                                     dim3(kPoisThreads), args, (size_t)pw->smem_bytes, st);
 }
 
 size_t poisson_args_bytes() { return sizeof(PoissonArgs); }
@@ -1101,18 +1127,16 @@ cudaError_t poisson_group_upload(PoissonWork* const* pws, const Inst* insts, int
 cudaError_t launch_poisson_group(PoissonWork* const* pws, const Inst* insts, int n_inst,
                                  void* d_args, int num_sms, cudaStream_t st) {
   (void)insts;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_poisson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
-    attr_set = true;
-  }
   int smem = 0, want = 1;
+  bool lines = false;
   for (int k = 0; k < n_inst; ++k) {
     smem = pws[k]->smem_bytes > smem ? pws[k]->smem_bytes : smem;
     want = pws[k]->nblocks > want ? pws[k]->nblocks : want;
+    lines = lines || has_lines(*pws[k]);
   }
+  const void* kern = poisson_kernel(lines);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_poisson, kPoisThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPoisThreads, smem);
   if (per_sm < 1) per_sm = 1;
   int bpi = (num_sms * per_sm) / n_inst;
   if (bpi > want) bpi = want;
@@ -1121,7 +1145,7 @@ cudaError_t launch_poisson_group(PoissonWork* const* pws, const Inst* insts, int
   std::memset(&a0, 0, sizeof(a0));
   const PoissonArgs* g = (const PoissonArgs*)d_args;
   void* args[] = {&a0, &g, &bpi};
-  return cudaLaunchCooperativeKernel((const void*)k_poisson, dim3(n_inst * bpi), dim3(kPoisThreads),
+  return cudaLaunchCooperativeKernel(kern, dim3(n_inst * bpi), dim3(kPoisThreads),
                                      args, (size_t)smem, st);
 }
 
