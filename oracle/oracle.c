@@ -513,6 +513,13 @@ struct orc_sim {
   double* qhist;
   double nu_max, p_null;
   orc_diag d;
+  /* region diagnostics */
+  int64_t* ied;            /* ied_bins counts */
+  int64_t ied_over;
+  int64_t *rc_n[2];        /* per cell particle counts, summed over samples */
+  double* rc_mom;          /* per cell electron sums: v_r, v_theta, v_z, |v|^2 */
+  double* rc_phi;          /* per node potential, summed over samples */
+  int64_t rc_samples;
 };
 
 static void ps_reserve(pstore* p, int64_t n) {
@@ -559,6 +566,11 @@ orc_sim* orc_create(const orc_config* c) {
   if (chol_build(c, &s->f) != 0) { orc_destroy(s); return NULL; }
   s->Vc = c->circuit_mode == 0 ? c->Vc_fixed : -c->Vs;
   s->qhist = (double*)calloc(c->n_avg > 0 ? c->n_avg : 1, sizeof(double));
+  s->ied = (int64_t*)calloc(c->ied_bins > 0 ? c->ied_bins : 1, sizeof(int64_t));
+  s->rc_n[0] = (int64_t*)calloc((size_t)c->nr * c->nz, sizeof(int64_t));
+  s->rc_n[1] = (int64_t*)calloc((size_t)c->nr * c->nz, sizeof(int64_t));
+  s->rc_mom = (double*)calloc((size_t)c->nr * c->nz * 4, sizeof(double));
+  s->rc_phi = (double*)calloc(nn, sizeof(double));
   s->nu_max = orc_nu_max(c);
   s->p_null = -expm1(-s->nu_max * c->dt);
   return s;
@@ -571,7 +583,9 @@ void orc_destroy(orc_sim* s) {
     free(s->sp[k].vz); free(s->sp[k].id); free(s->Qs[k]);
   }
   free(s->phi); free(s->rho); free(s->Q); free(s->Bnr); free(s->Bnz);
-  chol_free(&s->f); free(s->qhist); free(s);
+  chol_free(&s->f); free(s->qhist);
+  free(s->ied); free(s->rc_n[0]); free(s->rc_n[1]); free(s->rc_mom); free(s->rc_phi);
+  free(s);
 }
 
 int orc_set_particles(orc_sim* s, int sp, int64_t n, const double* r, const double* z,
@@ -849,6 +863,13 @@ int orc_step(orc_sim* s, int64_t nsteps) {
               draws(c, sp, p->id[k], s->step, 2, u);
               double gam = sp == 0 ? c->gamma_e : c->gamma_i;
               if (sp == 1) n_ion_cath++; else n_e_cath++;
+              /* cathode ion energy distribution (Section 7): impacts in the
+               * radial band, energy of the velocity the ion arrives with */
+              if (sp == 1 && c->ied_bins > 0 && rhit >= c->band_r_lo && rhit <= c->band_r_hi) {
+                double E = 0.5 * mass * (vr * vr + vt * vt + vz * vz) / QE;
+                double fb = floor(E / (c->ied_emax / c->ied_bins));
+                if (fb < (double)c->ied_bins) s->ied[(int)fb]++; else s->ied_over++;
+              }
               if (u[0] < gam) {
                 uint64_t key = ((uint64_t)p->id[k] << 2) | (sp == 1 ? 1u : 2u);
                 bl_push(&be, key, rhit, 0.0, 0.0, 0.0, 0.0);
@@ -924,4 +945,111 @@ int orc_step(orc_sim* s, int64_t nsteps) {
     s->step++;
   }
   return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Region diagnostics (Sections 4, 5 and 7).  Section 4 puts the sheath     */
+/* edge where the electron density is half the ion density and the bulk    */
+/* where E_z = d phi / dz vanishes; Section 5 averages the electron         */
+/* temperature, from the second moment of the particle velocities, over    */
+/* each region within 1.0 cm < r < 1.5 cm; Section 7 bins the energies of   */
+/* the ions hitting the cathode in the same radial band.  Readings: the     */
+/* state is accumulated over samples (the paper's steady-state averages);   */
+/* per cell column m (r_m .. r_{m+1}), walking up from the cathode, the     */
+/* sheath ends at the first cell with n_e >= n_i / 2 (2 N_e >= N_i in       */
+/* accumulated counts: same cell volume and weight) and the bulk starts at  */
+/* the first cell from there on whose axial field E_z = -d phi / dz, from   */
+/* the cell's four corner potentials, is >= 0; a cell's temperature is      */
+/* m_e (<|v|^2> - |<v>|^2) / (3 e) over its electron samples (cells with    */
+/* at least two), and a region's temperature the plain mean over its cells  */
+/* whose column centre lies in the band.                                   */
+/* ------------------------------------------------------------------------ */
+void orc_region_sample(orc_sim* s) {
+  const orc_config* c = &s->c;
+  for (int sp = 0; sp < 2; ++sp) {
+    const pstore* p = &s->sp[sp];
+    for (int64_t k = 0; k < p->n; ++k) {
+      int m, n;
+      double f;
+      locate(p->r[k], dr_of(c), c->nr, &m, &f);
+      locate(p->z[k], dz_of(c), c->nz, &n, &f);
+      size_t cell = (size_t)m * c->nz + n;
+      s->rc_n[sp][cell]++;
+      if (sp == 0) {
+        double vr = p->vr[k], vt = p->vt[k], vz = p->vz[k];
+        s->rc_mom[cell * 4 + 0] += vr;
+        s->rc_mom[cell * 4 + 1] += vt;
+        s->rc_mom[cell * 4 + 2] += vz;
+        s->rc_mom[cell * 4 + 3] += vr * vr + vt * vt + vz * vz;
+      }
+    }
+  }
+  size_t nn = (size_t)(c->nr + 1) * (c->nz + 1);
+  for (size_t i = 0; i < nn; ++i) s->rc_phi[i] += s->phi[i];
+  s->rc_samples++;
+}
+
+int orc_region_result(const orc_sim* s, orc_regions* out, double* zs, double* zb) {
+  const orc_config* c = &s->c;
+  memset(out, 0, sizeof(*out));
+  out->samples = s->rc_samples;
+  double dz = dz_of(c), dr = dr_of(c);
+  double tsum[3] = {0.0, 0.0, 0.0};
+  double zs_sum = 0.0, zb_sum = 0.0;
+  int ncol = 0;
+  for (int m = 0; m < c->nr; ++m) {
+    int ns = c->nz, nb = c->nz;
+    for (int n = 0; n < c->nz; ++n) {
+      size_t cell = (size_t)m * c->nz + n;
+      if (2 * s->rc_n[0][cell] >= s->rc_n[1][cell]) { ns = n; break; }
+    }
+    for (int n = ns; n < c->nz; ++n) {
+      /* -dphi/dz >= 0  <=>  upper-face potential sum <= lower-face sum */
+      double up = s->rc_phi[nidx(c, m, n + 1)] + s->rc_phi[nidx(c, m + 1, n + 1)];
+      double lo = s->rc_phi[nidx(c, m, n)] + s->rc_phi[nidx(c, m + 1, n)];
+      if (up - lo <= 0.0) { nb = n; break; }
+    }
+    if (zs) zs[m] = ns * dz;
+    if (zb) zb[m] = nb * dz;
+    double rcen = (m + 0.5) * dr;
+    if (rcen < c->band_r_lo || rcen > c->band_r_hi) continue;
+    ++ncol;
+    zs_sum += ns * dz;
+    zb_sum += nb * dz;
+    for (int n = 0; n < c->nz; ++n) {
+      size_t cell = (size_t)m * c->nz + n;
+      int64_t N = s->rc_n[0][cell];
+      if (N < 2) continue;
+      const double* mo = &s->rc_mom[cell * 4];
+      double mr = mo[0] / N, mt = mo[1] / N, mz = mo[2] / N;
+      double T = ME * (mo[3] / N - (mr * mr + mt * mt + mz * mz)) / (3.0 * QE);
+      int reg = n < ns ? 0 : (n < nb ? 1 : 2);
+      tsum[reg] += T;
+      out->ncell[reg]++;
+    }
+  }
+  for (int k = 0; k < 3; ++k) out->Te[k] = out->ncell[k] > 0 ? tsum[k] / out->ncell[k] : 0.0;
+  out->z_sheath = ncol > 0 ? zs_sum / ncol : 0.0;
+  out->z_bulk = ncol > 0 ? zb_sum / ncol : 0.0;
+  int64_t imp = s->ied_over;
+  for (int b = 0; b < c->ied_bins; ++b) imp += s->ied[b];
+  out->ion_impacts = imp;
+  return 0;
+}
+
+void orc_ied_get(const orc_sim* s, int64_t* hist, int64_t* overflow) {
+  for (int b = 0; b < s->c.ied_bins; ++b) hist[b] = s->ied[b];
+  if (overflow) *overflow = s->ied_over;
+}
+
+void orc_region_reset(orc_sim* s) {
+  const orc_config* c = &s->c;
+  size_t ncell = (size_t)c->nr * c->nz, nn = (size_t)(c->nr + 1) * (c->nz + 1);
+  memset(s->rc_n[0], 0, ncell * sizeof(int64_t));
+  memset(s->rc_n[1], 0, ncell * sizeof(int64_t));
+  memset(s->rc_mom, 0, ncell * 4 * sizeof(double));
+  memset(s->rc_phi, 0, nn * sizeof(double));
+  if (c->ied_bins > 0) memset(s->ied, 0, (size_t)c->ied_bins * sizeof(int64_t));
+  s->ied_over = 0;
+  s->rc_samples = 0;
 }

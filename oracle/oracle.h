@@ -27,6 +27,8 @@
  *   orc_efield_at          MC zero axial self-force, EC force = -dW/dx
  *   MCC inside orc_step    collision counts vs nu_k dt, exact energy losses
  *   circuit inside orc_step  prescribed-charge drive; Table 1 cases 1-2
+ *   region diagnostics     hand-built states with known sheath and bulk edges
+ *                          and temperatures; IED of mono-energetic beams
  *   orc_reweight           kept fraction within binomial bounds, kept records
  *                          unchanged, independent of particle order, charge
  *                          and density profile conserved in expectation
@@ -63,6 +65,9 @@ typedef struct orc_config {
   double meta_a, meta_I;   /* reaction (1d): sigma = meta_a ln(E/meta_I)/(E meta_I) */
   int32_t gap_neumann;     /* 1: z = 0 outside the cathode is the insulating block */
   int32_t wall_neumann;    /* 1: the wall r = R is insulating too */
+  double band_r_lo, band_r_hi; /* radial band of the region diagnostics (m) */
+  int32_t ied_bins;        /* cathode ion energy histogram bins (0: off) */
+  double ied_emax;         /* its upper edge (eV); bins of width ied_emax / ied_bins */
 } orc_config;
 
 typedef struct orc_diag {
@@ -72,6 +77,17 @@ typedef struct orc_diag {
   int64_t n_ionize_meta;   /* reaction (1d) events */
   int64_t ppc_max_e, ppc_max_i;  /* most macroparticles in one cell after the step */
 } orc_diag;
+
+/* Region diagnostics (Sections 4 and 5): the sheath (n_e < n_i / 2), the
+ * pre-sheath and the bulk (from the first E_z >= 0 on) along z in each cell
+ * column, electron temperatures by region in the radial band. */
+typedef struct orc_regions {
+  int64_t samples;         /* states accumulated */
+  double Te[3];            /* sheath, pre-sheath, bulk: mean cell temperature (eV) */
+  int64_t ncell[3];        /* band cells with >= 2 electron samples in each region */
+  double z_sheath, z_bulk; /* region edges averaged over the band's columns (m) */
+  int64_t ion_impacts;     /* ion cathode impacts in the band (IED incl. overflow) */
+} orc_regions;
 
 typedef struct orc_sim orc_sim;
 
@@ -112,6 +128,14 @@ int64_t orc_get_step(const orc_sim* s);
  * particles kept (both species), or -1 for factor < 1. */
 int64_t orc_reweight(orc_sim* s, int factor);
 double orc_get_weight(const orc_sim* s);
+/* Region diagnostics: accumulate the current state (per cell particle counts
+ * and electron velocity moments, node potential); evaluate the regions (the
+ * per-column edges zs, zb may be NULL, else nr values); read the cathode ion
+ * energy histogram (ied_bins values and the overflow count); clear both. */
+void orc_region_sample(orc_sim* s);
+int orc_region_result(const orc_sim* s, orc_regions* out, double* zs, double* zb);
+void orc_ied_get(const orc_sim* s, int64_t* hist, int64_t* overflow);
+void orc_region_reset(orc_sim* s);
 void orc_destroy(orc_sim* s);
 
 #ifdef __cplusplus

@@ -33,6 +33,8 @@ class OracleConfig(C.Structure):
         ("exc_C", C.c_double), ("exc_E", C.c_double), ("E_cap", C.c_double),
         ("n_meta", C.c_double), ("meta_a", C.c_double), ("meta_I", C.c_double),
         ("gap_neumann", C.c_int32), ("wall_neumann", C.c_int32),
+        ("band_r_lo", C.c_double), ("band_r_hi", C.c_double),
+        ("ied_bins", C.c_int32), ("ied_emax", C.c_double),
     ]
 
     @classmethod
@@ -52,6 +54,16 @@ class OracleDiag(C.Structure):
 
     def as_dict(self) -> dict:
         return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class OracleRegions(C.Structure):
+    _fields_ = [("samples", C.c_int64), ("Te", C.c_double * 3), ("ncell", C.c_int64 * 3),
+                ("z_sheath", C.c_double), ("z_bulk", C.c_double), ("ion_impacts", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {"samples": self.samples, "Te": list(self.Te), "ncell": list(self.ncell),
+                "z_sheath": self.z_sheath, "z_bulk": self.z_bulk,
+                "ion_impacts": self.ion_impacts}
 
 
 _D = C.POINTER(C.c_double)
@@ -101,6 +113,10 @@ def lib():
         L.orc_reweight.restype = C.c_int64
         L.orc_get_weight.argtypes = [C.c_void_p]
         L.orc_get_weight.restype = C.c_double
+        L.orc_region_sample.argtypes = [C.c_void_p]
+        L.orc_region_result.argtypes = [C.c_void_p, C.POINTER(OracleRegions), _D, _D]
+        L.orc_ied_get.argtypes = [C.c_void_p, _I64, _I64]
+        L.orc_region_reset.argtypes = [C.c_void_p]
         L.orc_destroy.argtypes = [C.c_void_p]
         _lib = L
     return _lib
@@ -284,3 +300,27 @@ class Oracle:
     @property
     def weight(self) -> float:
         return lib().orc_get_weight(self._h)
+
+    def region_sample(self):
+        lib().orc_region_sample(self._h)
+
+    def regions(self) -> dict:
+        """Region diagnostics of the accumulated samples (Sections 4, 5):
+        dict with samples, Te[3], ncell[3], z_sheath, z_bulk, ion_impacts and
+        the per-column edges zs, zb (nr values each)."""
+        out = OracleRegions()
+        zs, zb = np.zeros(self.p["nr"]), np.zeros(self.p["nr"])
+        lib().orc_region_result(self._h, C.byref(out), _dp(zs), _dp(zb))
+        d = out.as_dict()
+        d["zs"], d["zb"] = zs, zb
+        return d
+
+    def ied(self):
+        """Cathode ion energy histogram (Section 7) and its overflow count."""
+        h = np.zeros(max(1, self.p["ied_bins"]), dtype=np.int64)
+        over = C.c_int64()
+        lib().orc_ied_get(self._h, h.ctypes.data_as(_I64), C.byref(over))
+        return h[: self.p["ied_bins"]], over.value
+
+    def region_reset(self):
+        lib().orc_region_reset(self._h)

@@ -75,6 +75,7 @@ def base_params() -> dict:
         exc_C=3.63e-18, exc_E=11.55, E_cap=800.0,
         n_meta=0.0, meta_a=4.0e-18, meta_I=4.20,
         gap_neumann=0, wall_neumann=0,
+        band_r_lo=0.010, band_r_hi=0.015, ied_bins=0, ied_emax=600.0,
         poisson_tol=1e-10, poisson_max_iter=200,
         cap_e=0, cap_i=0, birth_cap=0, diag_every=1,
         sort_every=1,
@@ -120,7 +121,8 @@ def params_paper(gather: int = 0, precision: int = 0, seed: int = 0, cells: int 
              n_gas=gas_density(10.0, 300.0), gap_neumann=1, wall_neumann=0,
              circuit_mode=1, Vc_fixed=-300.0, Vs=300.0, Rext=Rext, n_avg=100,
              gamma_i=gamma_i, gamma_e=0.1, n_meta=2.5e17, B_k=2.405 / 0.012,
-             E_cap=600.0, gather=gather, precision=precision, seed=seed)
+             E_cap=600.0, ied_bins=160, ied_emax=320.0,
+             gather=gather, precision=precision, seed=seed)
     return p
 
 
