@@ -101,6 +101,10 @@ typedef struct pic_config {
                                 (Section 3: Neumann boundary, no normal field; its nodes are
                                 unknowns of the Poisson solve); 0: grounded conductor */
   int32_t wall_neumann;      /* 1: the wall r = R is insulating as well; 0: grounded */
+  double band_r_lo, band_r_hi; /* radial band of the region diagnostics (m); the paper's
+                                discharge region is 1.0 cm < r < 1.5 cm (Sections 5, 7) */
+  int32_t ied_bins;          /* cathode ion energy histogram: bins (0: off, at most 65536) */
+  double ied_emax;           /* its upper edge (eV); bins of width ied_emax / ied_bins */
 } pic_config;
 
 /* Device-memory provider.  alloc returns a device pointer aligned to at least
@@ -227,6 +231,43 @@ int pic_diagnostics(pic_handle* h, int instance, pic_diag* out);
  * Synchronous; drops the captured step graph.  factor 1 is a no-op;
  * factor < 1 returns PIC_ERR_INVALID. */
 int pic_reweight(pic_handle* h, int instance, int factor);
+
+/* Region diagnostics (Sections 4, 5 and 7).
+ *   pic_region_sample  adds the current state to per-cell accumulators:
+ *                      particle counts of both species, electron velocity
+ *                      sums (v_r, v_theta, v_z, |v|^2), node potentials.
+ *                      Async (a few kernels on the handle's stream).
+ *   pic_region_read    evaluates the accumulated samples (synchronous).  Per
+ *                      cell column m (r_m .. r_{m+1}), walking up from the
+ *                      cathode, the sheath ends at the first cell whose
+ *                      accumulated counts give n_e >= n_i / 2, the bulk
+ *                      starts at the first cell from there on whose axial
+ *                      field from the accumulated corner potentials is
+ *                      E_z >= 0; zs[m], zb[m] (m, nr values each, may be
+ *                      NULL) are those edges.  A cell's electron temperature
+ *                      is m_e (<|v|^2> - |<v>|^2) / (3 e) over its samples
+ *                      (cells with >= 2); Te[k] is the plain mean over the
+ *                      cells of region k (sheath, pre-sheath, bulk) whose
+ *                      column centre lies in [band_r_lo, band_r_hi].
+ *                      z_sheath, z_bulk: the edges averaged over those
+ *                      columns.  ied (ied_bins values, may be NULL) and
+ *                      *ied_overflow (may be NULL): ions that hit the cathode
+ *                      at band_r_lo <= r <= band_r_hi since the last reset,
+ *                      binned by 1/2 M |v|^2 of the arriving ion, the
+ *                      overflow counting energies at or above ied_emax; the
+ *                      histogram is filled by every step's push.
+ *   pic_region_reset   clears the accumulators and the histogram (async). */
+typedef struct pic_regions {
+  int64_t samples;         /* states accumulated */
+  double Te[3];            /* sheath, pre-sheath, bulk electron temperature (eV) */
+  int64_t ncell[3];        /* cells averaged in each region */
+  double z_sheath, z_bulk; /* mean region edges over the band's columns (m) */
+  int64_t ion_impacts;     /* ions in the histogram, overflow included */
+} pic_regions;
+int pic_region_sample(pic_handle* h, int instance);
+int pic_region_read(pic_handle* h, int instance, pic_regions* out, double* zs, double* zb,
+                    int64_t* ied, int64_t* ied_overflow);
+int pic_region_reset(pic_handle* h, int instance);
 
 /* Checkpoint of one instance to / from a file (particles, phi, circuit
  * state, step and id counters, weight).  A resumed run continues bit for bit

@@ -10,6 +10,7 @@ from .pic import (  # noqa: F401
     pic_create, pic_destroy, pic_set_particles, pic_count, pic_get_particles,
     pic_solve_fields, pic_set_phi, pic_get_fields, pic_set_circuit, pic_set_next_id,
     pic_get_next_id, pic_step, pic_uses_graph, pic_tuned_chunk, pic_sync, pic_diagnostics, pic_reweight,
+    pic_region_sample, pic_region_read, pic_region_reset, PicRegions,
     pic_save, pic_load,
     pic_profile, pic_profile_read, pic_poisson_workspace_bytes, pic_poisson_solve,
     pic_unet_param_count, pic_unet_create, pic_unet_set_params, pic_unet_get_params,

@@ -139,7 +139,23 @@ std::string validate(const pic_config& c) {
   if (c.n_meta > 0.0 && !(c.meta_I > 0.0 && c.meta_a >= 0.0)) return "meta_I > 0, meta_a >= 0";
   if ((c.gap_neumann != 0 && c.gap_neumann != 1) || (c.wall_neumann != 0 && c.wall_neumann != 1))
     return "gap_neumann, wall_neumann must be 0 or 1";
+  if (c.ied_bins < 0 || c.ied_bins > 65536) return "ied_bins must be in [0, 65536]";
+  if (c.ied_bins > 0 && !(c.ied_emax > 0.0)) return "ied_emax must be positive";
+  if (!(c.band_r_lo <= c.band_r_hi)) return "band_r_lo must not exceed band_r_hi";
   return "";
+}
+
+// zero the region accumulators and the ion energy histogram of one instance
+cudaError_t region_clear(const Inst& I, cudaStream_t st) {
+  const RegionDev& R = I.reg;
+  const size_t ncell = (size_t)I.nr * I.nz, nn = (size_t)(I.nr + 1) * (I.nz + 1);
+  cudaError_t e = cudaMemsetAsync(R.ied, 0, (size_t)(I.ied_bins + 1) * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(R.n[0], 0, ncell * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(R.n[1], 0, ncell * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(R.mom, 0, ncell * 32, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(R.phi, 0, nn * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(R.samples, 0, 8, st);
+  return e;
 }
 
 int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
@@ -163,6 +179,10 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
     if (m * I.dr <= c.Rc && m < c.nr) I.m_cath = m;
   I.bc_g = c.gap_neumann ? I.m_cath + 1 : c.nr + 1;
   I.bc_wall = c.wall_neumann ? 1 : 0;
+  I.band_lo = c.band_r_lo;
+  I.band_hi = c.band_r_hi;
+  I.ied_bins = c.ied_bins;
+  I.ied_de = c.ied_bins > 0 ? c.ied_emax / c.ied_bins : 1.0;
   I.dt = c.dt;
   I.weight = c.weight;
   I.qm[0] = -kQe / kMe;
@@ -270,6 +290,18 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
     I.btab = (double4_32a*)chk(A((size_t)I.nkey * 2 * sizeof(double4_32a)));
   }
   I.qhist = (double*)chk(A((size_t)c.n_avg * 8));
+  const size_t ncell = (size_t)c.nr * c.nz;
+  RegionDev& RG = I.reg;
+  RG.ied = (unsigned long long*)chk(A((size_t)(c.ied_bins + 1) * 8));
+  RG.n[0] = (unsigned long long*)chk(A(ncell * 8));
+  RG.n[1] = (unsigned long long*)chk(A(ncell * 8));
+  RG.mom = (double*)chk(A(ncell * 32));
+  RG.phi = (double*)chk(A(nn * 8));
+  RG.samples = (unsigned long long*)chk(A(8));
+  RG.col = (double*)chk(A((size_t)c.nr * 64));
+  RG.zs = (double*)chk(A((size_t)c.nr * 8));
+  RG.zb = (double*)chk(A((size_t)c.nr * 8));
+  RG.out = (double*)chk(A(64));
   I.S = (Scalars*)chk(A(sizeof(Scalars)));
   I.diag = (DiagDev*)chk(A(sizeof(DiagDev)));
   const size_t pwb = poisson_work_bytes(c.nr, c.nz);
@@ -286,6 +318,7 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
   if (e == cudaSuccess) e = cudaMemsetAsync(I.qhist, 0, (size_t)c.n_avg * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(I.diag, 0, sizeof(DiagDev), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(pwbase, 0, pwb, st);
+  if (e == cudaSuccess) e = region_clear(I, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "memset");
   ih.pw = poisson_work_init(pwbase, c.nr, c.nz, c.R, c.L, I.bc_g, I.bc_wall, h->num_sms);
 
@@ -914,6 +947,59 @@ int pic_reweight(pic_handle* h, int instance, int factor) {
   rc = set_weight(h, instance, ih.I.weight * (double)factor);
   if (rc != PIC_OK) return rc;
   return read_status(h, instance, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// region diagnostics
+// ---------------------------------------------------------------------------
+int pic_region_sample(pic_handle* h, int instance) {
+  if (bad_instance(h, instance)) return fail(h, PIC_ERR_INVALID, "bad instance");
+  const cudaError_t e = launch_region_sample(h->inst[instance].I, h->num_sms, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "region sample");
+  return PIC_OK;
+}
+
+int pic_region_read(pic_handle* h, int instance, pic_regions* out, double* zs, double* zb,
+                    int64_t* ied, int64_t* ied_overflow) {
+  if (bad_instance(h, instance) || !out) return fail(h, PIC_ERR_INVALID, "bad argument");
+  const Inst& I = h->inst[instance].I;
+  cudaStream_t st = h->stream;
+  cudaError_t e = launch_region_eval(I, st);
+  double o[8];
+  unsigned long long samples = 0;
+  std::vector<unsigned long long> hist((size_t)I.ied_bins + 1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(o, I.reg.out, sizeof(o), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&samples, I.reg.samples, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hist.data(), I.reg.ied, hist.size() * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && zs)
+    e = cudaMemcpyAsync(zs, I.reg.zs, (size_t)I.nr * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && zb)
+    e = cudaMemcpyAsync(zb, I.reg.zb, (size_t)I.nr * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "region read");
+  out->samples = (int64_t)samples;
+  long long impacts = 0;
+  for (int k = 0; k < 3; ++k) {
+    out->Te[k] = o[k];
+    out->ncell[k] = (int64_t)o[3 + k];
+  }
+  out->z_sheath = o[6];
+  out->z_bulk = o[7];
+  for (int b = 0; b <= I.ied_bins; ++b) {
+    impacts += (long long)hist[b];
+    if (ied && b < I.ied_bins) ied[b] = (int64_t)hist[b];
+  }
+  if (ied_overflow) *ied_overflow = (int64_t)hist[I.ied_bins];
+  out->ion_impacts = impacts;
+  return read_status(h, instance, nullptr);
+}
+
+int pic_region_reset(pic_handle* h, int instance) {
+  if (bad_instance(h, instance)) return fail(h, PIC_ERR_INVALID, "bad instance");
+  const cudaError_t e = region_clear(h->inst[instance].I, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "region reset");
+  return PIC_OK;
 }
 
 // ---------------------------------------------------------------------------

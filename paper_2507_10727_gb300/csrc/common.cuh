@@ -140,6 +140,20 @@ __device__ __forceinline__ bool queue_item(const WorkQueue* q, int item, int& in
 }
 
 // Everything a kernel needs about one instance; passed by value.
+// Region diagnostics (Sections 4, 5, 7): accumulated state and the cathode
+// ion energy histogram of one instance.
+struct RegionDev {
+  unsigned long long* ied;      // ied_bins + 1 counts; the last: above the top edge
+  unsigned long long* n[2];     // per cell particle counts, summed over samples
+  double* mom;                  // per cell electron sums: v_r, v_theta, v_z, |v|^2
+  double* phi;                  // per node potential, summed over samples
+  unsigned long long* samples;  // states accumulated
+  double* col;                  // evaluation: per cell column 8 values
+  double* zs;                   // evaluation: per column sheath and bulk edges (m)
+  double* zb;
+  double* out;                  // evaluation: Te[3], ncell[3], z_sheath, z_bulk
+};
+
 struct Inst {
   // geometry
   int nr, nz, ntz, nkey;   // ntz: tiles along z; nkey: number of cell keys
@@ -158,6 +172,10 @@ struct Inst {
   int gather, rweight, mcc_on, push_on, field_on, walls_reflect, circuit_mode, n_avg;
   int bc_g;                // first insulating node of row z = 0 (nr + 1: none)
   int bc_wall;             // 1: the wall r = R is insulating
+  // region diagnostics: radial band (m), ion energy histogram bins of width ied_de (eV)
+  double band_lo, band_hi, ied_de;
+  int ied_bins;
+  RegionDev reg;
   int diag_every;
   double Vc_fixed, Vs, Rext;
   double poisson_tol;
@@ -277,6 +295,37 @@ __host__ __device__ __forceinline__ bool field_free(int m, int n, int nr, int nz
   if (n < 0 || n >= nz || m < 0 || m > nr) return false;
   if (n == 0) return m >= g && (m < nr || wall != 0);
   return m < nr || wall != 0;
+}
+
+// region diagnostics: add one particle sample (cell < 0: none) of species sp;
+// a warp whose lanes all hold one cell adds warp-reduced values
+__device__ __forceinline__ void region_add(const RegionDev& R, int sp, int cell, double vr,
+                                           double vt, double vz) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int c0 = __shfl_sync(full, cell, 0);
+  if (__all_sync(full, cell == c0) && c0 >= 0) {
+    double s[4] = {vr, vt, vz, vr * vr + vt * vt + vz * vz};
+    if (sp == 0) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(full, s[k], o);
+    }
+    if (lane == 0) {
+      atomicAdd(&R.n[sp][c0], 32ULL);
+      if (sp == 0)
+        for (int k = 0; k < 4; ++k) atomicAdd(&R.mom[(size_t)c0 * 4 + k], s[k]);
+    }
+  } else if (cell >= 0) {
+    atomicAdd(&R.n[sp][cell], 1ULL);
+    if (sp == 0) {
+      atomicAdd(&R.mom[(size_t)cell * 4 + 0], vr);
+      atomicAdd(&R.mom[(size_t)cell * 4 + 1], vt);
+      atomicAdd(&R.mom[(size_t)cell * 4 + 2], vz);
+      atomicAdd(&R.mom[(size_t)cell * 4 + 3], vr * vr + vt * vt + vz * vz);
+    }
+  }
 }
 
 __device__ __forceinline__ double node_area(const Inst& I, int m) {

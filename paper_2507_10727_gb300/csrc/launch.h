@@ -43,6 +43,13 @@ cudaError_t launch_sort_species(const Inst& I, int sp, int num_sms, cudaStream_t
 cudaError_t launch_thin(const Inst& I, int factor, int num_sms, cudaStream_t st);
 cudaError_t launch_thin32(const Inst& I, int sp, int factor, int num_sms, cudaStream_t st);
 
+// region diagnostics: add one sample of the current state (both species and
+// phi) to the accumulators; evaluate the accumulated samples into reg.out,
+// reg.zs, reg.zb
+cudaError_t launch_region_sample(const Inst& I, int num_sms, cudaStream_t st);
+cudaError_t launch_region_sample32(const Inst& I, int sp, int num_sms, cudaStream_t st);
+cudaError_t launch_region_eval(const Inst& I, cudaStream_t st);
+
 // set the particle count of species sp (set-up)
 cudaError_t launch_set_n(const Inst& I, int sp, long long n, cudaStream_t st);
 

@@ -345,6 +345,12 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
               // cathode impact (Section 3): tally; secondary electron with
               // probability gamma, born at the impact point at rest
               atomicAdd(SP == 1 ? &S->cnt_ion_cath : &S->cnt_e_cath, 1ULL);
+              // ion energy distribution on the cathode band (Section 7)
+              if (SP == 1 && I.ied_bins > 0 && rhit >= I.band_lo && rhit <= I.band_hi) {
+                const double E = 0.5 * I.mass[1] * (vr * vr + vt * vt + vz * vz) / kQe;
+                const double fb = floor(E / I.ied_de);
+                atomicAdd(&I.reg.ied[fb < (double)I.ied_bins ? (int)fb : I.ied_bins], 1ULL);
+              }
               if (I.gamma[SP] > 0.0) {
                 const long long id = P.id[i];
                 double u[4];
@@ -696,6 +702,118 @@ __global__ void k_thin(Inst I, int sp, int factor) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Region diagnostics (Sections 4, 5): one sample of the state is added to the
+// per-cell sums (particle counts of both species, electron velocity moments)
+// and phi to the node sums.  The arrays are sorted by cell, so a warp whose
+// 32 particles share one cell adds warp-reduced values; other warps add per
+// particle.
+// ---------------------------------------------------------------------------
+__global__ void k_region_sample(Inst I, int sp) {
+  const Scalars* S = I.S;
+  if (S->status & ST_FATAL) return;
+  const long long n = S->n[sp];
+  const ParticlesDev P = I.buf[sp][S->flip[sp]];
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = warp * 32; base < n; base += nwarp * 32) {
+    const long long i = base + lane;
+    int cell = -1;
+    double vr = 0.0, vt = 0.0, vz = 0.0;
+    if (i < n) {
+      int m, nn;
+      double f;
+      locate(P.r[i], I.inv_dr, I.nr, m, f);
+      locate(P.z[i], I.inv_dz, I.nz, nn, f);
+      cell = m * I.nz + nn;
+      vr = P.vr[i];
+      vt = P.vt[i];
+      vz = P.vz[i];
+    }
+    region_add(I.reg, sp, cell, vr, vt, vz);
+  }
+}
+
+__global__ void k_region_phi(Inst I) {
+  if (I.S->status & ST_FATAL) return;
+  const long long nn = (long long)(I.nr + 1) * (I.nz + 1);
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nn;
+       k += (long long)gridDim.x * blockDim.x)
+    I.reg.phi[k] += I.phi[k];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *I.reg.samples += 1ULL;
+}
+
+// Evaluation of the accumulated samples (Section 4: the sheath ends where
+// n_e >= n_i / 2 -- 2 N_e >= N_i in counts, same volume and weight; the bulk
+// starts at the first cell from there on with E_z = -d phi/dz >= 0 from the
+// cell's corner potentials; Section 5: a cell's electron temperature is
+// m_e (<|v|^2> - |<v>|^2) / (3 e) over its samples (at least two), a
+// region's the plain mean over its cells in the radial band).  One block;
+// columns in parallel, the final sums in column order.
+__global__ void k_region_eval(Inst I) {
+  const RegionDev R = I.reg;
+  const int nr = I.nr, nz = I.nz, nz1 = nz + 1;
+  for (int m = threadIdx.x; m < nr; m += blockDim.x) {
+    int ns = nz, nb = nz;
+    for (int n = 0; n < nz; ++n) {
+      const size_t c = (size_t)m * nz + n;
+      if (2ULL * R.n[0][c] >= R.n[1][c]) {
+        ns = n;
+        break;
+      }
+    }
+    for (int n = ns; n < nz; ++n) {
+      const double up = R.phi[m * nz1 + n + 1] + R.phi[(m + 1) * nz1 + n + 1];
+      const double lo = R.phi[m * nz1 + n] + R.phi[(m + 1) * nz1 + n];
+      if (up - lo <= 0.0) {
+        nb = n;
+        break;
+      }
+    }
+    R.zs[m] = ns * I.dz;
+    R.zb[m] = nb * I.dz;
+    double* col = R.col + (size_t)m * 8;
+    for (int k = 0; k < 7; ++k) col[k] = 0.0;
+    const double rcen = (m + 0.5) * I.dr;
+    if (rcen < I.band_lo || rcen > I.band_hi) continue;
+    col[6] = 1.0;
+    for (int n = 0; n < nz; ++n) {
+      const size_t c = (size_t)m * nz + n;
+      const unsigned long long N = R.n[0][c];
+      if (N < 2ULL) continue;
+      const double Nd = (double)N;
+      const double* mo = R.mom + c * 4;
+      const double mr = mo[0] / Nd, mt = mo[1] / Nd, mz = mo[2] / Nd;
+      const double T = kMe * (mo[3] / Nd - (mr * mr + mt * mt + mz * mz)) / (3.0 * kQe);
+      const int reg = n < ns ? 0 : (n < nb ? 1 : 2);
+      col[reg] += T;
+      col[3 + reg] += 1.0;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[3] = {0.0, 0.0, 0.0}, c[3] = {0.0, 0.0, 0.0}, zs = 0.0, zb = 0.0, ncol = 0.0;
+    for (int m = 0; m < nr; ++m) {
+      const double* col = R.col + (size_t)m * 8;
+      if (col[6] == 0.0) continue;
+      for (int k = 0; k < 3; ++k) {
+        t[k] += col[k];
+        c[k] += col[3 + k];
+      }
+      zs += R.zs[m];
+      zb += R.zb[m];
+      ncol += 1.0;
+    }
+    for (int k = 0; k < 3; ++k) {
+      R.out[k] = c[k] > 0.0 ? t[k] / c[k] : 0.0;
+      R.out[3 + k] = c[k];
+    }
+    R.out[6] = ncol > 0.0 ? zs / ncol : 0.0;
+    R.out[7] = ncol > 0.0 ? zb / ncol : 0.0;
+  }
+}
+
 // n = n_next after a set-up sort (no births)
 __global__ void k_commit_n(Inst I, int sp) {
   if (threadIdx.x == 0 && !(I.S->status & ST_FATAL)) {
@@ -979,6 +1097,21 @@ cudaError_t launch_thin(const Inst& I, int factor, int num_sms, cudaStream_t st)
       k_commit_n<<<1, 32, 0, st>>>(I, sp);
     }
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_region_sample(const Inst& I, int num_sms, cudaStream_t st) {
+  for (int sp = 0; sp < 2; ++sp) {
+    if (I.prec32) launch_region_sample32(I, sp, num_sms, st);
+    else k_region_sample<<<grid_for(I.cap[sp], 256, num_sms, 8), 256, 0, st>>>(I, sp);
+  }
+  const long long nn = (long long)(I.nr + 1) * (I.nz + 1);
+  k_region_phi<<<grid_for(nn, 256, num_sms, 2), 256, 0, st>>>(I);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_region_eval(const Inst& I, cudaStream_t st) {
+  k_region_eval<<<1, 256, 0, st>>>(I);
   return cudaGetLastError();
 }
 

@@ -54,6 +54,8 @@ class PicConfig(C.Structure):
         ("diag_every", C.c_int32), ("sort_every", C.c_int32),
         ("n_meta", C.c_double), ("meta_a", C.c_double), ("meta_I", C.c_double),
         ("gap_neumann", C.c_int32), ("wall_neumann", C.c_int32),
+        ("band_r_lo", C.c_double), ("band_r_hi", C.c_double),
+        ("ied_bins", C.c_int32), ("ied_emax", C.c_double),
     ]
 
     @classmethod
@@ -79,6 +81,16 @@ class PicDiag(C.Structure):
 
     def as_dict(self) -> dict:
         return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class PicRegions(C.Structure):
+    _fields_ = [("samples", C.c_int64), ("Te", C.c_double * 3), ("ncell", C.c_int64 * 3),
+                ("z_sheath", C.c_double), ("z_bulk", C.c_double), ("ion_impacts", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {"samples": self.samples, "Te": list(self.Te), "ncell": list(self.ncell),
+                "z_sheath": self.z_sheath, "z_bulk": self.z_bulk,
+                "ion_impacts": self.ion_impacts}
 
 
 class PicUnetStats(C.Structure):
@@ -137,6 +149,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         L.pic_sync.argtypes = [vp]
         L.pic_diagnostics.argtypes = [vp, C.c_int, C.POINTER(PicDiag)]
         L.pic_reweight.argtypes = [vp, C.c_int, C.c_int]
+        L.pic_region_sample.argtypes = [vp, C.c_int]
+        L.pic_region_read.argtypes = [vp, C.c_int, C.POINTER(PicRegions), vp, vp, vp, _I64]
+        L.pic_region_reset.argtypes = [vp, C.c_int]
         L.pic_save.argtypes = [vp, C.c_int, C.c_char_p]
         L.pic_load.argtypes = [vp, C.c_int, C.c_char_p]
         L.pic_profile.argtypes = [vp, C.c_int]
@@ -352,6 +367,32 @@ def pic_diagnostics(h: Handle, instance: int = 0, check: bool = True) -> dict:
 
 def pic_reweight(h: Handle, instance: int, factor: int = 3):
     _check(h, load_library().pic_reweight(h.ptr, instance, factor))
+
+
+def pic_region_sample(h: Handle, instance: int = 0):
+    _check(h, load_library().pic_region_sample(h.ptr, instance))
+
+
+def pic_region_read(h: Handle, instance: int = 0) -> dict:
+    """Region diagnostics of the accumulated samples and the cathode ion
+    energy histogram: dict as PicRegions plus zs, zb (per cell column) and
+    ied, ied_overflow."""
+    nr = h.params[instance]["nr"]
+    bins = h.params[instance].get("ied_bins", 0)
+    out = PicRegions()
+    zs, zb = np.zeros(nr), np.zeros(nr)
+    ied = np.zeros(max(1, bins), dtype=np.int64)
+    over = C.c_int64()
+    _check(h, load_library().pic_region_read(h.ptr, instance, C.byref(out),
+                                             zs.ctypes.data, zb.ctypes.data, ied.ctypes.data,
+                                             C.byref(over)))
+    d = out.as_dict()
+    d.update(zs=zs, zb=zb, ied=ied[:bins], ied_overflow=over.value)
+    return d
+
+
+def pic_region_reset(h: Handle, instance: int = 0):
+    _check(h, load_library().pic_region_reset(h.ptr, instance))
 
 
 def pic_save(h: Handle, instance: int, path: str):

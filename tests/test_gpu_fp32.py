@@ -218,3 +218,25 @@ def test_fp32_insulating_block(pg):
     pg.pic_step(h, 1)
     _check(pg, h, orc)
     pg.pic_destroy(h)
+
+
+def test_fp32_region_diagnostics(pg):
+    """FP32 mode: the same region evaluation over FP32 records; temperatures
+    and the ion histogram's total agree with the FP64 oracle at the FP32
+    level."""
+    p = pic_inputs.params_rz32()
+    p.update(gamma_i=0.2, poisson_tol=1e-12, circuit_mode=1, Vs=400.0, Rext=100.0, n_avg=3,
+             band_r_lo=0.010, band_r_hi=0.015, ied_bins=64, ied_emax=256.0)
+    p, parts = busy_state(p, ppc=16, seed=67)
+    p, orc, h = _pair32(pg, p, parts)
+    orc.step(1)
+    pg.pic_step(h, 1)
+    orc.region_sample()
+    pg.pic_region_sample(h, 0)
+    a, b = pg.pic_region_read(h, 0), orc.regions()
+    assert a["samples"] == 1
+    assert a["ion_impacts"] == b["ion_impacts"] > 0
+    for k in range(3):
+        if b["ncell"][k] > 0:
+            assert a["Te"][k] == pytest.approx(b["Te"][k], rel=2e-3), k
+    pg.pic_destroy(h)

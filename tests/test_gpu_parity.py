@@ -403,3 +403,49 @@ def test_insulating_block_steps_match_oracle(pg, gather, wall):
     m_gap = int(0.6 * p["nr"]) + 2
     assert phi[m_gap, 0] != 0.0          # the block floats
     pg.pic_destroy(h)
+
+
+def _fast_cathode_ions(p, parts, seed):
+    """The cathode-bound ions of busy_state given a spread of energies
+    (about 20 to 330 eV) so that the ion energy histogram has many bins."""
+    rng = np.random.default_rng(seed)
+    i = parts["i"]
+    k = np.flatnonzero(i["vz"] == -2e4)
+    vz = -rng.uniform(1.0e4, 4.0e4, k.size)
+    i["vz"][k] = vz
+    i["z"][k] = rng.random(k.size) * np.abs(vz) * p["dt"]
+
+
+@pytest.mark.parametrize("gather", [0, 1])
+def test_region_diagnostics_match_oracle(pg, gather):
+    """Region diagnostics (Sections 4, 5, 7): per-column sheath and bulk
+    edges, electron temperatures by region and the cathode ion energy
+    histogram accumulated over three steps, against the oracle's."""
+    p = pic_inputs.params_rz32(gather=gather)
+    p.update(gamma_i=0.2, poisson_tol=1e-13, circuit_mode=1, Vs=400.0, Rext=100.0, n_avg=3,
+             band_r_lo=0.010, band_r_hi=0.015, ied_bins=64, ied_emax=256.0)
+    p, parts = busy_state(p, ppc=16, seed=61 + gather)
+    _fast_cathode_ions(p, parts, 7 + gather)
+    p, orc, h = _pair(pg, p, parts)
+    for _ in range(3):
+        orc.step(1)
+        pg.pic_step(h, 1)
+        orc.region_sample()
+        pg.pic_region_sample(h, 0)
+    _check_step(pg, h, orc)
+    a, b = pg.pic_region_read(h, 0), orc.regions()
+    bh, bo = orc.ied()
+    assert a["samples"] == b["samples"] == 3
+    assert np.array_equal(a["zs"], b["zs"]) and np.array_equal(a["zb"], b["zb"])
+    assert a["ncell"] == b["ncell"] and sum(a["ncell"]) > 0
+    for k in range(3):
+        assert a["Te"][k] == pytest.approx(b["Te"][k], rel=1e-10), k
+    assert a["z_sheath"] == pytest.approx(b["z_sheath"], rel=1e-14)
+    assert a["z_bulk"] == pytest.approx(b["z_bulk"], rel=1e-14)
+    assert np.array_equal(a["ied"], bh) and a["ied_overflow"] == bo
+    assert a["ion_impacts"] == b["ion_impacts"] > 50
+    assert np.count_nonzero(bh) > 10
+    pg.pic_region_reset(h, 0)
+    z = pg.pic_region_read(h, 0)
+    assert z["samples"] == 0 and z["ion_impacts"] == 0 and z["ncell"] == [0, 0, 0]
+    pg.pic_destroy(h)
