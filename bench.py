@@ -613,6 +613,27 @@ def main():
     prof_ps = d2["particle_steps"] - d1["particle_steps"]
     ne, ni = pg.pic_count(h, 0, 0), pg.pic_count(h, 0, 1)
 
+    # region diagnostics sampler (Sections 4, 5): one warp per cell bin of the
+    # sorted arrays; algorithmic bytes = the electron velocities (24 B FP64,
+    # the 32 B FP32 record) + the bin ends and the per-cell accumulators
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pg.pic_region_sample(h, 0)
+    torch.cuda.synchronize()
+    r0.record(stream)
+    for _ in range(5):
+        pg.pic_region_sample(h, 0)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    reg_ms = r0.elapsed_time(r1) / 5
+    ncell = p["nr"] * p["nz"]
+    reg_bytes = ((24.0 if args.precision == "fp64" else 32.0) * ne
+                 + 2 * 4.0 * ncell + 2 * (2 * 8.0 + 2 * 32.0) * ncell
+                 + 2 * 8.0 * (p["nr"] + 1) * (p["nz"] + 1))
+    regions_out = pg.pic_region_read(h, 0)
+    region = {"ms_per_sample": reg_ms, "achieved_gbs": reg_bytes / (reg_ms / 1e3) / 1e9,
+              "bytes_per_sample": reg_bytes, "Te_eV": regions_out["Te"],
+              "z_sheath_m": regions_out["z_sheath"], "z_bulk_m": regions_out["z_bulk"]}
+
     peaks, peak_kind = measured_peaks()
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
@@ -699,7 +720,8 @@ def main():
                 "poisson": {"iters_last_step": d1["poisson_iters"],
                             "resid_last_step": d1["poisson_resid"],
                             "ms_per_step": per_kernel["poisson"]},
-                "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
+                "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+                "region_diagnostics": region}
         print(json.dumps(line), flush=True)
     pg.pic_destroy(h)
     if world > 1:

@@ -311,6 +311,8 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
   cudaError_t e = cudaSuccess;
   for (int sp = 0; sp < 2 && e == cudaSuccess; ++sp) {
     e = cudaMemsetAsync(I.counts[sp], 0, (size_t)I.nkey * 4, st);
+    // cell bin ends of the sorted arrays (all empty until particles are set)
+    if (e == cudaSuccess) e = cudaMemsetAsync(I.cursor[sp], 0, (size_t)I.nkey * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(p32 ? (void*)I.qacc64[sp] : (void*)I.qacc[sp], 0, nn * 8, st);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(I.phi, 0, nn * 8, st);
@@ -1127,6 +1129,13 @@ int pic_load(pic_handle* h, int instance, const char* path) {
   if (e == cudaSuccess) e = cudaMemcpy(ih.I.qhist, qh.data(), qh.size() * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ih.I.phi, phi.data(), nn * 8, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(h, e, "load copy");
+  // FP32 records were copied as saved: sort them once here so that this
+  // handle's cell bins describe them (factor 1 keeps every particle)
+  if (ih.I.prec32) {
+    e = launch_thin(ih.I, 1, h->num_sms, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "load sort");
+  }
   // the checkpoint's weight (it differs from the handle's after re-weighting)
   if (fc.weight != ih.I.weight) return set_weight(h, instance, fc.weight);
   return PIC_OK;

@@ -297,37 +297,6 @@ __host__ __device__ __forceinline__ bool field_free(int m, int n, int nr, int nz
   return m < nr || wall != 0;
 }
 
-// region diagnostics: add one particle sample (cell < 0: none) of species sp;
-// a warp whose lanes all hold one cell adds warp-reduced values
-__device__ __forceinline__ void region_add(const RegionDev& R, int sp, int cell, double vr,
-                                           double vt, double vz) {
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const int c0 = __shfl_sync(full, cell, 0);
-  if (__all_sync(full, cell == c0) && c0 >= 0) {
-    double s[4] = {vr, vt, vz, vr * vr + vt * vt + vz * vz};
-    if (sp == 0) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(full, s[k], o);
-    }
-    if (lane == 0) {
-      atomicAdd(&R.n[sp][c0], 32ULL);
-      if (sp == 0)
-        for (int k = 0; k < 4; ++k) atomicAdd(&R.mom[(size_t)c0 * 4 + k], s[k]);
-    }
-  } else if (cell >= 0) {
-    atomicAdd(&R.n[sp][cell], 1ULL);
-    if (sp == 0) {
-      atomicAdd(&R.mom[(size_t)cell * 4 + 0], vr);
-      atomicAdd(&R.mom[(size_t)cell * 4 + 1], vt);
-      atomicAdd(&R.mom[(size_t)cell * 4 + 2], vz);
-      atomicAdd(&R.mom[(size_t)cell * 4 + 3], vr * vr + vt * vt + vz * vz);
-    }
-  }
-}
-
 __device__ __forceinline__ double node_area(const Inst& I, int m) {
   if (m == 0) return kPi * 0.25 * I.dr * I.dr;
   if (m == I.nr) return kPi * (I.R * I.R - (I.R - 0.5 * I.dr) * (I.R - 0.5 * I.dr));

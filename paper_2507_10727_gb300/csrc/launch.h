@@ -47,7 +47,6 @@ cudaError_t launch_thin32(const Inst& I, int sp, int factor, int num_sms, cudaSt
 // phi) to the accumulators; evaluate the accumulated samples into reg.out,
 // reg.zs, reg.zb
 cudaError_t launch_region_sample(const Inst& I, int num_sms, cudaStream_t st);
-cudaError_t launch_region_sample32(const Inst& I, int sp, int num_sms, cudaStream_t st);
 cudaError_t launch_region_eval(const Inst& I, cudaStream_t st);
 
 // set the particle count of species sp (set-up)

@@ -705,33 +705,59 @@ __global__ void k_thin(Inst I, int sp, int factor) {
 // ---------------------------------------------------------------------------
 // Region diagnostics (Sections 4, 5): one sample of the state is added to the
 // per-cell sums (particle counts of both species, electron velocity moments)
-// and phi to the node sums.  The arrays are sorted by cell, so a warp whose
-// 32 particles share one cell adds warp-reduced values; other warps add per
-// particle.
+// and phi to the node sums.  The particle arrays are sorted by cell: after the
+// scatter, cursor[k] is the end of cell bin k (its start the end of bin k - 1),
+// so one warp sums one cell's particles (strided per-lane sums, one warp
+// reduction per cell) and is the only writer of that cell's accumulators.
 // ---------------------------------------------------------------------------
+template <bool F32>
 __global__ void k_region_sample(Inst I, int sp) {
   const Scalars* S = I.S;
   if (S->status & ST_FATAL) return;
   const long long n = S->n[sp];
-  const ParticlesDev P = I.buf[sp][S->flip[sp]];
+  const int* ends = I.cursor[sp];
   const int lane = threadIdx.x & 31;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long base = warp * 32; base < n; base += nwarp * 32) {
-    const long long i = base + lane;
-    int cell = -1;
-    double vr = 0.0, vt = 0.0, vz = 0.0;
-    if (i < n) {
-      int m, nn;
-      double f;
-      locate(P.r[i], I.inv_dr, I.nr, m, f);
-      locate(P.z[i], I.inv_dz, I.nz, nn, f);
-      cell = m * I.nz + nn;
-      vr = P.vr[i];
-      vt = P.vt[i];
-      vz = P.vz[i];
+  const int warp = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwarp = (int)(((long long)gridDim.x * blockDim.x) >> 5);
+  const unsigned full = 0xffffffffu;
+  for (int k = warp; k < I.nkey; k += nwarp) {
+    long long b0 = k > 0 ? ends[k - 1] : 0, b1 = ends[k];
+    if (b1 > n) b1 = n;
+    if (b1 <= b0) continue;
+    const int tile = k / kTileCells, within = k - tile * kTileCells;
+    const int tm = tile / I.ntz, tn = tile - tm * I.ntz;
+    const int m = tm * kTile + (within >> 3), nn = tn * kTile + (within & 7);
+    if (m >= I.nr || nn >= I.nz) continue;   // padding keys hold no particles
+    const int cell = m * I.nz + nn;
+    if (sp == 0) {
+      double s[4] = {0.0, 0.0, 0.0, 0.0};
+      for (long long i = b0 + lane; i < b1; i += 32) {
+        double vr, vt, vz;
+        if (F32) {
+          const float4 a = I.buf32[0][S->flip[0]].a[i];
+          const uint4 b = I.buf32[0][S->flip[0]].b[i];
+          vr = (double)a.z;
+          vt = (double)a.w;
+          vz = (double)__uint_as_float(b.x);
+        } else {
+          const ParticlesDev P = I.buf[0][S->flip[0]];
+          vr = P.vr[i];
+          vt = P.vt[i];
+          vz = P.vz[i];
+        }
+        s[0] += vr;
+        s[1] += vt;
+        s[2] += vz;
+        s[3] += vr * vr + vt * vt + vz * vz;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(full, s[q], o);
+      if (lane == 0)
+        for (int q = 0; q < 4; ++q) I.reg.mom[(size_t)cell * 4 + q] += s[q];
     }
-    region_add(I.reg, sp, cell, vr, vt, vz);
+    if (lane == 0) I.reg.n[sp][cell] += (unsigned long long)(b1 - b0);
   }
 }
 
@@ -1101,9 +1127,11 @@ cudaError_t launch_thin(const Inst& I, int factor, int num_sms, cudaStream_t st)
 }
 
 cudaError_t launch_region_sample(const Inst& I, int num_sms, cudaStream_t st) {
+  // one warp per cell bin, eight warps per block
+  const int blocks = grid_for((long long)I.nkey * 32, 256, num_sms, 8);
   for (int sp = 0; sp < 2; ++sp) {
-    if (I.prec32) launch_region_sample32(I, sp, num_sms, st);
-    else k_region_sample<<<grid_for(I.cap[sp], 256, num_sms, 8), 256, 0, st>>>(I, sp);
+    if (I.prec32) k_region_sample<true><<<blocks, 256, 0, st>>>(I, sp);
+    else k_region_sample<false><<<blocks, 256, 0, st>>>(I, sp);
   }
   const long long nn = (long long)(I.nr + 1) * (I.nz + 1);
   k_region_phi<<<grid_for(nn, 256, num_sms, 2), 256, 0, st>>>(I);

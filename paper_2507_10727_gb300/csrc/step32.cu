@@ -618,36 +618,6 @@ __global__ void k_thin32(Inst I, int sp, int factor) {
   }
 }
 
-// one sample of the FP32 records for the region diagnostics (cells from the
-// records' cell index; moments from the FP32 velocities in FP64 sums)
-__global__ void k_region_sample32(Inst I, int sp) {
-  const Scalars* S = I.S;
-  if (S->status & ST_FATAL) return;
-  const long long n = S->n[sp];
-  const Particles32 P = I.buf32[sp][S->flip[sp]];
-  const int lane = threadIdx.x & 31;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long base = warp * 32; base < n; base += nwarp * 32) {
-    const long long i = base + lane;
-    int cell = -1;
-    double vr = 0.0, vt = 0.0, vz = 0.0;
-    if (i < n) {
-      const float4 a = P.a[i];
-      const uint4 b = P.b[i];
-      if (b.y != kDead) {
-        int m, nn;
-        cell_mn(b.y, m, nn);
-        cell = m * I.nz + nn;
-        vr = (double)a.z;
-        vt = (double)a.w;
-        vz = (double)__uint_as_float(b.x);
-      }
-    }
-    region_add(I.reg, sp, cell, vr, vt, vz);
-  }
-}
-
 // FP32 records [offset, offset + count) of cur32 -> FP64 SoA
 __global__ void k_unpack32(Inst I, int sp, long long offset, long long count, double* r, double* z,
                            double* vr, double* vt, double* vz, long long* id) {
@@ -714,11 +684,6 @@ cudaError_t launch_sort_species32(const Inst& I, int sp, int num_sms, cudaStream
 
 cudaError_t launch_thin32(const Inst& I, int sp, int factor, int num_sms, cudaStream_t st) {
   k_thin32<<<grid32(I.cap[sp], 256, num_sms, 8), 256, 0, st>>>(I, sp, factor);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_region_sample32(const Inst& I, int sp, int num_sms, cudaStream_t st) {
-  k_region_sample32<<<grid32(I.cap[sp], 256, num_sms, 8), 256, 0, st>>>(I, sp);
   return cudaGetLastError();
 }
 
