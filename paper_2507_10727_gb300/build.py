@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpic_gb300.so")
 SOURCES = ["step.cu", "step32.cu", "poisson.cu", "api.cu", "noalloc.cu", "unet.cu"]
-HEADERS = ["common.cuh", "launch.h", "device_util.cuh", "unet.h"]
+HEADERS = ["common.cuh", "bits.cuh", "launch.h", "device_util.cuh", "unet.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

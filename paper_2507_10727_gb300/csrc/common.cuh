@@ -16,6 +16,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "bits.cuh"
+
 namespace pic {
 
 // CODATA 2018
@@ -243,12 +245,10 @@ __device__ __forceinline__ void draws(const Inst& I, int sp, long long id, long 
 // ---------------------------------------------------------------------------
 // grid helpers
 // ---------------------------------------------------------------------------
+// cell k = (int)(x / d) (clamped to ncell - 1) and offset f = x / d - k, with
+// x / d taken as x * inv_d; the split runs on the integer pipes (bits.cuh)
 __device__ __forceinline__ void locate(double x, double inv_d, int ncell, int& k, double& f) {
-  double s = x * inv_d;
-  int i = (int)s;                       // x >= 0 for particles inside the domain
-  if (i > ncell - 1) i = ncell - 1;
-  k = i;
-  f = s - (double)i;
+  split_cell(x * inv_d, ncell, k, f);
 }
 
 __device__ __forceinline__ int cell_key(const Inst& I, int m, int n) {
@@ -267,11 +267,11 @@ __device__ __forceinline__ double rweight_upper(const Inst& I, double r, int m, 
 
 // Fixed-point corner weights of a unit charge at in-cell weights (wr, wz):
 // exact integers summing to 2^44.  w11 = round(ir iz / 2^44) from the 88-bit
-// integer product, so only two FP64 -> integer conversions are needed.
+// integer product; ir, iz come from the weights' bit patterns (no FP64 work).
 struct FixW { unsigned long long w00, w10, w01, w11; };
 __device__ __forceinline__ FixW fix_weights(double wr, double wz) {
-  const unsigned long long ir = (unsigned long long)__double2ll_rn(wr * kFixOne);  // exact scaling
-  const unsigned long long iz = (unsigned long long)__double2ll_rn(wz * kFixOne);
+  const unsigned long long ir = fix44(wr);   // round(wr 2^44), integer pipes
+  const unsigned long long iz = fix44(wz);
   const unsigned long long lo = ir * iz, hi = __umul64hi(ir, iz);
   const unsigned long long i11 = ((hi << (64 - kFixBits)) | (lo >> kFixBits)) + ((lo >> (kFixBits - 1)) & 1ULL);
   FixW f;

@@ -1,0 +1,80 @@
+"""The integer-pipe helpers of the particle push (csrc/bits.cuh) against the
+FP64 sequences they replace, bit for bit, on the CPU: the header's host build
+runs both forms over random and edge-case inputs.
+
+* split_cell(s): (int)s clamped to ncell - 1 and s - (double)k, for s in
+  [0, ncell) (random, integers and their neighbours one ulp away, tiny
+  values, 0) and for negative, clamped and non-finite s;
+* fix44(w): round-to-nearest-even of w 2^44 (llrint), for w in [0, 1]
+  (random, exact ties at the 2^-45 grid, the neighbours of ties, tiny, 0, 1)
+  and outside that range.
+"""
+import os
+import subprocess
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2507_10727_gb300", "csrc")
+
+PROGRAM = r"""
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include "bits.cuh"
+using namespace pic;
+static bool same(double a, double b) { uint64_t x, y; std::memcpy(&x, &a, 8); std::memcpy(&y, &b, 8); return x == y; }
+static long long bad = 0, n = 0;
+static void check_split(double s, int ncell) {
+  int k1; double f1; split_cell(s, ncell, k1, f1);
+  int k2 = (int)s; if (k2 > ncell - 1) k2 = ncell - 1; double f2 = s - (double)k2;
+  ++n; if (k1 != k2 || !same(f1, f2)) { if (bad < 5) std::printf("split %.17g %d: %d %.17g vs %d %.17g\n", s, ncell, k1, f1, k2, f2); ++bad; }
+}
+static void check_fix(double w) {
+  uint64_t a = fix44(w), b = (uint64_t)std::llrint(w * 17592186044416.0);
+  ++n; if (a != b) { if (bad < 5) std::printf("fix %.17g: %llu vs %llu\n", w, (unsigned long long)a, (unsigned long long)b); ++bad; }
+}
+int main() {
+  std::mt19937_64 g(12345);
+  std::uniform_real_distribution<double> u(0.0, 1.0);
+  for (int ncell : {1, 2, 7, 256, 512, 4096, 65536}) {
+    for (int t = 0; t < 400000; ++t) check_split(u(g) * ncell, ncell);
+    for (int k = 0; k <= ncell && k < 5000; ++k) {
+      double s = k;
+      check_split(s, ncell);
+      check_split(std::nextafter(s, -1.0), ncell);
+      check_split(std::nextafter(s, 1e9), ncell);
+    }
+    for (double s : {0.0, 1e-300, 5e-324, 1e-20, 0.5, -0.0, -1e-12, -0.75, -3.5,
+                     (double)ncell + 0.25, 1e12, 3e9, (double)INFINITY})
+      check_split(s, ncell);
+  }
+  for (int t = 0; t < 2000000; ++t) check_fix(u(g));
+  for (int t = 0; t < 200000; ++t) {   // exact ties and their neighbours
+    uint64_t j = g() & ((1ULL << 45) - 1);
+    double w = std::ldexp((double)(2 * j + 1), -45);
+    check_fix(w); check_fix(std::nextafter(w, 0.0)); check_fix(std::nextafter(w, 2.0));
+  }
+  for (double w : {0.0, -0.0, 5e-324, 1e-300, 1e-14, 2.842170943040401e-14, 5.684341886080802e-14,
+                   0.5, 1.0, std::nextafter(1.0, 0.0), 1.0000000000000002, 200.0, 255.999, 256.0,
+                   1e6, -1e-15, -0.5})
+    check_fix(w);
+  std::printf("checked %lld mismatches %lld\n", n, bad);
+  return bad != 0;
+}
+"""
+
+
+def test_integer_pipe_helpers_match_fp64_sequences(tmp_path):
+    src = tmp_path / "bits_check.cpp"
+    exe = tmp_path / "bits_check"
+    src.write_text(PROGRAM)
+    r = subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-I", CSRC, str(src),
+                        "-o", str(exe)], capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.fail(r.stderr)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    print(r.stdout)
+    assert r.returncode == 0, r.stdout
+    assert "mismatches 0" in r.stdout
