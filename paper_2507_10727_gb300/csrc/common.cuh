@@ -282,6 +282,14 @@ __device__ __forceinline__ FixW fix_weights(double wr, double wz) {
   return f;
 }
 
+// 1 / x for x >= 1 below the FP32 overflow: the FP32 approximate reciprocal
+// (PTX rcp.approx.ftz.f32, within one FP32 ulp) refined in FP64 (bits.cuh)
+__device__ __forceinline__ double recip(double x) {
+  float yf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"((float)x));
+  return recip_refine(x, (double)yf);
+}
+
 // finite test on the exponent bits (integer pipe)
 __device__ __forceinline__ bool finite64(double x) {
   return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;

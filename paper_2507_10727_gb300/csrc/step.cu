@@ -304,7 +304,7 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
           // Boris: half kick, rotation about B, half kick
           const double ax = vr + h * Er, ay = vt, az = vz + h * Ez;
           const double tx = h * Br, tz = h * Bz;
-          const double f2 = 2.0 / (1.0 + tx * tx + tz * tz);
+          const double f2 = 2.0 * recip(1.0 + tx * tx + tz * tz);   // 1 + t^2 >= 1
           const double sx = f2 * tx, sz = f2 * tz;
           const double px = ax + ay * tz;
           const double py = ay + (az * tx - ax * tz);

@@ -7,7 +7,10 @@ runs both forms over random and edge-case inputs.
   values, 0) and for negative, clamped and non-finite s;
 * fix44(w): round-to-nearest-even of w 2^44 (llrint), for w in [0, 1]
   (random, exact ties at the 2^-45 grid, the neighbours of ties, tiny, 0, 1)
-  and outside that range.
+  and outside that range;
+* recip_refine(x, seed): within one ulp of 1.0 / x for seeds up to two FP32
+  ulps from the rounded FP32 reciprocal (the device seed, PTX rcp.approx, is
+  within one), x in [1, 4) and log-uniform over 1e-30 .. 1e30.
 """
 import os
 import subprocess
@@ -35,6 +38,19 @@ static void check_fix(double w) {
   uint64_t a = fix44(w), b = (uint64_t)std::llrint(w * 17592186044416.0);
   ++n; if (a != b) { if (bad < 5) std::printf("fix %.17g: %llu vs %llu\n", w, (unsigned long long)a, (unsigned long long)b); ++bad; }
 }
+static void check_recip(double x) {
+  const double want = 1.0 / x;
+  float s = (float)(1.0 / x);
+  float seeds[5] = {s, std::nextafterf(s, 0.0f), std::nextafterf(s, 1e30f),
+                    std::nextafterf(std::nextafterf(s, 0.0f), 0.0f),
+                    std::nextafterf(std::nextafterf(s, 1e30f), 1e30f)};
+  for (float sd : seeds) {
+    const double y = recip_refine(x, (double)sd);
+    uint64_t a, b; std::memcpy(&a, &y, 8); std::memcpy(&b, &want, 8);
+    const uint64_t ulps = a > b ? a - b : b - a;
+    ++n; if (ulps > 1) { if (bad < 5) std::printf("recip %.17g: %.17g vs %.17g\n", x, y, want); ++bad; }
+  }
+}
 int main() {
   std::mt19937_64 g(12345);
   std::uniform_real_distribution<double> u(0.0, 1.0);
@@ -60,6 +76,8 @@ int main() {
                    0.5, 1.0, std::nextafter(1.0, 0.0), 1.0000000000000002, 200.0, 255.999, 256.0,
                    1e6, -1e-15, -0.5})
     check_fix(w);
+  for (int t = 0; t < 1000000; ++t) check_recip(1.0 + 3.0 * u(g));
+  for (int t = 0; t < 1000000; ++t) check_recip(std::pow(10.0, -30.0 + 60.0 * u(g)));
   std::printf("checked %lld mismatches %lld\n", n, bad);
   return bad != 0;
 }
