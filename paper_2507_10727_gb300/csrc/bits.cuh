@@ -108,6 +108,23 @@ PIC_HD uint64_t fix44(double w) {
 #endif
 }
 
+// Comparisons on the bit patterns (integer pipes), with the IEEE outcome for
+// every input, NaN included (all false).  x < 0: sign set, magnitude nonzero
+// and not NaN.  x >= c for c > 0 finite: for non-negative x the bit patterns
+// order like the values; negative x and NaN give false.
+constexpr uint64_t kAbsMask = 0x7FFFFFFFFFFFFFFFULL;
+constexpr uint64_t kInfBits = 0x7FF0000000000000ULL;
+PIC_HD bool lt_zero(double x) {
+  const uint64_t b = bits_of(x), a = b & kAbsMask;
+  return (b >> 63) != 0 && a != 0 && a <= kInfBits;
+}
+PIC_HD bool ge_pos(double x, double c) {
+  const uint64_t b = bits_of(x);
+  return b >= bits_of(c) && b <= kInfBits;
+}
+// x > 0 for x known to be >= 0 or NaN (a sum of squares): true also for NaN
+PIC_HD bool nonzero_sq(double x) { return bits_of(x) != 0; }
+
 // 1 / x refined from a seed y whose relative error e satisfies |e| < 2^-20:
 // a Newton-Raphson step y <- y + y (1 - x y) turns the error e into -e^2, so
 // after two steps only the rounding of the last operations remains (within

@@ -317,7 +317,7 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
           y1 = vy * dt;
           z1 = z + vzn * dt;
           const double s2 = x1 * x1 + y1 * y1;
-          if (s2 > 0.0) {
+          if (nonzero_sq(s2)) {   // s2 > 0 (a NaN goes on and is flagged below)
             const double inv = rsqrt(s2);
             r1 = s2 * inv;
             vr = (x1 * vx + y1 * vy) * inv;
@@ -335,9 +335,9 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
           if (z1 < 0.0) { z1 = -z1; vz = -vz; }
           if (z1 >= I.L) { z1 = 2.0 * I.L - z1; vz = -vz; if (z1 >= I.L) z1 = nextafter(I.L, 0.0); }
           if (r1 >= I.R) { r1 = 2.0 * I.R - r1; vr = -vr; if (r1 >= I.R) r1 = nextafter(I.R, 0.0); }
-        } else if (z1 < 0.0 || z1 >= I.L || r1 >= I.R) {
+        } else if (lt_zero(z1) || ge_pos(z1, I.L) || ge_pos(r1, I.R)) {   // integer-pipe compares
           alive = false;
-          if (z1 < 0.0) {
+          if (lt_zero(z1)) {
             const double tc = z / (z - z1);
             const double xh = r + tc * (x1 - r), yh = tc * y1;
             const double rhit = sqrt(xh * xh + yh * yh);

@@ -8,6 +8,8 @@ runs both forms over random and edge-case inputs.
 * fix44(w): round-to-nearest-even of w 2^44 (llrint), for w in [0, 1]
   (random, exact ties at the 2^-45 grid, the neighbours of ties, tiny, 0, 1)
   and outside that range;
+* lt_zero, ge_pos: the IEEE comparisons x < 0 and x >= c over random,
+  signed-zero, subnormal, infinite and NaN inputs;
 * recip_refine(x, seed): within one ulp of 1.0 / x for seeds up to two FP32
   ulps from the rounded FP32 reciprocal (the device seed, PTX rcp.approx, is
   within one), x in [1, 4) and log-uniform over 1e-30 .. 1e30.
@@ -51,6 +53,10 @@ static void check_recip(double x) {
     ++n; if (ulps > 1) { if (bad < 5) std::printf("recip %.17g: %.17g vs %.17g\n", x, y, want); ++bad; }
   }
 }
+static void check_cmp(double x, double c) {
+  ++n; if (lt_zero(x) != (x < 0.0) || ge_pos(x, c) != (x >= c)) {
+    if (bad < 5) std::printf("cmp %.17g %.17g\n", x, c); ++bad; }
+}
 int main() {
   std::mt19937_64 g(12345);
   std::uniform_real_distribution<double> u(0.0, 1.0);
@@ -76,6 +82,12 @@ int main() {
                    0.5, 1.0, std::nextafter(1.0, 0.0), 1.0000000000000002, 200.0, 255.999, 256.0,
                    1e6, -1e-15, -0.5})
     check_fix(w);
+  for (double c : {0.05, 1e-300, 3.5, 1e300}) {
+    for (int t = 0; t < 200000; ++t) { double x = (u(g) - 0.5) * 4.0 * c; check_cmp(x, c); }
+    for (double x : {0.0, -0.0, 5e-324, -5e-324, c, -c, std::nextafter(c, 0.0), std::nextafter(c, 1e308),
+                     (double)INFINITY, -(double)INFINITY, (double)NAN, -(double)NAN, 1e308, -1e308})
+      check_cmp(x, c);
+  }
   for (int t = 0; t < 1000000; ++t) check_recip(1.0 + 3.0 * u(g));
   for (int t = 0; t < 1000000; ++t) check_recip(std::pow(10.0, -30.0 + 60.0 * u(g)));
   std::printf("checked %lld mismatches %lld\n", n, bad);
