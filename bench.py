@@ -41,7 +41,7 @@ UNIT = "particle-steps/s"
 # kernel (gather + Boris + move + frame rotation + cell location + deposit
 # weights), counted from the formulas (add/mul = 1, fma = 2, div/sqrt = 1);
 # the derivation is listed with the design notes.
-FLOPS_PER_PARTICLE = {0: 78.0, 1: 86.0}   # EC, MC
+FLOPS_PER_PARTICLE = {0: 73.0, 1: 81.0}   # EC, MC (h E and h B read from per-species tables)
 # Algorithmic HBM bytes of one particle-step: read and write r, z, v_r,
 # v_theta, v_z, id once (FP64).
 BYTES_PER_PARTICLE = 96.0

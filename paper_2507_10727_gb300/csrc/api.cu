@@ -286,8 +286,10 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
     I.stage_len = cmax < (1LL << 22) ? cmax : (1LL << 22);
     I.stage = (double*)chk(A((size_t)I.stage_len * 6 * 8));
   } else {
-    I.etab = (double4_32a*)chk(A((size_t)I.nkey * (c.gather == 0 ? 1 : 2) * sizeof(double4_32a)));
-    I.btab = (double4_32a*)chk(A((size_t)I.nkey * 2 * sizeof(double4_32a)));
+    for (int sp = 0; sp < 2; ++sp) {
+      I.etab[sp] = (double4_32a*)chk(A((size_t)I.nkey * (c.gather == 0 ? 1 : 2) * sizeof(double4_32a)));
+      I.btab[sp] = (double4_32a*)chk(A((size_t)I.nkey * 2 * sizeof(double4_32a)));
+    }
   }
   I.qhist = (double*)chk(A((size_t)c.n_avg * 8));
   const size_t ncell = (size_t)c.nr * c.nz;
@@ -359,7 +361,16 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
       bt32[k] = make_float4((float)bt[k].x, (float)bt[k].y, (float)bt[k].z, (float)bt[k].w);
     e = cudaMemcpyAsync(I.btab32, bt32.data(), bt32.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
   } else {
-    e = cudaMemcpyAsync(I.btab, bt.data(), bt.size() * sizeof(double4_32a), cudaMemcpyHostToDevice, st);
+    // one copy per species, scaled by h = q dt / (2 m): the push reads t = h B
+    for (int sp = 0; sp < 2 && e == cudaSuccess; ++sp) {
+      const double hs = 0.5 * I.qm[sp] * c.dt;
+      std::vector<double4_32a> bs(bt.size());
+      for (size_t k = 0; k < bt.size(); ++k)
+        bs[k] = make_d4(hs * bt[k].x, hs * bt[k].y, hs * bt[k].z, hs * bt[k].w);
+      e = cudaMemcpyAsync(I.btab[sp], bs.data(), bs.size() * sizeof(double4_32a),
+                          cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // bs is freed at the loop end
+    }
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "upload B table");
   Scalars s0;

@@ -202,8 +202,10 @@ struct Inst {
   double* phi;
   double* Q;
   unsigned long long* qacc[2];
-  double4_32a* etab;           // EC: 1 per cell {Er0, dEr/dfz, Ez0, dEz/dwr}; MC: 2 per cell
-  double4_32a* btab;           // 2 per cell: {Br c0..c3}, {Bz c0..c3}
+  // FP64 gather tables per species, scaled by that species' h = q dt / (2 m):
+  // the push reads h E and h B directly
+  double4_32a* etab[2];        // EC: 1 per cell {Er0, dEr/dfz, Ez0, dEz/dwr}; MC: 2 per cell
+  double4_32a* btab[2];        // 2 per cell: {Br c0..c3}, {Bz c0..c3}
   double* qhist;
   Scalars* S;
   DiagDev* diag;

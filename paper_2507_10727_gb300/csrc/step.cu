@@ -67,8 +67,14 @@ __global__ void k_field_tables(Inst I) {
         }
         t = make_d4(er_lo, er_hi - er_lo, ez_lo, ez_hi - ez_lo);
       }
-      if (I.prec32) I.etab32[key] = make_float4((float)t.x, (float)t.y, (float)t.z, (float)t.w);
-      else I.etab[key] = t;
+      if (I.prec32) {
+        I.etab32[key] = make_float4((float)t.x, (float)t.y, (float)t.z, (float)t.w);
+      } else {
+        for (int sp = 0; sp < 2; ++sp) {
+          const double hs = 0.5 * I.qm[sp] * I.dt;
+          I.etab[sp][key] = make_d4(hs * t.x, hs * t.y, hs * t.z, hs * t.w);
+        }
+      }
     } else {
       double er[2][2], ez[2][2];
       for (int a = 0; a < 2; ++a)
@@ -99,8 +105,11 @@ __global__ void k_field_tables(Inst I) {
         I.etab32[2 * key] = make_float4((float)tr.x, (float)tr.y, (float)tr.z, (float)tr.w);
         I.etab32[2 * key + 1] = make_float4((float)tz.x, (float)tz.y, (float)tz.z, (float)tz.w);
       } else {
-        I.etab[2 * key] = tr;
-        I.etab[2 * key + 1] = tz;
+        for (int sp = 0; sp < 2; ++sp) {
+          const double hs = 0.5 * I.qm[sp] * I.dt;
+          I.etab[sp][2 * key] = make_d4(hs * tr.x, hs * tr.y, hs * tr.z, hs * tr.w);
+          I.etab[sp][2 * key + 1] = make_d4(hs * tz.x, hs * tz.y, hs * tz.z, hs * tz.w);
+        }
       }
     }
     if (diag) {
@@ -250,8 +259,9 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
   const long long step = S->step;
   const bool diag = S->diag_on != 0;
   const ParticlesDev P = I.buf[SP][S->flip[SP]];
-  const double h = 0.5 * I.qm[SP] * I.dt;
   const double dt = I.dt;
+  const double4_32a* etab = I.etab[SP];   // h E, h B of this species (h = q dt / 2m)
+  const double4_32a* btab = I.btab[SP];
   const int lane = threadIdx.x & 31;
   double Kloc = 0.0;
   {
@@ -281,37 +291,36 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
           locate(r, I.inv_dr, I.nr, m, fr);
           locate(z, I.inv_dz, I.nz, nn, fz);
           const int ck = cell_key(I, m, nn);
-          // gather E
-          double Er, Ez;
+          // gather h E
+          double hEr, hEz;
           if (GATHER == 0) {
-            const double4_32a t = I.etab[ck];
+            const double4_32a t = etab[ck];
             const double wr = rweight_upper(I, r, m, fr);
-            Er = t.x + t.y * fz;
-            if (I.rweight == 1) Er *= r;
-            Ez = t.z + t.w * wr;
+            hEr = t.x + t.y * fz;
+            if (I.rweight == 1) hEr *= r;
+            hEz = t.z + t.w * wr;
           } else {
             const double wr = rweight_upper(I, r, m, fr);
-            const double4_32a a = I.etab[2 * ck];
-            const double4_32a b = I.etab[2 * ck + 1];
-            Er = a.x + wr * (a.y + fz * a.w) + fz * a.z;
-            Ez = b.x + wr * (b.y + fz * b.w) + fz * b.z;
+            const double4_32a a = etab[2 * ck];
+            const double4_32a b = etab[2 * ck + 1];
+            hEr = a.x + wr * (a.y + fz * a.w) + fz * a.z;
+            hEz = b.x + wr * (b.y + fz * b.w) + fz * b.z;
           }
-          // gather B (bilinear node table)
-          const double4_32a br = I.btab[2 * ck];
-          const double4_32a bz = I.btab[2 * ck + 1];
-          const double Br = br.x + fr * (br.y + fz * br.w) + fz * br.z;
-          const double Bz = bz.x + fr * (bz.y + fz * bz.w) + fz * bz.z;
+          // gather t = h B (bilinear node table)
+          const double4_32a br = btab[2 * ck];
+          const double4_32a bz = btab[2 * ck + 1];
+          const double tx = br.x + fr * (br.y + fz * br.w) + fz * br.z;
+          const double tz = bz.x + fr * (bz.y + fz * bz.w) + fz * bz.z;
           // Boris: half kick, rotation about B, half kick
-          const double ax = vr + h * Er, ay = vt, az = vz + h * Ez;
-          const double tx = h * Br, tz = h * Bz;
+          const double ax = vr + hEr, ay = vt, az = vz + hEz;
           const double f2 = 2.0 * recip(1.0 + tx * tx + tz * tz);   // 1 + t^2 >= 1
           const double sx = f2 * tx, sz = f2 * tz;
           const double px = ax + ay * tz;
           const double py = ay + (az * tx - ax * tz);
           const double pz = az - ay * tx;
-          const double vx = ax + py * sz + h * Er;
+          const double vx = ax + py * sz + hEr;
           const double vy = ay + (pz * sx - px * sz);
-          const double vzn = az - py * sx + h * Ez;
+          const double vzn = az - py * sx + hEz;
           // straight move, then rotate the frame onto the new radius
           x1 = r + vx * dt;
           y1 = vy * dt;
