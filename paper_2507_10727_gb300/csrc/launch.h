@@ -49,6 +49,9 @@ cudaError_t launch_thin32(const Inst& I, int sp, int factor, int num_sms, cudaSt
 cudaError_t launch_region_sample(const Inst& I, int num_sms, cudaStream_t st);
 cudaError_t launch_region_eval(const Inst& I, cudaStream_t st);
 
+// ids of the step's births (both species, both precisions)
+cudaError_t launch_births(const Inst& I, int num_sms, cudaStream_t st);
+
 // set the particle count of species sp (set-up)
 cudaError_t launch_set_n(const Inst& I, int sp, long long n, cudaStream_t st);
 
@@ -87,7 +90,6 @@ cudaError_t launch_unpack32(const Inst& I, int sp, long long offset, long long c
                             int num_sms, cudaStream_t st);
 cudaError_t launch_sort_species32(const Inst& I, int sp, int num_sms, cudaStream_t st);
 cudaError_t launch_deposit_all32(const Inst& I, int num_sms, cudaStream_t st);
-cudaError_t launch_births32(const Inst& I, cudaStream_t st);
 cudaError_t launch_scatter32(const Inst& I, int num_sms, cudaStream_t st);
 
 // compute node charge Q from the fixed-point sums (and clear them)

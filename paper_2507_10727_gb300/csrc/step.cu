@@ -489,40 +489,106 @@ __global__ void __launch_bounds__(kPushThreads, 2) k_push_all(const Inst* insts,
 }
 
 // ---------------------------------------------------------------------------
-// Births: sort each species' births by (parent id, kind) and hand out ids
-// next_id, next_id + 1, ... (electrons first, then ions).  One CTA; bitonic
-// sort in shared memory up to kSmemSort entries, in global scratch beyond.
+// Births: the births of a step get ids next_id, next_id + 1, ... in order of
+// (parent id, kind), electrons first, then ions.  Only each birth's rank is
+// needed: chunks of kBirthChunk keys are sorted in shared memory, one CTA per
+// chunk (k_births_sort); a birth's rank is its place in its own sorted chunk
+// plus, for every other chunk, the number of keys there below it (binary
+// search; the keys are distinct) (k_births_rank); next_id advances last
+// (k_births_commit).
 // ---------------------------------------------------------------------------
-constexpr int kSmemSort = 4096;
+constexpr int kBirthChunk = 8192;
+constexpr int kBirthSmem = kBirthChunk * (8 + 4);
 
-__global__ void __launch_bounds__(1024) k_births(Inst I) {
-  Scalars* S = I.S;
-  if (S->status & ST_FATAL) return;
-  __shared__ unsigned long long skey[kSmemSort];
-  __shared__ unsigned int sidx[kSmemSort];
-  long long base = S->next_id;
+__device__ __forceinline__ long long births_of(const Inst& I, int sp) {
+  const long long nb = I.S->nbirth[sp];
+  return nb < I.birth_cap ? nb : I.birth_cap;
+}
+
+__global__ void __launch_bounds__(1024) k_births_sort(Inst I) {
+  if (I.S->status & ST_FATAL) return;
+  extern __shared__ __align__(16) unsigned char bsm[];
+  unsigned long long* key = reinterpret_cast<unsigned long long*>(bsm);
+  unsigned int* idx = reinterpret_cast<unsigned int*>(key + kBirthChunk);
+  const long long c0 = (long long)blockIdx.x * kBirthChunk;
   for (int sp = 0; sp < 2; ++sp) {
-    const long long nb = S->nbirth[sp] < I.birth_cap ? S->nbirth[sp] : I.birth_cap;
-    if (nb == 0) continue;
+    const long long nb = births_of(I, sp);
+    if (c0 >= nb) continue;                          // uniform over the block
+    const int len = (int)(nb - c0 < kBirthChunk ? nb - c0 : kBirthChunk);
     int P = 1;
-    while (P < nb) P <<= 1;
-    unsigned long long* key = skey;
-    unsigned int* idx = sidx;
-    if (P > kSmemSort) {
-      key = I.births[sp].skey;
-      idx = I.births[sp].sidx;
-    }
+    while (P < len) P <<= 1;
+    const BirthsDev B = I.births[sp];
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
-      key[i] = i < nb ? I.births[sp].pkey[i] : ~0ULL;
-      idx[i] = (unsigned int)i;
+      key[i] = i < len ? B.pkey[c0 + i] : ~0ULL;
+      idx[i] = (unsigned int)(c0 + i);
     }
     __syncthreads();
     bitonic(key, idx, P);
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) I.births[sp].id[idx[i]] = base + i;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+      B.skey[c0 + i] = key[i];
+      B.sidx[c0 + i] = idx[i];
+    }
     __syncthreads();
-    base += nb;
   }
-  if (threadIdx.x == 0) S->next_id = base;
+}
+
+template <bool F32>
+__global__ void k_births_rank(Inst I) {
+  const Scalars* S = I.S;
+  if (S->status & ST_FATAL) return;
+  const long long nb0 = births_of(I, 0), nb1 = births_of(I, 1);
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nb0 + nb1;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int sp = e < nb0 ? 0 : 1;
+    const long long nb = sp == 0 ? nb0 : nb1, q = sp == 0 ? e : e - nb0;
+    const BirthsDev B = I.births[sp];
+    const unsigned long long k = B.skey[q];
+    const long long c = q / kBirthChunk;
+    long long rank = q - c * kBirthChunk;
+    for (long long o = 0; o < nb; o += kBirthChunk) {
+      if (o == c * kBirthChunk) continue;
+      long long lo = 0, hi = nb - o < kBirthChunk ? nb - o : kBirthChunk;   // keys below k
+      while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (B.skey[o + mid] < k) lo = mid + 1;
+        else hi = mid;
+      }
+      rank += lo;
+    }
+    const unsigned long long id =
+        (unsigned long long)(S->next_id + (sp == 0 ? 0 : nb0) + rank);
+    const unsigned int b = B.sidx[q];
+    if (F32) {
+      unsigned int* rec = reinterpret_cast<unsigned int*>(B.b32 + b);
+      rec[2] = (unsigned int)(id & 0xffffffffULL);
+      rec[3] = (unsigned int)(id >> 32);
+    } else {
+      B.id[b] = (long long)id;
+    }
+  }
+}
+
+__global__ void k_births_commit(Inst I) {
+  Scalars* S = I.S;
+  if (threadIdx.x == 0 && !(S->status & ST_FATAL))
+    S->next_id += births_of(I, 0) + births_of(I, 1);
+}
+
+cudaError_t launch_births(const Inst& I, int num_sms, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_births_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, kBirthSmem);
+    attr = true;
+  }
+  const int chunks = (int)((I.birth_cap + kBirthChunk - 1) / kBirthChunk);
+  k_births_sort<<<chunks > 0 ? chunks : 1, 1024, kBirthSmem, st>>>(I);
+  const long long work = 2 * I.birth_cap;
+  const int blocks = (int)((work + 255) / 256 < (long long)num_sms * 4 ? (work + 255) / 256
+                                                                       : (long long)num_sms * 4);
+  if (I.prec32) k_births_rank<true><<<blocks > 0 ? blocks : 1, 256, 0, st>>>(I);
+  else k_births_rank<false><<<blocks > 0 ? blocks : 1, 256, 0, st>>>(I);
+  k_births_commit<<<1, 32, 0, st>>>(I);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -1184,8 +1250,7 @@ cudaError_t launch_field_tables(const Inst& I, int num_sms, cudaStream_t st) {
 
 // births, scan, scatter, charge and circuit of one instance (after its push)
 cudaError_t launch_post_push(const Inst& I, int num_sms, cudaStream_t st) {
-  if (I.prec32) launch_births32(I, st);
-  else k_births<<<1, 1024, 0, st>>>(I);
+  launch_births(I, num_sms, st);
   k_scan<<<2, 1024, 0, st>>>(I, 0);
   if (I.prec32) launch_scatter32(I, num_sms, st);
   else k_scatter<<<dim3(num_sms * 8, 2), 256, 0, st>>>(I, 0);
@@ -1216,8 +1281,7 @@ cudaError_t launch_step(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_
   mk(G_PUSH, false);
   if (e0 != cudaSuccess) return e0;
   mk(G_BIRTHS, true);
-  if (I.prec32) launch_births32(I, st);
-  else k_births<<<1, 1024, 0, st>>>(I);
+  launch_births(I, num_sms, st);
   mk(G_BIRTHS, false);
   mk(G_SCAN, true);
   k_scan<<<2, 1024, 0, st>>>(I, 0);

@@ -452,44 +452,6 @@ __global__ void __launch_bounds__(kPush32Threads, 4) k_push32_all(const Inst* in
   }
 }
 
-// births: sort by (parent id, kind), ids into the records' id words
-constexpr int kSmemSort32 = 4096;
-
-__global__ void __launch_bounds__(1024) k_births32(Inst I) {
-  Scalars* S = I.S;
-  if (S->status & ST_FATAL) return;
-  __shared__ unsigned long long skey[kSmemSort32];
-  __shared__ unsigned int sidx[kSmemSort32];
-  long long base = S->next_id;
-  for (int sp = 0; sp < 2; ++sp) {
-    const long long nb = S->nbirth[sp] < I.birth_cap ? S->nbirth[sp] : I.birth_cap;
-    if (nb == 0) continue;
-    int P = 1;
-    while (P < nb) P <<= 1;
-    unsigned long long* key = skey;
-    unsigned int* idx = sidx;
-    if (P > kSmemSort32) {
-      key = I.births[sp].skey;
-      idx = I.births[sp].sidx;
-    }
-    for (int i = threadIdx.x; i < P; i += blockDim.x) {
-      key[i] = i < nb ? I.births[sp].pkey[i] : ~0ULL;
-      idx[i] = (unsigned int)i;
-    }
-    __syncthreads();
-    bitonic(key, idx, P);
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-      const unsigned long long id = (unsigned long long)(base + i);
-      uint4* rec = I.births[sp].b32 + idx[i];
-      reinterpret_cast<unsigned int*>(rec)[2] = (unsigned int)(id & 0xffffffffULL);
-      reinterpret_cast<unsigned int*>(rec)[3] = (unsigned int)(id >> 32);
-    }
-    __syncthreads();
-    base += nb;
-  }
-  if (threadIdx.x == 0) S->next_id = base;
-}
-
 __global__ void k_scatter32(Inst I, int sp0) {
   Scalars* S = I.S;
   if (S->status & ST_FATAL) return;
@@ -702,11 +664,6 @@ cudaError_t launch_push32_all(const Inst* d_insts, WorkQueue* q, int gather, int
     k_push32_all<0><<<resident_blocks((const void*)k_push32_all<0>, kPush32Threads, num_sms), kPush32Threads, 0, st>>>(d_insts, q, ppt);
   else
     k_push32_all<1><<<resident_blocks((const void*)k_push32_all<1>, kPush32Threads, num_sms), kPush32Threads, 0, st>>>(d_insts, q, ppt);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_births32(const Inst& I, cudaStream_t st) {
-  k_births32<<<1, 1024, 0, st>>>(I);
   return cudaGetLastError();
 }
 
