@@ -850,69 +850,99 @@ __global__ void k_region_phi(Inst I) {
 // starts at the first cell from there on with E_z = -d phi/dz >= 0 from the
 // cell's corner potentials; Section 5: a cell's electron temperature is
 // m_e (<|v|^2> - |<v>|^2) / (3 e) over its samples (at least two), a
-// region's the plain mean over its cells in the radial band).  One block;
-// columns in parallel, the final sums in column order.
-__global__ void k_region_eval(Inst I) {
+// region's the plain mean over its cells in the radial band).  One warp per
+// cell column (ballots find the edges, warp sums per region), then the sums
+// over columns in column order (k_region_total).
+__global__ void k_region_cols(Inst I) {
   const RegionDev R = I.reg;
   const int nr = I.nr, nz = I.nz, nz1 = nz + 1;
-  for (int m = threadIdx.x; m < nr; m += blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
+  const int warp = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwarp = (int)(((long long)gridDim.x * blockDim.x) >> 5);
+  for (int m = warp; m < nr; m += nwarp) {
     int ns = nz, nb = nz;
-    for (int n = 0; n < nz; ++n) {
+    for (int n0 = 0; n0 < nz; n0 += 32) {
+      const int n = n0 + lane;
       const size_t c = (size_t)m * nz + n;
-      if (2ULL * R.n[0][c] >= R.n[1][c]) {
-        ns = n;
+      const unsigned hit = __ballot_sync(full, n < nz && 2ULL * R.n[0][c] >= R.n[1][c]);
+      if (hit) {
+        ns = n0 + __ffs(hit) - 1;
         break;
       }
     }
-    for (int n = ns; n < nz; ++n) {
-      const double up = R.phi[m * nz1 + n + 1] + R.phi[(m + 1) * nz1 + n + 1];
-      const double lo = R.phi[m * nz1 + n] + R.phi[(m + 1) * nz1 + n];
-      if (up - lo <= 0.0) {
-        nb = n;
+    for (int n0 = ns; n0 < nz; n0 += 32) {
+      const int n = n0 + lane;
+      bool ok = false;
+      if (n < nz) {
+        const double up = R.phi[m * nz1 + n + 1] + R.phi[(m + 1) * nz1 + n + 1];
+        const double lo = R.phi[m * nz1 + n] + R.phi[(m + 1) * nz1 + n];
+        ok = up - lo <= 0.0;
+      }
+      const unsigned hit = __ballot_sync(full, ok);
+      if (hit) {
+        nb = n0 + __ffs(hit) - 1;
         break;
       }
     }
-    R.zs[m] = ns * I.dz;
-    R.zb[m] = nb * I.dz;
-    double* col = R.col + (size_t)m * 8;
-    for (int k = 0; k < 7; ++k) col[k] = 0.0;
+    double t[3] = {0.0, 0.0, 0.0}, cnt[3] = {0.0, 0.0, 0.0};
     const double rcen = (m + 0.5) * I.dr;
-    if (rcen < I.band_lo || rcen > I.band_hi) continue;
-    col[6] = 1.0;
-    for (int n = 0; n < nz; ++n) {
-      const size_t c = (size_t)m * nz + n;
-      const unsigned long long N = R.n[0][c];
-      if (N < 2ULL) continue;
-      const double Nd = (double)N;
-      const double* mo = R.mom + c * 4;
-      const double mr = mo[0] / Nd, mt = mo[1] / Nd, mz = mo[2] / Nd;
-      const double T = kMe * (mo[3] / Nd - (mr * mr + mt * mt + mz * mz)) / (3.0 * kQe);
-      const int reg = n < ns ? 0 : (n < nb ? 1 : 2);
-      col[reg] += T;
-      col[3 + reg] += 1.0;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t[3] = {0.0, 0.0, 0.0}, c[3] = {0.0, 0.0, 0.0}, zs = 0.0, zb = 0.0, ncol = 0.0;
-    for (int m = 0; m < nr; ++m) {
-      const double* col = R.col + (size_t)m * 8;
-      if (col[6] == 0.0) continue;
-      for (int k = 0; k < 3; ++k) {
-        t[k] += col[k];
-        c[k] += col[3 + k];
+    const bool band = !(rcen < I.band_lo || rcen > I.band_hi);
+    if (band) {
+      for (int n = lane; n < nz; n += 32) {
+        const size_t c = (size_t)m * nz + n;
+        const unsigned long long N = R.n[0][c];
+        if (N < 2ULL) continue;
+        const double Nd = (double)N;
+        const double* mo = R.mom + c * 4;
+        const double mr = mo[0] / Nd, mt = mo[1] / Nd, mz = mo[2] / Nd;
+        const double T = kMe * (mo[3] / Nd - (mr * mr + mt * mt + mz * mz)) / (3.0 * kQe);
+        const int reg = n < ns ? 0 : (n < nb ? 1 : 2);
+        t[reg] += T;
+        cnt[reg] += 1.0;
       }
-      zs += R.zs[m];
-      zb += R.zb[m];
-      ncol += 1.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          t[k] += __shfl_xor_sync(full, t[k], o);
+          cnt[k] += __shfl_xor_sync(full, cnt[k], o);
+        }
     }
-    for (int k = 0; k < 3; ++k) {
-      R.out[k] = c[k] > 0.0 ? t[k] / c[k] : 0.0;
-      R.out[3 + k] = c[k];
+    if (lane == 0) {
+      R.zs[m] = ns * I.dz;
+      R.zb[m] = nb * I.dz;
+      double* col = R.col + (size_t)m * 8;
+      for (int k = 0; k < 3; ++k) {
+        col[k] = t[k];
+        col[3 + k] = cnt[k];
+      }
+      col[6] = band ? 1.0 : 0.0;
     }
-    R.out[6] = ncol > 0.0 ? zs / ncol : 0.0;
-    R.out[7] = ncol > 0.0 ? zb / ncol : 0.0;
   }
+}
+
+__global__ void k_region_total(Inst I) {
+  if (threadIdx.x != 0) return;
+  const RegionDev R = I.reg;
+  double t[3] = {0.0, 0.0, 0.0}, c[3] = {0.0, 0.0, 0.0}, zs = 0.0, zb = 0.0, ncol = 0.0;
+  for (int m = 0; m < I.nr; ++m) {
+    const double* col = R.col + (size_t)m * 8;
+    if (col[6] == 0.0) continue;
+    for (int k = 0; k < 3; ++k) {
+      t[k] += col[k];
+      c[k] += col[3 + k];
+    }
+    zs += R.zs[m];
+    zb += R.zb[m];
+    ncol += 1.0;
+  }
+  for (int k = 0; k < 3; ++k) {
+    R.out[k] = c[k] > 0.0 ? t[k] / c[k] : 0.0;
+    R.out[3 + k] = c[k];
+  }
+  R.out[6] = ncol > 0.0 ? zs / ncol : 0.0;
+  R.out[7] = ncol > 0.0 ? zb / ncol : 0.0;
 }
 
 // n = n_next after a set-up sort (no births)
@@ -1214,7 +1244,8 @@ cudaError_t launch_region_sample(const Inst& I, int num_sms, cudaStream_t st) {
 }
 
 cudaError_t launch_region_eval(const Inst& I, cudaStream_t st) {
-  k_region_eval<<<1, 256, 0, st>>>(I);
+  k_region_cols<<<(I.nr + 7) / 8, 256, 0, st>>>(I);   // one warp per cell column
+  k_region_total<<<1, 32, 0, st>>>(I);
   return cudaGetLastError();
 }
 
