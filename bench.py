@@ -41,6 +41,9 @@ UNIT = "particle-steps/s"
 # kernel (gather + Boris + move + frame rotation + cell location + deposit
 # weights), counted from the formulas (add/mul = 1, fma = 2, div/sqrt = 1);
 # the derivation is listed with the design notes.
+# kernels of one step of one discharge: field tables, queue set-up, push,
+# births (sort, rank, commit), scan, scatter, charge, circuit, Poisson, step end
+KERNELS_PER_STEP = 12
 FLOPS_PER_PARTICLE = {0: 73.0, 1: 81.0}   # EC, MC (h E and h B read from per-species tables)
 # Algorithmic HBM bytes of one particle-step: read and write r, z, v_r,
 # v_theta, v_z, id once (FP64).
@@ -715,7 +718,7 @@ def main():
                 "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
                 "data": "synthetic", "config": config_block(p, n, args),
-                "gpu_launches": args.steps * 10, "cuda_graph": pg.pic_uses_graph(h),
+                "gpu_launches": args.steps * KERNELS_PER_STEP, "cuda_graph": pg.pic_uses_graph(h),
                 "autotune_steps": AUTOTUNE_STEPS, "push_particles_per_thread": pg.pic_tuned_chunk(h),
                 "poisson": {"iters_last_step": d1["poisson_iters"],
                             "resid_last_step": d1["poisson_resid"],
