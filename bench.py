@@ -410,6 +410,21 @@ def run_learned(args, torch, pg):
 
     plain = measure(False)
     warm = measure(True)
+
+    # cold starts (no previous solution: phi set to zero before the step), the
+    # case the network is for; consecutive steps alternate plain / warm
+    nodes = np.zeros((p["nr"] + 1, p["nz"] + 1))
+    cold = {"plain_iters": [], "warm_iters": [], "warm_starts_network": 0}
+    for _ in range(3):
+        for on in (False, True):
+            pg.pic_unet_warm_start(h, on)
+            pg.pic_set_phi(h, 0, nodes)
+            s0 = pg.pic_unet_stats(h)
+            pg.pic_step(h, 1)
+            s1 = pg.pic_unet_stats(h)
+            cold["warm_iters" if on else "plain_iters"].append(s1["poisson_iters"] - s0["poisson_iters"])
+            if on:
+                cold["warm_starts_network"] += s1["starts_network"] - s0["starts_network"]
     line = {"metric": METRIC, "value": warm["value"], "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": warm["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -421,7 +436,7 @@ def run_learned(args, torch, pg):
                        "snapshots": args.snapshots, "train_iters": args.train_iters,
                        "train_batch": args.train_batch, "poisson_tol": p["poisson_tol"],
                        "l2": "inputs larger than L2"},
-            "plain": plain, "warm": warm,
+            "plain": plain, "warm": warm, "cold_start": cold,
             "training": {"loss_first": loss0, "loss_last": loss1, "seconds": t_train,
                          "record_seconds": t_rec, "stats": pg.pic_unet_stats(h)}}
     print(json.dumps(line), flush=True)
