@@ -144,3 +144,50 @@ def test_mixed_grid_ensemble_equals_individual_runs(pg):
             for q in a:
                 assert np.array_equal(a[q], b[q]), (k, sp, q)
         assert np.array_equal(pg.pic_get_fields(ens, k)["phi"], pg.pic_get_fields(one, 0)["phi"])
+
+
+def test_reweight_and_region_diagnostics_per_instance(pg):
+    """Re-weighting one instance of an ensemble and sampling the region
+    diagnostics of every instance give what the same discharges give one by
+    one: particles, edges, cell counts and the ion histogram bit for bit; the
+    temperatures to rounding (the velocity sums of a cell follow the order of
+    its particles, which the cell sort does not fix)."""
+    insts = _instances()
+    for p, _ in insts:
+        p.update(band_r_lo=0.006, band_r_hi=0.012, ied_bins=32, ied_emax=512.0)
+    ens = pg.pic_create([p for p, _ in insts])
+    for k, (p, parts) in enumerate(insts):
+        _load(pg, ens, k, parts)
+        pg.pic_solve_fields(ens, k)
+    pg.pic_step(ens, 3)
+    pg.pic_reweight(ens, 2, 3)
+    for _ in range(3):
+        pg.pic_step(ens, 1)
+        for k in range(len(insts)):
+            pg.pic_region_sample(ens, k)
+    for k, (p, parts) in enumerate(insts):
+        one = pg.pic_create(p)
+        _load(pg, one, 0, parts)
+        pg.pic_solve_fields(one, 0)
+        pg.pic_step(one, 3)
+        if k == 2:
+            pg.pic_reweight(one, 0, 3)
+        for _ in range(3):
+            pg.pic_step(one, 1)
+            pg.pic_region_sample(one, 0)
+        for sp in (0, 1):
+            a = sort_by_id(pg.pic_get_particles(ens, k, sp))
+            b = sort_by_id(pg.pic_get_particles(one, 0, sp))
+            for q in a:
+                assert np.array_equal(a[q], b[q]), (k, sp, q)
+        ra, rb = pg.pic_region_read(ens, k), pg.pic_region_read(one, 0)
+        assert ra["samples"] == rb["samples"] == 3
+        for key in ("ncell", "z_sheath", "z_bulk", "ion_impacts", "ied_overflow"):
+            assert ra[key] == rb[key], (k, key)
+        assert ra["Te"] == pytest.approx(rb["Te"], rel=1e-12), k
+        for key in ("zs", "zb", "ied"):
+            assert np.array_equal(ra[key], rb[key]), (k, key)
+        assert pg.pic_diagnostics(ens, k)["weight"] == pg.pic_diagnostics(one, 0)["weight"]
+        pg.pic_destroy(one)
+    assert pg.pic_diagnostics(ens, 2)["weight"] == 3 * insts[2][0]["weight"]
+    pg.pic_destroy(ens)
