@@ -316,10 +316,10 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
           const double f2 = 2.0 * recip(1.0 + tx * tx + tz * tz);   // 1 + t^2 >= 1
           const double sx = f2 * tx, sz = f2 * tz;
           const double px = ax + ay * tz;
-          const double py = ay + (az * tx - ax * tz);
+          const double py = fma(az, tx, fma(-ax, tz, ay));   // ay + (az tx - ax tz), two FMAs
           const double pz = az - ay * tx;
           const double vx = ax + py * sz + hEr;
-          const double vy = ay + (pz * sx - px * sz);
+          const double vy = fma(pz, sx, fma(-px, sz, ay));   // ay + (pz sx - px sz)
           const double vzn = az - py * sx + hEz;
           // straight move, then rotate the frame onto the new radius
           x1 = r + vx * dt;
