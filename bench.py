@@ -42,8 +42,13 @@ UNIT = "particle-steps/s"
 # weights), counted from the formulas (add/mul = 1, fma = 2, div/sqrt = 1);
 # the derivation is listed with the design notes.
 # kernels of one step of one discharge: field tables, queue set-up, push,
-# births (sort, rank, commit), scan, scatter, charge, circuit, Poisson, step end
+# births (sort, rank, commit), scan, scatter, charge, circuit, Poisson, step end,
+# and the births append when full sorts are periodic
 KERNELS_PER_STEP = 12
+# full cell sort period of the default runs (256 x 256, 4e7 per species,
+# measured: FP64 6.19e9 / 6.74e9 / 6.83e9 particle-steps/s at 1 / 8 / 16;
+# FP32 2.35e10 / 2.53e10 / 2.60e10 at 1 / 2 / 4)
+SORT_EVERY_DEFAULT = {"fp64": 16, "fp32": 4}
 FLOPS_PER_PARTICLE = {0: 73.0, 1: 81.0}   # EC, MC (h E and h B read from per-species tables)
 # Algorithmic HBM bytes of one particle-step: read and write r, z, v_r,
 # v_theta, v_z, id once (FP64).
@@ -84,6 +89,10 @@ def parse():
                          "SEY x R_ext ensemble on 128x128 grids; learned: the 256x512 "
                          "discharge with and without the learned Poisson warm start; unet: "
                          "the warm-start network alone on the 257x513 node grid")
+    ap.add_argument("--sort-every", type=int, default=None,
+                    help="full cell sort every this many steps (births appended in place "
+                         "between; results do not depend on it); default 16 for fp64, "
+                         "4 for fp32 (the fastest measured)")
     ap.add_argument("--geometry", default="rz256", choices=["rz256", "paper"],
                     help="rz256 workload's chamber: rz256 = 5 x 5 cm, cathode disk r <= 2 cm, "
                          "other walls grounded; paper = the 3 x 3 cm chamber of Section 3 "
@@ -100,7 +109,10 @@ def parse():
                     help="precision: steps of the closed-system energy runs")
     ap.add_argument("--steady-steps", type=int, default=20000,
                     help="precision: steps of the FP64 / FP32 discharge comparison")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.sort_every is None:
+        args.sort_every = SORT_EVERY_DEFAULT[args.precision]
+    return args
 
 
 def workload(args):
@@ -114,6 +126,7 @@ def workload(args):
     p = pic_inputs.with_capacity(p, parts, factor=1.25, births=1 << 20)
     p["diag_every"] = 10      # diagnostics reduction every 10 steps
     p["precision"] = 1 if args.precision == "fp32" else 0
+    p["sort_every"] = args.sort_every
     return p, parts
 
 
@@ -124,6 +137,7 @@ def config_block(p, n, args):
             "n_per_species": n, "gather": args.gather.upper() + "-PIC",
             "precision": args.precision, "circuit": {"Vs": p["Vs"], "Rext": p["Rext"]},
             "dt": p["dt"], "poisson_tol": p["poisson_tol"], "diag_every": p["diag_every"],
+            "sort_every": p["sort_every"],
             "insulating_boundary": {"z0_outside_cathode": p["gap_neumann"],
                                     "wall_r_R": p["wall_neumann"]},
             "l2": "inputs larger than L2 (particle state 3.8 GB >> 129 MB)"}
@@ -281,6 +295,7 @@ def sweep_workload(args):
         p = pic_inputs.with_capacity(p, parts, factor=1.25, births=1 << 18)
         p["diag_every"] = 10
         p["precision"] = 1 if args.precision == "fp32" else 0
+        p["sort_every"] = args.sort_every
         out.append((p, parts))
     return out
 
@@ -339,7 +354,7 @@ def run_sweep(args, torch, pg):
             "warmup": warm, "ms_per_step": ms_e / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
-            "config": {"workload": f"sweep16_rz128_{args.precision}",
+            "config": {"workload": f"sweep16_rz128_{args.precision}", "sort_every": args.sort_every,
                        "instances": len(insts), "grid": [128, 128], "domain_m": [0.05, 0.05],
                        "particles_per_species": [parts["e"]["r"].shape[0] for _, parts in insts],
                        "total_particles": ntot,
@@ -363,6 +378,7 @@ def run_learned(args, torch, pg):
     p = pic_inputs.with_capacity(p, parts, factor=1.25, births=1 << 20)
     p["diag_every"] = 10
     p["precision"] = 1 if args.precision == "fp32" else 0
+    p["sort_every"] = args.sort_every
     h = pg.pic_create(p)
     for k, sp in (("e", 0), ("i", 1)):
         pg.pic_set_particles(h, 0, sp, parts[k])
@@ -435,6 +451,7 @@ def run_learned(args, torch, pg):
                        "n_per_species": n, "unet_mode": args.unet_mode,
                        "snapshots": args.snapshots, "train_iters": args.train_iters,
                        "train_batch": args.train_batch, "poisson_tol": p["poisson_tol"],
+                       "sort_every": p["sort_every"],
                        "l2": "inputs larger than L2"},
             "plain": plain, "warm": warm, "cold_start": cold,
             "training": {"loss_first": loss0, "loss_last": loss1, "seconds": t_train,
@@ -733,7 +750,8 @@ def main():
                 "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
                 "data": "synthetic", "config": config_block(p, n, args),
-                "gpu_launches": args.steps * KERNELS_PER_STEP, "cuda_graph": pg.pic_uses_graph(h),
+                "gpu_launches": args.steps * (KERNELS_PER_STEP + (1 if args.sort_every > 1 else 0)),
+                "cuda_graph": pg.pic_uses_graph(h),
                 "autotune_steps": AUTOTUNE_STEPS, "push_particles_per_thread": pg.pic_tuned_chunk(h),
                 "poisson": {"iters_last_step": d1["poisson_iters"],
                             "resid_last_step": d1["poisson_resid"],

@@ -93,7 +93,13 @@ typedef struct pic_config {
   int64_t cap_e, cap_i;      /* particle capacities per species */
   int64_t birth_cap;         /* births per species per step */
   int32_t diag_every;        /* diagnostics are accumulated on steps that are multiples */
-  int32_t sort_every;        /* cell sort period in steps (1 = every step) */
+  int32_t sort_every;        /* full cell sort every this many steps (1..64); on the steps
+                                between, absorbed particles stay as dead slots and births
+                                are appended in place (a full sort also runs whenever the
+                                appended births would not fit).  Results do not depend on
+                                it (FP64 bit for bit); calls that read or replace particles
+                                (pic_count, pic_get_particles, pic_set_particles, pic_save,
+                                pic_solve_fields, pic_region_sample) compact first. */
   double n_meta;             /* metastable Ar* density (m^-3), a constant background; 0 = off */
   double meta_a, meta_I;     /* stepwise ionization (1d) from Ar*: sigma = meta_a ln(E/meta_I)/(E meta_I)
                                 (m^2 eV^2, eV; Section 3: threshold 4.20 eV) */

@@ -129,7 +129,7 @@ std::string validate(const pic_config& c) {
   if (c.cap_e >= (1LL << 31) || c.cap_i >= (1LL << 31) || c.birth_cap >= (1LL << 30))
     return "capacities must stay below 2^31 (2^30 births)";
   if (c.precision != 0 && c.precision != 1) return "precision must be 0 (FP64) or 1 (FP32 particles)";
-  if (c.sort_every != 1) return "sort_every must be 1";
+  if (c.sort_every < 1 || c.sort_every > 64) return "sort_every must be in [1, 64]";
   if (c.gather < 0 || c.gather > 1 || c.rweight < 0 || c.rweight > 1) return "gather/rweight";
   if (c.circuit_mode < 0 || c.circuit_mode > 1 || c.b_mode < 0 || c.b_mode > 1) return "modes";
   if (!(c.poisson_tol > 0) || c.poisson_max_iter < 1) return "poisson_tol/max_iter";
@@ -177,6 +177,7 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
   I.m_cath = -1;
   for (int m = 0; m <= c.nr; ++m)
     if (m * I.dr <= c.Rc && m < c.nr) I.m_cath = m;
+  I.sort_every = c.sort_every;
   I.bc_g = c.gap_neumann ? I.m_cath + 1 : c.nr + 1;
   I.bc_wall = c.wall_neumann ? 1 : 0;
   I.band_lo = c.band_r_lo;
@@ -507,6 +508,20 @@ void pic_destroy(pic_handle* h) {
 
 const char* pic_last_error(const pic_handle* h) { return h ? h->err.c_str() : "null handle"; }
 
+// Between full sorts (sort_every > 1) the particle arrays hold dead slots and
+// appended births; calls that read or replace particles first compact and
+// sort them (the thinning kernels with factor 1 keep every live particle).
+static int ensure_sorted(pic_handle* h, int instance) {
+  Scalars s;
+  const int rc = read_status(h, instance, &s);
+  if (rc != PIC_OK && rc != PIC_ERR_NONCONVERGED) return rc;
+  if (!s.unsorted) return PIC_OK;
+  cudaError_t e = launch_thin(h->inst[instance].I, 1, h->num_sms, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "compaction");
+  return read_status(h, instance, nullptr);
+}
+
 int pic_set_particles(pic_handle* h, int instance, int species, int64_t n, const double* r,
                       const double* z, const double* vr, const double* vt, const double* vz,
                       const int64_t* id, int on_device) {
@@ -516,6 +531,10 @@ int pic_set_particles(pic_handle* h, int instance, int species, int64_t n, const
   if (n > ih.I.cap[species]) return fail(h, PIC_ERR_CAPACITY, "n exceeds the species capacity");
   if (n > 0 && (!r || !z || !vr || !vt || !vz || !id))
     return fail(h, PIC_ERR_INVALID, "null array");
+  {
+    const int rc = ensure_sorted(h, instance);   // the other species must be compact too
+    if (rc != PIC_OK && rc != PIC_ERR_NONCONVERGED) return rc;
+  }
   cudaStream_t st = h->stream;
   cudaError_t e = cudaSuccess;
   if (ih.I.prec32) {
@@ -566,6 +585,10 @@ int pic_set_particles(pic_handle* h, int instance, int species, int64_t n, const
 int pic_count(pic_handle* h, int instance, int species, int64_t* n_out) {
   if (bad_instance(h, instance) || species < 0 || species > 1 || !n_out)
     return fail(h, PIC_ERR_INVALID, "bad argument");
+  {
+    const int rc = ensure_sorted(h, instance);
+    if (rc != PIC_OK && rc != PIC_ERR_NONCONVERGED) return rc;
+  }
   Scalars s;
   const int rc = read_status(h, instance, &s);
   *n_out = s.n[species];
@@ -621,6 +644,10 @@ int pic_get_particles(pic_handle* h, int instance, int species, double* r, doubl
 
 int pic_solve_fields(pic_handle* h, int instance) {
   if (bad_instance(h, instance)) return fail(h, PIC_ERR_INVALID, "bad instance");
+  {
+    const int rc = ensure_sorted(h, instance);
+    if (rc != PIC_OK && rc != PIC_ERR_NONCONVERGED) return rc;
+  }
   InstHost& ih = h->inst[instance];
   cudaError_t e = launch_solve_fields(ih.I, ih.pw, h->num_sms, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "solve_fields");
@@ -967,6 +994,10 @@ int pic_reweight(pic_handle* h, int instance, int factor) {
 // ---------------------------------------------------------------------------
 int pic_region_sample(pic_handle* h, int instance) {
   if (bad_instance(h, instance)) return fail(h, PIC_ERR_INVALID, "bad instance");
+  {
+    const int rc = ensure_sorted(h, instance);   // the sampler walks the cell bins
+    if (rc != PIC_OK && rc != PIC_ERR_NONCONVERGED) return rc;
+  }
   const cudaError_t e = launch_region_sample(h->inst[instance].I, h->num_sms, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "region sample");
   return PIC_OK;
@@ -1017,14 +1048,16 @@ int pic_region_reset(pic_handle* h, int instance) {
 
 // ---------------------------------------------------------------------------
 // checkpoints: a flat little-endian file
-//   "PICCKPT2", pic_config, Scalars, qhist[n_avg], phi[nodes],
+//   "PICCKPT3", pic_config, Scalars, qhist[n_avg], phi[nodes],
 //   then per species: n, r[n], z[n], vr[n], vt[n], vz[n], id[n]
 // ---------------------------------------------------------------------------
 int pic_save(pic_handle* h, int instance, const char* path) {
   if (bad_instance(h, instance) || !path) return fail(h, PIC_ERR_INVALID, "bad argument");
   InstHost& ih = h->inst[instance];
   Scalars s;
-  int rc = read_status(h, instance, &s);
+  int rc = ensure_sorted(h, instance);
+  if (rc != PIC_OK) return rc;
+  rc = read_status(h, instance, &s);
   if (rc != PIC_OK) return rc;
   const pic_config& c = ih.cfg;
   const size_t nn = (size_t)(c.nr + 1) * (c.nz + 1);
@@ -1034,7 +1067,7 @@ int pic_save(pic_handle* h, int instance, const char* path) {
   if (e != cudaSuccess) return cuda_fail(h, e, "save copy");
   FILE* f = std::fopen(path, "wb");
   if (!f) return fail(h, PIC_ERR_IO, std::string("cannot open ") + path);
-  bool ok = std::fwrite("PICCKPT2", 1, 8, f) == 8;
+  bool ok = std::fwrite("PICCKPT3", 1, 8, f) == 8;
   ok = ok && std::fwrite(&c, sizeof(c), 1, f) == 1;
   ok = ok && std::fwrite(&s, sizeof(s), 1, f) == 1;
   ok = ok && std::fwrite(qh.data(), 8, qh.size(), f) == qh.size();
@@ -1082,7 +1115,7 @@ int pic_load(pic_handle* h, int instance, const char* path) {
   Scalars s;
   const size_t nn = (size_t)(c.nr + 1) * (c.nz + 1);
   std::vector<double> qh((size_t)c.n_avg), phi(nn);
-  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "PICCKPT2", 8) == 0;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "PICCKPT3", 8) == 0;
   ok = ok && std::fread(&fc, sizeof(fc), 1, f) == 1;
   ok = ok && fc.nr == c.nr && fc.nz == c.nz && fc.n_avg == c.n_avg && fc.precision == c.precision;
   ok = ok && std::fread(&s, sizeof(s), 1, f) == 1;
@@ -1136,6 +1169,9 @@ int pic_load(pic_handle* h, int instance, const char* path) {
   s.n[1] = ih.I.prec32 ? n[1] : cur.n[1];
   s.flip[0] = cur.flip[0];   // the particles were placed in this handle's current buffers
   s.flip[1] = cur.flip[1];
+  s.n_live[0] = s.n[0];      // checkpoints hold compact arrays
+  s.n_live[1] = s.n[1];
+  s.unsorted = 0;
   cudaError_t e = cudaMemcpy(ih.I.S, &s, sizeof(s), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ih.I.qhist, qh.data(), qh.size() * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ih.I.phi, phi.data(), nn * 8, cudaMemcpyHostToDevice);

@@ -92,6 +92,9 @@ struct Scalars {
   int pad1[2];
   unsigned long long cnt_ionize_meta;   // stepwise ionizations from Ar* (1d) this step
   long long ppc_max[2];    // most particles in one cell, from the last sort's histogram
+  long long n_live[2];     // live particles (n also counts the dead slots between sorts)
+  int unsorted;            // 1: the arrays hold dead slots and appended births (no sort yet)
+  int pad2;
 };
 
 struct DiagDev {           // mirrors pic_diag
@@ -172,6 +175,7 @@ struct Inst {
   unsigned long long seed;
   // switches
   int gather, rweight, mcc_on, push_on, field_on, walls_reflect, circuit_mode, n_avg;
+  int sort_every;          // full cell sort every this many steps (others append in place)
   int bc_g;                // first insulating node of row z = 0 (nr + 1: none)
   int bc_wall;             // 1: the wall r = R is insulating
   // region diagnostics: radial band (m), ion energy histogram bins of width ied_de (eV)
@@ -210,6 +214,18 @@ struct Inst {
   Scalars* S;
   DiagDev* diag;
 };
+
+// Whether this step ends with the full cell sort: every sort_every-th step,
+// and whenever appending the births in place would overflow a buffer.  The
+// scatter and the step-end kernel take the same decision from the same state.
+__device__ __forceinline__ bool sort_this_step(const Inst& I, const Scalars* S) {
+  if (I.sort_every <= 1 || (S->step + 1) % I.sort_every == 0) return true;
+  for (int sp = 0; sp < 2; ++sp) {
+    const long long nb = S->nbirth[sp] < I.birth_cap ? S->nbirth[sp] : I.birth_cap;
+    if (S->n[sp] + nb > I.cap[sp]) return true;
+  }
+  return false;
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11)

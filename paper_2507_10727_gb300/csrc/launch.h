@@ -91,6 +91,7 @@ cudaError_t launch_unpack32(const Inst& I, int sp, long long offset, long long c
 cudaError_t launch_sort_species32(const Inst& I, int sp, int num_sms, cudaStream_t st);
 cudaError_t launch_deposit_all32(const Inst& I, int num_sms, cudaStream_t st);
 cudaError_t launch_scatter32(const Inst& I, int num_sms, cudaStream_t st);
+cudaError_t launch_append32(const Inst& I, int num_sms, cudaStream_t st);
 
 // compute node charge Q from the fixed-point sums (and clear them)
 cudaError_t launch_charge(const Inst& I, cudaStream_t st);

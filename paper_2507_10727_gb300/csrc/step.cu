@@ -281,7 +281,11 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
       int newkey = -1;
       unsigned long long w00 = 0ULL, w10 = 0ULL, w01 = 0ULL, w11 = 0ULL;
       int dm = 0, dn = 0;
-      if (i < n) {
+      // between full sorts the arrays hold dead slots, marked by r = -1
+      const bool live = i < n && (long long)bits_of(P.r[i]) >= 0;
+      if (!live) {
+        if (i < n) I.key[SP][i] = -1;
+      } else {
         double r = P.r[i], z = P.z[i], vr = P.vr[i], vt = P.vt[i], vz = P.vz[i];
         const double v2old = vr * vr + vt * vt + vz * vz;
         double x1 = r, y1 = 0.0, r1 = r, z1 = z;
@@ -396,6 +400,8 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
           w11 = f.w11;
           dm = m1;
           dn = n1;
+        } else {
+          P.r[i] = -1.0;   // dead slot until the next full sort
         }
         I.key[SP][i] = newkey;
       }
@@ -656,9 +662,10 @@ __global__ void __launch_bounds__(1024) k_scan(Inst I, int sp0) {
 
 // ---------------------------------------------------------------------------
 // Counting-sort scatter cur -> nxt of the surviving particles and the
-// births (blockIdx.y = species).
+// births (blockIdx.y = species).  per_step: on a step without the full sort
+// (sort_this_step) the births are appended to the current arrays instead.
 // ---------------------------------------------------------------------------
-__global__ void k_scatter(Inst I, int sp0) {
+__global__ void k_scatter(Inst I, int sp0, int per_step) {
   Scalars* S = I.S;
   if (S->status & ST_FATAL) return;
   const int sp = sp0 + blockIdx.y;
@@ -668,6 +675,7 @@ __global__ void k_scatter(Inst I, int sp0) {
   const int fl = S->flip[sp];
   const ParticlesDev src = I.buf[sp][fl], dst = I.buf[sp][fl ^ 1];
   const BirthsDev B = I.births[sp];
+  if (per_step && !sort_this_step(I, S)) return;   // k_append does this step
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -694,6 +702,25 @@ __global__ void k_scatter(Inst I, int sp0) {
         dst.id[pos] = B.id[b];
       }
     }
+  }
+}
+
+// On a step without the full sort the births go to the end of the current
+// arrays (blockIdx.y = species); sort_this_step checked that they fit.
+__global__ void k_append(Inst I) {
+  const Scalars* S = I.S;
+  if ((S->status & ST_FATAL) || sort_this_step(I, S)) return;
+  const int sp = blockIdx.y;
+  const long long n_old = S->n[sp];
+  const long long nb = S->nbirth[sp] < I.birth_cap ? S->nbirth[sp] : I.birth_cap;
+  const ParticlesDev P = I.buf[sp][S->flip[sp]];
+  const BirthsDev B = I.births[sp];
+  for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
+       b += (long long)gridDim.x * blockDim.x) {
+    const long long j = n_old + b;
+    P.r[j] = B.r[b]; P.z[j] = B.z[b];
+    P.vr[j] = B.vr[b]; P.vt[j] = B.vt[b]; P.vz[j] = B.vz[b];
+    P.id[j] = B.id[b];
   }
 }
 
@@ -763,7 +790,9 @@ __global__ void k_thin(Inst I, int sp, int factor) {
     const long long i = base + lane;
     int key = -1;
     if (i < n) {
-      if (thin_keep(I, sp, P.id[i], s, factor)) {
+      // dead slots (r = -1) go; factor 1 keeps every live particle (compaction)
+      const bool dead = (long long)bits_of(P.r[i]) < 0;
+      if (!dead && (factor == 1 || thin_keep(I, sp, P.id[i], s, factor))) {
         int m, nn;
         double f;
         locate(P.r[i], I.inv_dr, I.nr, m, f);
@@ -945,17 +974,20 @@ __global__ void k_region_total(Inst I) {
   R.out[7] = ncol > 0.0 ? zb / ncol : 0.0;
 }
 
-// n = n_next after a set-up sort (no births)
+// n = n_next after a set-up sort (no births); the arrays are compact
 __global__ void k_commit_n(Inst I, int sp) {
   if (threadIdx.x == 0 && !(I.S->status & ST_FATAL)) {
     I.S->n[sp] = I.S->n_next[sp];
+    I.S->n_live[sp] = I.S->n_next[sp];
     I.S->flip[sp] ^= 1;
+    if (sp == 1) I.S->unsorted = 0;   // sorts of both species run species 0 first
   }
 }
 
 __global__ void k_set_n(Inst I, int sp, long long n) {
   if (threadIdx.x == 0) {
     I.S->n[sp] = n;
+    I.S->n_live[sp] = n;
     I.S->nbirth[sp] = 0;
   }
 }
@@ -1108,15 +1140,22 @@ __global__ void k_step_end(Inst I) {
     d->poisson_resid = S->poisson_resid;
     d->status = S->status;
   }
-  (void)nb0;
-  (void)nb1;
-  I.diag->particle_steps = S->pushed + (ok ? S->n[0] + S->n[1] : 0);  // every step
+  I.diag->particle_steps = S->pushed + (ok ? S->n_live[0] + S->n_live[1] : 0);  // every step
   if (ok) {
-    S->flip[0] ^= 1;   // the scatter wrote the other buffer
-    S->flip[1] ^= 1;
-    S->pushed += S->n[0] + S->n[1];
-    S->n[0] = S->n_next[0];
-    S->n[1] = S->n_next[1];
+    S->pushed += S->n_live[0] + S->n_live[1];   // the live particles this step pushed
+    if (sort_this_step(I, S)) {
+      S->flip[0] ^= 1;   // the scatter wrote the other buffer
+      S->flip[1] ^= 1;
+      S->n[0] = S->n_next[0];
+      S->n[1] = S->n_next[1];
+      S->unsorted = 0;
+    } else {             // births appended in place, dead slots kept
+      S->n[0] += nb0;
+      S->n[1] += nb1;
+      S->unsorted = 1;
+    }
+    S->n_live[0] = S->n_next[0];
+    S->n_live[1] = S->n_next[1];
     S->step = S->step + 1;
   }
   S->nbirth[0] = S->nbirth[1] = 0;
@@ -1210,7 +1249,7 @@ cudaError_t launch_sort_species(const Inst& I, int sp, int num_sms, cudaStream_t
   long long cap = I.cap[sp];
   k_keys<<<grid_for(cap, 256, num_sms, 8), 256, 0, st>>>(I, sp);
   k_scan<<<1, 1024, 0, st>>>(I, sp);
-  k_scatter<<<dim3(grid_for(cap, 256, num_sms, 8), 1), 256, 0, st>>>(I, sp);
+  k_scatter<<<dim3(grid_for(cap, 256, num_sms, 8), 1), 256, 0, st>>>(I, sp, 0);
   k_commit_n<<<1, 32, 0, st>>>(I, sp);
   return cudaGetLastError();
 }
@@ -1224,7 +1263,7 @@ cudaError_t launch_thin(const Inst& I, int factor, int num_sms, cudaStream_t st)
       const long long cap = I.cap[sp];
       k_thin<<<grid_for(cap, 256, num_sms, 8), 256, 0, st>>>(I, sp, factor);
       k_scan<<<1, 1024, 0, st>>>(I, sp);
-      k_scatter<<<dim3(grid_for(cap, 256, num_sms, 8), 1), 256, 0, st>>>(I, sp);
+      k_scatter<<<dim3(grid_for(cap, 256, num_sms, 8), 1), 256, 0, st>>>(I, sp, 0);
       k_commit_n<<<1, 32, 0, st>>>(I, sp);
     }
   }
@@ -1284,7 +1323,11 @@ cudaError_t launch_post_push(const Inst& I, int num_sms, cudaStream_t st) {
   launch_births(I, num_sms, st);
   k_scan<<<2, 1024, 0, st>>>(I, 0);
   if (I.prec32) launch_scatter32(I, num_sms, st);
-  else k_scatter<<<dim3(num_sms * 8, 2), 256, 0, st>>>(I, 0);
+  else k_scatter<<<dim3(num_sms * 8, 2), 256, 0, st>>>(I, 0, 1);
+  if (I.sort_every > 1) {
+    if (I.prec32) launch_append32(I, num_sms, st);
+    else k_append<<<dim3(num_sms, 2), 256, 0, st>>>(I);
+  }
   cudaError_t e = launch_charge(I, st);
   if (e != cudaSuccess) return e;
   k_circuit<<<1, 256, 0, st>>>(I);
@@ -1319,7 +1362,11 @@ cudaError_t launch_step(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_
   mk(G_SCAN, false);
   mk(G_SCATTER, true);
   if (I.prec32) launch_scatter32(I, num_sms, st);
-  else k_scatter<<<dim3(num_sms * 8, 2), 256, 0, st>>>(I, 0);
+  else k_scatter<<<dim3(num_sms * 8, 2), 256, 0, st>>>(I, 0, 1);
+  if (I.sort_every > 1) {
+    if (I.prec32) launch_append32(I, num_sms, st);
+    else k_append<<<dim3(num_sms, 2), 256, 0, st>>>(I);
+  }
   mk(G_SCATTER, false);
   mk(G_CHARGE, true);
   cudaError_t e = launch_charge(I, st);

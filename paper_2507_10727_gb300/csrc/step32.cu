@@ -215,7 +215,7 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
           b_nx = P.b[i2];
         }
       }
-      if (i < n) {
+      if (i < n && b.y != kDead) {   // dead slots stay until the next full sort
         int m, nn;
         cell_mn(b.y, m, nn);
         const float dr = a.x, dz = a.y;
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(kPush32Threads, 4) k_push32_all(const Inst* in
   }
 }
 
-__global__ void k_scatter32(Inst I, int sp0) {
+__global__ void k_scatter32(Inst I, int sp0, int per_step) {
   Scalars* S = I.S;
   if (S->status & ST_FATAL) return;
   const int sp = sp0 + blockIdx.y;
@@ -462,6 +462,7 @@ __global__ void k_scatter32(Inst I, int sp0) {
   const int fl = S->flip[sp];
   const Particles32 src = I.buf32[sp][fl], dst = I.buf32[sp][fl ^ 1];
   const BirthsDev B = I.births[sp];
+  if (per_step && !sort_this_step(I, S)) return;   // k_append32 does this step
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -563,10 +564,14 @@ __global__ void k_thin32(Inst I, int sp, int factor) {
     int key = -1;
     if (i < n) {
       uint4 b = P.b[i];
-      unsigned long long w[4];
-      philox4x64((unsigned long long)id_of(b), (unsigned long long)s, 5ULL, 0ULL, I.seed,
-                 (unsigned long long)sp, w);
-      if (w[0] % (unsigned long long)factor == 0ULL) {
+      bool keep = b.y != kDead;   // dead slots go; factor 1 keeps every live particle
+      if (keep && factor > 1) {
+        unsigned long long w[4];
+        philox4x64((unsigned long long)id_of(b), (unsigned long long)s, 5ULL, 0ULL, I.seed,
+                   (unsigned long long)sp, w);
+        keep = w[0] % (unsigned long long)factor == 0ULL;
+      }
+      if (keep) {
         int m, nn;
         cell_mn(b.y, m, nn);
         key = cell_key(I, m, nn);
@@ -640,7 +645,7 @@ cudaError_t launch_unpack32(const Inst& I, int sp, long long offset, long long c
 
 cudaError_t launch_sort_species32(const Inst& I, int sp, int num_sms, cudaStream_t st) {
   launch_scan(I, sp, 1, st);
-  k_scatter32<<<dim3(grid32(I.cap[sp], 256, num_sms, 8), 1), 256, 0, st>>>(I, sp);
+  k_scatter32<<<dim3(grid32(I.cap[sp], 256, num_sms, 8), 1), 256, 0, st>>>(I, sp, 0);
   return launch_commit_n(I, sp, st);
 }
 
@@ -667,8 +672,29 @@ cudaError_t launch_push32_all(const Inst* d_insts, WorkQueue* q, int gather, int
   return cudaGetLastError();
 }
 
+// births appended to the current records on a step without the full sort
+__global__ void k_append32(Inst I) {
+  const Scalars* S = I.S;
+  if ((S->status & ST_FATAL) || sort_this_step(I, S)) return;
+  const int sp = blockIdx.y;
+  const long long n_old = S->n[sp];
+  const long long nb = S->nbirth[sp] < I.birth_cap ? S->nbirth[sp] : I.birth_cap;
+  const Particles32 P = I.buf32[sp][S->flip[sp]];
+  const BirthsDev B = I.births[sp];
+  for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
+       b += (long long)gridDim.x * blockDim.x) {
+    P.a[n_old + b] = B.a32[b];
+    P.b[n_old + b] = B.b32[b];
+  }
+}
+
+cudaError_t launch_append32(const Inst& I, int num_sms, cudaStream_t st) {
+  k_append32<<<dim3(num_sms, 2), 256, 0, st>>>(I);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_scatter32(const Inst& I, int num_sms, cudaStream_t st) {
-  k_scatter32<<<dim3(num_sms * 8, 2), 256, 0, st>>>(I, 0);
+  k_scatter32<<<dim3(num_sms * 8, 2), 256, 0, st>>>(I, 0, 1);
   return cudaGetLastError();
 }
 

@@ -240,3 +240,19 @@ def test_fp32_region_diagnostics(pg):
         if b["ncell"][k] > 0:
             assert a["Te"][k] == pytest.approx(b["Te"][k], rel=2e-3), k
     pg.pic_destroy(h)
+
+
+def test_fp32_sort_every(pg):
+    """FP32 records with a full sort every third step: dead records and
+    appended births between sorts; after five steps the run is on the FP64
+    oracle's track at the FP32 bar."""
+    p = pic_inputs.params_rz32()
+    p.update(gamma_i=0.3, poisson_tol=1e-12, circuit_mode=1, Vs=400.0, Rext=100.0, n_avg=3,
+             sort_every=3)
+    p, parts = busy_state(p, ppc=16, seed=83)
+    p, orc, h = _pair32(pg, p, parts)
+    for _ in range(5):
+        orc.step(1)
+        pg.pic_step(h, 1)
+    _check(pg, h, orc)
+    pg.pic_destroy(h)

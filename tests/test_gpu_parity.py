@@ -449,3 +449,65 @@ def test_region_diagnostics_match_oracle(pg, gather):
     z = pg.pic_region_read(h, 0)
     assert z["samples"] == 0 and z["ion_impacts"] == 0 and z["ncell"] == [0, 0, 0]
     pg.pic_destroy(h)
+
+
+@pytest.mark.parametrize("gather", [0, 1])
+def test_sort_every_matches_oracle(pg, gather, tmp_path):
+    """Full cell sorts only every third step (dead slots and appended births in
+    between): the step's results do not depend on the particle order, so the
+    run matches the oracle as with a sort every step -- integer counters every
+    step (no compaction), particles and fields at the end; a checkpoint taken
+    between sorts resumes identically."""
+    p = pic_inputs.params_rz32(gather=gather)
+    p.update(gamma_i=0.3, gamma_e=0.1, poisson_tol=1e-13, circuit_mode=1, Vs=400.0,
+             Rext=100.0, n_avg=3, sort_every=3)
+    p, parts = busy_state(p, ppc=16, seed=71 + gather)
+    p, orc, h = _pair(pg, p, parts)
+    for k in range(7):
+        orc.step(1)
+        pg.pic_step(h, 1)
+        de, do = pg.pic_diagnostics(h, 0), orc.diag()
+        for key in ("N_e", "N_i", "n_ion_cath", "n_e_cath", "n_sey", "n_ionize", "n_excite",
+                    "n_elastic"):
+            assert de[key] == do[key], (k, key)
+        if k == 3:   # between sorts (steps 2 and 5 sort): checkpoint, compacting
+            pg.pic_save(h, 0, str(tmp_path / "mid.bin"))
+    _check_step(pg, h, orc)
+    h2 = pg.pic_create(p)
+    pg.pic_load(h2, 0, str(tmp_path / "mid.bin"))
+    pg.pic_step(h2, 3)
+    for sp in (0, 1):
+        a = sort_by_id(pg.pic_get_particles(h2, 0, sp))
+        b = sort_by_id(pg.pic_get_particles(h, 0, sp))
+        for q in a:
+            assert np.array_equal(a[q], b[q]), (sp, q)
+    assert pg.pic_diagnostics(h2, 0)["particle_steps"] == pg.pic_diagnostics(h, 0)["particle_steps"]
+    pg.pic_destroy(h2)
+    pg.pic_destroy(h)
+
+
+def test_sort_every_graph_and_reads_between_sorts(pg):
+    """With the step captured in a CUDA graph and sorts every fourth step,
+    reads between sorts (count, particles, region sample, re-weighting)
+    compact the arrays and leave the run on the oracle's track."""
+    import torch
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        p = pic_inputs.params_rz32()
+        p.update(gamma_i=0.3, poisson_tol=1e-13, circuit_mode=1, Vs=400.0, Rext=100.0, n_avg=3,
+                 sort_every=4, ied_bins=16, ied_emax=512.0)
+        p, parts = busy_state(p, ppc=12, seed=81)
+        p, orc, h = _pair(pg, p, parts)
+        pg.pic_step(h, 6)
+        orc.step(6)
+        assert pg.pic_uses_graph(h) == 1
+        assert pg.pic_count(h, 0, 0) == orc.count(0)       # compacts (step 6: unsorted)
+        pg.pic_region_sample(h, 0)
+        pg.pic_step(h, 2)
+        orc.step(2)
+        pg.pic_reweight(h, 0, 2)
+        orc.reweight(2)
+        pg.pic_step(h, 3)
+        orc.step(3)
+        _check_step(pg, h, orc)
+        pg.pic_destroy(h)
