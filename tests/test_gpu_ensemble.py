@@ -191,3 +191,34 @@ def test_reweight_and_region_diagnostics_per_instance(pg):
         pg.pic_destroy(one)
     assert pg.pic_diagnostics(ens, 2)["weight"] == 3 * insts[2][0]["weight"]
     pg.pic_destroy(ens)
+
+
+def test_periodic_sort_ensemble_equals_individual_runs(pg):
+    """Full sorts every third step in an ensemble (each instance decides on
+    its own state): still the single-instance results bit for bit."""
+    import torch
+    insts = _instances()
+    for p, _ in insts:
+        p["sort_every"] = 3
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        ens = pg.pic_create([p for p, _ in insts])
+        for k, (p, parts) in enumerate(insts):
+            _load(pg, ens, k, parts)
+            pg.pic_solve_fields(ens, k)
+        pg.pic_step(ens, 8)
+        for k, (p, parts) in enumerate(insts):
+            one = pg.pic_create(p)
+            _load(pg, one, 0, parts)
+            pg.pic_solve_fields(one, 0)
+            pg.pic_step(one, 8)
+            assert pg.pic_diagnostics(ens, k)["N_e"] == pg.pic_diagnostics(one, 0)["N_e"]
+            for sp in (0, 1):
+                a = sort_by_id(pg.pic_get_particles(ens, k, sp))
+                b = sort_by_id(pg.pic_get_particles(one, 0, sp))
+                for q in a:
+                    assert np.array_equal(a[q], b[q]), (k, sp, q)
+            assert np.array_equal(pg.pic_get_fields(ens, k)["phi"], pg.pic_get_fields(one, 0)["phi"])
+            pg.pic_destroy(one)
+        pg.pic_destroy(ens)
+    side.synchronize()
