@@ -512,7 +512,7 @@ const char* pic_last_error(const pic_handle* h) { return h ? h->err.c_str() : "n
 // appended births; calls that read or replace particles first compact and
 // sort them (the thinning kernels with factor 1 keep every live particle).
 static int ensure_sorted(pic_handle* h, int instance) {
-  Scalars s;
+  Scalars s{};
   const int rc = read_status(h, instance, &s);
   if (rc != PIC_OK && rc != PIC_ERR_NONCONVERGED) return rc;
   if (!s.unsorted) return PIC_OK;

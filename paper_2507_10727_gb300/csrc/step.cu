@@ -23,8 +23,6 @@
 namespace pic {
 
 constexpr int kPushThreads = 256;
-constexpr int kPPT = 8;                          // particles per thread per chunk
-constexpr int kChunk = kPushThreads * kPPT;      // particles per chunk
 constexpr int kHalo = 3;                         // cells a particle may move and still hit the patch
 constexpr int kPR = kTile + 2 * kHalo + 1;       // patch nodes in r
 constexpr int kPZ = 2 * kTile + 2 * kHalo + 1;   // patch nodes in z (two tiles along z)

@@ -19,8 +19,6 @@
 namespace pic {
 
 constexpr int kPush32Threads = 256;
-constexpr int kPPT32 = 8;
-constexpr int kChunk32 = kPush32Threads * kPPT32;
 constexpr int kHalo32 = 3;
 constexpr int kPR32 = kTile + 2 * kHalo32 + 1;
 constexpr int kPZ32 = 2 * kTile + 2 * kHalo32 + 1;
