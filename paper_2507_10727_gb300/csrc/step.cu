@@ -239,8 +239,8 @@ __device__ bool mcc_electron(const Inst& I, long long id, long long step, double
 }
 
 // ---------------------------------------------------------------------------
-// The push.  One CTA processes chunks of kChunk consecutive (cell-sorted)
-// particles; the chunk's charge goes into a shared patch of kPR x kPZ nodes
+// The push.  One CTA processes chunks of ppt x kPushThreads consecutive
+// (cell-sorted) particles; the chunk's charge goes into a shared patch of kPR x kPZ nodes
 // anchored at the tile of the chunk's first particle, flushed with one
 // atomic per touched node.  Particles whose new 4 nodes fall outside the
 // patch (fast movers, chunk tails in sparse regions) add to global memory.
