@@ -164,8 +164,9 @@ const char* pic_last_error(const pic_handle* h);
 
 /* Replace the particles of one species of one instance.  Arrays of length n
  * (r in [0,R), z in [0,L), velocities (v_r, v_theta, v_z) in m/s, ids unique
- * and >= 0); host memory when on_device = 0, device memory otherwise.  The
- * particles are sorted by cell on the device.  next_id becomes max(id)+1 over
+ * and >= 0); host memory when on_device = 0, device memory otherwise.  Page-
+ * locked host arrays (all six) are read in place by the kernels; pageable ones
+ * go through staging copies.  The particles are sorted by cell on the device.  next_id becomes max(id)+1 over
  * both species if that is larger.  Synchronous. */
 int pic_set_particles(pic_handle* h, int instance, int species, int64_t n, const double* r,
                       const double* z, const double* vr, const double* vt, const double* vz,

@@ -522,6 +522,21 @@ static int ensure_sorted(pic_handle* h, int instance) {
   return read_status(h, instance, nullptr);
 }
 
+// Device addresses of host arrays that the device can read in place (pinned
+// memory under unified addressing); false when any of them is not such memory.
+static bool device_views(const void* const* host, int k, const void** dev) {
+  for (int i = 0; i < k; ++i) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, host[i]) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+    dev[i] = a.devicePointer;
+  }
+  return true;
+}
+
 int pic_set_particles(pic_handle* h, int instance, int species, int64_t n, const double* r,
                       const double* z, const double* vr, const double* vt, const double* vz,
                       const int64_t* id, int on_device) {
@@ -537,9 +552,18 @@ int pic_set_particles(pic_handle* h, int instance, int species, int64_t n, const
   }
   cudaStream_t st = h->stream;
   cudaError_t e = cudaSuccess;
+  // pinned host arrays are read in place by the kernels (faster than a copy engine)
+  const void* hv[6] = {r, z, vr, vt, vz, id};
+  const void* dv[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  const bool direct = !on_device && n > 0 && device_views(hv, 6, dv);
   if (ih.I.prec32) {
     e = launch_set_n(ih.I, species, n, st);
-    if (on_device) {
+    if (direct) {
+      if (e == cudaSuccess)
+        e = launch_pack32(ih.I, species, 0, n, (const double*)dv[0], (const double*)dv[1],
+                          (const double*)dv[2], (const double*)dv[3], (const double*)dv[4],
+                          (const long long*)dv[5], h->num_sms, st);
+    } else if (on_device) {
       if (e == cudaSuccess && n > 0)
         e = launch_pack32(ih.I, species, 0, n, r, z, vr, vt, vz, (const long long*)id, h->num_sms, st);
     } else {
@@ -565,7 +589,10 @@ int pic_set_particles(pic_handle* h, int instance, int species, int64_t n, const
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const ParticlesDev& P = ih.I.buf[species][current_buffer(h, instance, species)];
     const size_t b = (size_t)n * 8;
-    if (n > 0) {
+    if (direct) {
+      void* const dst[6] = {P.r, P.z, P.vr, P.vt, P.vz, P.id};
+      e = launch_copy_in(dv, dst, n, h->num_sms, st);
+    } else if (n > 0) {
       e = cudaMemcpyAsync(P.r, r, b, kind, st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(P.z, z, b, kind, st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(P.vr, vr, b, kind, st);

@@ -52,6 +52,10 @@ cudaError_t launch_region_eval(const Inst& I, cudaStream_t st);
 // ids of the step's births (both species, both precisions)
 cudaError_t launch_births(const Inst& I, int num_sms, cudaStream_t st);
 
+// copy six arrays of n 8-byte words from device-addressable host memory
+cudaError_t launch_copy_in(const void* const src[6], void* const dst[6], long long n, int num_sms,
+                           cudaStream_t st);
+
 // set the particle count of species sp (set-up)
 cudaError_t launch_set_n(const Inst& I, int sp, long long n, cudaStream_t st);
 

@@ -1286,6 +1286,36 @@ cudaError_t launch_region_eval(const Inst& I, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Particle arrays read in place from host memory that the device addresses
+// directly (pinned memory under unified addressing, over the CPU-GPU link):
+// six arrays of n 8-byte words, one pass by the SMs.
+struct Copy6 {
+  const unsigned long long* src[6];
+  unsigned long long* dst[6];
+};
+
+__global__ void k_copy_in(Copy6 c, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long v[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] = c.src[k][i];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) c.dst[k][i] = v[k];
+  }
+}
+
+cudaError_t launch_copy_in(const void* const src[6], void* const dst[6], long long n, int num_sms,
+                           cudaStream_t st) {
+  Copy6 c;
+  for (int k = 0; k < 6; ++k) {
+    c.src[k] = (const unsigned long long*)src[k];
+    c.dst[k] = (unsigned long long*)dst[k];
+  }
+  k_copy_in<<<grid_for(n, 256, num_sms, 8), 256, 0, st>>>(c, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_scan(const Inst& I, int sp0, int nsp, cudaStream_t st) {
   k_scan<<<nsp, 1024, 0, st>>>(I, sp0);
   return cudaGetLastError();

@@ -511,3 +511,30 @@ def test_sort_every_graph_and_reads_between_sorts(pg):
         orc.step(3)
         _check_step(pg, h, orc)
         pg.pic_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pinned_host_upload_equals_pageable(pg, precision):
+    """Pinned host arrays are read in place by the kernels; the loaded state is
+    the one the copy path (pageable arrays) gives, bit for bit."""
+    import ctypes as C
+    import torch
+    p = pic_inputs.params_rz32(precision=precision)
+    p, parts = busy_state(p, ppc=9, seed=91)
+    p = pic_inputs.with_capacity(p, parts, factor=2.0)
+    ha, hb = pg.pic_create(p), pg.pic_create(p)
+    lib = pg.load_library()
+    for k, sp in (("e", 0), ("i", 1)):
+        pg.pic_set_particles(ha, 0, sp, parts[k])                    # pageable numpy arrays
+        t = {q: torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for q, a in parts[k].items()}
+        rc = lib.pic_set_particles(hb.ptr, 0, sp, t["r"].numel(), t["r"].data_ptr(),
+                                   t["z"].data_ptr(), t["vr"].data_ptr(), t["vt"].data_ptr(),
+                                   t["vz"].data_ptr(), t["id"].data_ptr(), 0)
+        assert rc == 0
+    for sp in (0, 1):
+        a = sort_by_id(pg.pic_get_particles(ha, 0, sp))
+        b = sort_by_id(pg.pic_get_particles(hb, 0, sp))
+        for q in a:
+            assert np.array_equal(a[q], b[q]), (sp, q)
+    pg.pic_destroy(ha)
+    pg.pic_destroy(hb)
