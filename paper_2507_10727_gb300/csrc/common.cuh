@@ -260,6 +260,14 @@ __device__ __forceinline__ void draws(const Inst& I, int sp, long long id, long 
   u[0] = u01(w[0]); u[1] = u01(w[1]); u[2] = u01(w[2]); u[3] = u01(w[3]);
 }
 
+// The null-collision candidate test of an electron (U1 < p_null, on the
+// integer word of the collision stream)
+__device__ __forceinline__ bool mcc_candidate(const Inst& I, long long id, long long step) {
+  unsigned long long w[4];
+  philox4x64((unsigned long long)id, (unsigned long long)step, 0ULL, 0ULL, I.seed, 0ULL, w);
+  return (w[0] >> 11) < I.pnull_k;
+}
+
 // ---------------------------------------------------------------------------
 // grid helpers
 // ---------------------------------------------------------------------------

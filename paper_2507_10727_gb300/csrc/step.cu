@@ -26,6 +26,7 @@ constexpr int kPushThreads = 256;
 constexpr int kHalo = 3;                         // cells a particle may move and still hit the patch
 constexpr int kPR = kTile + 2 * kHalo + 1;       // patch nodes in r
 constexpr int kPZ = 2 * kTile + 2 * kHalo + 1;   // patch nodes in z (two tiles along z)
+constexpr int kCollQ = 512;                      // deferred collision candidates per chunk
 
 // ---------------------------------------------------------------------------
 // Field gather tables (Section 2).
@@ -238,6 +239,17 @@ __device__ bool mcc_electron(const Inst& I, long long id, long long step, double
   return true;
 }
 
+// The collision of a queued candidate i, on its state after the move.
+__device__ __noinline__ void collide_at(const Inst& I, const ParticlesDev& P, long long i,
+                                           long long step) {
+  double vr = P.vr[i], vt = P.vt[i], vz = P.vz[i];
+  if (mcc_electron(I, P.id[i], step, P.r[i], P.z[i], vr, vt, vz)) {
+    P.vr[i] = vr;
+    P.vt[i] = vt;
+    P.vz[i] = vz;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // The push.  One CTA processes chunks of ppt x kPushThreads consecutive
 // (cell-sorted) particles; the chunk's charge goes into a shared patch of kPR x kPZ nodes
@@ -247,11 +259,15 @@ __device__ bool mcc_electron(const Inst& I, long long id, long long step, double
 // ---------------------------------------------------------------------------
 // Push the chunk of `ppt * blockDim.x` particles of species SP starting at c0
 // (the whole CTA takes part).  `patch` is the CTA's zeroed shared deposit
-// patch; it is flushed and zeroed again before return.  Returns this thread's
-// share of the kinetic energy (diagnostic steps only).
+// patch; it is flushed and zeroed again before return.  `anchor` holds the
+// patch origin and the candidate count, `cq` the chunk's collision candidates:
+// the collision itself changes only the velocity, so it runs after the chunk
+// with the candidates packed onto consecutive lanes (a warp that met one
+// candidate inside the loop would run the whole collision for one lane).
+// Returns this thread's share of the kinetic energy (diagnostic steps only).
 template <int SP, int GATHER>
 __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned long long* patch,
-                               int* anchor) {
+                               int* anchor, int* cq) {
   Scalars* S = I.S;
   const long long n = S->n[SP];
   const long long step = S->step;
@@ -270,9 +286,11 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
       locate(P.z[c0], I.inv_dz, I.nz, nn, f);
       anchor[0] = (m & ~(kTile - 1)) - kHalo;
       anchor[1] = (nn & ~(kTile - 1)) - kHalo;
+      anchor[2] = 0;
     }
     __syncthreads();
     const int pm0 = anchor[0], pn0 = anchor[1];
+    unsigned over = 0u;   // candidates that found the queue full, bit j (ppt <= 32)
 #pragma unroll 1
     for (int j = 0; j < ppt; ++j) {
       const long long i = c0 + (long long)j * blockDim.x + threadIdx.x;
@@ -383,7 +401,14 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
           }
         }
         if (alive) {
-          if (SP == 0 && I.mcc_on) mcc_electron(I, P.id[i], step, r1, z1, vr, vt, vz);
+          if (SP == 0 && I.mcc_on) {
+            const long long id = P.id[i];
+            if (mcc_candidate(I, id, step)) {
+              const int slot = atomicAdd(&anchor[2], 1);
+              if (slot < kCollQ) cq[slot] = (int)(i - c0);
+              else over |= 1u << j;   // queue full: this thread runs it after the queue
+            }
+          }
           int m1, n1;
           double fr1, fz1;
           locate(r1, I.inv_dr, I.nr, m1, fr1);
@@ -427,6 +452,16 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
       if (newkey >= 0 && lane == __ffs(peers) - 1) atomicAdd(&I.counts[SP][newkey], __popc(peers));
     }
     __syncthreads();
+    if (SP == 0) {
+      // the queued collisions (Section 3), on the state written above
+      const int nq = min(anchor[2], kCollQ);
+      for (int k = threadIdx.x; k < nq; k += blockDim.x) collide_at(I, P, c0 + cq[k], step);
+      while (over) {
+        const int j = __ffs(over) - 1;
+        over &= over - 1;
+        collide_at(I, P, c0 + (long long)j * blockDim.x + threadIdx.x, step);
+      }
+    }
     // flush the patch
     for (int k = threadIdx.x; k < kPR * kPZ; k += blockDim.x) {
       const unsigned long long v = patch[k];
@@ -448,7 +483,8 @@ template <int GATHER>
 __global__ void __launch_bounds__(kPushThreads, 2) k_push_all(const Inst* insts, WorkQueue* q,
                                                                int ppt) {
   __shared__ unsigned long long patch[kPR * kPZ];
-  __shared__ int anchor[2];
+  __shared__ int anchor[3];
+  __shared__ int cq[kCollQ];
   __shared__ Inst sI;
   __shared__ int s_inst, s_sp, s_skip;
   __shared__ long long s_c0;
@@ -485,8 +521,8 @@ __global__ void __launch_bounds__(kPushThreads, 2) k_push_all(const Inst* insts,
       cur = inst;
     }
     if (!s_skip) {
-      if (s_sp == 0) K0 += push_chunk64<0, GATHER>(sI, s_c0, ppt, patch, anchor);
-      else K1 += push_chunk64<1, GATHER>(sI, s_c0, ppt, patch, anchor);
+      if (s_sp == 0) K0 += push_chunk64<0, GATHER>(sI, s_c0, ppt, patch, anchor, cq);
+      else K1 += push_chunk64<1, GATHER>(sI, s_c0, ppt, patch, anchor, cq);
     }
     __syncthreads();
   }

@@ -19,6 +19,7 @@
 namespace pic {
 
 constexpr int kPush32Threads = 256;
+constexpr int kCollQ32 = 256;   // deferred collision candidates per chunk
 constexpr int kHalo32 = 3;
 constexpr int kPR32 = kTile + 2 * kHalo32 + 1;
 constexpr int kPZ32 = 2 * kTile + 2 * kHalo32 + 1;
@@ -167,13 +168,29 @@ __device__ void mcc_electron32(const Inst& I, long long id, long long step, int 
 }
 
 // ---------------------------------------------------------------------------
+// The collision of a queued candidate i, on its state after the move.
+__device__ __noinline__ void collide_at32(const Inst& I, const Particles32& P, long long i,
+                                          long long step) {
+  const float4 a = P.a[i];
+  const uint4 b = P.b[i];
+  int m, n;
+  cell_mn(b.y, m, n);
+  float vr = a.z, vt = a.w, vz = __uint_as_float(b.x);
+  mcc_electron32(I, id_of(b), step, m, a.x, n, a.y, vr, vt, vz);
+  P.a[i] = make_float4(a.x, a.y, vr, vt);
+  reinterpret_cast<unsigned int*>(P.b + i)[0] = __float_as_uint(vz);
+}
+
 // The FP32 push: gather + Boris + move + walls + SEY + MCC + deposit, state
 // rewritten in place with the new cell key (read by the scatter).
 // ---------------------------------------------------------------------------
 // Push the chunk of `ppt * blockDim.x` particles starting at c0 (whole CTA);
-// `patch` is the CTA's zeroed deposit patch, flushed and zeroed on return.
+// `patch` is the CTA's zeroed deposit patch, flushed and zeroed on return;
+// `anchor` holds the patch origin and the candidate count, `cq` the chunk's
+// collision candidates, run after the chunk as in push_chunk64 (step.cu).
 template <int SP, int GATHER>
-__device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patch, int* anchor) {
+__device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patch, int* anchor,
+                               int* cq) {
   Scalars* S = I.S;
   const long long n = S->n[SP];
   const long long step = S->step;
@@ -189,6 +206,7 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
       cell_mn(P.b[c0].y, m, nn);
       anchor[0] = (m & ~(kTile - 1)) - kHalo32;
       anchor[1] = (nn & ~(kTile - 1)) - kHalo32;
+      anchor[2] = 0;
     }
     __syncthreads();
     const int pm0 = anchor[0], pn0 = anchor[1];
@@ -200,6 +218,7 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
       a_nx = P.a[i];
       b_nx = P.b[i];
     }
+    unsigned over = 0u;   // candidates that found the queue full, bit j (ppt <= 32)
 #pragma unroll 1
     for (int j = 0; j < ppt; ++j, i += blockDim.x) {
       int newkey = -1, dm = 0, dn = 0;
@@ -333,7 +352,11 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
           }
         }
         if (alive) {
-          if (SP == 0 && I.mcc_on) mcc_electron32(I, id_of(b), step, m1, dr1, n1, dz1, vr, vt, vz);
+          if (SP == 0 && I.mcc_on && mcc_candidate(I, id_of(b), step)) {
+            const int slot = atomicAdd(&anchor[2], 1);
+            if (slot < kCollQ32) cq[slot] = (int)(i - c0);
+            else over |= 1u << j;   // queue full: this thread runs it after the queue
+          }
           newkey = cell_key(I, m1, n1);
           P.a[i] = make_float4(dr1, dz1, vr, vt);
           P.b[i] = make_uint4(__float_as_uint(vz), pack_mn(m1, n1), b.z, b.w);
@@ -390,6 +413,16 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
       }
     }
     __syncthreads();
+    if (SP == 0) {
+      // the queued collisions (Section 3), on the state written above
+      const int nq = min(anchor[2], kCollQ32);
+      for (int k = threadIdx.x; k < nq; k += blockDim.x) collide_at32(I, P, c0 + cq[k], step);
+      while (over) {
+        const int j = __ffs(over) - 1;
+        over &= over - 1;
+        collide_at32(I, P, c0 + (long long)j * blockDim.x + threadIdx.x, step);
+      }
+    }
     for (int k = threadIdx.x; k < kPR32 * kPZ32; k += blockDim.x) {
       const float v = patch[k];
       if (v != 0.0f) {
@@ -409,7 +442,8 @@ template <int GATHER>
 __global__ void __launch_bounds__(kPush32Threads, 4) k_push32_all(const Inst* insts, WorkQueue* q,
                                                                    int ppt) {
   __shared__ float patch[kPR32 * kPZ32];
-  __shared__ int anchor[2];
+  __shared__ int anchor[3];
+  __shared__ int cq[kCollQ32];
   __shared__ Inst sI;
   __shared__ int s_inst, s_sp, s_skip;
   __shared__ long long s_c0;
@@ -443,8 +477,8 @@ __global__ void __launch_bounds__(kPush32Threads, 4) k_push32_all(const Inst* in
       cur = inst;
     }
     if (!s_skip) {
-      if (s_sp == 0) K0 += push_chunk32<0, GATHER>(sI, s_c0, ppt, patch, anchor);
-      else K1 += push_chunk32<1, GATHER>(sI, s_c0, ppt, patch, anchor);
+      if (s_sp == 0) K0 += push_chunk32<0, GATHER>(sI, s_c0, ppt, patch, anchor, cq);
+      else K1 += push_chunk32<1, GATHER>(sI, s_c0, ppt, patch, anchor, cq);
     }
     __syncthreads();
   }
