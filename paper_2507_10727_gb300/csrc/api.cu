@@ -235,6 +235,8 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
   I.hq32[1] = (float)(0.5 * I.qm[1] * c.dt);
   I.kr32 = (float)(c.dt * I.inv_dr);
   I.kz32 = (float)(c.dt * I.inv_dz);
+  I.kr64 = c.dt * I.inv_dr;
+  I.kz64 = c.dt * I.inv_dz;
   for (int sp = 0; sp < 2; ++sp) {
     const size_t cap = (size_t)I.cap[sp];
     if (p32) {
@@ -537,9 +539,11 @@ static bool device_views(const void* const* host, int k, const void** dev) {
   return true;
 }
 
-int pic_set_particles(pic_handle* h, int instance, int species, int64_t n, const double* r,
-                      const double* z, const double* vr, const double* vt, const double* vz,
-                      const int64_t* id, int on_device) {
+// pic_set_particles; `cells`: FP64 positions given in cell units already (a
+// checkpoint's arrays, host memory), copied without conversion
+static int set_particles(pic_handle* h, int instance, int species, int64_t n, const double* r,
+                         const double* z, const double* vr, const double* vt, const double* vz,
+                         const int64_t* id, int on_device, bool cells) {
   if (bad_instance(h, instance) || species < 0 || species > 1 || n < 0)
     return fail(h, PIC_ERR_INVALID, "bad instance/species/count");
   InstHost& ih = h->inst[instance];
@@ -555,7 +559,7 @@ int pic_set_particles(pic_handle* h, int instance, int species, int64_t n, const
   // pinned host arrays are read in place by the kernels (faster than a copy engine)
   const void* hv[6] = {r, z, vr, vt, vz, id};
   const void* dv[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  const bool direct = !on_device && n > 0 && device_views(hv, 6, dv);
+  const bool direct = !on_device && !cells && n > 0 && device_views(hv, 6, dv);
   if (ih.I.prec32) {
     e = launch_set_n(ih.I, species, n, st);
     if (direct) {
@@ -586,19 +590,24 @@ int pic_set_particles(pic_handle* h, int instance, int species, int64_t n, const
     }
     if (e == cudaSuccess) e = launch_sort_species32(ih.I, species, h->num_sms, st);
   } else {
-    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    // positions go to cell units on the way in (launch_copy_in)
     const ParticlesDev& P = ih.I.buf[species][current_buffer(h, instance, species)];
     const size_t b = (size_t)n * 8;
+    void* const dst[6] = {P.r, P.z, P.vr, P.vt, P.vz, P.id};
     if (direct) {
-      void* const dst[6] = {P.r, P.z, P.vr, P.vt, P.vz, P.id};
-      e = launch_copy_in(dv, dst, n, h->num_sms, st);
+      e = launch_copy_in(dv, dst, n, ih.I, h->num_sms, st);
+    } else if (on_device) {
+      e = launch_copy_in(hv, dst, n, ih.I, h->num_sms, st);
     } else if (n > 0) {
-      e = cudaMemcpyAsync(P.r, r, b, kind, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(P.z, z, b, kind, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(P.vr, vr, b, kind, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(P.vt, vt, b, kind, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(P.vz, vz, b, kind, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(P.id, id, b, kind, st);
+      // pageable host arrays: copy, then convert the positions in place
+      e = cudaMemcpyAsync(P.r, r, b, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(P.z, z, b, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(P.vr, vr, b, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(P.vt, vt, b, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(P.vz, vz, b, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(P.id, id, b, cudaMemcpyHostToDevice, st);
+      const void* const in_place[6] = {P.r, P.z, P.vr, P.vt, P.vz, P.id};
+      if (e == cudaSuccess && !cells) e = launch_copy_in(in_place, dst, n, ih.I, h->num_sms, st);
     }
     if (e == cudaSuccess) e = launch_set_n(ih.I, species, n, st);
     if (e == cudaSuccess) e = launch_sort_species(ih.I, species, h->num_sms, st);
@@ -607,6 +616,12 @@ int pic_set_particles(pic_handle* h, int instance, int species, int64_t n, const
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(h, e, "set_particles sync");
   return read_status(h, instance, nullptr);
+}
+
+int pic_set_particles(pic_handle* h, int instance, int species, int64_t n, const double* r,
+                      const double* z, const double* vr, const double* vt, const double* vz,
+                      const int64_t* id, int on_device) {
+  return set_particles(h, instance, species, n, r, z, vr, vt, vz, id, on_device, false);
 }
 
 int pic_count(pic_handle* h, int instance, int species, int64_t* n_out) {
@@ -630,6 +645,7 @@ int pic_get_particles(pic_handle* h, int instance, int species, double* r, doubl
   const Inst& I = h->inst[instance].I;
   cudaStream_t st = h->stream;
   cudaError_t e = cudaSuccess;
+  bool host_convert = false;   // FP64 positions copied to pageable memory
   if (I.prec32) {
     if (on_device) {
       if (n > 0)
@@ -655,9 +671,24 @@ int pic_get_particles(pic_handle* h, int instance, int species, double* r, doubl
     const ParticlesDev& P = I.buf[species][current_buffer(h, instance, species)];
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     const size_t b = (size_t)n * 8;
+    // positions leave cell units: by a kernel into device or page-locked
+    // host memory, else copied and converted on the host (the same product
+    // and clamp, from_cells)
+    if (n > 0 && (r || z)) {
+      const void* hv[2] = {r ? (const void*)r : (const void*)z, z ? (const void*)z : (const void*)r};
+      const void* dvw[2] = {nullptr, nullptr};
+      if (on_device) {
+        e = launch_positions_out(I, P.r, P.z, r, z, n, h->num_sms, st);
+      } else if (device_views(hv, 2, dvw)) {
+        e = launch_positions_out(I, P.r, P.z, r ? (double*)dvw[0] : nullptr,
+                                 z ? (double*)dvw[1] : nullptr, n, h->num_sms, st);
+      } else {
+        if (r) e = cudaMemcpyAsync(r, P.r, b, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && z) e = cudaMemcpyAsync(z, P.z, b, cudaMemcpyDeviceToHost, st);
+        host_convert = true;
+      }
+    }
     if (n > 0) {
-      if (r) e = cudaMemcpyAsync(r, P.r, b, kind, st);
-      if (e == cudaSuccess && z) e = cudaMemcpyAsync(z, P.z, b, kind, st);
       if (e == cudaSuccess && vr) e = cudaMemcpyAsync(vr, P.vr, b, kind, st);
       if (e == cudaSuccess && vt) e = cudaMemcpyAsync(vt, P.vt, b, kind, st);
       if (e == cudaSuccess && vz) e = cudaMemcpyAsync(vz, P.vz, b, kind, st);
@@ -666,6 +697,12 @@ int pic_get_particles(pic_handle* h, int instance, int species, double* r, doubl
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(h, e, "get_particles");
+  if (host_convert) {
+    for (int64_t i = 0; i < n; ++i) {
+      if (r) r[i] = from_cells(r[i], I.dr, I.R);
+      if (z) z[i] = from_cells(z[i], I.dz, I.L);
+    }
+  }
   return rc;
 }
 
@@ -1075,8 +1112,10 @@ int pic_region_reset(pic_handle* h, int instance) {
 
 // ---------------------------------------------------------------------------
 // checkpoints: a flat little-endian file
-//   "PICCKPT3", pic_config, Scalars, qhist[n_avg], phi[nodes],
-//   then per species: n, r[n], z[n], vr[n], vt[n], vz[n], id[n]
+//   "PICCKPT4", pic_config, Scalars, qhist[n_avg], phi[nodes],
+//   then per species: n, r[n], z[n], vr[n], vt[n], vz[n], id[n] (the device
+//   arrays as they are: positions in cell units) or, in FP32 mode, the raw
+//   records
 // ---------------------------------------------------------------------------
 int pic_save(pic_handle* h, int instance, const char* path) {
   if (bad_instance(h, instance) || !path) return fail(h, PIC_ERR_INVALID, "bad argument");
@@ -1094,7 +1133,7 @@ int pic_save(pic_handle* h, int instance, const char* path) {
   if (e != cudaSuccess) return cuda_fail(h, e, "save copy");
   FILE* f = std::fopen(path, "wb");
   if (!f) return fail(h, PIC_ERR_IO, std::string("cannot open ") + path);
-  bool ok = std::fwrite("PICCKPT3", 1, 8, f) == 8;
+  bool ok = std::fwrite("PICCKPT4", 1, 8, f) == 8;
   ok = ok && std::fwrite(&c, sizeof(c), 1, f) == 1;
   ok = ok && std::fwrite(&s, sizeof(s), 1, f) == 1;
   ok = ok && std::fwrite(qh.data(), 8, qh.size(), f) == qh.size();
@@ -1142,7 +1181,7 @@ int pic_load(pic_handle* h, int instance, const char* path) {
   Scalars s;
   const size_t nn = (size_t)(c.nr + 1) * (c.nz + 1);
   std::vector<double> qh((size_t)c.n_avg), phi(nn);
-  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "PICCKPT3", 8) == 0;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "PICCKPT4", 8) == 0;
   ok = ok && std::fread(&fc, sizeof(fc), 1, f) == 1;
   ok = ok && fc.nr == c.nr && fc.nz == c.nz && fc.n_avg == c.n_avg && fc.precision == c.precision;
   ok = ok && std::fread(&s, sizeof(s), 1, f) == 1;
@@ -1185,9 +1224,9 @@ int pic_load(pic_handle* h, int instance, const char* path) {
       if (e0 != cudaSuccess) return cuda_fail(h, e0, "load copy");
       continue;
     }
-    const int rc = pic_set_particles(h, instance, sp, n[sp], arr[sp][0].data(), arr[sp][1].data(),
-                                     arr[sp][2].data(), arr[sp][3].data(), arr[sp][4].data(),
-                                     (const int64_t*)ids[sp].data(), 0);
+    const int rc = set_particles(h, instance, sp, n[sp], arr[sp][0].data(), arr[sp][1].data(),
+                                 arr[sp][2].data(), arr[sp][3].data(), arr[sp][4].data(),
+                                 (const int64_t*)ids[sp].data(), 0, true);
     if (rc != PIC_OK) return rc;
   }
   Scalars cur;

@@ -136,4 +136,16 @@ PIC_HD double recip_refine(double x, double y) {
   return fma(y, e, y);
 }
 
+// 2 / x, exactly 2 recip_refine(x, y): the last step is written for 2y, which
+// is y with its exponent raised by one (an integer add; y is a positive normal
+// number below 2^1023 after the first step for the x this is used on), so the
+// doubling costs no FP64 operation.
+PIC_HD double recip2_refine(double x, double y) {
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  const double y2 = double_of(bits_of(y) + (1ULL << 52));
+  return fma(y2, e, y2);
+}
+
 }  // namespace pic

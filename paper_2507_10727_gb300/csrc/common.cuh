@@ -42,6 +42,9 @@ enum : int {
 };
 constexpr int ST_FATAL = ST_CAPACITY | ST_NONCONV | ST_NAN | ST_TIMEOUT;
 
+// FP64 particle arrays.  Positions are stored in cell units, r / dr in
+// [0, nr) and z / dz in [0, nz) (r = -1 marks a removed particle), so that a
+// cell split needs no scaling; velocities are in m/s.
 struct ParticlesDev {
   double *r, *z, *vr, *vt, *vz;
   long long* id;
@@ -59,7 +62,7 @@ struct Particles32 {
 struct BirthsDev {
   float4* a32;                // FP32 mode records (cell key in b32.y, id in b32.z/w)
   uint4* b32;
-  double *r, *z, *vr, *vt, *vz;
+  double *r, *z, *vr, *vt, *vz;   // FP64 mode: positions in cell units, as ParticlesDev
   unsigned long long* pkey;   // (parent id << 2) | kind
   int* cell;                  // cell key of the birth position
   long long* id;              // id assigned by the births kernel
@@ -165,6 +168,7 @@ struct Inst {
   int m_cath;              // last radial node index of the cathode (r_m <= Rc)
   double R, L, Rc, dr, dz, inv_dr, inv_dz;
   double dt;
+  double kr64, kz64;       // dt / dr, dt / dz: FP64 moves in cell units
   // species
   double weight;
   double qm[2], mass[2], gamma[2];
@@ -277,6 +281,27 @@ __device__ __forceinline__ void locate(double x, double inv_d, int ncell, int& k
   split_cell(x * inv_d, ncell, k, f);
 }
 
+// SI coordinate x on an axis of length X = ncell d -> cell units x / d (as
+// x * inv_d).  The domain test is kept: x in [0, X) gives a value below
+// ncell (a product rounded up to ncell is moved one ulp down), x >= X one of
+// at least ncell; negative and NaN x stay negative / NaN.
+__device__ __forceinline__ double to_cells(double x, double inv_d, int ncell, double X) {
+  double s = x * inv_d;
+  if (x < X) {
+    if (s >= (double)ncell) s = nextafter((double)ncell, 0.0);
+  } else if (x >= X && s < (double)ncell) {
+    s = (double)ncell;
+  }
+  return s;
+}
+
+// cell units s in [0, ncell) -> SI s d, kept below X = ncell d (host and
+// device give the same value: one rounded product and a clamp)
+__host__ __device__ __forceinline__ double from_cells(double s, double d, double X) {
+  const double x = s * d;
+  return x < X ? x : nextafter(X, 0.0);
+}
+
 __device__ __forceinline__ int cell_key(const Inst& I, int m, int n) {
   int tile = (m >> 3) * I.ntz + (n >> 3);
   return tile * kTileCells + ((m & 7) << 3) + (n & 7);
@@ -308,12 +333,13 @@ __device__ __forceinline__ FixW fix_weights(double wr, double wz) {
   return f;
 }
 
-// 1 / x for x >= 1 below the FP32 overflow: the FP32 approximate reciprocal
-// (PTX rcp.approx.ftz.f32, within one FP32 ulp) refined in FP64 (bits.cuh)
-__device__ __forceinline__ double recip(double x) {
+// 2 / x for x >= 1 below the FP32 overflow: the FP32 approximate reciprocal
+// (PTX rcp.approx.ftz.f32, within one FP32 ulp) refined in FP64, the doubling
+// on the exponent bits (bits.cuh)
+__device__ __forceinline__ double recip2(double x) {
   float yf;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"((float)x));
-  return recip_refine(x, (double)yf);
+  return recip2_refine(x, (double)yf);
 }
 
 // finite test on the exponent bits (integer pipe)

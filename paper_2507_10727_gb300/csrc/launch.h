@@ -52,9 +52,15 @@ cudaError_t launch_region_eval(const Inst& I, cudaStream_t st);
 // ids of the step's births (both species, both precisions)
 cudaError_t launch_births(const Inst& I, int num_sms, cudaStream_t st);
 
-// copy six arrays of n 8-byte words from device-addressable host memory
-cudaError_t launch_copy_in(const void* const src[6], void* const dst[6], long long n, int num_sms,
-                           cudaStream_t st);
+// load FP64 particles: r, z, v_r, v_theta, v_z, id from device-addressable
+// memory (device or page-locked host) into the particle arrays, positions
+// converted to cell units; with src == dst for the last four (already copied)
+// only the positions are converted in place
+cudaError_t launch_copy_in(const void* const src[6], void* const dst[6], long long n,
+                           const Inst& I, int num_sms, cudaStream_t st);
+// FP64 positions in cell units -> SI into device-addressable r, z (either null)
+cudaError_t launch_positions_out(const Inst& I, const double* rc, const double* zc, double* r,
+                                 double* z, long long n, int num_sms, cudaStream_t st);
 
 // set the particle count of species sp (set-up)
 cudaError_t launch_set_n(const Inst& I, int sp, long long n, cudaStream_t st);

@@ -70,8 +70,9 @@ __global__ void k_field_tables(Inst I) {
         I.etab32[key] = make_float4((float)t.x, (float)t.y, (float)t.z, (float)t.w);
       } else {
         for (int sp = 0; sp < 2; ++sp) {
-          const double hs = 0.5 * I.qm[sp] * I.dt;
-          I.etab[sp][key] = make_d4(hs * t.x, hs * t.y, hs * t.z, hs * t.w);
+          // volume weighting: the push multiplies by r in cell units, r / dr
+          const double hs = 0.5 * I.qm[sp] * I.dt, hr = I.rweight == 1 ? hs * I.dr : hs;
+          I.etab[sp][key] = make_d4(hr * t.x, hr * t.y, hs * t.z, hs * t.w);
         }
       }
     } else {
@@ -150,8 +151,8 @@ __device__ void add_birth(const Inst& I, int sp, unsigned long long pkey, double
   B.pkey[b] = pkey;
   int m, n;
   double fr, fz;
-  locate(r, I.inv_dr, I.nr, m, fr);
-  locate(z, I.inv_dz, I.nz, n, fz);
+  split_cell(r, I.nr, m, fr);
+  split_cell(z, I.nz, n, fz);
   const int key = cell_key(I, m, n);
   B.cell[b] = key;
   atomicAdd(&I.counts[sp][key], 1);
@@ -273,7 +274,6 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
   const long long step = S->step;
   const bool diag = S->diag_on != 0;
   const ParticlesDev P = I.buf[SP][S->flip[SP]];
-  const double dt = I.dt;
   const double4_32a* etab = I.etab[SP];   // h E, h B of this species (h = q dt / 2m)
   const double4_32a* btab = I.btab[SP];
   const int lane = threadIdx.x & 31;
@@ -282,8 +282,8 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
     if (threadIdx.x == 0) {
       int m, nn;
       double f;
-      locate(P.r[c0], I.inv_dr, I.nr, m, f);
-      locate(P.z[c0], I.inv_dz, I.nz, nn, f);
+      split_cell(P.r[c0], I.nr, m, f);
+      split_cell(P.z[c0], I.nz, nn, f);
       anchor[0] = (m & ~(kTile - 1)) - kHalo;
       anchor[1] = (nn & ~(kTile - 1)) - kHalo;
       anchor[2] = 0;
@@ -308,8 +308,8 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
         if (I.push_on) {
           int m, nn;
           double fr, fz;
-          locate(r, I.inv_dr, I.nr, m, fr);
-          locate(z, I.inv_dz, I.nz, nn, fz);
+          split_cell(r, I.nr, m, fr);
+          split_cell(z, I.nz, nn, fz);
           const int ck = cell_key(I, m, nn);
           // gather h E
           double hEr, hEz;
@@ -333,7 +333,7 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
           const double tz = bz.x + fr * (bz.y + fz * bz.w) + fz * bz.z;
           // Boris: half kick, rotation about B, half kick
           const double ax = vr + hEr, ay = vt, az = vz + hEz;
-          const double f2 = 2.0 * recip(1.0 + tx * tx + tz * tz);   // 1 + t^2 >= 1
+          const double f2 = recip2(1.0 + tx * tx + tz * tz);   // 2 / (1 + t^2), 1 + t^2 >= 1
           const double sx = f2 * tx, sz = f2 * tz;
           const double px = ax + ay * tz;
           const double py = fma(az, tx, fma(-ax, tz, ay));   // ay + (az tx - ax tz), two FMAs
@@ -341,10 +341,10 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
           const double vx = ax + py * sz + hEr;
           const double vy = fma(pz, sx, fma(-px, sz, ay));   // ay + (pz sx - px sz)
           const double vzn = az - py * sx + hEz;
-          // straight move, then rotate the frame onto the new radius
-          x1 = r + vx * dt;
-          y1 = vy * dt;
-          z1 = z + vzn * dt;
+          // straight move (in cell units), then rotate the frame onto the new radius
+          x1 = r + vx * I.kr64;
+          y1 = vy * I.kr64;
+          z1 = z + vzn * I.kz64;
           const double s2 = x1 * x1 + y1 * y1;
           if (nonzero_sq(s2)) {   // s2 > 0 (a NaN goes on and is flagged below)
             const double inv = rsqrt(s2);
@@ -360,22 +360,23 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
         }
         if (diag) Kloc += 0.5 * I.mass[SP] * I.weight * 0.5 * (v2old + vr * vr + vt * vt + vz * vz);
         bool alive = true;
+        const double Lc = (double)I.nz, Rw = (double)I.nr;   // z = L, r = R in cell units
         if (I.walls_reflect) {
           if (z1 < 0.0) { z1 = -z1; vz = -vz; }
-          if (z1 >= I.L) { z1 = 2.0 * I.L - z1; vz = -vz; if (z1 >= I.L) z1 = nextafter(I.L, 0.0); }
-          if (r1 >= I.R) { r1 = 2.0 * I.R - r1; vr = -vr; if (r1 >= I.R) r1 = nextafter(I.R, 0.0); }
-        } else if (lt_zero(z1) || ge_pos(z1, I.L) || ge_pos(r1, I.R)) {   // integer-pipe compares
+          if (z1 >= Lc) { z1 = 2.0 * Lc - z1; vz = -vz; if (z1 >= Lc) z1 = nextafter(Lc, 0.0); }
+          if (r1 >= Rw) { r1 = 2.0 * Rw - r1; vr = -vr; if (r1 >= Rw) r1 = nextafter(Rw, 0.0); }
+        } else if (lt_zero(z1) || ge_pos(z1, Lc) || ge_pos(r1, Rw)) {   // integer-pipe compares
           alive = false;
           if (lt_zero(z1)) {
             const double tc = z / (z - z1);
             const double xh = r + tc * (x1 - r), yh = tc * y1;
-            const double rhit = sqrt(xh * xh + yh * yh);
-            if (rhit <= I.Rc) {
+            const double rhit = sqrt(xh * xh + yh * yh);   // cell units
+            if (rhit <= I.Rc * I.inv_dr) {
               // cathode impact (Section 3): tally; secondary electron with
               // probability gamma, born at the impact point at rest
               atomicAdd(SP == 1 ? &S->cnt_ion_cath : &S->cnt_e_cath, 1ULL);
               // ion energy distribution on the cathode band (Section 7)
-              if (SP == 1 && I.ied_bins > 0 && rhit >= I.band_lo && rhit <= I.band_hi) {
+              if (SP == 1 && I.ied_bins > 0 && rhit * I.dr >= I.band_lo && rhit * I.dr <= I.band_hi) {
                 const double E = 0.5 * I.mass[1] * (vr * vr + vt * vt + vz * vz) / kQe;
                 const double fb = floor(E / I.ied_de);
                 atomicAdd(&I.reg.ied[fb < (double)I.ied_bins ? (int)fb : I.ied_bins], 1ULL);
@@ -411,8 +412,8 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
           }
           int m1, n1;
           double fr1, fz1;
-          locate(r1, I.inv_dr, I.nr, m1, fr1);
-          locate(z1, I.inv_dz, I.nz, n1, fz1);
+          split_cell(r1, I.nr, m1, fr1);
+          split_cell(z1, I.nz, n1, fz1);
           newkey = cell_key(I, m1, n1);
           P.r[i] = r1; P.z[i] = z1; P.vr[i] = vr; P.vt[i] = vt; P.vz[i] = vz;
           // deposit weights of x^{n+1} (Section 2: tent functions)
@@ -774,13 +775,14 @@ __global__ void k_keys(Inst I, int sp) {
     const long long i = base + lane;
     int key = -1;
     if (i < n) {
-      const double r = P.r[i], z = P.z[i];
-      if (r >= 0.0 && r < I.R && z >= 0.0 && z < I.L && finite64(P.vr[i]) && finite64(P.vt[i]) &&
+      const double r = P.r[i], z = P.z[i];   // cell units
+      if (r >= 0.0 && r < (double)I.nr && z >= 0.0 && z < (double)I.nz && finite64(P.vr[i]) &&
+          finite64(P.vt[i]) &&
           finite64(P.vz[i]) && P.id[i] >= 0) {
         int m, nn;
         double f;
-        locate(r, I.inv_dr, I.nr, m, f);
-        locate(z, I.inv_dz, I.nz, nn, f);
+        split_cell(r, I.nr, m, f);
+        split_cell(z, I.nz, nn, f);
         key = cell_key(I, m, nn);
         idmax = P.id[i] > idmax ? P.id[i] : idmax;
       } else {
@@ -829,8 +831,8 @@ __global__ void k_thin(Inst I, int sp, int factor) {
       if (!dead && (factor == 1 || thin_keep(I, sp, P.id[i], s, factor))) {
         int m, nn;
         double f;
-        locate(P.r[i], I.inv_dr, I.nr, m, f);
-        locate(P.z[i], I.inv_dz, I.nz, nn, f);
+        split_cell(P.r[i], I.nr, m, f);
+        split_cell(P.z[i], I.nz, nn, f);
         key = cell_key(I, m, nn);
       }
       I.key[sp][i] = key;
@@ -1034,8 +1036,8 @@ __global__ void k_deposit_all(Inst I, int sp) {
        i += (long long)gridDim.x * blockDim.x) {
     int m, nn;
     double fr, fz;
-    locate(P.r[i], I.inv_dr, I.nr, m, fr);
-    locate(P.z[i], I.inv_dz, I.nz, nn, fz);
+    split_cell(P.r[i], I.nr, m, fr);
+    split_cell(P.z[i], I.nz, nn, fz);
     const FixW f = fix_weights(rweight_upper(I, P.r[i], m, fr), fz);
     unsigned long long* q = I.qacc[sp];
     atomicAdd(q + node_index(I, m, nn), f.w00);
@@ -1330,25 +1332,52 @@ struct Copy6 {
   unsigned long long* dst[6];
 };
 
-__global__ void k_copy_in(Copy6 c, long long n) {
+// r, z, v_r, v_theta, v_z, id in, positions converted from SI to cell units;
+// with src == dst for the velocities and ids (already in place) only the
+// positions are rewritten
+__global__ void k_copy_in(Copy6 c, long long n, Inst I) {
+  const bool all = c.src[2] != c.dst[2];
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    unsigned long long v[6];
+    const double r = double_of(c.src[0][i]), z = double_of(c.src[1][i]);
+    if (all) {
+      unsigned long long v[4];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) v[k] = c.src[k][i];
+      for (int k = 0; k < 4; ++k) v[k] = c.src[k + 2][i];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) c.dst[k][i] = v[k];
+      for (int k = 0; k < 4; ++k) c.dst[k + 2][i] = v[k];
+    }
+    c.dst[0][i] = bits_of(to_cells(r, I.inv_dr, I.nr, I.R));
+    c.dst[1][i] = bits_of(to_cells(z, I.inv_dz, I.nz, I.L));
   }
 }
 
-cudaError_t launch_copy_in(const void* const src[6], void* const dst[6], long long n, int num_sms,
-                           cudaStream_t st) {
+cudaError_t launch_copy_in(const void* const src[6], void* const dst[6], long long n,
+                           const Inst& I, int num_sms, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
   Copy6 c;
   for (int k = 0; k < 6; ++k) {
     c.src[k] = (const unsigned long long*)src[k];
     c.dst[k] = (unsigned long long*)dst[k];
   }
-  k_copy_in<<<grid_for(n, 256, num_sms, 8), 256, 0, st>>>(c, n);
+  k_copy_in<<<grid_for(n, 256, num_sms, 8), 256, 0, st>>>(c, n, I);
+  return cudaGetLastError();
+}
+
+// positions out in SI (either output may be null)
+__global__ void k_positions_out(const double* rc, const double* zc, double* r, double* z,
+                                long long n, Inst I) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (r) r[i] = from_cells(rc[i], I.dr, I.R);
+    if (z) z[i] = from_cells(zc[i], I.dz, I.L);
+  }
+}
+
+cudaError_t launch_positions_out(const Inst& I, const double* rc, const double* zc, double* r,
+                                 double* z, long long n, int num_sms, cudaStream_t st) {
+  if (n <= 0 || (!r && !z)) return cudaSuccess;
+  k_positions_out<<<grid_for(n, 256, num_sms, 8), 256, 0, st>>>(rc, zc, r, z, n, I);
   return cudaGetLastError();
 }
 

@@ -12,7 +12,8 @@ runs both forms over random and edge-case inputs.
   signed-zero, subnormal, infinite and NaN inputs;
 * recip_refine(x, seed): within one ulp of 1.0 / x for seeds up to two FP32
   ulps from the rounded FP32 reciprocal (the device seed, PTX rcp.approx, is
-  within one), x in [1, 4) and log-uniform over 1e-30 .. 1e30.
+  within one), x in [1, 4) and log-uniform over 1e-30 .. 1e30;
+* recip2_refine(x, seed): bit for bit 2 recip_refine(x, seed) on the same x.
 """
 import os
 import subprocess
@@ -51,6 +52,7 @@ static void check_recip(double x) {
     uint64_t a, b; std::memcpy(&a, &y, 8); std::memcpy(&b, &want, 8);
     const uint64_t ulps = a > b ? a - b : b - a;
     ++n; if (ulps > 1) { if (bad < 5) std::printf("recip %.17g: %.17g vs %.17g\n", x, y, want); ++bad; }
+    ++n; if (!same(recip2_refine(x, (double)sd), 2.0 * y)) { if (bad < 5) std::printf("recip2 %.17g\n", x); ++bad; }
   }
 }
 static void check_cmp(double x, double c) {
