@@ -49,7 +49,7 @@ KERNELS_PER_STEP = 12
 # measured: FP64 6.19e9 / 6.74e9 / 6.83e9 particle-steps/s at 1 / 8 / 16;
 # FP32 2.35e10 / 2.53e10 / 2.60e10 at 1 / 2 / 4)
 SORT_EVERY_DEFAULT = {"fp64": 16, "fp32": 4}
-FLOPS_PER_PARTICLE = {0: 73.0, 1: 81.0}   # EC, MC (h E and h B read from per-species tables)
+FLOPS_PER_PARTICLE = {0: 69.0, 1: 77.0}   # EC, MC (h E and h B from per-species tables; positions in cell units)
 # Algorithmic HBM bytes of one particle-step: read and write r, z, v_r,
 # v_theta, v_z, id once (FP64).
 BYTES_PER_PARTICLE = 96.0
@@ -89,6 +89,9 @@ def parse():
                          "SEY x R_ext ensemble on 128x128 grids; learned: the 256x512 "
                          "discharge with and without the learned Poisson warm start; unet: "
                          "the warm-start network alone on the 257x513 node grid")
+    ap.add_argument("--phi-extrapolate", type=int, default=1, choices=(0, 1),
+                    help="1: each step's Poisson solve starts from 2 phi^(n-1) - phi^(n-2) "
+                         "(phi still solved to poisson_tol); 0: from phi^(n-1)")
     ap.add_argument("--sort-every", type=int, default=None,
                     help="full cell sort every this many steps (births appended in place "
                          "between; results do not depend on it); default 16 for fp64, "
@@ -127,6 +130,7 @@ def workload(args):
     p["diag_every"] = 10      # diagnostics reduction every 10 steps
     p["precision"] = 1 if args.precision == "fp32" else 0
     p["sort_every"] = args.sort_every
+    p["phi_extrapolate"] = args.phi_extrapolate
     return p, parts
 
 
@@ -138,6 +142,8 @@ def config_block(p, n, args):
             "precision": args.precision, "circuit": {"Vs": p["Vs"], "Rext": p["Rext"]},
             "dt": p["dt"], "poisson_tol": p["poisson_tol"], "diag_every": p["diag_every"],
             "sort_every": p["sort_every"],
+            "poisson_start": ("2 phi^(n-1) - phi^(n-2)" if p["phi_extrapolate"]
+                              else "phi^(n-1)"),
             "insulating_boundary": {"z0_outside_cathode": p["gap_neumann"],
                                     "wall_r_R": p["wall_neumann"]},
             "l2": "inputs larger than L2 (particle state 3.8 GB >> 129 MB)"}
@@ -296,6 +302,7 @@ def sweep_workload(args):
         p["diag_every"] = 10
         p["precision"] = 1 if args.precision == "fp32" else 0
         p["sort_every"] = args.sort_every
+        p["phi_extrapolate"] = args.phi_extrapolate
         out.append((p, parts))
     return out
 

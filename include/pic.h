@@ -111,6 +111,10 @@ typedef struct pic_config {
                                 discharge region is 1.0 cm < r < 1.5 cm (Sections 5, 7) */
   int32_t ied_bins;          /* cathode ion energy histogram: bins (0: off, at most 65536) */
   double ied_emax;           /* its upper edge (eV); bins of width ied_emax / ied_bins */
+  int32_t phi_extrapolate;   /* 1: each step's Poisson solve starts, on the unknown nodes,
+                                from the linear extrapolation 2 phi^{n-1} - phi^{n-2} of the
+                                last two solutions instead of phi^{n-1} (fewer iterations;
+                                phi is still solved to poisson_tol); 0: from phi^{n-1} */
 } pic_config;
 
 /* Device-memory provider.  alloc returns a device pointer aligned to at least

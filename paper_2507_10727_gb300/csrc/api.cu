@@ -140,6 +140,7 @@ std::string validate(const pic_config& c) {
   if ((c.gap_neumann != 0 && c.gap_neumann != 1) || (c.wall_neumann != 0 && c.wall_neumann != 1))
     return "gap_neumann, wall_neumann must be 0 or 1";
   if (c.ied_bins < 0 || c.ied_bins > 65536) return "ied_bins must be in [0, 65536]";
+  if (c.phi_extrapolate != 0 && c.phi_extrapolate != 1) return "phi_extrapolate must be 0 or 1";
   if (c.ied_bins > 0 && !(c.ied_emax > 0.0)) return "ied_emax must be positive";
   if (!(c.band_r_lo <= c.band_r_hi)) return "band_r_lo must not exceed band_r_hi";
   return "";
@@ -220,6 +221,7 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
   I.Vs = c.Vs;
   I.Rext = c.Rext;
   I.poisson_tol = c.poisson_tol;
+  I.phi_extrap = c.phi_extrapolate;
   I.poisson_max_iter = c.poisson_max_iter;
   I.cap[0] = c.cap_e;
   I.cap[1] = c.cap_i;
@@ -281,6 +283,7 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
     B.sidx = (unsigned int*)chk(A((size_t)P2 * 4));
   }
   I.phi = (double*)chk(A(nn * 8));
+  I.phi_old = (double*)chk(A(nn * 8));
   I.Q = (double*)chk(A(nn * 8));
   if (p32) {
     I.etab32 = (float4*)chk(A((size_t)I.nkey * (c.gather == 0 ? 1 : 2) * sizeof(float4)));
@@ -321,6 +324,7 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
     if (e == cudaSuccess) e = cudaMemsetAsync(p32 ? (void*)I.qacc64[sp] : (void*)I.qacc[sp], 0, nn * 8, st);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(I.phi, 0, nn * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(I.phi_old, 0, nn * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(I.Q, 0, nn * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(I.qhist, 0, (size_t)c.n_avg * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(I.diag, 0, sizeof(DiagDev), st);
@@ -725,6 +729,9 @@ int pic_set_phi(pic_handle* h, int instance, const double* phi, int on_device) {
   cudaError_t e = cudaMemcpyAsync(ih.I.phi, phi, nn * 8,
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                   h->stream);
+  // no earlier solution: the next step's extrapolation starts from this phi
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ih.I.phi_old, ih.I.phi, nn * 8, cudaMemcpyDeviceToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "set_phi");
   return PIC_OK;
@@ -872,9 +879,25 @@ static cudaError_t launch_all(pic_handle* h, const StepMarks* marks) {
 // Online autotuner of the push: the first steps of a handle run one
 // candidate chunk size each (timed with events around the push); the fastest
 // is kept for the rest of the run.
+// The push gets slower as the arrays lose their cell order between full
+// sorts, so every tuning step ends with a full sort: each candidate is timed
+// on freshly sorted arrays (set_particles and pic_load leave them sorted).
+static cudaError_t force_sorts(pic_handle* h, int on) {
+  cudaError_t e = cudaSuccess;
+  for (InstHost& ih : h->inst)
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&ih.I.S->sort_force, &on, sizeof(int), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e;
+}
+
 static int autotune_step(pic_handle* h) {
   const int c = h->tune_next;
   h->ppt = kTuneCandidates[c];
+  if (c == 0) {
+    const cudaError_t e0 = force_sorts(h, 1);
+    if (e0 != cudaSuccess) return cuda_fail(h, e0, "tune");
+  }
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
@@ -898,6 +921,8 @@ static int autotune_step(pic_handle* h) {
       if (h->tune_ms[k] < h->tune_ms[best]) best = k;
     h->ppt = kTuneCandidates[best];
     h->tune_next = -1;
+    const cudaError_t e1 = force_sorts(h, 0);
+    if (e1 != cudaSuccess) return cuda_fail(h, e1, "tune");
   }
   return PIC_OK;
 }
@@ -1112,7 +1137,7 @@ int pic_region_reset(pic_handle* h, int instance) {
 
 // ---------------------------------------------------------------------------
 // checkpoints: a flat little-endian file
-//   "PICCKPT4", pic_config, Scalars, qhist[n_avg], phi[nodes],
+//   "PICCKPT4", pic_config, Scalars, qhist[n_avg], phi[nodes], phi_old[nodes],
 //   then per species: n, r[n], z[n], vr[n], vt[n], vz[n], id[n] (the device
 //   arrays as they are: positions in cell units) or, in FP32 mode, the raw
 //   records
@@ -1127,9 +1152,10 @@ int pic_save(pic_handle* h, int instance, const char* path) {
   if (rc != PIC_OK) return rc;
   const pic_config& c = ih.cfg;
   const size_t nn = (size_t)(c.nr + 1) * (c.nz + 1);
-  std::vector<double> qh((size_t)c.n_avg), phi(nn);
+  std::vector<double> qh((size_t)c.n_avg), phi(nn), phi_old(nn);
   cudaError_t e = cudaMemcpy(qh.data(), ih.I.qhist, qh.size() * 8, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(phi.data(), ih.I.phi, nn * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(phi_old.data(), ih.I.phi_old, nn * 8, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(h, e, "save copy");
   FILE* f = std::fopen(path, "wb");
   if (!f) return fail(h, PIC_ERR_IO, std::string("cannot open ") + path);
@@ -1138,6 +1164,7 @@ int pic_save(pic_handle* h, int instance, const char* path) {
   ok = ok && std::fwrite(&s, sizeof(s), 1, f) == 1;
   ok = ok && std::fwrite(qh.data(), 8, qh.size(), f) == qh.size();
   ok = ok && std::fwrite(phi.data(), 8, nn, f) == nn;
+  ok = ok && std::fwrite(phi_old.data(), 8, nn, f) == nn;
   for (int sp = 0; sp < 2 && ok; ++sp) {
     const long long n = s.n[sp];
     ok = std::fwrite(&n, 8, 1, f) == 1;
@@ -1180,13 +1207,14 @@ int pic_load(pic_handle* h, int instance, const char* path) {
   pic_config fc;
   Scalars s;
   const size_t nn = (size_t)(c.nr + 1) * (c.nz + 1);
-  std::vector<double> qh((size_t)c.n_avg), phi(nn);
+  std::vector<double> qh((size_t)c.n_avg), phi(nn), phi_old(nn);
   bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "PICCKPT4", 8) == 0;
   ok = ok && std::fread(&fc, sizeof(fc), 1, f) == 1;
   ok = ok && fc.nr == c.nr && fc.nz == c.nz && fc.n_avg == c.n_avg && fc.precision == c.precision;
   ok = ok && std::fread(&s, sizeof(s), 1, f) == 1;
   ok = ok && std::fread(qh.data(), 8, qh.size(), f) == qh.size();
   ok = ok && std::fread(phi.data(), 8, nn, f) == nn;
+  ok = ok && std::fread(phi_old.data(), 8, nn, f) == nn;
   std::vector<double> arr[2][5];
   std::vector<long long> ids[2];
   std::vector<float4> ra[2];
@@ -1238,9 +1266,11 @@ int pic_load(pic_handle* h, int instance, const char* path) {
   s.n_live[0] = s.n[0];      // checkpoints hold compact arrays
   s.n_live[1] = s.n[1];
   s.unsorted = 0;
+  s.sort_force = h->tune_next > 0 ? 1 : 0;   // this handle's tuner, not the saved one's
   cudaError_t e = cudaMemcpy(ih.I.S, &s, sizeof(s), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ih.I.qhist, qh.data(), qh.size() * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ih.I.phi, phi.data(), nn * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ih.I.phi_old, phi_old.data(), nn * 8, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(h, e, "load copy");
   // FP32 records were copied as saved: sort them once here so that this
   // handle's cell bins describe them (factor 1 keeps every particle)

@@ -97,7 +97,7 @@ struct Scalars {
   long long ppc_max[2];    // most particles in one cell, from the last sort's histogram
   long long n_live[2];     // live particles (n also counts the dead slots between sorts)
   int unsorted;            // 1: the arrays hold dead slots and appended births (no sort yet)
-  int pad2;
+  int sort_force;          // 1: every step ends with a full sort (while the push is tuned)
 };
 
 struct DiagDev {           // mirrors pic_diag
@@ -188,6 +188,8 @@ struct Inst {
   RegionDev reg;
   int diag_every;
   double Vc_fixed, Vs, Rext;
+  int phi_extrap;          // per-step solves start from 2 phi - phi_old on the unknown nodes
+  double* phi_old;         // the solution before phi (the previous step's)
   double poisson_tol;
   int poisson_max_iter;
   long long cap[2], birth_cap;
@@ -223,7 +225,7 @@ struct Inst {
 // and whenever appending the births in place would overflow a buffer.  The
 // scatter and the step-end kernel take the same decision from the same state.
 __device__ __forceinline__ bool sort_this_step(const Inst& I, const Scalars* S) {
-  if (I.sort_every <= 1 || (S->step + 1) % I.sort_every == 0) return true;
+  if (I.sort_every <= 1 || S->sort_force || (S->step + 1) % I.sort_every == 0) return true;
   for (int sp = 0; sp < 2; ++sp) {
     const long long nb = S->nbirth[sp] < I.birth_cap ? S->nbirth[sp] : I.birth_cap;
     if (S->n[sp] + nb > I.cap[sp]) return true;

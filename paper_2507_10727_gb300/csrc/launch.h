@@ -104,7 +104,8 @@ cudaError_t launch_scatter32(const Inst& I, int num_sms, cudaStream_t st);
 cudaError_t launch_append32(const Inst& I, int num_sms, cudaStream_t st);
 
 // compute node charge Q from the fixed-point sums (and clear them)
-cudaError_t launch_charge(const Inst& I, cudaStream_t st);
+// node charges from the deposit; `step`: a step's (phi extrapolation when on)
+cudaError_t launch_charge(const Inst& I, bool step, cudaStream_t st);
 
 // Poisson workspace
 size_t poisson_work_bytes(int nr, int nz);

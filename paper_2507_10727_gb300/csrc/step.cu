@@ -1050,9 +1050,13 @@ __global__ void k_deposit_all(Inst I, int sp) {
 // ---------------------------------------------------------------------------
 // Node charge Q = e w (sum_i - sum_e) 2^-44; peak densities on diagnostic steps
 // ---------------------------------------------------------------------------
-__global__ void k_charge(Inst I) {
+// Node charges Q from the deposit sums (zeroed for the next step); with `step`
+// and phi_extrap the unknown nodes of phi also move to the start of this
+// step's solve, 2 phi^{n-1} - phi^{n-2}, and phi_old to phi^{n-1}.
+__global__ void k_charge(Inst I, bool step) {
   Scalars* S = I.S;
   const int nn = (I.nr + 1) * (I.nz + 1);
+  const bool extrap = step && I.phi_extrap;
   const bool diag = S->diag_on != 0;
   const double scale = kQe * I.weight * kFixInv;
   double pe = 0.0, pi = 0.0;
@@ -1071,6 +1075,12 @@ __global__ void k_charge(Inst I) {
       I.Q[k] = (double)(long long)(ui - ue) * scale;
       se = (double)ue * kFixInv;
       si = (double)ui * kFixInv;
+    }
+    if (extrap) {
+      const int m = k / (I.nz + 1), n = k - m * (I.nz + 1);
+      const double p1 = I.phi[k];
+      if (field_free(m, n, I.nr, I.nz, I.bc_g, I.bc_wall)) I.phi[k] = 2.0 * p1 - I.phi_old[k];
+      I.phi_old[k] = p1;
     }
     if (diag) {
       const int m = k / (I.nz + 1), n = k - m * (I.nz + 1);
@@ -1269,9 +1279,9 @@ cudaError_t launch_push_all(const Inst* d_insts, WorkQueue* q, int prec32, int g
   return cudaGetLastError();
 }
 
-cudaError_t launch_charge(const Inst& I, cudaStream_t st) {
+cudaError_t launch_charge(const Inst& I, bool step, cudaStream_t st) {
   const int nn = (I.nr + 1) * (I.nz + 1);
-  k_charge<<<grid_for(nn, 256, 1024, 1), 256, 0, st>>>(I);
+  k_charge<<<grid_for(nn, 256, 1024, 1), 256, 0, st>>>(I, step);
   return cudaGetLastError();
 }
 
@@ -1399,11 +1409,15 @@ cudaError_t launch_solve_fields(const Inst& I, PoissonWork* pw, int num_sms, cud
     for (int sp = 0; sp < 2; ++sp)
       k_deposit_all<<<grid_for(I.cap[sp], 256, num_sms, 8), 256, 0, st>>>(I, sp);
   }
-  cudaError_t e = launch_charge(I, st);
+  cudaError_t e = launch_charge(I, false, st);
   if (e != cudaSuccess) return e;
   k_set_cathode<<<1, 256, 0, st>>>(I);
-  return launch_poisson(pw, I.Q, I.phi, I.poisson_tol, I.poisson_max_iter, &I.S->status,
-                        &I.S->poisson_iters, &I.S->poisson_resid, st);
+  e = launch_poisson(pw, I.Q, I.phi, I.poisson_tol, I.poisson_max_iter, &I.S->status,
+                     &I.S->poisson_iters, &I.S->poisson_resid, st);
+  if (e != cudaSuccess) return e;
+  // no earlier solution: the next step's extrapolation starts from this one
+  return cudaMemcpyAsync(I.phi_old, I.phi, (size_t)(I.nr + 1) * (I.nz + 1) * 8,
+                         cudaMemcpyDeviceToDevice, st);
 }
 
 cudaError_t launch_field_tables(const Inst& I, int num_sms, cudaStream_t st) {
@@ -1421,7 +1435,7 @@ cudaError_t launch_post_push(const Inst& I, int num_sms, cudaStream_t st) {
     if (I.prec32) launch_append32(I, num_sms, st);
     else k_append<<<dim3(num_sms, 2), 256, 0, st>>>(I);
   }
-  cudaError_t e = launch_charge(I, st);
+  cudaError_t e = launch_charge(I, true, st);
   if (e != cudaSuccess) return e;
   k_circuit<<<1, 256, 0, st>>>(I);
   return cudaGetLastError();
@@ -1462,7 +1476,7 @@ cudaError_t launch_step(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_
   }
   mk(G_SCATTER, false);
   mk(G_CHARGE, true);
-  cudaError_t e = launch_charge(I, st);
+  cudaError_t e = launch_charge(I, true, st);
   mk(G_CHARGE, false);
   if (e != cudaSuccess) return e;
   mk(G_CIRCUIT, true);

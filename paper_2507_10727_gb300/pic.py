@@ -55,7 +55,7 @@ class PicConfig(C.Structure):
         ("n_meta", C.c_double), ("meta_a", C.c_double), ("meta_I", C.c_double),
         ("gap_neumann", C.c_int32), ("wall_neumann", C.c_int32),
         ("band_r_lo", C.c_double), ("band_r_hi", C.c_double),
-        ("ied_bins", C.c_int32), ("ied_emax", C.c_double),
+        ("ied_bins", C.c_int32), ("ied_emax", C.c_double), ("phi_extrapolate", C.c_int32),
     ]
 
     @classmethod

@@ -76,7 +76,7 @@ def base_params() -> dict:
         n_meta=0.0, meta_a=4.0e-18, meta_I=4.20,
         gap_neumann=0, wall_neumann=0,
         band_r_lo=0.010, band_r_hi=0.015, ied_bins=0, ied_emax=600.0,
-        poisson_tol=1e-10, poisson_max_iter=200,
+        poisson_tol=1e-10, poisson_max_iter=200, phi_extrapolate=0,
         cap_e=0, cap_i=0, birth_cap=0, diag_every=1,
         sort_every=1,
     )

@@ -103,10 +103,12 @@ def test_ragged_grid_and_counts(pg):
         _check_step(pg, h, orc)
 
 
+@pytest.mark.parametrize("extrap", [0, 1])
 @pytest.mark.parametrize("gather", [0, 1])
-def test_several_steps_seed_plasma(pg, gather):
+def test_several_steps_seed_plasma(pg, gather, extrap):
     p = pic_inputs.params_rz32(gather=gather)
-    p.update(poisson_tol=1e-13, circuit_mode=1, Vs=400.0, Rext=2000.0, n_avg=4, gamma_i=0.2)
+    p.update(poisson_tol=1e-13, circuit_mode=1, Vs=400.0, Rext=2000.0, n_avg=4, gamma_i=0.2,
+             phi_extrapolate=extrap)
     p, parts = pic_inputs.seed_plasma(p, 32 * 32 * 8, seed=5, Te_eV=5.0)
     p, orc, h = _pair(pg, p, parts)
     for _ in range(6):
@@ -451,8 +453,9 @@ def test_region_diagnostics_match_oracle(pg, gather):
     pg.pic_destroy(h)
 
 
+@pytest.mark.parametrize("extrap", [0, 1])
 @pytest.mark.parametrize("gather", [0, 1])
-def test_sort_every_matches_oracle(pg, gather, tmp_path):
+def test_sort_every_matches_oracle(pg, gather, extrap, tmp_path):
     """Full cell sorts only every third step (dead slots and appended births in
     between): the step's results do not depend on the particle order, so the
     run matches the oracle as with a sort every step -- integer counters every
@@ -460,7 +463,7 @@ def test_sort_every_matches_oracle(pg, gather, tmp_path):
     between sorts resumes identically."""
     p = pic_inputs.params_rz32(gather=gather)
     p.update(gamma_i=0.3, gamma_e=0.1, poisson_tol=1e-13, circuit_mode=1, Vs=400.0,
-             Rext=100.0, n_avg=3, sort_every=3)
+             Rext=100.0, n_avg=3, sort_every=3, phi_extrapolate=extrap)
     p, parts = busy_state(p, ppc=16, seed=71 + gather)
     p, orc, h = _pair(pg, p, parts)
     for k in range(7):
@@ -538,3 +541,40 @@ def test_pinned_host_upload_equals_pageable(pg, precision):
             assert np.array_equal(a[q], b[q]), (sp, q)
     pg.pic_destroy(ha)
     pg.pic_destroy(hb)
+
+
+def test_phi_extrapolation_same_phi_fewer_iterations(pg):
+    """Each step's Poisson solve started from 2 phi^(n-1) - phi^(n-2) on the
+    unknown nodes: the first step after pic_solve_fields has no earlier
+    solution and is the plain step bit for bit (2 phi - phi = phi exactly);
+    on the second both starts reach the 1e-10 relative residual, so the two
+    phi differ by at most the tolerance times the condition number of the
+    32 x 32 operator (below 1e4); over the run the extrapolated starts need no
+    more iterations than the previous solution as the start."""
+    p = pic_inputs.params_rz32()
+    p.update(circuit_mode=1, Vs=400.0, Rext=2000.0, n_avg=4)
+    p, parts = busy_state(p, ppc=32, seed=23)
+    p = pic_inputs.with_capacity(p, parts, factor=2.0)
+    hs = []
+    for ex in (0, 1):
+        h = pg.pic_create(dict(p, phi_extrapolate=ex))
+        for k, sp in (("e", 0), ("i", 1)):
+            pg.pic_set_particles(h, 0, sp, parts[k])
+        pg.pic_solve_fields(h, 0)
+        hs.append(h)
+    iters = [[], []]
+    for step in range(30):
+        for j, h in enumerate(hs):
+            pg.pic_step(h, 1)
+            iters[j].append(pg.pic_diagnostics(h, 0)["poisson_iters"])
+        phi0, phi1 = (pg.pic_get_fields(h, 0)["phi"] for h in hs)
+        if step == 0:
+            assert np.array_equal(phi0, phi1)
+        elif step == 1:
+            assert field_err(phi1, phi0) <= 1e4 * FIELD_TOL
+    print(f"Poisson iterations over 30 steps: start phi^(n-1) {sum(iters[0])}, "
+          f"extrapolated {sum(iters[1])}")
+    assert iters[0][0] == iters[1][0]
+    assert sum(iters[1]) <= sum(iters[0])
+    for h in hs:
+        pg.pic_destroy(h)
