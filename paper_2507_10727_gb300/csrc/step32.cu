@@ -181,6 +181,44 @@ __device__ __noinline__ void collide_at32(const Inst& I, const Particles32& P, l
   reinterpret_cast<unsigned int*>(P.b + i)[0] = __float_as_uint(vz);
 }
 
+// A particle that crossed z = 0 during the move (in cell units: from radius Xo at
+// height zo to (X, y) at height zn), on a cold path kept out of the push loop:
+// the cathode impact tally, the ion energy histogram of the cathode band and
+// secondary emission (Section 3).
+template <int SP>
+__device__ __noinline__ void cathode_hit32(const Inst& I, float Xo, float X, float y, float zo,
+                                           float zn, float vr, float vt, float vz, uint4 b,
+                                           long long step) {
+  Scalars* S = I.S;
+  const float tc = zo / (zo - zn);
+  const float xh = Xo + tc * (X - Xo), yh = tc * y;
+  const float rhit = sqrtf(xh * xh + yh * yh);   // cells
+  if (!(rhit <= (float)(I.Rc * I.inv_dr))) return;
+  atomicAdd(SP == 1 ? &S->cnt_ion_cath : &S->cnt_e_cath, 1ULL);
+  if (SP == 1 && I.ied_bins > 0) {
+    const double rh = (double)rhit * I.dr;
+    if (rh >= I.band_lo && rh <= I.band_hi) {
+      const double E =
+          0.5 * I.mass[1] * ((double)vr * vr + (double)vt * vt + (double)vz * vz) / kQe;
+      const double fb = floor(E / I.ied_de);
+      atomicAdd(&I.reg.ied[fb < (double)I.ied_bins ? (int)fb : I.ied_bins], 1ULL);
+    }
+  }
+  if (I.gamma[SP] > 0.0) {
+    const long long id = id_of(b);
+    double u[4];
+    draws(I, SP, id, step, 2, u);
+    if (u[0] < I.gamma[SP]) {
+      atomicAdd(&S->cnt_sey, 1ULL);
+      int mh = (int)floorf(rhit);
+      float drh = rhit - (float)mh;
+      if (mh > I.nr - 1) { mh = I.nr - 1; drh = 1.0f; }
+      add_birth32(I, 0, ((unsigned long long)id << 2) | (SP == 1 ? 1ULL : 2ULL), mh, drh, 0,
+                  0.0f, 0.0f, 0.0f, 0.0f);
+    }
+  }
+}
+
 // The FP32 push: gather + Boris + move + walls + SEY + MCC + deposit, state
 // rewritten in place with the new cell key (read by the scatter).
 // ---------------------------------------------------------------------------
@@ -197,7 +235,6 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
   const bool diag = S->diag_on != 0;
   const Particles32 P = I.buf32[SP][S->flip[SP]];
   const float h = I.hq32[SP], kr = I.kr32, kz = I.kz32;
-  const float rc_cells = (float)(I.Rc * I.inv_dr);
   const int lane = threadIdx.x & 31;
   double Kloc = 0.0;
   {
@@ -318,38 +355,9 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
           alive = false;
         } else if (!I.walls_reflect && (n1 < 0 || n1 >= I.nz || m1 >= I.nr)) {
           alive = false;
-          if (n1 < 0) {
-            const float zo = (float)nn + dz, zn = (float)nn + zeta;
-            const float tc = zo / (zo - zn);
-            const float Xo = (float)m + dr;
-            const float xh = Xo + tc * (X - Xo), yh = tc * y;
-            const float rhit = sqrtf(xh * xh + yh * yh);   // cells
-            if (rhit <= rc_cells) {
-              atomicAdd(SP == 1 ? &S->cnt_ion_cath : &S->cnt_e_cath, 1ULL);
-              if (SP == 1 && I.ied_bins > 0) {
-                const double rh = (double)rhit * I.dr;
-                if (rh >= I.band_lo && rh <= I.band_hi) {
-                  const double E = 0.5 * I.mass[1] *
-                                   ((double)vr * vr + (double)vt * vt + (double)vz * vz) / kQe;
-                  const double fb = floor(E / I.ied_de);
-                  atomicAdd(&I.reg.ied[fb < (double)I.ied_bins ? (int)fb : I.ied_bins], 1ULL);
-                }
-              }
-              if (I.gamma[SP] > 0.0) {
-                const long long id = id_of(b);
-                double u[4];
-                draws(I, SP, id, step, 2, u);
-                if (u[0] < I.gamma[SP]) {
-                  atomicAdd(&S->cnt_sey, 1ULL);
-                  int mh = (int)floorf(rhit);
-                  float drh = rhit - (float)mh;
-                  if (mh > I.nr - 1) { mh = I.nr - 1; drh = 1.0f; }
-                  add_birth32(I, 0, ((unsigned long long)id << 2) | (SP == 1 ? 1ULL : 2ULL), mh,
-                              drh, 0, 0.0f, 0.0f, 0.0f, 0.0f);
-                }
-              }
-            }
-          }
+          if (n1 < 0)
+            cathode_hit32<SP>(I, (float)m + dr, X, y, (float)nn + dz, (float)nn + zeta, vr, vt,
+                              vz, b, step);
         }
         if (alive) {
           if (SP == 0 && I.mcc_on && mcc_candidate(I, id_of(b), step)) {
