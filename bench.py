@@ -46,9 +46,9 @@ UNIT = "particle-steps/s"
 # and the births append when full sorts are periodic
 KERNELS_PER_STEP = 12
 # full cell sort period of the default runs (256 x 256, 4e7 per species,
-# measured: FP64 6.19e9 / 6.74e9 / 6.83e9 particle-steps/s at 1 / 8 / 16;
-# FP32 2.35e10 / 2.53e10 / 2.60e10 at 1 / 2 / 4)
-SORT_EVERY_DEFAULT = {"fp64": 16, "fp32": 4}
+# measured over 128 timed steps: FP64 7.84e9 / 7.92e9 / 7.95e9 particle-steps/s
+# at 16 / 32 / 64; FP32 2.85e10 / 2.99e10 / 3.13e10 at 8 / 16 / 32)
+SORT_EVERY_DEFAULT = {"fp64": 32, "fp32": 32}
 FLOPS_PER_PARTICLE = {0: 69.0, 1: 77.0}   # EC, MC (h E and h B from per-species tables; positions in cell units)
 # Algorithmic HBM bytes of one particle-step: read and write r, z, v_r,
 # v_theta, v_z, id once (FP64).
@@ -59,7 +59,7 @@ BYTES_PER_PARTICLE_FP32 = 64.0
 # (dram__bytes_read.sum + dram__bytes_write.sum) on this workload at full size
 # (profiles/traffic_push_rz256_ring_4e7.md); None until measured on the
 # kernel as it stands.
-TRAFFIC_PER_PARTICLE = {"fp64": 89.4, "fp32": 66.0}
+TRAFFIC_PER_PARTICLE = {"fp64": 89.4, "fp32": None}
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA pipes-lanes per SM per clock x 2
 # flop x 2.07 GHz = 1.26 TFLOP/s (nominal 1.25); scaled to the measured clock.
 FP64_FLOP_PER_CLK = 152 * 2 * 2
