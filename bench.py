@@ -59,7 +59,7 @@ BYTES_PER_PARTICLE_FP32 = 64.0
 # (dram__bytes_read.sum + dram__bytes_write.sum) on this workload at full size
 # (profiles/traffic_push_rz256_ring_4e7.md); None until measured on the
 # kernel as it stands.
-TRAFFIC_PER_PARTICLE = {"fp64": 89.4, "fp32": None}
+TRAFFIC_PER_PARTICLE = {"fp64": 89.4, "fp32": 65.7}
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA pipes-lanes per SM per clock x 2
 # flop x 2.07 GHz = 1.26 TFLOP/s (nominal 1.25); scaled to the measured clock.
 FP64_FLOP_PER_CLK = 152 * 2 * 2
