@@ -97,6 +97,21 @@ def test_fp32_one_step_busy_state(pg, gather, rweight):
     assert d["n_ionize"] > 0 and d["n_sey"] > 0
 
 
+def test_fp32_collision_queue_overflow(pg):
+    """A collision-dominated gas (p_null about 0.83): more candidates per chunk
+    than the FP32 queue holds (256); the rest run from the per-thread masks."""
+    p = pic_inputs.params_rz32()
+    p.update(n_gas=200.0 * p["n_gas"], poisson_tol=1e-12, circuit_mode=1, Vs=400.0,
+             Rext=100.0, n_avg=3)
+    p, parts = busy_state(p, ppc=16, seed=47)
+    p, orc, h = _pair32(pg, p, parts)
+    orc.step(1)
+    pg.pic_step(h, 1)
+    _check(pg, h, orc)
+    d = pg.pic_diagnostics(h, 0)
+    assert d["n_elastic"] + d["n_excite"] + d["n_ionize"] > 2048
+
+
 def test_fp32_metastable_ionization(pg):
     """Reaction (1d) in FP32 mode against the FP64 oracle (dense Ar* so that
     the step has tens of events)."""

@@ -74,6 +74,23 @@ def test_one_step_busy_state(pg, gather, rweight):
 
 
 @pytest.mark.parametrize("gather", [0, 1])
+def test_collision_queue_overflow(pg, gather):
+    """A collision-dominated gas (200 x the density: p_null about 0.83): in the
+    first step's 1024-particle chunks more electrons are collision candidates
+    than the per-chunk queue holds (512), so the rest run from the per-thread
+    masks after the queue; the step still matches the oracle."""
+    p = pic_inputs.params_rz32(gather=gather)
+    p.update(n_gas=200.0 * p["n_gas"], poisson_tol=1e-13, circuit_mode=1, Vs=400.0, Rext=100.0,
+             n_avg=3)
+    p, parts = busy_state(p, ppc=16, seed=43 + gather)
+    p, orc, h = _pair(pg, p, parts)
+    orc.step(1)
+    pg.pic_step(h, 1)
+    d = _check_step(pg, h, orc)
+    assert d["n_elastic"] + d["n_excite"] + d["n_ionize"] > 2048
+
+
+@pytest.mark.parametrize("gather", [0, 1])
 def test_metastable_ionization_and_electron_sey(pg, gather):
     """Reaction (1d) off an Ar* background (dense here, 3e20 m^-3, so that a
     step has tens of events) and electron-induced secondary emission at the
