@@ -94,8 +94,8 @@ def parse():
                          "(phi still solved to poisson_tol); 0: from phi^(n-1)")
     ap.add_argument("--sort-every", type=int, default=None,
                     help="full cell sort every this many steps (births appended in place "
-                         "between; results do not depend on it); default 16 for fp64, "
-                         "4 for fp32 (the fastest measured)")
+                         "between; results do not depend on it); default 32 for both "
+                         "precisions (the fastest measured)")
     ap.add_argument("--geometry", default="rz256", choices=["rz256", "paper"],
                     help="rz256 workload's chamber: rz256 = 5 x 5 cm, cathode disk r <= 2 cm, "
                          "other walls grounded; paper = the 3 x 3 cm chamber of Section 3 "
