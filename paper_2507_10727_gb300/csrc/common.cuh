@@ -277,8 +277,10 @@ __device__ __forceinline__ bool mcc_candidate(const Inst& I, long long id, long 
 // ---------------------------------------------------------------------------
 // grid helpers
 // ---------------------------------------------------------------------------
-// cell k = (int)(x / d) (clamped to ncell - 1) and offset f = x / d - k, with
-// x / d taken as x * inv_d; the split runs on the integer pipes (bits.cuh)
+// cell k = (int)(x / d) (clamped to ncell - 1) and offset f = x / d - k of an
+// SI coordinate, with x / d taken as x * inv_d; the split runs on the integer
+// pipes (bits.cuh).  FP64 particle positions are stored in cell units and
+// split directly (split_cell).
 __device__ __forceinline__ void locate(double x, double inv_d, int ncell, int& k, double& f) {
   split_cell(x * inv_d, ncell, k, f);
 }

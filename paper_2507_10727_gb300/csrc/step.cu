@@ -138,6 +138,8 @@ __global__ void k_field_tables(Inst I) {
 // ---------------------------------------------------------------------------
 // births
 // ---------------------------------------------------------------------------
+// A particle born this step at (r, z) in cell units with velocity (m/s): the
+// births buffer of its species, its cell's count and its charge.
 __device__ void add_birth(const Inst& I, int sp, unsigned long long pkey, double r, double z,
                           double vr, double vt, double vz) {
   Scalars* S = I.S;
