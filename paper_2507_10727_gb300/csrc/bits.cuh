@@ -6,8 +6,9 @@
 // of short FP64 sequences (truncation + conversion + subtraction; scaling +
 // rounding conversion) using integer operations on the bit pattern, which run
 // on the wide integer pipes.  Each falls back to the FP64 sequence outside the
-// range it handles.  Host and device versions are the same code, so the
-// equivalence is checked on the CPU.
+// range it handles.  Also here: the conversions of particle positions between SI
+// and cell units (pic_set_particles / pic_get_particles).  Host and device
+// versions are the same code, so the equivalences are checked on the CPU.
 #pragma once
 
 #include <cmath>
@@ -146,6 +147,30 @@ PIC_HD double recip2_refine(double x, double y) {
   e = fma(-x, y, 1.0);
   const double y2 = double_of(bits_of(y) + (1ULL << 52));
   return fma(y2, e, y2);
+}
+
+// SI coordinate x on an axis of length X = ncell d -> cell units x / d (as
+// x * inv_d).  The domain test is kept: x in [0, X) gives a value below
+// ncell (a product rounded up to ncell is moved one ulp down), x >= X one of
+// at least ncell; negative and NaN x stay negative / NaN.
+// the next double toward zero of a positive finite x (nextafter(x, 0))
+PIC_HD double next_down(double x) { return double_of(bits_of(x) - 1ULL); }
+
+PIC_HD double to_cells(double x, double inv_d, int ncell, double X) {
+  double s = x * inv_d;
+  if (x < X) {
+    if (s >= (double)ncell) s = next_down((double)ncell);
+  } else if (x >= X && s < (double)ncell) {
+    s = (double)ncell;
+  }
+  return s;
+}
+
+// cell units s in [0, ncell) -> SI s d, kept below X = ncell d (host and
+// device give the same value: one rounded product and a clamp)
+PIC_HD double from_cells(double s, double d, double X) {
+  const double x = s * d;
+  return x < X ? x : next_down(X);
 }
 
 }  // namespace pic

@@ -285,26 +285,6 @@ __device__ __forceinline__ void locate(double x, double inv_d, int ncell, int& k
   split_cell(x * inv_d, ncell, k, f);
 }
 
-// SI coordinate x on an axis of length X = ncell d -> cell units x / d (as
-// x * inv_d).  The domain test is kept: x in [0, X) gives a value below
-// ncell (a product rounded up to ncell is moved one ulp down), x >= X one of
-// at least ncell; negative and NaN x stay negative / NaN.
-__device__ __forceinline__ double to_cells(double x, double inv_d, int ncell, double X) {
-  double s = x * inv_d;
-  if (x < X) {
-    if (s >= (double)ncell) s = nextafter((double)ncell, 0.0);
-  } else if (x >= X && s < (double)ncell) {
-    s = (double)ncell;
-  }
-  return s;
-}
-
-// cell units s in [0, ncell) -> SI s d, kept below X = ncell d (host and
-// device give the same value: one rounded product and a clamp)
-__host__ __device__ __forceinline__ double from_cells(double s, double d, double X) {
-  const double x = s * d;
-  return x < X ? x : nextafter(X, 0.0);
-}
 
 __device__ __forceinline__ int cell_key(const Inst& I, int m, int n) {
   int tile = (m >> 3) * I.ntz + (n >> 3);

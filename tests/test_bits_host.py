@@ -13,7 +13,11 @@ runs both forms over random and edge-case inputs.
 * recip_refine(x, seed): within one ulp of 1.0 / x for seeds up to two FP32
   ulps from the rounded FP32 reciprocal (the device seed, PTX rcp.approx, is
   within one), x in [1, 4) and log-uniform over 1e-30 .. 1e30;
-* recip2_refine(x, seed): bit for bit 2 recip_refine(x, seed) on the same x.
+* recip2_refine(x, seed): bit for bit 2 recip_refine(x, seed) on the same x;
+* to_cells / from_cells (positions between SI and cell units) on axes of 2 .. 4096
+  cells of random lengths: x in [0, X) lands in [0, ncell), x >= X at or above ncell,
+  x < 0 below 0, NaN stays NaN; from_cells lands in [0, X) and the round trip is within
+  4 ulp of x (x of at least one cell; within 4 ulp of the cell width below that).
 """
 import os
 import subprocess
@@ -55,6 +59,20 @@ static void check_recip(double x) {
     ++n; if (!same(recip2_refine(x, (double)sd), 2.0 * y)) { if (bad < 5) std::printf("recip2 %.17g\n", x); ++bad; }
   }
 }
+static void check_cells(double x, double d, int ncell) {
+  const double X = ncell * d, inv = 1.0 / d;
+  const double s = to_cells(x, inv, ncell, X);
+  bool ok;
+  if (x != x) ok = s != s;
+  else if (x < 0.0) ok = s < 0.0;
+  else if (x >= X) ok = s >= (double)ncell;
+  else {
+    const double back = from_cells(s, d, X);
+    const double tol = 4.0 * std::ldexp(1.0, -52) * (x > d ? x : d);
+    ok = s >= 0.0 && s < (double)ncell && back >= 0.0 && back < X && std::fabs(back - x) <= tol;
+  }
+  ++n; if (!ok) { if (bad < 5) std::printf("cells %.17g %.17g %d -> %.17g\n", x, d, ncell, s); ++bad; }
+}
 static void check_cmp(double x, double c) {
   ++n; if (lt_zero(x) != (x < 0.0) || ge_pos(x, c) != (x >= c)) {
     if (bad < 5) std::printf("cmp %.17g %.17g\n", x, c); ++bad; }
@@ -92,6 +110,16 @@ int main() {
   }
   for (int t = 0; t < 1000000; ++t) check_recip(1.0 + 3.0 * u(g));
   for (int t = 0; t < 1000000; ++t) check_recip(std::pow(10.0, -30.0 + 60.0 * u(g)));
+  for (int ncell : {2, 32, 256, 512, 4096}) {
+    for (int t = 0; t < 2000; ++t) {
+      const double d = std::pow(10.0, -6.0 + 4.0 * u(g)) / ncell * 1000.0;
+      const double X = ncell * d;
+      for (int k = 0; k < 50; ++k) check_cells(u(g) * X, d, ncell);
+      for (double x : {0.0, -0.0, X, std::nextafter(X, 0.0), std::nextafter(X, 1e300), 2.0 * X,
+                       -1e-300, -X, d, std::nextafter(d, 0.0), 5e-324, (double)NAN})
+        check_cells(x, d, ncell);
+    }
+  }
   std::printf("checked %lld mismatches %lld\n", n, bad);
   return bad != 0;
 }
