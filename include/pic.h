@@ -280,9 +280,12 @@ int pic_region_read(pic_handle* h, int instance, pic_regions* out, double* zs, d
                     int64_t* ied, int64_t* ied_overflow);
 int pic_region_reset(pic_handle* h, int instance);
 
-/* Checkpoint of one instance to / from a file (particles, phi, circuit
- * state, step and id counters, weight).  A resumed run continues bit for bit
- * up to the order of particles inside a cell.  Synchronous. */
+/* Checkpoint of one instance to / from a file (particles as stored on the
+ * device, FP64 positions in cell units; phi and the solution before it, the
+ * start of an extrapolated solve; circuit state, step and id counters,
+ * weight).  A resumed run continues bit for bit up to the order of particles
+ * inside a cell.  The file is for a handle of the same grid, n_avg and
+ * precision (PIC_ERR_IO otherwise).  Synchronous. */
 int pic_save(pic_handle* h, int instance, const char* path);
 int pic_load(pic_handle* h, int instance, const char* path);
 
