@@ -85,3 +85,21 @@ def test_network_parameter_count_matches_reference(lib):
     import paper_2507_10727_gb300 as pg
     from oracle import unet
     assert pg.pic_unet_param_count() == unet.n_params(unet.init_params(0))
+
+
+def test_invalid_options_rejected_without_gpu(lib):
+    """Each option outside its documented range is rejected by pic_create
+    before any device call (PIC_ERR_INVALID, no handle)."""
+    L, _ = lib
+    import paper_2507_10727_gb300 as pg
+    import pic_inputs
+    L.pic_create.argtypes = [C.POINTER(pg.PicConfig), C.c_int, C.c_void_p, C.c_void_p,
+                             C.POINTER(C.c_void_p)]
+    base = pic_inputs.params_rz32() | dict(cap_e=10, cap_i=10, birth_cap=10)
+    for bad in (dict(phi_extrapolate=2), dict(phi_extrapolate=-1), dict(sort_every=0),
+                dict(sort_every=65), dict(ied_bins=-1), dict(ied_bins=65537),
+                dict(ied_bins=10, ied_emax=0.0)):
+        cfg = pg.PicConfig.from_params(base | bad)
+        out = C.c_void_p()
+        assert L.pic_create(C.byref(cfg), 1, None, None, C.byref(out)) == -1, bad
+        assert out.value is None, bad
