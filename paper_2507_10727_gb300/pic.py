@@ -267,7 +267,9 @@ def _f64(a):
 
 
 def pic_set_particles(h: Handle, instance: int, species: int, d: dict):
-    """Load particles from numpy arrays (host) or CUDA tensors (device)."""
+    """Load particles from host arrays (numpy arrays or CPU tensors, passed
+    without a copy: page-locked memory, e.g. a tensor's pin_memory(), is read
+    in place by the load kernels) or CUDA tensors (device)."""
     keys = ("r", "z", "vr", "vt", "vz")
     first = d["r"]
     if hasattr(first, "is_cuda") and first.is_cuda:
