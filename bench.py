@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -83,6 +84,17 @@ def parse():
     ap.add_argument("--cpu-sample", type=float, default=8e6,
                     help="oracle sample size per species for the CPU baseline")
     ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--cpu-sample-per-core", type=float, default=2e6,
+                    help="particles per species of each oracle process of the all-cores "
+                         "CPU baseline (and of the reference arm)")
+    ap.add_argument("--cpu-procs", type=int, default=0,
+                    help="oracle processes of the all-cores CPU baseline (0: one per core "
+                         "this process may run on)")
+    ap.add_argument("--cpu-cores-steps", type=int, default=8,
+                    help="timed oracle steps per process of the all-cores CPU baseline")
+    ap.add_argument("--no-subrecords", action="store_true",
+                    help="only the headline FP64 line: skip the FP32, ensemble and learned "
+                         "warm-start sub-records")
     ap.add_argument("--workload", default="rz256",
                     choices=["rz256", "sweep16", "learned", "unet", "precision"],
                     help="rz256: one 256x256 discharge; sweep16: the 16-discharge "
@@ -146,6 +158,9 @@ def config_block(p, n, args):
                               else "phi^(n-1)"),
             "insulating_boundary": {"z0_outside_cathode": p["gap_neumann"],
                                     "wall_r_R": p["wall_neumann"]},
+            "poisson_precond": ("multigrid V-cycle" if p["poisson_precond"] == 1 or p["gap_neumann"]
+                                or p["wall_neumann"] else
+                                "sine transform along z + tridiagonal solves in r (FP32)"),
             "l2": "inputs larger than L2 (particle state 3.8 GB >> 129 MB)"}
 
 
@@ -177,11 +192,11 @@ class ClockSampler:
     def __init__(self, gpu_id: str):
         self.gpu_id = gpu_id
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.tmp = tempfile.TemporaryDirectory(prefix="pic_clocks_")
+        self.path = os.path.join(self.tmp.name, "clocks.csv")
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
@@ -203,6 +218,12 @@ class ClockSampler:
             self.f.close()
 
     def summary(self):
+        try:
+            return self._summary()
+        finally:
+            self.tmp.cleanup()
+
+    def _summary(self):
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
         sm, smax, reasons = [], [], set()
@@ -265,25 +286,110 @@ def cpu_baseline(p, parts, sample: int, steps: int, seed: int):
                       f"{p['nr'] + 1}x{p['nz'] + 1}), single-threaded C, {dt:.1f} s"}
 
 
+def host_cores() -> int:
+    """Cores this process may run on (the affinity mask, not the machine's count)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_replica(k, p, n, steps, warm, seed, barrier, queue):
+    """One process of the all-cores oracle run: its own sample of the workload
+    (the same synthetic state drawn with n particles per species), `warm`
+    untimed steps, then `steps` timed ones started together with the others."""
+    try:
+        import oracle
+        p2, parts = pic_inputs.grown_ring_state(p, n, seed=seed + 1000 + k)
+        orc = oracle.Oracle(p2, parts)     # includes the one-time Cholesky factorisation
+        del parts
+        if warm:
+            orc.step(warm)
+        barrier.wait(timeout=600)
+        t0 = time.time()
+        total = 0
+        for _ in range(steps):
+            total += orc.count(0) + orc.count(1)
+            orc.step(1)
+        queue.put((k, total, t0, time.time(), None))
+    except Exception as exc:   # reported by the parent
+        queue.put((k, 0, 0.0, 0.0, repr(exc)))
+
+
+def cpu_baseline_all_cores(p, n: int, steps: int, warm: int, seed: int, procs: int = 0):
+    """The oracle as it stands on every host core: one single-threaded oracle
+    process per core, each on its own n-per-species sample of the workload,
+    timed together; value = all processes' particle-steps / the common wall
+    time.  Processes are spawned (not forked: the parent holds a CUDA context)."""
+    import multiprocessing as mp
+    from oracle import build as oracle_build
+    oracle_build.build()                   # built once, before the processes load it
+    procs = procs or host_cores()
+    ctx = mp.get_context("spawn")
+    barrier, queue = ctx.Barrier(procs), ctx.Queue()
+    env_keep = os.environ.get("OMP_NUM_THREADS")
+    os.environ["OMP_NUM_THREADS"] = "1"
+    workers = [ctx.Process(target=_oracle_replica,
+                           args=(k, p, n, steps, warm, seed, barrier, queue), daemon=True)
+               for k in range(procs)]
+    for w in workers:
+        w.start()
+    if env_keep is None:
+        os.environ.pop("OMP_NUM_THREADS")
+    else:
+        os.environ["OMP_NUM_THREADS"] = env_keep
+    res = [queue.get(timeout=1800) for _ in workers]
+    for w in workers:
+        w.join(timeout=60)
+    errors = [r[4] for r in res if r[4]]
+    if errors:
+        raise RuntimeError(f"oracle process failed: {errors[0]}")
+    total = sum(r[1] for r in res)
+    t = max(r[3] for r in res) - min(r[2] for r in res)
+    cpu = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    cpu = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"value": total / t, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"{procs} single-threaded oracle processes, one per core, each on its own "
+                      f"{n:.0e}-per-species draw of the same synthetic state, {steps} full "
+                      f"steps each (push, MCC, deposit, banded-Cholesky Poisson on "
+                      f"{p['nr'] + 1}x{p['nz'] + 1}) after {warm} untimed, {t:.1f} s wall",
+            "ms_per_step": t / steps * 1e3, "particles_per_step": total / steps,
+            "cpu_model": cpu, "nproc": os.cpu_count()}
+
+
 def run_reference(args, rank, world):
-    """--impl reference: the CPU oracle as it stands, on a bounded sample."""
+    """--impl reference: the CPU oracle as it stands, on every host core, on a
+    bounded sample of the workload (one sample per core)."""
     if rank != 0:
         return
-    p, parts = workload(args)
-    n = int(args.n_per_species)
-    vals = []
-    # no warm-up runs: the oracle is plain single-threaded C (nothing compiles or
-    # caches on first use) and each sample's factorisation is outside its timing
-    res = None
-    for _ in range(max(1, args.steps if args.steps <= 3 else 3)):
-        res = cpu_baseline(p, parts, int(args.cpu_sample), args.cpu_steps, args.seed)
-        vals.append(res["value"])
-    v = statistics.median(vals)
-    res["value"] = v
+    g = 0 if args.gather == "ec" else 1
+    p = (pic_inputs.params_paper(gather=g, seed=args.seed, cells=256) if args.geometry == "paper"
+         else pic_inputs.params_rz256(gather=g, seed=args.seed))
+    p.update(precision=1 if args.precision == "fp32" else 0, sort_every=args.sort_every,
+             phi_extrapolate=args.phi_extrapolate, diag_every=10)
+    n = int(args.cpu_sample_per_core)
+    res = cpu_baseline_all_cores(p, n, max(1, args.steps), max(0, args.warmup), args.seed,
+                                 args.cpu_procs)
+    v = res["value"]
+    cfg = config_block(p, n * res["cores"], args)
+    # the workload sampled is the GPU arm's (same grid, parameters and synthetic
+    # state); n_per_species states the particles actually stepped
+    cfg["workload"] = config_block(p, int(args.n_per_species), args)["workload"]
+    cfg["sample"] = {"processes": res["cores"], "n_per_species_per_process": n,
+                     "note": "n_per_species is the total over the processes; every process "
+                             "steps its own discharge (same synthetic state, own draw)"}
+    cfg["l2"] = "host run"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 2 * n / v * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_block(p, n, args), "cpu_baseline": res,
+            "data": "synthetic", "config": cfg, "cpu_baseline": res,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -309,7 +415,7 @@ def sweep_workload(args):
     return out
 
 
-def run_sweep(args, torch, pg):
+def run_sweep(args, torch, pg, emit: bool = True):
     insts = sweep_workload(args)
     ntot = sum(2 * parts["e"]["r"].shape[0] for _, parts in insts)
     warm = AUTOTUNE_STEPS + args.warmup
@@ -373,13 +479,15 @@ def run_sweep(args, torch, pg):
             "sequential_16_value": seq, "ensemble_over_sequential": value / seq,
             "autotuned_particles_per_thread": tuned, "cuda_graph": graph,
             "per_kernel_ms_per_step": {k: v["total_ms"] / nprof for k, v in prof.items()}}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 # ---------------------------------------------------------------------------
 # learned warm start workload: 256 x 512 cells, 10 cm long, 5e7 per species
 # ---------------------------------------------------------------------------
-def run_learned(args, torch, pg):
+def run_learned(args, torch, pg, emit: bool = True):
     g = 0 if args.gather == "ec" else 1
     n = int(args.n_per_species) if args.n_per_species != 4e7 else int(5e7)
     p = pic_inputs.params_rz256x512(gather=g, seed=args.seed)
@@ -388,6 +496,10 @@ def run_learned(args, torch, pg):
     p["diag_every"] = 10
     p["precision"] = 1 if args.precision == "fp32" else 0
     p["sort_every"] = args.sort_every
+    # the network proposes starts for the multigrid-preconditioned solve (the
+    # sine-transform preconditioner reaches the tolerance in two iterations
+    # from any start)
+    p["poisson_precond"] = 1
     h = pg.pic_create(p)
     for k, sp in (("e", 0), ("i", 1)):
         pg.pic_set_particles(h, 0, sp, parts[k])
@@ -459,14 +571,17 @@ def run_learned(args, torch, pg):
                        "grid": [p["nr"], p["nz"]], "domain_m": [p["R"], p["L"]],
                        "n_per_species": n, "unet_mode": args.unet_mode,
                        "snapshots": args.snapshots, "train_iters": args.train_iters,
+                       "poisson_precond": "multigrid V-cycle (both arms)",
                        "train_batch": args.train_batch, "poisson_tol": p["poisson_tol"],
                        "sort_every": p["sort_every"],
                        "l2": "inputs larger than L2"},
             "plain": plain, "warm": warm, "cold_start": cold,
             "training": {"loss_first": loss0, "loss_last": loss1, "seconds": t_train,
                          "record_seconds": t_rec, "stats": pg.pic_unet_stats(h)}}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
     pg.pic_destroy(h)
+    return line
 
 
 # ---------------------------------------------------------------------------
@@ -579,6 +694,150 @@ def run_precision(args, torch, pg):
 
 
 # ---------------------------------------------------------------------------
+# one discharge: create, load, tune, warm up, time K steps, per-kernel times
+# ---------------------------------------------------------------------------
+def timed_discharge(pg, torch, p, parts, args, local=0, world=1, barrier=lambda: None):
+    """Time args.steps steps of one discharge (CUDA events on the handle's
+    stream, graph replay), after the autotuner's steps and args.warmup warm-up
+    steps; then per-kernel CUDA-event times over a second pass of the same
+    step.  Returns the handle and a record."""
+    h = pg.pic_create(p)
+    for k, sp in (("e", 0), ("i", 1)):
+        pg.pic_set_particles(h, 0, sp, parts[k])
+    pg.pic_solve_fields(h, 0)
+    # the first 4 steps of a handle tune the push's chunk size (eager, untimed)
+    pg.pic_step(h, AUTOTUNE_STEPS)
+    pg.pic_step(h, args.warmup)
+    pg.pic_sync(h)
+    d0 = pg.pic_diagnostics(h, 0)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_uuid(torch, local)) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        pg.pic_step(h, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    d1 = pg.pic_diagnostics(h, 0)
+    pg.pic_profile(h, True)
+    pg.pic_step(h, min(args.steps, 10))
+    prof = pg.pic_profile_read(h)
+    pg.pic_profile(h, False)
+    prof_steps = max(1, prof["push"]["launches"])
+    per_kernel = {k: v["total_ms"] / prof_steps for k, v in prof.items()}
+    return h, {"ms": ms, "psteps": d1["particle_steps"] - d0["particle_steps"], "d1": d1,
+               "per_kernel": per_kernel, "clocks": clk.summary()}
+
+
+def push_roofline(precision, gather, rec, n_pushed, peaks, peak_kind):
+    """Roofline of the dominant kernel, the push of both species (one launch per
+    step): algorithmic HBM bytes per particle-step (read and write the particle
+    state once: 96 B FP64, 64 B FP32) x particles / its CUDA-event time against
+    the measured copy bandwidth; for FP64 also the FP64-pipe view (algorithmic
+    flops against 152 SMs x 4 flop/clk at the loaded clock), where that kernel
+    is bound."""
+    push_ms = rec["per_kernel"]["push"]
+    bpp = BYTES_PER_PARTICLE if precision == "fp64" else BYTES_PER_PARTICLE_FP32
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bw = bpp * n_pushed / (push_ms / 1e3) / 1e9
+    line = {"bound": "hbm", "kernel": ("k_push_all" if precision == "fp64" else "k_push32_all")
+            + " (both species)", "achieved": bw, "peak": hbm, "unit": "GB/s",
+            "frac": bw / hbm, "traffic": (TRAFFIC_PER_PARTICLE[precision] * n_pushed
+                                          if TRAFFIC_PER_PARTICLE[precision] else None),
+            "peak_kind": peak_kind, "bytes_per_particle": bpp, "particles_per_launch": n_pushed,
+            "push_ms": push_ms, "per_kernel_ms_per_step": rec["per_kernel"]}
+    if precision == "fp64":
+        sm_mhz = rec["clocks"].get("sm_mhz") or 2070.0
+        fp64_peak = FP64_FLOP_PER_CLK * sm_mhz * 1e6 / 1e12
+        fl = FLOPS_PER_PARTICLE[gather] * n_pushed / (push_ms / 1e3) / 1e12
+        line["alu_view"] = {"bound": "alu", "achieved": fl, "peak": fp64_peak, "unit": "TFLOP/s",
+                            "frac": fl / fp64_peak, "flops_per_particle": FLOPS_PER_PARTICLE[gather],
+                            "peak_kind": "derived",
+                            "peak_note": f"FP64 pipes: 152 SMs x 4 flop/clk at the median loaded "
+                                         f"SM clock {sm_mhz:.0f} MHz (1.25 TFLOP/s nominal at "
+                                         f"2.07 GHz)"}
+    return line
+
+
+def end_to_end(pg, torch, p, parts, args):
+    """The metric through the C ABI with host buffers: upload of the state from
+    pinned host memory, the field solve, then every step pic_step and a
+    diagnostics read-back."""
+    import ctypes
+    pinned = {k: {q: torch.from_numpy(a).pin_memory() for q, a in parts[k].items()}
+              for k in ("e", "i")}
+    state_bytes = sum(v.numel() * v.element_size() for k in pinned for v in pinned[k].values())
+    h2 = pg.pic_create(p)
+    torch.cuda.synchronize()
+    lib = pg.load_library()
+    t0 = time.perf_counter()
+    for k, sp in (("e", 0), ("i", 1)):
+        a = pinned[k]
+        rc = lib.pic_set_particles(h2.ptr, 0, sp, a["r"].numel(), a["r"].data_ptr(),
+                                   a["z"].data_ptr(), a["vr"].data_ptr(), a["vt"].data_ptr(),
+                                   a["vz"].data_ptr(), a["id"].data_ptr(), 0)
+        assert rc == 0, rc
+    pg.pic_solve_fields(h2, 0)
+    ps0 = pg.pic_diagnostics(h2, 0)["particle_steps"]
+    de = None
+    for _ in range(args.steps):
+        pg.pic_step(h2, 1)
+        de = pg.pic_diagnostics(h2, 0)
+    t_e2e = time.perf_counter() - t0
+    pg.pic_destroy(h2)
+    return {"value": (de["particle_steps"] - ps0) / t_e2e, "unit": UNIT,
+            "h2d_bytes_per_step": state_bytes / args.steps,
+            "d2h_bytes_per_step": float(ctypes.sizeof(pg.PicDiag)),
+            "note": "whole job through the C ABI: state upload from pinned host buffers "
+                    "(amortised over the steps), field solve, then per step pic_step + "
+                    "pic_diagnostics read-back"}
+
+
+def sub_records(args, torch, pg, p, parts, peaks, peak_kind, local, fp64_value):
+    """The other forms, each timed on its own: the FP32 particle mode on the
+    same workload and state, the 16-discharge ensemble against 16 sequential
+    runs (both precisions), the learned Poisson warm start against the plain
+    solver on the 256 x 512 workload."""
+    out = {}
+    g = 0 if args.gather == "ec" else 1
+    try:
+        p32 = dict(p, precision=1, sort_every=SORT_EVERY_DEFAULT["fp32"])
+        h, rec = timed_discharge(pg, torch, p32, parts, args, local)
+        n_pushed = pg.pic_count(h, 0, 0) + pg.pic_count(h, 0, 1)
+        out["fp32"] = {"value": rec["psteps"] / (rec["ms"] / 1e3), "unit": UNIT,
+                       "ms_per_step": rec["ms"] / args.steps, "over_fp64": None,
+                       "config": {"workload": f"rz256_ring_{int(args.n_per_species):.0e}_per_species_"
+                                              "fp32".replace("+", ""),
+                                  "sort_every": p32["sort_every"], "same_state_as_headline": True},
+                       "push_particles_per_thread": pg.pic_tuned_chunk(h),
+                       "poisson": {"iters_last_step": rec["d1"]["poisson_iters"],
+                                   "ms_per_step": rec["per_kernel"]["poisson"]},
+                       "roofline": push_roofline("fp32", g, rec, n_pushed, peaks, peak_kind),
+                       "clocks": rec["clocks"]}
+        out["fp32"]["over_fp64"] = out["fp32"]["value"] / fp64_value
+        pg.pic_destroy(h)
+    except Exception as exc:   # a failed sub-record is reported, the headline stands
+        out["fp32"] = {"error": repr(exc)}
+    for prec in ("fp32", "fp64"):
+        try:
+            a = argparse.Namespace(**vars(args))
+            a.precision, a.sort_every = prec, SORT_EVERY_DEFAULT[prec]
+            out[f"sweep16_{prec}"] = run_sweep(a, torch, pg, emit=False)
+        except Exception as exc:
+            out[f"sweep16_{prec}"] = {"error": repr(exc)}
+    try:
+        a = argparse.Namespace(**vars(args))
+        a.n_per_species = 5e7
+        out["learned"] = run_learned(a, torch, pg, emit=False)
+    except Exception as exc:
+        out["learned"] = {"error": repr(exc)}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def main():
@@ -620,46 +879,18 @@ def main():
 
     p, parts = workload(args)
     n = int(args.n_per_species)
-    h = pg.pic_create(p)
-    for k, sp in (("e", 0), ("i", 1)):
-        pg.pic_set_particles(h, 0, sp, parts[k])
-    pg.pic_solve_fields(h, 0)
-    # the first 4 steps of a handle tune the push's chunk size (eager, untimed)
-    pg.pic_step(h, AUTOTUNE_STEPS)
-    pg.pic_step(h, args.warmup)
-    pg.pic_sync(h)
-    d0 = pg.pic_diagnostics(h, 0)
-
-    stream = torch.cuda.current_stream()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(gpu_uuid(torch, local)) as clk:
-        barrier()
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        pg.pic_step(h, args.steps)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-    ms = ev0.elapsed_time(ev1)
-    d1 = pg.pic_diagnostics(h, 0)
-    psteps = d1["particle_steps"] - d0["particle_steps"]
-    t = ms / 1e3
-    t, psteps = aggregate_replicas(t, psteps, world, "cuda")
+    peaks, peak_kind = measured_peaks()
+    h, rec = timed_discharge(pg, torch, p, parts, args, local, world, barrier)
+    t, psteps = aggregate_replicas(rec["ms"] / 1e3, rec["psteps"], world, "cuda")
     value = psteps / t
-
-    # per-kernel CUDA-event times over a second timed pass of the same step
-    pg.pic_profile(h, True)
-    pg.pic_step(h, min(args.steps, 10))
-    prof = pg.pic_profile_read(h)
-    pg.pic_profile(h, False)
-    d2 = pg.pic_diagnostics(h, 0)
-    prof_steps = max(1, prof["push"]["launches"])
-    prof_ps = d2["particle_steps"] - d1["particle_steps"]
     ne, ni = pg.pic_count(h, 0, 0), pg.pic_count(h, 0, 1)
+    g = 0 if args.gather == "ec" else 1
+    roofline = push_roofline(args.precision, g, rec, ne + ni, peaks, peak_kind)
 
     # region diagnostics sampler (Sections 4, 5): one warp per cell bin of the
     # sorted arrays; algorithmic bytes = the electron velocities (24 B FP64,
     # the 32 B FP32 record) + the bin ends and the per-cell accumulators
+    stream = torch.cuda.current_stream()
     r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     pg.pic_region_sample(h, 0)
     torch.cuda.synchronize()
@@ -677,98 +908,45 @@ def main():
     region = {"ms_per_sample": reg_ms, "achieved_gbs": reg_bytes / (reg_ms / 1e3) / 1e9,
               "bytes_per_sample": reg_bytes, "Te_eV": regions_out["Te"],
               "z_sheath_m": regions_out["z_sheath"], "z_bulk_m": regions_out["z_bulk"]}
-
-    peaks, peak_kind = measured_peaks()
-    clocks = clk.summary()
-    sm_mhz = clocks.get("sm_mhz") or 2070.0
-    fp64_peak = FP64_FLOP_PER_CLK * sm_mhz * 1e6 / 1e12       # TFLOP/s at the loaded clock
-    # the dominant kernel: the push of both species (one launch per step)
-    push_ms = prof["push"]["total_ms"] / prof_steps
-    n_pushed = ne + ni
-    g = 0 if args.gather == "ec" else 1
-    achieved = FLOPS_PER_PARTICLE[g] * n_pushed / (push_ms / 1e3) / 1e12
-    achieved_bw = BYTES_PER_PARTICLE * n_pushed / (push_ms / 1e3) / 1e9
-    per_kernel = {k: v["total_ms"] / prof_steps for k, v in prof.items()}
-    if args.precision == "fp64":
-        roofline = {"bound": "alu", "kernel": "k_push_all (both species)", "achieved": achieved,
-                    "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                    "traffic": (TRAFFIC_PER_PARTICLE["fp64"] * n_pushed
-                                if TRAFFIC_PER_PARTICLE["fp64"] else None),
-                    "peak_note": f"FP64 pipes: 152 SMs x 4 flop/clk at the median loaded SM "
-                                 f"clock {sm_mhz:.0f} MHz (1.25 TFLOP/s nominal at 2.07 GHz)",
-                    "hbm_view": {"achieved_gbs": achieved_bw, "peak_gbs": peaks.get("hbm_gbs"),
-                                 "frac": achieved_bw / peaks.get("hbm_gbs", 6800.0),
-                                 "peak_kind": peak_kind,
-                                 "bytes_per_particle": BYTES_PER_PARTICLE},
-                    "flops_per_particle": FLOPS_PER_PARTICLE[g],
-                    "particles_per_launch": n_pushed,
-                    "per_kernel_ms_per_step": per_kernel}
-    else:
-        bw32 = BYTES_PER_PARTICLE_FP32 * n_pushed / (push_ms / 1e3) / 1e9
-        roofline = {"bound": "hbm", "kernel": "k_push32_all (both species)", "achieved": bw32,
-                    "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
-                    "frac": bw32 / peaks.get("hbm_gbs", 6800.0),
-                    "traffic": (TRAFFIC_PER_PARTICLE["fp32"] * n_pushed
-                                if TRAFFIC_PER_PARTICLE["fp32"] else None),
-                    "peak_kind": peak_kind, "bytes_per_particle": BYTES_PER_PARTICLE_FP32,
-                    "particles_per_launch": n_pushed,
-                    "per_kernel_ms_per_step": per_kernel}
+    graph, tuned = pg.pic_uses_graph(h), pg.pic_tuned_chunk(h)
+    pg.pic_destroy(h)
 
     # end to end through the C ABI with host buffers: upload the state from
     # pinned host memory, then each step pic_step + a diagnostics read-back
     e2e = None
     if not args.no_e2e:
-        pinned = {}
-        for k in ("e", "i"):
-            pinned[k] = {}
-            for q, a in parts[k].items():
-                t_ = torch.from_numpy(a).pin_memory()
-                pinned[k][q] = t_
-        state_bytes = sum(v.numel() * v.element_size() for k in pinned for v in pinned[k].values())
-        h2 = pg.pic_create(p)
-        torch.cuda.synchronize()
-        lib = pg.load_library()
-        t0 = time.perf_counter()
-        for k, sp in (("e", 0), ("i", 1)):
-            a = pinned[k]
-            rc = lib.pic_set_particles(h2.ptr, 0, sp, a["r"].numel(), a["r"].data_ptr(),
-                                       a["z"].data_ptr(), a["vr"].data_ptr(), a["vt"].data_ptr(),
-                                       a["vz"].data_ptr(), a["id"].data_ptr(), 0)
-            assert rc == 0, rc
-        pg.pic_solve_fields(h2, 0)
-        ps0 = pg.pic_diagnostics(h2, 0)["particle_steps"]
-        for _ in range(args.steps):
-            pg.pic_step(h2, 1)
-            de = pg.pic_diagnostics(h2, 0)
-        t_e2e = time.perf_counter() - t0
-        e2e = {"value": (de["particle_steps"] - ps0) / t_e2e, "unit": UNIT,
-               "h2d_bytes_per_step": state_bytes / args.steps,
-               "d2h_bytes_per_step": float(__import__("ctypes").sizeof(pg.PicDiag)),
-               "note": "whole job through the C ABI: state upload from pinned host buffers "
-                       "(amortised over the steps), field solve, then per step pic_step + "
-                       "pic_diagnostics read-back"}
-        pg.pic_destroy(h2)
+        e2e = end_to_end(pg, torch, p, parts, args)
 
+    subs = {}
     cpu = None
-    if not args.no_cpu_baseline and rank == 0 and world == 1:
-        cpu = cpu_baseline(p, parts, int(args.cpu_sample), args.cpu_steps, args.seed)
+    if rank == 0 and world == 1:
+        if not args.no_subrecords:
+            subs = sub_records(args, torch, pg, p, parts, peaks, peak_kind, local, value)
+        del parts
+        if not args.no_cpu_baseline:
+            cpu = cpu_baseline_all_cores(p, int(args.cpu_sample_per_core), args.cpu_cores_steps,
+                                         1, args.seed, args.cpu_procs)
+            p1, parts1 = workload(args)
+            cpu["single_thread"] = cpu_baseline(p1, parts1, int(args.cpu_sample), args.cpu_steps,
+                                                args.seed)
+            del parts1
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+                "ms_per_step": rec["ms"] / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "f32",
                 "data": "synthetic", "config": config_block(p, n, args),
                 "gpu_launches": args.steps * (KERNELS_PER_STEP + (1 if args.sort_every > 1 else 0)),
-                "cuda_graph": pg.pic_uses_graph(h),
-                "autotune_steps": AUTOTUNE_STEPS, "push_particles_per_thread": pg.pic_tuned_chunk(h),
-                "poisson": {"iters_last_step": d1["poisson_iters"],
-                            "resid_last_step": d1["poisson_resid"],
-                            "ms_per_step": per_kernel["poisson"]},
-                "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
-                "region_diagnostics": region}
+                "cuda_graph": graph,
+                "autotune_steps": AUTOTUNE_STEPS, "push_particles_per_thread": tuned,
+                "poisson": {"iters_last_step": rec["d1"]["poisson_iters"],
+                            "resid_last_step": rec["d1"]["poisson_resid"],
+                            "ms_per_step": rec["per_kernel"]["poisson"]},
+                "roofline": roofline, "clocks": rec["clocks"], "e2e": e2e, "cpu_baseline": cpu,
+                "region_diagnostics": region, **subs}
         print(json.dumps(line), flush=True)
-    pg.pic_destroy(h)
     if world > 1:
         dist.destroy_process_group()
 

@@ -52,7 +52,9 @@ enum pic_status {
   PIC_OK = 0,
   PIC_ERR_INVALID = -1,      /* bad argument or configuration */
   PIC_ERR_OOM = -2,          /* device allocation failed */
-  PIC_ERR_CAPACITY = -3,     /* particle or birth capacity exceeded */
+  PIC_ERR_CAPACITY = -3,     /* particle or birth capacity exceeded, or (FP64 particles) a
+                                cell holding 2^18 or more macroparticles of one species, where
+                                a node's 44-bit fixed-point charge sum could wrap */
   PIC_ERR_NONCONVERGED = -4, /* Poisson solve reached poisson_max_iter */
   PIC_ERR_NAN = -5,          /* non-finite particle coordinate */
   PIC_ERR_TIMEOUT = -6,      /* a device-side wait reached its iteration limit */
@@ -115,6 +117,13 @@ typedef struct pic_config {
                                 from the linear extrapolation 2 phi^{n-1} - phi^{n-2} of the
                                 last two solutions instead of phi^{n-1} (fewer iterations;
                                 phi is still solved to poisson_tol); 0: from phi^{n-1} */
+  int32_t poisson_precond;   /* preconditioner of the flexible PCG Poisson solve:
+                                0: a sine transform along z with one tridiagonal solve in r
+                                per mode (FP32), exact for the operator when every boundary
+                                node is a conductor (gap_neumann = wall_neumann = 0), so two
+                                or three PCG iterations reach poisson_tol; with insulating
+                                boundary parts the multigrid V-cycle instead;
+                                1: always the FP32 geometric-multigrid V-cycle */
 } pic_config;
 
 /* Device-memory provider.  alloc returns a device pointer aligned to at least
@@ -195,6 +204,14 @@ int pic_set_phi(pic_handle* h, int instance, const double* phi, int on_device);
 int pic_get_fields(pic_handle* h, int instance, double* phi, double* rho, double* Q,
                    int on_device);
 
+/* Copy out the node charge (C) that one species deposited in the last step
+ * (or by pic_solve_fields): q_s w sum_p S_mn(x_p) over that species' particles
+ * (Section 2: tent functions; the same weights as the deposit into Q, whose
+ * sum over both species it is).  Node array as above, host or device memory
+ * per on_device.  Dividing by the node control volume gives the species'
+ * density, e.g. for time averages of the density profile.  Synchronous. */
+int pic_get_species_charge(pic_handle* h, int instance, int species, double* Q, int on_device);
+
 /* Set the circuit state: cathode voltage, step index and the last n_avg
  * cathode charges (C; ring buffer indexed by step % n_avg).  Synchronous. */
 int pic_set_circuit(pic_handle* h, int instance, double Vc, int64_t step, const double* qhist,
@@ -223,6 +240,13 @@ int pic_uses_graph(pic_handle* h);
  * the fastest is kept: *particles_per_thread receives it, or 0 while tuning
  * is unfinished. */
 int pic_tuned_chunk(pic_handle* h, int* particles_per_thread);
+
+/* Fix the push's chunk size (particles_per_thread 4, 8, 16 or 32) for the
+ * rest of the run, ending any tuning under way; 0 restarts the tuning, so the
+ * next four steps time the four sizes again (e.g. after the particle counts
+ * have grown).  Results do not depend on the chunk size (FP64 bit for bit).
+ * Drops the captured step graph.  PIC_ERR_INVALID for any other value. */
+int pic_set_chunk(pic_handle* h, int particles_per_thread);
 
 /* Wait for the handle's stream; return the latched status of all instances. */
 int pic_sync(pic_handle* h);
@@ -439,8 +463,9 @@ int pic_poisson_solve(int nr, int nz, double R, double L, double tol, int max_it
  * allocated: no cudaMalloc/cudaFree, no allocator of any framework.
  *   - Grids whose pic_poisson_workspace_bytes(nr, nz) exceeds
  *     PIC_POISSON_STATIC_BYTES - 256 are rejected with PIC_ERR_CAPACITY.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress, once per device, with that device current);
+ *   - Each call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress), so a device reset between calls is harmless;
+ *     the first call on a device also loads the library's device code there:
  *     make that first call before any stream capture.
  *   - All calls on a device share the one array, which keeps the previous
  *     call's contents (each call clears what must start at zero).  Calls that

@@ -663,6 +663,11 @@ void orc_get_fields(const orc_sim* s, double* phi, double* rho, double* Q) {
   if (Q) memcpy(Q, s->Q, nn * sizeof(double));
 }
 
+void orc_get_species_charge(const orc_sim* s, int species, double* Q) {
+  size_t nn = (size_t)(s->c.nr + 1) * (s->c.nz + 1);
+  memcpy(Q, s->Qs[species == 0 ? 0 : 1], nn * sizeof(double));
+}
+
 void orc_set_circuit(orc_sim* s, double Vc, int64_t step, const double* qhist, int n) {
   s->Vc = Vc;
   s->step = step;

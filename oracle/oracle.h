@@ -117,6 +117,8 @@ int orc_get_particles(const orc_sim* s, int species, double* r, double* z, doubl
 int orc_solve_fields(orc_sim* s);              /* phi from current particles and V_c */
 void orc_set_phi(orc_sim* s, const double* phi);
 void orc_get_fields(const orc_sim* s, double* phi, double* rho, double* Q);
+/* node charge (C) deposited by one species in the last step (Q = sum of both) */
+void orc_get_species_charge(const orc_sim* s, int species, double* Q);
 void orc_set_circuit(orc_sim* s, double Vc, int64_t step, const double* qhist, int n);
 int orc_step(orc_sim* s, int64_t nsteps);
 void orc_get_diag(const orc_sim* s, orc_diag* d);

@@ -101,6 +101,7 @@ def lib():
         L.orc_solve_fields.argtypes = [C.c_void_p]
         L.orc_set_phi.argtypes = [C.c_void_p, _D]
         L.orc_get_fields.argtypes = [C.c_void_p, _D, _D, _D]
+        L.orc_get_species_charge.argtypes = [C.c_void_p, C.c_int, _D]
         L.orc_set_circuit.argtypes = [C.c_void_p, C.c_double, C.c_int64, _D, C.c_int]
         L.orc_step.argtypes = [C.c_void_p, C.c_int64]
         L.orc_get_diag.argtypes = [C.c_void_p, C.POINTER(OracleDiag)]
@@ -262,6 +263,12 @@ class Oracle:
         phi, rho, Q = (np.empty(self.shape) for _ in range(3))
         lib().orc_get_fields(self._h, _dp(phi), _dp(rho), _dp(Q))
         return {"phi": phi, "rho": rho, "Q": Q}
+
+    def species_charge(self, species: int) -> np.ndarray:
+        """Node charge (C) that one species deposited in the last step."""
+        Q = np.empty(self.shape)
+        lib().orc_get_species_charge(self._h, species, _dp(Q))
+        return Q
 
     def set_circuit(self, Vc: float, step: int, qhist=None):
         q = _f64(qhist if qhist is not None else np.zeros(max(1, self.p["n_avg"])))

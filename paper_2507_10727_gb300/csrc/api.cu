@@ -141,6 +141,7 @@ std::string validate(const pic_config& c) {
     return "gap_neumann, wall_neumann must be 0 or 1";
   if (c.ied_bins < 0 || c.ied_bins > 65536) return "ied_bins must be in [0, 65536]";
   if (c.phi_extrapolate != 0 && c.phi_extrapolate != 1) return "phi_extrapolate must be 0 or 1";
+  if (c.poisson_precond != 0 && c.poisson_precond != 1) return "poisson_precond must be 0 or 1";
   if (c.ied_bins > 0 && !(c.ied_emax > 0.0)) return "ied_emax must be positive";
   if (!(c.band_r_lo <= c.band_r_hi)) return "band_r_lo must not exceed band_r_hi";
   return "";
@@ -285,6 +286,8 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
   I.phi = (double*)chk(A(nn * 8));
   I.phi_old = (double*)chk(A(nn * 8));
   I.Q = (double*)chk(A(nn * 8));
+  I.qs[0] = (double*)chk(A(nn * 8));
+  I.qs[1] = (double*)chk(A(nn * 8));
   if (p32) {
     I.etab32 = (float4*)chk(A((size_t)I.nkey * (c.gather == 0 ? 1 : 2) * sizeof(float4)));
     I.btab32 = (float4*)chk(A((size_t)I.nkey * 2 * sizeof(float4)));
@@ -326,12 +329,20 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
   if (e == cudaSuccess) e = cudaMemsetAsync(I.phi, 0, nn * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(I.phi_old, 0, nn * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(I.Q, 0, nn * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(I.qs[0], 0, nn * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(I.qs[1], 0, nn * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(I.qhist, 0, (size_t)c.n_avg * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(I.diag, 0, sizeof(DiagDev), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(pwbase, 0, pwb, st);
   if (e == cudaSuccess) e = region_clear(I, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "memset");
   ih.pw = poisson_work_init(pwbase, c.nr, c.nz, c.R, c.L, I.bc_g, I.bc_wall, h->num_sms);
+  if (c.poisson_precond == 0 && poisson_sep_possible(ih.pw)) {
+    void* sb = dev_alloc(h, poisson_sep_bytes(c.nr, c.nz));
+    if (!sb) return fail(h, PIC_ERR_OOM, "device allocation failed");
+    e = poisson_sep_attach(ih.pw, sb, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "Poisson tables");
+  }
 
   // static magnetic field: node values in FP64, folded per cell into
   // bilinear coefficients (B table keyed like the cells)
@@ -487,7 +498,9 @@ int pic_create(const pic_config* cfgs, int n_instances, const pic_alloc* alloc, 
     cudaError_t e = cudaMemcpyAsync(h->d_insts, hi.data(), sizeof(Inst) * n_instances,
                                     cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_queue, 0, sizeof(WorkQueue), h->stream);
-    if (e == cudaSuccess) e = poisson_group_upload(h->pws.data(), hi.data(), n_instances, h->d_pargs, h->stream);
+    if (e == cudaSuccess)
+      e = poisson_group_upload(h->pws.data(), hi.data(), n_instances, h->d_pargs, h->num_sms,
+                               h->stream);
     if (e != cudaSuccess) {
       pic_destroy(h);
       return PIC_ERR_CUDA;
@@ -774,6 +787,19 @@ int pic_get_fields(pic_handle* h, int instance, double* phi, double* rho, double
   return PIC_OK;
 }
 
+int pic_get_species_charge(pic_handle* h, int instance, int species, double* Q, int on_device) {
+  if (bad_instance(h, instance) || species < 0 || species > 1 || !Q)
+    return fail(h, PIC_ERR_INVALID, "bad argument");
+  InstHost& ih = h->inst[instance];
+  const size_t nn = (size_t)(ih.cfg.nr + 1) * (ih.cfg.nz + 1);
+  cudaError_t e = cudaMemcpyAsync(Q, ih.I.qs[species], nn * 8,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_species_charge");
+  return PIC_OK;
+}
+
 int pic_set_circuit(pic_handle* h, int instance, double Vc, int64_t step, const double* qhist,
                     int n) {
   if (bad_instance(h, instance) || step < 0 || n < 0 || (n > 0 && !qhist))
@@ -987,6 +1013,27 @@ int pic_step(pic_handle* h, int64_t nsteps) {
   for (int64_t s = 0; s < nsteps; ++s) {
     const cudaError_t e = launch_all(h, h->prof.on ? &marks : nullptr);
     if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
+  }
+  return PIC_OK;
+}
+
+int pic_set_chunk(pic_handle* h, int particles_per_thread) {
+  if (!h) return PIC_ERR_INVALID;
+  int k = -1;
+  for (int j = 0; j < 4; ++j)
+    if (kTuneCandidates[j] == particles_per_thread) k = j;
+  if (particles_per_thread != 0 && k < 0)
+    return fail(h, PIC_ERR_INVALID, "particles_per_thread must be 0, 4, 8, 16 or 32");
+  drop_graph(h);
+  if (h->tune_next > 0) {   // tuning was under way: its forced sorts end here
+    const cudaError_t e = force_sorts(h, 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_chunk");
+  }
+  if (k >= 0) {
+    h->ppt = particles_per_thread;
+    h->tune_next = -1;
+  } else {
+    h->tune_next = 0;       // tune again over the next four steps
   }
   return PIC_OK;
 }

@@ -211,6 +211,7 @@ struct Inst {
   BirthsDev births[2];
   double* phi;
   double* Q;
+  double* qs[2];           // node charge (C) of each species from the last deposit
   unsigned long long* qacc[2];
   // FP64 gather tables per species, scaled by that species' h = q dt / (2 m):
   // the push reads h E and h B directly

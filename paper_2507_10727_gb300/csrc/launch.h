@@ -85,7 +85,7 @@ cudaError_t launch_poisson_group(PoissonWork* const* pws, const Inst* insts, int
                                  void* d_args, int num_sms, cudaStream_t st);
 size_t poisson_args_bytes();
 cudaError_t poisson_group_upload(PoissonWork* const* pws, const Inst* insts, int n_inst,
-                                 void* d_args, cudaStream_t st);
+                                 void* d_args, int num_sms, cudaStream_t st);
 
 // pieces shared with the FP32 path
 cudaError_t launch_scan(const Inst& I, int sp0, int nsp, cudaStream_t st);
@@ -114,6 +114,12 @@ size_t poisson_work_bytes(int nr, int nz);
 PoissonWork* poisson_work_init(void* base, int nr, int nz, double R, double L, int g, int wall,
                                int num_sms);
 void poisson_work_free(PoissonWork* pw);
+// sine-transform preconditioner: possible when every boundary node is a
+// conductor; its extra workspace; attach it (tables filled, synchronous) --
+// later solves of pw use it instead of the multigrid V-cycle
+bool poisson_sep_possible(const PoissonWork* pw);
+size_t poisson_sep_bytes(int nr, int nz);
+cudaError_t poisson_sep_attach(PoissonWork* pw, void* base, cudaStream_t st);
 // solve A phi = Q (+ Dirichlet values held in phi's boundary nodes)
 cudaError_t launch_poisson(PoissonWork* pw, const double* Q, double* phi, double tol, int max_iter,
                            int* status_dev, int* iters_dev, double* resid_dev, cudaStream_t st);

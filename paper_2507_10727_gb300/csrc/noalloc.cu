@@ -14,7 +14,6 @@
 // streams, or host threads racing) corrupt each other's scratch, so callers
 // must serialise them.  Each call clears what must start at zero.
 #include <cstring>
-#include <mutex>
 
 #include "../../include/pic.h"
 #include "common.cuh"
@@ -29,23 +28,16 @@ constexpr size_t kStaticScratchBytes = PIC_POISSON_STATIC_BYTES;
 // cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-void* g_addr[kMaxDevices] = {};
-
-// Device address of g_scratch on the current device (set-up once per device,
-// with that device current).
+// Device address of g_scratch on the current device.  Looked up on every
+// call (the lookup is cheap next to the synchronous solve): a cached address
+// would go stale if the application reset the device or its primary context,
+// which reloads the module at another address.  The first lookup on a device
+// loads this library's device code there.
 int scratch_address(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PIC_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess || !p) return PIC_ERR_CUDA;
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess || !p) return PIC_ERR_CUDA;
+  *out = p;
   return PIC_OK;
 }
 

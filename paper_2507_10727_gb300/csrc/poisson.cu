@@ -31,6 +31,7 @@
 // fit in shared memory run inside one CTA ("tail"); the finer levels use the
 // whole grid with a time-bounded grid barrier.  Nodes are visited as (row,
 // 32-wide segment) items per warp, so no per-node integer division is needed.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -64,6 +65,19 @@ struct PoissonWork {
   double *r, *p, *q, *z;
   double* partial;
   unsigned int* bar;
+  // Sine-transform preconditioner (every boundary node a conductor): the
+  // operator is D (x) T + L (x) I on the free nodes (m = 0..nr-1, n = 1..nz-1;
+  // T the 1D second difference along z, D = a_z(m), L the radial part), so
+  // the discrete sine transform along z splits it into nz-1 tridiagonal
+  // systems in m.  Null when the multigrid preconditioner is used.
+  int nk;                  // modes: nz - 1
+  int rows_per_block;      // rows of one block in the row-wise phases
+  int sep_blocks;          // blocks of one solve
+  float* sS;               // nk x nk orthonormal DST-I matrix (symmetric)
+  float* sW;               // nr x nk: 1 / pivot of the Thomas elimination of mode k at row m
+  float* sC;               // nr x nk: its upper factor
+  float* sE;               // nr: coupling a_r(m) / (2 pi eps0) between rows m and m + 1
+  float* sHat;             // nr x nk: transformed residual, then the mode solutions
 };
 
 struct PoissonArgs {
@@ -849,6 +863,302 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
 }
 
 // ----------------------------------------------------------------------------
+// Flexible PCG with the sine-transform preconditioner (all boundary nodes
+// conductors).  z = M^{-1} r in three phases separated by grid barriers:
+//   A  rows:    f_hat[m][k] = sum_n S[k][n] f[m][n],  f = scale r (FP32)
+//   B  columns: (lambda_k D + L) u_hat[:, k] = f_hat[:, k], Thomas in m
+//   C  rows:    u[m][n] = sum_k S[n][k] u_hat[m][k];  z = u unscale (FP64)
+// lambda_k = 4 sin^2(pi (k+1) / (2 nz)).  The FP32 transform makes M^{-1} A
+// the identity to about 1e-6, so the outer FP64 iteration -- the same
+// recurrences and stopping test as the multigrid kernel -- ends after two or
+// three iterations, with five grid barriers each.  Block b of a solve owns
+// rows [b R, (b + 1) R) in phases A and C (staged in shared memory) and
+// modes k = b blockDim + t in phase B.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void sep_rows(const PoissonWork& W, int nrow, float* out, int m0,
+                                         const float* stage) {
+  // out[(m0 + j) * nk + k] = sum_n S[k][n] stage[j * nk + n], j < nrow; a
+  // thread takes two rows of one k (each S element read once for both)
+  const int nk = W.nk;
+  const int pairs = (nrow + 1) >> 1;
+  for (int t = threadIdx.x; t < pairs * nk; t += blockDim.x) {
+    const int jp = t / nk, k = t - jp * nk;
+    const int j0 = 2 * jp, j1 = j0 + 1 < nrow ? j0 + 1 : j0;
+    const float* a = stage + j0 * nk;
+    const float* b = stage + j1 * nk;
+    const float* Sk = W.sS + k;   // S[n][k] = S[k][n]
+    float s0 = 0.0f, s1 = 0.0f;
+    int n = 0;
+    for (; n + 3 < nk; n += 4) {
+      const float c0 = Sk[(size_t)n * nk], c1 = Sk[(size_t)(n + 1) * nk];
+      const float c2 = Sk[(size_t)(n + 2) * nk], c3 = Sk[(size_t)(n + 3) * nk];
+      s0 = fmaf(c0, a[n], s0);
+      s1 = fmaf(c0, b[n], s1);
+      s0 = fmaf(c1, a[n + 1], s0);
+      s1 = fmaf(c1, b[n + 1], s1);
+      s0 = fmaf(c2, a[n + 2], s0);
+      s1 = fmaf(c2, b[n + 2], s1);
+      s0 = fmaf(c3, a[n + 3], s0);
+      s1 = fmaf(c3, b[n + 3], s1);
+    }
+    for (; n < nk; ++n) {
+      const float c = Sk[(size_t)n * nk];
+      s0 = fmaf(c, a[n], s0);
+      s1 = fmaf(c, b[n], s1);
+    }
+    out[(size_t)(m0 + j0) * nk + k] = s0;
+    if (j1 != j0) out[(size_t)(m0 + j1) * nk + k] = s1;
+  }
+}
+
+// Thomas elimination of mode k: forward sweep into sHat, back substitution
+// in place.  The tables hold the eliminated pivots (sW) and upper factors (sC).
+__device__ __forceinline__ void sep_modes(const PoissonWork& W, int lb, int nb) {
+  const int nk = W.nk, nr = W.nr;
+  for (int k = lb * blockDim.x + threadIdx.x; k < nk; k += nb * blockDim.x) {
+    float* h = W.sHat + k;
+    const float* w = W.sW + k;
+    const float* c = W.sC + k;
+    float y = 0.0f;
+    for (int m = 0; m < nr; ++m) {
+      // y_m = (f_m + e_{m-1} y_{m-1}) / pivot_m  (off-diagonal -e)
+      const float e = m > 0 ? W.sE[m - 1] : 0.0f;
+      y = (h[(size_t)m * nk] + e * y) * w[(size_t)m * nk];
+      h[(size_t)m * nk] = y;
+    }
+    float x = 0.0f;
+    for (int m = nr - 1; m >= 0; --m) {
+      // x_m = y_m + c_m x_{m+1}
+      x = fmaf(c[(size_t)m * nk], x, h[(size_t)m * nk]);
+      h[(size_t)m * nk] = x;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kPoisThreads) k_poisson_sep(PoissonArgs A0,
+                                                              const PoissonArgs* group, int bpi) {
+  __shared__ PoissonArgs sA;
+  int lb, nb;
+  {
+    const PoissonArgs* src = &A0;
+    if (group) {
+      const int inst = blockIdx.x / bpi;
+      lb = blockIdx.x - inst * bpi;
+      nb = bpi;
+      src = group + inst;
+    } else {
+      lb = blockIdx.x;
+      nb = gridDim.x;
+    }
+    const unsigned* s4 = reinterpret_cast<const unsigned*>(src);
+    unsigned* d4 = reinterpret_cast<unsigned*>(&sA);
+    for (int k = threadIdx.x; k < (int)(sizeof(PoissonArgs) / 4); k += blockDim.x) d4[k] = s4[k];
+    __syncthreads();
+  }
+  const PoissonArgs& A = sA;
+  const PoissonWork& W = A.W;
+  if (*(volatile int*)A.status & (ST_FATAL)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nr = W.nr, nz = W.nz, nz1 = nz + 1, nk = W.nk;
+  const int lane = threadIdx.x & 31;
+  const int gw = (lb * blockDim.x + threadIdx.x) >> 5;
+  const int ngw = (nb * blockDim.x) >> 5;
+  const int nsf = (nz - 1 + 31) >> 5;
+  const int items0 = nr * nsf;
+  const long long nfree = (long long)nr * (nz - 1);
+  double* phi = A.phi;
+  auto node_of = [&](int it, int& m, int& n) -> bool {
+    m = it / nsf;
+    n = 1 + (it - m * nsf) * 32 + lane;
+    return n <= nz - 1;
+  };
+  double* az0 = (double*)smem;
+  double* ar0 = az0 + (nr + 1);
+  float* stage = (float*)(ar0 + (nr + 1));
+  for (int m = threadIdx.x; m <= nr; m += blockDim.x) fine_coef(W, m, az0[m], ar0[m]);
+  __syncthreads();
+  const Tables T{az0, ar0, nullptr, nullptr, nullptr};
+  const int R = W.rows_per_block;
+  const int m0 = lb * R;
+  const int nrow = m0 >= nr ? 0 : (m0 + R <= nr ? R : nr - m0);
+
+  int parity = 0;
+  double vals[3];
+  double bb = 0.0, rr = 0.0;
+  for (int it = gw; it < items0; it += ngw) {
+    int m, n;
+    if (!node_of(it, m, n)) continue;
+    const int i = m * nz1 + n;
+    double b = A.Q[i];
+    if (n == 1) b += az0[m] * phi[i - 1];
+    if (n == nz - 1) b += az0[m] * phi[i + 1];
+    if (m == nr - 1) b += ar0[m] * phi[i + nz1];
+    const double r = A.Q[i] - apply64(T, phi, m, i, nz1);
+    W.r[i] = r;
+    bb += b * b;
+    rr += r * r;
+  }
+  vals[0] = bb;
+  vals[1] = rr;
+  block_partials(W.partial, parity, 2, vals, lb, nb);
+  if (!barrier_grid(W.bar, A.status, nb)) return;
+  read_partials(W.partial, parity, 2, vals, nb);
+  parity ^= 1;
+  bb = vals[0];
+  rr = vals[1];
+  const double tol2bb = A.tol * A.tol * bb;
+  const double ref = bb > 0.0 ? bb : rr;
+  const double scale = ref > 0.0 ? 1.0 / sqrt(ref / (double)nfree) : 1.0;
+  const double unscale = 1.0 / (2.0 * kPi * kEps0 * scale);
+
+  int it = 0;
+  bool converged = rr <= tol2bb;
+  double rz = 0.0, alpha = 0.0;
+  bool first = true;
+  int restarts = 0;
+  while (!converged && it < A.max_iter) {
+    // ---- A: rows of f = scale r, transformed along z -----------------------
+    for (int t = threadIdx.x; t < nrow * nk; t += blockDim.x) {
+      const int j = t / nk, n = t - j * nk;
+      stage[t] = (float)(W.r[(m0 + j) * nz1 + 1 + n] * scale);
+    }
+    __syncthreads();
+    if (nrow > 0) sep_rows(W, nrow, W.sHat, m0, stage);
+    if (!barrier_grid(W.bar, A.status, nb)) return;
+    // ---- B: the tridiagonal system of every mode ---------------------------
+    sep_modes(W, lb, nb);
+    if (!barrier_grid(W.bar, A.status, nb)) return;
+    // ---- C: back to nodes; z, r.z and z.q_old ------------------------------
+    for (int t = threadIdx.x; t < nrow * nk; t += blockDim.x) stage[t] = W.sHat[(size_t)m0 * nk + t];
+    __syncthreads();
+    double rz_loc = 0.0, zq_loc = 0.0;
+    {
+      const int pairs = (nrow + 1) >> 1;
+      for (int t = threadIdx.x; t < pairs * nk; t += blockDim.x) {
+        const int jp = t / nk, n = t - jp * nk;
+        const int j0 = 2 * jp, j1 = j0 + 1 < nrow ? j0 + 1 : j0;
+        const float* a = stage + j0 * nk;
+        const float* b = stage + j1 * nk;
+        const float* Sn = W.sS + n;
+        float s0 = 0.0f, s1 = 0.0f;
+        int k = 0;
+        for (; k + 3 < nk; k += 4) {
+          const float c0 = Sn[(size_t)k * nk], c1 = Sn[(size_t)(k + 1) * nk];
+          const float c2 = Sn[(size_t)(k + 2) * nk], c3 = Sn[(size_t)(k + 3) * nk];
+          s0 = fmaf(c0, a[k], s0);
+          s1 = fmaf(c0, b[k], s1);
+          s0 = fmaf(c1, a[k + 1], s0);
+          s1 = fmaf(c1, b[k + 1], s1);
+          s0 = fmaf(c2, a[k + 2], s0);
+          s1 = fmaf(c2, b[k + 2], s1);
+          s0 = fmaf(c3, a[k + 3], s0);
+          s1 = fmaf(c3, b[k + 3], s1);
+        }
+        for (; k < nk; ++k) {
+          const float c = Sn[(size_t)k * nk];
+          s0 = fmaf(c, a[k], s0);
+          s1 = fmaf(c, b[k], s1);
+        }
+        {
+          const int i = (m0 + j0) * nz1 + 1 + n;
+          const double zi = (double)s0 * unscale;
+          W.z[i] = zi;
+          rz_loc += W.r[i] * zi;
+          if (!first) zq_loc += zi * W.q[i];
+        }
+        if (j1 != j0) {
+          const int i = (m0 + j1) * nz1 + 1 + n;
+          const double zi = (double)s1 * unscale;
+          W.z[i] = zi;
+          rz_loc += W.r[i] * zi;
+          if (!first) zq_loc += zi * W.q[i];
+        }
+      }
+    }
+    vals[0] = rz_loc;
+    vals[1] = zq_loc;
+    block_partials(W.partial, parity, 2, vals, lb, nb);
+    if (!barrier_grid(W.bar, A.status, nb)) return;
+    read_partials(W.partial, parity, 2, vals, nb);
+    parity ^= 1;
+    // ---- p = z + beta p, q = A z + beta q (flexible Polak-Ribiere beta) ---
+    const double beta = first ? 0.0 : -alpha * vals[1] / rz;
+    rz = vals[0];
+    first = false;
+    double pq = 0.0;
+    for (int itm = gw; itm < items0; itm += ngw) {
+      int m, n;
+      if (!node_of(itm, m, n)) continue;
+      const int i = m * nz1 + n;
+      const double zi = W.z[i];
+      const double zl = n > 1 ? W.z[i - 1] : 0.0;
+      const double zu = n < nz - 1 ? W.z[i + 1] : 0.0;
+      const double zo = m < nr - 1 ? W.z[i + nz1] : 0.0;
+      double a = az0[m] * (2.0 * zi - zl - zu) + ar0[m] * (zi - zo);
+      if (m > 0) a += ar0[m - 1] * (zi - W.z[i - nz1]);
+      const double pi = zi + beta * W.p[i];
+      const double qi = a + beta * W.q[i];
+      W.p[i] = pi;
+      W.q[i] = qi;
+      pq += pi * qi;
+    }
+    vals[0] = pq;
+    block_partials(W.partial, parity, 1, vals, lb, nb);
+    if (!barrier_grid(W.bar, A.status, nb)) return;
+    read_partials(W.partial, parity, 1, vals, nb);
+    parity ^= 1;
+    alpha = vals[0] != 0.0 ? rz / vals[0] : 0.0;
+    // ---- phi += alpha p, r -= alpha q --------------------------------------
+    double rl = 0.0;
+    for (int itm = gw; itm < items0; itm += ngw) {
+      int m, n;
+      if (!node_of(itm, m, n)) continue;
+      const int i = m * nz1 + n;
+      phi[i] += alpha * W.p[i];
+      const double r = W.r[i] - alpha * W.q[i];
+      W.r[i] = r;
+      rl += r * r;
+    }
+    vals[0] = rl;
+    block_partials(W.partial, parity, 1, vals, lb, nb);
+    if (!barrier_grid(W.bar, A.status, nb)) return;
+    read_partials(W.partial, parity, 1, vals, nb);
+    parity ^= 1;
+    rr = vals[0];
+    ++it;
+    if (rr <= tol2bb) {
+      // confirm with the true residual b - A phi (also the restart's input)
+      double rt = 0.0;
+      for (int itm = gw; itm < items0; itm += ngw) {
+        int m, n;
+        if (!node_of(itm, m, n)) continue;
+        const int i = m * nz1 + n;
+        const double r = A.Q[i] - apply64(T, phi, m, i, nz1);
+        W.r[i] = r;
+        rt += r * r;
+      }
+      vals[0] = rt;
+      block_partials(W.partial, parity, 1, vals, lb, nb);
+      if (!barrier_grid(W.bar, A.status, nb)) return;
+      read_partials(W.partial, parity, 1, vals, nb);
+      parity ^= 1;
+      rr = vals[0];
+      if (rr <= tol2bb || restarts >= 3) {
+        converged = rr <= tol2bb;
+        break;
+      }
+      ++restarts;
+      first = true;  // restart the Krylov space from the true residual
+    }
+  }
+  if (lb == 0 && threadIdx.x == 0) {
+    *A.iters = it;
+    *A.resid = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
+    if (!converged) atomicOr(A.status, ST_NONCONV);
+  }
+}
+
+// ----------------------------------------------------------------------------
 // Pieces of the learned warm start, on the fine FP64 operator of the solve.
 // Start selection among three starting points -- x = phi as it stands (the
 // previous solution with this step's Dirichlet values), x = the candidate from
@@ -1078,10 +1388,107 @@ PoissonWork* poisson_work_init(void* base, int nr, int nz, double R, double L, i
   return pw;
 }
 
+// ---- sine-transform preconditioner ------------------------------------------
+constexpr int kSepMaxBlocks = 64;
+
+bool poisson_sep_possible(const PoissonWork* pw) { return !has_lines(*pw); }
+
+size_t poisson_sep_bytes(int nr, int nz) {
+  const size_t nk = (size_t)(nz - 1);
+  return round256(nk * nk * 4) + 3 * round256((size_t)nr * nk * 4) + round256((size_t)nr * 4);
+}
+
+static void sep_rows_per_block(PoissonWork& w, int blocks) {
+  if (blocks < 1) blocks = 1;
+  w.rows_per_block = (w.nr + blocks - 1) / blocks;
+}
+
+static int sep_smem(const PoissonWork& w) {
+  return (int)(2 * (size_t)(w.nr + 1) * sizeof(double) +
+               (size_t)w.rows_per_block * (size_t)w.nk * sizeof(float));
+}
+
+cudaError_t poisson_sep_attach(PoissonWork* pw, void* base, cudaStream_t st) {
+  PoissonWork& w = *pw;
+  const int nr = w.nr, nk = w.nz - 1;
+  w.nk = nk;
+  char* p = (char*)base;
+  auto take = [&](size_t b) {
+    char* q = p;
+    p += round256(b);
+    return (float*)q;
+  };
+  w.sS = take((size_t)nk * nk * 4);
+  w.sW = take((size_t)nr * nk * 4);
+  w.sC = take((size_t)nr * nk * 4);
+  w.sHat = take((size_t)nr * nk * 4);
+  w.sE = take((size_t)nr * 4);
+  // tables in FP64 on the host, stored in FP32; couplings scaled by
+  // 1 / (2 pi eps0) like the multigrid tables
+  std::vector<float> S((size_t)nk * nk), Wt((size_t)nr * nk), Ct((size_t)nr * nk), E(nr);
+  const double norm = std::sqrt(2.0 / w.nz);
+  for (int k = 0; k < nk; ++k)
+    for (int n = 0; n < nk; ++n) {
+      const long long a = ((long long)(k + 1) * (n + 1)) % (2LL * w.nz);
+      S[(size_t)k * nk + n] = (float)(norm * std::sin(kPi * (double)a / w.nz));
+    }
+  std::vector<double> az(nr), ar(nr);
+  for (int m = 0; m < nr; ++m) {
+    az[m] = m == 0 ? w.dr * w.dr / (8.0 * w.dz) : m * w.dr * w.dr / w.dz;
+    ar[m] = w.dz * (m + 0.5);
+    E[m] = (float)ar[m];
+  }
+  for (int k = 0; k < nk; ++k) {
+    const double sk = std::sin(kPi * (k + 1) / (2.0 * w.nz));
+    const double lam = 4.0 * sk * sk;
+    double cprev = 0.0;   // c'_{m-1} = -ar(m-1) / pivot_{m-1}
+    for (int m = 0; m < nr; ++m) {
+      const double d = lam * az[m] + ar[m] + (m > 0 ? ar[m - 1] : 0.0);
+      const double piv = d - (m > 0 ? -ar[m - 1] * cprev : 0.0);
+      const double cm = m < nr - 1 ? -ar[m] / piv : 0.0;
+      Wt[(size_t)m * nk + k] = (float)(1.0 / piv);
+      Ct[(size_t)m * nk + k] = (float)(-cm);
+      cprev = cm;
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(w.sS, S.data(), S.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w.sW, Wt.data(), Wt.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w.sC, Ct.data(), Ct.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w.sE, E.data(), E.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // host tables go out of scope
+  if (e != cudaSuccess) return e;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_poisson_sep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kSmemBudget);
+    attr = true;
+  }
+  int blocks = nr / 2 < kSepMaxBlocks ? nr / 2 : kSepMaxBlocks;
+  sep_rows_per_block(w, blocks);
+  w.sep_blocks = (nr + w.rows_per_block - 1) / w.rows_per_block;
+  return cudaSuccess;
+}
+
 void poisson_work_free(PoissonWork* pw) { delete pw; }
 
 cudaError_t launch_poisson(PoissonWork* pw, const double* Q, double* phi, double tol, int max_iter,
                            int* status_dev, int* iters_dev, double* resid_dev, cudaStream_t st) {
+  if (pw->sS) {
+    PoissonArgs a;
+    a.W = *pw;
+    a.Q = Q;
+    a.phi = phi;
+    a.tol = tol;
+    a.max_iter = max_iter;
+    a.status = status_dev;
+    a.iters = iters_dev;
+    a.resid = resid_dev;
+    const PoissonArgs* none = nullptr;
+    int one = 1;
+    void* args[] = {&a, &none, &one};
+    return cudaLaunchCooperativeKernel((const void*)k_poisson_sep, dim3(pw->sep_blocks),
+                                       dim3(kPoisThreads), args, (size_t)sep_smem(*pw), st);
+  }
   PoissonArgs a;
   a.W = *pw;
   a.Q = Q;
@@ -1102,13 +1509,39 @@ size_t poisson_args_bytes() { return sizeof(PoissonArgs); }
 
 // Argument records of the grouped launch, written once (the pointers they hold
 // do not change over a handle's life) to d_args: n_inst * poisson_args_bytes().
+static bool group_sep(PoissonWork* const* pws, int n_inst) {
+  for (int k = 0; k < n_inst; ++k)
+    if (!pws[k]->sS) return false;
+  return true;
+}
+
+// blocks per instance of the grouped sine-transform solve
+static int group_sep_bpi(PoissonWork* const* pws, int n_inst, int num_sms) {
+  int smem = 0, want = 1;
+  for (int k = 0; k < n_inst; ++k) {
+    PoissonWork w = *pws[k];
+    want = w.sep_blocks > want ? w.sep_blocks : want;
+    sep_rows_per_block(w, 1);
+    smem = sep_smem(w) > smem ? sep_smem(w) : smem;
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_poisson_sep, kPoisThreads,
+                                                smem);
+  if (per_sm < 1) per_sm = 1;
+  int bpi = (num_sms * per_sm) / n_inst;
+  return bpi > want ? want : bpi;
+}
+
 cudaError_t poisson_group_upload(PoissonWork* const* pws, const Inst* insts, int n_inst,
-                                 void* d_args, cudaStream_t st) {
+                                 void* d_args, int num_sms, cudaStream_t st) {
   std::vector<PoissonArgs> host((size_t)n_inst);
+  const bool sep = group_sep(pws, n_inst);
+  const int bpi = sep ? group_sep_bpi(pws, n_inst, num_sms) : 0;
   for (int k = 0; k < n_inst; ++k) {
     PoissonArgs& a = host[k];
     std::memset(&a, 0, sizeof(a));
     a.W = *pws[k];
+    if (sep) sep_rows_per_block(a.W, bpi);
     a.Q = insts[k].Q;
     a.phi = insts[k].phi;
     a.tol = insts[k].poisson_tol;
@@ -1127,6 +1560,22 @@ cudaError_t poisson_group_upload(PoissonWork* const* pws, const Inst* insts, int
 cudaError_t launch_poisson_group(PoissonWork* const* pws, const Inst* insts, int n_inst,
                                  void* d_args, int num_sms, cudaStream_t st) {
   (void)insts;
+  if (group_sep(pws, n_inst)) {
+    int bpi = group_sep_bpi(pws, n_inst, num_sms);
+    if (bpi < 1) return cudaErrorInvalidConfiguration;
+    int smem = 0;
+    for (int k = 0; k < n_inst; ++k) {
+      PoissonWork w = *pws[k];
+      sep_rows_per_block(w, bpi);
+      smem = sep_smem(w) > smem ? sep_smem(w) : smem;
+    }
+    PoissonArgs a0;
+    std::memset(&a0, 0, sizeof(a0));
+    const PoissonArgs* g = (const PoissonArgs*)d_args;
+    void* args[] = {&a0, &g, &bpi};
+    return cudaLaunchCooperativeKernel((const void*)k_poisson_sep, dim3(n_inst * bpi),
+                                       dim3(kPoisThreads), args, (size_t)smem, st);
+  }
   int smem = 0, want = 1;
   bool lines = false;
   for (int k = 0; k < n_inst; ++k) {

@@ -255,11 +255,40 @@ __device__ __noinline__ void collide_at(const Inst& I, const ParticlesDev& P, lo
 
 // ---------------------------------------------------------------------------
 // The push.  One CTA processes chunks of ppt x kPushThreads consecutive
-// (cell-sorted) particles; the chunk's charge goes into a shared patch of kPR x kPZ nodes
-// anchored at the tile of the chunk's first particle, flushed with one
-// atomic per touched node.  Particles whose new 4 nodes fall outside the
-// patch (fast movers, chunk tails in sparse regions) add to global memory.
+// (cell-sorted) particles, warp w the contiguous run of 32 ppt of them from
+// c0 + 32 ppt w, 32 consecutive particles per iteration.  A lane therefore
+// meets the same new cell over many iterations: it sums its fixed-point
+// deposit weights and its cell count in registers (integers: exact, order
+// free) and adds them, when its cell changes, to the CTA's shared patches of
+// kPR x kPZ nodes (charge) and kPR-1 x kPZ-1 cells (counts) anchored at the
+// tile of the chunk's first particle, flushed with one atomic per touched
+// node or cell.  Cells whose nodes fall outside the patch (fast movers, chunk
+// tails in sparse regions) add to global memory.
 // ---------------------------------------------------------------------------
+template <int SP>
+__device__ __forceinline__ void deposit_run64(const Inst& I, int key, int m, int n,
+                                              unsigned long long a00, unsigned long long a10,
+                                              unsigned long long a01, unsigned long long a11,
+                                              int cnt, int pm0, int pn0, unsigned long long* patch,
+                                              int* cpatch) {
+  const int lm = m - pm0, ln = n - pn0;
+  if (lm >= 0 && lm + 1 < kPR && ln >= 0 && ln + 1 < kPZ) {
+    unsigned long long* p = patch + lm * kPZ + ln;
+    atomicAdd(p, a00);
+    atomicAdd(p + kPZ, a10);
+    atomicAdd(p + 1, a01);
+    atomicAdd(p + kPZ + 1, a11);
+    atomicAdd(cpatch + lm * (kPZ - 1) + ln, cnt);
+  } else {
+    unsigned long long* q = I.qacc[SP];
+    atomicAdd(q + node_index(I, m, n), a00);
+    atomicAdd(q + node_index(I, m + 1, n), a10);
+    atomicAdd(q + node_index(I, m, n + 1), a01);
+    atomicAdd(q + node_index(I, m + 1, n + 1), a11);
+    atomicAdd(&I.counts[SP][key], cnt);
+  }
+}
+
 // Push the chunk of `ppt * blockDim.x` particles of species SP starting at c0
 // (the whole CTA takes part).  `patch` is the CTA's zeroed shared deposit
 // patch; it is flushed and zeroed again before return.  `anchor` holds the
@@ -270,7 +299,7 @@ __device__ __noinline__ void collide_at(const Inst& I, const ParticlesDev& P, lo
 // Returns this thread's share of the kinetic energy (diagnostic steps only).
 template <int SP, int GATHER>
 __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned long long* patch,
-                               int* anchor, int* cq) {
+                               int* cpatch, int* anchor, int* cq) {
   Scalars* S = I.S;
   const long long n = S->n[SP];
   const long long step = S->step;
@@ -292,13 +321,15 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
     }
     __syncthreads();
     const int pm0 = anchor[0], pn0 = anchor[1];
+    const long long run0 = c0 + (long long)(threadIdx.x >> 5) * 32 * ppt + lane;
+    // this lane's open deposit: cell, its fixed-point node sums and count
+    int acc_key = -1, acc_m = 0, acc_n = 0, acc_cnt = 0;
+    unsigned long long s00 = 0ULL, s10 = 0ULL, s01 = 0ULL, s11 = 0ULL;
     unsigned over = 0u;   // candidates that found the queue full, bit j (ppt <= 32)
 #pragma unroll 1
     for (int j = 0; j < ppt; ++j) {
-      const long long i = c0 + (long long)j * blockDim.x + threadIdx.x;
+      const long long i = run0 + (long long)j * 32;
       int newkey = -1;
-      unsigned long long w00 = 0ULL, w10 = 0ULL, w01 = 0ULL, w11 = 0ULL;
-      int dm = 0, dn = 0;
       // between full sorts the arrays hold dead slots, marked by r = -1
       const bool live = i < n && (long long)bits_of(P.r[i]) >= 0;
       if (!live) {
@@ -418,42 +449,32 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
           split_cell(z1, I.nz, n1, fz1);
           newkey = cell_key(I, m1, n1);
           P.r[i] = r1; P.z[i] = z1; P.vr[i] = vr; P.vt[i] = vt; P.vz[i] = vz;
-          // deposit weights of x^{n+1} (Section 2: tent functions)
+          // deposit weights of x^{n+1} (Section 2: tent functions), summed per cell
+          if (newkey != acc_key) {
+            if (acc_key >= 0)
+              deposit_run64<SP>(I, acc_key, acc_m, acc_n, s00, s10, s01, s11, acc_cnt, pm0, pn0,
+                                patch, cpatch);
+            acc_key = newkey;
+            acc_m = m1;
+            acc_n = n1;
+            acc_cnt = 0;
+            s00 = s10 = s01 = s11 = 0ULL;
+          }
           const FixW f = fix_weights(rweight_upper(I, r1, m1, fr1), fz1);
-          w00 = f.w00;
-          w10 = f.w10;
-          w01 = f.w01;
-          w11 = f.w11;
-          dm = m1;
-          dn = n1;
+          s00 += f.w00;
+          s10 += f.w10;
+          s01 += f.w01;
+          s11 += f.w11;
+          ++acc_cnt;
         } else {
           P.r[i] = -1.0;   // dead slot until the next full sort
         }
         I.key[SP][i] = newkey;
       }
-      // deposit: integer sums of neighbouring lanes in the same cell (exact,
-      // order free), then one shared-memory (or global) atomic per node and run
-      if (run_sum4(newkey, w00, w10, w01, w11) && newkey >= 0) {
-        const int lm = dm - pm0, ln = dn - pn0;
-        if (lm >= 0 && lm + 1 < kPR && ln >= 0 && ln + 1 < kPZ) {
-          unsigned long long* p = patch + lm * kPZ + ln;
-          atomicAdd(p, w00);
-          atomicAdd(p + kPZ, w10);
-          atomicAdd(p + 1, w01);
-          atomicAdd(p + kPZ + 1, w11);
-        } else {
-          unsigned long long* q = I.qacc[SP];
-          atomicAdd(q + node_index(I, dm, dn), w00);
-          atomicAdd(q + node_index(I, dm + 1, dn), w10);
-          atomicAdd(q + node_index(I, dm, dn + 1), w01);
-          atomicAdd(q + node_index(I, dm + 1, dn + 1), w11);
-        }
-      }
-      // histogram of new cells, aggregated over the lanes of a warp that
-      // share a cell (sorted input keeps most of a warp in one cell)
-      const unsigned peers = __match_any_sync(0xffffffffu, newkey);
-      if (newkey >= 0 && lane == __ffs(peers) - 1) atomicAdd(&I.counts[SP][newkey], __popc(peers));
     }
+    if (acc_key >= 0)
+      deposit_run64<SP>(I, acc_key, acc_m, acc_n, s00, s10, s01, s11, acc_cnt, pm0, pn0, patch,
+                        cpatch);
     __syncthreads();
     if (SP == 0) {
       // the queued collisions (Section 3), on the state written above
@@ -462,16 +483,24 @@ __device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned lo
       while (over) {
         const int j = __ffs(over) - 1;
         over &= over - 1;
-        collide_at(I, P, c0 + (long long)j * blockDim.x + threadIdx.x, step);
+        collide_at(I, P, run0 + (long long)j * 32, step);
       }
     }
-    // flush the patch
+    // flush the patches
     for (int k = threadIdx.x; k < kPR * kPZ; k += blockDim.x) {
       const unsigned long long v = patch[k];
       if (v != 0ULL) {
         const int gm = pm0 + k / kPZ, gn = pn0 + k % kPZ;
         atomicAdd(I.qacc[SP] + node_index(I, gm, gn), v);
         patch[k] = 0ULL;
+      }
+    }
+    for (int k = threadIdx.x; k < (kPR - 1) * (kPZ - 1); k += blockDim.x) {
+      const int c = cpatch[k];
+      if (c != 0) {
+        const int gm = pm0 + k / (kPZ - 1), gn = pn0 + k % (kPZ - 1);
+        atomicAdd(&I.counts[SP][cell_key(I, gm, gn)], c);
+        cpatch[k] = 0;
       }
     }
     __syncthreads();
@@ -486,12 +515,14 @@ template <int GATHER>
 __global__ void __launch_bounds__(kPushThreads, 2) k_push_all(const Inst* insts, WorkQueue* q,
                                                                int ppt) {
   __shared__ unsigned long long patch[kPR * kPZ];
+  __shared__ int cpatch[(kPR - 1) * (kPZ - 1)];
   __shared__ int anchor[3];
   __shared__ int cq[kCollQ];
   __shared__ Inst sI;
   __shared__ int s_inst, s_sp, s_skip;
   __shared__ long long s_c0;
   for (int k = threadIdx.x; k < kPR * kPZ; k += blockDim.x) patch[k] = 0ULL;
+  for (int k = threadIdx.x; k < (kPR - 1) * (kPZ - 1); k += blockDim.x) cpatch[k] = 0;
   int cur = -1;
   double K0 = 0.0, K1 = 0.0;
   const long long chunk = (long long)ppt * blockDim.x;
@@ -524,8 +555,8 @@ __global__ void __launch_bounds__(kPushThreads, 2) k_push_all(const Inst* insts,
       cur = inst;
     }
     if (!s_skip) {
-      if (s_sp == 0) K0 += push_chunk64<0, GATHER>(sI, s_c0, ppt, patch, anchor, cq);
-      else K1 += push_chunk64<1, GATHER>(sI, s_c0, ppt, patch, anchor, cq);
+      if (s_sp == 0) K0 += push_chunk64<0, GATHER>(sI, s_c0, ppt, patch, cpatch, anchor, cq);
+      else K1 += push_chunk64<1, GATHER>(sI, s_c0, ppt, patch, cpatch, anchor, cq);
     }
     __syncthreads();
   }
@@ -694,6 +725,9 @@ __global__ void __launch_bounds__(1024) k_scan(Inst I, int sp0) {
     S->ppc_max[sp] = vmax;
     S->n_next[sp] = carry;
     if (carry > I.cap[sp]) atomicOr(&S->status, ST_CAPACITY);
+    // FP64 deposit: a node's u64 sum of 2^44-scaled weights holds fewer than
+    // 2^20 macroparticles, and a node gathers from at most 4 cells
+    if (!I.prec32 && 4LL * vmax >= (1LL << (64 - kFixBits))) atomicOr(&S->status, ST_CAPACITY);
   }
 }
 
@@ -1078,6 +1112,8 @@ __global__ void k_charge(Inst I, bool step) {
       se = (double)ue * kFixInv;
       si = (double)ui * kFixInv;
     }
+    I.qs[0][k] = -se * (kQe * I.weight);
+    I.qs[1][k] = si * (kQe * I.weight);
     if (extrap) {
       const int m = k / (I.nz + 1), n = k - m * (I.nz + 1);
       const double p1 = I.phi[k];

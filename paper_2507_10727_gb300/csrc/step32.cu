@@ -222,13 +222,41 @@ __device__ __noinline__ void cathode_hit32(const Inst& I, float Xo, float X, flo
 // The FP32 push: gather + Boris + move + walls + SEY + MCC + deposit, state
 // rewritten in place with the new cell key (read by the scatter).
 // ---------------------------------------------------------------------------
-// Push the chunk of `ppt * blockDim.x` particles starting at c0 (whole CTA);
-// `patch` is the CTA's zeroed deposit patch, flushed and zeroed on return;
+// Push the chunk of `ppt * blockDim.x` particles starting at c0 (whole CTA).
+// Warp w takes the contiguous run [c0 + 32 ppt w, c0 + 32 ppt (w + 1)), 32
+// consecutive particles per iteration, so that a lane meets the same new cell
+// over many iterations in a cell-sorted array: it sums its deposit weights
+// and its cell count in registers and adds them to the CTA's shared patches
+// (node charge `patch`, cell counts `cpatch`; global memory outside them)
+// only when its cell changes.  The patches are flushed and zeroed on return.
 // `anchor` holds the patch origin and the candidate count, `cq` the chunk's
 // collision candidates, run after the chunk as in push_chunk64 (step.cu).
+template <int SP>
+__device__ __forceinline__ void deposit_run32(const Inst& I, int key, int m, int n, float a00,
+                                              float a10, float a01, float a11, int cnt, int pm0,
+                                              int pn0, float* patch, int* cpatch) {
+  const int lm = m - pm0, ln = n - pn0;
+  if (lm >= 0 && lm + 1 < kPR32 && ln >= 0 && ln + 1 < kPZ32) {
+    float* p = patch + lm * kPZ32 + ln;
+    atomicAdd(p, a00);
+    atomicAdd(p + kPZ32, a10);
+    atomicAdd(p + 1, a01);
+    atomicAdd(p + kPZ32 + 1, a11);
+    atomicAdd(cpatch + lm * (kPZ32 - 1) + ln, cnt);
+  } else {
+    double* q = I.qacc64[SP];
+    const int gi = node_index(I, m, n), nz1 = I.nz + 1;
+    atomicAdd(q + gi, (double)a00);
+    atomicAdd(q + gi + nz1, (double)a10);
+    atomicAdd(q + gi + 1, (double)a01);
+    atomicAdd(q + gi + nz1 + 1, (double)a11);
+    atomicAdd(&I.counts[SP][key], cnt);
+  }
+}
+
 template <int SP, int GATHER>
-__device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patch, int* anchor,
-                               int* cq) {
+__device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patch, int* cpatch,
+                               int* anchor, int* cq) {
   Scalars* S = I.S;
   const long long n = S->n[SP];
   const long long step = S->step;
@@ -236,6 +264,7 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
   const Particles32 P = I.buf32[SP][S->flip[SP]];
   const float h = I.hq32[SP], kr = I.kr32, kz = I.kz32;
   const int lane = threadIdx.x & 31;
+  const long long run0 = c0 + (long long)(threadIdx.x >> 5) * 32 * ppt;
   double Kloc = 0.0;
   {
     if (threadIdx.x == 0) {
@@ -248,22 +277,23 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
     __syncthreads();
     const int pm0 = anchor[0], pn0 = anchor[1];
     // the next particle's two records are loaded while this one is pushed
-    long long i = c0 + threadIdx.x;
+    long long i = run0 + lane;
     float4 a_nx = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     uint4 b_nx = make_uint4(0u, 0u, 0u, 0u);
     if (i < n) {
       a_nx = P.a[i];
       b_nx = P.b[i];
     }
+    // this lane's open deposit: cell, its node sums and particle count
+    int acc_key = -1, acc_m = 0, acc_n = 0, acc_cnt = 0;
+    float s00 = 0.0f, s10 = 0.0f, s01 = 0.0f, s11 = 0.0f;
     unsigned over = 0u;   // candidates that found the queue full, bit j (ppt <= 32)
 #pragma unroll 1
-    for (int j = 0; j < ppt; ++j, i += blockDim.x) {
-      int newkey = -1, dm = 0, dn = 0;
-      float w00 = 0.0f, w10 = 0.0f, w01 = 0.0f, w11 = 0.0f;
+    for (int j = 0; j < ppt; ++j, i += 32) {
       const float4 a = a_nx;
       const uint4 b = b_nx;
       {
-        const long long i2 = i + blockDim.x;
+        const long long i2 = i + 32;
         if (j + 1 < ppt && i2 < n) {
           a_nx = P.a[i2];
           b_nx = P.b[i2];
@@ -365,61 +395,34 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
             if (slot < kCollQ32) cq[slot] = (int)(i - c0);
             else over |= 1u << j;   // queue full: this thread runs it after the queue
           }
-          newkey = cell_key(I, m1, n1);
+          const int newkey = cell_key(I, m1, n1);
           P.a[i] = make_float4(dr1, dz1, vr, vt);
           P.b[i] = make_uint4(__float_as_uint(vz), pack_mn(m1, n1), b.z, b.w);
+          // deposit of x^{n+1} (Section 2: tent functions), summed per cell
+          if (newkey != acc_key) {
+            if (acc_key >= 0)
+              deposit_run32<SP>(I, acc_key, acc_m, acc_n, s00, s10, s01, s11, acc_cnt, pm0, pn0,
+                                patch, cpatch);
+            acc_key = newkey;
+            acc_m = m1;
+            acc_n = n1;
+            acc_cnt = 0;
+            s00 = s10 = s01 = s11 = 0.0f;
+          }
           const float wr1 = rweight_upper32(I, dr1, m1), wz1 = dz1;
-          w00 = (1.0f - wr1) * (1.0f - wz1);
-          w10 = wr1 * (1.0f - wz1);
-          w01 = (1.0f - wr1) * wz1;
-          w11 = wr1 * wz1;
-          dm = m1;
-          dn = n1;
+          s00 += (1.0f - wr1) * (1.0f - wz1);
+          s10 += wr1 * (1.0f - wz1);
+          s01 += (1.0f - wr1) * wz1;
+          s11 += wr1 * wz1;
+          ++acc_cnt;
         } else {
           reinterpret_cast<unsigned int*>(P.b + i)[1] = kDead;
         }
       }
-      // deposit: sum the weights of lanes in the same cell (one exact integer
-      // warp reduction of 2^-26 fixed-point weights when the whole warp is in
-      // one cell, runs of neighbouring lanes otherwise), then one shared-memory
-      // (or global) atomic per node and group
-      const unsigned full = 0xffffffffu;
-      const bool one_cell = __all_sync(full, newkey == __shfl_sync(full, newkey, 0));
-      bool tail;
-      if (one_cell) {
-        const float kf = 67108864.0f, ki = 1.0f / 67108864.0f;
-        w00 = (float)__reduce_add_sync(full, __float2uint_rn(w00 * kf)) * ki;
-        w10 = (float)__reduce_add_sync(full, __float2uint_rn(w10 * kf)) * ki;
-        w01 = (float)__reduce_add_sync(full, __float2uint_rn(w01 * kf)) * ki;
-        w11 = (float)__reduce_add_sync(full, __float2uint_rn(w11 * kf)) * ki;
-        tail = lane == 0;
-      } else {
-        tail = run_sum4(newkey, w00, w10, w01, w11);
-      }
-      if (tail && newkey >= 0) {
-        const int lm = dm - pm0, ln = dn - pn0;
-        if (lm >= 0 && lm + 1 < kPR32 && ln >= 0 && ln + 1 < kPZ32) {
-          float* p = patch + lm * kPZ32 + ln;
-          atomicAdd(p, w00);
-          atomicAdd(p + kPZ32, w10);
-          atomicAdd(p + 1, w01);
-          atomicAdd(p + kPZ32 + 1, w11);
-        } else {
-          double* q = I.qacc64[SP];
-          const int gi = node_index(I, dm, dn), nz1 = I.nz + 1;
-          atomicAdd(q + gi, (double)w00);
-          atomicAdd(q + gi + nz1, (double)w10);
-          atomicAdd(q + gi + 1, (double)w01);
-          atomicAdd(q + gi + nz1 + 1, (double)w11);
-        }
-      }
-      if (one_cell) {
-        if (lane == 0 && newkey >= 0) atomicAdd(&I.counts[SP][newkey], 32);
-      } else {
-        const unsigned peers = __match_any_sync(full, newkey);
-        if (newkey >= 0 && lane == __ffs(peers) - 1) atomicAdd(&I.counts[SP][newkey], __popc(peers));
-      }
     }
+    if (acc_key >= 0)
+      deposit_run32<SP>(I, acc_key, acc_m, acc_n, s00, s10, s01, s11, acc_cnt, pm0, pn0, patch,
+                        cpatch);
     __syncthreads();
     if (SP == 0) {
       // the queued collisions (Section 3), on the state written above
@@ -428,7 +431,7 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
       while (over) {
         const int j = __ffs(over) - 1;
         over &= over - 1;
-        collide_at32(I, P, c0 + (long long)j * blockDim.x + threadIdx.x, step);
+        collide_at32(I, P, run0 + (long long)j * 32 + lane, step);
       }
     }
     for (int k = threadIdx.x; k < kPR32 * kPZ32; k += blockDim.x) {
@@ -437,6 +440,14 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
         const int gm = pm0 + k / kPZ32, gn = pn0 + k % kPZ32;
         atomicAdd(I.qacc64[SP] + node_index(I, gm, gn), (double)v);
         patch[k] = 0.0f;
+      }
+    }
+    for (int k = threadIdx.x; k < (kPR32 - 1) * (kPZ32 - 1); k += blockDim.x) {
+      const int c = cpatch[k];
+      if (c != 0) {
+        const int gm = pm0 + k / (kPZ32 - 1), gn = pn0 + k % (kPZ32 - 1);
+        atomicAdd(&I.counts[SP][cell_key(I, gm, gn)], c);
+        cpatch[k] = 0;
       }
     }
     __syncthreads();
@@ -450,12 +461,14 @@ template <int GATHER>
 __global__ void __launch_bounds__(kPush32Threads, 4) k_push32_all(const Inst* insts, WorkQueue* q,
                                                                    int ppt) {
   __shared__ float patch[kPR32 * kPZ32];
+  __shared__ int cpatch[(kPR32 - 1) * (kPZ32 - 1)];
   __shared__ int anchor[3];
   __shared__ int cq[kCollQ32];
   __shared__ Inst sI;
   __shared__ int s_inst, s_sp, s_skip;
   __shared__ long long s_c0;
   for (int k = threadIdx.x; k < kPR32 * kPZ32; k += blockDim.x) patch[k] = 0.0f;
+  for (int k = threadIdx.x; k < (kPR32 - 1) * (kPZ32 - 1); k += blockDim.x) cpatch[k] = 0;
   int cur = -1;
   double K0 = 0.0, K1 = 0.0;
   const long long chunk = (long long)ppt * blockDim.x;
@@ -485,8 +498,8 @@ __global__ void __launch_bounds__(kPush32Threads, 4) k_push32_all(const Inst* in
       cur = inst;
     }
     if (!s_skip) {
-      if (s_sp == 0) K0 += push_chunk32<0, GATHER>(sI, s_c0, ppt, patch, anchor, cq);
-      else K1 += push_chunk32<1, GATHER>(sI, s_c0, ppt, patch, anchor, cq);
+      if (s_sp == 0) K0 += push_chunk32<0, GATHER>(sI, s_c0, ppt, patch, cpatch, anchor, cq);
+      else K1 += push_chunk32<1, GATHER>(sI, s_c0, ppt, patch, cpatch, anchor, cq);
     }
     __syncthreads();
   }

@@ -56,6 +56,7 @@ class PicConfig(C.Structure):
         ("gap_neumann", C.c_int32), ("wall_neumann", C.c_int32),
         ("band_r_lo", C.c_double), ("band_r_hi", C.c_double),
         ("ied_bins", C.c_int32), ("ied_emax", C.c_double), ("phi_extrapolate", C.c_int32),
+        ("poisson_precond", C.c_int32),
     ]
 
     @classmethod
@@ -146,6 +147,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         L.pic_step.argtypes = [vp, C.c_int64]
         L.pic_uses_graph.argtypes = [vp]
         L.pic_tuned_chunk.argtypes = [vp, C.POINTER(C.c_int)]
+        L.pic_set_chunk.argtypes = [vp, C.c_int]
+        L.pic_get_species_charge.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int]
         L.pic_sync.argtypes = [vp]
         L.pic_diagnostics.argtypes = [vp, C.c_int, C.POINTER(PicDiag)]
         L.pic_reweight.argtypes = [vp, C.c_int, C.c_int]
@@ -325,6 +328,12 @@ def pic_get_fields(h: Handle, instance: int = 0) -> dict:
     return {"phi": phi, "rho": rho, "Q": Q}
 
 
+def pic_get_species_charge(h: Handle, instance: int, species: int) -> np.ndarray:
+    Q = np.empty(_node_shape(h, instance))
+    _check(h, load_library().pic_get_species_charge(h.ptr, instance, species, Q.ctypes.data, 0))
+    return Q
+
+
 def pic_set_circuit(h: Handle, instance: int, Vc: float, step: int, qhist=None):
     q = _f64(qhist if qhist is not None else np.zeros(h.params[instance]["n_avg"]))
     _check(h, load_library().pic_set_circuit(h.ptr, instance, Vc, step,
@@ -353,6 +362,10 @@ def pic_tuned_chunk(h: Handle) -> int:
     v = C.c_int()
     _check(h, load_library().pic_tuned_chunk(h.ptr, C.byref(v)))
     return v.value
+
+
+def pic_set_chunk(h: Handle, particles_per_thread: int):
+    _check(h, load_library().pic_set_chunk(h.ptr, particles_per_thread))
 
 
 def pic_sync(h: Handle):

@@ -76,7 +76,7 @@ def base_params() -> dict:
         n_meta=0.0, meta_a=4.0e-18, meta_I=4.20,
         gap_neumann=0, wall_neumann=0,
         band_r_lo=0.010, band_r_hi=0.015, ied_bins=0, ied_emax=600.0,
-        poisson_tol=1e-10, poisson_max_iter=200, phi_extrapolate=0,
+        poisson_tol=1e-10, poisson_max_iter=200, phi_extrapolate=0, poisson_precond=0,
         cap_e=0, cap_i=0, birth_cap=0, diag_every=1,
         sort_every=1,
     )
@@ -124,6 +124,26 @@ def params_paper(gather: int = 0, precision: int = 0, seed: int = 0, cells: int 
              E_cap=600.0, ied_bins=160, ied_emax=320.0,
              gather=gather, precision=precision, seed=seed)
     return p
+
+
+# Long-run statistics of the 32 x 32 discharge with the external circuit
+# ("cfg 1L": V_s = 400 V, R_ext = 200 Ohm, 1e5 steps of 50 ps = 5 us): the
+# averages are taken over the second half, sampled every STEADY_EVERY steps.
+STEADY_STEPS = 100_000
+STEADY_WINDOW = 50_000
+STEADY_EVERY = 50
+
+
+def steady_cfg1L(seed: int, gather: int = 0, precision: int = 0) -> tuple[dict, dict]:
+    """The 32 x 32 discharge of ``params_rz32`` with the external circuit
+    V_s = 400 V, R_ext = 200 Ohm (100-step current average), seeded by
+    ``seed`` (Philox key and the seed plasma's draw): 64 macroparticles per
+    cell per species of a uniform 1e15 m^-3, 2 eV / 0.026 eV plasma."""
+    p = params_rz32(gather=gather, precision=precision, seed=seed)
+    p.update(circuit_mode=1, Vs=400.0, Rext=200.0, n_avg=100, diag_every=STEADY_EVERY,
+             poisson_tol=1e-10)
+    p, parts = seed_plasma(p, 32 * 32 * 64, n0=1e15, seed=1000 + seed)
+    return with_capacity(p, parts, factor=2.0, births=1 << 16), parts
 
 
 def params_rz128_sweep(gather: int = 0, precision: int = 0, seed: int = 0) -> list[dict]:

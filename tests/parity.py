@@ -5,6 +5,7 @@ from __future__ import annotations
 import math
 
 import numpy as np
+import pytest
 
 import pic_inputs
 from pic_inputs import E_CHARGE, M_ELECTRON
@@ -68,3 +69,32 @@ def electron_energy_eV(d: dict) -> np.ndarray:
 
 def thermal_speed(T_eV: float, mass: float) -> float:
     return math.sqrt(T_eV * E_CHARGE / mass)
+
+
+COUNT_KEYS = ("N_e", "N_i", "n_ion_cath", "n_e_cath", "n_sey", "n_ionize", "n_excite",
+              "n_elastic", "n_ionize_meta", "ppc_max_e", "ppc_max_i")
+
+
+def check_step64(pg, h, orc, instance: int = 0, check_phi: bool = True) -> dict:
+    """One FP64 step of instance `instance` of handle h against the oracle
+    `orc`: integer counters equal; positions and velocities per species within
+    PARTICLE_TOL (identical id sets); node charge of each species and in total
+    within 1e-12; phi within FIELD_TOL; I, V_c within 1e-12; energies and
+    peak densities within 1e-10.  Returns the GPU diagnostics."""
+    de, do = pg.pic_diagnostics(h, instance), orc.diag()
+    for key in COUNT_KEYS:
+        assert de[key] == do[key], (instance, key, de[key], do[key])
+    for sp in (0, 1):
+        err = compare_species(pg.pic_get_particles(h, instance, sp), orc.get_particles(sp))
+        assert err["pos"] <= PARTICLE_TOL and err["vel"] <= PARTICLE_TOL, (instance, sp, err)
+        qs = field_err(pg.pic_get_species_charge(h, instance, sp), orc.species_charge(sp))
+        assert qs <= 1e-12, (instance, sp, qs)
+    fg, fo = pg.pic_get_fields(h, instance), orc.fields()
+    assert field_err(fg["Q"], fo["Q"]) <= 1e-12
+    if check_phi:
+        assert field_err(fg["phi"], fo["phi"]) <= FIELD_TOL
+    for key in ("I_cath", "V_cath"):
+        assert de[key] == pytest.approx(do[key], rel=1e-12, abs=1e-12), (instance, key)
+    for key in ("K_e", "K_i", "W_field", "n_e_peak", "n_i_peak"):
+        assert de[key] == pytest.approx(do[key], rel=1e-10), (instance, key)
+    return de

@@ -11,8 +11,8 @@ import pytest
 
 import oracle
 import pic_inputs
-from parity import (FIELD_TOL, PARTICLE_TOL, busy_state, compare_species, field_err,
-                    sort_by_id)
+from parity import (FIELD_TOL, PARTICLE_TOL, busy_state, check_step64, compare_species,
+                    field_err, sort_by_id)
 
 pytestmark = pytest.mark.gpu
 
@@ -39,22 +39,7 @@ def _pair(pg, p, parts, set_phi=True):
 
 
 def _check_step(pg, h, orc, check_phi=True):
-    de, do = pg.pic_diagnostics(h, 0), orc.diag()
-    for key in ("N_e", "N_i", "n_ion_cath", "n_e_cath", "n_sey", "n_ionize", "n_excite",
-                "n_elastic", "n_ionize_meta", "ppc_max_e", "ppc_max_i"):
-        assert de[key] == do[key], (key, de[key], do[key])
-    for sp in (0, 1):
-        err = compare_species(pg.pic_get_particles(h, 0, sp), orc.get_particles(sp))
-        assert err["pos"] <= PARTICLE_TOL and err["vel"] <= PARTICLE_TOL, (sp, err)
-    fg, fo = pg.pic_get_fields(h, 0), orc.fields()
-    assert field_err(fg["Q"], fo["Q"]) <= 1e-12
-    if check_phi:
-        assert field_err(fg["phi"], fo["phi"]) <= FIELD_TOL
-    for key in ("I_cath", "V_cath"):
-        assert de[key] == pytest.approx(do[key], rel=1e-12, abs=1e-12)
-    for key in ("K_e", "K_i", "W_field", "n_e_peak", "n_i_peak"):
-        assert de[key] == pytest.approx(do[key], rel=1e-10), key
-    return de
+    return check_step64(pg, h, orc, 0, check_phi)
 
 
 @pytest.mark.parametrize("gather", [0, 1])
@@ -564,12 +549,13 @@ def test_phi_extrapolation_same_phi_fewer_iterations(pg):
     """Each step's Poisson solve started from 2 phi^(n-1) - phi^(n-2) on the
     unknown nodes: the first step after pic_solve_fields has no earlier
     solution and is the plain step bit for bit (2 phi - phi = phi exactly);
-    on the second both starts reach the 1e-10 relative residual, so the two
-    phi differ by at most the tolerance times the condition number of the
-    32 x 32 operator (below 1e4); over the run the extrapolated starts need no
-    more iterations than the previous solution as the start."""
+    on the second both starts reach a 1e-13 relative residual, so with the
+    condition number of the 32 x 32 operator (below 1e4) the two phi agree to
+    1e-10; over the run the extrapolated starts need no more multigrid-PCG
+    iterations than the previous solution as the start."""
     p = pic_inputs.params_rz32()
-    p.update(circuit_mode=1, Vs=400.0, Rext=2000.0, n_avg=4)
+    p.update(circuit_mode=1, Vs=400.0, Rext=2000.0, n_avg=4, poisson_tol=1e-13,
+             poisson_precond=1, poisson_max_iter=400)
     p, parts = busy_state(p, ppc=32, seed=23)
     p = pic_inputs.with_capacity(p, parts, factor=2.0)
     hs = []
@@ -588,10 +574,66 @@ def test_phi_extrapolation_same_phi_fewer_iterations(pg):
         if step == 0:
             assert np.array_equal(phi0, phi1)
         elif step == 1:
-            assert field_err(phi1, phi0) <= 1e4 * FIELD_TOL
+            assert field_err(phi1, phi0) <= FIELD_TOL
     print(f"Poisson iterations over 30 steps: start phi^(n-1) {sum(iters[0])}, "
           f"extrapolated {sum(iters[1])}")
     assert iters[0][0] == iters[1][0]
     assert sum(iters[1]) <= sum(iters[0])
     for h in hs:
         pg.pic_destroy(h)
+
+
+@pytest.mark.parametrize("gather", [0, 1])
+def test_sine_transform_and_multigrid_preconditioners_agree(pg, gather):
+    """The two preconditioners of the PCG solve (Section 3's Poisson problem
+    with every boundary node a conductor): the sine transform along z with a
+    tridiagonal solve per mode is exact for the operator up to its FP32
+    arithmetic, the multigrid V-cycle is not; both solve to the same relative
+    residual, so over several steps the particles and phi of the two runs
+    match the oracle, and the sine-transform runs need at most three
+    iterations per step."""
+    p = pic_inputs.params_rz32(gather=gather)
+    p.update(poisson_tol=1e-13, circuit_mode=1, Vs=400.0, Rext=2000.0, n_avg=4, gamma_i=0.2)
+    p, parts = pic_inputs.seed_plasma(p, 32 * 32 * 8, seed=19, Te_eV=5.0)
+    p = pic_inputs.with_capacity(p, parts, factor=2.0)
+    orc = oracle.Oracle(p, parts)
+    hs = []
+    for pre in (0, 1):
+        h = pg.pic_create(dict(p, poisson_precond=pre))
+        for k, sp in (("e", 0), ("i", 1)):
+            pg.pic_set_particles(h, 0, sp, parts[k])
+        pg.pic_set_phi(h, 0, orc.fields()["phi"])
+        hs.append(h)
+    iters = [0, 0]
+    for _ in range(4):
+        orc.step(1)
+        for j, h in enumerate(hs):
+            pg.pic_step(h, 1)
+            d = check_step64(pg, h, orc)
+            iters[j] = max(iters[j], d["poisson_iters"])
+            assert d["poisson_resid"] <= 1e-13
+    print(f"most PCG iterations per step: sine transform {iters[0]}, multigrid {iters[1]}")
+    assert iters[0] <= 3 and iters[0] < iters[1]
+    for h in hs:
+        pg.pic_destroy(h)
+
+
+@pytest.mark.parametrize("nr, nz", [(256, 256), (256, 512), (128, 128), (20, 36)])
+def test_sine_transform_solve_fields(pg, nr, nz):
+    """pic_solve_fields on the sine-transform preconditioner against the
+    oracle's banded Cholesky solve, on the benchmark grids and a ragged one."""
+    p = pic_inputs.params_rz256()
+    p.update(nr=nr, nz=nz, L=p["R"] * nz / nr, poisson_tol=1e-13)
+    p, parts = pic_inputs.grown_ring_state(p, 20 * nr * nz, seed=nr + nz)
+    p = pic_inputs.with_capacity(p, parts)
+    orc = oracle.Oracle(p, parts)
+    h = pg.pic_create(p)
+    for k, sp in (("e", 0), ("i", 1)):
+        pg.pic_set_particles(h, 0, sp, parts[k])
+    pg.pic_solve_fields(h, 0)
+    assert field_err(pg.pic_get_fields(h, 0)["phi"], orc.fields()["phi"]) <= FIELD_TOL
+    pg.pic_set_chunk(h, 8)
+    pg.pic_step(h, 1)
+    d = pg.pic_diagnostics(h, 0)
+    assert d["poisson_iters"] <= 3 and d["poisson_resid"] <= 1e-13
+    pg.pic_destroy(h)

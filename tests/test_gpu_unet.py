@@ -136,8 +136,11 @@ def test_single_layer_paths_are_exact_in_structure(pg):
 
 def _simulation(pg, steps, mode, every=1, cap=128, seed=5, nr=32, nz=32, ppc=16):
     p = pic_inputs.params_rz32(gather=0)
-    p.update(nr=nr, nz=nz, L=p["R"] * nz / nr, poisson_tol=1e-10, circuit_mode=1, Vs=400.0,
-             Rext=500.0, n_avg=4, gamma_i=0.2)
+    # the warm start serves the multigrid-preconditioned solve (with the
+    # sine-transform preconditioner two iterations reach the tolerance from
+    # any start); both arms solve to 1e-13 so that their phi agree to 1e-10
+    p.update(nr=nr, nz=nz, L=p["R"] * nz / nr, poisson_tol=1e-13, circuit_mode=1, Vs=400.0,
+             Rext=500.0, n_avg=4, gamma_i=0.2, poisson_precond=1, poisson_max_iter=400)
     p, parts = pic_inputs.seed_plasma(p, nr * nz * ppc, seed=seed, Te_eV=5.0)
     p = pic_inputs.with_capacity(p, parts, factor=2.0)
     h = pg.pic_create(p)
@@ -175,9 +178,9 @@ def test_correction_mode_saves_iterations_and_keeps_phi(pg, tmp_path):
     """Mode 1 (the network predicts the change of phi from the residual of the
     previous solution): from identical states, steps with the warm start need
     fewer Poisson iterations than the plain solver started from the previous
-    solution, and the first step reaches the same phi: both solves meet the
-    1e-10 relative residual, and the condition number of the 32 x 32 RZ
-    operator (below 1e4) bounds the difference of the two solutions."""
+    solution, and the first step reaches the same phi: both solves meet a
+    1e-13 relative residual, so with the condition number of the 32 x 32 RZ
+    operator (below 1e4) the two solutions agree to 1e-10."""
     p, h = _simulation(pg, 96, 1, seed=9)
     pg.pic_unet_train(h, 1500, 8, 2e-3, seed=3)
     path = str(tmp_path / "ck.bin")
@@ -193,7 +196,7 @@ def test_correction_mode_saves_iterations_and_keeps_phi(pg, tmp_path):
     phi_on = pg.pic_get_fields(h, 0)["phi"]
     on, starts = _iters(pg, h, 15)
     print(f"correction mode, 15 steps: Poisson iterations plain {off}, warm {on}; starts {starts}")
-    assert field_err(phi_on, phi_off) <= 1e4 * FIELD_TOL
+    assert field_err(phi_on, phi_off) <= FIELD_TOL
     assert starts["starts_network"] >= 8
     assert on < off
 
@@ -219,4 +222,4 @@ def test_potential_mode_beats_a_cold_start(pg, tmp_path):
     assert starts["starts_network"] == 1
     assert on < off
     assert field_err(pg.pic_get_fields(h, 0)["phi"], pg.pic_get_fields(plain, 0)["phi"]) <= \
-        1e4 * FIELD_TOL
+        FIELD_TOL

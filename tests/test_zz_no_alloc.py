@@ -3,8 +3,9 @@ allocate device memory while they run (its scratch is a fixed device array
 inside the library) -- must give the same phi as pic_poisson_solve, whose
 scratch the caller allocates.
 
-Two calls in a row with different grids and data check that what the first
-call leaves in the shared array does not leak into the second.  The file is
+Three calls in a row with different grids and data (the largest grid the
+array holds, 256 x 512 cells, first) check that what one call leaves in the
+shared array does not leak into the next.  The file is
 named to be collected last; it builds and loads the library itself so that it
 also passes alone in a fresh process.
 """
@@ -48,7 +49,7 @@ def _problem(nr, nz, seed):
 def test_static_scratch_matches_caller_scratch(lib):
     import torch
     stream = torch.cuda.current_stream().cuda_stream
-    for call, (nr, nz) in enumerate([(256, 256), (64, 48)]):
+    for call, (nr, nz) in enumerate([(256, 512), (64, 48), (256, 256)]):
         R, L, Q, bc = _problem(nr, nz, seed=100 + call)
         Qd = torch.tensor(Q, device="cuda")
         phi_ref = torch.tensor(bc, device="cuda")
