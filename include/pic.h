@@ -248,6 +248,17 @@ int pic_tuned_chunk(pic_handle* h, int* particles_per_thread);
  * Drops the captured step graph.  PIC_ERR_INVALID for any other value. */
 int pic_set_chunk(pic_handle* h, int particles_per_thread);
 
+/* The push's online tuning.  The first four steps of a handle time the four
+ * chunk sizes; later, when at the start of a pic_step call the live particle
+ * count of all instances (as copied after the previous call) differs from the
+ * count at the last tuning by a factor of 4 or more, the next four steps tune
+ * again and the step graph is captured anew (unless the size was fixed with
+ * pic_set_chunk).  *tunings: tunings completed; *particles_per_thread: the
+ * size in use (0 while tuning); *particles_at_tuning: live particles when the
+ * last tuning ended.  Any pointer may be NULL. */
+int pic_autotune_info(pic_handle* h, int* tunings, int* particles_per_thread,
+                      int64_t* particles_at_tuning);
+
 /* Wait for the handle's stream; return the latched status of all instances. */
 int pic_sync(pic_handle* h);
 

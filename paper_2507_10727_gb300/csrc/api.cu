@@ -48,6 +48,15 @@ struct pic_handle {
   int ppt = 8;                       // particles per thread per work item (autotuned)
   int tune_next = 0;                 // next autotuner candidate; -1 = done
   float tune_ms[4] = {0, 0, 0, 0};
+  // re-tuning when the particle count has changed by kRetuneFactor since the
+  // last tuning: the live count of all instances is copied to page-locked
+  // host memory after each pic_step call and read at the next one
+  bool retune = true;                // off after pic_set_chunk with a fixed size
+  int tunings = 0;                   // tunings completed
+  long long tuned_at = 0;            // live particles (all instances) at the last tuning
+  long long* d_live = nullptr;       // device: live particles after the last step
+  long long* h_live = nullptr;       // page-locked copy
+  cudaEvent_t live_ev = nullptr;     // recorded after the copy
   UNet* unet = nullptr;              // learned warm start (single instance)
   pic_alloc alloc;
   bool own_alloc = true;
@@ -486,10 +495,14 @@ int pic_create(const pic_config* cfgs, int n_instances, const pic_alloc* alloc, 
     h->d_insts = (Inst*)dev_alloc(h, sizeof(Inst) * n_instances);
     h->d_queue = (WorkQueue*)dev_alloc(h, sizeof(WorkQueue));
     h->d_pargs = dev_alloc(h, poisson_args_bytes() * n_instances);
-    if (!h->d_insts || !h->d_queue || !h->d_pargs) {
+    h->d_live = (long long*)dev_alloc(h, sizeof(long long));
+    if (!h->d_insts || !h->d_queue || !h->d_pargs || !h->d_live ||
+        cudaHostAlloc((void**)&h->h_live, sizeof(long long), cudaHostAllocDefault) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->live_ev, cudaEventDisableTiming) != cudaSuccess) {
       pic_destroy(h);
       return PIC_ERR_OOM;
     }
+    *h->h_live = -1;
     std::vector<Inst> hi(n_instances);
     for (int k = 0; k < n_instances; ++k) {
       hi[k] = h->inst[k].I;
@@ -515,6 +528,8 @@ void pic_destroy(pic_handle* h) {
   cudaStreamSynchronize(h->stream);
   if (h->graph) cudaGraphExecDestroy(h->graph);
   for (cudaEvent_t ev : h->prof.pool) cudaEventDestroy(ev);
+  if (h->live_ev) cudaEventDestroy(h->live_ev);
+  if (h->h_live) cudaFreeHost(h->h_live);
   for (InstHost& ih : h->inst)
     if (ih.pw) poisson_work_free(ih.pw);
   if (h->unet) unet_destroy(h->unet);
@@ -854,9 +869,18 @@ static cudaError_t launch_ensemble_step(pic_handle* h, const StepMarks* marks) {
   const Inst& I0 = h->inst[0].I;
   cudaStream_t st = h->stream;
   cudaError_t e = cudaSuccess;
+  BatchDims bd{};
+  for (const InstHost& ih : h->inst) {
+    const long long cells = (long long)ih.I.nr * ih.I.nz;
+    const long long nodes = (long long)(ih.I.nr + 1) * (ih.I.nz + 1);
+    bd.cells_max = cells > bd.cells_max ? cells : bd.cells_max;
+    bd.nodes_max = nodes > bd.nodes_max ? nodes : bd.nodes_max;
+    bd.birth_cap_max = ih.I.birth_cap > bd.birth_cap_max ? ih.I.birth_cap : bd.birth_cap_max;
+    bd.any_append = bd.any_append || ih.I.sort_every > 1;
+  }
+  bd.prec32 = I0.prec32;
   mk(G_FIELD, true);
-  for (InstHost& ih : h->inst)
-    if (e == cudaSuccess) e = launch_field_tables(ih.I, h->num_sms, st);
+  if (e == cudaSuccess) e = launch_field_tables_batch(h->d_insts, n, bd, h->num_sms, st);
   mk(G_FIELD, false);
   const int threads = 256;
   mk(G_PUSH, true);
@@ -865,15 +889,13 @@ static cudaError_t launch_ensemble_step(pic_handle* h, const StepMarks* marks) {
     e = launch_push_all(h->d_insts, h->d_queue, I0.prec32, I0.gather, h->ppt, h->num_sms, st);
   mk(G_PUSH, false);
   mk(G_SCATTER, true);
-  for (InstHost& ih : h->inst)
-    if (e == cudaSuccess) e = launch_post_push(ih.I, h->num_sms, st);
+  if (e == cudaSuccess) e = launch_post_push_batch(h->d_insts, n, bd, h->num_sms, st);
   mk(G_SCATTER, false);
   mk(G_POISSON, true);
   if (e == cudaSuccess) e = launch_poisson_group(h->pws.data(), nullptr, n, h->d_pargs, h->num_sms, st);
   mk(G_POISSON, false);
   mk(G_STEP_END, true);
-  for (InstHost& ih : h->inst)
-    if (e == cudaSuccess) e = launch_step_end(ih.I, st);
+  if (e == cudaSuccess) e = launch_step_end_batch(h->d_insts, n, st);
   mk(G_STEP_END, false);
   return e;
 }
@@ -917,6 +939,23 @@ static cudaError_t force_sorts(pic_handle* h, int on) {
   return e;
 }
 
+// live particles of all instances: `out` after a synchronous read (tuning),
+// or copied to h_live behind the step's work (read at the next pic_step)
+static cudaError_t enqueue_live_count(pic_handle* h) {
+  cudaError_t e = launch_live_total(h->d_insts, (int)h->inst.size(), h->d_live, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->h_live, h->d_live, sizeof(long long), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(h->live_ev, h->stream);
+  return e;
+}
+
+static cudaError_t live_count(pic_handle* h, long long* out) {
+  cudaError_t e = enqueue_live_count(h);
+  if (e == cudaSuccess) e = cudaEventSynchronize(h->live_ev);
+  if (e == cudaSuccess) *out = *h->h_live;
+  return e;
+}
+
 static int autotune_step(pic_handle* h) {
   const int c = h->tune_next;
   h->ppt = kTuneCandidates[c];
@@ -947,6 +986,11 @@ static int autotune_step(pic_handle* h) {
       if (h->tune_ms[k] < h->tune_ms[best]) best = k;
     h->ppt = kTuneCandidates[best];
     h->tune_next = -1;
+    ++h->tunings;
+    long long live = 0;
+    const cudaError_t e2 = live_count(h, &live);
+    if (e2 != cudaSuccess) return cuda_fail(h, e2, "tune");
+    h->tuned_at = live;
     const cudaError_t e1 = force_sorts(h, 0);
     if (e1 != cudaSuccess) return cuda_fail(h, e1, "tune");
   }
@@ -989,9 +1033,40 @@ static void build_graph(pic_handle* h) {
   else h->graph_failed = true;
 }
 
+static int step_calls(pic_handle* h, int64_t nsteps);
+static const double kRetuneFactor = 4.0;
+
+// Re-tune the push when the live particle count seen after the previous call
+// differs from the count at the last tuning by kRetuneFactor or more (the
+// best chunk size depends on the work per instance); the captured graph is
+// rebuilt after the tuning steps.
+static void check_retune(pic_handle* h) {
+  if (!h->retune || h->tune_next >= 0 || h->tunings == 0) return;
+  if (cudaEventQuery(h->live_ev) != cudaSuccess) {
+    cudaGetLastError();   // not done yet: look again at the next call
+    return;
+  }
+  const long long live = *h->h_live;
+  if (live < 0 || h->tuned_at <= 0) return;
+  const double ratio = (double)live / (double)h->tuned_at;
+  if (ratio >= kRetuneFactor || ratio <= 1.0 / kRetuneFactor) {
+    drop_graph(h);
+    h->tune_next = 0;
+  }
+}
+
 int pic_step(pic_handle* h, int64_t nsteps) {
   if (!h || nsteps < 0) return fail(h, PIC_ERR_INVALID, "bad argument");
   if (nsteps == 0) return PIC_OK;
+  check_retune(h);
+  const int rc = step_calls(h, nsteps);
+  if (rc != PIC_OK) return rc;
+  const cudaError_t e = enqueue_live_count(h);
+  if (e != cudaSuccess) return cuda_fail(h, e, "live count");
+  return PIC_OK;
+}
+
+static int step_calls(pic_handle* h, int64_t nsteps) {
   // the first steps of a handle tune the push's chunk size
   while (h->tune_next >= 0 && nsteps > 0) {
     const int rc = autotune_step(h);
@@ -1032,9 +1107,20 @@ int pic_set_chunk(pic_handle* h, int particles_per_thread) {
   if (k >= 0) {
     h->ppt = particles_per_thread;
     h->tune_next = -1;
+    h->retune = false;      // fixed by the caller
   } else {
     h->tune_next = 0;       // tune again over the next four steps
+    h->retune = true;
   }
+  return PIC_OK;
+}
+
+int pic_autotune_info(pic_handle* h, int* tunings, int* particles_per_thread,
+                      int64_t* particles_at_tuning) {
+  if (!h) return PIC_ERR_INVALID;
+  if (tunings) *tunings = h->tunings;
+  if (particles_per_thread) *particles_per_thread = h->tune_next < 0 ? h->ppt : 0;
+  if (particles_at_tuning) *particles_at_tuning = h->tuned_at;
   return PIC_OK;
 }
 

@@ -222,6 +222,16 @@ struct Inst {
   DiagDev* diag;
 };
 
+// Copy an instance's parameters into shared memory (whole block; ends with a
+// barrier): the batched launches of an ensemble's per-instance kernels take
+// the instance from blockIdx.z and the array of the instances' parameters.
+__device__ __forceinline__ void stage_inst(const Inst* src, Inst* dst) {
+  const unsigned* s4 = reinterpret_cast<const unsigned*>(src);
+  unsigned* d4 = reinterpret_cast<unsigned*>(dst);
+  for (int k = threadIdx.x; k < (int)(sizeof(Inst) / 4); k += blockDim.x) d4[k] = s4[k];
+  __syncthreads();
+}
+
 // Whether this step ends with the full cell sort: every sort_every-th step,
 // and whenever appending the births in place would overflow a buffer.  The
 // scatter and the step-end kernel take the same decision from the same state.

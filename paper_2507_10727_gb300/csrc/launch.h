@@ -79,6 +79,22 @@ cudaError_t launch_push_all(const Inst* d_insts, WorkQueue* q, int prec32, int g
 cudaError_t launch_push32_all(const Inst* d_insts, WorkQueue* q, int gather, int ppt, int num_sms,
                               cudaStream_t st);
 cudaError_t launch_post_push(const Inst& I, int num_sms, cudaStream_t st);
+// the per-instance kernels of an ensemble step as one launch each over all
+// instances (gridDim.z = instances); extents from the largest instance
+struct BatchDims {
+  long long cells_max, nodes_max, birth_cap_max;
+  int prec32;
+  int any_append;   // some instance appends births between full sorts
+};
+cudaError_t launch_field_tables_batch(const Inst* d_insts, int n_inst, const BatchDims& bd,
+                                      int num_sms, cudaStream_t st);
+cudaError_t launch_post_push_batch(const Inst* d_insts, int n_inst, const BatchDims& bd,
+                                   int num_sms, cudaStream_t st);
+cudaError_t launch_step_end_batch(const Inst* d_insts, int n_inst, cudaStream_t st);
+cudaError_t launch_scatter32_batch(const Inst* d_insts, int n_inst, int blocks, cudaStream_t st);
+cudaError_t launch_append32_batch(const Inst* d_insts, int n_inst, int blocks, cudaStream_t st);
+// live particles summed over the instances into *out (device)
+cudaError_t launch_live_total(const Inst* d_insts, int n_inst, long long* out, cudaStream_t st);
 cudaError_t launch_step_end(const Inst& I, cudaStream_t st);
 // all instances' Poisson solves in one cooperative launch (block groups)
 cudaError_t launch_poisson_group(PoissonWork* const* pws, const Inst* insts, int n_inst,

@@ -864,74 +864,159 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
 
 // ----------------------------------------------------------------------------
 // Flexible PCG with the sine-transform preconditioner (all boundary nodes
-// conductors).  z = M^{-1} r in three phases separated by grid barriers:
-//   A  rows:    f_hat[m][k] = sum_n S[k][n] f[m][n],  f = scale r (FP32)
-//   B  columns: (lambda_k D + L) u_hat[:, k] = f_hat[:, k], Thomas in m
-//   C  rows:    u[m][n] = sum_k S[n][k] u_hat[m][k];  z = u unscale (FP64)
+// conductors).  z = M^{-1} r:
+//   rows:    f_hat[m][k] = sum_n S[k][n] f[m][n],  f = scale r (FP32)
+//   columns: (lambda_k D + L) u_hat[:, k] = f_hat[:, k], Thomas in m
+//   rows:    u[m][n] = sum_k S[n][k] u_hat[m][k];  z = u unscale (FP64)
 // lambda_k = 4 sin^2(pi (k+1) / (2 nz)).  The FP32 transform makes M^{-1} A
-// the identity to about 1e-6, so the outer FP64 iteration -- the same
-// recurrences and stopping test as the multigrid kernel -- ends after two or
-// three iterations, with five grid barriers each.  Block b of a solve owns
-// rows [b R, (b + 1) R) in phases A and C (staged in shared memory) and
-// modes k = b blockDim + t in phase B.
+// the identity to about 1e-6, so the outer FP64 iteration ends after two or
+// three iterations.
+//
+// Block b of a solve owns rows [b R, (b + 1) R) (R = rows_per_block) for
+// everything but the column phase, so an iteration needs three grid barriers:
+//   1. columns: the Thomas eliminations, 32 modes per block at a time, staged
+//      in shared memory;
+//   2. rows: u_hat -> z of the own rows and the two neighbour rows, A z, and
+//      the row sums of r.z, z.q_old, z.Az;
+//   3. rows: the coefficients from the row sums, p = z + beta p,
+//      q = A z + beta q, phi += alpha p, r -= alpha q, the row sums of r.r,
+//      and the next f_hat of the own rows.
+// p.q comes from the identity (z + beta p).A(z + beta p) = z.Az + 2 beta z.q +
+// beta^2 p.q (A symmetric, q = A p).  Every dot product is summed per row by
+// one warp (lanes over n, then a fixed shuffle tree) and over the rows in
+// row order by every block, so phi does not depend on the number of blocks.
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ void sep_rows(const PoissonWork& W, int nrow, float* out, int m0,
-                                         const float* stage) {
-  // out[(m0 + j) * nk + k] = sum_n S[k][n] stage[j * nk + n], j < nrow; a
-  // thread takes two rows of one k (each S element read once for both)
+constexpr int kSepModes = 32;   // modes per block in the column phase
+enum { kRzSlot = 0, kZqSlot, kZazSlot, kRrSlot, kBbSlot, kRtSlot, kSepSlots };
+
+// row sums of `nv` values, summed over rows in order (every thread gets the
+// totals); the last slot's row r is at rows[slot * nr + r]
+__device__ __forceinline__ void sum_rows(const double* rows, int nr, int slot0, int nv,
+                                         double* out) {
+  __shared__ double tot[4];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (w < nv) {
+    const volatile double* p = rows + (size_t)(slot0 + w) * nr;
+    double s = 0.0;
+    for (int r = lane; r < nr; r += 32) s += p[r];
+    s = warp_sum64(s);
+    if (lane == 0) tot[w] = s;
+  }
+  __syncthreads();
+  for (int j = 0; j < nv; ++j) out[j] = tot[j];
+  __syncthreads();
+}
+
+// out(j, k, sum_n S[k][n] in[j][n]) for the block's rows j < nrow (in: FP32
+// rows of nk values in shared memory); a thread takes a pair of rows at one
+// k, so each element of S (read through L1 / L2, coalesced over k) serves
+// two rows; eight independent loads of S are in flight per thread.
+template <typename Out>
+__device__ __forceinline__ void sep_transform(const PoissonWork& W, const float* in, int nrow,
+                                              Out out) {
   const int nk = W.nk;
   const int pairs = (nrow + 1) >> 1;
   for (int t = threadIdx.x; t < pairs * nk; t += blockDim.x) {
     const int jp = t / nk, k = t - jp * nk;
     const int j0 = 2 * jp, j1 = j0 + 1 < nrow ? j0 + 1 : j0;
-    const float* a = stage + j0 * nk;
-    const float* b = stage + j1 * nk;
+    const float* a = in + j0 * nk;
+    const float* b = in + j1 * nk;
     const float* Sk = W.sS + k;   // S[n][k] = S[k][n]
     float s0 = 0.0f, s1 = 0.0f;
     int n = 0;
-    for (; n + 3 < nk; n += 4) {
-      const float c0 = Sk[(size_t)n * nk], c1 = Sk[(size_t)(n + 1) * nk];
-      const float c2 = Sk[(size_t)(n + 2) * nk], c3 = Sk[(size_t)(n + 3) * nk];
-      s0 = fmaf(c0, a[n], s0);
-      s1 = fmaf(c0, b[n], s1);
-      s0 = fmaf(c1, a[n + 1], s0);
-      s1 = fmaf(c1, b[n + 1], s1);
-      s0 = fmaf(c2, a[n + 2], s0);
-      s1 = fmaf(c2, b[n + 2], s1);
-      s0 = fmaf(c3, a[n + 3], s0);
-      s1 = fmaf(c3, b[n + 3], s1);
+    for (; n + 7 < nk; n += 8) {
+      float c[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) c[u] = __ldg(Sk + (size_t)(n + u) * nk);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        s0 = fmaf(c[u], a[n + u], s0);
+        s1 = fmaf(c[u], b[n + u], s1);
+      }
     }
     for (; n < nk; ++n) {
-      const float c = Sk[(size_t)n * nk];
+      const float c = __ldg(Sk + (size_t)n * nk);
       s0 = fmaf(c, a[n], s0);
       s1 = fmaf(c, b[n], s1);
     }
-    out[(size_t)(m0 + j0) * nk + k] = s0;
-    if (j1 != j0) out[(size_t)(m0 + j1) * nk + k] = s1;
+    out(j0, k, s0);
+    if (j1 != j0) out(j1, k, s1);
   }
 }
 
-// Thomas elimination of mode k: forward sweep into sHat, back substitution
-// in place.  The tables hold the eliminated pivots (sW) and upper factors (sC).
-__device__ __forceinline__ void sep_modes(const PoissonWork& W, int lb, int nb) {
+// Thomas eliminations of modes [k0, k0 + kSepModes) in shared memory (h, w, c
+// staged column-wise, kSepModes per row); one thread per mode runs the
+// forward sweep and the back substitution, then the block writes u_hat back.
+__device__ void sep_columns(const PoissonWork& W, int lb, int nb, float* sm) {
   const int nk = W.nk, nr = W.nr;
-  for (int k = lb * blockDim.x + threadIdx.x; k < nk; k += nb * blockDim.x) {
-    float* h = W.sHat + k;
-    const float* w = W.sW + k;
-    const float* c = W.sC + k;
-    float y = 0.0f;
-    for (int m = 0; m < nr; ++m) {
-      // y_m = (f_m + e_{m-1} y_{m-1}) / pivot_m  (off-diagonal -e)
-      const float e = m > 0 ? W.sE[m - 1] : 0.0f;
-      y = (h[(size_t)m * nk] + e * y) * w[(size_t)m * nk];
-      h[(size_t)m * nk] = y;
+  float* h = sm;
+  float* w = h + (size_t)nr * kSepModes;
+  float* c = w + (size_t)nr * kSepModes;
+  float* e = c + (size_t)nr * kSepModes;   // e[m] = a_r(m - 1) (e[0] = 0)
+  for (int m = threadIdx.x; m < nr; m += blockDim.x) e[m] = m > 0 ? W.sE[m - 1] : 0.0f;
+  for (int k0 = lb * kSepModes; k0 < nk; k0 += nb * kSepModes) {
+    const int nm = nk - k0 < kSepModes ? nk - k0 : kSepModes;
+    for (int t = threadIdx.x; t < nr * kSepModes; t += blockDim.x) {
+      const int m = t / kSepModes, j = t - m * kSepModes;
+      if (j < nm) {
+        const size_t g = (size_t)m * nk + k0 + j;
+        h[t] = W.sHat[g];
+        w[t] = W.sW[g];
+        c[t] = W.sC[g];
+      }
     }
-    float x = 0.0f;
-    for (int m = nr - 1; m >= 0; --m) {
+    __syncthreads();
+    if (threadIdx.x < nm) {
+      const int j = threadIdx.x;
+      // y_m = (f_m + e_m y_{m-1}) / pivot_m  (off-diagonals -e), four rows of
+      // operands loaded ahead of the recurrence
+      float y = 0.0f;
+      int m = 0;
+      for (; m + 3 < nr; m += 4) {
+        float hv[4], wv[4], ev[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          hv[u] = h[(m + u) * kSepModes + j];
+          wv[u] = w[(m + u) * kSepModes + j];
+          ev[u] = e[m + u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          y = (hv[u] + ev[u] * y) * wv[u];
+          h[(m + u) * kSepModes + j] = y;
+        }
+      }
+      for (; m < nr; ++m) {
+        y = (h[m * kSepModes + j] + e[m] * y) * w[m * kSepModes + j];
+        h[m * kSepModes + j] = y;
+      }
       // x_m = y_m + c_m x_{m+1}
-      x = fmaf(c[(size_t)m * nk], x, h[(size_t)m * nk]);
-      h[(size_t)m * nk] = x;
+      float x = 0.0f;
+      m = nr - 1;
+      for (; m - 3 >= 0; m -= 4) {
+        float hv[4], cv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          hv[u] = h[(m - u) * kSepModes + j];
+          cv[u] = c[(m - u) * kSepModes + j];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          x = fmaf(cv[u], x, hv[u]);
+          h[(m - u) * kSepModes + j] = x;
+        }
+      }
+      for (; m >= 0; --m) {
+        x = fmaf(c[m * kSepModes + j], x, h[m * kSepModes + j]);
+        h[m * kSepModes + j] = x;
+      }
     }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nr * kSepModes; t += blockDim.x) {
+      const int m = t / kSepModes, j = t - m * kSepModes;
+      if (j < nm) W.sHat[(size_t)m * nk + k0 + j] = h[t];
+    }
+    __syncthreads();
   }
 }
 
@@ -960,189 +1045,178 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson_sep(PoissonArgs A0,
   if (*(volatile int*)A.status & (ST_FATAL)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int nr = W.nr, nz = W.nz, nz1 = nz + 1, nk = W.nk;
-  const int lane = threadIdx.x & 31;
-  const int gw = (lb * blockDim.x + threadIdx.x) >> 5;
-  const int ngw = (nb * blockDim.x) >> 5;
-  const int nsf = (nz - 1 + 31) >> 5;
-  const int items0 = nr * nsf;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const long long nfree = (long long)nr * (nz - 1);
   double* phi = A.phi;
-  auto node_of = [&](int it, int& m, int& n) -> bool {
-    m = it / nsf;
-    n = 1 + (it - m * nsf) * 32 + lane;
-    return n <= nz - 1;
-  };
+  double* rows = W.partial;     // kSepSlots x nr row sums
   double* az0 = (double*)smem;
   double* ar0 = az0 + (nr + 1);
-  float* stage = (float*)(ar0 + (nr + 1));
+  unsigned char* work = (unsigned char*)(ar0 + (nr + 1));
   for (int m = threadIdx.x; m <= nr; m += blockDim.x) fine_coef(W, m, az0[m], ar0[m]);
   __syncthreads();
   const Tables T{az0, ar0, nullptr, nullptr, nullptr};
   const int R = W.rows_per_block;
   const int m0 = lb * R;
   const int nrow = m0 >= nr ? 0 : (m0 + R <= nr ? R : nr - m0);
+  // shared layout of the row phases: z of rows m0 - 1 .. m0 + R (FP64), A z
+  // of the own rows (FP64), then f or u_hat rows (FP32); the column phase
+  // reuses the same memory
+  double* zs = (double*)work;
+  double* azs = zs + (size_t)(R + 2) * nk;
+  float* fs = (float*)(azs + (size_t)R * nk);
 
-  int parity = 0;
-  double vals[3];
-  double bb = 0.0, rr = 0.0;
-  for (int it = gw; it < items0; it += ngw) {
-    int m, n;
-    if (!node_of(it, m, n)) continue;
-    const int i = m * nz1 + n;
-    double b = A.Q[i];
-    if (n == 1) b += az0[m] * phi[i - 1];
-    if (n == nz - 1) b += az0[m] * phi[i + 1];
-    if (m == nr - 1) b += ar0[m] * phi[i + nz1];
-    const double r = A.Q[i] - apply64(T, phi, m, i, nz1);
-    W.r[i] = r;
-    bb += b * b;
-    rr += r * r;
+  // ---- r = Q - A phi (Dirichlet values in phi), row sums of b.b and r.r ----
+  for (int j = wid; j < nrow; j += nw) {
+    const int m = m0 + j;
+    double bb = 0.0, rr = 0.0;
+    for (int n = 1 + lane; n <= nz - 1; n += 32) {
+      const int i = m * nz1 + n;
+      double b = A.Q[i];
+      if (n == 1) b += az0[m] * phi[i - 1];
+      if (n == nz - 1) b += az0[m] * phi[i + 1];
+      if (m == nr - 1) b += ar0[m] * phi[i + nz1];
+      const double r = A.Q[i] - apply64(T, phi, m, i, nz1);
+      W.r[i] = r;
+      bb += b * b;
+      rr += r * r;
+    }
+    bb = warp_sum64(bb);
+    rr = warp_sum64(rr);
+    if (lane == 0) {
+      rows[kBbSlot * nr + m] = bb;
+      rows[kRrSlot * nr + m] = rr;
+    }
   }
-  vals[0] = bb;
-  vals[1] = rr;
-  block_partials(W.partial, parity, 2, vals, lb, nb);
   if (!barrier_grid(W.bar, A.status, nb)) return;
-  read_partials(W.partial, parity, 2, vals, nb);
-  parity ^= 1;
-  bb = vals[0];
-  rr = vals[1];
+  double tot[4];
+  sum_rows(rows, nr, kRrSlot, 2, tot);   // slots kRrSlot, kBbSlot
+  double rr = tot[0];
+  const double bb = tot[1];
   const double tol2bb = A.tol * A.tol * bb;
   const double ref = bb > 0.0 ? bb : rr;
   const double scale = ref > 0.0 ? 1.0 / sqrt(ref / (double)nfree) : 1.0;
   const double unscale = 1.0 / (2.0 * kPi * kEps0 * scale);
 
-  int it = 0;
-  bool converged = rr <= tol2bb;
-  double rz = 0.0, alpha = 0.0;
-  bool first = true;
-  int restarts = 0;
-  while (!converged && it < A.max_iter) {
-    // ---- A: rows of f = scale r, transformed along z -----------------------
+  // f_hat of the own rows from W.r
+  auto forward_own = [&]() {
     for (int t = threadIdx.x; t < nrow * nk; t += blockDim.x) {
       const int j = t / nk, n = t - j * nk;
-      stage[t] = (float)(W.r[(m0 + j) * nz1 + 1 + n] * scale);
+      fs[t] = (float)(W.r[(m0 + j) * nz1 + 1 + n] * scale);
     }
     __syncthreads();
-    if (nrow > 0) sep_rows(W, nrow, W.sHat, m0, stage);
+    if (nrow > 0) {
+      float* hat = W.sHat + (size_t)m0 * nk;
+      sep_transform(W, fs, nrow, [&](int j, int k, float v) { hat[(size_t)j * nk + k] = v; });
+    }
+  };
+
+  int it = 0;
+  bool converged = rr <= tol2bb;
+  double rz_old = 0.0, alpha = 0.0, pq_old = 0.0;
+  bool first = true;
+  int restarts = 0;
+  if (!converged) {
+    forward_own();
     if (!barrier_grid(W.bar, A.status, nb)) return;
-    // ---- B: the tridiagonal system of every mode ---------------------------
-    sep_modes(W, lb, nb);
+  }
+  while (!converged && it < A.max_iter) {
+    // ---- 1. columns ---------------------------------------------------------
+    sep_columns(W, lb, nb, (float*)work);
     if (!barrier_grid(W.bar, A.status, nb)) return;
-    // ---- C: back to nodes; z, r.z and z.q_old ------------------------------
-    for (int t = threadIdx.x; t < nrow * nk; t += blockDim.x) stage[t] = W.sHat[(size_t)m0 * nk + t];
-    __syncthreads();
-    double rz_loc = 0.0, zq_loc = 0.0;
-    {
-      const int pairs = (nrow + 1) >> 1;
-      for (int t = threadIdx.x; t < pairs * nk; t += blockDim.x) {
-        const int jp = t / nk, n = t - jp * nk;
-        const int j0 = 2 * jp, j1 = j0 + 1 < nrow ? j0 + 1 : j0;
-        const float* a = stage + j0 * nk;
-        const float* b = stage + j1 * nk;
-        const float* Sn = W.sS + n;
-        float s0 = 0.0f, s1 = 0.0f;
-        int k = 0;
-        for (; k + 3 < nk; k += 4) {
-          const float c0 = Sn[(size_t)k * nk], c1 = Sn[(size_t)(k + 1) * nk];
-          const float c2 = Sn[(size_t)(k + 2) * nk], c3 = Sn[(size_t)(k + 3) * nk];
-          s0 = fmaf(c0, a[k], s0);
-          s1 = fmaf(c0, b[k], s1);
-          s0 = fmaf(c1, a[k + 1], s0);
-          s1 = fmaf(c1, b[k + 1], s1);
-          s0 = fmaf(c2, a[k + 2], s0);
-          s1 = fmaf(c2, b[k + 2], s1);
-          s0 = fmaf(c3, a[k + 3], s0);
-          s1 = fmaf(c3, b[k + 3], s1);
+    // ---- 2. rows: z (own rows and neighbours), A z, row sums ---------------
+    if (nrow > 0) {
+      const int ja = m0 > 0 ? 0 : 1;                          // first staged row (m0 - 1)
+      const int jb = m0 + nrow < nr ? nrow + 2 : nrow + 1;    // past the last (m0 + nrow)
+      for (int t = threadIdx.x; t < (jb - ja) * nk; t += blockDim.x) {
+        const int j = ja + t / nk, k = t - (t / nk) * nk;
+        fs[j * nk + k] = W.sHat[(size_t)(m0 - 1 + j) * nk + k];
+      }
+      __syncthreads();
+      // u rows: zs[j][n] = unscale sum_k S[n][k] u_hat[j][k] (S symmetric)
+      sep_transform(W, fs + ja * nk, jb - ja, [&](int j, int n, float v) {
+        zs[(size_t)(ja + j) * nk + n] = (double)v * unscale;
+      });
+      __syncthreads();
+      for (int j = wid; j < nrow; j += nw) {
+        const int m = m0 + j;
+        const double* zr = zs + (size_t)(j + 1) * nk;
+        double rz = 0.0, zq = 0.0, zaz = 0.0;
+        for (int n = lane; n < nk; n += 32) {
+          const int i = m * nz1 + 1 + n;
+          const double zi = zr[n];
+          const double zl = n > 0 ? zr[n - 1] : 0.0;
+          const double zu = n < nk - 1 ? zr[n + 1] : 0.0;
+          const double zo = m < nr - 1 ? zr[n + nk] : 0.0;
+          double a = az0[m] * (2.0 * zi - zl - zu) + ar0[m] * (zi - zo);
+          if (m > 0) a += ar0[m - 1] * (zi - zr[n - nk]);
+          azs[(size_t)j * nk + n] = a;
+          rz += W.r[i] * zi;
+          if (!first) zq += zi * W.q[i];
+          zaz += zi * a;
         }
-        for (; k < nk; ++k) {
-          const float c = Sn[(size_t)k * nk];
-          s0 = fmaf(c, a[k], s0);
-          s1 = fmaf(c, b[k], s1);
-        }
-        {
-          const int i = (m0 + j0) * nz1 + 1 + n;
-          const double zi = (double)s0 * unscale;
-          W.z[i] = zi;
-          rz_loc += W.r[i] * zi;
-          if (!first) zq_loc += zi * W.q[i];
-        }
-        if (j1 != j0) {
-          const int i = (m0 + j1) * nz1 + 1 + n;
-          const double zi = (double)s1 * unscale;
-          W.z[i] = zi;
-          rz_loc += W.r[i] * zi;
-          if (!first) zq_loc += zi * W.q[i];
+        rz = warp_sum64(rz);
+        zq = warp_sum64(zq);
+        zaz = warp_sum64(zaz);
+        if (lane == 0) {
+          rows[kRzSlot * nr + m] = rz;
+          rows[kZqSlot * nr + m] = zq;
+          rows[kZazSlot * nr + m] = zaz;
         }
       }
     }
-    vals[0] = rz_loc;
-    vals[1] = zq_loc;
-    block_partials(W.partial, parity, 2, vals, lb, nb);
     if (!barrier_grid(W.bar, A.status, nb)) return;
-    read_partials(W.partial, parity, 2, vals, nb);
-    parity ^= 1;
-    // ---- p = z + beta p, q = A z + beta q (flexible Polak-Ribiere beta) ---
-    const double beta = first ? 0.0 : -alpha * vals[1] / rz;
-    rz = vals[0];
+    // ---- 3. rows: coefficients, p, q, phi, r, next f_hat -------------------
+    sum_rows(rows, nr, kRzSlot, 3, tot);
+    const double rz = tot[0], zq = tot[1], zaz = tot[2];
+    // flexible (Polak-Ribiere) beta = -alpha z.q_old / r.z_old
+    const double beta = first ? 0.0 : -alpha * zq / rz_old;
+    const double pq = first ? zaz : zaz + 2.0 * beta * zq + beta * beta * pq_old;
+    alpha = pq != 0.0 ? rz / pq : 0.0;
+    rz_old = rz;
+    pq_old = pq;
+    for (int j = wid; j < nrow; j += nw) {
+      const int m = m0 + j;
+      double rl = 0.0;
+      for (int n = lane; n < nk; n += 32) {
+        const int i = m * nz1 + 1 + n;
+        const double pi = zs[(size_t)(j + 1) * nk + n] + (first ? 0.0 : beta * W.p[i]);
+        const double qi = azs[(size_t)j * nk + n] + (first ? 0.0 : beta * W.q[i]);
+        W.p[i] = pi;
+        W.q[i] = qi;
+        phi[i] += alpha * pi;
+        const double r = W.r[i] - alpha * qi;
+        W.r[i] = r;
+        rl += r * r;
+      }
+      rl = warp_sum64(rl);
+      if (lane == 0) rows[kRrSlot * nr + m] = rl;
+    }
     first = false;
-    double pq = 0.0;
-    for (int itm = gw; itm < items0; itm += ngw) {
-      int m, n;
-      if (!node_of(itm, m, n)) continue;
-      const int i = m * nz1 + n;
-      const double zi = W.z[i];
-      const double zl = n > 1 ? W.z[i - 1] : 0.0;
-      const double zu = n < nz - 1 ? W.z[i + 1] : 0.0;
-      const double zo = m < nr - 1 ? W.z[i + nz1] : 0.0;
-      double a = az0[m] * (2.0 * zi - zl - zu) + ar0[m] * (zi - zo);
-      if (m > 0) a += ar0[m - 1] * (zi - W.z[i - nz1]);
-      const double pi = zi + beta * W.p[i];
-      const double qi = a + beta * W.q[i];
-      W.p[i] = pi;
-      W.q[i] = qi;
-      pq += pi * qi;
-    }
-    vals[0] = pq;
-    block_partials(W.partial, parity, 1, vals, lb, nb);
+    __syncthreads();
+    forward_own();
     if (!barrier_grid(W.bar, A.status, nb)) return;
-    read_partials(W.partial, parity, 1, vals, nb);
-    parity ^= 1;
-    alpha = vals[0] != 0.0 ? rz / vals[0] : 0.0;
-    // ---- phi += alpha p, r -= alpha q --------------------------------------
-    double rl = 0.0;
-    for (int itm = gw; itm < items0; itm += ngw) {
-      int m, n;
-      if (!node_of(itm, m, n)) continue;
-      const int i = m * nz1 + n;
-      phi[i] += alpha * W.p[i];
-      const double r = W.r[i] - alpha * W.q[i];
-      W.r[i] = r;
-      rl += r * r;
-    }
-    vals[0] = rl;
-    block_partials(W.partial, parity, 1, vals, lb, nb);
-    if (!barrier_grid(W.bar, A.status, nb)) return;
-    read_partials(W.partial, parity, 1, vals, nb);
-    parity ^= 1;
-    rr = vals[0];
+    sum_rows(rows, nr, kRrSlot, 1, tot);
+    rr = tot[0];
     ++it;
     if (rr <= tol2bb) {
       // confirm with the true residual b - A phi (also the restart's input)
-      double rt = 0.0;
-      for (int itm = gw; itm < items0; itm += ngw) {
-        int m, n;
-        if (!node_of(itm, m, n)) continue;
-        const int i = m * nz1 + n;
-        const double r = A.Q[i] - apply64(T, phi, m, i, nz1);
-        W.r[i] = r;
-        rt += r * r;
+      for (int j = wid; j < nrow; j += nw) {
+        const int m = m0 + j;
+        double rt = 0.0;
+        for (int n = 1 + lane; n <= nz - 1; n += 32) {
+          const int i = m * nz1 + n;
+          const double r = A.Q[i] - apply64(T, phi, m, i, nz1);
+          W.r[i] = r;
+          rt += r * r;
+        }
+        rt = warp_sum64(rt);
+        if (lane == 0) rows[kRtSlot * nr + m] = rt;
       }
-      vals[0] = rt;
-      block_partials(W.partial, parity, 1, vals, lb, nb);
+      __syncthreads();
+      forward_own();
       if (!barrier_grid(W.bar, A.status, nb)) return;
-      read_partials(W.partial, parity, 1, vals, nb);
-      parity ^= 1;
-      rr = vals[0];
+      sum_rows(rows, nr, kRtSlot, 1, tot);
+      rr = tot[0];
       if (rr <= tol2bb || restarts >= 3) {
         converged = rr <= tol2bb;
         break;
@@ -1391,7 +1465,17 @@ PoissonWork* poisson_work_init(void* base, int nr, int nz, double R, double L, i
 // ---- sine-transform preconditioner ------------------------------------------
 constexpr int kSepMaxBlocks = 64;
 
-bool poisson_sep_possible(const PoissonWork* pw) { return !has_lines(*pw); }
+static int sep_smem(const PoissonWork& w);
+
+// every boundary node a conductor, and the column phase's staging of
+// kSepModes columns fits in shared memory
+bool poisson_sep_possible(const PoissonWork* pw) {
+  if (has_lines(*pw) || pw->nz < 3) return false;
+  PoissonWork w = *pw;
+  w.nk = w.nz - 1;
+  w.rows_per_block = 1;
+  return sep_smem(w) <= (int)kSmemBudget;
+}
 
 size_t poisson_sep_bytes(int nr, int nz) {
   const size_t nk = (size_t)(nz - 1);
@@ -1404,8 +1488,10 @@ static void sep_rows_per_block(PoissonWork& w, int blocks) {
 }
 
 static int sep_smem(const PoissonWork& w) {
-  return (int)(2 * (size_t)(w.nr + 1) * sizeof(double) +
-               (size_t)w.rows_per_block * (size_t)w.nk * sizeof(float));
+  const size_t R = (size_t)w.rows_per_block, nk = (size_t)w.nk;
+  const size_t rows = (R + 2) * nk * 8 + R * nk * 8 + (R + 2) * nk * 4;
+  const size_t cols = (3 * (size_t)w.nr * kSepModes + (size_t)w.nr) * 4;
+  return (int)(2 * (size_t)(w.nr + 1) * sizeof(double) + (rows > cols ? rows : cols));
 }
 
 cudaError_t poisson_sep_attach(PoissonWork* pw, void* base, cudaStream_t st) {
@@ -1515,28 +1601,39 @@ static bool group_sep(PoissonWork* const* pws, int n_inst) {
   return true;
 }
 
-// blocks per instance of the grouped sine-transform solve
-static int group_sep_bpi(PoissonWork* const* pws, int n_inst, int num_sms) {
-  int smem = 0, want = 1;
+// dynamic shared memory of the grouped sine-transform solve with bpi blocks
+// per instance
+static int group_sep_smem(PoissonWork* const* pws, int n_inst, int bpi) {
+  int smem = 0;
   for (int k = 0; k < n_inst; ++k) {
     PoissonWork w = *pws[k];
-    want = w.sep_blocks > want ? w.sep_blocks : want;
-    sep_rows_per_block(w, 1);
+    sep_rows_per_block(w, bpi);
     smem = sep_smem(w) > smem ? sep_smem(w) : smem;
   }
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_poisson_sep, kPoisThreads,
-                                                smem);
-  if (per_sm < 1) per_sm = 1;
-  int bpi = (num_sms * per_sm) / n_inst;
-  return bpi > want ? want : bpi;
+  return smem;
+}
+
+// blocks per instance of the grouped sine-transform solve: the most (up to
+// each instance's own count) for which every block of the launch is resident
+static int group_sep_bpi(PoissonWork* const* pws, int n_inst, int num_sms) {
+  int want = 1;
+  for (int k = 0; k < n_inst; ++k) want = pws[k]->sep_blocks > want ? pws[k]->sep_blocks : want;
+  for (int bpi = want; bpi >= 1; --bpi) {
+    const int smem = group_sep_smem(pws, n_inst, bpi);
+    if (smem > (int)kSmemBudget) return 0;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_poisson_sep,
+                                                  kPoisThreads, smem);
+    if ((long long)bpi * n_inst <= (long long)num_sms * per_sm) return bpi;
+  }
+  return 0;
 }
 
 cudaError_t poisson_group_upload(PoissonWork* const* pws, const Inst* insts, int n_inst,
                                  void* d_args, int num_sms, cudaStream_t st) {
   std::vector<PoissonArgs> host((size_t)n_inst);
-  const bool sep = group_sep(pws, n_inst);
-  const int bpi = sep ? group_sep_bpi(pws, n_inst, num_sms) : 0;
+  const int bpi = group_sep(pws, n_inst) ? group_sep_bpi(pws, n_inst, num_sms) : 0;
+  const bool sep = bpi > 0;   // else the multigrid kernel serves the group
   for (int k = 0; k < n_inst; ++k) {
     PoissonArgs& a = host[k];
     std::memset(&a, 0, sizeof(a));
@@ -1560,15 +1657,9 @@ cudaError_t poisson_group_upload(PoissonWork* const* pws, const Inst* insts, int
 cudaError_t launch_poisson_group(PoissonWork* const* pws, const Inst* insts, int n_inst,
                                  void* d_args, int num_sms, cudaStream_t st) {
   (void)insts;
-  if (group_sep(pws, n_inst)) {
-    int bpi = group_sep_bpi(pws, n_inst, num_sms);
-    if (bpi < 1) return cudaErrorInvalidConfiguration;
-    int smem = 0;
-    for (int k = 0; k < n_inst; ++k) {
-      PoissonWork w = *pws[k];
-      sep_rows_per_block(w, bpi);
-      smem = sep_smem(w) > smem ? sep_smem(w) : smem;
-    }
+  int bpi = group_sep(pws, n_inst) ? group_sep_bpi(pws, n_inst, num_sms) : 0;
+  if (bpi > 0) {
+    const int smem = group_sep_smem(pws, n_inst, bpi);
     PoissonArgs a0;
     std::memset(&a0, 0, sizeof(a0));
     const PoissonArgs* g = (const PoissonArgs*)d_args;
@@ -1587,7 +1678,7 @@ cudaError_t launch_poisson_group(PoissonWork* const* pws, const Inst* insts, int
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPoisThreads, smem);
   if (per_sm < 1) per_sm = 1;
-  int bpi = (num_sms * per_sm) / n_inst;
+  bpi = (num_sms * per_sm) / n_inst;
   if (bpi > want) bpi = want;
   if (bpi < 1) return cudaErrorInvalidConfiguration;
   PoissonArgs a0;

@@ -41,7 +41,7 @@ constexpr int kCollQ = 512;                      // deferred collision candidate
 //  bilinear coefficient form in the deposit's weights.
 // Field energy (diagnostic): 1/2 sum over edges of a_e (delta phi)^2.
 // ---------------------------------------------------------------------------
-__global__ void k_field_tables(Inst I) {
+__device__ __forceinline__ void k_field_tables_body(const Inst& I) {
   const Scalars* S = I.S;
   if (S->status & ST_FATAL) return;
   const int ncell = I.nr * I.nz;
@@ -133,6 +133,12 @@ __global__ void k_field_tables(Inst I) {
     }
   }
   if (diag) block_add(wloc, &I.S->W);
+}
+__global__ void k_field_tables(Inst I) { k_field_tables_body(I); }
+__global__ void k_field_tables_b(const Inst* insts) {
+  __shared__ Inst sI;
+  stage_inst(insts + blockIdx.z, &sI);
+  k_field_tables_body(sI);
 }
 
 // ---------------------------------------------------------------------------
@@ -579,7 +585,7 @@ __device__ __forceinline__ long long births_of(const Inst& I, int sp) {
   return nb < I.birth_cap ? nb : I.birth_cap;
 }
 
-__global__ void __launch_bounds__(1024) k_births_sort(Inst I) {
+__device__ __forceinline__ void k_births_sort_body(const Inst& I) {
   if (I.S->status & ST_FATAL) return;
   extern __shared__ __align__(16) unsigned char bsm[];
   unsigned long long* key = reinterpret_cast<unsigned long long*>(bsm);
@@ -605,9 +611,15 @@ __global__ void __launch_bounds__(1024) k_births_sort(Inst I) {
     __syncthreads();
   }
 }
+__global__ void __launch_bounds__(1024) k_births_sort(Inst I) { k_births_sort_body(I); }
+__global__ void __launch_bounds__(1024) k_births_sort_b(const Inst* insts) {
+  __shared__ Inst sI;
+  stage_inst(insts + blockIdx.z, &sI);
+  k_births_sort_body(sI);
+}
 
 template <bool F32>
-__global__ void k_births_rank(Inst I) {
+__device__ __forceinline__ void k_births_rank_body(const Inst& I) {
   const Scalars* S = I.S;
   if (S->status & ST_FATAL) return;
   const long long nb0 = births_of(I, 0), nb1 = births_of(I, 1);
@@ -641,11 +653,25 @@ __global__ void k_births_rank(Inst I) {
     }
   }
 }
+template <bool F32>
+__global__ void k_births_rank(Inst I) { k_births_rank_body<F32>(I); }
+template <bool F32>
+__global__ void k_births_rank_b(const Inst* insts) {
+  __shared__ Inst sI;
+  stage_inst(insts + blockIdx.z, &sI);
+  k_births_rank_body<F32>(sI);
+}
 
-__global__ void k_births_commit(Inst I) {
+__device__ __forceinline__ void k_births_commit_body(const Inst& I) {
   Scalars* S = I.S;
   if (threadIdx.x == 0 && !(S->status & ST_FATAL))
     S->next_id += births_of(I, 0) + births_of(I, 1);
+}
+__global__ void k_births_commit(Inst I) { k_births_commit_body(I); }
+__global__ void k_births_commit_b(const Inst* insts) {
+  __shared__ Inst sI;
+  stage_inst(insts + blockIdx.z, &sI);
+  k_births_commit_body(sI);
 }
 
 cudaError_t launch_births(const Inst& I, int num_sms, cudaStream_t st) {
@@ -669,7 +695,7 @@ cudaError_t launch_births(const Inst& I, int num_sms, cudaStream_t st) {
 // Exclusive scan of the cell histogram of one species -> cursors; clears the
 // histogram; n_next = total (checked against the capacity).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_scan(Inst I, int sp0) {
+__device__ __forceinline__ void k_scan_body(const Inst& I, int sp0) {
   Scalars* S = I.S;
   if (S->status & ST_FATAL) return;
   const int sp = sp0 + blockIdx.x;
@@ -730,13 +756,19 @@ __global__ void __launch_bounds__(1024) k_scan(Inst I, int sp0) {
     if (!I.prec32 && 4LL * vmax >= (1LL << (64 - kFixBits))) atomicOr(&S->status, ST_CAPACITY);
   }
 }
+__global__ void __launch_bounds__(1024) k_scan(Inst I, int sp0) { k_scan_body(I, sp0); }
+__global__ void __launch_bounds__(1024) k_scan_b(const Inst* insts, int sp0) {
+  __shared__ Inst sI;
+  stage_inst(insts + blockIdx.z, &sI);
+  k_scan_body(sI, sp0);
+}
 
 // ---------------------------------------------------------------------------
 // Counting-sort scatter cur -> nxt of the surviving particles and the
 // births (blockIdx.y = species).  per_step: on a step without the full sort
 // (sort_this_step) the births are appended to the current arrays instead.
 // ---------------------------------------------------------------------------
-__global__ void k_scatter(Inst I, int sp0, int per_step) {
+__device__ __forceinline__ void k_scatter_body(const Inst& I, int sp0, int per_step) {
   Scalars* S = I.S;
   if (S->status & ST_FATAL) return;
   const int sp = sp0 + blockIdx.y;
@@ -775,10 +807,16 @@ __global__ void k_scatter(Inst I, int sp0, int per_step) {
     }
   }
 }
+__global__ void k_scatter(Inst I, int sp0, int per_step) { k_scatter_body(I, sp0, per_step); }
+__global__ void k_scatter_b(const Inst* insts, int sp0, int per_step) {
+  __shared__ Inst sI;
+  stage_inst(insts + blockIdx.z, &sI);
+  k_scatter_body(sI, sp0, per_step);
+}
 
 // On a step without the full sort the births go to the end of the current
 // arrays (blockIdx.y = species); sort_this_step checked that they fit.
-__global__ void k_append(Inst I) {
+__device__ __forceinline__ void k_append_body(const Inst& I) {
   const Scalars* S = I.S;
   if ((S->status & ST_FATAL) || sort_this_step(I, S)) return;
   const int sp = blockIdx.y;
@@ -793,6 +831,12 @@ __global__ void k_append(Inst I) {
     P.vr[j] = B.vr[b]; P.vt[j] = B.vt[b]; P.vz[j] = B.vz[b];
     P.id[j] = B.id[b];
   }
+}
+__global__ void k_append(Inst I) { k_append_body(I); }
+__global__ void k_append_b(const Inst* insts) {
+  __shared__ Inst sI;
+  stage_inst(insts + blockIdx.z, &sI);
+  k_append_body(sI);
 }
 
 // keys + histogram of particles loaded by pic_set_particles; range check.
@@ -1089,7 +1133,7 @@ __global__ void k_deposit_all(Inst I, int sp) {
 // Node charges Q from the deposit sums (zeroed for the next step); with `step`
 // and phi_extrap the unknown nodes of phi also move to the start of this
 // step's solve, 2 phi^{n-1} - phi^{n-2}, and phi_old to phi^{n-1}.
-__global__ void k_charge(Inst I, bool step) {
+__device__ __forceinline__ void k_charge_body(const Inst& I, bool step) {
   Scalars* S = I.S;
   const int nn = (I.nr + 1) * (I.nz + 1);
   const bool extrap = step && I.phi_extrap;
@@ -1153,13 +1197,19 @@ __global__ void k_charge(Inst I, bool step) {
     }
   }
 }
+__global__ void k_charge(Inst I, bool step) { k_charge_body(I, step); }
+__global__ void k_charge_b(const Inst* insts, bool step) {
+  __shared__ Inst sI;
+  stage_inst(insts + blockIdx.z, &sI);
+  k_charge_body(sI, step);
+}
 
 // ---------------------------------------------------------------------------
 // External circuit (Sections 3, 4, 6): cathode charge of the step, running
 // mean current over n_avg steps, V_c = -V_s + I R_ext clamped to [-V_s, 0];
 // writes the cathode nodes' Dirichlet value into phi.
 // ---------------------------------------------------------------------------
-__global__ void k_circuit(Inst I) {
+__device__ __forceinline__ void k_circuit_body(const Inst& I) {
   Scalars* S = I.S;
   if (S->status & ST_FATAL) return;
   if (threadIdx.x == 0) {
@@ -1185,6 +1235,12 @@ __global__ void k_circuit(Inst I) {
   const double V = S->Vc;
   for (int m = threadIdx.x; m <= I.m_cath; m += blockDim.x) I.phi[m * (I.nz + 1)] = V;
 }
+__global__ void k_circuit(Inst I) { k_circuit_body(I); }
+__global__ void k_circuit_b(const Inst* insts) {
+  __shared__ Inst sI;
+  stage_inst(insts + blockIdx.z, &sI);
+  k_circuit_body(sI);
+}
 
 __global__ void k_set_cathode(Inst I) {
   const double V = I.S->Vc;
@@ -1192,7 +1248,7 @@ __global__ void k_set_cathode(Inst I) {
 }
 
 // diagnostics record, counters for the next step, step index
-__global__ void k_step_end(Inst I) {
+__device__ __forceinline__ void k_step_end_body(const Inst& I) {
   Scalars* S = I.S;
   if (threadIdx.x != 0) return;
   const long long nb0 = S->nbirth[0] < I.birth_cap ? S->nbirth[0] : I.birth_cap;
@@ -1250,6 +1306,25 @@ __global__ void k_step_end(Inst I) {
   S->W = 0.0;
   S->peak_bits[0] = S->peak_bits[1] = 0ULL;
   S->diag_on = (S->step % (I.diag_every > 0 ? I.diag_every : 1)) == 0;
+}
+__global__ void k_step_end(Inst I) { k_step_end_body(I); }
+__global__ void k_step_end_b(const Inst* insts) {
+  __shared__ Inst sI;
+  stage_inst(insts + blockIdx.z, &sI);
+  k_step_end_body(sI);
+}
+
+// live particles of all instances (the autotuner's view of the work)
+__global__ void k_live_total(const Inst* insts, int n_inst, long long* out) {
+  if (threadIdx.x != 0) return;
+  long long t = 0;
+  for (int k = 0; k < n_inst; ++k) t += insts[k].S->n_live[0] + insts[k].S->n_live[1];
+  *out = t;
+}
+
+cudaError_t launch_live_total(const Inst* d_insts, int n_inst, long long* out, cudaStream_t st) {
+  k_live_total<<<1, 32, 0, st>>>(d_insts, n_inst, out);
+  return cudaGetLastError();
 }
 
 // Fill the push queue: chunks of `chunk` particles per instance and species
@@ -1478,6 +1553,48 @@ cudaError_t launch_post_push(const Inst& I, int num_sms, cudaStream_t st) {
   cudaError_t e = launch_charge(I, true, st);
   if (e != cudaSuccess) return e;
   k_circuit<<<1, 256, 0, st>>>(I);
+  return cudaGetLastError();
+}
+
+// ---- batched launches of the per-instance kernels of an ensemble ----------
+// gridDim.z = instances (the kernels take the instance from blockIdx.z); the
+// x extent covers the largest instance, and the grid-stride loops of the
+// per-instance kernels make any extent correct.
+cudaError_t launch_field_tables_batch(const Inst* d_insts, int n_inst, const BatchDims& bd,
+                                      int num_sms, cudaStream_t st) {
+  const int g = grid_for(bd.cells_max, 256, num_sms, 8 / n_inst > 0 ? 8 / n_inst : 1);
+  k_field_tables_b<<<dim3(g, 1, n_inst), 256, 0, st>>>(d_insts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_post_push_batch(const Inst* d_insts, int n_inst, const BatchDims& bd,
+                                   int num_sms, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_births_sort_b, cudaFuncAttributeMaxDynamicSharedMemorySize, kBirthSmem);
+    attr = true;
+  }
+  const int per = num_sms / n_inst > 0 ? num_sms / n_inst : 1;   // blocks of one instance per SM-share
+  const int chunks = (int)((bd.birth_cap_max + kBirthChunk - 1) / kBirthChunk);
+  k_births_sort_b<<<dim3(chunks > 0 ? chunks : 1, 1, n_inst), 1024, kBirthSmem, st>>>(d_insts);
+  const int rank_blocks = grid_for(2 * bd.birth_cap_max, 256, per, 4);
+  if (bd.prec32) k_births_rank_b<true><<<dim3(rank_blocks, 1, n_inst), 256, 0, st>>>(d_insts);
+  else k_births_rank_b<false><<<dim3(rank_blocks, 1, n_inst), 256, 0, st>>>(d_insts);
+  k_births_commit_b<<<dim3(1, 1, n_inst), 32, 0, st>>>(d_insts);
+  k_scan_b<<<dim3(2, 1, n_inst), 1024, 0, st>>>(d_insts, 0);
+  if (bd.prec32) launch_scatter32_batch(d_insts, n_inst, per * 8, st);
+  else k_scatter_b<<<dim3(per * 8, 2, n_inst), 256, 0, st>>>(d_insts, 0, 1);
+  if (bd.any_append) {
+    if (bd.prec32) launch_append32_batch(d_insts, n_inst, per, st);
+    else k_append_b<<<dim3(per, 2, n_inst), 256, 0, st>>>(d_insts);
+  }
+  k_charge_b<<<dim3(grid_for(bd.nodes_max, 256, 1024, 1), 1, n_inst), 256, 0, st>>>(d_insts, true);
+  k_circuit_b<<<dim3(1, 1, n_inst), 256, 0, st>>>(d_insts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_end_batch(const Inst* d_insts, int n_inst, cudaStream_t st) {
+  k_step_end_b<<<dim3(1, 1, n_inst), 32, 0, st>>>(d_insts);
   return cudaGetLastError();
 }
 

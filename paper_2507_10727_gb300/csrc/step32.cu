@@ -288,6 +288,7 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
     int acc_key = -1, acc_m = 0, acc_n = 0, acc_cnt = 0;
     float s00 = 0.0f, s10 = 0.0f, s01 = 0.0f, s11 = 0.0f;
     unsigned over = 0u;   // candidates that found the queue full, bit j (ppt <= 32)
+    float k2 = 0.0f;
 #pragma unroll 1
     for (int j = 0; j < ppt; ++j, i += 32) {
       const float4 a = a_nx;
@@ -355,9 +356,10 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
           vz = vzn;
           zeta = dz + vzn * kz;
         }
-        if (diag)
-          Kloc += 0.5 * I.mass[SP] * I.weight * 0.5 *
-                  ((double)v2old + (double)(vr * vr + vt * vt + vz * vz));
+        // kinetic energy: |v|^2 before and after summed in FP32 over this
+        // thread's particles of the chunk (at most 32), the FP64 sum is the
+        // block's and the step's
+        if (diag) k2 += v2old + (vr * vr + vt * vt + vz * vz);
         bool alive = true;
         int m1, n1;
         float dr1, dz1;
@@ -423,6 +425,7 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
     if (acc_key >= 0)
       deposit_run32<SP>(I, acc_key, acc_m, acc_n, s00, s10, s01, s11, acc_cnt, pm0, pn0, patch,
                         cpatch);
+    if (diag) Kloc = 0.25 * I.mass[SP] * I.weight * (double)k2;
     __syncthreads();
     if (SP == 0) {
       // the queued collisions (Section 3), on the state written above
@@ -505,7 +508,7 @@ __global__ void __launch_bounds__(kPush32Threads, 4) k_push32_all(const Inst* in
   }
 }
 
-__global__ void k_scatter32(Inst I, int sp0, int per_step) {
+__device__ __forceinline__ void k_scatter32_body(const Inst& I, int sp0, int per_step) {
   Scalars* S = I.S;
   if (S->status & ST_FATAL) return;
   const int sp = sp0 + blockIdx.y;
@@ -547,6 +550,12 @@ __global__ void k_scatter32(Inst I, int sp0, int per_step) {
       dst.b[pos] = b;
     }
   }
+}
+__global__ void k_scatter32(Inst I, int sp0, int per_step) { k_scatter32_body(I, sp0, per_step); }
+__global__ void k_scatter32_b(const Inst* insts, int sp0, int per_step) {
+  __shared__ Inst sI;
+  stage_inst(insts + blockIdx.z, &sI);
+  k_scatter32_body(sI, sp0, per_step);
 }
 
 // FP64 SoA (r, z, v, id) -> FP32 records at [offset, offset + count) of cur32,
@@ -726,7 +735,7 @@ cudaError_t launch_push32_all(const Inst* d_insts, WorkQueue* q, int gather, int
 }
 
 // births appended to the current records on a step without the full sort
-__global__ void k_append32(Inst I) {
+__device__ __forceinline__ void k_append32_body(const Inst& I) {
   const Scalars* S = I.S;
   if ((S->status & ST_FATAL) || sort_this_step(I, S)) return;
   const int sp = blockIdx.y;
@@ -740,9 +749,25 @@ __global__ void k_append32(Inst I) {
     P.b[n_old + b] = B.b32[b];
   }
 }
+__global__ void k_append32(Inst I) { k_append32_body(I); }
+__global__ void k_append32_b(const Inst* insts) {
+  __shared__ Inst sI;
+  stage_inst(insts + blockIdx.z, &sI);
+  k_append32_body(sI);
+}
 
 cudaError_t launch_append32(const Inst& I, int num_sms, cudaStream_t st) {
   k_append32<<<dim3(num_sms, 2), 256, 0, st>>>(I);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter32_batch(const Inst* d_insts, int n_inst, int blocks, cudaStream_t st) {
+  k_scatter32_b<<<dim3(blocks, 2, n_inst), 256, 0, st>>>(d_insts, 0, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_append32_batch(const Inst* d_insts, int n_inst, int blocks, cudaStream_t st) {
+  k_append32_b<<<dim3(blocks, 2, n_inst), 256, 0, st>>>(d_insts);
   return cudaGetLastError();
 }
 

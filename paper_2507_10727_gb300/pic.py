@@ -148,6 +148,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         L.pic_uses_graph.argtypes = [vp]
         L.pic_tuned_chunk.argtypes = [vp, C.POINTER(C.c_int)]
         L.pic_set_chunk.argtypes = [vp, C.c_int]
+        L.pic_autotune_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _I64]
         L.pic_get_species_charge.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int]
         L.pic_sync.argtypes = [vp]
         L.pic_diagnostics.argtypes = [vp, C.c_int, C.POINTER(PicDiag)]
@@ -366,6 +367,12 @@ def pic_tuned_chunk(h: Handle) -> int:
 
 def pic_set_chunk(h: Handle, particles_per_thread: int):
     _check(h, load_library().pic_set_chunk(h.ptr, particles_per_thread))
+
+
+def pic_autotune_info(h: Handle) -> dict:
+    t, ppt, n = C.c_int(), C.c_int(), C.c_int64()
+    _check(h, load_library().pic_autotune_info(h.ptr, C.byref(t), C.byref(ppt), C.byref(n)))
+    return {"tunings": t.value, "particles_per_thread": ppt.value, "particles_at_tuning": n.value}
 
 
 def pic_sync(h: Handle):

@@ -222,3 +222,56 @@ def test_periodic_sort_ensemble_equals_individual_runs(pg):
             pg.pic_destroy(one)
         pg.pic_destroy(ens)
     side.synchronize()
+
+
+def test_autotuner_retunes_when_the_counts_grow(pg):
+    """The push's chunk size is tuned again when the live particle count has
+    changed by a factor of 4 since the last tuning (an ensemble whose
+    discharges grow); the tuning steps and the recaptured graph leave the
+    results as they are: the ensemble still equals the instances run one by
+    one, bit for bit."""
+    import torch
+    insts = []
+    for k, (p, parts) in enumerate(_instances()):
+        p = pic_inputs.with_capacity(p, parts, factor=16.0)
+        insts.append((p, parts))
+    grown = []
+    for k, (p, _) in enumerate(insts):
+        _, big = busy_state(dict(p), ppc=6 * (k + 4), seed=500 + k)
+        grown.append(big)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        runs = [pg.pic_create([p for p, _ in insts])] + [pg.pic_create(p) for p, _ in insts]
+        for k, (p, parts) in enumerate(insts):
+            for h, j in ((runs[0], k), (runs[k + 1], 0)):
+                _load(pg, h, j, parts)
+                pg.pic_solve_fields(h, j)
+        for h in runs:
+            pg.pic_step(h, 6)
+        info0 = pg.pic_autotune_info(runs[0])
+        assert info0["tunings"] == 1
+        for k in range(len(insts)):
+            for h, j in ((runs[0], k), (runs[k + 1], 0)):
+                _load(pg, h, j, grown[k])
+                pg.pic_solve_fields(h, j)
+        for h in runs:
+            pg.pic_step(h, 1)      # its end copies the grown count to the host
+            pg.pic_sync(h)         # (the next call reads it once the copy is done)
+            pg.pic_step(h, 6)      # sees it: four tuning steps, then the new graph
+        info1 = pg.pic_autotune_info(runs[0])
+        print("tunings", info0, info1)
+        assert info1["tunings"] == 2
+        assert info1["particles_at_tuning"] >= 4 * info0["particles_at_tuning"]
+        assert info1["particles_per_thread"] in (4, 8, 16, 32)
+        pg.pic_step(runs[0], 3)
+        assert pg.pic_uses_graph(runs[0])
+        for k in range(len(insts)):
+            pg.pic_step(runs[k + 1], 3)
+            for sp in (0, 1):
+                a = sort_by_id(pg.pic_get_particles(runs[0], k, sp))
+                b = sort_by_id(pg.pic_get_particles(runs[k + 1], 0, sp))
+                for q in a:
+                    assert np.array_equal(a[q], b[q]), (k, sp, q)
+        for h in runs:
+            pg.pic_destroy(h)
+    side.synchronize()
