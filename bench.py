@@ -44,8 +44,11 @@ UNIT = "particle-steps/s"
 # the derivation is listed with the design notes.
 # kernels of one step of one discharge: field tables, queue set-up, push,
 # births (sort, rank, commit), scan, scatter, charge, circuit, Poisson, step end,
-# and the births append when full sorts are periodic
+# and the births append when full sorts are periodic; plus, once per pic_step
+# call, the live-count kernel of the push's re-tuning check.  An ensemble step
+# launches the same kernels once each over all its discharges.
 KERNELS_PER_STEP = 12
+KERNELS_PER_CALL = 1
 # full cell sort period of the default runs (256 x 256, 4e7 per species,
 # measured over 128 timed steps: FP64 7.84e9 / 7.92e9 / 7.95e9 particle-steps/s
 # at 16 / 32 / 64; FP32 2.85e10 / 2.99e10 / 3.13e10 at 8 / 16 / 32)
@@ -938,7 +941,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if args.precision == "fp64" else "f32",
                 "data": "synthetic", "config": config_block(p, n, args),
-                "gpu_launches": args.steps * (KERNELS_PER_STEP + (1 if args.sort_every > 1 else 0)),
+                "gpu_launches": args.steps * (KERNELS_PER_STEP + (1 if args.sort_every > 1 else 0))
+                                + KERNELS_PER_CALL,
                 "cuda_graph": graph,
                 "autotune_steps": AUTOTUNE_STEPS, "push_particles_per_thread": tuned,
                 "poisson": {"iters_last_step": rec["d1"]["poisson_iters"],

@@ -78,6 +78,9 @@ cudaError_t launch_push_all(const Inst* d_insts, WorkQueue* q, int prec32, int g
                             int num_sms, cudaStream_t st);
 cudaError_t launch_push32_all(const Inst* d_insts, WorkQueue* q, int gather, int ppt, int num_sms,
                               cudaStream_t st);
+// the push of a single-instance handle (the instance a kernel argument)
+cudaError_t launch_push_one(const Inst& I, WorkQueue* q, int ppt, int num_sms, cudaStream_t st);
+cudaError_t launch_push32_one(const Inst& I, WorkQueue* q, int ppt, int num_sms, cudaStream_t st);
 cudaError_t launch_post_push(const Inst& I, int num_sms, cudaStream_t st);
 // the per-instance kernels of an ensemble step as one launch each over all
 // instances (gridDim.z = instances); extents from the largest instance

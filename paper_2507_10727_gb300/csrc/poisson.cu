@@ -73,7 +73,8 @@ struct PoissonWork {
   int nk;                  // modes: nz - 1
   int rows_per_block;      // rows of one block in the row-wise phases
   int sep_blocks;          // blocks of one solve
-  float* sS;               // nk x nk orthonormal DST-I matrix (symmetric)
+  float* sTab;             // 2 nz values sqrt(2/nz) sin(pi a / nz): the orthonormal DST-I
+                           // matrix is S[k][n] = sTab[(k+1)(n+1) mod 2nz] (symmetric)
   float* sW;               // nr x nk: 1 / pivot of the Thomas elimination of mode k at row m
   float* sC;               // nr x nk: its upper factor
   float* sE;               // nr: coupling a_r(m) / (2 pi eps0) between rows m and m + 1
@@ -865,9 +866,9 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
 // ----------------------------------------------------------------------------
 // Flexible PCG with the sine-transform preconditioner (all boundary nodes
 // conductors).  z = M^{-1} r:
-//   rows:    f_hat[m][k] = sum_n S[k][n] f[m][n],  f = scale r (FP32)
+//   rows:    f_hat[m][k] = sum_n S[k][n] r[m][n]  (FP32)
 //   columns: (lambda_k D + L) u_hat[:, k] = f_hat[:, k], Thomas in m
-//   rows:    u[m][n] = sum_k S[n][k] u_hat[m][k];  z = u unscale (FP64)
+//   rows:    u[m][n] = sum_k S[n][k] u_hat[m][k];  z = u / (2 pi eps0) (FP64)
 // lambda_k = 4 sin^2(pi (k+1) / (2 nz)).  The FP32 transform makes M^{-1} A
 // the identity to about 1e-6, so the outer FP64 iteration ends after two or
 // three iterations.
@@ -881,6 +882,9 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
 //   3. rows: the coefficients from the row sums, p = z + beta p,
 //      q = A z + beta q, phi += alpha p, r -= alpha q, the row sums of r.r,
 //      and the next f_hat of the own rows.
+// The first f_hat is computed with the initial residual, before the first
+// barrier; the true-residual check at convergence transforms again only when
+// the iteration restarts.
 // p.q comes from the identity (z + beta p).A(z + beta p) = z.Az + 2 beta z.q +
 // beta^2 p.q (A symmetric, q = A p).  Every dot product is summed per row by
 // one warp (lanes over n, then a fixed shuffle tree) and over the rows in
@@ -908,36 +912,30 @@ __device__ __forceinline__ void sum_rows(const double* rows, int nr, int slot0, 
 }
 
 // out(j, k, sum_n S[k][n] in[j][n]) for the block's rows j < nrow (in: FP32
-// rows of nk values in shared memory); a thread takes a pair of rows at one
-// k, so each element of S (read through L1 / L2, coalesced over k) serves
-// two rows; eight independent loads of S are in flight per thread.
+// rows of nk values in shared memory).  S[k][n] = tab[(k+1)(n+1) mod 2 nz]
+// with tab[a] = sqrt(2/nz) sin(pi a / nz) in shared memory, the index
+// advanced by k + 1 per n; a thread takes a pair of rows at one k, so each
+// table value serves two rows.
 template <typename Out>
-__device__ __forceinline__ void sep_transform(const PoissonWork& W, const float* in, int nrow,
-                                              Out out) {
-  const int nk = W.nk;
+__device__ __forceinline__ void sep_transform(const PoissonWork& W, const float* tab, const float* in,
+                                              int nrow, Out out) {
+  const int nk = W.nk, per = 2 * W.nz;
   const int pairs = (nrow + 1) >> 1;
   for (int t = threadIdx.x; t < pairs * nk; t += blockDim.x) {
     const int jp = t / nk, k = t - jp * nk;
     const int j0 = 2 * jp, j1 = j0 + 1 < nrow ? j0 + 1 : j0;
     const float* a = in + j0 * nk;
     const float* b = in + j1 * nk;
-    const float* Sk = W.sS + k;   // S[n][k] = S[k][n]
+    const int step = (k + 1) % per;
+    int idx = step;                         // (k + 1)(n + 1) mod 2 nz at n = 0
     float s0 = 0.0f, s1 = 0.0f;
-    int n = 0;
-    for (; n + 7 < nk; n += 8) {
-      float c[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) c[u] = __ldg(Sk + (size_t)(n + u) * nk);
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        s0 = fmaf(c[u], a[n + u], s0);
-        s1 = fmaf(c[u], b[n + u], s1);
-      }
-    }
-    for (; n < nk; ++n) {
-      const float c = __ldg(Sk + (size_t)n * nk);
+#pragma unroll 4
+    for (int n = 0; n < nk; ++n) {
+      const float c = tab[idx];
       s0 = fmaf(c, a[n], s0);
       s1 = fmaf(c, b[n], s1);
+      idx += step;
+      if (idx >= per) idx -= per;
     }
     out(j0, k, s0);
     if (j1 != j0) out(j1, k, s1);
@@ -1051,8 +1049,10 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson_sep(PoissonArgs A0,
   double* rows = W.partial;     // kSepSlots x nr row sums
   double* az0 = (double*)smem;
   double* ar0 = az0 + (nr + 1);
-  unsigned char* work = (unsigned char*)(ar0 + (nr + 1));
+  float* tab = (float*)(ar0 + (nr + 1));          // 2 nz sine values
+  unsigned char* work = (unsigned char*)(tab + 2 * nz);
   for (int m = threadIdx.x; m <= nr; m += blockDim.x) fine_coef(W, m, az0[m], ar0[m]);
+  for (int a = threadIdx.x; a < 2 * nz; a += blockDim.x) tab[a] = W.sTab[a];
   __syncthreads();
   const Tables T{az0, ar0, nullptr, nullptr, nullptr};
   const int R = W.rows_per_block;
@@ -1065,7 +1065,24 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson_sep(PoissonArgs A0,
   double* azs = zs + (size_t)(R + 2) * nk;
   float* fs = (float*)(azs + (size_t)R * nk);
 
-  // ---- r = Q - A phi (Dirichlet values in phi), row sums of b.b and r.r ----
+  // f_hat of the own rows from W.r.  The transform solve is linear and its
+  // values (charges of 1e-20 .. 1e-8 C over couplings of ~1e-4 m) sit many
+  // decades inside FP32's normal range, so r enters unscaled
+  const double unscale = 1.0 / (2.0 * kPi * kEps0);
+  auto forward_own = [&]() {
+    for (int t = threadIdx.x; t < nrow * nk; t += blockDim.x) {
+      const int j = t / nk, n = t - j * nk;
+      fs[t] = (float)W.r[(m0 + j) * nz1 + 1 + n];
+    }
+    __syncthreads();
+    if (nrow > 0) {
+      float* hat = W.sHat + (size_t)m0 * nk;
+      sep_transform(W, tab, fs, nrow, [&](int j, int k, float v) { hat[(size_t)j * nk + k] = v; });
+    }
+  };
+
+  // ---- r = Q - A phi (Dirichlet values in phi), row sums of b.b and r.r,
+  //      and the first f_hat ------------------------------------------------
   for (int j = wid; j < nrow; j += nw) {
     const int m = m0 + j;
     double bb = 0.0, rr = 0.0;
@@ -1087,38 +1104,20 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson_sep(PoissonArgs A0,
       rows[kRrSlot * nr + m] = rr;
     }
   }
+  __syncthreads();
+  forward_own();
   if (!barrier_grid(W.bar, A.status, nb)) return;
   double tot[4];
   sum_rows(rows, nr, kRrSlot, 2, tot);   // slots kRrSlot, kBbSlot
   double rr = tot[0];
   const double bb = tot[1];
   const double tol2bb = A.tol * A.tol * bb;
-  const double ref = bb > 0.0 ? bb : rr;
-  const double scale = ref > 0.0 ? 1.0 / sqrt(ref / (double)nfree) : 1.0;
-  const double unscale = 1.0 / (2.0 * kPi * kEps0 * scale);
-
-  // f_hat of the own rows from W.r
-  auto forward_own = [&]() {
-    for (int t = threadIdx.x; t < nrow * nk; t += blockDim.x) {
-      const int j = t / nk, n = t - j * nk;
-      fs[t] = (float)(W.r[(m0 + j) * nz1 + 1 + n] * scale);
-    }
-    __syncthreads();
-    if (nrow > 0) {
-      float* hat = W.sHat + (size_t)m0 * nk;
-      sep_transform(W, fs, nrow, [&](int j, int k, float v) { hat[(size_t)j * nk + k] = v; });
-    }
-  };
 
   int it = 0;
   bool converged = rr <= tol2bb;
   double rz_old = 0.0, alpha = 0.0, pq_old = 0.0;
   bool first = true;
   int restarts = 0;
-  if (!converged) {
-    forward_own();
-    if (!barrier_grid(W.bar, A.status, nb)) return;
-  }
   while (!converged && it < A.max_iter) {
     // ---- 1. columns ---------------------------------------------------------
     sep_columns(W, lb, nb, (float*)work);
@@ -1133,7 +1132,7 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson_sep(PoissonArgs A0,
       }
       __syncthreads();
       // u rows: zs[j][n] = unscale sum_k S[n][k] u_hat[j][k] (S symmetric)
-      sep_transform(W, fs + ja * nk, jb - ja, [&](int j, int n, float v) {
+      sep_transform(W, tab, fs + ja * nk, jb - ja, [&](int j, int n, float v) {
         zs[(size_t)(ja + j) * nk + n] = (double)v * unscale;
       });
       __syncthreads();
@@ -1212,8 +1211,6 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson_sep(PoissonArgs A0,
         rt = warp_sum64(rt);
         if (lane == 0) rows[kRtSlot * nr + m] = rt;
       }
-      __syncthreads();
-      forward_own();
       if (!barrier_grid(W.bar, A.status, nb)) return;
       sum_rows(rows, nr, kRtSlot, 1, tot);
       rr = tot[0];
@@ -1223,6 +1220,8 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson_sep(PoissonArgs A0,
       }
       ++restarts;
       first = true;  // restart the Krylov space from the true residual
+      forward_own();
+      if (!barrier_grid(W.bar, A.status, nb)) return;
     }
   }
   if (lb == 0 && threadIdx.x == 0) {
@@ -1479,7 +1478,8 @@ bool poisson_sep_possible(const PoissonWork* pw) {
 
 size_t poisson_sep_bytes(int nr, int nz) {
   const size_t nk = (size_t)(nz - 1);
-  return round256(nk * nk * 4) + 3 * round256((size_t)nr * nk * 4) + round256((size_t)nr * 4);
+  return round256((size_t)2 * nz * 4) + 3 * round256((size_t)nr * nk * 4) +
+         round256((size_t)nr * 4);
 }
 
 static void sep_rows_per_block(PoissonWork& w, int blocks) {
@@ -1491,7 +1491,8 @@ static int sep_smem(const PoissonWork& w) {
   const size_t R = (size_t)w.rows_per_block, nk = (size_t)w.nk;
   const size_t rows = (R + 2) * nk * 8 + R * nk * 8 + (R + 2) * nk * 4;
   const size_t cols = (3 * (size_t)w.nr * kSepModes + (size_t)w.nr) * 4;
-  return (int)(2 * (size_t)(w.nr + 1) * sizeof(double) + (rows > cols ? rows : cols));
+  return (int)(2 * (size_t)(w.nr + 1) * sizeof(double) + 2 * (size_t)w.nz * sizeof(float) +
+               (rows > cols ? rows : cols));
 }
 
 cudaError_t poisson_sep_attach(PoissonWork* pw, void* base, cudaStream_t st) {
@@ -1504,20 +1505,16 @@ cudaError_t poisson_sep_attach(PoissonWork* pw, void* base, cudaStream_t st) {
     p += round256(b);
     return (float*)q;
   };
-  w.sS = take((size_t)nk * nk * 4);
+  w.sTab = take((size_t)2 * w.nz * 4);
   w.sW = take((size_t)nr * nk * 4);
   w.sC = take((size_t)nr * nk * 4);
   w.sHat = take((size_t)nr * nk * 4);
   w.sE = take((size_t)nr * 4);
   // tables in FP64 on the host, stored in FP32; couplings scaled by
   // 1 / (2 pi eps0) like the multigrid tables
-  std::vector<float> S((size_t)nk * nk), Wt((size_t)nr * nk), Ct((size_t)nr * nk), E(nr);
+  std::vector<float> S((size_t)2 * w.nz), Wt((size_t)nr * nk), Ct((size_t)nr * nk), E(nr);
   const double norm = std::sqrt(2.0 / w.nz);
-  for (int k = 0; k < nk; ++k)
-    for (int n = 0; n < nk; ++n) {
-      const long long a = ((long long)(k + 1) * (n + 1)) % (2LL * w.nz);
-      S[(size_t)k * nk + n] = (float)(norm * std::sin(kPi * (double)a / w.nz));
-    }
+  for (int a = 0; a < 2 * w.nz; ++a) S[a] = (float)(norm * std::sin(kPi * (double)a / w.nz));
   std::vector<double> az(nr), ar(nr);
   for (int m = 0; m < nr; ++m) {
     az[m] = m == 0 ? w.dr * w.dr / (8.0 * w.dz) : m * w.dr * w.dr / w.dz;
@@ -1537,7 +1534,7 @@ cudaError_t poisson_sep_attach(PoissonWork* pw, void* base, cudaStream_t st) {
       cprev = cm;
     }
   }
-  cudaError_t e = cudaMemcpyAsync(w.sS, S.data(), S.size() * 4, cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaMemcpyAsync(w.sTab, S.data(), S.size() * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(w.sW, Wt.data(), Wt.size() * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(w.sC, Ct.data(), Ct.size() * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(w.sE, E.data(), E.size() * 4, cudaMemcpyHostToDevice, st);
@@ -1559,7 +1556,7 @@ void poisson_work_free(PoissonWork* pw) { delete pw; }
 
 cudaError_t launch_poisson(PoissonWork* pw, const double* Q, double* phi, double tol, int max_iter,
                            int* status_dev, int* iters_dev, double* resid_dev, cudaStream_t st) {
-  if (pw->sS) {
+  if (pw->sTab) {
     PoissonArgs a;
     a.W = *pw;
     a.Q = Q;
@@ -1597,7 +1594,7 @@ size_t poisson_args_bytes() { return sizeof(PoissonArgs); }
 // do not change over a handle's life) to d_args: n_inst * poisson_args_bytes().
 static bool group_sep(PoissonWork* const* pws, int n_inst) {
   for (int k = 0; k < n_inst; ++k)
-    if (!pws[k]->sS) return false;
+    if (!pws[k]->sTab) return false;
   return true;
 }
 

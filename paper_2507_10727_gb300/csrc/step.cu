@@ -304,8 +304,9 @@ __device__ __forceinline__ void deposit_run64(const Inst& I, int key, int m, int
 // candidate inside the loop would run the whole collision for one lane).
 // Returns this thread's share of the kinetic energy (diagnostic steps only).
 template <int SP, int GATHER>
-__device__ double push_chunk64(const Inst& I, long long c0, int ppt, unsigned long long* patch,
-                               int* cpatch, int* anchor, int* cq) {
+__device__ __forceinline__ double push_chunk64(const Inst& I, long long c0, int ppt,
+                                               unsigned long long* patch, int* cpatch, int* anchor,
+                                               int* cq) {
   Scalars* S = I.S;
   const long long n = S->n[SP];
   const long long step = S->step;
@@ -565,6 +566,46 @@ __global__ void __launch_bounds__(kPushThreads, 2) k_push_all(const Inst* insts,
       else K1 += push_chunk64<1, GATHER>(sI, s_c0, ppt, patch, cpatch, anchor, cq);
     }
     __syncthreads();
+  }
+}
+
+// The FP64 push of a single-instance handle: the instance's parameters are a
+// kernel argument (constant-bank operands in the particle loop instead of
+// shared-memory loads); otherwise k_push_all.
+template <int GATHER>
+__global__ void __launch_bounds__(kPushThreads, 2) k_push_one(const Inst I, WorkQueue* q,
+                                                               int ppt) {
+  __shared__ unsigned long long patch[kPR * kPZ];
+  __shared__ int cpatch[(kPR - 1) * (kPZ - 1)];
+  __shared__ int anchor[3];
+  __shared__ int cq[kCollQ];
+  __shared__ int s_sp, s_done, s_skip;
+  __shared__ long long s_c0;
+  for (int k = threadIdx.x; k < kPR * kPZ; k += blockDim.x) patch[k] = 0ULL;
+  for (int k = threadIdx.x; k < (kPR - 1) * (kPZ - 1); k += blockDim.x) cpatch[k] = 0;
+  double K0 = 0.0, K1 = 0.0;
+  const long long chunk = (long long)ppt * blockDim.x;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int item = (int)atomicAdd(&q->next, 1u);
+      int inst = -1, sp = 0, c = 0;
+      if (!queue_item(q, item, inst, sp, c)) inst = -1;
+      s_done = inst < 0;
+      s_sp = sp;
+      s_c0 = (long long)c * chunk;
+      s_skip = *(volatile int*)&I.S->status & ST_FATAL;
+    }
+    __syncthreads();
+    if (s_done) break;
+    if (!s_skip) {
+      if (s_sp == 0) K0 += push_chunk64<0, GATHER>(I, s_c0, ppt, patch, cpatch, anchor, cq);
+      else K1 += push_chunk64<1, GATHER>(I, s_c0, ppt, patch, cpatch, anchor, cq);
+    }
+    __syncthreads();
+  }
+  if (I.S->diag_on) {
+    block_add(K0, &I.S->K[0]);
+    block_add(K1, &I.S->K[1]);
   }
 }
 
@@ -1382,6 +1423,17 @@ cudaError_t launch_queue_setup(const Inst* d_insts, WorkQueue* q, int n_inst, lo
   return cudaGetLastError();
 }
 
+cudaError_t launch_push_one(const Inst& I, WorkQueue* q, int ppt, int num_sms, cudaStream_t st) {
+  if (I.prec32) return launch_push32_one(I, q, ppt, num_sms, st);
+  if (I.gather == 0)
+    k_push_one<0><<<resident_blocks((const void*)k_push_one<0>, kPushThreads, num_sms),
+                    kPushThreads, 0, st>>>(I, q, ppt);
+  else
+    k_push_one<1><<<resident_blocks((const void*)k_push_one<1>, kPushThreads, num_sms),
+                    kPushThreads, 0, st>>>(I, q, ppt);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_push_all(const Inst* d_insts, WorkQueue* q, int prec32, int gather, int ppt,
                             int num_sms, cudaStream_t st) {
   // a thread's queue-overflow candidates are a 32-bit mask over its chunk slots
@@ -1615,7 +1667,7 @@ cudaError_t launch_step(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_
   mk(G_FIELD, false);
   mk(G_PUSH, true);
   cudaError_t e0 = launch_queue_setup(d_inst, q, 1, (long long)ppt * kPushThreads, st);
-  if (e0 == cudaSuccess) e0 = launch_push_all(d_inst, q, I.prec32, I.gather, ppt, num_sms, st);
+  if (e0 == cudaSuccess) e0 = launch_push_one(I, q, ppt, num_sms, st);
   mk(G_PUSH, false);
   if (e0 != cudaSuccess) return e0;
   mk(G_BIRTHS, true);

@@ -255,8 +255,8 @@ __device__ __forceinline__ void deposit_run32(const Inst& I, int key, int m, int
 }
 
 template <int SP, int GATHER>
-__device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patch, int* cpatch,
-                               int* anchor, int* cq) {
+__device__ __forceinline__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patch,
+                                               int* cpatch, int* anchor, int* cq) {
   Scalars* S = I.S;
   const long long n = S->n[SP];
   const long long step = S->step;
@@ -458,6 +458,9 @@ __device__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patc
   return diag ? Kloc : 0.0;
 }
 
+// one wave of the persistent push: resident blocks per SM x SMs (cached per kernel)
+int resident_blocks(const void* fn, int threads, int num_sms);   // step.cu
+
 // The FP32 push of both species of every instance over the work queue (see
 // k_push_all in step.cu).
 template <int GATHER>
@@ -506,6 +509,59 @@ __global__ void __launch_bounds__(kPush32Threads, 4) k_push32_all(const Inst* in
     }
     __syncthreads();
   }
+}
+
+// The FP32 push of a single-instance handle: the same chunks over the same
+// queue, with the instance's parameters a kernel argument, so that the push
+// reads them as constant-bank operands instead of loads from shared memory
+// (fewer instructions and registers in the particle loop).
+template <int GATHER>
+__global__ void __launch_bounds__(kPush32Threads, 4) k_push32_one(const Inst I, WorkQueue* q,
+                                                                   int ppt) {
+  __shared__ float patch[kPR32 * kPZ32];
+  __shared__ int cpatch[(kPR32 - 1) * (kPZ32 - 1)];
+  __shared__ int anchor[3];
+  __shared__ int cq[kCollQ32];
+  __shared__ int s_sp, s_done, s_skip;
+  __shared__ long long s_c0;
+  for (int k = threadIdx.x; k < kPR32 * kPZ32; k += blockDim.x) patch[k] = 0.0f;
+  for (int k = threadIdx.x; k < (kPR32 - 1) * (kPZ32 - 1); k += blockDim.x) cpatch[k] = 0;
+  double K0 = 0.0, K1 = 0.0;
+  const long long chunk = (long long)ppt * blockDim.x;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int item = (int)atomicAdd(&q->next, 1u);
+      int inst = -1, sp = 0, c = 0;
+      if (!queue_item(q, item, inst, sp, c)) inst = -1;
+      s_done = inst < 0;
+      s_sp = sp;
+      s_c0 = (long long)c * chunk;
+      // one reading of the status word for the whole CTA (see k_push_all)
+      s_skip = *(volatile int*)&I.S->status & ST_FATAL;
+    }
+    __syncthreads();
+    if (s_done) break;
+    if (!s_skip) {
+      if (s_sp == 0) K0 += push_chunk32<0, GATHER>(I, s_c0, ppt, patch, cpatch, anchor, cq);
+      else K1 += push_chunk32<1, GATHER>(I, s_c0, ppt, patch, cpatch, anchor, cq);
+    }
+    __syncthreads();
+  }
+  if (I.S->diag_on) {
+    block_add(K0, &I.S->K[0]);
+    block_add(K1, &I.S->K[1]);
+  }
+}
+
+cudaError_t launch_push32_one(const Inst& I, WorkQueue* q, int ppt, int num_sms,
+                              cudaStream_t st) {
+  if (I.gather == 0)
+    k_push32_one<0><<<resident_blocks((const void*)k_push32_one<0>, kPush32Threads, num_sms),
+                      kPush32Threads, 0, st>>>(I, q, ppt);
+  else
+    k_push32_one<1><<<resident_blocks((const void*)k_push32_one<1>, kPush32Threads, num_sms),
+                      kPush32Threads, 0, st>>>(I, q, ppt);
+  return cudaGetLastError();
 }
 
 __device__ __forceinline__ void k_scatter32_body(const Inst& I, int sp0, int per_step) {
@@ -722,8 +778,6 @@ cudaError_t launch_deposit_all32(const Inst& I, int num_sms, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// one wave of the persistent push: resident blocks per SM x SMs (cached per kernel)
-int resident_blocks(const void* fn, int threads, int num_sms);   // step.cu
 
 cudaError_t launch_push32_all(const Inst* d_insts, WorkQueue* q, int gather, int ppt, int num_sms,
                               cudaStream_t st) {

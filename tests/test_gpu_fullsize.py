@@ -119,8 +119,14 @@ def test_rz256_ring_fp32_steps_around_a_full_sort(pg):
             n_total += b["id"].size
             flips += f
         assert flips <= math.ceil(1e-5 * n_total), flips
+        # the deposit (each species' node charge) and the field at the FP32 bar;
+        # the net charge is their difference, nearly cancelling in this
+        # quasi-neutral state, so its error relative to its own (small)
+        # maximum is not bounded separately
+        for sp in (0, 1):
+            err = field_err(pg.pic_get_species_charge(h, 0, sp), orc.species_charge(sp))
+            assert err <= TOL32, (sp, err)
         fg, fo = pg.pic_get_fields(h, 0), orc.fields()
-        assert field_err(fg["Q"], fo["Q"]) <= TOL32
         assert field_err(fg["phi"], fo["phi"]) <= TOL32
     pg.pic_destroy(h)
 
