@@ -254,17 +254,17 @@ __device__ __forceinline__ void deposit_run32(const Inst& I, int key, int m, int
   }
 }
 
-template <int SP, int GATHER>
-__device__ __forceinline__ double push_chunk32(const Inst& I, long long c0, int ppt, float* patch,
+template <int SP, int GATHER, bool PLAIN>
+__device__ __forceinline__ double push_chunk32(const Inst& I, int c0, int ppt, float* patch,
                                                int* cpatch, int* anchor, int* cq) {
   Scalars* S = I.S;
-  const long long n = S->n[SP];
+  const int n = (int)S->n[SP];   // counts stay below 2^31 (capacities are checked)
   const long long step = S->step;
   const bool diag = S->diag_on != 0;
   const Particles32 P = I.buf32[SP][S->flip[SP]];
   const float h = I.hq32[SP], kr = I.kr32, kz = I.kz32;
   const int lane = threadIdx.x & 31;
-  const long long run0 = c0 + (long long)(threadIdx.x >> 5) * 32 * ppt;
+  const int run0 = c0 + (threadIdx.x >> 5) * 32 * ppt;
   double Kloc = 0.0;
   {
     if (threadIdx.x == 0) {
@@ -277,7 +277,7 @@ __device__ __forceinline__ double push_chunk32(const Inst& I, long long c0, int 
     __syncthreads();
     const int pm0 = anchor[0], pn0 = anchor[1];
     // the next particle's two records are loaded while this one is pushed
-    long long i = run0 + lane;
+    int i = run0 + lane;
     float4 a_nx = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     uint4 b_nx = make_uint4(0u, 0u, 0u, 0u);
     if (i < n) {
@@ -294,7 +294,7 @@ __device__ __forceinline__ double push_chunk32(const Inst& I, long long c0, int 
       const float4 a = a_nx;
       const uint4 b = b_nx;
       {
-        const long long i2 = i + 32;
+        const int i2 = i + 32;
         if (j + 1 < ppt && i2 < n) {
           a_nx = P.a[i2];
           b_nx = P.b[i2];
@@ -307,14 +307,14 @@ __device__ __forceinline__ double push_chunk32(const Inst& I, long long c0, int 
         float vr = a.z, vt = a.w, vz = __uint_as_float(b.x);
         const float v2old = vr * vr + vt * vt + vz * vz;
         float rho = dr, zeta = dz, X = (float)m + dr, y = 0.0f;
-        if (I.push_on) {
+        if (PLAIN || I.push_on) {
           const int ck = cell_key(I, m, nn);
-          const float wr = rweight_upper32(I, dr, m);
+          const float wr = PLAIN ? dr : rweight_upper32(I, dr, m);
           float Er, Ez;
           if (GATHER == 0) {
             const float4 t = I.etab32[ck];
             Er = t.x + t.y * dz;
-            if (I.rweight == 1) Er *= ((float)m + dr) * (float)I.dr;
+            if (!PLAIN && I.rweight == 1) Er *= ((float)m + dr) * (float)I.dr;
             Ez = t.z + t.w * wr;
           } else {
             const float4 ta = I.etab32[2 * ck];
@@ -363,7 +363,7 @@ __device__ __forceinline__ double push_chunk32(const Inst& I, long long c0, int 
         bool alive = true;
         int m1, n1;
         float dr1, dz1;
-        if (I.walls_reflect) {
+        if (!PLAIN && I.walls_reflect) {
           float rc = (float)m + rho, zc = (float)nn + zeta;
           if (zc < 0.0f) { zc = -zc; vz = -vz; }
           if (zc >= (float)I.nz) { zc = 2.0f * I.nz - zc; vz = -vz; if (zc >= (float)I.nz) zc = nextafterf((float)I.nz, 0.0f); }
@@ -385,7 +385,7 @@ __device__ __forceinline__ double push_chunk32(const Inst& I, long long c0, int 
         if (!(isfinite(rho) && isfinite(zeta))) {
           atomicOr(&S->status, ST_NAN);
           alive = false;
-        } else if (!I.walls_reflect && (n1 < 0 || n1 >= I.nz || m1 >= I.nr)) {
+        } else if ((PLAIN || !I.walls_reflect) && (n1 < 0 || n1 >= I.nz || m1 >= I.nr)) {
           alive = false;
           if (n1 < 0)
             cathode_hit32<SP>(I, (float)m + dr, X, y, (float)nn + dz, (float)nn + zeta, vr, vt,
@@ -411,7 +411,7 @@ __device__ __forceinline__ double push_chunk32(const Inst& I, long long c0, int 
             acc_cnt = 0;
             s00 = s10 = s01 = s11 = 0.0f;
           }
-          const float wr1 = rweight_upper32(I, dr1, m1), wz1 = dz1;
+          const float wr1 = PLAIN ? dr1 : rweight_upper32(I, dr1, m1), wz1 = dz1;
           s00 += (1.0f - wr1) * (1.0f - wz1);
           s10 += wr1 * (1.0f - wz1);
           s01 += (1.0f - wr1) * wz1;
@@ -434,7 +434,7 @@ __device__ __forceinline__ double push_chunk32(const Inst& I, long long c0, int 
       while (over) {
         const int j = __ffs(over) - 1;
         over &= over - 1;
-        collide_at32(I, P, run0 + (long long)j * 32 + lane, step);
+        collide_at32(I, P, run0 + j * 32 + lane, step);
       }
     }
     for (int k = threadIdx.x; k < kPR32 * kPZ32; k += blockDim.x) {
@@ -504,8 +504,8 @@ __global__ void __launch_bounds__(kPush32Threads, 4) k_push32_all(const Inst* in
       cur = inst;
     }
     if (!s_skip) {
-      if (s_sp == 0) K0 += push_chunk32<0, GATHER>(sI, s_c0, ppt, patch, cpatch, anchor, cq);
-      else K1 += push_chunk32<1, GATHER>(sI, s_c0, ppt, patch, cpatch, anchor, cq);
+      if (s_sp == 0) K0 += push_chunk32<0, GATHER, false>(sI, (int)s_c0, ppt, patch, cpatch, anchor, cq);
+      else K1 += push_chunk32<1, GATHER, false>(sI, (int)s_c0, ppt, patch, cpatch, anchor, cq);
     }
     __syncthreads();
   }
@@ -515,7 +515,9 @@ __global__ void __launch_bounds__(kPush32Threads, 4) k_push32_all(const Inst* in
 // queue, with the instance's parameters a kernel argument, so that the push
 // reads them as constant-bank operands instead of loads from shared memory
 // (fewer instructions and registers in the particle loop).
-template <int GATHER>
+// PLAIN: the model's own switches (push on, tent weights in r, absorbing
+// walls) fixed at compile time; the other settings take the general variant.
+template <int GATHER, bool PLAIN>
 __global__ void __launch_bounds__(kPush32Threads, 4) k_push32_one(const Inst I, WorkQueue* q,
                                                                    int ppt) {
   __shared__ float patch[kPR32 * kPZ32];
@@ -542,8 +544,8 @@ __global__ void __launch_bounds__(kPush32Threads, 4) k_push32_one(const Inst I, 
     __syncthreads();
     if (s_done) break;
     if (!s_skip) {
-      if (s_sp == 0) K0 += push_chunk32<0, GATHER>(I, s_c0, ppt, patch, cpatch, anchor, cq);
-      else K1 += push_chunk32<1, GATHER>(I, s_c0, ppt, patch, cpatch, anchor, cq);
+      if (s_sp == 0) K0 += push_chunk32<0, GATHER, PLAIN>(I, (int)s_c0, ppt, patch, cpatch, anchor, cq);
+      else K1 += push_chunk32<1, GATHER, PLAIN>(I, (int)s_c0, ppt, patch, cpatch, anchor, cq);
     }
     __syncthreads();
   }
@@ -553,14 +555,23 @@ __global__ void __launch_bounds__(kPush32Threads, 4) k_push32_one(const Inst I, 
   }
 }
 
+template <int GATHER, bool PLAIN>
+static void push32_one(const Inst& I, WorkQueue* q, int ppt, int num_sms, cudaStream_t st) {
+  k_push32_one<GATHER, PLAIN><<<resident_blocks((const void*)k_push32_one<GATHER, PLAIN>,
+                                                kPush32Threads, num_sms),
+                                kPush32Threads, 0, st>>>(I, q, ppt);
+}
+
 cudaError_t launch_push32_one(const Inst& I, WorkQueue* q, int ppt, int num_sms,
                               cudaStream_t st) {
-  if (I.gather == 0)
-    k_push32_one<0><<<resident_blocks((const void*)k_push32_one<0>, kPush32Threads, num_sms),
-                      kPush32Threads, 0, st>>>(I, q, ppt);
-  else
-    k_push32_one<1><<<resident_blocks((const void*)k_push32_one<1>, kPush32Threads, num_sms),
-                      kPush32Threads, 0, st>>>(I, q, ppt);
+  const bool plain = I.push_on && I.rweight == 0 && !I.walls_reflect;
+  if (I.gather == 0) {
+    if (plain) push32_one<0, true>(I, q, ppt, num_sms, st);
+    else push32_one<0, false>(I, q, ppt, num_sms, st);
+  } else {
+    if (plain) push32_one<1, true>(I, q, ppt, num_sms, st);
+    else push32_one<1, false>(I, q, ppt, num_sms, st);
+  }
   return cudaGetLastError();
 }
 
