@@ -349,7 +349,7 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
   if (c.poisson_precond == 0 && poisson_sep_possible(ih.pw)) {
     void* sb = dev_alloc(h, poisson_sep_bytes(c.nr, c.nz));
     if (!sb) return fail(h, PIC_ERR_OOM, "device allocation failed");
-    e = poisson_sep_attach(ih.pw, sb, st);
+    e = poisson_sep_attach(ih.pw, sb, h->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "Poisson tables");
   }
 

@@ -138,7 +138,7 @@ void poisson_work_free(PoissonWork* pw);
 // later solves of pw use it instead of the multigrid V-cycle
 bool poisson_sep_possible(const PoissonWork* pw);
 size_t poisson_sep_bytes(int nr, int nz);
-cudaError_t poisson_sep_attach(PoissonWork* pw, void* base, cudaStream_t st);
+cudaError_t poisson_sep_attach(PoissonWork* pw, void* base, int num_sms, cudaStream_t st);
 // solve A phi = Q (+ Dirichlet values held in phi's boundary nodes)
 cudaError_t launch_poisson(PoissonWork* pw, const double* Q, double* phi, double tol, int max_iter,
                            int* status_dev, int* iters_dev, double* resid_dev, cudaStream_t st);

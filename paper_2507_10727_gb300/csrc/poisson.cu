@@ -966,20 +966,20 @@ __device__ void sep_columns(const PoissonWork& W, int lb, int nb, float* sm) {
     __syncthreads();
     if (threadIdx.x < nm) {
       const int j = threadIdx.x;
-      // y_m = (f_m + e_m y_{m-1}) / pivot_m  (off-diagonals -e), four rows of
+      // y_m = (f_m + e_m y_{m-1}) / pivot_m  (off-diagonals -e), eight rows of
       // operands loaded ahead of the recurrence
       float y = 0.0f;
       int m = 0;
-      for (; m + 3 < nr; m += 4) {
-        float hv[4], wv[4], ev[4];
+      for (; m + 7 < nr; m += 8) {
+        float hv[8], wv[8], ev[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 8; ++u) {
           hv[u] = h[(m + u) * kSepModes + j];
           wv[u] = w[(m + u) * kSepModes + j];
           ev[u] = e[m + u];
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 8; ++u) {
           y = (hv[u] + ev[u] * y) * wv[u];
           h[(m + u) * kSepModes + j] = y;
         }
@@ -991,15 +991,15 @@ __device__ void sep_columns(const PoissonWork& W, int lb, int nb, float* sm) {
       // x_m = y_m + c_m x_{m+1}
       float x = 0.0f;
       m = nr - 1;
-      for (; m - 3 >= 0; m -= 4) {
-        float hv[4], cv[4];
+      for (; m - 7 >= 0; m -= 8) {
+        float hv[8], cv[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 8; ++u) {
           hv[u] = h[(m - u) * kSepModes + j];
           cv[u] = c[(m - u) * kSepModes + j];
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 8; ++u) {
           x = fmaf(cv[u], x, hv[u]);
           h[(m - u) * kSepModes + j] = x;
         }
@@ -1462,7 +1462,7 @@ PoissonWork* poisson_work_init(void* base, int nr, int nz, double R, double L, i
 }
 
 // ---- sine-transform preconditioner ------------------------------------------
-constexpr int kSepMaxBlocks = 64;
+constexpr int kSepMaxBlocks = 256;
 
 static int sep_smem(const PoissonWork& w);
 
@@ -1495,7 +1495,7 @@ static int sep_smem(const PoissonWork& w) {
                (rows > cols ? rows : cols));
 }
 
-cudaError_t poisson_sep_attach(PoissonWork* pw, void* base, cudaStream_t st) {
+cudaError_t poisson_sep_attach(PoissonWork* pw, void* base, int num_sms, cudaStream_t st) {
   PoissonWork& w = *pw;
   const int nr = w.nr, nk = w.nz - 1;
   w.nk = nk;
@@ -1547,6 +1547,7 @@ cudaError_t poisson_sep_attach(PoissonWork* pw, void* base, cudaStream_t st) {
     attr = true;
   }
   int blocks = nr / 2 < kSepMaxBlocks ? nr / 2 : kSepMaxBlocks;
+  if (blocks > num_sms) blocks = num_sms;
   sep_rows_per_block(w, blocks);
   w.sep_blocks = (nr + w.rows_per_block - 1) / w.rows_per_block;
   return cudaSuccess;
