@@ -60,10 +60,11 @@ BYTES_PER_PARTICLE = 96.0
 # FP32 mode: read and write the two 16-byte records of a particle once.
 BYTES_PER_PARTICLE_FP32 = 64.0
 # DRAM traffic of one push launch per particle pushed, from ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum) on this workload at full size
-# (profiles/traffic_push_rz256_ring_4e7.md); None until measured on the
+# (dram__bytes_read.sum + dram__bytes_write.sum) on this workload at 1e7 per
+# species, scaled by the particles of a launch (one pass over each particle)
+# (profiles/traffic_push_one_rz256_ring_1e7.md); None until measured on the
 # kernel as it stands.
-TRAFFIC_PER_PARTICLE = {"fp64": 89.4, "fp32": 65.7}
+TRAFFIC_PER_PARTICLE = {"fp64": 87.8, "fp32": 64.3}
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA pipes-lanes per SM per clock x 2
 # flop x 2.07 GHz = 1.26 TFLOP/s (nominal 1.25); scaled to the measured clock.
 FP64_FLOP_PER_CLK = 152 * 2 * 2
@@ -99,11 +100,12 @@ def parse():
                     help="only the headline FP64 line: skip the FP32, ensemble and learned "
                          "warm-start sub-records")
     ap.add_argument("--workload", default="rz256",
-                    choices=["rz256", "sweep16", "learned", "unet", "precision"],
+                    choices=["rz256", "sweep16", "learned", "combined", "unet", "precision"],
                     help="rz256: one 256x256 discharge; sweep16: the 16-discharge "
                          "SEY x R_ext ensemble on 128x128 grids; learned: the 256x512 "
-                         "discharge with and without the learned Poisson warm start; unet: "
-                         "the warm-start network alone on the 257x513 node grid")
+                         "discharge with and without the learned Poisson warm start; "
+                         "combined: the sweep as one FP32 ensemble with the learned warm "
+                         "start; unet: the warm-start network alone on the 257x513 node grid")
     ap.add_argument("--phi-extrapolate", type=int, default=1, choices=(0, 1),
                     help="1: each step's Poisson solve starts from 2 phi^(n-1) - phi^(n-2) "
                          "(phi still solved to poisson_tol); 0: from phi^(n-1)")
@@ -121,6 +123,8 @@ def parse():
                          "previous solution's residual to the change of phi")
     ap.add_argument("--snapshots", type=int, default=512,
                     help="learned: recorded steps (one snapshot per step)")
+    ap.add_argument("--combined-snapshots", type=int, default=1024,
+                    help="combined: snapshots recorded over the 16 discharges (16 per step)")
     ap.add_argument("--train-iters", type=int, default=1000)
     ap.add_argument("--train-batch", type=int, default=8)
     ap.add_argument("--energy-steps", type=int, default=100000,
@@ -464,6 +468,14 @@ def run_sweep(args, torch, pg, emit: bool = True):
         singles.append(h)
     pg.pic_sync(singles[0])
     ms_s, ps_s = timed([(h, 0) for h in singles], args.steps)
+    # Poisson time of the 16 sequential runs per step of all 16
+    seq_poisson = 0.0
+    for h in singles:
+        pg.pic_profile(h, True)
+        pg.pic_step(h, min(args.steps, 5))
+        pr = pg.pic_profile_read(h)
+        pg.pic_profile(h, False)
+        seq_poisson += pr["poisson"]["total_ms"] / max(1, pr["push"]["launches"])
     for h in singles:
         pg.pic_destroy(h)
     value = ps_e / (ms_e / 1e3)
@@ -480,6 +492,7 @@ def run_sweep(args, torch, pg, emit: bool = True):
                        "l2": "inputs larger than L2"},
             "clocks": clk.summary(),
             "sequential_16_value": seq, "ensemble_over_sequential": value / seq,
+            "sequential_16_poisson_ms_per_step": seq_poisson,
             "autotuned_particles_per_thread": tuned, "cuda_graph": graph,
             "per_kernel_ms_per_step": {k: v["total_ms"] / nprof for k, v in prof.items()}}
     if emit:
@@ -581,6 +594,96 @@ def run_learned(args, torch, pg, emit: bool = True):
             "plain": plain, "warm": warm, "cold_start": cold,
             "training": {"loss_first": loss0, "loss_last": loss1, "seconds": t_train,
                          "record_seconds": t_rec, "stats": pg.pic_unet_stats(h)}}
+    if emit:
+        print(json.dumps(line), flush=True)
+    pg.pic_destroy(h)
+    return line
+
+
+# ---------------------------------------------------------------------------
+# the three forms together: the 16-discharge sweep as one FP32 ensemble whose
+# Poisson solves start from the learned warm start (one network for all 16,
+# trained on the ensemble's own recorded steps), against the plain FP64 form
+# (the same 16 discharges run one after the other, default solver)
+# ---------------------------------------------------------------------------
+def run_combined(args, torch, pg, emit: bool = True, plain_fp64=None):
+    a = argparse.Namespace(**vars(args))
+    a.precision, a.sort_every = "fp32", SORT_EVERY_DEFAULT["fp32"]
+    insts = sweep_workload(a)
+    for p, _ in insts:
+        # the network proposes starts for the multigrid-preconditioned solve
+        p["poisson_precond"] = 1
+    n_inst = len(insts)
+    h = pg.pic_create([p for p, _ in insts])
+    for k, (_, parts) in enumerate(insts):
+        for key, sp in (("e", 0), ("i", 1)):
+            pg.pic_set_particles(h, k, sp, parts[key])
+        pg.pic_solve_fields(h, k)
+    del insts[:]
+    pg.pic_unet_create(h, args.seed + 1, args.train_batch, 1)
+    record = max(1, args.combined_snapshots // n_inst)
+    pg.pic_unet_snapshots(h, record * n_inst, 1)
+    t0 = time.perf_counter()
+    pg.pic_step(h, record)
+    pg.pic_sync(h)
+    t_rec = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    loss0, loss1 = pg.pic_unet_train(h, args.train_iters, args.train_batch, 2e-3, args.seed + 7)
+    t_train = time.perf_counter() - t0
+
+    def psteps():
+        return sum(pg.pic_diagnostics(h, k)["particle_steps"] for k in range(n_inst))
+
+    def measure(on: bool):
+        pg.pic_unet_warm_start(h, on)
+        pg.pic_step(h, args.warmup)
+        pg.pic_sync(h)
+        s0, p0 = pg.pic_unet_stats(h), psteps()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with ClockSampler(gpu_uuid(torch)) as clk:
+            ev0.record()
+            pg.pic_step(h, args.steps)
+            ev1.record()
+            torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        s1, p1 = pg.pic_unet_stats(h), psteps()
+        pg.pic_profile(h, True)
+        pg.pic_step(h, 5)
+        prof = pg.pic_profile_read(h)
+        pg.pic_profile(h, False)
+        nprof = max(1, prof["push"]["launches"])
+        return {"value": (p1 - p0) / (ms / 1e3), "ms_per_step": ms / args.steps,
+                "poisson_iters_per_instance_step":
+                    (s1["poisson_iters"] - s0["poisson_iters"]) / (args.steps * n_inst),
+                "starts": {k: s1[k] - s0[k] for k in ("starts_previous", "starts_network",
+                                                       "starts_zero")},
+                "poisson_ms_per_step": prof["poisson"]["total_ms"] / nprof,
+                "warm_start_ms_per_step": prof["warm_start"]["total_ms"] / nprof,
+                "cuda_graph": pg.pic_uses_graph(h), "clocks": clk.summary()}
+
+    without = measure(False)
+    warm = measure(True)
+    line = {"metric": METRIC, "value": warm["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": warm["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "sweep16_rz128_fp32_learned_mode1", "instances": n_inst,
+                       "grid": [128, 128], "sort_every": a.sort_every,
+                       "poisson_precond": "multigrid V-cycle",
+                       "snapshots": record * n_inst, "train_iters": args.train_iters,
+                       "train_batch": args.train_batch, "l2": "inputs larger than L2"},
+            "warm": warm, "without_warm_start": without,
+            "training": {"loss_first": loss0, "loss_last": loss1, "seconds": t_train,
+                         "record_seconds": t_rec}}
+    if plain_fp64 and "sequential_16_value" in plain_fp64:
+        seq, seq_p = plain_fp64["sequential_16_value"], plain_fp64.get("sequential_16_poisson_ms_per_step")
+        line["plain_fp64"] = {"value": seq, "poisson_ms_per_step": seq_p,
+                              "form": "the 16 discharges as 16 sequential FP64 single-discharge "
+                                      "runs (sine-transform preconditioner, extrapolated start)"}
+        line["over_plain_fp64"] = warm["value"] / seq
+        if seq_p:
+            line["poisson_time_over_plain_fp64"] = warm["poisson_ms_per_step"] / seq_p
     if emit:
         print(json.dumps(line), flush=True)
     pg.pic_destroy(h)
@@ -746,7 +849,7 @@ def push_roofline(precision, gather, rec, n_pushed, peaks, peak_kind):
     bpp = BYTES_PER_PARTICLE if precision == "fp64" else BYTES_PER_PARTICLE_FP32
     hbm = peaks.get("hbm_gbs", 6800.0)
     bw = bpp * n_pushed / (push_ms / 1e3) / 1e9
-    line = {"bound": "hbm", "kernel": ("k_push_all" if precision == "fp64" else "k_push32_all")
+    line = {"bound": "hbm", "kernel": ("k_push_one" if precision == "fp64" else "k_push32_one")
             + " (both species)", "achieved": bw, "peak": hbm, "unit": "GB/s",
             "frac": bw / hbm, "traffic": (TRAFFIC_PER_PARTICLE[precision] * n_pushed
                                           if TRAFFIC_PER_PARTICLE[precision] else None),
@@ -803,7 +906,8 @@ def sub_records(args, torch, pg, p, parts, peaks, peak_kind, local, fp64_value):
     """The other forms, each timed on its own: the FP32 particle mode on the
     same workload and state, the 16-discharge ensemble against 16 sequential
     runs (both precisions), the learned Poisson warm start against the plain
-    solver on the 256 x 512 workload."""
+    solver on the 256 x 512 workload, and the three together (FP32 ensemble
+    with the learned warm start) against the plain FP64 form."""
     out = {}
     g = 0 if args.gather == "ec" else 1
     try:
@@ -837,6 +941,11 @@ def sub_records(args, torch, pg, p, parts, peaks, peak_kind, local, fp64_value):
         out["learned"] = run_learned(a, torch, pg, emit=False)
     except Exception as exc:
         out["learned"] = {"error": repr(exc)}
+    try:
+        out["combined"] = run_combined(args, torch, pg, emit=False,
+                                       plain_fp64=out.get("sweep16_fp64"))
+    except Exception as exc:
+        out["combined"] = {"error": repr(exc)}
     return out
 
 
@@ -875,6 +984,8 @@ def main():
         return run_sweep(args, torch, pg)
     if args.workload == "learned":
         return run_learned(args, torch, pg)
+    if args.workload == "combined":
+        return run_combined(args, torch, pg)
     if args.workload == "unet":
         return run_unet(args, torch, pg)
     if args.workload == "precision":

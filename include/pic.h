@@ -377,11 +377,17 @@ int pic_profile_read(pic_handle* h, pic_kernel_time* out, int max, int* n_out);
 /* Number of network parameters (302849). */
 int pic_unet_param_count(int64_t* n);
 
-/* Attach a network to a single-instance handle (nr, nz divisible by 8).
- * He-normal weights from `seed`, zero biases; max_batch = largest batch of
- * pic_unet_loss_grad / pic_unet_train; mode 0 or 1 (see above).  Allocates
- * through the handle's allocator.  Synchronous.  PIC_ERR_INVALID for
- * ensembles, other grids, another mode or a second call. */
+/* Attach a network to a handle (nr, nz divisible by 8).  On an ensemble the
+ * instances must share nr, nz and the boundary kinds (insulating z = 0 nodes
+ * and wall); the one network then serves all of them: each step's inputs of
+ * all instances form one forward batch, each instance's solve picks its own
+ * start, and every instance records into the one snapshot ring (instance k
+ * of a recording step into slot count + k, the step counter of instance 0
+ * deciding which steps record).  V_ref is instance 0's.  He-normal weights
+ * from `seed`, zero biases; max_batch = largest batch of pic_unet_loss_grad /
+ * pic_unet_train; mode 0 or 1 (see above).  Allocates through the handle's
+ * allocator.  Synchronous.  PIC_ERR_INVALID for instances of different grids
+ * or boundary kinds, other grid sizes, another mode or a second call. */
 int pic_unet_create(pic_handle* h, uint64_t seed, int max_batch, int mode);
 
 /* Set / get the FP32 parameter vector (host, n = pic_unet_param_count). */
@@ -411,10 +417,18 @@ int pic_unet_snapshots(pic_handle* h, int64_t capacity, int every);
 int pic_unet_train(pic_handle* h, int iters, int batch, float lr, uint64_t seed,
                    double* loss_first, double* loss_last);
 
+/* Set the network's input and output scales (in_norm, out_norm as in the
+ * stats below; both > 0), which the first pic_unet_train call otherwise fixes
+ * from the recorded snapshots: with pic_unet_set_params this moves a trained
+ * network to another handle.  Synchronous.  PIC_ERR_INVALID for a scale that
+ * is not positive and finite. */
+int pic_unet_set_norms(pic_handle* h, double in_norm, double out_norm);
+
 /* Turn the warm start of later pic_step solves on (1) or off (0). */
 int pic_unet_warm_start(pic_handle* h, int on);
 
-/* Counters since pic_unet_create (synchronous). */
+/* Counters since pic_unet_create, summed over the instances of the handle
+ * (synchronous); last_start is that of the last instance solved. */
 typedef struct pic_unet_stats {
   int64_t snapshots;           /* snapshots recorded */
   int64_t starts_previous;     /* solves started from the previous phi */

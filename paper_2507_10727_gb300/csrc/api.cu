@@ -3,6 +3,7 @@
 // solve.  No compute happens here beyond set-up tables (the magnetron field
 // table, the null-collision frequency) evaluated once on the host in FP64.
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -57,7 +58,7 @@ struct pic_handle {
   long long* d_live = nullptr;       // device: live particles after the last step
   long long* h_live = nullptr;       // page-locked copy
   cudaEvent_t live_ev = nullptr;     // recorded after the copy
-  UNet* unet = nullptr;              // learned warm start (single instance)
+  UNet* unet = nullptr;              // learned warm start (all instances)
   pic_alloc alloc;
   bool own_alloc = true;
   cudaStream_t stream = nullptr;
@@ -891,9 +892,19 @@ static cudaError_t launch_ensemble_step(pic_handle* h, const StepMarks* marks) {
   mk(G_SCATTER, true);
   if (e == cudaSuccess) e = launch_post_push_batch(h->d_insts, n, bd, h->num_sms, st);
   mk(G_SCATTER, false);
+  std::vector<Inst> hi;
+  if (h->unet) {
+    for (const InstHost& ih : h->inst) hi.push_back(ih.I);
+    if (e == cudaSuccess && unet_pre_solve_needed(h->unet)) {
+      mk(G_WARM, true);
+      e = launch_pre_solve(h->unet, hi.data(), h->pws.data(), n, st);
+      mk(G_WARM, false);
+    }
+  }
   mk(G_POISSON, true);
   if (e == cudaSuccess) e = launch_poisson_group(h->pws.data(), nullptr, n, h->d_pargs, h->num_sms, st);
   mk(G_POISSON, false);
+  if (e == cudaSuccess && h->unet) e = launch_after_solve(h->unet, hi.data(), n, st);
   mk(G_STEP_END, true);
   if (e == cudaSuccess) e = launch_step_end_batch(h->d_insts, n, st);
   mk(G_STEP_END, false);
@@ -903,10 +914,10 @@ static cudaError_t launch_ensemble_step(pic_handle* h, const StepMarks* marks) {
 // launches around the Poisson solve of a single-instance step: the learned
 // warm start before it, snapshot recording and iteration counts after it
 static cudaError_t hook_pre_poisson(void* ctx, const Inst& I, PoissonWork* pw, cudaStream_t st) {
-  return launch_pre_solve(((pic_handle*)ctx)->unet, I, pw, st);
+  return launch_pre_solve(((pic_handle*)ctx)->unet, &I, &pw, 1, st);
 }
 static cudaError_t hook_post_poisson(void* ctx, const Inst& I, cudaStream_t st) {
-  return launch_after_solve(((pic_handle*)ctx)->unet, I, st);
+  return launch_after_solve(((pic_handle*)ctx)->unet, &I, 1, st);
 }
 
 static cudaError_t launch_all(pic_handle* h, const StepMarks* marks) {
@@ -1437,13 +1448,16 @@ int pic_unet_param_count(int64_t* n) {
 int pic_unet_create(pic_handle* h, uint64_t seed, int max_batch, int mode) {
   if (!h) return PIC_ERR_INVALID;
   if (h->unet) return fail(h, PIC_ERR_INVALID, "the handle already has a network");
-  if (h->inst.size() != 1) return fail(h, PIC_ERR_INVALID, "warm start needs a single-instance handle");
   const pic_config& c = h->inst[0].cfg;
+  for (const InstHost& ih : h->inst)
+    if (ih.cfg.nr != c.nr || ih.cfg.nz != c.nz || ih.I.bc_g != h->inst[0].I.bc_g ||
+        ih.I.bc_wall != h->inst[0].I.bc_wall)
+      return fail(h, PIC_ERR_INVALID, "the instances must share the grid and its boundary kinds");
   if (c.nr % 8 || c.nz % 8 || max_batch < 1 || mode < 0 || mode > 1)
     return fail(h, PIC_ERR_INVALID, "nr and nz must be multiples of 8, max_batch >= 1, mode 0 or 1");
   const double vref = c.circuit_mode == 1 ? std::fabs(c.Vs) : std::fabs(c.Vc_fixed);
-  UNet* u = unet_create(c.nr, c.nz, max_batch, mode, seed, vref > 0.0 ? vref : 1.0, unet_alloc_cb,
-                        h, h->stream);
+  UNet* u = unet_create(c.nr, c.nz, max_batch, (int)h->inst.size(), mode, seed,
+                        vref > 0.0 ? vref : 1.0, unet_alloc_cb, h, h->stream);
   if (!u) return fail(h, PIC_ERR_OOM, "network allocation or set-up failed");
   unet_set_boundary(u, h->inst[0].I.bc_g, h->inst[0].I.bc_wall);
   h->unet = u;
@@ -1502,6 +1516,21 @@ int pic_unet_train(pic_handle* h, int iters, int batch, float lr, uint64_t seed,
   if (e == cudaErrorInvalidValue) return fail(h, PIC_ERR_INVALID, "no snapshot recorded yet");
   if (e == cudaErrorTimeout) return fail(h, PIC_ERR_TIMEOUT, "tensor-core wait reached its limit");
   if (e != cudaSuccess) return cuda_fail(h, e, "unet_train");
+  return PIC_OK;
+}
+
+int pic_unet_set_norms(pic_handle* h, double in_norm, double out_norm) {
+  const int rc = need_unet(h);
+  if (rc != PIC_OK) return rc;
+  if (!(in_norm > 0.0) || !(out_norm > 0.0) || !std::isfinite(in_norm) || !std::isfinite(out_norm))
+    return fail(h, PIC_ERR_INVALID, "scales must be positive and finite");
+  const double v[2] = {in_norm, out_norm};
+  static_assert(offsetof(UDev, out_norm) == offsetof(UDev, in_norm) + sizeof(double),
+                "in_norm and out_norm adjacent");
+  cudaError_t e = cudaMemcpyAsync((char*)unet_dev(h->unet) + offsetof(UDev, in_norm), v, sizeof(v),
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "unet_set_norms");
   return PIC_OK;
 }
 

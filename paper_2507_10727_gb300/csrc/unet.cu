@@ -678,13 +678,15 @@ __global__ void k_train_input(const float* f0, const float* f1, const float* slo
   }
 }
 
-// network input from the live state (batch 1): mode 0 from rho = Q / V and
-// phi's Dirichlet values, mode 1 from the residual of the previous solution
-__global__ void k_step_input(Inst I, const UDev* ud, int mode, const float* res, bf16* x_in) {
+// network input of one instance from its live state (its sample of the
+// batch): mode 0 from rho = Q / V and phi's Dirichlet values, mode 1 from the
+// residual of the previous solution scaled by its RMS *scale
+__global__ void k_step_input(Inst I, const UDev* ud, int mode, const float* res,
+                             const double* scale, bf16* x_in) {
   const int W = I.nz + 1;
   const long long npx = (long long)(I.nr + 1) * W;
   if (I.S->status & ST_FATAL) return;
-  const double inv_in = 1.0 / (mode == 0 ? ud->in_norm : ud->cur_scale);
+  const double inv_in = 1.0 / (mode == 0 ? ud->in_norm : *scale);
   const double inv_out = 1.0 / ud->out_norm;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
        q += (long long)gridDim.x * blockDim.x) {
@@ -708,10 +710,10 @@ __global__ void k_step_input(Inst I, const UDev* ud, int mode, const float* res,
 
 // candidate start from the network output (Dirichlet values of phi)
 __global__ void k_make_cand(int nr, int nz, int g, int wall, const double* phi, const float* net,
-                            const UDev* ud, int mode, double* cand) {
+                            const UDev* ud, const double* scale, int mode, double* cand) {
   const int W = nz + 1;
   const long long npx = (long long)(nr + 1) * W;
-  const double s = mode == 0 ? ud->out_norm : ud->cur_scale * (ud->out_norm / ud->in_norm);
+  const double s = mode == 0 ? ud->out_norm : *scale * (ud->out_norm / ud->in_norm);
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
        q += (long long)gridDim.x * blockDim.x) {
     const int m = (int)(q / W), n = (int)(q - (long long)m * W);
@@ -720,14 +722,15 @@ __global__ void k_make_cand(int nr, int nz, int g, int wall, const double* phi, 
   }
 }
 
+// Recording: instance k of a recording step (the clock's step a multiple of
+// `every`) writes slot (snap_count + k) mod cap.
 // mode 0 recording (after the solve): rho and phi
-__global__ void k_snap_record(Inst I, const UDev* ud, float* f0, float* f1, long long cap,
-                              int every) {
-  const Scalars* S = I.S;
-  if ((S->status & ST_FATAL) || (S->step % every) != 0) return;
+__global__ void k_snap_record(Inst I, const Scalars* clock, const UDev* ud, float* f0, float* f1,
+                              long long cap, int every, int k) {
+  if ((I.S->status & ST_FATAL) || (clock->step % every) != 0) return;
   const int W = I.nz + 1;
   const long long npx = (long long)(I.nr + 1) * W;
-  const long long slot = ud->snap_count % cap;
+  const long long slot = (ud->snap_count + k) % cap;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
        q += (long long)gridDim.x * blockDim.x) {
     const int m = (int)(q / W), n = (int)(q - (long long)m * W);
@@ -738,12 +741,11 @@ __global__ void k_snap_record(Inst I, const UDev* ud, float* f0, float* f1, long
 
 // mode 1 recording, before the solve: the residual of the previous solution
 // into the slot, the previous solution kept in FP64
-__global__ void k_snap_pre(Inst I, const UDev* ud, const float* res, float* f0, double* phi_prev,
-                           long long cap, int every) {
-  const Scalars* S = I.S;
-  if ((S->status & ST_FATAL) || (S->step % every) != 0) return;
+__global__ void k_snap_pre(Inst I, const Scalars* clock, const UDev* ud, const float* res,
+                           float* f0, double* phi_prev, long long cap, int every, int k) {
+  if ((I.S->status & ST_FATAL) || (clock->step % every) != 0) return;
   const long long npx = (long long)(I.nr + 1) * (I.nz + 1);
-  const long long slot = ud->snap_count % cap;
+  const long long slot = (ud->snap_count + k) % cap;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
        q += (long long)gridDim.x * blockDim.x) {
     f0[slot * npx + q] = res[q];
@@ -752,12 +754,11 @@ __global__ void k_snap_pre(Inst I, const UDev* ud, const float* res, float* f0, 
 }
 
 // mode 1 recording, after the solve: the change of phi
-__global__ void k_snap_post(Inst I, const UDev* ud, float* f1, const double* phi_prev,
-                            long long cap, int every) {
-  const Scalars* S = I.S;
-  if ((S->status & ST_FATAL) || (S->step % every) != 0) return;
+__global__ void k_snap_post(Inst I, const Scalars* clock, const UDev* ud, float* f1,
+                            const double* phi_prev, long long cap, int every, int k) {
+  if ((I.S->status & ST_FATAL) || (clock->step % every) != 0) return;
   const long long npx = (long long)(I.nr + 1) * (I.nz + 1);
-  const long long slot = ud->snap_count % cap;
+  const long long slot = (ud->snap_count + k) % cap;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
        q += (long long)gridDim.x * blockDim.x)
     f1[slot * npx + q] = (float)(I.phi[q] - phi_prev[q]);
@@ -786,27 +787,29 @@ __device__ void cta_rms(const float* f, long long n, double* out_d, float* out_f
 }
 
 // mode-1 recording: RMS of the residual just stored in the current slot
-__global__ void __launch_bounds__(1024) k_slot_rms(Inst I, const UDev* ud, const float* f0,
-                                                   float* slot_scale, long long cap, int every) {
-  const Scalars* S = I.S;
-  if ((S->status & ST_FATAL) || (S->step % every) != 0) return;
+__global__ void __launch_bounds__(1024) k_slot_rms(Inst I, const Scalars* clock, const UDev* ud,
+                                                   const float* f0, float* slot_scale,
+                                                   long long cap, int every, int k) {
+  if ((I.S->status & ST_FATAL) || (clock->step % every) != 0) return;
   const long long npx = (long long)(I.nr + 1) * (I.nz + 1);
-  const long long slot = ud->snap_count % cap;
+  const long long slot = (ud->snap_count + k) % cap;
   cta_rms(f0 + slot * npx, npx, nullptr, slot_scale + slot);
 }
 
-// mode-1 warm start: RMS of the live residual
-__global__ void __launch_bounds__(1024) k_live_rms(const float* res, long long npx, UDev* ud) {
-  cta_rms(res, npx, &ud->cur_scale, nullptr);
+// mode-1 warm start: RMS of an instance's live residual
+__global__ void __launch_bounds__(1024) k_live_rms(const float* res, long long npx, double* scale) {
+  cta_rms(res, npx, scale, nullptr);
 }
 
-__global__ void k_after_solve(Inst I, UDev* ud, int every, int record) {
+// after an instance's solve: its iterations; the last instance of a
+// recording step advances the ring by `inc` (the instances of the step)
+__global__ void k_after_solve(Inst I, const Scalars* clock, UDev* ud, int every, int record,
+                              int inc) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   Scalars* S = I.S;
   if (ud->err) atomicOr(&S->status, ST_TIMEOUT);
-  if (S->status & ST_FATAL) return;
-  ud->iters_total += S->poisson_iters;
-  if (record && (S->step % every) == 0) ud->snap_count += 1;
+  if (!(S->status & ST_FATAL)) ud->iters_total += S->poisson_iters;
+  if (record && inc > 0 && (clock->step % every) == 0) ud->snap_count += inc;
 }
 
 // mean square of a recorded field over the stored snapshots (input and
@@ -907,6 +910,7 @@ struct ULayerInfo {
 
 struct UNet {
   int nr, nz, bmax;
+  int n_inst = 1;              // instances served (forward batch of a step)
   int H[kLev], W[kLev];
   double v_ref;
   ULayerInfo L[kNumLayers];
@@ -928,9 +932,11 @@ struct UNet {
   double* gpart = nullptr;     // guess-selection partials
   int gblk = 0;
   int mode = 0;
+  // per instance k at offset k * npx(0) (gpart: k * gblk * 3, scale: k)
   double* cand = nullptr;      // candidate start (FP64 node array)
   float* res = nullptr;        // residual of the previous solution (mode 1)
   double* phi_prev = nullptr;  // previous solution (mode-1 recording)
+  double* scale = nullptr;     // mode 1: RMS of the live residual of this step
   float *snap_f0 = nullptr, *snap_f1 = nullptr;
   float* slot_scale = nullptr;  // mode 1: residual RMS of each snapshot
   long long snap_cap = 0;
@@ -1182,15 +1188,17 @@ long long unet_param_count() {
   return n + kCh[0] + 1;
 }
 
-UNet* unet_create(int nr, int nz, int bmax, int mode, unsigned long long seed, double v_ref,
-                  UAllocFn alloc, void* ctx, cudaStream_t st) {
-  if (nr % 8 || nz % 8 || nr < 8 || nz < 8 || bmax < 1 || !alloc || mode < 0 || mode > 1)
+UNet* unet_create(int nr, int nz, int bmax, int n_inst, int mode, unsigned long long seed,
+                  double v_ref, UAllocFn alloc, void* ctx, cudaStream_t st) {
+  if (nr % 8 || nz % 8 || nr < 8 || nz < 8 || bmax < 1 || n_inst < 1 || !alloc || mode < 0 ||
+      mode > 1)
     return nullptr;
   UNet* u = new UNet();
   u->mode = mode;
   u->nr = nr;
   u->nz = nz;
   u->bmax = bmax;
+  u->n_inst = n_inst;
   u->v_ref = v_ref > 0.0 ? v_ref : 1.0;
   u->bc_g = nr + 1;
   u->alloc = alloc;
@@ -1256,7 +1264,7 @@ UNet* unet_create(int nr, int nz, int bmax, int mode, unsigned long long seed, d
   u->v = (float*)A(u->np * 4);
   u->wf = (bf16*)A(u->nwf * 2);
   u->wd = (bf16*)A(u->nwd * 2);
-  const long long B = bmax;
+  const long long B = bmax > n_inst ? bmax : n_inst;   // activations of the larger batch
   u->x_in = (bf16*)A(B * u->npx(0) * kInPad * 2);
   for (int l = 0; l < kLev; ++l) {
     u->ea[l] = (bf16*)A(B * u->npx(l) * kCh[l] * 2);
@@ -1282,10 +1290,11 @@ UNet* unet_create(int nr, int nz, int bmax, int mode, unsigned long long seed, d
   u->d_loss = (double*)A(8);
   u->ud = (UDev*)A(sizeof(UDev));
   u->gblk = guess_blocks(nr, nz);
-  u->gpart = (double*)A((size_t)u->gblk * 3 * 8);
-  u->cand = (double*)A(u->npx(0) * 8);
-  u->res = (float*)A(u->npx(0) * 4);
-  u->phi_prev = (double*)A(u->npx(0) * 8);
+  u->gpart = (double*)A((size_t)n_inst * u->gblk * 3 * 8);
+  u->cand = (double*)A((size_t)n_inst * u->npx(0) * 8);
+  u->res = (float*)A((size_t)n_inst * u->npx(0) * 4);
+  u->phi_prev = (double*)A((size_t)n_inst * u->npx(0) * 8);
+  u->scale = (double*)A((size_t)n_inst * 8);
   if (!ok) {
     delete u;
     return nullptr;
@@ -1393,40 +1402,66 @@ bool unet_recording(const UNet* u) { return u->snap_cap > 0; }
 
 bool unet_pre_solve_needed(const UNet* u) { return u->warm || (u->mode == 1 && u->snap_cap > 0); }
 
-cudaError_t launch_pre_solve(UNet* u, const Inst& I, PoissonWork* pw, cudaStream_t st) {
-  const int g0 = grid1(u->npx(0), 256);
+cudaError_t launch_pre_solve(UNet* u, const Inst* insts, PoissonWork* const* pws, int n,
+                             cudaStream_t st) {
+  if (n < 1 || n > u->n_inst) return cudaErrorInvalidValue;
+  const long long npx = u->npx(0);
+  const int g0 = grid1(npx, 256);
+  const Scalars* clock = insts[0].S;
   cudaError_t e = cudaSuccess;
   if (u->mode == 1) {
-    e = launch_residual32(pw, I.Q, I.phi, u->res, st);
-    if (e) return e;
-    if (u->snap_cap > 0) {
-      k_snap_pre<<<g0, 256, 0, st>>>(I, u->ud, u->res, u->snap_f0, u->phi_prev, u->snap_cap,
-                                     u->snap_every);
-      k_slot_rms<<<1, 1024, 0, st>>>(I, u->ud, u->snap_f0, u->slot_scale, u->snap_cap,
-                                     u->snap_every);
+    for (int k = 0; k < n; ++k) {
+      const Inst& I = insts[k];
+      float* res = u->res + k * npx;
+      e = launch_residual32(pws[k], I.Q, I.phi, res, st);
+      if (e) return e;
+      if (u->snap_cap > 0) {
+        k_snap_pre<<<g0, 256, 0, st>>>(I, clock, u->ud, res, u->snap_f0, u->phi_prev + k * npx,
+                                       u->snap_cap, u->snap_every, k);
+        k_slot_rms<<<1, 1024, 0, st>>>(I, clock, u->ud, u->snap_f0, u->slot_scale, u->snap_cap,
+                                       u->snap_every, k);
+      }
+      if (u->warm) k_live_rms<<<1, 1024, 0, st>>>(res, npx, u->scale + k);
     }
-    if (u->warm) k_live_rms<<<1, 1024, 0, st>>>(u->res, u->npx(0), u->ud);
   }
   if (!u->warm) return cudaGetLastError();
-  k_step_input<<<g0, 256, 0, st>>>(I, u->ud, u->mode, u->res, u->x_in);
-  e = forward(u, 1, st);
+  // the inputs of all instances as one batch of the forward pass
+  for (int k = 0; k < n; ++k)
+    k_step_input<<<g0, 256, 0, st>>>(insts[k], u->ud, u->mode, u->res + k * npx, u->scale + k,
+                                     u->x_in + k * npx * kInPad);
+  e = forward(u, n, st);
   if (e) return e;
-  k_make_cand<<<g0, 256, 0, st>>>(u->nr, u->nz, I.bc_g, I.bc_wall, I.phi, u->out, u->ud, u->mode,
-                                  u->cand);
-  e = launch_gs_sweeps(pw, I.Q, u->cand, 2, st);
-  if (e) return e;
-  return launch_guess_select(pw, I.Q, I.phi, u->cand, u->gpart, u->gblk, u->ud, &I.S->status, st);
+  for (int k = 0; k < n && e == cudaSuccess; ++k) {
+    const Inst& I = insts[k];
+    double* cand = u->cand + k * npx;
+    k_make_cand<<<g0, 256, 0, st>>>(u->nr, u->nz, I.bc_g, I.bc_wall, I.phi, u->out + k * npx, u->ud,
+                                    u->scale + k, u->mode, cand);
+    e = launch_gs_sweeps(pws[k], I.Q, cand, 2, st);
+    if (e == cudaSuccess)
+      e = launch_guess_select(pws[k], I.Q, I.phi, cand, u->gpart + (size_t)k * u->gblk * 3,
+                              u->gblk, u->ud, &I.S->status, st);
+  }
+  return e;
 }
 
-cudaError_t launch_after_solve(UNet* u, const Inst& I, cudaStream_t st) {
-  const int g0 = grid1(u->npx(0), 256);
-  if (u->snap_cap > 0) {
-    if (u->mode == 0)
-      k_snap_record<<<g0, 256, 0, st>>>(I, u->ud, u->snap_f0, u->snap_f1, u->snap_cap, u->snap_every);
-    else
-      k_snap_post<<<g0, 256, 0, st>>>(I, u->ud, u->snap_f1, u->phi_prev, u->snap_cap, u->snap_every);
+cudaError_t launch_after_solve(UNet* u, const Inst* insts, int n, cudaStream_t st) {
+  if (n < 1 || n > u->n_inst) return cudaErrorInvalidValue;
+  const long long npx = u->npx(0);
+  const int g0 = grid1(npx, 256);
+  const Scalars* clock = insts[0].S;
+  for (int k = 0; k < n; ++k) {
+    const Inst& I = insts[k];
+    if (u->snap_cap > 0) {
+      if (u->mode == 0)
+        k_snap_record<<<g0, 256, 0, st>>>(I, clock, u->ud, u->snap_f0, u->snap_f1, u->snap_cap,
+                                          u->snap_every, k);
+      else
+        k_snap_post<<<g0, 256, 0, st>>>(I, clock, u->ud, u->snap_f1, u->phi_prev + k * npx,
+                                        u->snap_cap, u->snap_every, k);
+    }
+    k_after_solve<<<1, 32, 0, st>>>(I, clock, u->ud, u->snap_every, u->snap_cap > 0 ? 1 : 0,
+                                    k == n - 1 ? n : 0);
   }
-  k_after_solve<<<1, 32, 0, st>>>(I, u->ud, u->snap_every, u->snap_cap > 0 ? 1 : 0);
   return cudaGetLastError();
 }
 

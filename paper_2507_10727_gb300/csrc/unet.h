@@ -20,6 +20,12 @@
 // The guess (mode 0: V_ref * y; mode 1: phi_prev + s K y on the free
 // nodes) is smoothed by two red-black Gauss-Seidel sweeps of the FP64 fine
 // operator, then competes with phi_prev and zero by residual norm.
+//
+// One network serves every instance of a handle whose instances share the
+// grid and its boundary kinds: the inputs of all instances form one batch of
+// the forward pass, each instance keeps its own residual scale, candidate and
+// start choice, and every instance records into the one snapshot ring
+// (instance k of a recording step into slot count + k).
 #pragma once
 
 #include <cstdint>
@@ -32,7 +38,8 @@ namespace pic {
 struct PoissonWork;
 struct UNet;
 
-// device counters of the warm start (one per handle)
+// device counters of the warm start (one per handle; counts summed over the
+// instances)
 struct UDev {
   long long snap_count;     // snapshots recorded so far
   long long n_choice[3];    // solves started from: previous phi, network, zero
@@ -41,15 +48,15 @@ struct UDev {
   double out_norm;          // output scale (mode 0: V_ref; mode 1: set by the first training)
   int choice;               // guess used by the last solve
   int err;                  // 1 once a tensor-core wait reached its time limit
-  double cur_scale;         // mode 1: RMS of the live residual of this step
 };
 
 typedef void* (*UAllocFn)(void* ctx, size_t bytes);
 
 long long unet_param_count();
-// nr, nz divisible by 8; bmax = largest training/gradient batch; mode 0 / 1
-UNet* unet_create(int nr, int nz, int bmax, int mode, unsigned long long seed, double v_ref,
-                  UAllocFn alloc, void* ctx, cudaStream_t st);
+// nr, nz divisible by 8; bmax = largest training/gradient batch; n_inst =
+// instances served (the forward batch of a step); mode 0 / 1
+UNet* unet_create(int nr, int nz, int bmax, int n_inst, int mode, unsigned long long seed,
+                  double v_ref, UAllocFn alloc, void* ctx, cudaStream_t st);
 int unet_mode(const UNet* u);
 // insulating boundary nodes of the field (field_free's g and wall): they are
 // unknowns of the solve, not Dirichlet inputs of the network
@@ -79,9 +86,13 @@ cudaError_t unet_train(UNet* u, int iters, int batch, float lr, unsigned long lo
 void unet_set_warm(UNet* u, bool on);
 bool unet_warm(const UNet* u);
 bool unet_pre_solve_needed(const UNet* u);
-cudaError_t launch_pre_solve(UNet* u, const Inst& I, PoissonWork* pw, cudaStream_t st);
-// after the solve: recording and iteration count bookkeeping
-cudaError_t launch_after_solve(UNet* u, const Inst& I, cudaStream_t st);
+// start of the n instances insts[0..n) (host copies) with workspaces pws
+// (n at most the n_inst of the network); instance 0's step counter is the
+// recording clock of all
+cudaError_t launch_pre_solve(UNet* u, const Inst* insts, PoissonWork* const* pws, int n,
+                             cudaStream_t st);
+// after the solves: recording and iteration count bookkeeping
+cudaError_t launch_after_solve(UNet* u, const Inst* insts, int n, cudaStream_t st);
 
 // operator pieces (poisson.cu), all on the fine FP64 operator of the solve
 // res = Q - A phi on free nodes (0 on Dirichlet nodes), FP32 output

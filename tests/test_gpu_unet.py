@@ -233,3 +233,85 @@ def test_potential_mode_beats_a_cold_start(pg, tmp_path):
     print(f"potential mode, cold start: Poisson iterations plain {off}, warm {on}; starts {starts}")
     assert starts["starts_network"] == 1
     assert on < off
+
+
+def _sweep_instances(nr=32, nz=32, ppc=16):
+    """Four discharges of the gamma x R_ext sweep on one 32 x 32 grid (the
+    multigrid-preconditioned solve, as above)."""
+    out = []
+    for k, (gamma, rext) in enumerate([(0.05, 50.0), (0.1, 100.0), (0.2, 200.0), (0.3, 400.0)]):
+        p = pic_inputs.params_rz32(gather=0)
+        p.update(nr=nr, nz=nz, L=p["R"] * nz / nr, poisson_tol=1e-10, circuit_mode=1, Vs=400.0,
+                 Rext=rext, n_avg=4, gamma_i=gamma, poisson_precond=1, poisson_max_iter=400,
+                 seed=40 + k)
+        p, parts = pic_inputs.seed_plasma(p, nr * nz * ppc, seed=50 + k, Te_eV=5.0)
+        out.append((pic_inputs.with_capacity(p, parts, factor=2.0), parts))
+    return out
+
+
+def _begin(pg, h, k, parts):
+    for key, sp in (("e", 0), ("i", 1)):
+        pg.pic_set_particles(h, k, sp, parts[key])
+    pg.pic_solve_fields(h, k)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_ensemble_network_equals_single_runs(pg, mode):
+    """One network serves a 4-discharge ensemble.  Every instance records into
+    the one ring (4 snapshots per step) and training runs on the mixed ring.
+    With the warm start on, the batched forward (the 4 instances as one batch)
+    gives each instance the start that a single-instance handle with the same
+    network (parameters and scales) gives it: particles, phi, the step
+    counters, the start choices and the iteration counts equal the single
+    runs bit for bit, under graph replay."""
+    from parity import sort_by_id
+    insts = _sweep_instances()
+    record_steps, steps = 24, 6
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        ens = pg.pic_create([p for p, _ in insts])
+        for k, (_, parts) in enumerate(insts):
+            _begin(pg, ens, k, parts)
+        pg.pic_unet_create(ens, 2, 8, mode)
+        pg.pic_unet_snapshots(ens, 256, 1)
+        pg.pic_step(ens, record_steps)
+        assert pg.pic_unet_stats(ens)["snapshots"] == len(insts) * record_steps
+        first, last = pg.pic_unet_train(ens, 300, 8, 2e-3, seed=3)
+        assert last < first, (first, last)
+        params = pg.pic_unet_get_params(ens)
+        st = pg.pic_unet_stats(ens)
+        pg.pic_unet_warm_start(ens, True)
+        pg.pic_step(ens, steps)
+        assert pg.pic_uses_graph(ens)
+        s1 = pg.pic_unet_stats(ens)
+        totals = {"starts_previous": 0, "starts_network": 0, "starts_zero": 0,
+                  "poisson_iters": 0}
+        for k, (p, parts) in enumerate(insts):
+            one = pg.pic_create(p)
+            _begin(pg, one, 0, parts)
+            pg.pic_step(one, record_steps)   # the state of instance k (FP64: bit for bit)
+            pg.pic_unet_create(one, 2, 1, mode)
+            pg.pic_unet_set_params(one, params)
+            pg.pic_unet_set_norms(one, st["in_norm"], st["out_norm"])
+            pg.pic_unet_warm_start(one, True)
+            pg.pic_step(one, steps)
+            so = pg.pic_unet_stats(one)
+            for key in totals:
+                totals[key] += so[key]
+            for sp in (0, 1):
+                a = sort_by_id(pg.pic_get_particles(ens, k, sp))
+                b = sort_by_id(pg.pic_get_particles(one, 0, sp))
+                for q in a:
+                    assert np.array_equal(a[q], b[q]), (k, sp, q)
+            assert np.array_equal(pg.pic_get_fields(ens, k)["phi"],
+                                  pg.pic_get_fields(one, 0)["phi"]), k
+            da, db = pg.pic_diagnostics(ens, k), pg.pic_diagnostics(one, 0)
+            for key in ("N_e", "N_i", "V_cath", "I_cath", "step", "poisson_iters"):
+                assert da[key] == db[key], (k, key)
+            pg.pic_destroy(one)
+        print(f"mode {mode}: ensemble starts/iterations over {steps} steps:",
+              {key: s1[key] - st[key] for key in totals})
+        for key in totals:
+            assert s1[key] - st[key] == totals[key], key
+        pg.pic_destroy(ens)
+    side.synchronize()
