@@ -532,6 +532,7 @@ def run_learned(args, torch, pg, emit: bool = True):
     t0 = time.perf_counter()
     loss0, loss1 = pg.pic_unet_train(h, args.train_iters, args.train_batch, 2e-3, args.seed + 7)
     t_train = time.perf_counter() - t0
+    pg.pic_unet_record(h, False)   # both arms below without the recording
 
     def measure(on: bool):
         pg.pic_unet_warm_start(h, on)
@@ -630,6 +631,7 @@ def run_combined(args, torch, pg, emit: bool = True, plain_fp64=None):
     t0 = time.perf_counter()
     loss0, loss1 = pg.pic_unet_train(h, args.train_iters, args.train_batch, 2e-3, args.seed + 7)
     t_train = time.perf_counter() - t0
+    pg.pic_unet_record(h, False)   # both arms below without the recording
 
     def psteps():
         return sum(pg.pic_diagnostics(h, k)["particle_steps"] for k in range(n_inst))

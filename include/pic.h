@@ -410,6 +410,11 @@ int pic_unet_loss_grad(pic_handle* h, int batch, const float* x, const float* y,
  * around it.  Recording continues in later pic_step calls.  Synchronous. */
 int pic_unet_snapshots(pic_handle* h, int64_t capacity, int every);
 
+/* Pause (on = 0) or resume (on = 1) the recording into the ring set by
+ * pic_unet_snapshots; the ring and its snapshots are kept (training still
+ * draws from them).  PIC_ERR_INVALID without a ring. */
+int pic_unet_record(pic_handle* h, int on);
+
 /* `iters` Adam steps (beta 0.9, 0.999) of learning rate lr on batches of
  * `batch` snapshots drawn from the ring by a hash of (seed, iteration,
  * index); targets as the mode defines.  *loss_first and *loss_last (may be NULL)

@@ -16,5 +16,5 @@ from .pic import (  # noqa: F401
     pic_profile, pic_profile_read, pic_poisson_workspace_bytes, pic_poisson_solve,
     pic_unet_param_count, pic_unet_create, pic_unet_set_params, pic_unet_get_params,
     pic_unet_loss_grad, pic_unet_snapshots, pic_unet_train, pic_unet_warm_start, pic_unet_stats,
-    pic_unet_set_norms,
+    pic_unet_set_norms, pic_unet_record,
 )

@@ -892,19 +892,15 @@ static cudaError_t launch_ensemble_step(pic_handle* h, const StepMarks* marks) {
   mk(G_SCATTER, true);
   if (e == cudaSuccess) e = launch_post_push_batch(h->d_insts, n, bd, h->num_sms, st);
   mk(G_SCATTER, false);
-  std::vector<Inst> hi;
-  if (h->unet) {
-    for (const InstHost& ih : h->inst) hi.push_back(ih.I);
-    if (e == cudaSuccess && unet_pre_solve_needed(h->unet)) {
-      mk(G_WARM, true);
-      e = launch_pre_solve(h->unet, hi.data(), h->pws.data(), n, st);
-      mk(G_WARM, false);
-    }
+  if (e == cudaSuccess && h->unet && unet_pre_solve_needed(h->unet)) {
+    mk(G_WARM, true);
+    e = launch_pre_solve(h->unet, h->d_insts, h->d_pargs, n, st);
+    mk(G_WARM, false);
   }
   mk(G_POISSON, true);
   if (e == cudaSuccess) e = launch_poisson_group(h->pws.data(), nullptr, n, h->d_pargs, h->num_sms, st);
   mk(G_POISSON, false);
-  if (e == cudaSuccess && h->unet) e = launch_after_solve(h->unet, hi.data(), n, st);
+  if (e == cudaSuccess && h->unet) e = launch_after_solve(h->unet, h->d_insts, n, st);
   mk(G_STEP_END, true);
   if (e == cudaSuccess) e = launch_step_end_batch(h->d_insts, n, st);
   mk(G_STEP_END, false);
@@ -914,10 +910,15 @@ static cudaError_t launch_ensemble_step(pic_handle* h, const StepMarks* marks) {
 // launches around the Poisson solve of a single-instance step: the learned
 // warm start before it, snapshot recording and iteration counts after it
 static cudaError_t hook_pre_poisson(void* ctx, const Inst& I, PoissonWork* pw, cudaStream_t st) {
-  return launch_pre_solve(((pic_handle*)ctx)->unet, &I, &pw, 1, st);
+  (void)I;
+  (void)pw;
+  const pic_handle* h = (const pic_handle*)ctx;
+  return launch_pre_solve(h->unet, h->d_insts, h->d_pargs, 1, st);
 }
 static cudaError_t hook_post_poisson(void* ctx, const Inst& I, cudaStream_t st) {
-  return launch_after_solve(((pic_handle*)ctx)->unet, &I, 1, st);
+  (void)I;
+  const pic_handle* h = (const pic_handle*)ctx;
+  return launch_after_solve(h->unet, h->d_insts, 1, st);
 }
 
 static cudaError_t launch_all(pic_handle* h, const StepMarks* marks) {
@@ -1516,6 +1517,15 @@ int pic_unet_train(pic_handle* h, int iters, int batch, float lr, uint64_t seed,
   if (e == cudaErrorInvalidValue) return fail(h, PIC_ERR_INVALID, "no snapshot recorded yet");
   if (e == cudaErrorTimeout) return fail(h, PIC_ERR_TIMEOUT, "tensor-core wait reached its limit");
   if (e != cudaSuccess) return cuda_fail(h, e, "unet_train");
+  return PIC_OK;
+}
+
+int pic_unet_record(pic_handle* h, int on) {
+  const int rc = need_unet(h);
+  if (rc != PIC_OK) return rc;
+  if (!unet_recording(h->unet)) return fail(h, PIC_ERR_INVALID, "no snapshot ring (pic_unet_snapshots)");
+  unet_set_record(h->unet, on != 0);
+  drop_graph(h);
   return PIC_OK;
 }
 

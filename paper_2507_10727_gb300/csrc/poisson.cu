@@ -1262,10 +1262,21 @@ __device__ __forceinline__ double start_value(int k, const double* phi, const do
   return k == 1 ? cand[i] : 0.0;
 }
 
-// Score of a start: ||Q - A x||_2^2 over the free nodes.
-__global__ void __launch_bounds__(256) k_guess_norms(PoissonWork W, const double* Q, const double* phi,
-                                                     const double* cand, double* partial) {
+// The warm-start pieces run over all instances of a handle at once:
+// blockIdx.y = instance k, its operator, Q and phi from A[k] (the device
+// PoissonArgs of the grouped solve), its node fields at offset k * stride of
+// the per-instance buffers.
+
+// Score of a start: ||Q - A x||_2^2 over the free nodes; partial[k][j][b]
+// for start j of instance k from block b.
+__global__ void __launch_bounds__(256) k_guess_norms(const PoissonArgs* A, const double* cand_all,
+                                                     long long stride, double* partial) {
   __shared__ double red[3][8];
+  const int k = blockIdx.y;
+  const PoissonWork& W = A[k].W;
+  const double* Q = A[k].Q;
+  const double* phi = A[k].phi;
+  const double* cand = cand_all + k * stride;
   const int nr = W.nr, nz = W.nz, nz1 = nz + 1;
   const long long nn = (long long)(nr + 1) * nz1;
   const int dm[4] = {-1, 1, 0, 0}, dn[4] = {0, 0, -1, 1};
@@ -1278,68 +1289,82 @@ __global__ void __launch_bounds__(256) k_guess_norms(PoissonWork W, const double
     double c[4];
     node_coup(W, m, n, c);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const double xi = start_value(k, phi, cand, true, i);
+    for (int j = 0; j < 3; ++j) {
+      const double xi = start_value(j, phi, cand, true, i);
       double a = 0.0;
 #pragma unroll
       for (int d = 0; d < 4; ++d) {
         if (c[d] == 0.0) continue;
         const int mm = m + dm[d], nn2 = n + dn[d];
-        a += c[d] * (xi - start_value(k, phi, cand, free_node(W, mm, nn2), mm * nz1 + nn2));
+        a += c[d] * (xi - start_value(j, phi, cand, free_node(W, mm, nn2), mm * nz1 + nn2));
       }
       const double r = Q[i] - a;
-      loc[k] += r * r;
+      loc[j] += r * r;
     }
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const double s = warp_sum64(loc[k]);
-    if (lane == 0) red[k][w] = s;
+  for (int j = 0; j < 3; ++j) {
+    const double s = warp_sum64(loc[j]);
+    if (lane == 0) red[j][w] = s;
   }
   __syncthreads();
   if (threadIdx.x < 3) {
     double s = 0.0;
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[threadIdx.x][q];
-    partial[(long long)threadIdx.x * gridDim.x + blockIdx.x] = s;
+    partial[((long long)k * 3 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
   }
 }
 
-__global__ void k_guess_pick(const double* partial, int nblk, UDev* ud, const int* status) {
+// one block per instance: the start with the smallest score (block-ordered
+// sums); counts summed over the instances, ud->choice = the last instance's
+__global__ void k_guess_pick(const PoissonArgs* A, const double* partial, int nblk, UDev* ud,
+                             int* choice) {
   __shared__ double tot[3];
+  const int k = blockIdx.x;
   if (threadIdx.x < 3) {
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += partial[(long long)threadIdx.x * nblk + b];
+    const double* p = partial + ((long long)k * 3 + threadIdx.x) * nblk;
+    for (int b = 0; b < nblk; ++b) s += p[b];
     tot[threadIdx.x] = s;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    if (*status & ST_FATAL) {
-      ud->choice = 0;
-      return;
-    }
     int best = 0;
-    for (int k = 1; k < 3; ++k)
-      if (tot[k] < tot[best]) best = k;   // NaN norms never win
-    ud->choice = best;
-    ud->n_choice[best] += 1;
+    if (!(*A[k].status & ST_FATAL)) {
+      for (int j = 1; j < 3; ++j)
+        if (tot[j] < tot[best]) best = j;   // NaN norms never win
+      atomicAdd((unsigned long long*)&ud->n_choice[best], 1ULL);
+    }
+    choice[k] = best;
+    if (k == (int)gridDim.x - 1) ud->choice = best;
   }
 }
 
-__global__ void k_guess_apply(PoissonWork W, double* phi, const double* cand, const UDev* ud) {
-  const int choice = ud->choice;
-  if (choice == 0) return;
+__global__ void k_guess_apply(const PoissonArgs* A, const double* cand_all, long long stride,
+                              const int* choice) {
+  const int k = blockIdx.y;
+  const int c = choice[k];
+  if (c == 0) return;
+  const PoissonWork& W = A[k].W;
+  double* phi = A[k].phi;
+  const double* cand = cand_all + k * stride;
   const int nz1 = W.nz + 1;
   const long long nn = (long long)(W.nr + 1) * nz1;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn;
        e += (long long)gridDim.x * blockDim.x) {
     const int m = (int)(e / nz1), n = (int)(e - (long long)m * nz1);
-    if (free_node(W, m, n)) phi[e] = choice == 1 ? cand[e] : 0.0;
+    if (free_node(W, m, n)) phi[e] = c == 1 ? cand[e] : 0.0;
   }
 }
 
 // res = Q - A phi on free nodes, 0 on Dirichlet nodes
-__global__ void k_residual32(PoissonWork W, const double* Q, const double* phi, float* res) {
+__global__ void k_residual32(const PoissonArgs* A, float* res_all, long long stride) {
+  const int k = blockIdx.y;
+  const PoissonWork& W = A[k].W;
+  const double* Q = A[k].Q;
+  const double* phi = A[k].phi;
+  float* res = res_all + k * stride;
   const int nr = W.nr, nz = W.nz, nz1 = nz + 1;
   const long long nn = (long long)(nr + 1) * nz1;
   const int off[4] = {-nz1, nz1, -1, 1};
@@ -1361,7 +1386,11 @@ __global__ void k_residual32(PoissonWork W, const double* Q, const double* phi, 
 }
 
 // one colour of a red-black Gauss-Seidel sweep on A x = Q
-__global__ void k_gs_color(PoissonWork W, const double* Q, double* x, int color) {
+__global__ void k_gs_color(const PoissonArgs* A, double* x_all, long long stride, int color) {
+  const int k = blockIdx.y;
+  const PoissonWork& W = A[k].W;
+  const double* Q = A[k].Q;
+  double* x = x_all + k * stride;
   const int nr = W.nr, nz = W.nz, nz1 = nz + 1;
   const long long nn = (long long)(nr + 1) * nz1;
   const int off[4] = {-nz1, nz1, -1, 1};
@@ -1373,10 +1402,10 @@ __global__ void k_gs_color(PoissonWork W, const double* Q, double* x, int color)
     node_coup(W, m, n, c);
     double s = Q[i], d = 0.0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (c[k] != 0.0) {
-        s += c[k] * x[i + off[k]];
-        d += c[k];
+    for (int q = 0; q < 4; ++q)
+      if (c[q] != 0.0) {
+        s += c[q] * x[i + off[q]];
+        d += c[q];
       }
     x[i] = s / d;
   }
@@ -1390,31 +1419,32 @@ int guess_blocks(int nr, int nz) {
   return (int)b;
 }
 
-cudaError_t launch_residual32(PoissonWork* pw, const double* Q, const double* phi, float* res,
+cudaError_t launch_residual32(const void* pargs, int n, int nr, int nz, float* res,
                               cudaStream_t st) {
-  const long long nn = (long long)(pw->nr + 1) * (pw->nz + 1);
-  long long b = (nn + 255) / 256;
-  if (b > 592) b = 592;
-  k_residual32<<<(int)b, 256, 0, st>>>(*pw, Q, phi, res);
+  const long long nn = (long long)(nr + 1) * (nz + 1);
+  k_residual32<<<dim3(guess_blocks(nr, nz), n), 256, 0, st>>>((const PoissonArgs*)pargs, res, nn);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gs_sweeps(PoissonWork* pw, const double* Q, double* x, int sweeps,
+cudaError_t launch_gs_sweeps(const void* pargs, int n, int nr, int nz, double* x, int sweeps,
                              cudaStream_t st) {
-  const int nb = guess_blocks(pw->nr, pw->nz);
+  const long long nn = (long long)(nr + 1) * (nz + 1);
+  const dim3 grid(guess_blocks(nr, nz), n);
   for (int s = 0; s < sweeps; ++s) {
-    k_gs_color<<<nb, 256, 0, st>>>(*pw, Q, x, 0);
-    k_gs_color<<<nb, 256, 0, st>>>(*pw, Q, x, 1);
+    k_gs_color<<<grid, 256, 0, st>>>((const PoissonArgs*)pargs, x, nn, 0);
+    k_gs_color<<<grid, 256, 0, st>>>((const PoissonArgs*)pargs, x, nn, 1);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_guess_select(PoissonWork* pw, const double* Q, double* phi, const double* cand,
-                                double* partial, int nblk, UDev* ud, const int* status,
-                                cudaStream_t st) {
-  k_guess_norms<<<nblk, 256, 0, st>>>(*pw, Q, phi, cand, partial);
-  k_guess_pick<<<1, 32, 0, st>>>(partial, nblk, ud, status);
-  k_guess_apply<<<nblk, 256, 0, st>>>(*pw, phi, cand, ud);
+cudaError_t launch_guess_select(const void* pargs, int n, int nr, int nz, const double* cand,
+                                double* partial, UDev* ud, int* choice, cudaStream_t st) {
+  const long long nn = (long long)(nr + 1) * (nz + 1);
+  const int nblk = guess_blocks(nr, nz);
+  const PoissonArgs* A = (const PoissonArgs*)pargs;
+  k_guess_norms<<<dim3(nblk, n), 256, 0, st>>>(A, cand, nn, partial);
+  k_guess_pick<<<n, 32, 0, st>>>(A, partial, nblk, ud, choice);
+  k_guess_apply<<<dim3(nblk, n), 256, 0, st>>>(A, cand, nn, choice);
   return cudaGetLastError();
 }
 

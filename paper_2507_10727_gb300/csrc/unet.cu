@@ -678,15 +678,24 @@ __global__ void k_train_input(const float* f0, const float* f1, const float* slo
   }
 }
 
-// network input of one instance from its live state (its sample of the
+// The per-step kernels run over all instances of a handle at once:
+// blockIdx.y (grid-stride kernels) or blockIdx.x (one-CTA kernels) = instance
+// k, read from the device array insts; instance k's node fields sit at
+// offset k * npx of the per-instance buffers.
+
+// network input of each instance from its live state (sample k of the
 // batch): mode 0 from rho = Q / V and phi's Dirichlet values, mode 1 from the
-// residual of the previous solution scaled by its RMS *scale
-__global__ void k_step_input(Inst I, const UDev* ud, int mode, const float* res,
-                             const double* scale, bf16* x_in) {
+// residual of the previous solution scaled by its RMS scale[k]
+__global__ void k_step_input(const Inst* insts, const UDev* ud, int mode, const float* res_all,
+                             const double* scale, bf16* x_all) {
+  const int k = blockIdx.y;
+  const Inst& I = insts[k];
   const int W = I.nz + 1;
   const long long npx = (long long)(I.nr + 1) * W;
   if (I.S->status & ST_FATAL) return;
-  const double inv_in = 1.0 / (mode == 0 ? ud->in_norm : *scale);
+  const float* res = res_all + k * npx;
+  bf16* x_in = x_all + k * npx * kInPad;
+  const double inv_in = 1.0 / (mode == 0 ? ud->in_norm : scale[k]);
   const double inv_out = 1.0 / ud->out_norm;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
        q += (long long)gridDim.x * blockDim.x) {
@@ -708,26 +717,38 @@ __global__ void k_step_input(Inst I, const UDev* ud, int mode, const float* res,
   }
 }
 
-// candidate start from the network output (Dirichlet values of phi)
-__global__ void k_make_cand(int nr, int nz, int g, int wall, const double* phi, const float* net,
-                            const UDev* ud, const double* scale, int mode, double* cand) {
-  const int W = nz + 1;
-  const long long npx = (long long)(nr + 1) * W;
-  const double s = mode == 0 ? ud->out_norm : *scale * (ud->out_norm / ud->in_norm);
+// candidate start of each instance from its network output (Dirichlet
+// values of phi)
+__global__ void k_make_cand(const Inst* insts, const float* net_all, const UDev* ud,
+                            const double* scale, int mode, double* cand_all) {
+  const int k = blockIdx.y;
+  const Inst& I = insts[k];
+  const int W = I.nz + 1;
+  const long long npx = (long long)(I.nr + 1) * W;
+  const float* net = net_all + k * npx;
+  double* cand = cand_all + k * npx;
+  const double* phi = I.phi;
+  const double s = mode == 0 ? ud->out_norm : scale[k] * (ud->out_norm / ud->in_norm);
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
        q += (long long)gridDim.x * blockDim.x) {
     const int m = (int)(q / W), n = (int)(q - (long long)m * W);
-    if (dirichlet_node(m, n, nr, nz, g, wall)) cand[q] = phi[q];
+    if (dirichlet_node(m, n, I.nr, I.nz, I.bc_g, I.bc_wall)) cand[q] = phi[q];
     else cand[q] = (mode == 0 ? 0.0 : phi[q]) + s * (double)net[q];
   }
 }
 
-// Recording: instance k of a recording step (the clock's step a multiple of
+// Recording: instance k of a recording step (instance 0's step a multiple of
 // `every`) writes slot (snap_count + k) mod cap.
+__device__ __forceinline__ bool records(const Inst* insts, const Inst& I, int every) {
+  return !(I.S->status & ST_FATAL) && (insts[0].S->step % every) == 0;
+}
+
 // mode 0 recording (after the solve): rho and phi
-__global__ void k_snap_record(Inst I, const Scalars* clock, const UDev* ud, float* f0, float* f1,
-                              long long cap, int every, int k) {
-  if ((I.S->status & ST_FATAL) || (clock->step % every) != 0) return;
+__global__ void k_snap_record(const Inst* insts, const UDev* ud, float* f0, float* f1,
+                              long long cap, int every) {
+  const int k = blockIdx.y;
+  const Inst& I = insts[k];
+  if (!records(insts, I, every)) return;
   const int W = I.nz + 1;
   const long long npx = (long long)(I.nr + 1) * W;
   const long long slot = (ud->snap_count + k) % cap;
@@ -741,11 +762,15 @@ __global__ void k_snap_record(Inst I, const Scalars* clock, const UDev* ud, floa
 
 // mode 1 recording, before the solve: the residual of the previous solution
 // into the slot, the previous solution kept in FP64
-__global__ void k_snap_pre(Inst I, const Scalars* clock, const UDev* ud, const float* res,
-                           float* f0, double* phi_prev, long long cap, int every, int k) {
-  if ((I.S->status & ST_FATAL) || (clock->step % every) != 0) return;
+__global__ void k_snap_pre(const Inst* insts, const UDev* ud, const float* res_all, float* f0,
+                           double* phi_prev_all, long long cap, int every) {
+  const int k = blockIdx.y;
+  const Inst& I = insts[k];
+  if (!records(insts, I, every)) return;
   const long long npx = (long long)(I.nr + 1) * (I.nz + 1);
   const long long slot = (ud->snap_count + k) % cap;
+  const float* res = res_all + k * npx;
+  double* phi_prev = phi_prev_all + k * npx;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
        q += (long long)gridDim.x * blockDim.x) {
     f0[slot * npx + q] = res[q];
@@ -754,11 +779,14 @@ __global__ void k_snap_pre(Inst I, const Scalars* clock, const UDev* ud, const f
 }
 
 // mode 1 recording, after the solve: the change of phi
-__global__ void k_snap_post(Inst I, const Scalars* clock, const UDev* ud, float* f1,
-                            const double* phi_prev, long long cap, int every, int k) {
-  if ((I.S->status & ST_FATAL) || (clock->step % every) != 0) return;
+__global__ void k_snap_post(const Inst* insts, const UDev* ud, float* f1,
+                            const double* phi_prev_all, long long cap, int every) {
+  const int k = blockIdx.y;
+  const Inst& I = insts[k];
+  if (!records(insts, I, every)) return;
   const long long npx = (long long)(I.nr + 1) * (I.nz + 1);
   const long long slot = (ud->snap_count + k) % cap;
+  const double* phi_prev = phi_prev_all + k * npx;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
        q += (long long)gridDim.x * blockDim.x)
     f1[slot * npx + q] = (float)(I.phi[q] - phi_prev[q]);
@@ -786,30 +814,35 @@ __device__ void cta_rms(const float* f, long long n, double* out_d, float* out_f
   }
 }
 
-// mode-1 recording: RMS of the residual just stored in the current slot
-__global__ void __launch_bounds__(1024) k_slot_rms(Inst I, const Scalars* clock, const UDev* ud,
+// mode-1 recording: RMS of the residual just stored in instance k's slot
+// (one CTA per instance)
+__global__ void __launch_bounds__(1024) k_slot_rms(const Inst* insts, const UDev* ud,
                                                    const float* f0, float* slot_scale,
-                                                   long long cap, int every, int k) {
-  if ((I.S->status & ST_FATAL) || (clock->step % every) != 0) return;
+                                                   long long cap, int every) {
+  const int k = blockIdx.x;
+  const Inst& I = insts[k];
+  if (!records(insts, I, every)) return;
   const long long npx = (long long)(I.nr + 1) * (I.nz + 1);
   const long long slot = (ud->snap_count + k) % cap;
   cta_rms(f0 + slot * npx, npx, nullptr, slot_scale + slot);
 }
 
-// mode-1 warm start: RMS of an instance's live residual
-__global__ void __launch_bounds__(1024) k_live_rms(const float* res, long long npx, double* scale) {
-  cta_rms(res, npx, scale, nullptr);
+// mode-1 warm start: RMS of each instance's live residual (one CTA each)
+__global__ void __launch_bounds__(1024) k_live_rms(const float* res_all, long long npx,
+                                                   double* scale) {
+  cta_rms(res_all + blockIdx.x * npx, npx, scale + blockIdx.x, nullptr);
 }
 
-// after an instance's solve: its iterations; the last instance of a
-// recording step advances the ring by `inc` (the instances of the step)
-__global__ void k_after_solve(Inst I, const Scalars* clock, UDev* ud, int every, int record,
-                              int inc) {
+// after the solves: each instance's iterations; a recording step advances
+// the ring by n (one thread, instances in order)
+__global__ void k_after_solve(const Inst* insts, int n, UDev* ud, int every, int record) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  Scalars* S = I.S;
-  if (ud->err) atomicOr(&S->status, ST_TIMEOUT);
-  if (!(S->status & ST_FATAL)) ud->iters_total += S->poisson_iters;
-  if (record && inc > 0 && (clock->step % every) == 0) ud->snap_count += inc;
+  for (int k = 0; k < n; ++k) {
+    Scalars* S = insts[k].S;
+    if (ud->err) atomicOr(&S->status, ST_TIMEOUT);
+    if (!(S->status & ST_FATAL)) ud->iters_total += S->poisson_iters;
+  }
+  if (record && (insts[0].S->step % every) == 0) ud->snap_count += n;
 }
 
 // mean square of a recorded field over the stored snapshots (input and
@@ -937,10 +970,12 @@ struct UNet {
   float* res = nullptr;        // residual of the previous solution (mode 1)
   double* phi_prev = nullptr;  // previous solution (mode-1 recording)
   double* scale = nullptr;     // mode 1: RMS of the live residual of this step
+  int* choice = nullptr;       // start chosen for each instance's solve
   float *snap_f0 = nullptr, *snap_f1 = nullptr;
   float* slot_scale = nullptr;  // mode 1: residual RMS of each snapshot
   long long snap_cap = 0;
   int snap_every = 1;
+  bool rec_on = true;          // recording into the ring (paused by unet_set_record)
   int bc_g = 0, bc_wall = 0;   // insulating boundary nodes (field_free), set at creation
   bool warm = false;
   long long adam_t = 0;
@@ -1295,6 +1330,7 @@ UNet* unet_create(int nr, int nz, int bmax, int n_inst, int mode, unsigned long 
   u->res = (float*)A((size_t)n_inst * u->npx(0) * 4);
   u->phi_prev = (double*)A((size_t)n_inst * u->npx(0) * 8);
   u->scale = (double*)A((size_t)n_inst * 8);
+  u->choice = (int*)A((size_t)n_inst * 4);
   if (!ok) {
     delete u;
     return nullptr;
@@ -1400,68 +1436,50 @@ cudaError_t unet_snapshots(UNet* u, long long cap, int every, UAllocFn alloc, vo
 
 bool unet_recording(const UNet* u) { return u->snap_cap > 0; }
 
-bool unet_pre_solve_needed(const UNet* u) { return u->warm || (u->mode == 1 && u->snap_cap > 0); }
+static bool rec_live(const UNet* u) { return u->snap_cap > 0 && u->rec_on; }
+void unet_set_record(UNet* u, bool on) { u->rec_on = on; }
+bool unet_pre_solve_needed(const UNet* u) { return u->warm || (u->mode == 1 && rec_live(u)); }
 
-cudaError_t launch_pre_solve(UNet* u, const Inst* insts, PoissonWork* const* pws, int n,
+cudaError_t launch_pre_solve(UNet* u, const Inst* d_insts, const void* d_pargs, int n,
                              cudaStream_t st) {
   if (n < 1 || n > u->n_inst) return cudaErrorInvalidValue;
   const long long npx = u->npx(0);
-  const int g0 = grid1(npx, 256);
-  const Scalars* clock = insts[0].S;
+  const dim3 g0(grid1(npx, 256), n);
   cudaError_t e = cudaSuccess;
   if (u->mode == 1) {
-    for (int k = 0; k < n; ++k) {
-      const Inst& I = insts[k];
-      float* res = u->res + k * npx;
-      e = launch_residual32(pws[k], I.Q, I.phi, res, st);
-      if (e) return e;
-      if (u->snap_cap > 0) {
-        k_snap_pre<<<g0, 256, 0, st>>>(I, clock, u->ud, res, u->snap_f0, u->phi_prev + k * npx,
-                                       u->snap_cap, u->snap_every, k);
-        k_slot_rms<<<1, 1024, 0, st>>>(I, clock, u->ud, u->snap_f0, u->slot_scale, u->snap_cap,
-                                       u->snap_every, k);
-      }
-      if (u->warm) k_live_rms<<<1, 1024, 0, st>>>(res, npx, u->scale + k);
+    e = launch_residual32(d_pargs, n, u->nr, u->nz, u->res, st);
+    if (e) return e;
+    if (rec_live(u)) {
+      k_snap_pre<<<g0, 256, 0, st>>>(d_insts, u->ud, u->res, u->snap_f0, u->phi_prev, u->snap_cap,
+                                     u->snap_every);
+      k_slot_rms<<<n, 1024, 0, st>>>(d_insts, u->ud, u->snap_f0, u->slot_scale, u->snap_cap,
+                                     u->snap_every);
     }
+    if (u->warm) k_live_rms<<<n, 1024, 0, st>>>(u->res, npx, u->scale);
   }
   if (!u->warm) return cudaGetLastError();
   // the inputs of all instances as one batch of the forward pass
-  for (int k = 0; k < n; ++k)
-    k_step_input<<<g0, 256, 0, st>>>(insts[k], u->ud, u->mode, u->res + k * npx, u->scale + k,
-                                     u->x_in + k * npx * kInPad);
+  k_step_input<<<g0, 256, 0, st>>>(d_insts, u->ud, u->mode, u->res, u->scale, u->x_in);
   e = forward(u, n, st);
   if (e) return e;
-  for (int k = 0; k < n && e == cudaSuccess; ++k) {
-    const Inst& I = insts[k];
-    double* cand = u->cand + k * npx;
-    k_make_cand<<<g0, 256, 0, st>>>(u->nr, u->nz, I.bc_g, I.bc_wall, I.phi, u->out + k * npx, u->ud,
-                                    u->scale + k, u->mode, cand);
-    e = launch_gs_sweeps(pws[k], I.Q, cand, 2, st);
-    if (e == cudaSuccess)
-      e = launch_guess_select(pws[k], I.Q, I.phi, cand, u->gpart + (size_t)k * u->gblk * 3,
-                              u->gblk, u->ud, &I.S->status, st);
-  }
-  return e;
+  k_make_cand<<<g0, 256, 0, st>>>(d_insts, u->out, u->ud, u->scale, u->mode, u->cand);
+  e = launch_gs_sweeps(d_pargs, n, u->nr, u->nz, u->cand, 2, st);
+  if (e) return e;
+  return launch_guess_select(d_pargs, n, u->nr, u->nz, u->cand, u->gpart, u->ud, u->choice, st);
 }
 
-cudaError_t launch_after_solve(UNet* u, const Inst* insts, int n, cudaStream_t st) {
+cudaError_t launch_after_solve(UNet* u, const Inst* d_insts, int n, cudaStream_t st) {
   if (n < 1 || n > u->n_inst) return cudaErrorInvalidValue;
-  const long long npx = u->npx(0);
-  const int g0 = grid1(npx, 256);
-  const Scalars* clock = insts[0].S;
-  for (int k = 0; k < n; ++k) {
-    const Inst& I = insts[k];
-    if (u->snap_cap > 0) {
-      if (u->mode == 0)
-        k_snap_record<<<g0, 256, 0, st>>>(I, clock, u->ud, u->snap_f0, u->snap_f1, u->snap_cap,
-                                          u->snap_every, k);
-      else
-        k_snap_post<<<g0, 256, 0, st>>>(I, clock, u->ud, u->snap_f1, u->phi_prev + k * npx,
-                                        u->snap_cap, u->snap_every, k);
-    }
-    k_after_solve<<<1, 32, 0, st>>>(I, clock, u->ud, u->snap_every, u->snap_cap > 0 ? 1 : 0,
-                                    k == n - 1 ? n : 0);
+  const dim3 g0(grid1(u->npx(0), 256), n);
+  if (rec_live(u)) {
+    if (u->mode == 0)
+      k_snap_record<<<g0, 256, 0, st>>>(d_insts, u->ud, u->snap_f0, u->snap_f1, u->snap_cap,
+                                        u->snap_every);
+    else
+      k_snap_post<<<g0, 256, 0, st>>>(d_insts, u->ud, u->snap_f1, u->phi_prev, u->snap_cap,
+                                      u->snap_every);
   }
+  k_after_solve<<<1, 32, 0, st>>>(d_insts, n, u->ud, u->snap_every, rec_live(u) ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -76,6 +76,8 @@ cudaError_t unet_loss_grad(UNet* u, int B, const float* x, const float* y, float
 // mode 0 (rho, phi), mode 1 (res, phi - phi_prev)
 cudaError_t unet_snapshots(UNet* u, long long cap, int every, UAllocFn alloc, void* ctx);
 bool unet_recording(const UNet* u);
+// pause (false) / resume (true) the recording into the ring
+void unet_set_record(UNet* u, bool on);
 
 // Adam training on the snapshot ring
 cudaError_t unet_train(UNet* u, int iters, int batch, float lr, unsigned long long seed,
@@ -86,26 +88,30 @@ cudaError_t unet_train(UNet* u, int iters, int batch, float lr, unsigned long lo
 void unet_set_warm(UNet* u, bool on);
 bool unet_warm(const UNet* u);
 bool unet_pre_solve_needed(const UNet* u);
-// start of the n instances insts[0..n) (host copies) with workspaces pws
-// (n at most the n_inst of the network); instance 0's step counter is the
-// recording clock of all
-cudaError_t launch_pre_solve(UNet* u, const Inst* insts, PoissonWork* const* pws, int n,
+// before the solves of the n instances of a handle (n at most the network's
+// n_inst): d_insts and d_pargs are the handle's device copies of the
+// instances and of their solve arguments (only fields fixed at creation are
+// read: grid, boundary kinds, Q, phi, the scalars); instance 0's step counter
+// is the recording clock of all
+cudaError_t launch_pre_solve(UNet* u, const Inst* d_insts, const void* d_pargs, int n,
                              cudaStream_t st);
 // after the solves: recording and iteration count bookkeeping
-cudaError_t launch_after_solve(UNet* u, const Inst* insts, int n, cudaStream_t st);
+cudaError_t launch_after_solve(UNet* u, const Inst* d_insts, int n, cudaStream_t st);
 
-// operator pieces (poisson.cu), all on the fine FP64 operator of the solve
+// operator pieces (poisson.cu), all on the fine FP64 operator of the solve,
+// over the n instances of the device PoissonArgs array pargs at once
+// (instance k's node fields at offset k (nr+1)(nz+1) of res, x, cand)
 // res = Q - A phi on free nodes (0 on Dirichlet nodes), FP32 output
-cudaError_t launch_residual32(PoissonWork* pw, const double* Q, const double* phi, float* res,
+cudaError_t launch_residual32(const void* pargs, int n, int nr, int nz, float* res,
                               cudaStream_t st);
 // `sweeps` red-black Gauss-Seidel sweeps on A x = Q (Dirichlet values in x)
-cudaError_t launch_gs_sweeps(PoissonWork* pw, const double* Q, double* x, int sweeps,
+cudaError_t launch_gs_sweeps(const void* pargs, int n, int nr, int nz, double* x, int sweeps,
                              cudaStream_t st);
-// start of the solve: of x in {phi, cand, 0} (Dirichlet values of phi) the
-// one with the smallest residual norm is copied into phi; counts in *ud
-cudaError_t launch_guess_select(PoissonWork* pw, const double* Q, double* phi, const double* cand,
-                                double* partial, int nblk, UDev* ud, const int* status,
-                                cudaStream_t st);
+// start of each solve: of x in {phi, cand, 0} (Dirichlet values of phi) the
+// one with the smallest residual norm is copied into phi; choice[k] = the
+// start of instance k, counts in *ud; partial: n * 3 * guess_blocks doubles
+cudaError_t launch_guess_select(const void* pargs, int n, int nr, int nz, const double* cand,
+                                double* partial, UDev* ud, int* choice, cudaStream_t st);
 int guess_blocks(int nr, int nz);
 
 }  // namespace pic

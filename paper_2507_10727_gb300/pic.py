@@ -170,6 +170,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         L.pic_unet_train.argtypes = [vp, C.c_int, C.c_int, C.c_float, C.c_uint64, _D, _D]
         L.pic_unet_warm_start.argtypes = [vp, C.c_int]
         L.pic_unet_set_norms.argtypes = [vp, C.c_double, C.c_double]
+        L.pic_unet_record.argtypes = [vp, C.c_int]
         L.pic_unet_stats_read.argtypes = [vp, C.POINTER(PicUnetStats)]
         L.pic_poisson_workspace_bytes.argtypes = [C.c_int, C.c_int]
         L.pic_poisson_workspace_bytes.restype = C.c_size_t
@@ -519,6 +520,10 @@ def pic_unet_train(h: Handle, iters: int, batch: int, lr: float, seed: int = 0):
     a, b = C.c_double(), C.c_double()
     _check(h, load_library().pic_unet_train(h.ptr, iters, batch, lr, seed, C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def pic_unet_record(h: Handle, on: bool = True):
+    _check(h, load_library().pic_unet_record(h.ptr, 1 if on else 0))
 
 
 def pic_unet_set_norms(h: Handle, in_norm: float, out_norm: float):

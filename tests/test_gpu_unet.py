@@ -258,7 +258,8 @@ def _begin(pg, h, k, parts):
 @pytest.mark.parametrize("mode", [0, 1])
 def test_ensemble_network_equals_single_runs(pg, mode):
     """One network serves a 4-discharge ensemble.  Every instance records into
-    the one ring (4 snapshots per step) and training runs on the mixed ring.
+    the one ring (4 snapshots per step), training runs on the mixed ring, and
+    the recording is then paused.
     With the warm start on, the batched forward (the 4 instances as one batch)
     gives each instance the start that a single-instance handle with the same
     network (parameters and scales) gives it: particles, phi, the step
@@ -279,11 +280,13 @@ def test_ensemble_network_equals_single_runs(pg, mode):
         first, last = pg.pic_unet_train(ens, 300, 8, 2e-3, seed=3)
         assert last < first, (first, last)
         params = pg.pic_unet_get_params(ens)
+        pg.pic_unet_record(ens, False)
         st = pg.pic_unet_stats(ens)
         pg.pic_unet_warm_start(ens, True)
         pg.pic_step(ens, steps)
         assert pg.pic_uses_graph(ens)
         s1 = pg.pic_unet_stats(ens)
+        assert s1["snapshots"] == st["snapshots"]   # recording paused
         totals = {"starts_previous": 0, "starts_network": 0, "starts_zero": 0,
                   "poisson_iters": 0}
         for k, (p, parts) in enumerate(insts):
