@@ -15,9 +15,9 @@
 // nodes.  One thread issues the 9 MMAs of a chunk; the next chunk is staged
 // while they run (two stages, mbarrier completion); the epilogue reads the
 // accumulator with tcgen05.ld.  The data gradient is the same kernel on
-// flipped, transposed weights.  The weight gradient contracts over nodes with
-// ldmatrix + mma.sync (9 warps = 9 taps, split-K over tiles, deterministic
-// reduction).
+// flipped, transposed weights.  The weight gradient contracts over nodes on
+// the same tensor cores (operands transposed into K-major tiles by
+// ldmatrix.trans, split-K over tiles, deterministic reduction).
 #include <cmath>
 #include <cstring>
 #include <random>
@@ -42,11 +42,8 @@ constexpr int kNumConv = 14;
 constexpr int kHead = 14;
 constexpr int kNumLayers = 15;
 
-constexpr int kTH = 8, kTW = 16;              // output tile: rows x columns
-constexpr int kPH = kTH + 2, kPW = kTW + 2;   // input halo patch
-constexpr int kPS = 24;                       // bf16 per staged row (16 + 8 pad = 48 bytes)
-constexpr int kWgThreads = 288;               // 9 warps = 9 taps
-constexpr int kMaxSplit = 608;                // 4 x 152 weight-gradient CTAs
+constexpr int kWgThreads = 256;               // weight gradient: 8 warps stage, 2 read TMEM
+constexpr int kMaxSplit = 608;                // bound of splits x input chunks (partials)
 constexpr int kHeadVals = 18;                 // loss, d bias, d w[16]
 
 // ---------------------------------------------------------------------------
@@ -70,16 +67,6 @@ __device__ __forceinline__ void ldsm_x4_t(unsigned& r0, unsigned& r1, unsigned& 
                : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
                : "r"(smem_u32(p)));
 }
-// D += A (16x16, row) * B (16x8, col), BF16 in, FP32 accumulate
-__device__ __forceinline__ void mma_bf16(float* d, unsigned a0, unsigned a1, unsigned a2,
-                                         unsigned a3, unsigned b0, unsigned b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
 __device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
   // splitmix64 finaliser (Steele, Lea, Flood 2014)
   x += 0x9E3779B97F4A7C15ULL;
@@ -332,8 +319,22 @@ __global__ void __launch_bounds__(kTcThreads) k_conv3_tc(ConvArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// weight gradient: dW[co][ci][tap] = sum over nodes of dZ[node][co] *
-// X[node + tap][ci]; CTA (ci chunk, split s) runs over tiles s, s + S, ...
+// Weight gradient on the tensor cores: dW[co][ci][tap] = sum over nodes of
+// dZ[node][co] X[node + (dr - 1, dc - 1)][ci], tap = 3 dr + dc.  A CTA (input
+// channel chunk kc, split s) runs over output tiles of 8 x 16 nodes, t = s,
+// s + S, ...  Per tile the input patch (10 x 18 nodes x 16 channels) and the
+// dZ tile (128 nodes x COUT) are staged node-major by cp.async (two buffers:
+// the next tile loads while this one is transposed), then transposed by
+// ldmatrix.trans into K-major operand tiles with the nodes as K:
+//   A[(dc, ci)][patch node (pr, c)] = X at patch (pr, c + dc): 48 rows, 10
+//     patch rows x 16 columns of K, so a row shift dr is a shift of K by 16
+//     (two core matrices: a descriptor offset);
+//   B[co][output node (i, c)] = dZ: COUT rows.
+// Per output row i three MMAs (M = 128, N = COUT, K = 16), one per dr, A from
+// patch row i + dr, each into its own TMEM accumulator of COUT columns; A rows
+// 48..127 read neighbouring operand memory and their accumulator lanes are
+// discarded.  The accumulator stays in TMEM over the CTA's tiles; the splits'
+// partials are summed in split order afterwards (deterministic).
 // ---------------------------------------------------------------------------
 struct WgArgs {
   const bf16* x;
@@ -345,114 +346,263 @@ struct WgArgs {
   int cin, H, W, B;   // cin: padded (multiple of 16)
   float* pw;          // [S][cin / 16][9][COUT][16]
   float* pb;          // [S][COUT]
+  int* err;           // set to 1 if a tensor-core wait reached its time limit
 };
+
+constexpr int kWgTH = 8, kWgTW = 16;                     // output tile: rows x columns
+constexpr int kWgPH = kWgTH + 2, kWgPW = kWgTW + 2;      // input patch
+constexpr int kWgPatch = kWgPH * kWgPW * 32;             // patch bytes (16 channels)
+constexpr int kWgLboA = 48 * 16;                         // A: bytes per core-matrix column
+constexpr int kWgA = kWgPH * 2 * kWgLboA;                // A tile bytes (20 core-matrix columns)
+constexpr int kWgAOver = 128 * 16 - 48 * 16;             // A rows 48..127 past a core-matrix column
+__host__ __device__ constexpr int wg_b(int cout) { return kWgTH * kWgTW * cout * 2; }
+__host__ __device__ constexpr int wg_raw(int cout) { return kWgPatch + wg_b(cout); }
+__host__ __device__ constexpr int wg_smem(int cout) {
+  return 2 * wg_raw(cout) + kWgA + wg_b(cout) + 64;
+}
+__host__ __device__ constexpr unsigned wg_tcols(int cout) {
+  return 3 * cout <= 32 ? 32u : 3 * cout <= 64 ? 64u : 3 * cout <= 128 ? 128u : 256u;
+}
+static_assert(kWgAOver <= wg_b(16), "A rows read past the A tile stay inside the B tile");
 
 template <int COUT>
 __global__ void __launch_bounds__(kWgThreads) k_conv3_wgrad(WgArgs a) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  constexpr int DS = COUT + 8;
-  bf16* dzs = reinterpret_cast<bf16*>(sm_raw);   // [128 nodes][DS]
-  bf16* patch = dzs + kTH * kTW * DS;              // [kPH * kPW][kPS]
-  const int kc = blockIdx.x, s = blockIdx.y, S = gridDim.y;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int dr = warp / 3, dc = warp - dr * 3;
-  const int tw = (a.W + kTW - 1) / kTW, th = (a.H + kTH - 1) / kTH;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  constexpr int BB = wg_b(COUT);
+  constexpr int RAW = wg_raw(COUT);
+  constexpr unsigned TCOLS = wg_tcols(COUT);
+  // raw buffer r at sm + r RAW: patch [10][18][2][16 B], then dZ [COUT / 8][128][16 B]
+  unsigned char* At = sm + 2 * RAW;        // A operand tile (its last MMAs read into Bt)
+  unsigned char* Bt = At + kWgA;           // B operand tile
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(Bt + BB);
+  unsigned* taddr_s = reinterpret_cast<unsigned*>(mbar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int kc = blockIdx.x, nkc = gridDim.x, s = blockIdx.y, S = gridDim.y;
+  const int tw = (a.W + kWgTW - 1) / kWgTW, th = (a.H + kWgTH - 1) / kWgTH;
   const int T = a.B * tw * th;
-  float acc[COUT / 16][2][4];
-#pragma unroll
-  for (int mt = 0; mt < COUT / 16; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 2; ++nt) acc[mt][nt][0] = acc[mt][nt][1] = acc[mt][nt][2] = acc[mt][nt][3] = 0.0f;
-  float bsum = 0.0f;
-  for (int t = s; t < T; t += S) {
-    const int b = t / (tw * th);
-    const int r = t - b * tw * th;
-    const int i0 = (r / tw) * kTH, j0 = (r % tw) * kTW;
-    const bf16* dzb = a.dz + (long long)b * a.dz_bs;
-    for (int e = threadIdx.x; e < kTH * kTW * (COUT / 8); e += blockDim.x) {
-      const int p = e / (COUT / 8), c8 = e - p * (COUT / 8);
-      const int gi = i0 + p / kTW, gj = j0 + p % kTW;
-      const bool ok = gi < a.H && gj < a.W;
-      const bf16* src = ok ? dzb + ((long long)gi * a.W + gj) * a.dz_cs + a.dz_c0 + c8 * 8 : a.dz;
-      cp_async16(dzs + p * DS + c8 * 8, src, ok ? 16 : 0);
-    }
+
+  auto stage_raw = [&](int t, int r) {
+    unsigned char* Xp = sm + r * RAW;
+    unsigned char* Ds = Xp + kWgPatch;
+    const int b = t / (tw * th), rr = t - b * tw * th;
+    const int i0 = (rr / tw) * kWgTH, j0 = (rr % tw) * kWgTW;
     const bf16* xb = a.x + (long long)b * a.x_bs;
-    for (int e = threadIdx.x; e < kPH * kPW * 2; e += blockDim.x) {
+    for (int e = tid; e < kWgPH * kWgPW * 2; e += kWgThreads) {
       const int p = e >> 1, half = e & 1;
-      const int pi = p / kPW, pj = p - pi * kPW;
+      const int pi = p / kWgPW, pj = p - pi * kWgPW;
       const int gi = i0 + pi - 1, gj = j0 + pj - 1;
       const bool ok = gi >= 0 && gi < a.H && gj >= 0 && gj < a.W;
       const bf16* src = ok ? xb + ((long long)gi * a.x_step * a.x_w + (long long)gj * a.x_step) * a.x_cs +
                                  a.x_c0 + kc * 16 + half * 8
                            : a.x;
-      cp_async16(patch + p * kPS + half * 8, src, ok ? 16 : 0);
+      cp_async16(Xp + p * 32 + half * 16, src, ok ? 16 : 0);
+    }
+    const bf16* dzb = a.dz + (long long)b * a.dz_bs;
+    for (int e = tid; e < kWgTH * kWgTW * (COUT / 8); e += kWgThreads) {
+      const int g8 = e >> 7, k = e & 127;
+      const int gi = i0 + (k >> 4), gj = j0 + (k & 15);
+      const bool ok = gi < a.H && gj < a.W;
+      const bf16* src = ok ? dzb + ((long long)gi * a.W + gj) * a.dz_cs + a.dz_c0 + g8 * 8 : a.dz;
+      cp_async16(Ds + (g8 * 128 + k) * 16, src, ok ? 16 : 0);
     }
     cp_async_commit();
-    cp_async_wait_all();
-    __syncthreads();
-    if (kc == 0 && threadIdx.x < COUT)
-      for (int p = 0; p < kTH * kTW; ++p) bsum += __bfloat162float(dzs[p * DS + threadIdx.x]);
-#pragma unroll 1
-    for (int ks = 0; ks < kTH; ++ks) {
-      // B (16 nodes x 16 input channels) from the halo patch, shifted by the tap
-      unsigned b0, b1, b2, b3;
-      {
-        const int pxl = (lane & 7) + ((lane >> 3) & 1) * 8;
-        const int cio = (lane >> 4) * 8;
-        ldsm_x4_t(b0, b1, b2, b3, patch + ((ks + dr) * kPW + pxl + dc) * kPS + cio);
-      }
+  };
+
+  float bpart[COUT / 16];
 #pragma unroll
-      for (int mt = 0; mt < COUT / 16; ++mt) {
-        // A (16 output channels x 16 nodes) = dZ^T
-        const int pxl = (lane & 7) + (lane >> 4) * 8;
-        const int coo = ((lane >> 3) & 1) * 8;
-        unsigned a0, a1, a2, a3;
-        ldsm_x4_t(a0, a1, a2, a3, dzs + (ks * kTW + pxl) * DS + mt * 16 + coo);
-        mma_bf16(acc[mt][0], a0, a1, a2, a3, b0, b1);
-        mma_bf16(acc[mt][1], a0, a1, a2, a3, b2, b3);
+  for (int m = 0; m < COUT / 16; ++m) bpart[m] = 0.0f;
+
+  // node-major raw tiles of buffer r -> K-major operand tiles (four 8 x 8
+  // blocks per ldmatrix.x4.trans; a lane then holds one channel at two
+  // consecutive nodes, one 32-bit word of the K-major layout); the bias
+  // gradient's per-lane partial sums come from the dZ words
+  auto transpose = [&](int r) {
+    const unsigned char* Xp = sm + r * RAW;
+    const unsigned char* Ds = Xp + kWgPatch;
+    // A: 6 row blocks (dc, channel half) x 20 node blocks (patch row, column half)
+    for (int job = warp; job < 6 * 20 / 4; job += kWgThreads / 32) {
+      const int blk = job * 4 + (lane >> 3);
+      const int rb = blk / 20, kb = blk - rb * 20;
+      const int dc = rb >> 1, g = rb & 1;
+      const int pr = kb >> 1, c = (kb & 1) * 8 + (lane & 7) + dc;
+      unsigned v[4];
+      ldsm_x4_t(v[0], v[1], v[2], v[3], Xp + (pr * kWgPW + c) * 32 + g * 16);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int bj = job * 4 + j;
+        const int rbj = bj / 20, kbj = bj - rbj * 20;
+        const int row = rbj * 8 + (lane >> 2);
+        *reinterpret_cast<unsigned*>(At + kbj * kWgLboA + row * 16 + (lane & 3) * 4) = v[j];
       }
     }
-    __syncthreads();
+    // B: COUT / 8 row blocks x 16 node blocks; job m of this warp holds
+    // channel block (warp + 8 m) / 4
+#pragma unroll
+    for (int m = 0; m < COUT / 16; ++m) {
+      const int job = warp + 8 * m;
+      const int blk = job * 4 + (lane >> 3);
+      const int cb = blk >> 4, kb = blk & 15;
+      unsigned v[4];
+      ldsm_x4_t(v[0], v[1], v[2], v[3], Ds + (cb * 128 + kb * 8 + (lane & 7)) * 16);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int bj = job * 4 + j;
+        const int row = (bj >> 4) * 8 + (lane >> 2);
+        *reinterpret_cast<unsigned*>(Bt + (bj & 15) * (COUT * 16) + row * 16 + (lane & 3) * 4) = v[j];
+        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v[j]));
+        bpart[m] += f.x + f.y;
+      }
+    }
+  };
+
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  float* pw = a.pw + (((long long)s * (a.cin >> 4) + kc) * 9 + warp) * COUT * 16;
-#pragma unroll
-  for (int mt = 0; mt < COUT / 16; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 2; ++nt) {
-      const int co = mt * 16 + (lane >> 2), ci = nt * 8 + (lane & 3) * 2;
-      pw[co * 16 + ci] = acc[mt][nt][0];
-      pw[co * 16 + ci + 1] = acc[mt][nt][1];
-      pw[(co + 8) * 16 + ci] = acc[mt][nt][2];
-      pw[(co + 8) * 16 + ci + 1] = acc[mt][nt][3];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(taddr_s)),
+                 "r"(TCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  stage_raw(s, 0);   // s < T: the host launches at most T splits
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned taddr = *taddr_s;
+  // D f32, A and B bf16, both K-major, N = COUT, M = 128
+  const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(COUT >> 3) << 17) |
+                         ((unsigned)(128 >> 4) << 24);
+  bool bad = false;
+  int i = 0;
+  for (int t = s; t < T; t += S, ++i) {
+    const int rb = i & 1;
+    cp_async_wait<0>();   // tile i in raw buffer rb (the only group in flight)
+    __syncthreads();
+    // the next tile loads while this one is transposed (raw buffer rb ^ 1 was
+    // read by the transposition of tile i - 1, finished at the barrier above)
+    if (t + S < T) stage_raw(t + S, rb ^ 1);
+    // the MMAs of tile i - 1 read the operand tiles
+    bool f = false;
+    if (i >= 1) f = !mbar_wait(&mbar[0], (unsigned)(i - 1) & 1u);
+    if (__syncthreads_or(f)) {
+      bad = true;
+      break;
     }
-  if (kc == 0 && threadIdx.x < COUT) a.pb[(long long)s * COUT + threadIdx.x] = bsum;
+    transpose(rb);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const unsigned aA = smem_u32(At), aB = smem_u32(Bt);
+#pragma unroll
+      for (int kk = 0; kk < kWgTH; ++kk) {
+        const unsigned long long bd = smem_desc(aB + (unsigned)(kk * 2 * COUT * 16), COUT * 16, 128);
+#pragma unroll
+        for (int dr = 0; dr < 3; ++dr) {
+          const unsigned long long ad = smem_desc(aA + (unsigned)((kk + dr) * 2 * kWgLboA), kWgLboA, 128);
+          const unsigned acc = (i > 0 || kk > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr + (unsigned)(dr * COUT)),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&mbar[0]))
+                   : "memory");
+    }
+  }
+  if (!bad && i > 0) {
+    const bool f = !mbar_wait(&mbar[0], (unsigned)(i - 1) & 1u);
+    bad = __syncthreads_or(f);
+  }
+  if (bad) {
+    cp_async_wait<0>();
+    if (tid == 0) atomicExch(a.err, 1);
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp < 2) {
+      // TMEM lane 32 warp + lane = A row (dc, ci); lanes 48.. discarded
+      const int r = 32 * warp + lane;
+      float* pw = a.pw + ((long long)s * nkc + kc) * 9 * COUT * 16 + (r & 15);
+#pragma unroll
+      for (int dr = 0; dr < 3; ++dr) {
+        const int tap = dr * 3 + (r >> 4);
+#pragma unroll
+        for (int c = 0; c < COUT; c += 16) {
+          float v[16];
+          tmem_ld16(taddr + ((unsigned)(32 * warp) << 16) + (unsigned)(dr * COUT + c), v);
+          if (r < 48) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) pw[((long long)tap * COUT + c + k) * 16] = v[k];
+          }
+        }
+      }
+    }
+    if (kc == 0) {
+      // bias gradient: the four lanes of a channel, then the warps, in order
+      float* red = reinterpret_cast<float*>(At);   // the operand tiles are free now
+      for (int q = tid; q < 8 * COUT; q += kWgThreads) red[q] = 0.0f;
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < COUT / 16; ++m) {
+        float v = bpart[m];
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        const int cb = (warp + 8 * m) >> 2;
+        if ((lane & 3) == 0) red[warp * COUT + cb * 8 + (lane >> 2)] = v;
+      }
+      __syncthreads();
+      if (tid < COUT) {
+        float v = 0.0f;
+        for (int w = 0; w < 8; ++w) v += red[w * COUT + tid];
+        a.pb[(long long)s * COUT + tid] = v;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TCOLS));
 }
 
-// sum the split partials (in split order) into the layer's weight/bias
-// gradient; threads run along the partials' own layout (kc, tap, co, k), so
-// neighbouring threads read neighbouring words
-__global__ void k_wgrad_reduce(const float* pw, const float* pb, int S, int cin, int cin_pad,
-                               int cout, float* gw, float* gb) {
+// sum the split partials into the layer's weight/bias gradient.  A block
+// (256 threads) owns 16 consecutive partial words e (the partials' own layout
+// (kc, tap, co, k), so neighbouring threads read neighbouring words); its 16
+// split groups g sum splits g, g + 16, ... in order, then the 16 group sums
+// are added in group order (deterministic).
+constexpr int kRedE = 16, kRedG = 16;
+__global__ void __launch_bounds__(kRedE * kRedG) k_wgrad_reduce(const float* pw, const float* pb,
+                                                                  int S, int cin, int cin_pad,
+                                                                  int cout, float* gw, float* gb) {
+  __shared__ float part[kRedG][kRedE];
   const long long per = (long long)(cin_pad >> 4) * 9 * cout * 16;   // one split's partials
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < per + cout;
-       e += (long long)gridDim.x * blockDim.x) {
-    float s = 0.0f;
-    if (e < per) {
-      const int k = (int)(e & 15);
-      long long r = e >> 4;
-      const int co = (int)(r % cout);
-      r /= cout;
-      const int tap = (int)(r % 9);
-      const int kc = (int)(r / 9);
-      const int ci = kc * 16 + k;
-      if (ci >= cin) continue;
-      for (int sp = 0; sp < S; ++sp) s += pw[(long long)sp * per + e];
-      gw[((long long)co * cin + ci) * 9 + tap] = s;
-    } else {
-      const int co = (int)(e - per);
-      for (int sp = 0; sp < S; ++sp) s += pb[(long long)sp * cout + co];
-      gb[co] = s;
-    }
+  const int tx = threadIdx.x % kRedE, g = threadIdx.x / kRedE;
+  const long long e = (long long)blockIdx.x * kRedE + tx;
+  float s = 0.0f;
+  if (e < per) {
+#pragma unroll 4
+    for (int sp = g; sp < S; sp += kRedG) s += pw[(long long)sp * per + e];
+  } else if (e < per + cout) {
+    const int co = (int)(e - per);
+#pragma unroll 4
+    for (int sp = g; sp < S; sp += kRedG) s += pb[(long long)sp * cout + co];
+  }
+  part[g][tx] = s;
+  __syncthreads();
+  if (g != 0 || e >= per + cout) return;
+  float t = 0.0f;
+  for (int q = 0; q < kRedG; ++q) t += part[q][tx];
+  if (e < per) {
+    const int k = (int)(e & 15);
+    long long r = e >> 4;
+    const int co = (int)(r % cout);
+    r /= cout;
+    const int tap = (int)(r % 9);
+    const int kc = (int)(r / 9);
+    const int ci = kc * 16 + k;
+    if (ci < cin) gw[((long long)co * cin + ci) * 9 + tap] = t;
+  } else {
+    gb[e - per] = t;
   }
 }
 
@@ -979,6 +1129,7 @@ struct UNet {
   int bc_g = 0, bc_wall = 0;   // insulating boundary nodes (field_free), set at creation
   bool warm = false;
   long long adam_t = 0;
+  int wg_ctas[3] = {0, 0, 0};  // resident weight-gradient CTAs (COUT 16, 32, 64), at most kMaxSplit
   UAllocFn alloc = nullptr;
   void* actx = nullptr;
   long long npx(int l) const { return (long long)H[l] * W[l]; }
@@ -1045,21 +1196,22 @@ cudaError_t conv_wgrad(UNet* u, int Lx, const bf16* x, long long x_bs, int x_cs,
   a.cin = L.cin_pad; a.H = H; a.W = W; a.B = B;
   a.pw = u->part;
   a.pb = u->part + (long long)kMaxSplit * 9 * 16 * 64;
+  a.err = &u->ud->err;
   const int nkc = L.cin_pad >> 4;
-  const int T = B * ((W + kTW - 1) / kTW) * ((H + kTH - 1) / kTH);
-  int S = kMaxSplit / nkc;
+  const long long T = (long long)B * ((H + kWgTH - 1) / kWgTH) * ((W + kWgTW - 1) / kWgTW);
+  const int ctas = L.cout == 64 ? u->wg_ctas[2] : L.cout == 32 ? u->wg_ctas[1] : u->wg_ctas[0];
+  long long S = ctas / nkc;
   if (S > T) S = T;
   if (S < 1) S = 1;
-  const dim3 grid(nkc, S);
-  const size_t sm = (size_t)(kTH * kTW * (L.cout + 8) + kPH * kPW * kPS) * sizeof(bf16);
+  const dim3 grid(nkc, (unsigned)S);
   switch (L.cout) {
-    case 64: k_conv3_wgrad<64><<<grid, kWgThreads, sm, st>>>(a); break;
-    case 32: k_conv3_wgrad<32><<<grid, kWgThreads, sm, st>>>(a); break;
-    default: k_conv3_wgrad<16><<<grid, kWgThreads, sm, st>>>(a); break;
+    case 64: k_conv3_wgrad<64><<<grid, kWgThreads, wg_smem(64), st>>>(a); break;
+    case 32: k_conv3_wgrad<32><<<grid, kWgThreads, wg_smem(32), st>>>(a); break;
+    default: k_conv3_wgrad<16><<<grid, kWgThreads, wg_smem(16), st>>>(a); break;
   }
   const long long n = (long long)(L.cin_pad >> 4) * 9 * L.cout * 16 + L.cout;
-  k_wgrad_reduce<<<grid1(n, 256), 256, 0, st>>>(a.pw, a.pb, S, L.cin, L.cin_pad, L.cout,
-                                                u->g + L.w_off, u->g + L.b_off);
+  k_wgrad_reduce<<<(unsigned)((n + kRedE - 1) / kRedE), kRedE * kRedG, 0, st>>>(
+      a.pw, a.pb, (int)S, L.cin, L.cin_pad, L.cout, u->g + L.w_off, u->g + L.b_off);
   return cudaGetLastError();
 }
 
@@ -1360,7 +1512,47 @@ UNet* unet_create(int nr, int nz, int bmax, int n_inst, int mode, unsigned long 
     cudaFuncSetAttribute(k_conv3_tc<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(48));
     cudaFuncSetAttribute(k_conv3_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(32));
     cudaFuncSetAttribute(k_conv3_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(16));
+    cudaFuncSetAttribute(k_conv3_wgrad<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, wg_smem(64));
+    cudaFuncSetAttribute(k_conv3_wgrad<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, wg_smem(32));
+    cudaFuncSetAttribute(k_conv3_wgrad<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, wg_smem(16));
+    // all of the unified L1 as shared memory, so that the occupancy below is
+    // what the launches get
+    const void* kerns[7] = {(const void*)k_conv3_tc<64>, (const void*)k_conv3_tc<48>,
+                            (const void*)k_conv3_tc<32>, (const void*)k_conv3_tc<16>,
+                            (const void*)k_conv3_wgrad<64>, (const void*)k_conv3_wgrad<32>,
+                            (const void*)k_conv3_wgrad<16>};
+    for (const void* k : kerns)
+      cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
     attr = true;
+  }
+  {
+    // resident weight-gradient CTAs per SM: by threads, registers, shared
+    // memory and the 512 TMEM columns of an SM
+    int dev = 0, sms = 1, smem_sm = 0, smem_rsv = 0, regs_sm = 65536;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    const void* wk[3] = {(const void*)k_conv3_wgrad<16>, (const void*)k_conv3_wgrad<32>,
+                         (const void*)k_conv3_wgrad<64>};
+    const int wsm[3] = {wg_smem(16), wg_smem(32), wg_smem(64)};
+    const int tcols[3] = {(int)wg_tcols(16), (int)wg_tcols(32), (int)wg_tcols(64)};
+    for (int q = 0; q < 3; ++q) {
+      cudaFuncAttributes fa;
+      int regs = 64;
+      if (cudaFuncGetAttributes(&fa, wk[q]) == cudaSuccess && fa.numRegs > 0) regs = fa.numRegs;
+      int per_sm = 2048 / kWgThreads;
+      const int by_regs = regs_sm / (((regs + 7) / 8 * 8) * kWgThreads);
+      const int by_smem = smem_sm > 0 ? smem_sm / (wsm[q] + smem_rsv) : 1;
+      per_sm = by_regs < per_sm ? by_regs : per_sm;
+      per_sm = by_smem < per_sm ? by_smem : per_sm;
+      per_sm = 512 / tcols[q] < per_sm ? 512 / tcols[q] : per_sm;
+      if (per_sm < 1) per_sm = 1;
+      const int c = per_sm * (sms > 0 ? sms : 1);
+      u->wg_ctas[q] = c < kMaxSplit ? c : kMaxSplit;
+    }
   }
   if (e != cudaSuccess) {
     delete u;
