@@ -495,8 +495,7 @@ int pic_poisson_solve(int nr, int nz, double R, double L, double tol, int max_it
  *     PIC_POISSON_STATIC_BYTES - 256 are rejected with PIC_ERR_CAPACITY.
  *   - Each call looks up the array's device address on the current device
  *     (cudaGetSymbolAddress), so a device reset between calls is harmless;
- *     the first call on a device also loads the library's device code there:
- *     make that first call before any stream capture.
+ *     the first call on a device also loads the library's device code there.
  *   - All calls on a device share the one array, which keeps the previous
  *     call's contents (each call clears what must start at zero).  Calls that
  *     overlap on the GPU race on it: serialise them (one stream, one thread).
