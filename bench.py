@@ -68,8 +68,9 @@ TRAFFIC_PER_PARTICLE = {"fp64": 87.8, "fp32": 64.3}
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA pipes-lanes per SM per clock x 2
 # flop x 2.07 GHz = 1.26 TFLOP/s (nominal 1.25); scaled to the measured clock.
 FP64_FLOP_PER_CLK = 152 * 2 * 2
-# steps a new handle spends tuning the push's chunk size (pic_tuned_chunk)
-AUTOTUNE_STEPS = 4
+# steps a new handle spends tuning the push (chunk size, then cell tile shape)
+AUTOTUNE_STEPS = 6
+TILE_NAMES = {1: "8x8", 2: "16x8", 3: "8x16"}   # cells, r x z (pic_tuned_tile)
 
 
 def parse():
@@ -456,7 +457,7 @@ def run_sweep(args, torch, pg, emit: bool = True):
     prof = pg.pic_profile_read(ens)
     pg.pic_profile(ens, False)
     nprof = max(1, prof["push"]["launches"])
-    tuned = pg.pic_tuned_chunk(ens)
+    tuned, tile = pg.pic_tuned_chunk(ens), pg.pic_tuned_tile(ens)
     graph = pg.pic_uses_graph(ens)
     pg.pic_destroy(ens)
     # the same 16 discharges as 16 sequential single-discharge runs
@@ -493,7 +494,8 @@ def run_sweep(args, torch, pg, emit: bool = True):
             "clocks": clk.summary(),
             "sequential_16_value": seq, "ensemble_over_sequential": value / seq,
             "sequential_16_poisson_ms_per_step": seq_poisson,
-            "autotuned_particles_per_thread": tuned, "cuda_graph": graph,
+            "autotuned_particles_per_thread": tuned, "autotuned_cell_tile": TILE_NAMES[tile],
+            "cuda_graph": graph,
             "per_kernel_ms_per_step": {k: v["total_ms"] / nprof for k, v in prof.items()}}
     if emit:
         print(json.dumps(line), flush=True)
@@ -922,6 +924,7 @@ def sub_records(args, torch, pg, p, parts, peaks, peak_kind, local, fp64_value):
                                               "fp32".replace("+", ""),
                                   "sort_every": p32["sort_every"], "same_state_as_headline": True},
                        "push_particles_per_thread": pg.pic_tuned_chunk(h),
+                       "cell_tile": TILE_NAMES[pg.pic_tuned_tile(h)],
                        "poisson": {"iters_last_step": rec["d1"]["poisson_iters"],
                                    "ms_per_step": rec["per_kernel"]["poisson"]},
                        "roofline": push_roofline("fp32", g, rec, n_pushed, peaks, peak_kind),
@@ -1024,7 +1027,7 @@ def main():
     region = {"ms_per_sample": reg_ms, "achieved_gbs": reg_bytes / (reg_ms / 1e3) / 1e9,
               "bytes_per_sample": reg_bytes, "Te_eV": regions_out["Te"],
               "z_sheath_m": regions_out["z_sheath"], "z_bulk_m": regions_out["z_bulk"]}
-    graph, tuned = pg.pic_uses_graph(h), pg.pic_tuned_chunk(h)
+    graph, tuned, tile = pg.pic_uses_graph(h), pg.pic_tuned_chunk(h), pg.pic_tuned_tile(h)
     pg.pic_destroy(h)
 
     # end to end through the C ABI with host buffers: upload the state from
@@ -1058,6 +1061,7 @@ def main():
                                 + KERNELS_PER_CALL,
                 "cuda_graph": graph,
                 "autotune_steps": AUTOTUNE_STEPS, "push_particles_per_thread": tuned,
+                "cell_tile": TILE_NAMES[tile],
                 "poisson": {"iters_last_step": rec["d1"]["poisson_iters"],
                             "resid_last_step": rec["d1"]["poisson_resid"],
                             "ms_per_step": rec["per_kernel"]["poisson"]},

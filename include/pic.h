@@ -237,23 +237,37 @@ int pic_uses_graph(pic_handle* h);
  * chunks interleaved; ensembles (n_instances > 1) also solve all Poisson
  * problems in one grouped launch.  The first four steps of a handle each try
  * one chunk size (4, 8, 16, 32 particles per thread) with eager launches and
- * the fastest is kept: *particles_per_thread receives it, or 0 while tuning
- * is unfinished. */
+ * the fastest is kept (then two more steps try the other tile shapes, see
+ * pic_set_tile): *particles_per_thread receives it, or 0 while tuning is
+ * unfinished. */
 int pic_tuned_chunk(pic_handle* h, int* particles_per_thread);
 
 /* Fix the push's chunk size (particles_per_thread 4, 8, 16 or 32) for the
- * rest of the run, ending any tuning under way; 0 restarts the tuning, so the
- * next four steps time the four sizes again (e.g. after the particle counts
- * have grown).  Results do not depend on the chunk size (FP64 bit for bit).
+ * rest of the run, ending any tuning under way (the tile shape then stays);
+ * 0 restarts the tuning, so the next steps time the four sizes (and the tile
+ * shapes) again (e.g. after the particle counts have grown).  Results do not depend on the chunk size (FP64 bit for bit).
  * Drops the captured step graph.  PIC_ERR_INVALID for any other value. */
 int pic_set_chunk(pic_handle* h, int particles_per_thread);
 
+/* Cell tile shape of the particle sort key and of the push's shared deposit
+ * patch, for every instance of the handle: 1 = 8 x 8, 2 = 16 x 8, 3 = 8 x 16
+ * cells (r x z) fixed from now on, the particles re-sorted by the new keys at
+ * once (results do not depend on the shape: FP64 exactly, FP32 up to the
+ * order of the FP32 patch sums); 0 = chosen by the autotuner, which (after the
+ * chunk size) times one step on each shape and keeps the fastest, here and at
+ * every re-tuning (this restarts the tuning).  Default 0, starting on 8 x 8.
+ * Synchronous.  PIC_ERR_INVALID for another shape. */
+int pic_set_tile(pic_handle* h, int shape);
+
+/* The current tile shape (1, 2 or 3 as in pic_set_tile). */
+int pic_tuned_tile(pic_handle* h, int* shape);
+
 /* The push's online tuning.  The first four steps of a handle time the four
- * chunk sizes; later, when at the start of a pic_step call the live particle
- * count of all instances (as copied after the previous call) differs from the
- * count at the last tuning by a factor of 4 or more, the next four steps tune
- * again and the step graph is captured anew (unless the size was fixed with
- * pic_set_chunk).  *tunings: tunings completed; *particles_per_thread: the
+ * chunk sizes and the next two the other two tile shapes (pic_set_tile);
+ * later, when at the start of a pic_step call the live particle count of all
+ * instances (as copied after the previous call) differs from the count at the
+ * last tuning by a factor of 4 or more, the next steps tune again and the step
+ * graph is captured anew (unless the size was fixed with pic_set_chunk).  *tunings: tunings completed; *particles_per_thread: the
  * size in use (0 while tuning); *particles_at_tuning: live particles when the
  * last tuning ended.  Any pointer may be NULL. */
 int pic_autotune_info(pic_handle* h, int* tunings, int* particles_per_thread,

@@ -23,6 +23,8 @@ struct InstHost {
   Inst I;
   PoissonWork* pw = nullptr;
   int swapped = 0;
+  int nkey_max = 0;                  // cell keys of the tile shape with the most
+  std::vector<double4_32a> bcell;    // B-table entries of cell m nz + n (2 per cell)
 };
 
 }  // namespace
@@ -49,6 +51,10 @@ struct pic_handle {
   int ppt = 8;                       // particles per thread per work item (autotuned)
   int tune_next = 0;                 // next autotuner candidate; -1 = done
   float tune_ms[4] = {0, 0, 0, 0};
+  int tile = 0;                      // cell tile shape of every instance (index of kTileLog)
+  int tile0 = 0;                     // shape during the chunk-size candidates of a tuning
+  bool tile_tune = true;             // off after pic_set_tile with a fixed shape
+  float tile_ms[kTileShapes] = {0, 0, 0};
   // re-tuning when the particle count has changed by kRetuneFactor since the
   // last tuning: the live count of all instances is copied to page-locked
   // host memory after each pic_step call and read at the next one
@@ -170,15 +176,54 @@ cudaError_t region_clear(const Inst& I, cudaStream_t st) {
   return e;
 }
 
+// The magnetic-field table in the order of the cell keys of the instance's
+// tile shape (FP32 coefficients, or per species FP64 scaled by h = q dt / 2m:
+// the push reads t = h B); synchronous.
+cudaError_t upload_btab(const InstHost& ih, cudaStream_t st) {
+  const Inst& I = ih.I;
+  const int nr = I.nr, nz = I.nz;
+  cudaError_t e = cudaSuccess;
+  if (I.prec32) {
+    std::vector<float4> bt((size_t)I.nkey * 2, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int m = 0; m < nr; ++m)
+      for (int n = 0; n < nz; ++n)
+        for (int comp = 0; comp < 2; ++comp) {
+          const double4_32a& v = ih.bcell[((size_t)m * nz + n) * 2 + comp];
+          bt[(size_t)2 * cell_key(I, m, n) + comp] =
+              make_float4((float)v.x, (float)v.y, (float)v.z, (float)v.w);
+        }
+    e = cudaMemcpyAsync(I.btab32, bt.data(), bt.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  } else {
+    for (int sp = 0; sp < 2 && e == cudaSuccess; ++sp) {
+      const double hs = 0.5 * I.qm[sp] * I.dt;
+      std::vector<double4_32a> bs((size_t)I.nkey * 2, make_d4(0, 0, 0, 0));
+      for (int m = 0; m < nr; ++m)
+        for (int n = 0; n < nz; ++n)
+          for (int comp = 0; comp < 2; ++comp) {
+            const double4_32a& v = ih.bcell[((size_t)m * nz + n) * 2 + comp];
+            bs[(size_t)2 * cell_key(I, m, n) + comp] = make_d4(hs * v.x, hs * v.y, hs * v.z, hs * v.w);
+          }
+      e = cudaMemcpyAsync(I.btab[sp], bs.data(), bs.size() * sizeof(double4_32a),
+                          cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // bs is freed at the loop end
+    }
+  }
+  return e;
+}
+
 int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
   ih.cfg = c;
   Inst& I = ih.I;
   std::memset(&I, 0, sizeof(I));
   I.nr = c.nr;
   I.nz = c.nz;
-  const int ntr = (c.nr + kTile - 1) / kTile;
-  I.ntz = (c.nz + kTile - 1) / kTile;
-  I.nkey = ntr * I.ntz * kTileCells;
+  ih.nkey_max = 0;
+  for (int shape = 0; shape < kTileShapes; ++shape) {
+    set_tile_shape(I, shape);
+    ih.nkey_max = I.nkey > ih.nkey_max ? I.nkey : ih.nkey_max;
+  }
+  set_tile_shape(I, h->tile);
   I.R = c.R;
   I.L = c.L;
   I.Rc = c.Rc;
@@ -270,8 +315,8 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
       I.key[sp] = (int*)chk(A(cap * 4));
       I.qacc[sp] = (unsigned long long*)chk(A(nn * 8));
     }
-    I.counts[sp] = (int*)chk(A((size_t)I.nkey * 4));
-    I.cursor[sp] = (int*)chk(A((size_t)I.nkey * 4));
+    I.counts[sp] = (int*)chk(A((size_t)ih.nkey_max * 4));
+    I.cursor[sp] = (int*)chk(A((size_t)ih.nkey_max * 4));
     BirthsDev& B = I.births[sp];
     const size_t bc = (size_t)c.birth_cap;
     if (p32) {
@@ -299,15 +344,15 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
   I.qs[0] = (double*)chk(A(nn * 8));
   I.qs[1] = (double*)chk(A(nn * 8));
   if (p32) {
-    I.etab32 = (float4*)chk(A((size_t)I.nkey * (c.gather == 0 ? 1 : 2) * sizeof(float4)));
-    I.btab32 = (float4*)chk(A((size_t)I.nkey * 2 * sizeof(float4)));
+    I.etab32 = (float4*)chk(A((size_t)ih.nkey_max * (c.gather == 0 ? 1 : 2) * sizeof(float4)));
+    I.btab32 = (float4*)chk(A((size_t)ih.nkey_max * 2 * sizeof(float4)));
     long long cmax = I.cap[0] > I.cap[1] ? I.cap[0] : I.cap[1];
     I.stage_len = cmax < (1LL << 22) ? cmax : (1LL << 22);
     I.stage = (double*)chk(A((size_t)I.stage_len * 6 * 8));
   } else {
     for (int sp = 0; sp < 2; ++sp) {
-      I.etab[sp] = (double4_32a*)chk(A((size_t)I.nkey * (c.gather == 0 ? 1 : 2) * sizeof(double4_32a)));
-      I.btab[sp] = (double4_32a*)chk(A((size_t)I.nkey * 2 * sizeof(double4_32a)));
+      I.etab[sp] = (double4_32a*)chk(A((size_t)ih.nkey_max * (c.gather == 0 ? 1 : 2) * sizeof(double4_32a)));
+      I.btab[sp] = (double4_32a*)chk(A((size_t)ih.nkey_max * 2 * sizeof(double4_32a)));
     }
   }
   I.qhist = (double*)chk(A((size_t)c.n_avg * 8));
@@ -331,9 +376,9 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
   cudaStream_t st = h->stream;
   cudaError_t e = cudaSuccess;
   for (int sp = 0; sp < 2 && e == cudaSuccess; ++sp) {
-    e = cudaMemsetAsync(I.counts[sp], 0, (size_t)I.nkey * 4, st);
+    e = cudaMemsetAsync(I.counts[sp], 0, (size_t)ih.nkey_max * 4, st);
     // cell bin ends of the sorted arrays (all empty until particles are set)
-    if (e == cudaSuccess) e = cudaMemsetAsync(I.cursor[sp], 0, (size_t)I.nkey * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(I.cursor[sp], 0, (size_t)ih.nkey_max * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(p32 ? (void*)I.qacc64[sp] : (void*)I.qacc[sp], 0, nn * 8, st);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(I.phi, 0, nn * 8, st);
@@ -369,37 +414,20 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
       br[(size_t)m * (c.nz + 1) + n] = vr;
       bz[(size_t)m * (c.nz + 1) + n] = vz;
     }
-  std::vector<double4_32a> bt((size_t)I.nkey * 2, make_d4(0, 0, 0, 0));
+  ih.bcell.assign((size_t)c.nr * c.nz * 2, make_d4(0, 0, 0, 0));
   for (int m = 0; m < c.nr; ++m)
     for (int n = 0; n < c.nz; ++n) {
-      const int key = ((m >> 3) * I.ntz + (n >> 3)) * kTileCells + ((m & 7) << 3) + (n & 7);
       auto at = [&](const std::vector<double>& v, int a, int b) {
         return v[(size_t)(m + a) * (c.nz + 1) + (n + b)];
       };
       for (int comp = 0; comp < 2; ++comp) {
         const std::vector<double>& v = comp == 0 ? br : bz;
         const double b00 = at(v, 0, 0), b10 = at(v, 1, 0), b01 = at(v, 0, 1), b11 = at(v, 1, 1);
-        bt[(size_t)2 * key + comp] = make_d4(b00, b10 - b00, b01 - b00, b11 - b10 - b01 + b00);
+        ih.bcell[((size_t)m * c.nz + n) * 2 + comp] =
+            make_d4(b00, b10 - b00, b01 - b00, b11 - b10 - b01 + b00);
       }
     }
-  std::vector<float4> bt32;
-  if (p32) {
-    bt32.resize(bt.size());
-    for (size_t k = 0; k < bt.size(); ++k)
-      bt32[k] = make_float4((float)bt[k].x, (float)bt[k].y, (float)bt[k].z, (float)bt[k].w);
-    e = cudaMemcpyAsync(I.btab32, bt32.data(), bt32.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
-  } else {
-    // one copy per species, scaled by h = q dt / (2 m): the push reads t = h B
-    for (int sp = 0; sp < 2 && e == cudaSuccess; ++sp) {
-      const double hs = 0.5 * I.qm[sp] * c.dt;
-      std::vector<double4_32a> bs(bt.size());
-      for (size_t k = 0; k < bt.size(); ++k)
-        bs[k] = make_d4(hs * bt[k].x, hs * bt[k].y, hs * bt[k].z, hs * bt[k].w);
-      e = cudaMemcpyAsync(I.btab[sp], bs.data(), bs.size() * sizeof(double4_32a),
-                          cudaMemcpyHostToDevice, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // bs is freed at the loop end
-    }
-  }
+  e = upload_btab(ih, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "upload B table");
   Scalars s0;
   std::memset(&s0, 0, sizeof(s0));
@@ -968,12 +996,53 @@ static cudaError_t live_count(pic_handle* h, long long* out) {
   return e;
 }
 
+static void drop_graph(pic_handle* h);
+
+// Switch every instance to cell tile shape `shape`: the keys, the B table in
+// the new key order and the particles re-sorted by the new keys (compacted,
+// as after a full sort); the captured step is dropped.
+static int apply_tile(pic_handle* h, int shape) {
+  if (shape == h->tile) return PIC_OK;
+  drop_graph(h);
+  cudaError_t e = cudaSuccess;
+  for (InstHost& ih : h->inst) {
+    set_tile_shape(ih.I, shape);
+    if (e == cudaSuccess) e = upload_btab(ih, h->stream);
+  }
+  std::vector<Inst> hi;
+  for (const InstHost& ih : h->inst) hi.push_back(ih.I);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_insts, hi.data(), sizeof(Inst) * hi.size(), cudaMemcpyHostToDevice,
+                        h->stream);
+  for (InstHost& ih : h->inst)
+    if (e == cudaSuccess) e = launch_thin(ih.I, 1, h->num_sms, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "tile shape");
+  h->tile = shape;
+  for (int k = 0; k < (int)h->inst.size(); ++k) {
+    const int rc = read_status(h, k, nullptr);
+    if (rc != PIC_OK && rc != PIC_ERR_NONCONVERGED) return rc;
+  }
+  return PIC_OK;
+}
+
+// Tuning sequence: steps 0..3 time the chunk sizes on the current tile shape;
+// then (unless the shape is fixed) steps 4 and 5 time the other two shapes
+// with the chosen chunk size, each after re-sorting the particles by its keys,
+// and the fastest shape is kept.
 static int autotune_step(pic_handle* h) {
   const int c = h->tune_next;
-  h->ppt = kTuneCandidates[c];
+  if (c < 4) h->ppt = kTuneCandidates[c];
   if (c == 0) {
+    h->tile0 = h->tile;
     const cudaError_t e0 = force_sorts(h, 1);
     if (e0 != cudaSuccess) return cuda_fail(h, e0, "tune");
+  }
+  int shape = h->tile;
+  if (c >= 4) {
+    shape = (h->tile0 + (c - 3)) % kTileShapes;
+    const int rc = apply_tile(h, shape);
+    if (rc != PIC_OK) return rc;
   }
   cudaEvent_t a, b;
   cudaEventCreate(&a);
@@ -991,12 +1060,24 @@ static int autotune_step(pic_handle* h) {
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (e != cudaSuccess) return cuda_fail(h, e, "step");
-  h->tune_ms[c] = ms;
-  if (++h->tune_next == 4) {
+  if (c < 4) h->tune_ms[c] = ms;
+  else h->tile_ms[shape] = ms;
+  ++h->tune_next;
+  if (h->tune_next == 4) {
     int best = 0;
     for (int k = 1; k < 4; ++k)
       if (h->tune_ms[k] < h->tune_ms[best]) best = k;
     h->ppt = kTuneCandidates[best];
+    h->tile_ms[h->tile0] = h->tune_ms[best];
+  }
+  if ((h->tune_next == 4 && !h->tile_tune) || h->tune_next == 4 + kTileShapes - 1) {
+    if (h->tune_next > 4) {
+      int best = 0;
+      for (int k = 1; k < kTileShapes; ++k)
+        if (h->tile_ms[k] < h->tile_ms[best]) best = k;
+      const int rc = apply_tile(h, best);
+      if (rc != PIC_OK) return rc;
+    }
     h->tune_next = -1;
     ++h->tunings;
     long long live = 0;
@@ -1121,9 +1202,39 @@ int pic_set_chunk(pic_handle* h, int particles_per_thread) {
     h->tune_next = -1;
     h->retune = false;      // fixed by the caller
   } else {
-    h->tune_next = 0;       // tune again over the next four steps
+    h->tune_next = 0;       // tune again over the next steps
     h->retune = true;
   }
+  return PIC_OK;
+}
+
+int pic_set_tile(pic_handle* h, int shape) {
+  if (!h) return PIC_ERR_INVALID;
+  if (shape < 0 || shape > kTileShapes) return fail(h, PIC_ERR_INVALID, "shape must be 0, 1, 2 or 3");
+  if (shape == 0) {
+    h->tile_tune = true;
+    drop_graph(h);
+    if (h->tune_next > 0) {
+      const cudaError_t e = force_sorts(h, 0);
+      if (e != cudaSuccess) return cuda_fail(h, e, "set_tile");
+    }
+    h->tune_next = 0;       // tune chunk size and tile shape over the next steps
+    h->retune = true;
+    return PIC_OK;
+  }
+  h->tile_tune = false;
+  if (h->tune_next >= 4) {  // the shape trials of a tuning end here (its chunk size is chosen)
+    h->tune_next = -1;
+    ++h->tunings;
+    const cudaError_t e = force_sorts(h, 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_tile");
+  }
+  return apply_tile(h, shape - 1);
+}
+
+int pic_tuned_tile(pic_handle* h, int* shape) {
+  if (!h || !shape) return PIC_ERR_INVALID;
+  *shape = h->tile + 1;
   return PIC_OK;
 }
 

@@ -2,8 +2,9 @@
 //
 // Layout decisions (all memory is HBM-resident for the whole run):
 //  * particles: structure of arrays per species, double buffered, sorted by a
-//    tile-major cell key (8 x 8 cell tiles) so that a CTA's chunk of
-//    consecutive particles covers a compact patch of the grid;
+//    tile-major cell key (tiles of 8 x 8, 16 x 8 or 8 x 16 cells in r x z, the
+//    shape chosen by the autotuner) so that a CTA's chunk of consecutive
+//    particles covers a compact patch of the grid;
 //  * node arrays (phi, Q): (nr+1) x (nz+1), z fastest;
 //  * per-cell gather tables: the field and the magnetic field around a cell
 //    folded into polynomial coefficients in the in-cell offsets, so one cell
@@ -27,8 +28,9 @@ constexpr double kEps0 = 8.8541878128e-12;
 constexpr double kBoltz = 1.380649e-23;
 constexpr double kPi = 3.14159265358979323846;
 
-constexpr int kTile = 8;                 // cells per tile side
-constexpr int kTileCells = kTile * kTile;
+// cell tiles: 2^tsr x 2^tsz cells (r x z); the shapes 8 x 8, 16 x 8, 8 x 16
+constexpr int kTileShapes = 3;
+constexpr int kTileLog[kTileShapes][2] = {{3, 3}, {4, 3}, {3, 4}};
 constexpr int kFixBits = 44;             // fixed-point fraction bits of the deposit
 constexpr double kFixOne = 17592186044416.0;          // 2^44
 constexpr double kFixInv = 1.0 / 17592186044416.0;    // 2^-44
@@ -164,7 +166,8 @@ struct RegionDev {
 
 struct Inst {
   // geometry
-  int nr, nz, ntz, nkey;   // ntz: tiles along z; nkey: number of cell keys
+  int nr, nz, ntz, nkey;   // ntz: tiles along z; nkey: number of cell keys (this shape)
+  int tsr, tsz;            // log2 of the tile's extent in r and in z (cells)
   int m_cath;              // last radial node index of the cathode (r_m <= Rc)
   double R, L, Rc, dr, dz, inv_dr, inv_dz;
   double dt;
@@ -297,9 +300,27 @@ __device__ __forceinline__ void locate(double x, double inv_d, int ncell, int& k
 }
 
 
-__device__ __forceinline__ int cell_key(const Inst& I, int m, int n) {
-  int tile = (m >> 3) * I.ntz + (n >> 3);
-  return tile * kTileCells + ((m & 7) << 3) + (n & 7);
+__host__ __device__ __forceinline__ int cell_key(const Inst& I, int m, int n) {
+  const int tile = (m >> I.tsr) * I.ntz + (n >> I.tsz);
+  return (tile << (I.tsr + I.tsz)) + ((m & ((1 << I.tsr) - 1)) << I.tsz) + (n & ((1 << I.tsz) - 1));
+}
+
+// the cell (m, n) of key k (cells of padding keys lie outside the grid)
+__device__ __forceinline__ void key_cell(const Inst& I, int k, int& m, int& n) {
+  const int tile = k >> (I.tsr + I.tsz), within = k & ((1 << (I.tsr + I.tsz)) - 1);
+  const int tm = tile / I.ntz, tn = tile - tm * I.ntz;
+  m = (tm << I.tsr) + (within >> I.tsz);
+  n = (tn << I.tsz) + (within & ((1 << I.tsz) - 1));
+}
+
+// tile shape `shape` (index into kTileLog) on an nr x nz grid: its extents,
+// tiles along z and number of keys (host)
+inline void set_tile_shape(Inst& I, int shape) {
+  I.tsr = kTileLog[shape][0];
+  I.tsz = kTileLog[shape][1];
+  const int ntr = (I.nr + (1 << I.tsr) - 1) >> I.tsr;
+  I.ntz = (I.nz + (1 << I.tsz) - 1) >> I.tsz;
+  I.nkey = (ntr * I.ntz) << (I.tsr + I.tsz);
 }
 
 __device__ __forceinline__ int node_index(const Inst& I, int m, int n) { return m * (I.nz + 1) + n; }

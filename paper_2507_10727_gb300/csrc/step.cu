@@ -24,8 +24,15 @@ namespace pic {
 
 constexpr int kPushThreads = 256;
 constexpr int kHalo = 3;                         // cells a particle may move and still hit the patch
-constexpr int kPR = kTile + 2 * kHalo + 1;       // patch nodes in r
-constexpr int kPZ = 2 * kTile + 2 * kHalo + 1;   // patch nodes in z (two tiles along z)
+// The deposit patch: (tile extent in r + 2 halo + 1) x (two tiles along z + 2
+// halo + 1) nodes; the arrays hold the largest of the tile shapes.
+__device__ __forceinline__ int patch_pr(const Inst& I) { return (1 << I.tsr) + 2 * kHalo + 1; }
+__device__ __forceinline__ int patch_pz(const Inst& I) { return (2 << I.tsz) + 2 * kHalo + 1; }
+constexpr int patch_nodes(int lr, int lz) { return ((1 << lr) + 2 * kHalo + 1) * ((2 << lz) + 2 * kHalo + 1); }
+constexpr int patch_cells(int lr, int lz) { return ((1 << lr) + 2 * kHalo) * ((2 << lz) + 2 * kHalo); }
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+constexpr int kPatchNodes = cmax(patch_nodes(3, 3), cmax(patch_nodes(4, 3), patch_nodes(3, 4)));
+constexpr int kPatchCells = cmax(patch_cells(3, 3), cmax(patch_cells(4, 3), patch_cells(3, 4)));
 constexpr int kCollQ = 512;                      // deferred collision candidates per chunk
 
 // ---------------------------------------------------------------------------
@@ -266,7 +273,7 @@ __device__ __noinline__ void collide_at(const Inst& I, const ParticlesDev& P, lo
 // meets the same new cell over many iterations: it sums its fixed-point
 // deposit weights and its cell count in registers (integers: exact, order
 // free) and adds them, when its cell changes, to the CTA's shared patches of
-// kPR x kPZ nodes (charge) and kPR-1 x kPZ-1 cells (counts) anchored at the
+// pr x pz nodes (charge) and pr-1 x pz-1 cells (counts) anchored at the
 // tile of the chunk's first particle, flushed with one atomic per touched
 // node or cell.  Cells whose nodes fall outside the patch (fast movers, chunk
 // tails in sparse regions) add to global memory.
@@ -275,16 +282,16 @@ template <int SP>
 __device__ __forceinline__ void deposit_run64(const Inst& I, int key, int m, int n,
                                               unsigned long long a00, unsigned long long a10,
                                               unsigned long long a01, unsigned long long a11,
-                                              int cnt, int pm0, int pn0, unsigned long long* patch,
-                                              int* cpatch) {
+                                              int cnt, int pm0, int pn0, int pr, int pz,
+                                              unsigned long long* patch, int* cpatch) {
   const int lm = m - pm0, ln = n - pn0;
-  if (lm >= 0 && lm + 1 < kPR && ln >= 0 && ln + 1 < kPZ) {
-    unsigned long long* p = patch + lm * kPZ + ln;
+  if (lm >= 0 && lm + 1 < pr && ln >= 0 && ln + 1 < pz) {
+    unsigned long long* p = patch + lm * pz + ln;
     atomicAdd(p, a00);
-    atomicAdd(p + kPZ, a10);
+    atomicAdd(p + pz, a10);
     atomicAdd(p + 1, a01);
-    atomicAdd(p + kPZ + 1, a11);
-    atomicAdd(cpatch + lm * (kPZ - 1) + ln, cnt);
+    atomicAdd(p + pz + 1, a11);
+    atomicAdd(cpatch + lm * (pz - 1) + ln, cnt);
   } else {
     unsigned long long* q = I.qacc[SP];
     atomicAdd(q + node_index(I, m, n), a00);
@@ -322,12 +329,13 @@ __device__ __forceinline__ double push_chunk64(const Inst& I, long long c0, int 
       double f;
       split_cell(P.r[c0], I.nr, m, f);
       split_cell(P.z[c0], I.nz, nn, f);
-      anchor[0] = (m & ~(kTile - 1)) - kHalo;
-      anchor[1] = (nn & ~(kTile - 1)) - kHalo;
+      anchor[0] = (m & ~((1 << I.tsr) - 1)) - kHalo;
+      anchor[1] = (nn & ~((1 << I.tsz) - 1)) - kHalo;
       anchor[2] = 0;
     }
     __syncthreads();
     const int pm0 = anchor[0], pn0 = anchor[1];
+    const int pr = patch_pr(I), pz = patch_pz(I);
     const long long run0 = c0 + (long long)(threadIdx.x >> 5) * 32 * ppt + lane;
     // this lane's open deposit: cell, its fixed-point node sums and count
     int acc_key = -1, acc_m = 0, acc_n = 0, acc_cnt = 0;
@@ -460,7 +468,7 @@ __device__ __forceinline__ double push_chunk64(const Inst& I, long long c0, int 
           if (newkey != acc_key) {
             if (acc_key >= 0)
               deposit_run64<SP>(I, acc_key, acc_m, acc_n, s00, s10, s01, s11, acc_cnt, pm0, pn0,
-                                patch, cpatch);
+                                pr, pz, patch, cpatch);
             acc_key = newkey;
             acc_m = m1;
             acc_n = n1;
@@ -480,8 +488,8 @@ __device__ __forceinline__ double push_chunk64(const Inst& I, long long c0, int 
       }
     }
     if (acc_key >= 0)
-      deposit_run64<SP>(I, acc_key, acc_m, acc_n, s00, s10, s01, s11, acc_cnt, pm0, pn0, patch,
-                        cpatch);
+      deposit_run64<SP>(I, acc_key, acc_m, acc_n, s00, s10, s01, s11, acc_cnt, pm0, pn0, pr, pz,
+                        patch, cpatch);
     __syncthreads();
     if (SP == 0) {
       // the queued collisions (Section 3), on the state written above
@@ -494,18 +502,18 @@ __device__ __forceinline__ double push_chunk64(const Inst& I, long long c0, int 
       }
     }
     // flush the patches
-    for (int k = threadIdx.x; k < kPR * kPZ; k += blockDim.x) {
+    for (int k = threadIdx.x; k < pr * pz; k += blockDim.x) {
       const unsigned long long v = patch[k];
       if (v != 0ULL) {
-        const int gm = pm0 + k / kPZ, gn = pn0 + k % kPZ;
+        const int gm = pm0 + k / pz, gn = pn0 + k % pz;
         atomicAdd(I.qacc[SP] + node_index(I, gm, gn), v);
         patch[k] = 0ULL;
       }
     }
-    for (int k = threadIdx.x; k < (kPR - 1) * (kPZ - 1); k += blockDim.x) {
+    for (int k = threadIdx.x; k < (pr - 1) * (pz - 1); k += blockDim.x) {
       const int c = cpatch[k];
       if (c != 0) {
-        const int gm = pm0 + k / (kPZ - 1), gn = pn0 + k % (kPZ - 1);
+        const int gm = pm0 + k / (pz - 1), gn = pn0 + k % (pz - 1);
         atomicAdd(&I.counts[SP][cell_key(I, gm, gn)], c);
         cpatch[k] = 0;
       }
@@ -521,15 +529,15 @@ __device__ __forceinline__ double push_chunk64(const Inst& I, long long c0, int 
 template <int GATHER>
 __global__ void __launch_bounds__(kPushThreads, 2) k_push_all(const Inst* insts, WorkQueue* q,
                                                                int ppt) {
-  __shared__ unsigned long long patch[kPR * kPZ];
-  __shared__ int cpatch[(kPR - 1) * (kPZ - 1)];
+  __shared__ unsigned long long patch[kPatchNodes];
+  __shared__ int cpatch[kPatchCells];
   __shared__ int anchor[3];
   __shared__ int cq[kCollQ];
   __shared__ Inst sI;
   __shared__ int s_inst, s_sp, s_skip;
   __shared__ long long s_c0;
-  for (int k = threadIdx.x; k < kPR * kPZ; k += blockDim.x) patch[k] = 0ULL;
-  for (int k = threadIdx.x; k < (kPR - 1) * (kPZ - 1); k += blockDim.x) cpatch[k] = 0;
+  for (int k = threadIdx.x; k < kPatchNodes; k += blockDim.x) patch[k] = 0ULL;
+  for (int k = threadIdx.x; k < kPatchCells; k += blockDim.x) cpatch[k] = 0;
   int cur = -1;
   double K0 = 0.0, K1 = 0.0;
   const long long chunk = (long long)ppt * blockDim.x;
@@ -575,14 +583,14 @@ __global__ void __launch_bounds__(kPushThreads, 2) k_push_all(const Inst* insts,
 template <int GATHER>
 __global__ void __launch_bounds__(kPushThreads, 2) k_push_one(const Inst I, WorkQueue* q,
                                                                int ppt) {
-  __shared__ unsigned long long patch[kPR * kPZ];
-  __shared__ int cpatch[(kPR - 1) * (kPZ - 1)];
+  __shared__ unsigned long long patch[kPatchNodes];
+  __shared__ int cpatch[kPatchCells];
   __shared__ int anchor[3];
   __shared__ int cq[kCollQ];
   __shared__ int s_sp, s_done, s_skip;
   __shared__ long long s_c0;
-  for (int k = threadIdx.x; k < kPR * kPZ; k += blockDim.x) patch[k] = 0ULL;
-  for (int k = threadIdx.x; k < (kPR - 1) * (kPZ - 1); k += blockDim.x) cpatch[k] = 0;
+  for (int k = threadIdx.x; k < kPatchNodes; k += blockDim.x) patch[k] = 0ULL;
+  for (int k = threadIdx.x; k < kPatchCells; k += blockDim.x) cpatch[k] = 0;
   double K0 = 0.0, K1 = 0.0;
   const long long chunk = (long long)ppt * blockDim.x;
   for (;;) {
@@ -985,9 +993,8 @@ __global__ void k_region_sample(Inst I, int sp) {
     long long b0 = k > 0 ? ends[k - 1] : 0, b1 = ends[k];
     if (b1 > n) b1 = n;
     if (b1 <= b0) continue;
-    const int tile = k / kTileCells, within = k - tile * kTileCells;
-    const int tm = tile / I.ntz, tn = tile - tm * I.ntz;
-    const int m = tm * kTile + (within >> 3), nn = tn * kTile + (within & 7);
+    int m, nn;
+    key_cell(I, k, m, nn);
     if (m >= I.nr || nn >= I.nz) continue;   // padding keys hold no particles
     const int cell = m * I.nz + nn;
     if (sp == 0) {

@@ -21,8 +21,17 @@ namespace pic {
 constexpr int kPush32Threads = 256;
 constexpr int kCollQ32 = 256;   // deferred collision candidates per chunk
 constexpr int kHalo32 = 3;
-constexpr int kPR32 = kTile + 2 * kHalo32 + 1;
-constexpr int kPZ32 = 2 * kTile + 2 * kHalo32 + 1;
+// the deposit patch: (tile extent in r + 2 halo + 1) x (two tiles along z + 2
+// halo + 1) nodes; the arrays hold the largest of the tile shapes
+__device__ __forceinline__ int patch32_pr(const Inst& I) { return (1 << I.tsr) + 2 * kHalo32 + 1; }
+__device__ __forceinline__ int patch32_pz(const Inst& I) { return (2 << I.tsz) + 2 * kHalo32 + 1; }
+constexpr int patch32_nodes(int lr, int lz) {
+  return ((1 << lr) + 2 * kHalo32 + 1) * ((2 << lz) + 2 * kHalo32 + 1);
+}
+constexpr int patch32_cells(int lr, int lz) { return ((1 << lr) + 2 * kHalo32) * ((2 << lz) + 2 * kHalo32); }
+constexpr int cmax32(int a, int b) { return a > b ? a : b; }
+constexpr int kPatch32Nodes = cmax32(patch32_nodes(3, 3), cmax32(patch32_nodes(4, 3), patch32_nodes(3, 4)));
+constexpr int kPatch32Cells = cmax32(patch32_cells(3, 3), cmax32(patch32_cells(4, 3), patch32_cells(3, 4)));
 constexpr float kHalfMeOverE = (float)(0.5 * kMe / kQe);   // E[eV] = kHalfMeOverE v^2
 constexpr float kTwoEOverMe = (float)(2.0 * kQe / kMe);    // v^2 = kTwoEOverMe E[eV]
 
@@ -234,15 +243,15 @@ __device__ __noinline__ void cathode_hit32(const Inst& I, float Xo, float X, flo
 template <int SP>
 __device__ __forceinline__ void deposit_run32(const Inst& I, int key, int m, int n, float a00,
                                               float a10, float a01, float a11, int cnt, int pm0,
-                                              int pn0, float* patch, int* cpatch) {
+                                              int pn0, int pr, int pz, float* patch, int* cpatch) {
   const int lm = m - pm0, ln = n - pn0;
-  if (lm >= 0 && lm + 1 < kPR32 && ln >= 0 && ln + 1 < kPZ32) {
-    float* p = patch + lm * kPZ32 + ln;
+  if (lm >= 0 && lm + 1 < pr && ln >= 0 && ln + 1 < pz) {
+    float* p = patch + lm * pz + ln;
     atomicAdd(p, a00);
-    atomicAdd(p + kPZ32, a10);
+    atomicAdd(p + pz, a10);
     atomicAdd(p + 1, a01);
-    atomicAdd(p + kPZ32 + 1, a11);
-    atomicAdd(cpatch + lm * (kPZ32 - 1) + ln, cnt);
+    atomicAdd(p + pz + 1, a11);
+    atomicAdd(cpatch + lm * (pz - 1) + ln, cnt);
   } else {
     double* q = I.qacc64[SP];
     const int gi = node_index(I, m, n), nz1 = I.nz + 1;
@@ -270,12 +279,13 @@ __device__ __forceinline__ double push_chunk32(const Inst& I, int c0, int ppt, f
     if (threadIdx.x == 0) {
       int m, nn;
       cell_mn(P.b[c0].y, m, nn);
-      anchor[0] = (m & ~(kTile - 1)) - kHalo32;
-      anchor[1] = (nn & ~(kTile - 1)) - kHalo32;
+      anchor[0] = (m & ~((1 << I.tsr) - 1)) - kHalo32;
+      anchor[1] = (nn & ~((1 << I.tsz) - 1)) - kHalo32;
       anchor[2] = 0;
     }
     __syncthreads();
     const int pm0 = anchor[0], pn0 = anchor[1];
+    const int pr = patch32_pr(I), pz = patch32_pz(I);
     // the next particle's two records are loaded while this one is pushed
     int i = run0 + lane;
     float4 a_nx = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -404,7 +414,7 @@ __device__ __forceinline__ double push_chunk32(const Inst& I, int c0, int ppt, f
           if (newkey != acc_key) {
             if (acc_key >= 0)
               deposit_run32<SP>(I, acc_key, acc_m, acc_n, s00, s10, s01, s11, acc_cnt, pm0, pn0,
-                                patch, cpatch);
+                                pr, pz, patch, cpatch);
             acc_key = newkey;
             acc_m = m1;
             acc_n = n1;
@@ -423,8 +433,8 @@ __device__ __forceinline__ double push_chunk32(const Inst& I, int c0, int ppt, f
       }
     }
     if (acc_key >= 0)
-      deposit_run32<SP>(I, acc_key, acc_m, acc_n, s00, s10, s01, s11, acc_cnt, pm0, pn0, patch,
-                        cpatch);
+      deposit_run32<SP>(I, acc_key, acc_m, acc_n, s00, s10, s01, s11, acc_cnt, pm0, pn0, pr, pz,
+                        patch, cpatch);
     if (diag) Kloc = 0.25 * I.mass[SP] * I.weight * (double)k2;
     __syncthreads();
     if (SP == 0) {
@@ -437,18 +447,18 @@ __device__ __forceinline__ double push_chunk32(const Inst& I, int c0, int ppt, f
         collide_at32(I, P, run0 + j * 32 + lane, step);
       }
     }
-    for (int k = threadIdx.x; k < kPR32 * kPZ32; k += blockDim.x) {
+    for (int k = threadIdx.x; k < pr * pz; k += blockDim.x) {
       const float v = patch[k];
       if (v != 0.0f) {
-        const int gm = pm0 + k / kPZ32, gn = pn0 + k % kPZ32;
+        const int gm = pm0 + k / pz, gn = pn0 + k % pz;
         atomicAdd(I.qacc64[SP] + node_index(I, gm, gn), (double)v);
         patch[k] = 0.0f;
       }
     }
-    for (int k = threadIdx.x; k < (kPR32 - 1) * (kPZ32 - 1); k += blockDim.x) {
+    for (int k = threadIdx.x; k < (pr - 1) * (pz - 1); k += blockDim.x) {
       const int c = cpatch[k];
       if (c != 0) {
-        const int gm = pm0 + k / (kPZ32 - 1), gn = pn0 + k % (kPZ32 - 1);
+        const int gm = pm0 + k / (pz - 1), gn = pn0 + k % (pz - 1);
         atomicAdd(&I.counts[SP][cell_key(I, gm, gn)], c);
         cpatch[k] = 0;
       }
@@ -466,15 +476,15 @@ int resident_blocks(const void* fn, int threads, int num_sms);   // step.cu
 template <int GATHER>
 __global__ void __launch_bounds__(kPush32Threads, 4) k_push32_all(const Inst* insts, WorkQueue* q,
                                                                    int ppt) {
-  __shared__ float patch[kPR32 * kPZ32];
-  __shared__ int cpatch[(kPR32 - 1) * (kPZ32 - 1)];
+  __shared__ float patch[kPatch32Nodes];
+  __shared__ int cpatch[kPatch32Cells];
   __shared__ int anchor[3];
   __shared__ int cq[kCollQ32];
   __shared__ Inst sI;
   __shared__ int s_inst, s_sp, s_skip;
   __shared__ long long s_c0;
-  for (int k = threadIdx.x; k < kPR32 * kPZ32; k += blockDim.x) patch[k] = 0.0f;
-  for (int k = threadIdx.x; k < (kPR32 - 1) * (kPZ32 - 1); k += blockDim.x) cpatch[k] = 0;
+  for (int k = threadIdx.x; k < kPatch32Nodes; k += blockDim.x) patch[k] = 0.0f;
+  for (int k = threadIdx.x; k < kPatch32Cells; k += blockDim.x) cpatch[k] = 0;
   int cur = -1;
   double K0 = 0.0, K1 = 0.0;
   const long long chunk = (long long)ppt * blockDim.x;
@@ -520,14 +530,14 @@ __global__ void __launch_bounds__(kPush32Threads, 4) k_push32_all(const Inst* in
 template <int GATHER, bool PLAIN>
 __global__ void __launch_bounds__(kPush32Threads, 4) k_push32_one(const Inst I, WorkQueue* q,
                                                                    int ppt) {
-  __shared__ float patch[kPR32 * kPZ32];
-  __shared__ int cpatch[(kPR32 - 1) * (kPZ32 - 1)];
+  __shared__ float patch[kPatch32Nodes];
+  __shared__ int cpatch[kPatch32Cells];
   __shared__ int anchor[3];
   __shared__ int cq[kCollQ32];
   __shared__ int s_sp, s_done, s_skip;
   __shared__ long long s_c0;
-  for (int k = threadIdx.x; k < kPR32 * kPZ32; k += blockDim.x) patch[k] = 0.0f;
-  for (int k = threadIdx.x; k < (kPR32 - 1) * (kPZ32 - 1); k += blockDim.x) cpatch[k] = 0;
+  for (int k = threadIdx.x; k < kPatch32Nodes; k += blockDim.x) patch[k] = 0.0f;
+  for (int k = threadIdx.x; k < kPatch32Cells; k += blockDim.x) cpatch[k] = 0;
   double K0 = 0.0, K1 = 0.0;
   const long long chunk = (long long)ppt * blockDim.x;
   for (;;) {

@@ -148,6 +148,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         L.pic_uses_graph.argtypes = [vp]
         L.pic_tuned_chunk.argtypes = [vp, C.POINTER(C.c_int)]
         L.pic_set_chunk.argtypes = [vp, C.c_int]
+        L.pic_set_tile.argtypes = [vp, C.c_int]
+        L.pic_tuned_tile.argtypes = [vp, C.POINTER(C.c_int)]
         L.pic_autotune_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _I64]
         L.pic_get_species_charge.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int]
         L.pic_sync.argtypes = [vp]
@@ -364,6 +366,17 @@ def pic_uses_graph(h: Handle) -> bool:
 def pic_tuned_chunk(h: Handle) -> int:
     v = C.c_int()
     _check(h, load_library().pic_tuned_chunk(h.ptr, C.byref(v)))
+    return v.value
+
+
+def pic_set_tile(h: Handle, shape: int = 0):
+    """Cell tile shape: 1 = 8 x 8, 2 = 16 x 8, 3 = 8 x 16 (r x z) fixed; 0 = autotuned."""
+    _check(h, load_library().pic_set_tile(h.ptr, int(shape)))
+
+
+def pic_tuned_tile(h: Handle) -> int:
+    v = C.c_int(0)
+    _check(h, load_library().pic_tuned_tile(h.ptr, C.byref(v)))
     return v.value
 
 

@@ -225,11 +225,12 @@ def test_periodic_sort_ensemble_equals_individual_runs(pg):
 
 
 def test_autotuner_retunes_when_the_counts_grow(pg):
-    """The push's chunk size is tuned again when the live particle count has
-    changed by a factor of 4 since the last tuning (an ensemble whose
-    discharges grow); the tuning steps and the recaptured graph leave the
-    results as they are: the ensemble still equals the instances run one by
-    one, bit for bit."""
+    """The push's chunk size and cell tile shape are tuned again when the live
+    particle count has changed by a factor of 4 since the last tuning (an
+    ensemble whose discharges grow); the tuning steps (the shape trials re-sort
+    the particles) and the recaptured graph leave the results as they are: the
+    ensemble still equals the instances run one by one, bit for bit, whatever
+    shapes the ensemble and the single runs ended on."""
     import torch
     insts = []
     for k, (p, parts) in enumerate(_instances()):
@@ -247,7 +248,7 @@ def test_autotuner_retunes_when_the_counts_grow(pg):
                 _load(pg, h, j, parts)
                 pg.pic_solve_fields(h, j)
         for h in runs:
-            pg.pic_step(h, 6)
+            pg.pic_step(h, 6)      # four chunk sizes, two more tile shapes
         info0 = pg.pic_autotune_info(runs[0])
         assert info0["tunings"] == 1
         for k in range(len(insts)):
@@ -257,9 +258,9 @@ def test_autotuner_retunes_when_the_counts_grow(pg):
         for h in runs:
             pg.pic_step(h, 1)      # its end copies the grown count to the host
             pg.pic_sync(h)         # (the next call reads it once the copy is done)
-            pg.pic_step(h, 6)      # sees it: four tuning steps, then the new graph
+            pg.pic_step(h, 6)      # sees it: six tuning steps, then the new graph
         info1 = pg.pic_autotune_info(runs[0])
-        print("tunings", info0, info1)
+        print("tunings", info0, info1, "tile shapes", [pg.pic_tuned_tile(h) for h in runs])
         assert info1["tunings"] == 2
         assert info1["particles_at_tuning"] >= 4 * info0["particles_at_tuning"]
         assert info1["particles_per_thread"] in (4, 8, 16, 32)

@@ -271,3 +271,22 @@ def test_fp32_sort_every(pg):
         pg.pic_step(h, 1)
     _check(pg, h, orc)
     pg.pic_destroy(h)
+
+
+@pytest.mark.parametrize("shape", [2, 3])
+def test_fp32_tile_shapes(pg, shape):
+    """FP32 records on the 16 x 8 and 8 x 16 cell tiles (the sort key and the
+    deposit patch of that shape, a full sort every third step): on the FP64
+    oracle's track at the FP32 bar after five steps."""
+    p = pic_inputs.params_rz32()
+    p.update(gamma_i=0.3, poisson_tol=1e-12, circuit_mode=1, Vs=400.0, Rext=100.0, n_avg=3,
+             sort_every=3)
+    p, parts = busy_state(p, ppc=16, seed=85 + shape)
+    p, orc, h = _pair32(pg, p, parts)
+    pg.pic_set_tile(h, shape)
+    for _ in range(5):
+        orc.step(1)
+        pg.pic_step(h, 1)
+    assert pg.pic_tuned_tile(h) == shape
+    _check(pg, h, orc)
+    pg.pic_destroy(h)

@@ -260,14 +260,16 @@ def test_graph_replay_matches_oracle(pg):
         p.update(gamma_i=0.5, poisson_tol=1e-13, circuit_mode=1, Vs=400.0, Rext=100.0, n_avg=3)
         p, parts = busy_state(p, ppc=8, seed=41)
         p, orc, h = _pair(pg, p, parts)
-        # the first four steps tune the push's chunk size (eager launches),
-        # later ones replay the captured step
-        for k in range(6):
+        # the first four steps tune the push's chunk size and the next two the
+        # other cell tile shapes (eager launches; a shape trial re-sorts the
+        # particles first), later ones replay the captured step
+        for k in range(8):
             orc.step(1)
             pg.pic_step(h, 1)
-            assert pg.pic_uses_graph(h) == (k >= 4)
+            assert pg.pic_uses_graph(h) == (k >= 6)
             _check_step(pg, h, orc)
         assert pg.pic_tuned_chunk(h) in (4, 8, 16, 32)
+        assert pg.pic_tuned_tile(h) in (1, 2, 3)
     side.synchronize()
 
 
@@ -335,7 +337,7 @@ def test_reweight_factor_checks_and_graph(pg):
         n0 = pg.pic_count(h, 0, 0)
         pg.pic_reweight(h, 0, 1)
         assert pg.pic_count(h, 0, 0) == n0
-        for _ in range(5):
+        for _ in range(7):    # six tuning steps, then the captured step
             orc.step(1)
             pg.pic_step(h, 1)
         assert pg.pic_uses_graph(h) == 1
@@ -503,10 +505,10 @@ def test_sort_every_graph_and_reads_between_sorts(pg):
                  sort_every=4, ied_bins=16, ied_emax=512.0)
         p, parts = busy_state(p, ppc=12, seed=81)
         p, orc, h = _pair(pg, p, parts)
-        pg.pic_step(h, 6)
-        orc.step(6)
+        pg.pic_step(h, 7)     # six tuning steps (each sorts), then the captured step
+        orc.step(7)
         assert pg.pic_uses_graph(h) == 1
-        assert pg.pic_count(h, 0, 0) == orc.count(0)       # compacts (step 6: unsorted)
+        assert pg.pic_count(h, 0, 0) == orc.count(0)       # compacts (step 7: unsorted)
         pg.pic_region_sample(h, 0)
         pg.pic_step(h, 2)
         orc.step(2)
@@ -636,4 +638,32 @@ def test_sine_transform_solve_fields(pg, nr, nz):
     pg.pic_step(h, 1)
     d = pg.pic_diagnostics(h, 0)
     assert d["poisson_iters"] <= 3 and d["poisson_resid"] <= 1e-13
+    pg.pic_destroy(h)
+
+
+@pytest.mark.parametrize("gather", [0, 1])
+def test_tile_shapes_match_oracle(pg, gather):
+    """The cell tile shape (8 x 8, 16 x 8, 8 x 16) changes the particles' sort
+    order and the push's deposit patch, not the results: with a full sort every
+    third step (dead slots and appended births in between) and the shape
+    switched between steps (the particles re-sorted by the new keys, mid-way
+    between two sorts), every step's counters and the final particles and
+    fields match the oracle at the FP64 bar, on a ragged 20 x 36 grid whose
+    tiles are partly outside it."""
+    p = pic_inputs.params_rz32(gather=gather)
+    p.update(nr=20, nz=36, L=p["R"] * 36 / 20, gamma_i=0.3, gamma_e=0.1, poisson_tol=1e-13,
+             circuit_mode=1, Vs=400.0, Rext=100.0, n_avg=3, sort_every=3)
+    p, parts = busy_state(p, ppc=16, seed=91 + gather)
+    p, orc, h = _pair(pg, p, parts)
+    pg.pic_set_chunk(h, 4)
+    for k, shape in enumerate((2, 2, 3, 3, 1, 2, 3)):
+        pg.pic_set_tile(h, shape)
+        assert pg.pic_tuned_tile(h) == shape
+        orc.step(1)
+        pg.pic_step(h, 1)
+        de, do = pg.pic_diagnostics(h, 0), orc.diag()
+        for key in ("N_e", "N_i", "n_ion_cath", "n_e_cath", "n_sey", "n_ionize", "n_excite",
+                    "n_elastic"):
+            assert de[key] == do[key], (k, shape, key)
+    _check_step(pg, h, orc)
     pg.pic_destroy(h)
