@@ -493,6 +493,13 @@ int pic_poisson_solve(int nr, int nz, double R, double L, double tol, int max_it
                       const double* Q_dev, double* phi_dev, void* work_dev, void* cuda_stream,
                       int* iters, double* resid);
 
+/* Measured FP64 FMA throughput of the current device (TFLOP/s, an FMA = 2
+ * flop): independent FMA chains on every SM, the fastest of three timed
+ * launches on `cuda_stream` (NULL: the default stream).  The denominator of
+ * the roofline of an FP64-pipe-bound kernel.  Allocates and frees a small
+ * output buffer on the stream; synchronous. */
+int pic_fp64_fma_rate(void* cuda_stream, double* tflops);
+
 /* Size in bytes of the device array that pic_poisson_solve_static uses as
  * its scratch; it holds the workspace of grids up to 256 x 512 cells. */
 #define PIC_POISSON_STATIC_BYTES (6u * 1024u * 1024u)

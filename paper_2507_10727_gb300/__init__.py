@@ -10,7 +10,7 @@ from .pic import (  # noqa: F401
     pic_create, pic_destroy, pic_set_particles, pic_count, pic_get_particles,
     pic_solve_fields, pic_set_phi, pic_get_fields, pic_set_circuit, pic_set_next_id,
     pic_get_next_id, pic_step, pic_uses_graph, pic_tuned_chunk, pic_set_chunk, pic_autotune_info,
-    pic_set_tile, pic_tuned_tile, pic_sync,
+    pic_set_tile, pic_tuned_tile, pic_fp64_fma_rate, pic_sync,
     pic_diagnostics, pic_reweight, pic_get_species_charge,
     pic_region_sample, pic_region_read, pic_region_reset, PicRegions,
     pic_save, pic_load,

@@ -13,7 +13,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpic_gb300.so")
-SOURCES = ["step.cu", "step32.cu", "poisson.cu", "api.cu", "noalloc.cu", "unet.cu"]
+SOURCES = ["step.cu", "step32.cu", "poisson.cu", "api.cu", "noalloc.cu", "unet.cu", "fp64_rate.cu"]
 HEADERS = ["common.cuh", "bits.cuh", "launch.h", "device_util.cuh", "unet.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]

@@ -149,6 +149,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         L.pic_tuned_chunk.argtypes = [vp, C.POINTER(C.c_int)]
         L.pic_set_chunk.argtypes = [vp, C.c_int]
         L.pic_set_tile.argtypes = [vp, C.c_int]
+        L.pic_fp64_fma_rate.argtypes = [vp, _D]
         L.pic_tuned_tile.argtypes = [vp, C.POINTER(C.c_int)]
         L.pic_autotune_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _I64]
         L.pic_get_species_charge.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int]
@@ -366,6 +367,17 @@ def pic_uses_graph(h: Handle) -> bool:
 def pic_tuned_chunk(h: Handle) -> int:
     v = C.c_int()
     _check(h, load_library().pic_tuned_chunk(h.ptr, C.byref(v)))
+    return v.value
+
+
+def pic_fp64_fma_rate(stream=None) -> float:
+    """Measured FP64 FMA throughput of the current device, TFLOP/s."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    v = C.c_double(0.0)
+    rc = load_library().pic_fp64_fma_rate(C.c_void_p(st.cuda_stream), C.byref(v))
+    if rc != 0:
+        raise PicError(rc, "pic_fp64_fma_rate")
     return v.value
 
 
