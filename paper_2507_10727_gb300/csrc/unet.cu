@@ -23,6 +23,7 @@
 #include <random>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "launch.h"
@@ -323,9 +324,11 @@ __global__ void __launch_bounds__(kTcThreads) k_conv3_tc(ConvArgs a) {
 // dZ[node][co] X[node + (dr - 1, dc - 1)][ci], tap = 3 dr + dc.  A CTA (input
 // channel chunk kc, split s) runs over output tiles of 8 x 16 nodes, t = s,
 // s + S, ...  Per tile the input patch (10 x 18 nodes x 16 channels) and the
-// dZ tile (128 nodes x COUT) are staged node-major by cp.async (two buffers:
-// the next tile loads while this one is transposed), then transposed by
-// ldmatrix.trans into K-major operand tiles with the nodes as K:
+// dZ tile (128 nodes x COUT) are staged node-major by two TMA tiled loads
+// (4-D tensor maps over channels, columns, rows, batch; zero fill outside
+// the grid; two buffers: the next tile loads while this one is transposed),
+// then transposed by ldmatrix.trans into K-major operand tiles with the nodes
+// as K:
 //   A[(dc, ci)][patch node (pr, c)] = X at patch (pr, c + dc): 48 rows, 10
 //     patch rows x 16 columns of K, so a row shift dr is a shift of K by 16
 //     (two core matrices: a descriptor offset);
@@ -349,6 +352,22 @@ struct WgArgs {
   int* err;           // set to 1 if a tensor-core wait reached its time limit
 };
 
+// TMA: a 4-D tiled load into shared memory, completion counted on an mbarrier
+__device__ __forceinline__ void tma_load4(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                          int c3, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+      "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
 constexpr int kWgTH = 8, kWgTW = 16;                     // output tile: rows x columns
 constexpr int kWgPH = kWgTH + 2, kWgPW = kWgTW + 2;      // input patch
 constexpr int kWgPatch = kWgPH * kWgPW * 32;             // patch bytes (16 channels)
@@ -365,47 +384,36 @@ __host__ __device__ constexpr unsigned wg_tcols(int cout) {
 }
 static_assert(kWgAOver <= wg_b(16), "A rows read past the A tile stay inside the B tile");
 
+// tmx: the layer input (channels, columns, rows, batch; the column and row
+// steps of a strided input in its byte strides); tmd: dZ (channels, columns,
+// rows, batch)
 template <int COUT>
-__global__ void __launch_bounds__(kWgThreads) k_conv3_wgrad(WgArgs a) {
+__global__ void __launch_bounds__(kWgThreads) k_conv3_wgrad(WgArgs a,
+                                                            const __grid_constant__ CUtensorMap tmx,
+                                                            const __grid_constant__ CUtensorMap tmd) {
   extern __shared__ __align__(1024) unsigned char sm[];
   constexpr int BB = wg_b(COUT);
   constexpr int RAW = wg_raw(COUT);
   constexpr unsigned TCOLS = wg_tcols(COUT);
-  // raw buffer r at sm + r RAW: patch [10][18][2][16 B], then dZ [COUT / 8][128][16 B]
+  // raw buffer r at sm + r RAW: patch [10][18][16 channels], then dZ [8][16][COUT]
   unsigned char* At = sm + 2 * RAW;        // A operand tile (its last MMAs read into Bt)
   unsigned char* Bt = At + kWgA;           // B operand tile
-  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(Bt + BB);
-  unsigned* taddr_s = reinterpret_cast<unsigned*>(mbar + 2);
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(Bt + BB);   // [0] MMA, [1..2] raw
+  unsigned* taddr_s = reinterpret_cast<unsigned*>(mbar + 3);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int kc = blockIdx.x, nkc = gridDim.x, s = blockIdx.y, S = gridDim.y;
   const int tw = (a.W + kWgTW - 1) / kWgTW, th = (a.H + kWgTH - 1) / kWgTH;
   const int T = a.B * tw * th;
 
+  // one thread: the TMA loads of tile t into raw buffer r
   auto stage_raw = [&](int t, int r) {
     unsigned char* Xp = sm + r * RAW;
-    unsigned char* Ds = Xp + kWgPatch;
     const int b = t / (tw * th), rr = t - b * tw * th;
     const int i0 = (rr / tw) * kWgTH, j0 = (rr % tw) * kWgTW;
-    const bf16* xb = a.x + (long long)b * a.x_bs;
-    for (int e = tid; e < kWgPH * kWgPW * 2; e += kWgThreads) {
-      const int p = e >> 1, half = e & 1;
-      const int pi = p / kWgPW, pj = p - pi * kWgPW;
-      const int gi = i0 + pi - 1, gj = j0 + pj - 1;
-      const bool ok = gi >= 0 && gi < a.H && gj >= 0 && gj < a.W;
-      const bf16* src = ok ? xb + ((long long)gi * a.x_step * a.x_w + (long long)gj * a.x_step) * a.x_cs +
-                                 a.x_c0 + kc * 16 + half * 8
-                           : a.x;
-      cp_async16(Xp + p * 32 + half * 16, src, ok ? 16 : 0);
-    }
-    const bf16* dzb = a.dz + (long long)b * a.dz_bs;
-    for (int e = tid; e < kWgTH * kWgTW * (COUT / 8); e += kWgThreads) {
-      const int g8 = e >> 7, k = e & 127;
-      const int gi = i0 + (k >> 4), gj = j0 + (k & 15);
-      const bool ok = gi < a.H && gj < a.W;
-      const bf16* src = ok ? dzb + ((long long)gi * a.W + gj) * a.dz_cs + a.dz_c0 + g8 * 8 : a.dz;
-      cp_async16(Ds + (g8 * 128 + k) * 16, src, ok ? 16 : 0);
-    }
-    cp_async_commit();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // after the generic reads
+    mbar_expect_tx(&mbar[1 + r], (unsigned)(kWgPatch + BB));
+    tma_load4(Xp, &tmx, a.x_c0 + kc * 16, j0 - 1, i0 - 1, b, &mbar[1 + r]);
+    tma_load4(Xp + kWgPatch, &tmd, a.dz_c0, j0, i0, b, &mbar[1 + r]);
   };
 
   float bpart[COUT / 16];
@@ -443,7 +451,7 @@ __global__ void __launch_bounds__(kWgThreads) k_conv3_wgrad(WgArgs a) {
       const int blk = job * 4 + (lane >> 3);
       const int cb = blk >> 4, kb = blk & 15;
       unsigned v[4];
-      ldsm_x4_t(v[0], v[1], v[2], v[3], Ds + (cb * 128 + kb * 8 + (lane & 7)) * 16);
+      ldsm_x4_t(v[0], v[1], v[2], v[3], Ds + (kb * 8 + (lane & 7)) * (COUT * 2) + cb * 16);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int bj = job * 4 + j;
@@ -456,15 +464,15 @@ __global__ void __launch_bounds__(kWgThreads) k_conv3_wgrad(WgArgs a) {
   };
 
   if (tid == 0) {
-    mbar_init(&mbar[0], 1);
+    for (int q = 0; q < 3; ++q) mbar_init(&mbar[q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    stage_raw(s, 0);   // s < T: the host launches at most T splits
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(taddr_s)),
                  "r"(TCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  stage_raw(s, 0);   // s < T: the host launches at most T splits
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const unsigned taddr = *taddr_s;
@@ -475,14 +483,14 @@ __global__ void __launch_bounds__(kWgThreads) k_conv3_wgrad(WgArgs a) {
   int i = 0;
   for (int t = s; t < T; t += S, ++i) {
     const int rb = i & 1;
-    cp_async_wait<0>();   // tile i in raw buffer rb (the only group in flight)
-    __syncthreads();
     // the next tile loads while this one is transposed (raw buffer rb ^ 1 was
-    // read by the transposition of tile i - 1, finished at the barrier above)
-    if (t + S < T) stage_raw(t + S, rb ^ 1);
-    // the MMAs of tile i - 1 read the operand tiles
-    bool f = false;
-    if (i >= 1) f = !mbar_wait(&mbar[0], (unsigned)(i - 1) & 1u);
+    // read by the transposition of tile i - 1, finished at that iteration's
+    // last barrier)
+    if (tid == 0 && t + S < T) stage_raw(t + S, rb ^ 1);
+    // tile i in raw buffer rb (its (i / 2)-th load), and the MMAs of tile
+    // i - 1 done with the operand tiles
+    bool f = !mbar_wait(&mbar[1 + rb], (unsigned)(i >> 1) & 1u);
+    if (i >= 1) f = f || !mbar_wait(&mbar[0], (unsigned)(i - 1) & 1u);
     if (__syncthreads_or(f)) {
       bad = true;
       break;
@@ -516,8 +524,14 @@ __global__ void __launch_bounds__(kWgThreads) k_conv3_wgrad(WgArgs a) {
     bad = __syncthreads_or(f);
   }
   if (bad) {
-    cp_async_wait<0>();
     if (tid == 0) atomicExch(a.err, 1);
+    // a load still in flight must not land after the CTA has gone: wait
+    // (time-limited) for tile i's load and, if it was issued, tile i + 1's
+    if (tid == 0) {
+      mbar_wait(&mbar[1 + (i & 1)], (unsigned)(i >> 1) & 1u);
+      if (s + (long long)(i + 1) * S < T) mbar_wait(&mbar[1 + ((i + 1) & 1)], (unsigned)((i + 1) >> 1) & 1u);
+    }
+    __syncthreads();
   } else {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp < 2) {
@@ -1186,6 +1200,44 @@ cudaError_t conv_dgrad(UNet* u, int Lx, const bf16* dz, long long dz_bs, int dz_
   return run_conv(a, st);
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// A 4-D BF16 tensor map (channels, columns, rows, batch) over node-major
+// activations: `cs` channels per node, nodes `step` apart along a row of
+// `row` buffer nodes, rows `step` apart, images `bs` elements apart; box of
+// bc channels x bw columns x bh rows x 1 image, zero fill outside.  Every
+// stride is a multiple of 16 bytes because cs is a multiple of 8.
+bool tensor_map4(CUtensorMap* m, const bf16* base, int cs, int W, int H, int B, int step, int row,
+                 long long bs, int bc, int bw, int bh) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn || cs % 8 || bc % 8) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)cs, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {(cuuint64_t)step * cs * 2, (cuuint64_t)step * row * cs * 2,
+                                 (cuuint64_t)bs * 2};
+  const cuuint32_t box[4] = {(cuuint32_t)bc, (cuuint32_t)bw, (cuuint32_t)bh, 1u};
+  const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)base, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t conv_wgrad(UNet* u, int Lx, const bf16* x, long long x_bs, int x_cs, int x_c0,
                        int x_step, int x_w, const bf16* dz, long long dz_bs, int dz_cs, int dz_c0,
                        int H, int W, int B, cudaStream_t st) {
@@ -1204,10 +1256,17 @@ cudaError_t conv_wgrad(UNet* u, int Lx, const bf16* x, long long x_bs, int x_cs,
   if (S > T) S = T;
   if (S < 1) S = 1;
   const dim3 grid(nkc, (unsigned)S);
+  // the TMA boxes start at channels x_c0 + 16 kc and dz_c0: multiples of 8
+  // (16 bytes), as a tiled load's innermost coordinate must be
+  if (x_c0 % 8 || dz_c0 % 8) return cudaErrorInvalidValue;
+  alignas(64) CUtensorMap tmx, tmd;
+  if (!tensor_map4(&tmx, x, x_cs, W, H, B, x_step, x_w, x_bs, 16, kWgPW, kWgPH) ||
+      !tensor_map4(&tmd, dz, dz_cs, W, H, B, 1, W, dz_bs, L.cout, kWgTW, kWgTH))
+    return cudaErrorInvalidValue;
   switch (L.cout) {
-    case 64: k_conv3_wgrad<64><<<grid, kWgThreads, wg_smem(64), st>>>(a); break;
-    case 32: k_conv3_wgrad<32><<<grid, kWgThreads, wg_smem(32), st>>>(a); break;
-    default: k_conv3_wgrad<16><<<grid, kWgThreads, wg_smem(16), st>>>(a); break;
+    case 64: k_conv3_wgrad<64><<<grid, kWgThreads, wg_smem(64), st>>>(a, tmx, tmd); break;
+    case 32: k_conv3_wgrad<32><<<grid, kWgThreads, wg_smem(32), st>>>(a, tmx, tmd); break;
+    default: k_conv3_wgrad<16><<<grid, kWgThreads, wg_smem(16), st>>>(a, tmx, tmd); break;
   }
   const long long n = (long long)(L.cin_pad >> 4) * 9 * L.cout * 16 + L.cout;
   k_wgrad_reduce<<<(unsigned)((n + kRedE - 1) / kRedE), kRedE * kRedG, 0, st>>>(
