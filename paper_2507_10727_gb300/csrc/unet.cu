@@ -114,13 +114,18 @@ __device__ __forceinline__ void store8(bf16* p, const float* v) {
 
 // ---- tcgen05 helpers --------------------------------------------------------
 constexpr int kTcThreads = 128;          // 4 warps = the 4 TMEM lane quarters
-constexpr int kTcM = 128;                // output nodes per CTA (MMA M)
-constexpr int kWinPos = 136;             // staged nodes per window (130 used)
-constexpr int kAStage = 3 * 2 * kWinPos * 16;   // 3 windows x 2 k-groups, bytes
+constexpr int kTcM = 128;                // output nodes per tile (MMA M)
 constexpr double kWaitLimitNs = 1.0e9;   // tensor-core completion wait limit
 
+// forward convolution: output tiles of 8 x 16 nodes; per 16-channel input
+// chunk six input boxes (3 column shifts x 2 groups of 8 channels) of 10 rows
+// x 16 columns x 8 channels, then the chunk's 9 x 2 x COB weight rows
+constexpr int kFwTH = 8, kFwTW = 16;
+constexpr int kFwBox = (kFwTH + 2) * kFwTW * 16;          // 2,560 bytes
+constexpr int kFwA = 6 * kFwBox;
 __host__ __device__ constexpr int tc_b_stage(int cob) { return 9 * 2 * cob * 16; }
-__host__ __device__ constexpr int tc_smem(int cob) { return 2 * (kAStage + tc_b_stage(cob)) + 64; }
+__host__ __device__ constexpr int tc_stage(int cob) { return kFwA + tc_b_stage(cob); }
+__host__ __device__ constexpr int tc_smem(int cob) { return 2 * tc_stage(cob) + 64; }
 __host__ __device__ constexpr int tc_tcols(int cob) { return cob <= 32 ? 32 : 64; }
 
 // shared-memory matrix descriptor: canonical K-major layout without swizzle;
@@ -178,119 +183,151 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v) {
   for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+// TMA: a 4-D tiled load into shared memory, completion counted on an mbarrier
+__device__ __forceinline__ void tma_load4(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                          int c3, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+      "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// bulk copy of `bytes` (a multiple of 16) from global to shared memory
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,
+                                          unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Persistent: a CTA takes work items (output tile of 8 x 16 nodes, block of
+// COB output channels), item = blockIdx.x, + gridDim.x, ...; its chunks of 16
+// input channels run through two stages: thread 0 loads a chunk's six input
+// boxes by TMA (tensor map tmx over channels, columns, rows, batch of the
+// input; zero fill outside the grid) and its weight rows by bulk copies
+// (packed [cin / 16][9][2][cout][8]), one mbarrier per stage counting the
+// bytes; the next chunk (of this item, or the next item's first) loads while
+// this one's MMAs run.  A tap (dr, dc) is the box of column shift dc read
+// from row dr on: 8 output rows x 16 columns are M = 128 consecutive 16-byte
+// rows of the K-major layout, so its A descriptor starts dr x 16 nodes into
+// the box.  The accumulator (COB FP32 columns of TMEM) is read after the
+// item's last chunk, bias, ReLU and the accumulate option applied, stored as
+// BF16 (output node step y_step).
 template <int COB>
-__global__ void __launch_bounds__(kTcThreads) k_conv3_tc(ConvArgs a) {
+__global__ void __launch_bounds__(kTcThreads) k_conv3_tc(ConvArgs a,
+                                                         const __grid_constant__ CUtensorMap tmx) {
   extern __shared__ __align__(1024) unsigned char sm[];
   constexpr int BST = tc_b_stage(COB);
+  constexpr int STG = tc_stage(COB);
   constexpr unsigned TCOLS = tc_tcols(COB);
-  unsigned char* stA0 = sm;
-  unsigned char* stB0 = sm + 2 * kAStage;
-  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sm + 2 * (kAStage + BST));
-  unsigned* taddr_s = reinterpret_cast<unsigned*>(mbar + 2);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm + 2 * STG);   // [s] loads, [2 + s] MMAs
+  unsigned* taddr_s = reinterpret_cast<unsigned*>(bar + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int Wp = a.W + 2;
-  // padded node index q = (i + 1) * Wp + j + 1 of one image (< 2^31 for any grid that fits)
-  const int q_first = Wp + 1, q_last = a.H * Wp + a.W;
-  const int T = (q_last - q_first + kTcM) / kTcM;
-  const int b = blockIdx.x / T, t = blockIdx.x - b * T;
-  const int q0 = q_first + kTcM * t;
-  const int co0 = blockIdx.y * COB;
-  const bf16* xb = a.x + (long long)b * a.x_bs;
-
+  const int tw = (a.W + kFwTW - 1) / kFwTW, th = (a.H + kFwTH - 1) / kFwTH;
+  const int ncob = a.cout / COB;
+  const long long items = (long long)a.B * tw * th * ncob;
+  const int nkc = a.cin >> 4;
+  auto decode = [&](long long item, int& b, int& i0, int& j0, int& co0) {
+    const long long tile = item / ncob;
+    co0 = (int)(item - tile * ncob) * COB;
+    b = (int)(tile / ((long long)tw * th));
+    const int r = (int)(tile - (long long)b * tw * th);
+    i0 = (r / tw) * kFwTH;
+    j0 = (r % tw) * kFwTW;
+  };
+  // thread 0: the loads of chunk kc of `item` into stage st
+  auto stage = [&](long long item, int kc, int st) {
+    int b, i0, j0, co0;
+    decode(item, b, i0, j0, co0);
+    unsigned char* base = sm + st * STG;
+    mbar_expect_tx(&bar[st], (unsigned)STG);
+#pragma unroll
+    for (int dc = 0; dc < 3; ++dc)
+#pragma unroll
+      for (int g = 0; g < 2; ++g)
+        tma_load4(base + (dc * 2 + g) * kFwBox, &tmx, a.x_c0 + kc * 16 + g * 8, j0 + dc - 1, i0 - 1,
+                  b, &bar[st]);
+    for (int q = 0; q < 18; ++q)   // q = 2 tap + g
+      bulk_load(base + kFwA + q * COB * 16, a.w + (((long long)kc * 18 + q) * a.cout + co0) * 8,
+                COB * 16, &bar[st]);
+  };
   if (tid == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    for (int q = 0; q < 4; ++q) mbar_init(&bar[q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (blockIdx.x < items) stage(blockIdx.x, 0, 0);
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(taddr_s)),
                  "r"(TCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // stage chunk kc (16 input channels) into buffer s
-  auto stage = [&](int kc, int s) {
-    unsigned char* A = stA0 + s * kAStage;
-    unsigned char* Bs = stB0 + s * BST;
-    for (int e = tid; e < 3 * 2 * 130; e += kTcThreads) {
-      const int w = e / 260, r = e - w * 260, g = r / 130, p = r - g * 130;
-      const int qq = q0 + (w - 1) * Wp - 1 + p;     // >= 0 since q0 >= Wp + 1
-      const int pi = (int)((unsigned)qq / (unsigned)Wp);
-      const int pj = qq - pi * Wp;
-      const bool ok = pi >= 1 && pi <= a.H && pj >= 1 && pj <= a.W;
-      const bf16* src = ok ? xb + ((long long)(pi - 1) * a.x_step * a.x_w + (long long)(pj - 1) * a.x_step) * a.x_cs +
-                                 a.x_c0 + kc * 16 + g * 8
-                           : a.x;
-      cp_async16(A + ((w * 2 + g) * kWinPos + p) * 16, src, ok ? 16 : 0);
-    }
-    for (int e = tid; e < 9 * 2 * COB; e += kTcThreads) {
-      const int tap = e / (2 * COB), r = e - tap * 2 * COB, g = r / COB, c = r - g * COB;
-      const bf16* src = a.w + (((long long)kc * 9 + tap) * a.cout + co0 + c) * 16 + g * 8;
-      cp_async16(Bs + ((tap * 2 + g) * COB + c) * 16, src, 16);
-    }
-    cp_async_commit();
-  };
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const unsigned taddr = *taddr_s;
   // D f32, A and B bf16, both K-major, N = COB, M = 128
   const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(COB >> 3) << 17) |
                          ((unsigned)(kTcM >> 4) << 24);
-  const int nkc = a.cin >> 4;
+  long long g = 0;                                  // chunk being computed (thread 0)
+  long long issued = blockIdx.x < items ? 1 : 0;    // chunks whose loads were issued (thread 0)
   bool bad = false;
-  stage(0, 0);
-  for (int kc = 0; kc < nkc; ++kc) {
-    const int s = kc & 1;
-    if (kc + 1 < nkc) {
-      // the MMAs of chunk kc - 1 read buffer s ^ 1
-      bool f = false;
-      if (kc >= 1) f = !mbar_wait(&mbar[s ^ 1], (unsigned)((kc - 1) >> 1) & 1u);
-      if (__syncthreads_or(f)) {
-        bad = true;
-        break;
-      }
-      stage(kc + 1, s ^ 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+  for (long long item = blockIdx.x; item < items; item += gridDim.x) {
+    bool f = false;
     if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const unsigned aA = smem_u32(stA0 + s * kAStage), aB = smem_u32(stB0 + s * BST);
+      for (int kc = 0; kc < nkc && !f; ++kc, ++g) {
+        const int st = (int)(g & 1);
+        // the next chunk into the other stage, once the MMAs of chunk g - 1
+        // (which read that stage) are done
+        const bool more = kc + 1 < nkc || item + gridDim.x < items;
+        if (more) {
+          if (g >= 1) f = !mbar_wait(&bar[2 + (st ^ 1)], (unsigned)((g - 1) >> 1) & 1u);
+          if (f) break;
+          if (kc + 1 < nkc) stage(item, kc + 1, st ^ 1);
+          else stage(item + gridDim.x, 0, st ^ 1);
+          ++issued;
+        }
+        f = !mbar_wait(&bar[st], (unsigned)(g >> 1) & 1u);
+        if (f) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned aA = smem_u32(sm + st * STG), aB = aA + kFwA;
 #pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        const int dr = tap / 3, dc = tap - dr * 3;
-        const unsigned long long ad =
-            smem_desc(aA + (unsigned)((dr * 2 * kWinPos + dc) * 16), kWinPos * 16, 128);
-        const unsigned long long bd = smem_desc(aB + (unsigned)(tap * 2 * COB * 16), COB * 16, 128);
-        const unsigned acc = (kc > 0 || tap > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
-            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        for (int tap = 0; tap < 9; ++tap) {
+          const int dr = tap / 3, dc = tap - dr * 3;
+          const unsigned long long ad =
+              smem_desc(aA + (unsigned)(dc * 2 * kFwBox + dr * kFwTW * 16), kFwBox, 128);
+          const unsigned long long bd = smem_desc(aB + (unsigned)(tap * 2 * COB * 16), COB * 16, 128);
+          const unsigned acc = (kc > 0 || tap > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&bar[2 + st]))
+                     : "memory");
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&mbar[s]))
-                   : "memory");
+      // the item's accumulator is complete once its last chunk's MMAs are
+      if (!f) f = !mbar_wait(&bar[2 + (int)((g - 1) & 1)], (unsigned)((g - 1) >> 1) & 1u);
     }
-  }
-  if (!bad) {
-    const bool f = !mbar_wait(&mbar[(nkc - 1) & 1], (unsigned)((nkc - 1) >> 1) & 1u);
-    bad = __syncthreads_or(f);
-  }
-  if (bad) {
-    cp_async_wait<0>();
-    if (tid == 0) atomicExch(a.err, 1);
-  } else {
+    if (__syncthreads_or(f)) {
+      bad = true;
+      break;
+    }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int q = q0 + 32 * warp + lane;
-    const int pi = (int)((unsigned)q / (unsigned)Wp);
-    const int pj = q - pi * Wp;
-    const bool mine = q <= q_last && pj >= 1 && pj <= a.W;
+    int b, i0, j0, co0;
+    decode(item, b, i0, j0, co0);
+    const int r = 32 * warp + lane;
+    const int gi = i0 + (r >> 4), gj = j0 + (r & 15);
+    const bool mine = gi < a.H && gj < a.W;
     bf16* dst = a.y + (long long)b * a.y_bs +
-                ((long long)(pi - 1) * a.y_step * a.y_w + (long long)(pj - 1) * a.y_step) * a.y_cs +
-                a.y_c0 + co0;
+                ((long long)gi * a.y_step * a.y_w + (long long)gj * a.y_step) * a.y_cs + a.y_c0 + co0;
 #pragma unroll
     for (int c = 0; c < COB; c += 16) {
       float v[16];
@@ -312,6 +349,18 @@ __global__ void __launch_bounds__(kTcThreads) k_conv3_tc(ConvArgs a) {
       store8(dst + c, v);
       store8(dst + c + 8, v + 8);
     }
+    // the next item's MMAs overwrite the accumulator after every lane read it
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  if (bad) {
+    if (tid == 0) {
+      atomicExch(a.err, 1);
+      // loads still in flight must land before the CTA goes: wait
+      // (time-limited) for every issued chunk not yet consumed
+      for (long long c = g; c < issued; ++c) mbar_wait(&bar[c & 1], (unsigned)(c >> 1) & 1u);
+    }
+    __syncthreads();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -351,22 +400,6 @@ struct WgArgs {
   float* pb;          // [S][COUT]
   int* err;           // set to 1 if a tensor-core wait reached its time limit
 };
-
-// TMA: a 4-D tiled load into shared memory, completion counted on an mbarrier
-__device__ __forceinline__ void tma_load4(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
-                                          int c3, unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
-      "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
 
 constexpr int kWgTH = 8, kWgTW = 16;                     // output tile: rows x columns
 constexpr int kWgPH = kWgTH + 2, kWgPW = kWgTW + 2;      // input patch
@@ -1057,6 +1090,11 @@ struct PackTable {
   long long w_off[kNumConv], wf_off[kNumConv], wd_off[kNumConv];
 };
 
+// packed layout [K / 16][9][2][N][8]: element e holds input channel
+// 16 kc + 8 g + k8 of output channel n for tap `tap` (the forward weights:
+// K = cin_pad, N = cout; the data gradient's: K = cout, N = cin_pad, taps
+// flipped), so that a chunk's rows of 8 channels for a block of N are one
+// contiguous run
 __global__ void k_pack_all(PackTable t, const float* p, bf16* wf, bf16* wd) {
   const int L = blockIdx.y;
   const int cin = t.cin[L], cinp = t.cin_pad[L], cout = t.cout[L];
@@ -1064,25 +1102,29 @@ __global__ void k_pack_all(PackTable t, const float* p, bf16* wf, bf16* wd) {
   const long long nf = (long long)cinp * 9 * cout;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nf;
        e += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(e & 15);
-    long long r = e >> 4;
+    const int k8 = (int)(e & 7);
+    long long r = e >> 3;
     const int co = (int)(r % cout);
     r /= cout;
+    const int g = (int)(r & 1);
+    r >>= 1;
     const int tap = (int)(r % 9);
     const int kc = (int)(r / 9);
-    const int ci = kc * 16 + k;
+    const int ci = kc * 16 + g * 8 + k8;
     wf[t.wf_off[L] + e] = __float2bfloat16_rn(ci < cin ? W[((long long)co * cin + ci) * 9 + tap] : 0.0f);
   }
   if (t.wd_off[L] < 0) return;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nf;
        e += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(e & 15);
-    long long r = e >> 4;
+    const int k8 = (int)(e & 7);
+    long long r = e >> 3;
     const int ci = (int)(r % cinp);
     r /= cinp;
+    const int g = (int)(r & 1);
+    r >>= 1;
     const int tapd = (int)(r % 9);
     const int kc = (int)(r / 9);
-    const int co = kc * 16 + k;
+    const int co = kc * 16 + g * 8 + k8;
     wd[t.wd_off[L] + e] =
         __float2bfloat16_rn(ci < cin ? W[((long long)co * cin + ci) * 9 + (8 - tapd)] : 0.0f);
   }
@@ -1144,6 +1186,7 @@ struct UNet {
   bool warm = false;
   long long adam_t = 0;
   int wg_ctas[3] = {0, 0, 0};  // resident weight-gradient CTAs (COUT 16, 32, 64), at most kMaxSplit
+  long long tc_ctas[4] = {1, 1, 1, 1};   // resident forward-convolution CTAs (COB 16, 32, 48, 64)
   UAllocFn alloc = nullptr;
   void* actx = nullptr;
   long long npx(int l) const { return (long long)H[l] * W[l]; }
@@ -1158,46 +1201,6 @@ int cob_for(int cout) {
   if (cout % 48 == 0) return 48;
   if (cout % 32 == 0) return 32;
   return 16;
-}
-
-cudaError_t run_conv(const ConvArgs& a, cudaStream_t st) {
-  const int cob = cob_for(a.cout);
-  const long long count = (long long)(a.H - 1) * (a.W + 2) + a.W;   // padded-row nodes spanned
-  const int T = (int)((count + kTcM - 1) / kTcM);
-  const dim3 grid(T * a.B, a.cout / cob);
-  switch (cob) {
-    case 64: k_conv3_tc<64><<<grid, kTcThreads, tc_smem(64), st>>>(a); break;
-    case 48: k_conv3_tc<48><<<grid, kTcThreads, tc_smem(48), st>>>(a); break;
-    case 32: k_conv3_tc<32><<<grid, kTcThreads, tc_smem(32), st>>>(a); break;
-    default: k_conv3_tc<16><<<grid, kTcThreads, tc_smem(16), st>>>(a); break;
-  }
-  return cudaGetLastError();
-}
-
-// forward conv of layer L
-cudaError_t conv_fwd(UNet* u, int Lx, const bf16* x, long long x_bs, int x_cs, int x_c0, int x_step,
-                     int x_w, bf16* y, long long y_bs, int y_cs, int y_c0, int H, int W, int B,
-                     cudaStream_t st) {
-  const ULayerInfo& L = u->L[Lx];
-  ConvArgs a;
-  a.x = x; a.x_bs = x_bs; a.x_cs = x_cs; a.x_c0 = x_c0; a.x_step = x_step; a.x_w = x_w;
-  a.w = u->wf + L.wf_off; a.bias = u->p + L.b_off; a.cin = L.cin_pad; a.cout = L.cout;
-  a.y = y; a.y_bs = y_bs; a.y_cs = y_cs; a.y_c0 = y_c0; a.y_step = 1; a.y_w = W;
-  a.H = H; a.W = W; a.B = B; a.relu = 1; a.accumulate = 0; a.err = &u->ud->err;
-  return run_conv(a, st);
-}
-
-// data gradient of layer L: dz (node step 1) -> dx (node step dx_step)
-cudaError_t conv_dgrad(UNet* u, int Lx, const bf16* dz, long long dz_bs, int dz_cs, int dz_c0,
-                       bf16* dx, long long dx_bs, int dx_cs, int dx_c0, int dx_step, int dx_w,
-                       int H, int W, int B, bool accumulate, cudaStream_t st) {
-  const ULayerInfo& L = u->L[Lx];
-  ConvArgs a;
-  a.x = dz; a.x_bs = dz_bs; a.x_cs = dz_cs; a.x_c0 = dz_c0; a.x_step = 1; a.x_w = W;
-  a.w = u->wd + L.wd_off; a.bias = nullptr; a.cin = L.cout; a.cout = L.cin_pad;
-  a.y = dx; a.y_bs = dx_bs; a.y_cs = dx_cs; a.y_c0 = dx_c0; a.y_step = dx_step; a.y_w = dx_w;
-  a.H = H; a.W = W; a.B = B; a.relu = 0; a.accumulate = accumulate ? 1 : 0; a.err = &u->ud->err;
-  return run_conv(a, st);
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
@@ -1236,6 +1239,53 @@ bool tensor_map4(CUtensorMap* m, const bf16* base, int cs, int W, int H, int B, 
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)base, dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t run_conv(UNet* u, const ConvArgs& a, cudaStream_t st) {
+  const int cob = cob_for(a.cout);
+  // the TMA boxes start at channel x_c0 + 16 kc + 8 g: a multiple of 8 (16
+  // bytes), as a tiled load's innermost coordinate must be
+  if (a.x_c0 % 8) return cudaErrorInvalidValue;
+  alignas(64) CUtensorMap tmx;
+  if (!tensor_map4(&tmx, a.x, a.x_cs, a.W, a.H, a.B, a.x_step, a.x_w, a.x_bs, 8, kFwTW, kFwTH + 2))
+    return cudaErrorInvalidValue;
+  const long long items = (long long)a.B * ((a.W + kFwTW - 1) / kFwTW) *
+                          ((a.H + kFwTH - 1) / kFwTH) * (a.cout / cob);
+  const int q = cob == 64 ? 3 : cob == 48 ? 2 : cob == 32 ? 1 : 0;
+  const long long grid = items < u->tc_ctas[q] ? items : u->tc_ctas[q];
+  switch (cob) {
+    case 64: k_conv3_tc<64><<<(unsigned)grid, kTcThreads, tc_smem(64), st>>>(a, tmx); break;
+    case 48: k_conv3_tc<48><<<(unsigned)grid, kTcThreads, tc_smem(48), st>>>(a, tmx); break;
+    case 32: k_conv3_tc<32><<<(unsigned)grid, kTcThreads, tc_smem(32), st>>>(a, tmx); break;
+    default: k_conv3_tc<16><<<(unsigned)grid, kTcThreads, tc_smem(16), st>>>(a, tmx); break;
+  }
+  return cudaGetLastError();
+}
+
+// forward conv of layer L
+cudaError_t conv_fwd(UNet* u, int Lx, const bf16* x, long long x_bs, int x_cs, int x_c0, int x_step,
+                     int x_w, bf16* y, long long y_bs, int y_cs, int y_c0, int H, int W, int B,
+                     cudaStream_t st) {
+  const ULayerInfo& L = u->L[Lx];
+  ConvArgs a;
+  a.x = x; a.x_bs = x_bs; a.x_cs = x_cs; a.x_c0 = x_c0; a.x_step = x_step; a.x_w = x_w;
+  a.w = u->wf + L.wf_off; a.bias = u->p + L.b_off; a.cin = L.cin_pad; a.cout = L.cout;
+  a.y = y; a.y_bs = y_bs; a.y_cs = y_cs; a.y_c0 = y_c0; a.y_step = 1; a.y_w = W;
+  a.H = H; a.W = W; a.B = B; a.relu = 1; a.accumulate = 0; a.err = &u->ud->err;
+  return run_conv(u, a, st);
+}
+
+// data gradient of layer L: dz (node step 1) -> dx (node step dx_step)
+cudaError_t conv_dgrad(UNet* u, int Lx, const bf16* dz, long long dz_bs, int dz_cs, int dz_c0,
+                       bf16* dx, long long dx_bs, int dx_cs, int dx_c0, int dx_step, int dx_w,
+                       int H, int W, int B, bool accumulate, cudaStream_t st) {
+  const ULayerInfo& L = u->L[Lx];
+  ConvArgs a;
+  a.x = dz; a.x_bs = dz_bs; a.x_cs = dz_cs; a.x_c0 = dz_c0; a.x_step = 1; a.x_w = W;
+  a.w = u->wd + L.wd_off; a.bias = nullptr; a.cin = L.cout; a.cout = L.cin_pad;
+  a.y = dx; a.y_bs = dx_bs; a.y_cs = dx_cs; a.y_c0 = dx_c0; a.y_step = dx_step; a.y_w = dx_w;
+  a.H = H; a.W = W; a.B = B; a.relu = 0; a.accumulate = accumulate ? 1 : 0; a.err = &u->ud->err;
+  return run_conv(u, a, st);
 }
 
 cudaError_t conv_wgrad(UNet* u, int Lx, const bf16* x, long long x_bs, int x_cs, int x_c0,
@@ -1598,6 +1648,23 @@ UNet* unet_create(int nr, int nz, int bmax, int n_inst, int mode, unsigned long 
                          (const void*)k_conv3_wgrad<64>};
     const int wsm[3] = {wg_smem(16), wg_smem(32), wg_smem(64)};
     const int tcols[3] = {(int)wg_tcols(16), (int)wg_tcols(32), (int)wg_tcols(64)};
+    const void* tk[4] = {(const void*)k_conv3_tc<16>, (const void*)k_conv3_tc<32>,
+                         (const void*)k_conv3_tc<48>, (const void*)k_conv3_tc<64>};
+    const int tsm[4] = {tc_smem(16), tc_smem(32), tc_smem(48), tc_smem(64)};
+    const int tcc[4] = {tc_tcols(16), tc_tcols(32), tc_tcols(48), tc_tcols(64)};
+    for (int q = 0; q < 4; ++q) {
+      cudaFuncAttributes fa;
+      int regs = 64;
+      if (cudaFuncGetAttributes(&fa, tk[q]) == cudaSuccess && fa.numRegs > 0) regs = fa.numRegs;
+      int per_sm = 2048 / kTcThreads;
+      const int by_regs = regs_sm / (((regs + 7) / 8 * 8) * kTcThreads);
+      const int by_smem = smem_sm > 0 ? smem_sm / (tsm[q] + smem_rsv) : 1;
+      per_sm = by_regs < per_sm ? by_regs : per_sm;
+      per_sm = by_smem < per_sm ? by_smem : per_sm;
+      per_sm = 512 / tcc[q] < per_sm ? 512 / tcc[q] : per_sm;
+      if (per_sm < 1) per_sm = 1;
+      u->tc_ctas[q] = (long long)per_sm * (sms > 0 ? sms : 1);
+    }
     for (int q = 0; q < 3; ++q) {
       cudaFuncAttributes fa;
       int regs = 64;
