@@ -4,20 +4,17 @@
 // the paper's solver is the judge: the guess only changes where the solve
 // starts, never where it ends).
 //
-// Forward and data-gradient convolutions run on the 5th-generation tensor
-// cores (tcgen05.mma, BF16 operands, FP32 accumulator in tensor memory): a CTA
-// owns 128 consecutive nodes of the row-major node grid with one virtual zero
-// column on each side, so that every 3x3 tap of those 128 outputs reads 128
-// consecutive (padded) input nodes.  Three such windows (rows above, at and
-// below) of one 16-channel input chunk and the chunk's 9 x COB weights are
-// staged in shared memory in the canonical K-major layout (8 nodes x 16 bytes
-// per core matrix); a tap's operand is a window at a start offset of 0-2
-// nodes.  One thread issues the 9 MMAs of a chunk; the next chunk is staged
-// while they run (two stages, mbarrier completion); the epilogue reads the
-// accumulator with tcgen05.ld.  The data gradient is the same kernel on
-// flipped, transposed weights.  The weight gradient contracts over nodes on
-// the same tensor cores (operands transposed into K-major tiles by
-// ldmatrix.trans, split-K over tiles, deterministic reduction).
+// All convolutions run on the 5th-generation tensor cores (tcgen05.mma, BF16
+// operands, FP32 accumulator in tensor memory) over output tiles of 8 x 16
+// nodes, their operands staged by TMA tiled loads (4-D tensor maps over
+// channels, columns, rows and batch of the node-major activations; zero fill
+// outside the grid).  The forward convolution (and the data gradient, the same
+// kernel on flipped, transposed weights) is persistent: a tap (dr, dc) is a
+// box of column shift dc read from row dr on, a descriptor offset, and the
+// next chunk loads while this one's MMAs run.  The weight gradient contracts
+// over nodes: its operands are transposed into K-major tiles by ldmatrix.trans
+// and each output row takes three MMAs (one per row shift); split-K over tiles
+// with a deterministic reduction.
 #include <cmath>
 #include <cstring>
 #include <random>
