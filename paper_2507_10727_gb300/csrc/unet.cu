@@ -1,8 +1,8 @@
 // unet.cu -- the learned Poisson warm start: a BF16 U-Net on the node grid,
 // its forward and backward passes, Adam training on snapshots the simulation
-// records, and the per-step guess (north-star pattern "learned warm start";
-// the paper's solver is the judge: the guess only changes where the solve
-// starts, never where it ends).
+// records, and the per-step guess of the Poisson start (the solver still
+// runs to its tolerance: the guess only changes where the solve starts, never
+// where it ends).
 //
 // All convolutions run on the 5th-generation tensor cores (tcgen05.mma, BF16
 // operands, FP32 accumulator in tensor memory) over output tiles of 8 x 16
