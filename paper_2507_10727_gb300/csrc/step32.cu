@@ -263,6 +263,43 @@ __device__ __forceinline__ void deposit_run32(const Inst& I, int key, int m, int
   }
 }
 
+// The flush of the lanes whose cell changed this iteration (flag fl), by the
+// whole warp: the flushing lanes hold consecutive particles, so lanes of one
+// cell form runs of adjacent lanes; a segmented suffix sum by shuffles (runs
+// of adjacent flushing lanes with the same key) leaves each run's sums in its
+// first lane, which alone adds them to the patch (one set of shared atomics
+// per cell instead of one per lane: lanes of one cell would conflict on the
+// same words).  All 32 lanes must take part.
+template <int SP>
+__device__ __forceinline__ void warp_flush32(const Inst& I, bool fl, int key, int m, int n,
+                                             float a00, float a10, float a01, float a11, int cnt,
+                                             int pm0, int pn0, int pr, int pz, float* patch,
+                                             int* cpatch, int lane) {
+  const unsigned full = 0xffffffffu;
+  const int k = fl ? key : -1;
+  const int kprev = __shfl_up_sync(full, k, 1);
+  const bool head = fl && (lane == 0 || kprev != k);
+  // a run ends below the next lane that starts a run or does not flush
+  const unsigned starts = __ballot_sync(full, head || !fl);
+  const unsigned above = lane == 31 ? 0u : (starts & (full << (lane + 1)));
+  const int end = above ? __ffs(above) - 1 : 32;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const float b00 = __shfl_down_sync(full, a00, off), b10 = __shfl_down_sync(full, a10, off);
+    const float b01 = __shfl_down_sync(full, a01, off), b11 = __shfl_down_sync(full, a11, off);
+    const int bc = __shfl_down_sync(full, cnt, off);
+    if (lane + off < end) {
+      a00 += b00;
+      a10 += b10;
+      a01 += b01;
+      a11 += b11;
+      cnt += bc;
+    }
+  }
+  if (head)
+    deposit_run32<SP>(I, key, m, n, a00, a10, a01, a11, cnt, pm0, pn0, pr, pz, patch, cpatch);
+}
+
 template <int SP, int GATHER, bool PLAIN>
 __device__ __forceinline__ double push_chunk32(const Inst& I, int c0, int ppt, float* patch,
                                                int* cpatch, int* anchor, int* cq) {
@@ -303,6 +340,9 @@ __device__ __forceinline__ double push_chunk32(const Inst& I, int c0, int ppt, f
     for (int j = 0; j < ppt; ++j, i += 32) {
       const float4 a = a_nx;
       const uint4 b = b_nx;
+      bool add = false, fl = false;   // this particle's deposit; flush of the open sums
+      int nkey = 0, nm = 0, nn1 = 0;
+      float wr1 = 0.0f, wz1 = 0.0f;
       {
         const int i2 = i + 32;
         if (j + 1 < ppt && i2 < n) {
@@ -410,31 +450,39 @@ __device__ __forceinline__ double push_chunk32(const Inst& I, int c0, int ppt, f
           const int newkey = cell_key(I, m1, n1);
           P.a[i] = make_float4(dr1, dz1, vr, vt);
           P.b[i] = make_uint4(__float_as_uint(vz), pack_mn(m1, n1), b.z, b.w);
-          // deposit of x^{n+1} (Section 2: tent functions), summed per cell
-          if (newkey != acc_key) {
-            if (acc_key >= 0)
-              deposit_run32<SP>(I, acc_key, acc_m, acc_n, s00, s10, s01, s11, acc_cnt, pm0, pn0,
-                                pr, pz, patch, cpatch);
-            acc_key = newkey;
-            acc_m = m1;
-            acc_n = n1;
-            acc_cnt = 0;
-            s00 = s10 = s01 = s11 = 0.0f;
-          }
-          const float wr1 = PLAIN ? dr1 : rweight_upper32(I, dr1, m1), wz1 = dz1;
-          s00 += (1.0f - wr1) * (1.0f - wz1);
-          s10 += wr1 * (1.0f - wz1);
-          s01 += (1.0f - wr1) * wz1;
-          s11 += wr1 * wz1;
-          ++acc_cnt;
+          // deposit of x^{n+1} (Section 2: tent functions), summed per cell;
+          // a lane whose cell changes flushes its open sums below (whole warp)
+          add = true;
+          nkey = newkey;
+          nm = m1;
+          nn1 = n1;
+          wr1 = PLAIN ? dr1 : rweight_upper32(I, dr1, m1);
+          wz1 = dz1;
+          fl = newkey != acc_key && acc_key >= 0;
         } else {
           reinterpret_cast<unsigned int*>(P.b + i)[1] = kDead;
         }
       }
+      if (__any_sync(0xffffffffu, fl))
+        warp_flush32<SP>(I, fl, acc_key, acc_m, acc_n, s00, s10, s01, s11, acc_cnt, pm0, pn0, pr,
+                         pz, patch, cpatch, lane);
+      if (add) {
+        if (nkey != acc_key) {
+          acc_key = nkey;
+          acc_m = nm;
+          acc_n = nn1;
+          acc_cnt = 0;
+          s00 = s10 = s01 = s11 = 0.0f;
+        }
+        s00 += (1.0f - wr1) * (1.0f - wz1);
+        s10 += wr1 * (1.0f - wz1);
+        s01 += (1.0f - wr1) * wz1;
+        s11 += wr1 * wz1;
+        ++acc_cnt;
+      }
     }
-    if (acc_key >= 0)
-      deposit_run32<SP>(I, acc_key, acc_m, acc_n, s00, s10, s01, s11, acc_cnt, pm0, pn0, pr, pz,
-                        patch, cpatch);
+    warp_flush32<SP>(I, acc_key >= 0, acc_key, acc_m, acc_n, s00, s10, s01, s11, acc_cnt, pm0, pn0,
+                     pr, pz, patch, cpatch, lane);
     if (diag) Kloc = 0.25 * I.mass[SP] * I.weight * (double)k2;
     __syncthreads();
     if (SP == 0) {
