@@ -270,9 +270,12 @@ __device__ __forceinline__ void deposit_run32(const Inst& I, int key, int m, int
 // first lane, which alone adds them to the patch (one set of shared atomics
 // per cell instead of one per lane: lanes of one cell would conflict on the
 // same words).  All 32 lanes must take part.
+// The open sums of a lane are sr = sum w_r, sz = sum w_z, srz = sum w_r w_z
+// and the count c: the four tent weights of the cell's nodes are
+// c - sr - sz + srz, sr - srz, sz - srz and srz.
 template <int SP>
 __device__ __forceinline__ void warp_flush32(const Inst& I, bool fl, int key, int m, int n,
-                                             float a00, float a10, float a01, float a11, int cnt,
+                                             float sr, float sz, float srz, int cnt,
                                              int pm0, int pn0, int pr, int pz, float* patch,
                                              int* cpatch, int lane) {
   const unsigned full = 0xffffffffu;
@@ -285,19 +288,19 @@ __device__ __forceinline__ void warp_flush32(const Inst& I, bool fl, int key, in
   const int end = above ? __ffs(above) - 1 : 32;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
-    const float b00 = __shfl_down_sync(full, a00, off), b10 = __shfl_down_sync(full, a10, off);
-    const float b01 = __shfl_down_sync(full, a01, off), b11 = __shfl_down_sync(full, a11, off);
+    const float br = __shfl_down_sync(full, sr, off), bz = __shfl_down_sync(full, sz, off);
+    const float brz = __shfl_down_sync(full, srz, off);
     const int bc = __shfl_down_sync(full, cnt, off);
     if (lane + off < end) {
-      a00 += b00;
-      a10 += b10;
-      a01 += b01;
-      a11 += b11;
+      sr += br;
+      sz += bz;
+      srz += brz;
       cnt += bc;
     }
   }
   if (head)
-    deposit_run32<SP>(I, key, m, n, a00, a10, a01, a11, cnt, pm0, pn0, pr, pz, patch, cpatch);
+    deposit_run32<SP>(I, key, m, n, ((float)cnt - sr) - (sz - srz), sr - srz, sz - srz, srz, cnt,
+                      pm0, pn0, pr, pz, patch, cpatch);
 }
 
 template <int SP, int GATHER, bool PLAIN>
@@ -331,9 +334,9 @@ __device__ __forceinline__ double push_chunk32(const Inst& I, int c0, int ppt, f
       a_nx = P.a[i];
       b_nx = P.b[i];
     }
-    // this lane's open deposit: cell, its node sums and particle count
+    // this lane's open deposit: cell, its weight sums and particle count
     int acc_key = -1, acc_m = 0, acc_n = 0, acc_cnt = 0;
-    float s00 = 0.0f, s10 = 0.0f, s01 = 0.0f, s11 = 0.0f;
+    float sr = 0.0f, sz = 0.0f, srz = 0.0f;
     unsigned over = 0u;   // candidates that found the queue full, bit j (ppt <= 32)
     float k2 = 0.0f;
 #pragma unroll 1
@@ -464,25 +467,24 @@ __device__ __forceinline__ double push_chunk32(const Inst& I, int c0, int ppt, f
         }
       }
       if (__any_sync(0xffffffffu, fl))
-        warp_flush32<SP>(I, fl, acc_key, acc_m, acc_n, s00, s10, s01, s11, acc_cnt, pm0, pn0, pr,
-                         pz, patch, cpatch, lane);
+        warp_flush32<SP>(I, fl, acc_key, acc_m, acc_n, sr, sz, srz, acc_cnt, pm0, pn0, pr, pz,
+                         patch, cpatch, lane);
       if (add) {
         if (nkey != acc_key) {
           acc_key = nkey;
           acc_m = nm;
           acc_n = nn1;
           acc_cnt = 0;
-          s00 = s10 = s01 = s11 = 0.0f;
+          sr = sz = srz = 0.0f;
         }
-        s00 += (1.0f - wr1) * (1.0f - wz1);
-        s10 += wr1 * (1.0f - wz1);
-        s01 += (1.0f - wr1) * wz1;
-        s11 += wr1 * wz1;
+        sr += wr1;
+        sz += wz1;
+        srz = fmaf(wr1, wz1, srz);
         ++acc_cnt;
       }
     }
-    warp_flush32<SP>(I, acc_key >= 0, acc_key, acc_m, acc_n, s00, s10, s01, s11, acc_cnt, pm0, pn0,
-                     pr, pz, patch, cpatch, lane);
+    warp_flush32<SP>(I, acc_key >= 0, acc_key, acc_m, acc_n, sr, sz, srz, acc_cnt, pm0, pn0, pr,
+                     pz, patch, cpatch, lane);
     if (diag) Kloc = 0.25 * I.mass[SP] * I.weight * (double)k2;
     __syncthreads();
     if (SP == 0) {
