@@ -335,6 +335,17 @@ __device__ __forceinline__ double rweight_upper(const Inst& I, double r, int m, 
 // Fixed-point corner weights of a unit charge at in-cell weights (wr, wz):
 // exact integers summing to 2^44.  w11 = round(ir iz / 2^44) from the 88-bit
 // integer product; ir, iz come from the weights' bit patterns (no FP64 work).
+// the three fixed-point quantities of the tent weights: round(wr 2^44),
+// round(wz 2^44) and their product rounded to 2^-44 (the weights of the four
+// nodes are 2^44 - ir - iz + i11, ir - i11, iz - i11 and i11)
+__device__ __forceinline__ void fix_parts(double wr, double wz, unsigned long long& ir,
+                                          unsigned long long& iz, unsigned long long& i11) {
+  ir = fix44(wr);   // round(wr 2^44), integer pipes
+  iz = fix44(wz);
+  const unsigned long long lo = ir * iz, hi = __umul64hi(ir, iz);
+  i11 = ((hi << (64 - kFixBits)) | (lo >> kFixBits)) + ((lo >> (kFixBits - 1)) & 1ULL);
+}
+
 struct FixW { unsigned long long w00, w10, w01, w11; };
 __device__ __forceinline__ FixW fix_weights(double wr, double wz) {
   const unsigned long long ir = fix44(wr);   // round(wr 2^44), integer pipes

@@ -302,6 +302,45 @@ __device__ __forceinline__ void deposit_run64(const Inst& I, int key, int m, int
   }
 }
 
+// The flush of the lanes whose cell changed this iteration (flag fl), by the
+// whole warp: lanes of one cell form runs of adjacent lanes (they hold
+// consecutive particles); a segmented suffix sum by shuffles leaves each run's
+// sums in its first lane, which alone adds the cell's four node weights to the
+// patch (lanes of one cell would conflict on the same shared words).  The open
+// sums are sr = sum round(w_r 2^44), sz = sum round(w_z 2^44), srz = sum of the
+// rounded products and the count c; integer sums, so the result is exact and
+// independent of the grouping.  All 32 lanes must take part.
+template <int SP>
+__device__ __forceinline__ void warp_flush64(const Inst& I, bool fl, int key, int m, int n,
+                                             unsigned long long sr, unsigned long long sz,
+                                             unsigned long long srz, int cnt, int pm0, int pn0,
+                                             int pr, int pz, unsigned long long* patch, int* cpatch,
+                                             int lane) {
+  const unsigned full = 0xffffffffu;
+  const int k = fl ? key : -1;
+  const int kprev = __shfl_up_sync(full, k, 1);
+  const bool head = fl && (lane == 0 || kprev != k);
+  const unsigned starts = __ballot_sync(full, head || !fl);
+  const unsigned above = lane == 31 ? 0u : (starts & (full << (lane + 1)));
+  const int end = above ? __ffs(above) - 1 : 32;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned long long br = __shfl_down_sync(full, sr, off);
+    const unsigned long long bz = __shfl_down_sync(full, sz, off);
+    const unsigned long long brz = __shfl_down_sync(full, srz, off);
+    const int bc = __shfl_down_sync(full, cnt, off);
+    if (lane + off < end) {
+      sr += br;
+      sz += bz;
+      srz += brz;
+      cnt += bc;
+    }
+  }
+  if (head)
+    deposit_run64<SP>(I, key, m, n, ((unsigned long long)cnt << kFixBits) - sr - sz + srz,
+                      sr - srz, sz - srz, srz, cnt, pm0, pn0, pr, pz, patch, cpatch);
+}
+
 // Push the chunk of `ppt * blockDim.x` particles of species SP starting at c0
 // (the whole CTA takes part).  `patch` is the CTA's zeroed shared deposit
 // patch; it is flushed and zeroed again before return.  `anchor` holds the
@@ -337,14 +376,17 @@ __device__ __forceinline__ double push_chunk64(const Inst& I, long long c0, int 
     const int pm0 = anchor[0], pn0 = anchor[1];
     const int pr = patch_pr(I), pz = patch_pz(I);
     const long long run0 = c0 + (long long)(threadIdx.x >> 5) * 32 * ppt + lane;
-    // this lane's open deposit: cell, its fixed-point node sums and count
+    // this lane's open deposit: cell, its fixed-point weight sums and count
     int acc_key = -1, acc_m = 0, acc_n = 0, acc_cnt = 0;
-    unsigned long long s00 = 0ULL, s10 = 0ULL, s01 = 0ULL, s11 = 0ULL;
+    unsigned long long sr = 0ULL, sz = 0ULL, srz = 0ULL;
     unsigned over = 0u;   // candidates that found the queue full, bit j (ppt <= 32)
 #pragma unroll 1
     for (int j = 0; j < ppt; ++j) {
       const long long i = run0 + (long long)j * 32;
       int newkey = -1;
+      bool add = false, fl = false;   // this particle's deposit; flush of the open sums
+      int nm = 0, nn1 = 0;
+      unsigned long long ir = 0ULL, iz = 0ULL, i11 = 0ULL;
       // between full sorts the arrays hold dead slots, marked by r = -1
       const bool live = i < n && (long long)bits_of(P.r[i]) >= 0;
       if (!live) {
@@ -464,32 +506,37 @@ __device__ __forceinline__ double push_chunk64(const Inst& I, long long c0, int 
           split_cell(z1, I.nz, n1, fz1);
           newkey = cell_key(I, m1, n1);
           P.r[i] = r1; P.z[i] = z1; P.vr[i] = vr; P.vt[i] = vt; P.vz[i] = vz;
-          // deposit weights of x^{n+1} (Section 2: tent functions), summed per cell
-          if (newkey != acc_key) {
-            if (acc_key >= 0)
-              deposit_run64<SP>(I, acc_key, acc_m, acc_n, s00, s10, s01, s11, acc_cnt, pm0, pn0,
-                                pr, pz, patch, cpatch);
-            acc_key = newkey;
-            acc_m = m1;
-            acc_n = n1;
-            acc_cnt = 0;
-            s00 = s10 = s01 = s11 = 0ULL;
-          }
-          const FixW f = fix_weights(rweight_upper(I, r1, m1, fr1), fz1);
-          s00 += f.w00;
-          s10 += f.w10;
-          s01 += f.w01;
-          s11 += f.w11;
-          ++acc_cnt;
+          // deposit weights of x^{n+1} (Section 2: tent functions), summed per
+          // cell; a lane whose cell changes flushes its open sums below
+          fix_parts(rweight_upper(I, r1, m1, fr1), fz1, ir, iz, i11);
+          add = true;
+          nm = m1;
+          nn1 = n1;
+          fl = newkey != acc_key && acc_key >= 0;
         } else {
           P.r[i] = -1.0;   // dead slot until the next full sort
         }
         I.key[SP][i] = newkey;
       }
+      if (__any_sync(0xffffffffu, fl))
+        warp_flush64<SP>(I, fl, acc_key, acc_m, acc_n, sr, sz, srz, acc_cnt, pm0, pn0, pr, pz,
+                         patch, cpatch, lane);
+      if (add) {
+        if (newkey != acc_key) {
+          acc_key = newkey;
+          acc_m = nm;
+          acc_n = nn1;
+          acc_cnt = 0;
+          sr = sz = srz = 0ULL;
+        }
+        sr += ir;
+        sz += iz;
+        srz += i11;
+        ++acc_cnt;
+      }
     }
-    if (acc_key >= 0)
-      deposit_run64<SP>(I, acc_key, acc_m, acc_n, s00, s10, s01, s11, acc_cnt, pm0, pn0, pr, pz,
-                        patch, cpatch);
+    warp_flush64<SP>(I, acc_key >= 0, acc_key, acc_m, acc_n, sr, sz, srz, acc_cnt, pm0, pn0, pr,
+                     pz, patch, cpatch, lane);
     __syncthreads();
     if (SP == 0) {
       // the queued collisions (Section 3), on the state written above
