@@ -64,7 +64,7 @@ BYTES_PER_PARTICLE_FP32 = 64.0
 # species, scaled by the particles of a launch (one pass over each particle)
 # (profiles/traffic_push_one_rz256_ring_1e7.md); None until measured on the
 # kernel as it stands.
-TRAFFIC_PER_PARTICLE = {"fp64": 87.8, "fp32": 64.3}
+TRAFFIC_PER_PARTICLE = {"fp64": 87.8, "fp32": 62.9}
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA pipes-lanes per SM per clock x 2
 # flop x 2.07 GHz = 1.26 TFLOP/s (nominal 1.25); scaled to the measured clock.
 FP64_FLOP_PER_CLK = 152 * 2 * 2
@@ -1009,10 +1009,11 @@ def main():
     value = psteps / t
     ne, ni = pg.pic_count(h, 0, 0), pg.pic_count(h, 0, 1)
     g = 0 if args.gather == "ec" else 1
-    try:
-        peaks = dict(peaks, fp64_fma_tflops=pg.pic_fp64_fma_rate())
-    except Exception:   # the derived FP64 peak stands in
-        pass
+    if args.precision == "fp64":   # the FP64 push's ALU view (the FP32 push has none)
+        try:
+            peaks = dict(peaks, fp64_fma_tflops=pg.pic_fp64_fma_rate())
+        except Exception:   # the derived FP64 peak stands in
+            pass
     roofline = push_roofline(args.precision, g, rec, ne + ni, peaks, peak_kind)
 
     # region diagnostics sampler (Sections 4, 5): one warp per cell bin of the
