@@ -773,22 +773,26 @@ __global__ void __launch_bounds__(256) k_head_bwd(const bf16* h, const float* w,
                                                   const float* y, bf16* gh, long long npx,
                                                   double inv_n, double* partial) {
   __shared__ double red[kHeadVals][8];
-  double loc[kHeadVals];
+  // a thread's partial sums in FP32 (a few tens of nodes each; the FP64
+  // pipes of this part are a small fraction of its FP32 rate), FP64 from the
+  // warp sums on
+  float loc[kHeadVals];
 #pragma unroll
-  for (int k = 0; k < kHeadVals; ++k) loc[k] = 0.0;
+  for (int k = 0; k < kHeadVals; ++k) loc[k] = 0.0f;
+  const float ginv = (float)(2.0 * inv_n);
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npx;
        p += (long long)gridDim.x * blockDim.x) {
-    const double d = (double)out[p] - (double)y[p];
-    const double g = 2.0 * d * inv_n;
-    loc[0] += d * d;
+    const float d = out[p] - y[p];
+    const float g = ginv * d;
+    loc[0] = fmaf(d, d, loc[0]);
     loc[1] += g;
     float v[16], o[16];
     load8(h + p * 16, v);
     load8(h + p * 16 + 8, v + 8);
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-      loc[2 + c] += g * (double)v[c];
-      o[c] = (float)((double)w[c] * g);
+      loc[2 + c] = fmaf(g, v[c], loc[2 + c]);
+      o[c] = w[c] * g;
     }
     store8(gh + p * 16, o);
     store8(gh + p * 16 + 8, o + 8);
@@ -796,7 +800,7 @@ __global__ void __launch_bounds__(256) k_head_bwd(const bf16* h, const float* w,
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < kHeadVals; ++k) {
-    const double s = warp_sum_d(loc[k]);
+    const double s = warp_sum_d((double)loc[k]);
     if (lane == 0) red[k][wid] = s;
   }
   __syncthreads();
