@@ -799,45 +799,71 @@ __device__ __forceinline__ void k_scan_body(const Inst& I, int sp0) {
   int* cursor = I.cursor[sp];
   __shared__ int wsum[32];
   __shared__ long long carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nkey = I.nkey;
+  // thread t owns the keys [t per, (t + 1) per), per a multiple of 4: one
+  // pass sums them, one block-wide scan of the thread sums, a second pass
+  // (from L1/L2) writes the bin starts and clears the counts
+  const int per = ((nkey + (int)blockDim.x - 1) / (int)blockDim.x + 3) & ~3;
+  const int i0 = threadIdx.x * per;
   int vmax = 0;   // most particles in one cell
-  for (int base = 0; base < I.nkey; base += blockDim.x * 4) {
-    const int i0 = base + threadIdx.x * 4;
-    int v[4];
-    for (int k = 0; k < 4; ++k) v[k] = i0 + k < I.nkey ? counts[i0 + k] : 0;
-    vmax = max(vmax, max(max(v[0], v[1]), max(v[2], v[3])));
-    const int s = v[0] + v[1] + v[2] + v[3];
-    int incl = s;
+  int s = 0;
+  for (int k = 0; k < per; k += 4) {
+    const int i = i0 + k;
+    if (i + 3 < nkey) {
+      const int4 v = *reinterpret_cast<const int4*>(counts + i);
+      s += v.x + v.y + v.z + v.w;
+      vmax = max(vmax, max(max(v.x, v.y), max(v.z, v.w)));
+    } else {
+      for (int q = i; q < nkey && q < i + 4; ++q) {
+        const int v = counts[q];
+        s += v;
+        vmax = max(vmax, v);
+      }
+    }
+  }
+  int incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int x = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
+      const int t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
     }
-    if (lane == 31) wsum[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-      int x = wsum[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += t;
-      }
-      wsum[lane] = x;  // inclusive over warps
-    }
-    __syncthreads();
-    long long off = carry + (w > 0 ? wsum[w - 1] : 0) + (incl - s);
-    for (int k = 0; k < 4; ++k)
-      if (i0 + k < I.nkey) {
-        cursor[i0 + k] = (int)off;
-        counts[i0 + k] = 0;
-        off += v[k];
-      }
-    __syncthreads();
-    if (threadIdx.x == 0) carry += wsum[31];
-    __syncthreads();
+    wsum[lane] = x;  // inclusive over warps
+    if (lane == 31) carry = x;
   }
+  __syncthreads();
+  int off = (w > 0 ? wsum[w - 1] : 0) + (incl - s);
+  for (int k = 0; k < per; k += 4) {
+    const int i = i0 + k;
+    if (i + 3 < nkey) {
+      const int4 v = *reinterpret_cast<const int4*>(counts + i);
+      int4 c;
+      c.x = off;
+      c.y = c.x + v.x;
+      c.z = c.y + v.y;
+      c.w = c.z + v.z;
+      off = c.w + v.w;
+      *reinterpret_cast<int4*>(cursor + i) = c;
+      *reinterpret_cast<int4*>(counts + i) = make_int4(0, 0, 0, 0);
+    } else {
+      for (int q = i; q < nkey && q < i + 4; ++q) {
+        const int v = counts[q];
+        cursor[q] = off;
+        counts[q] = 0;
+        off += v;
+      }
+    }
+  }
+  __syncthreads();   // wsum is reused below
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
   if (lane == 0) wsum[w] = vmax;   // free after the last loop's barrier
