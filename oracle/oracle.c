@@ -47,6 +47,27 @@ void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4
   out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (the same paper): the 32-bit form, four 32-bit words,      */
+/* multipliers 0xD2511F53 and 0xCD9E8D57, Weyl key increments 0x9E3779B9    */
+/* and 0xBB67AE85.                                                          */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) { k0 += W0; k1 += W1; }
+    uint64_t p0 = (uint64_t)M0 * x0, p1 = (uint64_t)M1 * x2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
 /* uniform on [0,1) from the top 53 bits */
 static double u01(uint64_t x) { return (double)(x >> 11) * (1.0 / 9007199254740992.0); }
 
@@ -57,6 +78,24 @@ static void draws(const orc_config* c, int species, int64_t id, int64_t step, in
   uint64_t w[4];
   orc_philox4x64(ctr, key, w);
   for (int j = 0; j < 4; ++j) u[j] = u01(w[j]);
+}
+
+/* The null-collision candidate draw of electron `id` at step `step`: the
+ * first word of Philox4x32-10 with counter (id, step) as four 32-bit halves
+ * (low half first) and key (seed low half, seed high half), as a uniform
+ * U = word 2^-32 on [0,1) (exact in a double).  Reading: Section 3 draws one
+ * uniform number per electron and step for the null-collision test and fixes
+ * no generator; the test is the one draw made for every electron at every
+ * step, so it takes the 32-bit form of the generator, whose 2^-32 resolution
+ * is far below the collision probabilities of these runs, and the collision
+ * itself draws from stream 0 of the 64-bit form. */
+static double candidate_draw(const orc_config* c, int64_t id, int64_t step) {
+  const uint64_t uid = (uint64_t)id, ust = (uint64_t)step;
+  uint32_t ctr[4] = {(uint32_t)uid, (uint32_t)(uid >> 32), (uint32_t)ust, (uint32_t)(ust >> 32)};
+  uint32_t key[2] = {(uint32_t)c->seed, (uint32_t)(c->seed >> 32)};
+  uint32_t w[4];
+  orc_philox4x32(ctr, key, w);
+  return (double)w[0] * (1.0 / 4294967296.0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -765,9 +804,9 @@ static double ionize(orc_sim* s, int64_t k, double E, double I, const double e[3
 static void mcc_electron(orc_sim* s, int64_t k, blist* be, blist* bi) {
   const orc_config* c = &s->c;
   pstore* p = &s->sp[0];
+  if (!(candidate_draw(c, p->id[k], s->step) < s->p_null)) return;
   double u[4];
-  draws(c, 0, p->id[k], s->step, 0, u);
-  if (!(u[0] < s->p_null)) return;
+  draws(c, 0, p->id[k], s->step, 0, u);   /* u[1..3]: process and angles */
   double v[3] = {p->vr[k], p->vt[k], p->vz[k]};
   double vmag = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
   double E = 0.5 * ME * vmag * vmag / QE;

@@ -15,6 +15,7 @@
  *
  * Parity status per function (what pins it, in tests/test_oracle_*.py):
  *   orc_philox4x64         known-answer test against numpy's Philox
+ *   orc_philox4x32         the published Philox4x32-10 known-answer vectors
  *   orc_boris_move         Larmor polygon radius, rotation angle, E x B drift,
  *                          |v| conservation (closed forms)
  *   orc_bfield             div B = 0, curl B = 0 (finite differences), B_r zero
@@ -93,6 +94,7 @@ typedef struct orc_sim orc_sim;
 
 /* ---- pure pieces (used by the pins) ---- */
 void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+void orc_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 void orc_boris_move(double q_over_m, double dt, double Er, double Ez, double Br, double Bz,
                     double* r, double* z, double* vr, double* vt, double* vz);
 void orc_bfield(const orc_config* c, double r, double z, double* Br, double* Bz);

@@ -69,6 +69,7 @@ class OracleRegions(C.Structure):
 _D = C.POINTER(C.c_double)
 _I64 = C.POINTER(C.c_int64)
 _U64 = C.POINTER(C.c_uint64)
+_U32 = C.POINTER(C.c_uint32)
 
 
 def lib():
@@ -78,6 +79,7 @@ def lib():
         L = C.CDLL(path)
         cfgp = C.POINTER(OracleConfig)
         L.orc_philox4x64.argtypes = [_U64, _U64, _U64]
+        L.orc_philox4x32.argtypes = [_U32, _U32, _U32]
         L.orc_boris_move.argtypes = [C.c_double] * 6 + [_D] * 5
         L.orc_bfield.argtypes = [cfgp, C.c_double, C.c_double, _D, _D]
         L.orc_node_volume.argtypes = [cfgp, C.c_int, C.c_int]
@@ -136,6 +138,14 @@ def philox4x64(ctr, key) -> np.ndarray:
     k = np.ascontiguousarray(key, dtype=np.uint64)
     out = np.zeros(4, dtype=np.uint64)
     lib().orc_philox4x64(c.ctypes.data_as(_U64), k.ctypes.data_as(_U64), out.ctypes.data_as(_U64))
+    return out
+
+
+def philox4x32(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32(c.ctypes.data_as(_U32), k.ctypes.data_as(_U32), out.ctypes.data_as(_U32))
     return out
 
 

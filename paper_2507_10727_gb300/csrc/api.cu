@@ -262,7 +262,7 @@ int build_instance(pic_handle* h, const pic_config& c, InstHost& ih) {
   I.exc_E = c.exc_E;
   I.nu_max = nu_max_of(c);
   I.p_null = -std::expm1(-I.nu_max * c.dt);
-  I.pnull_k = (unsigned long long)std::ceil(std::ldexp(I.p_null, 53));
+  I.pnull32 = (unsigned long long)std::ceil(std::ldexp(I.p_null, 32));
   I.seed = c.seed;
   I.gather = c.gather;
   I.rweight = c.rweight;

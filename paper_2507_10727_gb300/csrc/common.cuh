@@ -178,7 +178,7 @@ struct Inst {
   // collisions
   double n_gas, T_gas, m_ion, sigma_el, ion_a, ion_I, exc_C, exc_E, nu_max, p_null;
   double n_meta, meta_a, meta_I;   // reaction (1d) off a constant Ar* background
-  unsigned long long pnull_k;   // ceil(p_null 2^53): U < p_null  <=>  (word >> 11) < pnull_k
+  unsigned long long pnull32;   // ceil(p_null 2^32): word 2^-32 < p_null  <=>  word < pnull32
   unsigned long long seed;
   // switches
   int gather, rweight, mcc_on, push_on, field_on, walls_reflect, circuit_mode, n_avg;
@@ -280,12 +280,34 @@ __device__ __forceinline__ void draws(const Inst& I, int sp, long long id, long 
   u[0] = u01(w[0]); u[1] = u01(w[1]); u[2] = u01(w[2]); u[3] = u01(w[3]);
 }
 
-// The null-collision candidate test of an electron (U1 < p_null, on the
-// integer word of the collision stream)
+// The first word of Philox4x32-10 (same paper): multipliers 0xD2511F53 and
+// 0xCD9E8D57, Weyl key increments 0x9E3779B9 and 0xBB67AE85; the 32 x 32 ->
+// 64-bit products are single integer multiply-adds on the GPU, against the
+// several a 64 x 64 -> 128-bit product of the 64-bit form takes.
+__device__ __forceinline__ unsigned philox4x32_w0(unsigned c0, unsigned c1, unsigned c2,
+                                                  unsigned c3, unsigned k0, unsigned k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    const unsigned hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const unsigned hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const unsigned y0 = hi1 ^ c1 ^ k0, y2 = hi0 ^ c3 ^ k1;
+    c0 = y0; c1 = lo1; c2 = y2; c3 = lo0;
+  }
+  return c0;
+}
+
+// The null-collision candidate test of an electron (Section 3: U < p_null):
+// U is the first word of Philox4x32-10 with counter (id, step) as 32-bit
+// halves, low half first, and key (seed low, seed high), times 2^-32; the
+// test is done exactly on the integer word.  The collision of a candidate
+// draws its process and angles from stream 0 of Philox4x64-10.
 __device__ __forceinline__ bool mcc_candidate(const Inst& I, long long id, long long step) {
-  unsigned long long w[4];
-  philox4x64((unsigned long long)id, (unsigned long long)step, 0ULL, 0ULL, I.seed, 0ULL, w);
-  return (w[0] >> 11) < I.pnull_k;
+  const unsigned long long uid = (unsigned long long)id, ust = (unsigned long long)step;
+  const unsigned w = philox4x32_w0((unsigned)uid, (unsigned)(uid >> 32), (unsigned)ust,
+                                   (unsigned)(ust >> 32), (unsigned)I.seed,
+                                   (unsigned)(I.seed >> 32));
+  return (unsigned long long)w < I.pnull32;
 }
 
 // ---------------------------------------------------------------------------

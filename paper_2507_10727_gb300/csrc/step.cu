@@ -209,12 +209,11 @@ __device__ double ionize64(const Inst& I, long long id, long long step, double r
 
 __device__ bool mcc_electron(const Inst& I, long long id, long long step, double r, double z,
                              double& vr, double& vt, double& vz) {
+  // a candidate (mcc_candidate): process and angles from words 1..3 of stream 0
   unsigned long long w[4];
   philox4x64((unsigned long long)id, (unsigned long long)step, 0ULL, 0ULL, I.seed, 0ULL, w);
-  // candidate test U1 < p_null done exactly on the integer word
-  if ((w[0] >> 11) >= I.pnull_k) return false;
   double u[4];
-  u[0] = u01(w[0]); u[1] = u01(w[1]); u[2] = u01(w[2]); u[3] = u01(w[3]);
+  u[1] = u01(w[1]); u[2] = u01(w[2]); u[3] = u01(w[3]);
   const double v[3] = {vr, vt, vz};
   const double vmag = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
   const double E = 0.5 * kMe * vmag * vmag / kQe;

@@ -132,9 +132,9 @@ __device__ float ionize32(const Inst& I, long long id, long long step, int m, fl
 
 __device__ void mcc_electron32(const Inst& I, long long id, long long step, int m, float dr, int n,
                                float dz, float& vr, float& vt, float& vz) {
+  // a candidate (mcc_candidate): process and angles from words 1..3 of stream 0
   unsigned long long w[4];
   philox4x64((unsigned long long)id, (unsigned long long)step, 0ULL, 0ULL, I.seed, 0ULL, w);
-  if ((w[0] >> 11) >= I.pnull_k) return;
   const float v2 = vr * vr + vt * vt + vz * vz;
   const float vmag = sqrtf(v2);
   const float E = kHalfMeOverE * v2;

@@ -3,6 +3,9 @@
 * Philox4x64-10 against numpy's independent implementation (numpy advances its
   128-bit counter by one before each block, so numpy's first block with
   counter c is Philox(c + 1)).
+* Philox4x32-10 (the null-collision candidate draw) against the known-answer
+  vectors published with the generator (Salmon et al., SC'11, Random123
+  distribution): all-zero, all-ones and the digits of pi as counter and key.
 * Boris push closed forms (the paper says only "explicit"; the Boris scheme is
   the reading): in a uniform B the velocity turns by exactly 2 atan(w dt / 2)
   per step and the positions lie on a circle of radius
@@ -47,6 +50,16 @@ def test_philox_consecutive_counters_match_numpy_stream():
     ref = _numpy_philox([10, 0, 0, 0], key, nblocks=5)
     got = np.concatenate([oracle.philox4x64([10 + k, 0, 0, 0], key) for k in range(5)])
     assert [int(x) for x in got] == [int(x) for x in ref]
+
+
+@pytest.mark.parametrize("ctr,key,expected", [
+    ([0, 0, 0, 0], [0, 0], [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]),
+    ([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2, [0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]),
+    ([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344], [0xA4093822, 0x299F31D0],
+     [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]),
+])
+def test_philox4x32_known_answers(ctr, key, expected):
+    assert [int(x) for x in oracle.philox4x32(ctr, key)] == expected
 
 
 def _lab_track(q_over_m, dt, E, B, state, nsteps):
