@@ -908,6 +908,9 @@ static cudaError_t launch_ensemble_step(pic_handle* h, const StepMarks* marks) {
     bd.any_append = bd.any_append || ih.I.sort_every > 1;
   }
   bd.prec32 = I0.prec32;
+  bool plain = true;   // the model's own switches in every instance (fixed at creation)
+  for (const InstHost& ih : h->inst)
+    plain = plain && ih.I.push_on && ih.I.rweight == 0 && !ih.I.walls_reflect;
   mk(G_FIELD, true);
   if (e == cudaSuccess) e = launch_field_tables_batch(h->d_insts, n, bd, h->num_sms, st);
   mk(G_FIELD, false);
@@ -915,7 +918,8 @@ static cudaError_t launch_ensemble_step(pic_handle* h, const StepMarks* marks) {
   mk(G_PUSH, true);
   if (e == cudaSuccess) e = launch_queue_setup(h->d_insts, h->d_queue, n, (long long)h->ppt * threads, st);
   if (e == cudaSuccess)
-    e = launch_push_all(h->d_insts, h->d_queue, I0.prec32, I0.gather, h->ppt, h->num_sms, st);
+    e = launch_push_all(h->d_insts, h->d_queue, I0.prec32, I0.gather, plain, h->ppt, h->num_sms,
+                        st);
   mk(G_PUSH, false);
   mk(G_SCATTER, true);
   if (e == cudaSuccess) e = launch_post_push_batch(h->d_insts, n, bd, h->num_sms, st);

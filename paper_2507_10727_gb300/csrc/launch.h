@@ -73,11 +73,12 @@ cudaError_t launch_solve_fields(const Inst& I, PoissonWork* pw, int num_sms, cud
 cudaError_t launch_field_tables(const Inst& I, int num_sms, cudaStream_t st);
 cudaError_t launch_queue_setup(const Inst* d_insts, WorkQueue* q, int n_inst, long long chunk,
                                cudaStream_t st);
-// the push of both species of every instance over the work queue
-cudaError_t launch_push_all(const Inst* d_insts, WorkQueue* q, int prec32, int gather, int ppt,
-                            int num_sms, cudaStream_t st);
-cudaError_t launch_push32_all(const Inst* d_insts, WorkQueue* q, int gather, int ppt, int num_sms,
-                              cudaStream_t st);
+// the push of both species of every instance over the work queue (plain:
+// every instance has the push on, tent weights in r and absorbing walls)
+cudaError_t launch_push_all(const Inst* d_insts, WorkQueue* q, int prec32, int gather, bool plain,
+                            int ppt, int num_sms, cudaStream_t st);
+cudaError_t launch_push32_all(const Inst* d_insts, WorkQueue* q, int gather, bool plain, int ppt,
+                              int num_sms, cudaStream_t st);
 // the push of a single-instance handle (the instance a kernel argument)
 cudaError_t launch_push_one(const Inst& I, WorkQueue* q, int ppt, int num_sms, cudaStream_t st);
 cudaError_t launch_push32_one(const Inst& I, WorkQueue* q, int ppt, int num_sms, cudaStream_t st);

@@ -1513,11 +1513,11 @@ cudaError_t launch_push_one(const Inst& I, WorkQueue* q, int ppt, int num_sms, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_push_all(const Inst* d_insts, WorkQueue* q, int prec32, int gather, int ppt,
-                            int num_sms, cudaStream_t st) {
+cudaError_t launch_push_all(const Inst* d_insts, WorkQueue* q, int prec32, int gather, bool plain,
+                            int ppt, int num_sms, cudaStream_t st) {
   // a thread's queue-overflow candidates are a 32-bit mask over its chunk slots
   if (ppt < 1 || ppt > 32) return cudaErrorInvalidValue;
-  if (prec32) return launch_push32_all(d_insts, q, gather, ppt, num_sms, st);
+  if (prec32) return launch_push32_all(d_insts, q, gather, plain, ppt, num_sms, st);
   if (gather == 0)
     k_push_all<0><<<resident_blocks((const void*)k_push_all<0>, kPushThreads, num_sms), kPushThreads, 0, st>>>(d_insts, q, ppt);
   else

@@ -522,8 +522,9 @@ __device__ __forceinline__ double push_chunk32(const Inst& I, int c0, int ppt, f
 int resident_blocks(const void* fn, int threads, int num_sms);   // step.cu
 
 // The FP32 push of both species of every instance over the work queue (see
-// k_push_all in step.cu).
-template <int GATHER>
+// k_push_all in step.cu).  PLAIN: every instance runs the model's own switches
+// (push on, tent weights in r, absorbing walls; see k_push32_one).
+template <int GATHER, bool PLAIN>
 __global__ void __launch_bounds__(kPush32Threads, 4) k_push32_all(const Inst* insts, WorkQueue* q,
                                                                    int ppt) {
   __shared__ float patch[kPatch32Nodes];
@@ -564,8 +565,8 @@ __global__ void __launch_bounds__(kPush32Threads, 4) k_push32_all(const Inst* in
       cur = inst;
     }
     if (!s_skip) {
-      if (s_sp == 0) K0 += push_chunk32<0, GATHER, false>(sI, (int)s_c0, ppt, patch, cpatch, anchor, cq);
-      else K1 += push_chunk32<1, GATHER, false>(sI, (int)s_c0, ppt, patch, cpatch, anchor, cq);
+      if (s_sp == 0) K0 += push_chunk32<0, GATHER, PLAIN>(sI, (int)s_c0, ppt, patch, cpatch, anchor, cq);
+      else K1 += push_chunk32<1, GATHER, PLAIN>(sI, (int)s_c0, ppt, patch, cpatch, anchor, cq);
     }
     __syncthreads();
   }
@@ -850,12 +851,22 @@ cudaError_t launch_deposit_all32(const Inst& I, int num_sms, cudaStream_t st) {
 }
 
 
-cudaError_t launch_push32_all(const Inst* d_insts, WorkQueue* q, int gather, int ppt, int num_sms,
-                              cudaStream_t st) {
-  if (gather == 0)
-    k_push32_all<0><<<resident_blocks((const void*)k_push32_all<0>, kPush32Threads, num_sms), kPush32Threads, 0, st>>>(d_insts, q, ppt);
-  else
-    k_push32_all<1><<<resident_blocks((const void*)k_push32_all<1>, kPush32Threads, num_sms), kPush32Threads, 0, st>>>(d_insts, q, ppt);
+template <int GATHER, bool PLAIN>
+static void push32_all(const Inst* d_insts, WorkQueue* q, int ppt, int num_sms, cudaStream_t st) {
+  k_push32_all<GATHER, PLAIN><<<resident_blocks((const void*)k_push32_all<GATHER, PLAIN>,
+                                                kPush32Threads, num_sms),
+                                kPush32Threads, 0, st>>>(d_insts, q, ppt);
+}
+
+cudaError_t launch_push32_all(const Inst* d_insts, WorkQueue* q, int gather, bool plain, int ppt,
+                              int num_sms, cudaStream_t st) {
+  if (gather == 0) {
+    if (plain) push32_all<0, true>(d_insts, q, ppt, num_sms, st);
+    else push32_all<0, false>(d_insts, q, ppt, num_sms, st);
+  } else {
+    if (plain) push32_all<1, true>(d_insts, q, ppt, num_sms, st);
+    else push32_all<1, false>(d_insts, q, ppt, num_sms, st);
+  }
   return cudaGetLastError();
 }
 
