@@ -16,13 +16,18 @@
 //   k_step_end        diagnostics record, counters, step index
 #include <cstdio>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "device_util.cuh"
 #include "launch.h"
 
 namespace pic {
 
+namespace cg = cooperative_groups;
+
 constexpr int kPushThreads = 256;
+constexpr int kScanCta = 8;                      // CTAs of one species' scan (a cluster)
 constexpr int kHalo = 3;                         // cells a particle may move and still hit the patch
 // The deposit patch: (tile extent in r + 2 halo + 1) x (two tiles along z + 2
 // halo + 1) nodes; the arrays hold the largest of the tile shapes.
@@ -790,21 +795,31 @@ cudaError_t launch_births(const Inst& I, int num_sms, cudaStream_t st) {
 // Exclusive scan of the cell histogram of one species -> cursors; clears the
 // histogram; n_next = total (checked against the capacity).
 // ---------------------------------------------------------------------------
+// One species' scan runs on a cluster of kScanCta CTAs (distributed shared
+// memory): CTA c owns a contiguous kScanCta-th of the keys and thread t of it
+// `per` consecutive keys (per a multiple of 4).  One pass sums them, a
+// block-wide scan of the thread sums gives the CTA's total, the CTAs read
+// the totals of the lower ranks after a cluster barrier, and a second pass
+// (from L1/L2) writes the bin starts and clears the counts.  A CTA stays
+// until every CTA has read its totals (second cluster barrier).
 __device__ __forceinline__ void k_scan_body(const Inst& I, int sp0) {
+  cg::cluster_group cl = cg::this_cluster();
   Scalars* S = I.S;
-  if (S->status & ST_FATAL) return;
-  const int sp = sp0 + blockIdx.x;
+  // every CTA takes part in the cluster barriers, so a fatal status skips
+  // the work instead of returning (it is read before any CTA writes it)
+  const bool fatal = (S->status & ST_FATAL) != 0;
+  const int rank = (int)cl.block_rank();
+  const int sp = sp0 + (int)(blockIdx.x / kScanCta);
   int* counts = I.counts[sp];
   int* cursor = I.cursor[sp];
-  __shared__ int wsum[32];
-  __shared__ long long carry;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int nkey = I.nkey;
-  // thread t owns the keys [t per, (t + 1) per), per a multiple of 4: one
-  // pass sums them, one block-wide scan of the thread sums, a second pass
-  // (from L1/L2) writes the bin starts and clears the counts
-  const int per = ((nkey + (int)blockDim.x - 1) / (int)blockDim.x + 3) & ~3;
-  const int i0 = threadIdx.x * per;
+  __shared__ int wsum[32], wmax[32];
+  __shared__ int ctot, cmaxv;            // this CTA's total and largest count
+  __shared__ int sbase, stotal, smax;    // lower ranks' total; the cluster's
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)blockDim.x >> 5;
+  const int nkey = fatal ? 0 : I.nkey;
+  const int span = kScanCta * (int)blockDim.x;
+  const int per = ((nkey + span - 1) / span + 3) & ~3;
+  const int i0 = (rank * (int)blockDim.x + (int)threadIdx.x) * per;
   int vmax = 0;   // most particles in one cell
   int s = 0;
   for (int k = 0; k < per; k += 4) {
@@ -827,20 +842,50 @@ __device__ __forceinline__ void k_scan_body(const Inst& I, int sp0) {
     const int t = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += t;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
   if (lane == 31) wsum[w] = incl;
+  if (lane == 0) wmax[w] = vmax;
   __syncthreads();
   if (w == 0) {
-    int x = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+    int x = lane < nw ? wsum[lane] : 0;
+    int m = lane < nw ? wmax[lane] : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int t = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += t;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     wsum[lane] = x;  // inclusive over warps
-    if (lane == 31) carry = x;
+    if (lane == 31) {
+      ctot = x;
+      cmaxv = m;
+    }
   }
-  __syncthreads();
-  int off = (w > 0 ? wsum[w - 1] : 0) + (incl - s);
+  cl.sync();   // every CTA's total and maximum are written
+  if (w == 0) {
+    int t = 0, m = 0;
+    if (lane < kScanCta) {
+      t = *cl.map_shared_rank(&ctot, (unsigned)lane);
+      m = *cl.map_shared_rank(&cmaxv, (unsigned)lane);
+    }
+    const int below = lane < rank ? t : 0;
+    int tb = below, tt = t;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      tb += __shfl_xor_sync(0xffffffffu, tb, o);
+      tt += __shfl_xor_sync(0xffffffffu, tt, o);
+      m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if (lane == 0) {
+      sbase = tb;
+      stotal = tt;
+      smax = m;
+    }
+  }
+  cl.sync();   // the remote reads are done; sbase, stotal, smax visible to the CTA
+  int off = sbase + (w > 0 ? wsum[w - 1] : 0) + (incl - s);
   for (int k = 0; k < per; k += 4) {
     const int i = i0 + k;
     if (i + 3 < nkey) {
@@ -862,23 +907,19 @@ __device__ __forceinline__ void k_scan_body(const Inst& I, int sp0) {
       }
     }
   }
-  __syncthreads();   // wsum is reused below
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-  if (lane == 0) wsum[w] = vmax;   // free after the last loop's barrier
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int j = 1; j < (int)(blockDim.x >> 5); ++j) vmax = max(vmax, wsum[j]);
-    S->ppc_max[sp] = vmax;
-    S->n_next[sp] = carry;
-    if (carry > I.cap[sp]) atomicOr(&S->status, ST_CAPACITY);
+  if (rank == 0 && threadIdx.x == 0 && !fatal) {
+    S->ppc_max[sp] = smax;
+    S->n_next[sp] = stotal;
+    if (stotal > I.cap[sp]) atomicOr(&S->status, ST_CAPACITY);
     // FP64 deposit: a node's u64 sum of 2^44-scaled weights holds fewer than
     // 2^20 macroparticles, and a node gathers from at most 4 cells
-    if (!I.prec32 && 4LL * vmax >= (1LL << (64 - kFixBits))) atomicOr(&S->status, ST_CAPACITY);
+    if (!I.prec32 && 4LL * smax >= (1LL << (64 - kFixBits))) atomicOr(&S->status, ST_CAPACITY);
   }
 }
-__global__ void __launch_bounds__(1024) k_scan(Inst I, int sp0) { k_scan_body(I, sp0); }
-__global__ void __launch_bounds__(1024) k_scan_b(const Inst* insts, int sp0) {
+__global__ void __cluster_dims__(kScanCta, 1, 1) __launch_bounds__(1024)
+    k_scan(Inst I, int sp0) { k_scan_body(I, sp0); }
+__global__ void __cluster_dims__(kScanCta, 1, 1) __launch_bounds__(1024)
+    k_scan_b(const Inst* insts, int sp0) {
   __shared__ Inst sI;
   stage_inst(insts + blockIdx.z, &sI);
   k_scan_body(sI, sp0);
@@ -1540,7 +1581,7 @@ cudaError_t launch_sort_species(const Inst& I, int sp, int num_sms, cudaStream_t
   // n is already in S->n[sp]; births are none
   long long cap = I.cap[sp];
   k_keys<<<grid_for(cap, 256, num_sms, 8), 256, 0, st>>>(I, sp);
-  k_scan<<<1, 1024, 0, st>>>(I, sp);
+  k_scan<<<kScanCta, 1024, 0, st>>>(I, sp);
   k_scatter<<<dim3(grid_for(cap, 256, num_sms, 8), 1), 256, 0, st>>>(I, sp, 0);
   k_commit_n<<<1, 32, 0, st>>>(I, sp);
   return cudaGetLastError();
@@ -1554,7 +1595,7 @@ cudaError_t launch_thin(const Inst& I, int factor, int num_sms, cudaStream_t st)
     } else {
       const long long cap = I.cap[sp];
       k_thin<<<grid_for(cap, 256, num_sms, 8), 256, 0, st>>>(I, sp, factor);
-      k_scan<<<1, 1024, 0, st>>>(I, sp);
+      k_scan<<<kScanCta, 1024, 0, st>>>(I, sp);
       k_scatter<<<dim3(grid_for(cap, 256, num_sms, 8), 1), 256, 0, st>>>(I, sp, 0);
       k_commit_n<<<1, 32, 0, st>>>(I, sp);
     }
@@ -1638,7 +1679,7 @@ cudaError_t launch_positions_out(const Inst& I, const double* rc, const double* 
 }
 
 cudaError_t launch_scan(const Inst& I, int sp0, int nsp, cudaStream_t st) {
-  k_scan<<<nsp, 1024, 0, st>>>(I, sp0);
+  k_scan<<<nsp * kScanCta, 1024, 0, st>>>(I, sp0);
   return cudaGetLastError();
 }
 
@@ -1674,7 +1715,7 @@ cudaError_t launch_field_tables(const Inst& I, int num_sms, cudaStream_t st) {
 // births, scan, scatter, charge and circuit of one instance (after its push)
 cudaError_t launch_post_push(const Inst& I, int num_sms, cudaStream_t st) {
   launch_births(I, num_sms, st);
-  k_scan<<<2, 1024, 0, st>>>(I, 0);
+  k_scan<<<2 * kScanCta, 1024, 0, st>>>(I, 0);
   if (I.prec32) launch_scatter32(I, num_sms, st);
   else k_scatter<<<dim3(num_sms * 8, 2), 256, 0, st>>>(I, 0, 1);
   if (I.sort_every > 1) {
@@ -1712,7 +1753,7 @@ cudaError_t launch_post_push_batch(const Inst* d_insts, int n_inst, const BatchD
   if (bd.prec32) k_births_rank_b<true><<<dim3(rank_blocks, 1, n_inst), 256, 0, st>>>(d_insts);
   else k_births_rank_b<false><<<dim3(rank_blocks, 1, n_inst), 256, 0, st>>>(d_insts);
   k_births_commit_b<<<dim3(1, 1, n_inst), 32, 0, st>>>(d_insts);
-  k_scan_b<<<dim3(2, 1, n_inst), 1024, 0, st>>>(d_insts, 0);
+  k_scan_b<<<dim3(2 * kScanCta, 1, n_inst), 1024, 0, st>>>(d_insts, 0);
   if (bd.prec32) launch_scatter32_batch(d_insts, n_inst, per * 8, st);
   else k_scatter_b<<<dim3(per * 8, 2, n_inst), 256, 0, st>>>(d_insts, 0, 1);
   if (bd.any_append) {
@@ -1753,7 +1794,7 @@ cudaError_t launch_step(const Inst& I, PoissonWork* pw, int num_sms, cudaStream_
   launch_births(I, num_sms, st);
   mk(G_BIRTHS, false);
   mk(G_SCAN, true);
-  k_scan<<<2, 1024, 0, st>>>(I, 0);
+  k_scan<<<2 * kScanCta, 1024, 0, st>>>(I, 0);
   mk(G_SCAN, false);
   mk(G_SCATTER, true);
   if (I.prec32) launch_scatter32(I, num_sms, st);
