@@ -73,8 +73,9 @@ struct PoissonWork {
   int nk;                  // modes: nz - 1
   int rows_per_block;      // rows of one block in the row-wise phases
   int sep_blocks;          // blocks of one solve
-  float* sTab;             // 2 nz values sqrt(2/nz) sin(pi a / nz): the orthonormal DST-I
-                           // matrix is S[k][n] = sTab[(k+1)(n+1) mod 2nz] (symmetric)
+  int ldS;                 // row stride of sMat: nk rounded up to a multiple of 4
+  float* sMat;             // nk x ldS: the orthonormal DST-I matrix S[n][k] =
+                           // sqrt(2/nz) sin(pi (n+1)(k+1) / nz) (symmetric), zero for k >= nk
   float* sW;               // nr x nk: 1 / pivot of the Thomas elimination of mode k at row m
   float* sC;               // nr x nk: its upper factor
   float* sE;               // nr: coupling a_r(m) / (2 pi eps0) between rows m and m + 1
@@ -890,7 +891,7 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson(PoissonArgs A0, const 
 // one warp (lanes over n, then a fixed shuffle tree) and over the rows in
 // row order by every block, so phi does not depend on the number of blocks.
 // ----------------------------------------------------------------------------
-constexpr int kSepModes = 32;   // modes per block in the column phase
+constexpr int kSepModes = 32;   // most modes per block in the column phase
 enum { kRzSlot = 0, kZqSlot, kZazSlot, kRrSlot, kBbSlot, kRtSlot, kSepSlots };
 
 // row sums of `nv` values, summed over rows in order (every thread gets the
@@ -911,51 +912,81 @@ __device__ __forceinline__ void sum_rows(const double* rows, int nr, int slot0, 
   __syncthreads();
 }
 
-// out(j, k, sum_n S[k][n] in[j][n]) for the block's rows j < nrow (in: FP32
-// rows of nk values in shared memory).  S[k][n] = tab[(k+1)(n+1) mod 2 nz]
-// with tab[a] = sqrt(2/nz) sin(pi a / nz) in shared memory, the index
-// advanced by k + 1 per n; a thread takes a pair of rows at one k, so each
-// table value serves two rows.
+// out(j, k, sum_n S[n][k] in[j][n]) for the block's rows j < nrow (in: FP32
+// rows of nk values in shared memory), S read from global memory (L2
+// resident, shared by every block) as float4 rows.  Thread t takes the four
+// modes 4g..4g+3 (g = t mod ldS/4) of up to four rows over the part t div
+// (ldS/4) of the n range; the parts' sums meet in `part` (shared memory,
+// 16 blockDim.x floats), summed over the parts in a fixed order.
 template <typename Out>
-__device__ __forceinline__ void sep_transform(const PoissonWork& W, const float* tab, const float* in,
-                                              int nrow, Out out) {
-  const int nk = W.nk, per = 2 * W.nz;
-  const int pairs = (nrow + 1) >> 1;
-  for (int t = threadIdx.x; t < pairs * nk; t += blockDim.x) {
-    const int jp = t / nk, k = t - jp * nk;
-    const int j0 = 2 * jp, j1 = j0 + 1 < nrow ? j0 + 1 : j0;
-    const float* a = in + j0 * nk;
-    const float* b = in + j1 * nk;
-    const int step = (k + 1) % per;
-    int idx = step;                         // (k + 1)(n + 1) mod 2 nz at n = 0
-    float s0 = 0.0f, s1 = 0.0f;
+__device__ __forceinline__ void sep_transform(const PoissonWork& W, const float* in, int nrow,
+                                              float* part, Out out) {
+  const int nk = W.nk, ld = W.ldS, kg = ld >> 2;
+  const int T = (int)blockDim.x;
+  const int ns = T / kg;                              // parts of the n range (>= 1)
+  const int g = (int)threadIdx.x % kg, pt = (int)threadIdx.x / kg;
+  const int per = (nk + ns - 1) / ns;
+  const int n0 = pt * per, n1 = min(nk, n0 + per);
+  const float4* S4 = reinterpret_cast<const float4*>(W.sMat);
+  for (int r0 = 0; r0 < nrow; r0 += 4) {
+    const int nr4 = min(4, nrow - r0);
+    if (pt < ns) {
+      float acc[4][4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[j][c] = 0.0f;
+      const float* row = in + (size_t)r0 * nk;
 #pragma unroll 4
-    for (int n = 0; n < nk; ++n) {
-      const float c = tab[idx];
-      s0 = fmaf(c, a[n], s0);
-      s1 = fmaf(c, b[n], s1);
-      idx += step;
-      if (idx >= per) idx -= per;
+      for (int n = n0; n < n1; ++n) {
+        const float4 sv = __ldg(S4 + (size_t)n * kg + g);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (j < nr4) {
+            const float a = row[j * nk + n];
+            acc[j][0] = fmaf(a, sv.x, acc[j][0]);
+            acc[j][1] = fmaf(a, sv.y, acc[j][1]);
+            acc[j][2] = fmaf(a, sv.z, acc[j][2]);
+            acc[j][3] = fmaf(a, sv.w, acc[j][3]);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        *reinterpret_cast<float4*>(part + (size_t)(pt * 4 + j) * ld + 4 * g) =
+            make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
     }
-    out(j0, k, s0);
-    if (j1 != j0) out(j1, k, s1);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nr4 * ld; t += T) {
+      const int j = t / ld, k = t - j * ld;
+      if (k < nk) {
+        float v = 0.0f;
+        for (int q = 0; q < ns; ++q) v += part[(size_t)(q * 4 + j) * ld + k];
+        out(r0 + j, k, v);
+      }
+    }
+    __syncthreads();
   }
 }
 
-// Thomas eliminations of modes [k0, k0 + kSepModes) in shared memory (h, w, c
-// staged column-wise, kSepModes per row); one thread per mode runs the
-// forward sweep and the back substitution, then the block writes u_hat back.
+// Thomas eliminations of the block's modes in shared memory: the nk modes
+// are spread evenly over the nb blocks (mpb = ceil(nk / nb) <= kSepModes per
+// block, so every block works), h, w, c staged column-wise (mpb per row); one
+// thread per mode runs the forward sweep and the back substitution, then the
+// block writes u_hat back.
 __device__ void sep_columns(const PoissonWork& W, int lb, int nb, float* sm) {
   const int nk = W.nk, nr = W.nr;
+  int mpb = (nk + nb - 1) / nb;
+  if (mpb > kSepModes) mpb = kSepModes;
   float* h = sm;
-  float* w = h + (size_t)nr * kSepModes;
-  float* c = w + (size_t)nr * kSepModes;
-  float* e = c + (size_t)nr * kSepModes;   // e[m] = a_r(m - 1) (e[0] = 0)
+  float* w = h + (size_t)nr * mpb;
+  float* c = w + (size_t)nr * mpb;
+  float* e = c + (size_t)nr * mpb;   // e[m] = a_r(m - 1) (e[0] = 0)
   for (int m = threadIdx.x; m < nr; m += blockDim.x) e[m] = m > 0 ? W.sE[m - 1] : 0.0f;
-  for (int k0 = lb * kSepModes; k0 < nk; k0 += nb * kSepModes) {
-    const int nm = nk - k0 < kSepModes ? nk - k0 : kSepModes;
-    for (int t = threadIdx.x; t < nr * kSepModes; t += blockDim.x) {
-      const int m = t / kSepModes, j = t - m * kSepModes;
+  for (int k0 = lb * mpb; k0 < nk; k0 += nb * mpb) {
+    const int nm = nk - k0 < mpb ? nk - k0 : mpb;
+    for (int t = threadIdx.x; t < nr * mpb; t += blockDim.x) {
+      const int m = t / mpb, j = t - m * mpb;
       if (j < nm) {
         const size_t g = (size_t)m * nk + k0 + j;
         h[t] = W.sHat[g];
@@ -964,7 +995,7 @@ __device__ void sep_columns(const PoissonWork& W, int lb, int nb, float* sm) {
       }
     }
     __syncthreads();
-    if (threadIdx.x < nm) {
+    if ((int)threadIdx.x < nm) {
       const int j = threadIdx.x;
       // y_m = (f_m + e_m y_{m-1}) / pivot_m  (off-diagonals -e), eight rows of
       // operands loaded ahead of the recurrence
@@ -974,19 +1005,19 @@ __device__ void sep_columns(const PoissonWork& W, int lb, int nb, float* sm) {
         float hv[8], wv[8], ev[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          hv[u] = h[(m + u) * kSepModes + j];
-          wv[u] = w[(m + u) * kSepModes + j];
+          hv[u] = h[(m + u) * mpb + j];
+          wv[u] = w[(m + u) * mpb + j];
           ev[u] = e[m + u];
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           y = (hv[u] + ev[u] * y) * wv[u];
-          h[(m + u) * kSepModes + j] = y;
+          h[(m + u) * mpb + j] = y;
         }
       }
       for (; m < nr; ++m) {
-        y = (h[m * kSepModes + j] + e[m] * y) * w[m * kSepModes + j];
-        h[m * kSepModes + j] = y;
+        y = (h[m * mpb + j] + e[m] * y) * w[m * mpb + j];
+        h[m * mpb + j] = y;
       }
       // x_m = y_m + c_m x_{m+1}
       float x = 0.0f;
@@ -995,23 +1026,23 @@ __device__ void sep_columns(const PoissonWork& W, int lb, int nb, float* sm) {
         float hv[8], cv[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          hv[u] = h[(m - u) * kSepModes + j];
-          cv[u] = c[(m - u) * kSepModes + j];
+          hv[u] = h[(m - u) * mpb + j];
+          cv[u] = c[(m - u) * mpb + j];
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           x = fmaf(cv[u], x, hv[u]);
-          h[(m - u) * kSepModes + j] = x;
+          h[(m - u) * mpb + j] = x;
         }
       }
       for (; m >= 0; --m) {
-        x = fmaf(c[m * kSepModes + j], x, h[m * kSepModes + j]);
-        h[m * kSepModes + j] = x;
+        x = fmaf(c[m * mpb + j], x, h[m * mpb + j]);
+        h[m * mpb + j] = x;
       }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < nr * kSepModes; t += blockDim.x) {
-      const int m = t / kSepModes, j = t - m * kSepModes;
+    for (int t = threadIdx.x; t < nr * mpb; t += blockDim.x) {
+      const int m = t / mpb, j = t - m * mpb;
       if (j < nm) W.sHat[(size_t)m * nk + k0 + j] = h[t];
     }
     __syncthreads();
@@ -1049,21 +1080,20 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson_sep(PoissonArgs A0,
   double* rows = W.partial;     // kSepSlots x nr row sums
   double* az0 = (double*)smem;
   double* ar0 = az0 + (nr + 1);
-  float* tab = (float*)(ar0 + (nr + 1));          // 2 nz sine values
-  unsigned char* work = (unsigned char*)(tab + 2 * nz);
+  unsigned char* work = (unsigned char*)(ar0 + (nr + 1));
   for (int m = threadIdx.x; m <= nr; m += blockDim.x) fine_coef(W, m, az0[m], ar0[m]);
-  for (int a = threadIdx.x; a < 2 * nz; a += blockDim.x) tab[a] = W.sTab[a];
   __syncthreads();
   const Tables T{az0, ar0, nullptr, nullptr, nullptr};
   const int R = W.rows_per_block;
   const int m0 = lb * R;
   const int nrow = m0 >= nr ? 0 : (m0 + R <= nr ? R : nr - m0);
   // shared layout of the row phases: z of rows m0 - 1 .. m0 + R (FP64), A z
-  // of the own rows (FP64), then f or u_hat rows (FP32); the column phase
-  // reuses the same memory
+  // of the own rows (FP64), f or u_hat rows (FP32), the transform's partial
+  // sums (16 blockDim.x floats); the column phase reuses the same memory
   double* zs = (double*)work;
   double* azs = zs + (size_t)(R + 2) * nk;
   float* fs = (float*)(azs + (size_t)R * nk);
+  float* tpart = (float*)(((uintptr_t)(fs + (size_t)(R + 2) * nk) + 15) & ~(uintptr_t)15);
 
   // f_hat of the own rows from W.r.  The transform solve is linear and its
   // values (charges of 1e-20 .. 1e-8 C over couplings of ~1e-4 m) sit many
@@ -1077,7 +1107,7 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson_sep(PoissonArgs A0,
     __syncthreads();
     if (nrow > 0) {
       float* hat = W.sHat + (size_t)m0 * nk;
-      sep_transform(W, tab, fs, nrow, [&](int j, int k, float v) { hat[(size_t)j * nk + k] = v; });
+      sep_transform(W, fs, nrow, tpart, [&](int j, int k, float v) { hat[(size_t)j * nk + k] = v; });
     }
   };
 
@@ -1132,7 +1162,7 @@ __global__ void __launch_bounds__(kPoisThreads) k_poisson_sep(PoissonArgs A0,
       }
       __syncthreads();
       // u rows: zs[j][n] = unscale sum_k S[n][k] u_hat[j][k] (S symmetric)
-      sep_transform(W, tab, fs + ja * nk, jb - ja, [&](int j, int n, float v) {
+      sep_transform(W, fs + ja * nk, jb - ja, tpart, [&](int j, int n, float v) {
         zs[(size_t)(ja + j) * nk + n] = (double)v * unscale;
       });
       __syncthreads();
@@ -1496,19 +1526,25 @@ constexpr int kSepMaxBlocks = 256;
 
 static int sep_smem(const PoissonWork& w);
 
-// every boundary node a conductor, and the column phase's staging of
-// kSepModes columns fits in shared memory
+// row stride of the transform matrix (float4 rows)
+static int sep_ld(int nk) { return (nk + 3) & ~3; }
+
+// every boundary node a conductor, the column phase's staging of
+// kSepModes columns fits in shared memory, and a block's threads cover the
+// transform's float4 columns
 bool poisson_sep_possible(const PoissonWork* pw) {
   if (has_lines(*pw) || pw->nz < 3) return false;
   PoissonWork w = *pw;
   w.nk = w.nz - 1;
+  w.ldS = sep_ld(w.nk);
+  if (w.ldS / 4 > kPoisThreads) return false;
   w.rows_per_block = 1;
   return sep_smem(w) <= (int)kSmemBudget;
 }
 
 size_t poisson_sep_bytes(int nr, int nz) {
   const size_t nk = (size_t)(nz - 1);
-  return round256((size_t)2 * nz * 4) + 3 * round256((size_t)nr * nk * 4) +
+  return round256(nk * (size_t)sep_ld((int)nk) * 4) + 3 * round256((size_t)nr * nk * 4) +
          round256((size_t)nr * 4);
 }
 
@@ -1519,10 +1555,10 @@ static void sep_rows_per_block(PoissonWork& w, int blocks) {
 
 static int sep_smem(const PoissonWork& w) {
   const size_t R = (size_t)w.rows_per_block, nk = (size_t)w.nk;
-  const size_t rows = (R + 2) * nk * 8 + R * nk * 8 + (R + 2) * nk * 4;
+  const size_t rows = (R + 2) * nk * 8 + R * nk * 8 + (R + 2) * nk * 4 + 16 +
+                      (size_t)16 * kPoisThreads * 4;
   const size_t cols = (3 * (size_t)w.nr * kSepModes + (size_t)w.nr) * 4;
-  return (int)(2 * (size_t)(w.nr + 1) * sizeof(double) + 2 * (size_t)w.nz * sizeof(float) +
-               (rows > cols ? rows : cols));
+  return (int)(2 * (size_t)(w.nr + 1) * sizeof(double) + (rows > cols ? rows : cols));
 }
 
 cudaError_t poisson_sep_attach(PoissonWork* pw, void* base, int num_sms, cudaStream_t st) {
@@ -1535,16 +1571,21 @@ cudaError_t poisson_sep_attach(PoissonWork* pw, void* base, int num_sms, cudaStr
     p += round256(b);
     return (float*)q;
   };
-  w.sTab = take((size_t)2 * w.nz * 4);
+  w.ldS = sep_ld(nk);
+  w.sMat = take((size_t)nk * w.ldS * 4);
   w.sW = take((size_t)nr * nk * 4);
   w.sC = take((size_t)nr * nk * 4);
   w.sHat = take((size_t)nr * nk * 4);
   w.sE = take((size_t)nr * 4);
   // tables in FP64 on the host, stored in FP32; couplings scaled by
   // 1 / (2 pi eps0) like the multigrid tables
-  std::vector<float> S((size_t)2 * w.nz), Wt((size_t)nr * nk), Ct((size_t)nr * nk), E(nr);
+  std::vector<float> S((size_t)nk * w.ldS, 0.0f), Wt((size_t)nr * nk), Ct((size_t)nr * nk), E(nr);
   const double norm = std::sqrt(2.0 / w.nz);
-  for (int a = 0; a < 2 * w.nz; ++a) S[a] = (float)(norm * std::sin(kPi * (double)a / w.nz));
+  for (int n = 0; n < nk; ++n)
+    for (int k = 0; k < nk; ++k) {
+      const long long a = (long long)(n + 1) * (k + 1) % (2LL * w.nz);   // exact argument
+      S[(size_t)n * w.ldS + k] = (float)(norm * std::sin(kPi * (double)a / w.nz));
+    }
   std::vector<double> az(nr), ar(nr);
   for (int m = 0; m < nr; ++m) {
     az[m] = m == 0 ? w.dr * w.dr / (8.0 * w.dz) : m * w.dr * w.dr / w.dz;
@@ -1564,7 +1605,7 @@ cudaError_t poisson_sep_attach(PoissonWork* pw, void* base, int num_sms, cudaStr
       cprev = cm;
     }
   }
-  cudaError_t e = cudaMemcpyAsync(w.sTab, S.data(), S.size() * 4, cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaMemcpyAsync(w.sMat, S.data(), S.size() * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(w.sW, Wt.data(), Wt.size() * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(w.sC, Ct.data(), Ct.size() * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(w.sE, E.data(), E.size() * 4, cudaMemcpyHostToDevice, st);
@@ -1587,7 +1628,7 @@ void poisson_work_free(PoissonWork* pw) { delete pw; }
 
 cudaError_t launch_poisson(PoissonWork* pw, const double* Q, double* phi, double tol, int max_iter,
                            int* status_dev, int* iters_dev, double* resid_dev, cudaStream_t st) {
-  if (pw->sTab) {
+  if (pw->sMat) {
     PoissonArgs a;
     a.W = *pw;
     a.Q = Q;
@@ -1625,7 +1666,7 @@ size_t poisson_args_bytes() { return sizeof(PoissonArgs); }
 // do not change over a handle's life) to d_args: n_inst * poisson_args_bytes().
 static bool group_sep(PoissonWork* const* pws, int n_inst) {
   for (int k = 0; k < n_inst; ++k)
-    if (!pws[k]->sTab) return false;
+    if (!pws[k]->sMat) return false;
   return true;
 }
 
