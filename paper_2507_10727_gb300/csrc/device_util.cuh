@@ -83,20 +83,20 @@ __device__ __forceinline__ bool run_sum4(int key, T& a, T& b, T& c, T& d) {
 
 // Bitonic sort of P (a power of two) keys with their indices, one CTA.
 static __device__ void bitonic(unsigned long long* key, unsigned int* idx, int P) {
+  const int half = P >> 1;   // compare-exchange pairs per stage, one per thread and pass
   for (int k = 2; k <= P; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const int l = i ^ j;
-        if (l > i) {
-          const bool up = (i & k) == 0;
-          const unsigned long long a = key[i], b = key[l];
-          if ((a > b) == up) {
-            key[i] = b;
-            key[l] = a;
-            const unsigned int t = idx[i];
-            idx[i] = idx[l];
-            idx[l] = t;
-          }
+      for (int q = threadIdx.x; q < half; q += blockDim.x) {
+        const int i = ((q & ~(j - 1)) << 1) | (q & (j - 1));   // pair q: (i, i + j), bit j of i clear
+        const int l = i + j;
+        const bool up = (i & k) == 0;
+        const unsigned long long a = key[i], b = key[l];
+        if ((a > b) == up) {
+          key[i] = b;
+          key[l] = a;
+          const unsigned int t = idx[i];
+          idx[i] = idx[l];
+          idx[l] = t;
         }
       }
       __syncthreads();

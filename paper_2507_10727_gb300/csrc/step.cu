@@ -691,9 +691,10 @@ __device__ __forceinline__ void k_births_sort_body(const Inst& I) {
   unsigned long long* key = reinterpret_cast<unsigned long long*>(bsm);
   unsigned int* idx = reinterpret_cast<unsigned int*>(key + kBirthChunk);
   const long long c0 = (long long)blockIdx.x * kBirthChunk;
-  for (int sp = 0; sp < 2; ++sp) {
+  {
+    const int sp = blockIdx.y;                       // the species' chunks sort side by side
     const long long nb = births_of(I, sp);
-    if (c0 >= nb) continue;                          // uniform over the block
+    if (c0 >= nb) return;                            // uniform over the block
     const int len = (int)(nb - c0 < kBirthChunk ? nb - c0 : kBirthChunk);
     int P = 1;
     while (P < len) P <<= 1;
@@ -781,7 +782,7 @@ cudaError_t launch_births(const Inst& I, int num_sms, cudaStream_t st) {
     attr = true;
   }
   const int chunks = (int)((I.birth_cap + kBirthChunk - 1) / kBirthChunk);
-  k_births_sort<<<chunks > 0 ? chunks : 1, 1024, kBirthSmem, st>>>(I);
+  k_births_sort<<<dim3(chunks > 0 ? chunks : 1, 2), 1024, kBirthSmem, st>>>(I);
   const long long work = 2 * I.birth_cap;
   const int blocks = (int)((work + 255) / 256 < (long long)num_sms * 4 ? (work + 255) / 256
                                                                        : (long long)num_sms * 4);
@@ -1748,7 +1749,7 @@ cudaError_t launch_post_push_batch(const Inst* d_insts, int n_inst, const BatchD
   }
   const int per = num_sms / n_inst > 0 ? num_sms / n_inst : 1;   // blocks of one instance per SM-share
   const int chunks = (int)((bd.birth_cap_max + kBirthChunk - 1) / kBirthChunk);
-  k_births_sort_b<<<dim3(chunks > 0 ? chunks : 1, 1, n_inst), 1024, kBirthSmem, st>>>(d_insts);
+  k_births_sort_b<<<dim3(chunks > 0 ? chunks : 1, 2, n_inst), 1024, kBirthSmem, st>>>(d_insts);
   const int rank_blocks = grid_for(2 * bd.birth_cap_max, 256, per, 4);
   if (bd.prec32) k_births_rank_b<true><<<dim3(rank_blocks, 1, n_inst), 256, 0, st>>>(d_insts);
   else k_births_rank_b<false><<<dim3(rank_blocks, 1, n_inst), 256, 0, st>>>(d_insts);
