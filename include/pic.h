@@ -85,7 +85,11 @@ typedef struct pic_config {
   int32_t precision;         /* 0: FP64 particles; 1: FP32 particles (cell index + FP32 offsets,
                                 FP32 push/deposit, FP64 field solve, circuit and reductions) */
   int32_t mcc_on, push_on, field_on, walls_reflect; /* 1,1,1,0 for the physical model */
-  uint64_t seed;             /* Philox key word 0 */
+  uint64_t seed;             /* random-number key: word 0 of the Philox4x64-10 key of the
+                                collision, emission and re-weighting draws (key word 1 the
+                                species); the two 32-bit halves of the Philox4x32-10 key of
+                                the null-collision candidate draw (counter: id and step as
+                                32-bit halves, low first) */
   double sigma_el;           /* elastic cross section (m^2) */
   double ion_a, ion_I;       /* ionization: sigma = ion_a ln(E/I)/(E I) (m^2 eV^2, eV) */
   double exc_C, exc_E;       /* excitation: sigma = exc_C ln(E/E_x)/(E E_x) (m^2 eV^2, eV) */
