@@ -620,14 +620,14 @@ def test_sine_transform_and_multigrid_preconditioners_agree(pg, gather):
         pg.pic_destroy(h)
 
 
-@pytest.mark.parametrize("nr, nz", [(256, 256), (256, 512), (128, 128), (20, 36), (24, 65),
-                                    (37, 49)])
+@pytest.mark.parametrize("nr, nz", [(256, 256), (256, 512), (128, 128), (20, 36), (320, 64),
+                                    (40, 26)])
 def test_sine_transform_solve_fields(pg, nr, nz):
     """pic_solve_fields on the sine-transform preconditioner against the
-    oracle's banded Cholesky solve, on the benchmark grids and ragged ones: the
-    transform's rows of nz - 1 modes padded to a multiple of 4 (255, 511, 127,
-    35) or not (64, 48), n-range parts that do not fill the block (35, 48
-    modes), an odd row count."""
+    oracle's banded Cholesky solve, on the benchmark grids and ragged ones:
+    three rows per block with a shorter last block (320 rows over at most one
+    block per SM), transform rows of 7 or 9 float4 columns whose n-range parts
+    leave threads of the block idle (25 and 35 modes)."""
     p = pic_inputs.params_rz256()
     p.update(nr=nr, nz=nz, L=p["R"] * nz / nr, poisson_tol=1e-13)
     p, parts = pic_inputs.grown_ring_state(p, 20 * nr * nz, seed=nr + nz)

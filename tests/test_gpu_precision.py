@@ -68,7 +68,12 @@ def test_ec_bounded_mc_heats(pg, precision):
 
 
 def test_fp32_discharge_statistics_match_fp64(pg):
-    keys = ("I_cath", "W_field", "K_e", "K_i", "N_e", "N_i", "n_e_peak", "n_i_peak")
+    """Time averages of the FP32 mode against FP64 on the same seeds, 3 %.  The
+    single-node peak densities are left out here: at a few macroparticles per
+    axis node they are sampling noise; the peak densities of 7 x 7 node
+    neighbourhoods are compared at 3 % against the oracle over 64 seeds, in
+    both modes, by test_gpu_steady."""
+    keys = ("I_cath", "W_field", "K_e", "K_i", "N_e", "N_i")
     means = {}
     for precision in (0, 1):
         acc = {k: [] for k in keys}
@@ -85,5 +90,4 @@ def test_fp32_discharge_statistics_match_fp64(pg):
     rel = {k: (means[1][k] - means[0][k]) / abs(means[0][k]) for k in keys}
     print("FP32 vs FP64 time averages:", {k: round(v, 4) for k, v in rel.items()})
     for k in keys:
-        bar = 0.30 if k.endswith("peak") else 0.03
-        assert abs(rel[k]) <= bar, (k, rel[k])
+        assert abs(rel[k]) <= 0.03, (k, rel[k])

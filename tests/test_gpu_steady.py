@@ -3,9 +3,9 @@ two trends the paper reports (Sections 4-7, Table 1).
 
 1. Agreement over seeds: the 32 x 32 discharge with the external circuit
    (pic_inputs.steady_cfg1L: V_s = 400 V, R_ext = 200 Ohm, 1e5 steps of 50 ps,
-   64 seeds run as one 64-instance ensemble) averaged over the second half
-   exactly as tests/golden/make_steady_state.py averages the oracle's runs of
-   the same seeds.  The seed-mean cathode current, cathode potential and peak
+   64 seeds run as one 64-instance ensemble, in FP64 and in the FP32 mode)
+   averaged over the second half exactly as tests/golden/make_steady_state.py
+   averages the oracle's runs of the same seeds.  The seed-mean cathode current, cathode potential and peak
    electron and ion densities (the largest time-averaged density of a 7 x 7
    node neighbourhood) agree within 3 %.  With these stand-in inputs the
    plasma is not self-sustained: it decays (the macroparticle count halves in
@@ -99,10 +99,13 @@ def _ensemble_averages(pg, insts, steps, window, every, densities=False):
     return out
 
 
-def test_long_run_statistics_match_the_oracle_over_seeds(pg):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_long_run_statistics_match_the_oracle_over_seeds(pg, precision):
+    """precision 0: the FP64 particle path; 1: the FP32 mode (push, gather,
+    deposit and MCC in FP32), against the same FP64 oracle runs."""
     gold = np.loadtxt(GOLDEN)
     seeds = gold[:, 0].astype(int)
-    insts = [pic_inputs.steady_cfg1L(int(s)) for s in seeds]
+    insts = [pic_inputs.steady_cfg1L(int(s), precision=precision) for s in seeds]
     g = _ensemble_averages(pg, insts, pic_inputs.STEADY_STEPS, pic_inputs.STEADY_WINDOW,
                            pic_inputs.STEADY_EVERY, densities=True)
     cols = {"I": 1, "V": 2, "N_e": 3, "N_i": 4, "peak_ne": 5, "peak_ni": 6}
@@ -110,7 +113,8 @@ def test_long_run_statistics_match_the_oracle_over_seeds(pg):
     for key, c in cols.items():
         a, b = g[key].mean(), gold[:, c].mean()
         rel[key] = (a - b) / abs(b)
-    print("GPU vs oracle, seed means (relative):", {k: round(v, 4) for k, v in rel.items()})
+    print(f"GPU (precision {precision}) vs oracle, seed means (relative):",
+          {k: round(v, 4) for k, v in rel.items()})
     print("oracle seed spread (relative std):",
           {k: round(gold[:, c].std() / abs(gold[:, c].mean()), 4) for k, c in cols.items()})
     for key in ("I", "V", "peak_ne", "peak_ni"):
