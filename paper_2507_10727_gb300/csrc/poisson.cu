@@ -180,28 +180,37 @@ static void layout(PoissonWork& w, void* base, int nr, int nz, double R, double 
 // contend with the arrivals.
 constexpr int kBarGen = 32;   // bar[0]: arrivals, bar[kBarGen]: generation
 
+// The block's writes are ordered before its arrival by the CTA barrier and
+// the arrival's release; the last arrival's release of the generation word,
+// read with acquire by the waiting blocks, orders every block's writes before
+// what the waiters do after the barrier (acquire/release at GPU scope instead
+// of sequentially consistent fences).
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ bool barrier_grid(unsigned int* bar, int* status, int nb) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = bar + kBarGen;
-    const unsigned int g = *vgen;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(bar, 1u);
+    const unsigned int g = ld_acquire_gpu(bar + kBarGen);
+    unsigned int arrived;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(bar) : "memory");
     if (arrived == (unsigned)nb - 1u) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + kBarGen, 1u);
+      // every block has arrived, none arrives again before the generation moves
+      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + kBarGen) : "memory");
     } else {
       const double t0 = global_time_ns();
       unsigned int spins = 0;
-      while (*vgen == g) {
+      while (ld_acquire_gpu(bar + kBarGen) == g) {
         if ((++spins & 255u) == 0u && global_time_ns() - t0 > kBarrierLimitNs) {
           atomicOr(status, ST_TIMEOUT);
           break;
         }
       }
     }
-    __threadfence();
   }
   __syncthreads();
   return (*(volatile int*)status & ST_TIMEOUT) == 0;
