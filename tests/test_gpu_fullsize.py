@@ -13,7 +13,8 @@ take on the benchmark's workloads; these do:
   makes chunks span many tiles, so the deposit patch spills to global atomics),
   the extrapolated Poisson start -- FP64 EC and MC at 1e-12, FP32 at 1e-5;
 * the 16-instance 128 x 128 gamma x R_ext sweep with uneven counts
-  (2e4 - 2e5 per species) under CUDA-graph replay;
+  (2e4 - 2e5 per species, and the benchmark's 1e6 - 8e6) under CUDA-graph
+  replay;
 * one step on the 256 x 512 grid of the learned warm-start workload;
 * the benchmark's own size, 4e7 per species on 256 x 256, in its launch
   configuration (32 particles per thread, 8 x 8 tiles), FP64 and FP32, the
@@ -210,6 +211,38 @@ def test_sweep16_ensemble_uneven_counts_graph_replay(pg):
             for k, orc in enumerate(orcs):
                 orc.step(1)
                 check_step64(pg, h, orc, instance=k)
+        pg.pic_destroy(h)
+    side.synchronize()
+
+
+def test_sweep16_ensemble_bench_sizes(pg):
+    """The sweep at the benchmark's sizes: 16 discharges of 128 x 128 cells with
+    1e6 8^(k/15) macroparticles per species (1e6 .. 8e6, 1.1e8 in all, shuffled
+    over the gamma x R_ext grid), the push at 32 particles per thread, stepped
+    by graph replay through the step that ends with the full sort and the one
+    after it; every instance against its own oracle after each step."""
+    import torch
+    plist = pic_inputs.params_rz128_sweep()
+    sizes = [int(1e6 * 8.0 ** (k / 15.0)) for k in range(16)]
+    np.random.default_rng(5).shuffle(sizes)
+    insts = []
+    for k, p in enumerate(plist):
+        p.update(poisson_tol=1e-13, sort_every=32, phi_extrapolate=1)
+        insts.append(_ring(p, sizes[k], seed=31 * k))
+    orcs = [oracle.Oracle(p, parts) for p, parts in insts]
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        h = pg.pic_create([p for p, _ in insts])
+        for k, ((p, parts), orc) in enumerate(zip(insts, orcs)):
+            _start(pg, h, orc, parts, k=k, step=31)
+        pg.pic_set_chunk(h, 32)
+        for step in (31, 32):   # ends with the full sort, then in place
+            pg.pic_step(h, 1)
+            assert pg.pic_uses_graph(h)
+            for k, orc in enumerate(orcs):
+                orc.step(1)
+                d = check_step64(pg, h, orc, instance=k)
+                assert d["step"] == step
         pg.pic_destroy(h)
     side.synchronize()
 
