@@ -353,7 +353,7 @@ __device__ __forceinline__ void warp_flush64(const Inst& I, bool fl, int key, in
 // with the candidates packed onto consecutive lanes (a warp that met one
 // candidate inside the loop would run the whole collision for one lane).
 // Returns this thread's share of the kinetic energy (diagnostic steps only).
-template <int SP, int GATHER>
+template <int SP, int GATHER, bool PLAIN>
 __device__ __forceinline__ double push_chunk64(const Inst& I, long long c0, int ppt,
                                                unsigned long long* patch, int* cpatch, int* anchor,
                                                int* cq) {
@@ -399,7 +399,7 @@ __device__ __forceinline__ double push_chunk64(const Inst& I, long long c0, int 
         double r = P.r[i], z = P.z[i], vr = P.vr[i], vt = P.vt[i], vz = P.vz[i];
         const double v2old = vr * vr + vt * vt + vz * vz;
         double x1 = r, y1 = 0.0, r1 = r, z1 = z;
-        if (I.push_on) {
+        if (PLAIN || I.push_on) {
           int m, nn;
           double fr, fz;
           split_cell(r, I.nr, m, fr);
@@ -409,12 +409,12 @@ __device__ __forceinline__ double push_chunk64(const Inst& I, long long c0, int 
           double hEr, hEz;
           if (GATHER == 0) {
             const double4_32a t = etab[ck];
-            const double wr = rweight_upper(I, r, m, fr);
+            const double wr = PLAIN ? fr : rweight_upper(I, r, m, fr);
             hEr = t.x + t.y * fz;
-            if (I.rweight == 1) hEr *= r;
+            if (!PLAIN && I.rweight == 1) hEr *= r;
             hEz = t.z + t.w * wr;
           } else {
-            const double wr = rweight_upper(I, r, m, fr);
+            const double wr = PLAIN ? fr : rweight_upper(I, r, m, fr);
             const double4_32a a = etab[2 * ck];
             const double4_32a b = etab[2 * ck + 1];
             hEr = a.x + wr * (a.y + fz * a.w) + fz * a.z;
@@ -455,7 +455,7 @@ __device__ __forceinline__ double push_chunk64(const Inst& I, long long c0, int 
         if (diag) Kloc += 0.5 * I.mass[SP] * I.weight * 0.5 * (v2old + vr * vr + vt * vt + vz * vz);
         bool alive = true;
         const double Lc = (double)I.nz, Rw = (double)I.nr;   // z = L, r = R in cell units
-        if (I.walls_reflect) {
+        if (!PLAIN && I.walls_reflect) {
           if (z1 < 0.0) { z1 = -z1; vz = -vz; }
           if (z1 >= Lc) { z1 = 2.0 * Lc - z1; vz = -vz; if (z1 >= Lc) z1 = nextafter(Lc, 0.0); }
           if (r1 >= Rw) { r1 = 2.0 * Rw - r1; vr = -vr; if (r1 >= Rw) r1 = nextafter(Rw, 0.0); }
@@ -512,7 +512,7 @@ __device__ __forceinline__ double push_chunk64(const Inst& I, long long c0, int 
           P.r[i] = r1; P.z[i] = z1; P.vr[i] = vr; P.vt[i] = vt; P.vz[i] = vz;
           // deposit weights of x^{n+1} (Section 2: tent functions), summed per
           // cell; a lane whose cell changes flushes its open sums below
-          fix_parts(rweight_upper(I, r1, m1, fr1), fz1, ir, iz, i11);
+          fix_parts(PLAIN ? fr1 : rweight_upper(I, r1, m1, fr1), fz1, ir, iz, i11);
           add = true;
           nm = m1;
           nn1 = n1;
@@ -577,7 +577,7 @@ __device__ __forceinline__ double push_chunk64(const Inst& I, long long c0, int 
 // The push of both species of every instance: persistent CTAs take (instance,
 // species, chunk) items from the work queue; an instance's parameters are
 // staged in shared memory when a CTA moves to it.
-template <int GATHER>
+template <int GATHER, bool PLAIN>
 __global__ void __launch_bounds__(kPushThreads, 2) k_push_all(const Inst* insts, WorkQueue* q,
                                                                int ppt) {
   __shared__ unsigned long long patch[kPatchNodes];
@@ -621,8 +621,8 @@ __global__ void __launch_bounds__(kPushThreads, 2) k_push_all(const Inst* insts,
       cur = inst;
     }
     if (!s_skip) {
-      if (s_sp == 0) K0 += push_chunk64<0, GATHER>(sI, s_c0, ppt, patch, cpatch, anchor, cq);
-      else K1 += push_chunk64<1, GATHER>(sI, s_c0, ppt, patch, cpatch, anchor, cq);
+      if (s_sp == 0) K0 += push_chunk64<0, GATHER, PLAIN>(sI, s_c0, ppt, patch, cpatch, anchor, cq);
+      else K1 += push_chunk64<1, GATHER, PLAIN>(sI, s_c0, ppt, patch, cpatch, anchor, cq);
     }
     __syncthreads();
   }
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(kPushThreads, 2) k_push_all(const Inst* insts,
 // The FP64 push of a single-instance handle: the instance's parameters are a
 // kernel argument (constant-bank operands in the particle loop instead of
 // shared-memory loads); otherwise k_push_all.
-template <int GATHER>
+template <int GATHER, bool PLAIN>
 __global__ void __launch_bounds__(kPushThreads, 2) k_push_one(const Inst I, WorkQueue* q,
                                                                int ppt) {
   __shared__ unsigned long long patch[kPatchNodes];
@@ -657,8 +657,8 @@ __global__ void __launch_bounds__(kPushThreads, 2) k_push_one(const Inst I, Work
     __syncthreads();
     if (s_done) break;
     if (!s_skip) {
-      if (s_sp == 0) K0 += push_chunk64<0, GATHER>(I, s_c0, ppt, patch, cpatch, anchor, cq);
-      else K1 += push_chunk64<1, GATHER>(I, s_c0, ppt, patch, cpatch, anchor, cq);
+      if (s_sp == 0) K0 += push_chunk64<0, GATHER, PLAIN>(I, s_c0, ppt, patch, cpatch, anchor, cq);
+      else K1 += push_chunk64<1, GATHER, PLAIN>(I, s_c0, ppt, patch, cpatch, anchor, cq);
     }
     __syncthreads();
   }
@@ -1544,14 +1544,31 @@ cudaError_t launch_queue_setup(const Inst* d_insts, WorkQueue* q, int n_inst, lo
   return cudaGetLastError();
 }
 
+template <int GATHER, bool PLAIN>
+static void push_one(const Inst& I, WorkQueue* q, int ppt, int num_sms, cudaStream_t st) {
+  k_push_one<GATHER, PLAIN><<<resident_blocks((const void*)k_push_one<GATHER, PLAIN>,
+                                              kPushThreads, num_sms),
+                              kPushThreads, 0, st>>>(I, q, ppt);
+}
+
+template <int GATHER, bool PLAIN>
+static void push_all(const Inst* d_insts, WorkQueue* q, int ppt, int num_sms, cudaStream_t st) {
+  k_push_all<GATHER, PLAIN><<<resident_blocks((const void*)k_push_all<GATHER, PLAIN>,
+                                              kPushThreads, num_sms),
+                              kPushThreads, 0, st>>>(d_insts, q, ppt);
+}
+
 cudaError_t launch_push_one(const Inst& I, WorkQueue* q, int ppt, int num_sms, cudaStream_t st) {
   if (I.prec32) return launch_push32_one(I, q, ppt, num_sms, st);
-  if (I.gather == 0)
-    k_push_one<0><<<resident_blocks((const void*)k_push_one<0>, kPushThreads, num_sms),
-                    kPushThreads, 0, st>>>(I, q, ppt);
-  else
-    k_push_one<1><<<resident_blocks((const void*)k_push_one<1>, kPushThreads, num_sms),
-                    kPushThreads, 0, st>>>(I, q, ppt);
+  // plain: the model's own switches (push on, tent weights in r, absorbing walls)
+  const bool plain = I.push_on && I.rweight == 0 && !I.walls_reflect;
+  if (I.gather == 0) {
+    if (plain) push_one<0, true>(I, q, ppt, num_sms, st);
+    else push_one<0, false>(I, q, ppt, num_sms, st);
+  } else {
+    if (plain) push_one<1, true>(I, q, ppt, num_sms, st);
+    else push_one<1, false>(I, q, ppt, num_sms, st);
+  }
   return cudaGetLastError();
 }
 
@@ -1560,10 +1577,13 @@ cudaError_t launch_push_all(const Inst* d_insts, WorkQueue* q, int prec32, int g
   // a thread's queue-overflow candidates are a 32-bit mask over its chunk slots
   if (ppt < 1 || ppt > 32) return cudaErrorInvalidValue;
   if (prec32) return launch_push32_all(d_insts, q, gather, plain, ppt, num_sms, st);
-  if (gather == 0)
-    k_push_all<0><<<resident_blocks((const void*)k_push_all<0>, kPushThreads, num_sms), kPushThreads, 0, st>>>(d_insts, q, ppt);
-  else
-    k_push_all<1><<<resident_blocks((const void*)k_push_all<1>, kPushThreads, num_sms), kPushThreads, 0, st>>>(d_insts, q, ppt);
+  if (gather == 0) {
+    if (plain) push_all<0, true>(d_insts, q, ppt, num_sms, st);
+    else push_all<0, false>(d_insts, q, ppt, num_sms, st);
+  } else {
+    if (plain) push_all<1, true>(d_insts, q, ppt, num_sms, st);
+    else push_all<1, false>(d_insts, q, ppt, num_sms, st);
+  }
   return cudaGetLastError();
 }
 
